@@ -1,0 +1,163 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module only builds inputs: mesh node coordinates, boundary conditions,
+discrete velocity grids (nodes and quadrature weights), gas parameters and
+initial macroscopic states.  It holds none of the solver's arithmetic, and both
+the CUDA library and the CPU oracle consume what it returns.
+
+Units are those of the solver: lengths in L, velocities in v0 = sqrt(2 R T0),
+density in rho0 and temperature in T0.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+WALL, PERIODIC = 1, 2
+SHAKHOV, RYKOV = 0, 1
+# Nitrogen relaxation data of Section 5 (d_r = 2, omega = 0.74, A = Att, Atr, Art, Arr).
+N2_A = (0.786, -0.201, -0.059, 0.842)
+
+
+@dataclass
+class Problem:
+    ni: int
+    nj: int
+    nk: int
+    nodes: np.ndarray            # (nk+1, nj+1, ni+1, 3) float64, i fastest in memory
+    bc: list                     # 6 ints: x-, x+, y-, y+, z-, z+
+    wall_u: np.ndarray           # (6, 3)
+    wall_T: np.ndarray           # (6,)
+    vx: np.ndarray
+    vy: np.ndarray
+    vz: np.ndarray
+    wx: np.ndarray
+    wy: np.ndarray
+    wz: np.ndarray
+    model: int = SHAKHOV
+    omega: float = 0.81
+    Kn: float = 0.1
+    d_r: float = 0.0
+    Z_r: float = 1.0
+    A: tuple = (2.0 / 3.0, 0.0, 0.0, 1.0)
+    W0: np.ndarray = field(default=None)   # (ncells, 6): rho, ux, uy, uz, Tt, Tr
+    name: str = ""
+
+    @property
+    def ncells(self) -> int:
+        return self.ni * self.nj * self.nk
+
+    @property
+    def nvel(self) -> int:
+        return len(self.vx) * len(self.vy) * len(self.vz)
+
+
+def midpoint_grid(n: int, lo: float, hi: float):
+    """Uniform midpoint nodes and equal weights on [lo, hi]."""
+    d = (hi - lo) / n
+    x = lo + (np.arange(n) + 0.5) * d
+    return x.astype(np.float64), np.full(n, d, dtype=np.float64)
+
+
+def box_nodes(xs, ys, zs) -> np.ndarray:
+    """Rectilinear node coordinates from per-axis node positions."""
+    zz, yy, xx = np.meshgrid(np.asarray(zs, float), np.asarray(ys, float), np.asarray(xs, float), indexing="ij")
+    return np.ascontiguousarray(np.stack([xx, yy, zz], axis=-1))
+
+
+def _uniform_state(nc, rho=1.0, u=(0.0, 0.0, 0.0), Tt=1.0, Tr=1.0):
+    W = np.zeros((nc, 6))
+    W[:, 0] = rho
+    W[:, 1:4] = u
+    W[:, 4] = Tt
+    W[:, 5] = Tr
+    return W
+
+
+def couette(n_cells=100, nv=24, vmax=5.0, U=0.2, Kn=0.1, omega=0.81, Tw=(1.0, 1.0)) -> Problem:
+    """Planar Couette flow: plates at x = 0 and x = 1 moving at -U and +U along y, diffuse at Tw."""
+    dx = 1.0 / n_cells
+    nodes = box_nodes(np.linspace(0.0, 1.0, n_cells + 1), [0.0, dx], [0.0, dx])
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[0, 1] = -U
+    wall_u[1, 1] = U
+    wall_T = np.ones(6)
+    wall_T[0], wall_T[1] = Tw
+    return Problem(n_cells, 1, 1, nodes, [WALL, WALL, PERIODIC, PERIODIC, PERIODIC, PERIODIC], wall_u, wall_T,
+                   v, v.copy(), v.copy(), w, w.copy(), w.copy(), SHAKHOV, omega, Kn,
+                   W0=_uniform_state(n_cells), name=f"couette{n_cells}x{nv}^3")
+
+
+def cavity(n=128, nv=32, vmax=5.0, lid=0.16, Kn=0.1, omega=0.81, stretch=0.0) -> Problem:
+    """Lid-driven square cavity [0,1]^2: lid y = 1 moves at +lid along x, all walls at T = 1.
+
+    stretch > 0 clusters cells towards the walls (tanh spacing); 0 gives a uniform grid.
+    """
+    s = np.linspace(0.0, 1.0, n + 1)
+    if stretch > 0:
+        s = 0.5 * (1.0 + np.tanh(stretch * (2.0 * s - 1.0)) / np.tanh(stretch))
+    dz = 1.0 / n
+    nodes = box_nodes(s, s, [0.0, dz])
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[3, 0] = lid
+    return Problem(n, n, 1, nodes, [WALL, WALL, WALL, WALL, PERIODIC, PERIODIC], wall_u, np.ones(6),
+                   v, v.copy(), v.copy(), w, w.copy(), w.copy(), SHAKHOV, omega, Kn,
+                   W0=_uniform_state(n * n), name=f"cavity{n}^2x{nv}^3_Kn{Kn:g}")
+
+
+def box3d(ni=6, nj=5, nk=4, nv=12, vmax=5.0, Kn=0.1, omega=0.81, wall_speed=0.2) -> Problem:
+    """Small closed 3D box with one moving wall (z+ moves along x); all walls diffuse at T = 1."""
+    nodes = box_nodes(np.linspace(0, 1, ni + 1), np.linspace(0, 0.8, nj + 1), np.linspace(0, 0.6, nk + 1))
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[5, 0] = wall_speed
+    return Problem(ni, nj, nk, nodes, [WALL] * 6, wall_u, np.ones(6), v, v.copy(), v.copy(), w, w.copy(), w.copy(),
+                   SHAKHOV, omega, Kn, W0=_uniform_state(ni * nj * nk), name=f"box{ni}x{nj}x{nk}")
+
+
+def as_rykov(p: Problem, d_r=2.0, Z_r=5.0, A=N2_A, omega=0.74) -> Problem:
+    """The same geometry with the diatomic Rykov-type gas of Section 2.2 (nitrogen data of Section 5)."""
+    p.model, p.d_r, p.Z_r, p.A, p.omega = RYKOV, d_r, Z_r, tuple(A), omega
+    p.name += "_rykov"
+    return p
+
+
+def perturbed_state(p: Problem, seed=0, amp=0.05) -> np.ndarray:
+    """Seeded smooth perturbation of the uniform initial state (rho, u, Tt, Tr per cell)."""
+    rng = np.random.default_rng(seed)
+    W = p.W0.copy()
+    nc = p.ncells
+    W[:, 0] *= 1.0 + amp * rng.uniform(-1, 1, nc)
+    W[:, 1:4] += amp * rng.uniform(-1, 1, (nc, 3))
+    W[:, 4] *= 1.0 + amp * rng.uniform(-1, 1, nc)
+    W[:, 5] *= 1.0 + amp * rng.uniform(-1, 1, nc)
+    return W
+
+
+def random_vdf(p: Problem, seed=0, amp=0.1, W=None):
+    """Seeded non-equilibrium VDFs [cell][v] (v = ix + nx (iy + ny iz)): a local
+    Maxwellian-shaped envelope times a random positive modulation.
+
+    The envelope is written out here only to make positive, decaying test data; it is
+    an input recipe, not the solver's equilibrium routine.
+    """
+    rng = np.random.default_rng(seed)
+    W = p.W0 if W is None else W
+    VX, VY, VZ = np.meshgrid(p.vx, p.vy, p.vz, indexing="ij")
+    # flatten with ix fastest: transpose (iz, iy, ix)
+    X = VX.transpose(2, 1, 0).ravel()
+    Y = VY.transpose(2, 1, 0).ravel()
+    Z = VZ.transpose(2, 1, 0).ravel()
+    nc, nv = p.ncells, p.nvel
+    f0 = np.empty((nc, nv))
+    for c in range(nc):
+        rho, ux, uy, uz, T = W[c, 0], W[c, 1], W[c, 2], W[c, 3], W[c, 4]
+        env = rho * (np.pi * T) ** -1.5 * np.exp(-((X - ux) ** 2 + (Y - uy) ** 2 + (Z - uz) ** 2) / T)
+        f0[c] = env * (1.0 + amp * rng.uniform(-1, 1, nv))
+    f1 = None
+    if p.model == RYKOV:
+        f1 = f0 * (p.d_r * W[:, 5:6] / 4.0) * (1.0 + amp * rng.uniform(-1, 1, (nc, nv)))
+    return f0, f1

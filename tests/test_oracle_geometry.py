@@ -1,0 +1,71 @@
+"""Pins of the oracle's finite-volume geometry, LSQ gradient and limiter."""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2310_18916_gb300 import workloads as wl
+
+
+def _skewed(ni=5, nj=4, nk=3):
+    """A box mapped by a constant shear (determinant 1): every cell is the same parallelepiped."""
+    p = wl.box3d(ni, nj, nk, nv=4)
+    X = p.nodes.copy()
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    p.nodes = np.ascontiguousarray(np.stack([x + 0.3 * y + 0.1 * z, y + 0.2 * z, z], -1))
+    J = np.array([[1, 0.3, 0.1], [0, 1, 0.2], [0, 0, 1]])
+    return p, J
+
+
+def test_rectilinear_volumes_and_closed_faces():
+    p = wl.cavity(n=6, nv=4, stretch=1.5)
+    o = Oracle(p, mode=1)
+    vol, xc, S, xf = o.geometry()
+    xs = p.nodes[0, 0, :, 0]
+    dz = p.nodes[1, 0, 0, 2] - p.nodes[0, 0, 0, 2]
+    expect = np.outer(np.diff(xs), np.diff(xs)).ravel() * dz   # cells ordered i fastest (j outer)
+    np.testing.assert_allclose(vol, expect, rtol=1e-13)
+    assert vol.sum() == pytest.approx(1.0 * 1.0 * dz, rel=1e-13)
+
+
+def test_skewed_geometry_parallelepiped():
+    p, J = _skewed()
+    o = Oracle(p, mode=1)
+    vol, xc, S, xf = o.geometry()
+    h = np.array([1 / 5, 0.8 / 4, 0.6 / 3])
+    np.testing.assert_allclose(vol, np.linalg.det(J) * h.prod(), rtol=1e-12)
+    # geometric conservation: the closed surface of every cell sums to zero
+    assert np.abs(S.sum(axis=1)).max() < 1e-15
+    # outward: S . (x_f - x_c) > 0 on every face
+    assert ((S * (xf - xc[:, None, :])).sum(-1) > 0).all()
+    # face area vector of an x-face = (e_y x e_z) of the mapped cell
+    ey, ez = J[:, 1] * h[1], J[:, 2] * h[2]
+    np.testing.assert_allclose(S[0, 1], np.cross(ey, ez), rtol=1e-12)
+
+
+def test_lsq_gradient_exact_for_linear_fields_on_skewed_mesh():
+    p, J = _skewed()
+    o = Oracle(p, mode=1)
+    _, xc, _, _ = o.geometry()
+    a = np.array([0.7, -1.3, 2.1])
+    q = 0.4 + xc @ a
+    for c in range(o.nc):
+        np.testing.assert_allclose(o.cell_gradient(c, q), a, rtol=1e-10, atol=1e-12)
+
+
+def test_limiter_is_one_for_linear_data_and_small_at_extrema():
+    p = wl.cavity(n=8, nv=4)
+    o = Oracle(p, mode=1)
+    _, xc, _, _ = o.geometry()
+    q = 1.0 + 0.5 * xc[:, 0] - 0.2 * xc[:, 1]
+    interior = [i + 8 * j for i in range(1, 7) for j in range(1, 7)]
+    for c in interior:
+        assert o.cell_limiter(c, q) == pytest.approx(1.0, abs=1e-12)
+    # a strict local maximum with a non-zero LSQ slope (east neighbour higher than the west):
+    # no face value may exceed the maximum, so the limiter nearly switches the slope off
+    q = np.zeros(o.nc)
+    q[27], q[28], q[26] = 1.0, 0.5, 0.0
+    g = o.cell_gradient(27, q)
+    assert g[0] == pytest.approx(0.25 * 8, rel=1e-13)   # (q_E - q_W) / (2 dx), dx = 1/8
+    # east face: D2 = g dx/2 = 1/8, Dm = 0; eps^2 = (K h)^3 with h = V^(1/3) = 1/8 (K = 1):
+    # phi = eps^2 / (2 D2^2 + eps^2) = (1/512) / (1/32 + 1/512) = 1/17
+    assert o.cell_limiter(27, q) == pytest.approx(1.0 / 17.0, rel=1e-12)
