@@ -1,0 +1,268 @@
+"""Benchmark: phase-space updates per second of the GSIS solver on the 2D lid-driven cavity
+(128 x 128 cells, 32^3 velocities on [-5, 5]^3 = 537M phase-space points, Kn = 0.1, lid 0.16,
+FP32 VDF storage with the FP64 synthetic NSF solve).
+
+One step = one outer GSIS iteration (Algorithm 1): wall pre-pass, fused kinetic step,
+moments, FP64 synthetic solve (300 inner steps), residual and the next state.  The VDF (2.1 GB)
+is far larger than L2 (129 MB), so no L2 flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU ("replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFG = dict(n=128, nv=32, vmax=5.0, Kn=0.1, lid=0.16)
+METRIC = "phase-space updates/s (GSIS outer step, 2D cavity)"
+UNIT = "updates/s"
+
+
+def workload_name(c=CFG):
+    return f"2D lid-driven cavity {c['n']}x{c['n']} cells, {c['nv']}^3 velocities on [-{c['vmax']},{c['vmax']}]^3, Kn={c['Kn']}, lid {c['lid']}"
+
+
+def problem(c=CFG):
+    from paper_2310_18916_gb300 import workloads as wl
+    return wl.cavity(n=c["n"], nv=c["nv"], vmax=c["vmax"], Kn=c["Kn"], lid=c["lid"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_sample(c=CFG, nv_sample=16, macro_sample=100):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the same 128^2 mesh
+    with an nv_sample^3 velocity grid (kinetic cost per phase-space point does not depend on the
+    velocity count) and macro_sample of the 300 inner synthetic steps.  Returns the estimated
+    seconds of one full outer step and a description."""
+    from oracle.oracle import Oracle
+    from paper_2310_18916_gb300 import workloads as wl
+
+    p = wl.cavity(n=c["n"], nv=nv_sample, vmax=c["vmax"], Kn=c["Kn"], lid=c["lid"])
+    o = Oracle(p, mode=0, macro_steps=macro_sample, macro_tol=0.0)
+    t0 = time.perf_counter()
+    o.wall_prepass()
+    o.kinetic_velocities(0, o.nv)
+    t1 = time.perf_counter()
+    o.macro_from_current()
+    t2 = time.perf_counter()
+    full_pts = c["n"] ** 2 * c["nv"] ** 3
+    kin_scale = c["nv"] ** 3 / o.nv
+    est = (t1 - t0) * kin_scale + (t2 - t1) * (300.0 / macro_sample)
+    desc = (f"oracle kinetic step on the {c['n']}^2 mesh with {nv_sample}^3 velocities ({t1 - t0:.2f} s, scaled x"
+            f"{kin_scale:.0f} to 32^3) + moments and {macro_sample} of 300 synthetic inner steps ({t2 - t1:.2f} s, "
+            f"scaled x{300.0 / macro_sample:.0f}); {full_pts} points per full step")
+    return est, desc, (t2 - t0)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    times, desc = [], ""
+    for i in range(args.warmup + args.steps):
+        est, desc, _ = oracle_sample(nv_sample=6, macro_sample=15)
+        if i >= args.warmup:
+            times.append(est)
+    pts = CFG["n"] ** 2 * CFG["nv"] ** 3
+    ms = 1e3 * statistics.mean(times)
+    value = pts / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(), "precision": "f64 (CPU oracle)", "parallelism": f"{cores} host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=CFG["n"], help="cells per side (profiling cases use 64)")
+    ap.add_argument("--nv", type=int, default=CFG["nv"], help="velocities per axis")
+    ap.add_argument("--kn", type=float, default=CFG["Kn"])
+    args = ap.parse_args()
+    CFG.update(n=args.n, nv=args.nv, Kn=args.kn)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2310_18916_gb300 import gsis
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = problem()
+    pts = p.ncells * p.nvel
+    s = gsis.Solver(p, precision=args.precision, mode="gsis")
+    for _ in range(args.warmup):
+        s.step()
+    s.profile(True, reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.step()
+        e1.record(stream)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    phase, nsteps, launches = s.profile(False)
+    eps = float(s.residual()[3])
+    _, macro_iters = s.stats()
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    value = world * pts * args.steps / (ms_total / 1e3)
+    kin_ms = phase[1] / max(nsteps, 1)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+
+    # end to end through the public API: create from host inputs, K steps each followed by a
+    # device->host read of the state, destroy
+    barrier()
+    t0 = time.perf_counter()
+    s2 = gsis.Solver(p, precision=args.precision, mode="gsis", kinetic_presteps=0)
+    for _ in range(args.steps):
+        s2.step()
+        W = s2.W()
+    s2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    del s2
+    h2d = p.nodes.nbytes + 6 * p.vx.nbytes + p.W0.nbytes
+    d2h = W.nbytes + 4 * 8
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = measured_peaks()
+    sbytes = 4 if args.precision == "f32" else 8
+    alg_bytes = 2 * sbytes * pts
+    achieved = alg_bytes / (kin_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": workload_name(), "precision": f"{args.precision} VDF, f64 synthetic solve",
+                   "cells": p.ncells, "velocities": p.nvel, "points": pts, "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (VDF 2.1 GB)", "macro_inner_steps": macro_iters, "eps_last": eps},
+        "phase_ms_per_step": {k: v / max(nsteps, 1) for k, v in zip(
+            ("wall_prepass", "kinetic", "reduce_moments", "synthetic_fp64", "residual_state"), phase)},
+        "kinetic_updates_per_s": pts / (kin_ms / 1e3),
+        "roofline": {"kernel": "kinetic_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": kin_ms},
+        "e2e": {"value": args.steps * pts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h, "seconds": e2e_s, "includes": "create from host inputs, steps, per-step state read, destroy"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        est, desc, wall = oracle_sample()
+        line["cpu_baseline"] = {"value": pts / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": desc, "sample_seconds": wall}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * gsis.h -- C ABI of the GB300 GSIS steady rarefied-flow solver.
+ *
+ * Method: general synthetic iterative scheme (GSIS-II) of arXiv 2310.18916,
+ * "Efficient parallel solver for rarefied gas flow using GSIS":
+ *   - kinetic step over phase space (Section 3.1, Eq. delta_equations and the
+ *     point-implicit form that follows it; Algorithm 3 body),
+ *   - velocity moments (Eq. getmoment), high-order terms (Eq. full_constitutive),
+ *   - FP64 synthetic NSF solve (Section 3.2, Eq. macro, delta_Macroscopic_equations,
+ *     res_macro; Algorithm 2 body),
+ *   - VDF correction (Eq. updatef) and residual (Eq. convergence_critertion),
+ *   - driven by the outer loop of Algorithm 1.
+ *
+ * Units (nondimensional): lengths in L, velocities in v0 = sqrt(2 R T0), density in rho0,
+ * temperature in T0 (so R T -> T/2 and the Maxwellian is rho (pi T)^(-3/2) exp(-|xi-u|^2/T)).
+ *
+ * Conventions for every entry point:
+ *   - return value: GSIS_OK (0) or a negative GSIS_E_* code; no exception crosses the ABI;
+ *     gsis_last_error() gives a one-line message for the last failure on a handle;
+ *   - pointers named host_* or documented as host point to host memory, owned by the caller
+ *     and only read/written during the call;
+ *   - all device memory is owned by the handle (allocated at gsis_create through the
+ *     caller's allocator callback, or cudaMalloc when none is given) and released by
+ *     gsis_destroy;
+ *   - one handle is used by one host thread at a time; distinct handles are independent;
+ *   - work is issued on the stream given in gsis_options (default stream when NULL);
+ *     calls that return host data synchronise that stream.
+ */
+#ifndef GSIS_H
+#define GSIS_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSIS_OK 0
+#define GSIS_E_INVALID (-1)       /* bad argument, mesh or grid */
+#define GSIS_E_OOM (-2)           /* allocation failed */
+#define GSIS_E_CUDA (-3)          /* CUDA error (message in gsis_last_error) */
+#define GSIS_E_DIVERGED (-4)      /* non-finite or non-positive density / temperature */
+#define GSIS_E_TIMEOUT (-5)       /* a bounded device-side wait gave up */
+#define GSIS_E_NOT_CONVERGED (-6) /* max_outer reached above tol; results are valid */
+#define GSIS_E_UNSUPPORTED (-7)   /* valid input outside what this build implements */
+
+enum gsis_bc_type { GSIS_BC_WALL = 1, GSIS_BC_PERIODIC = 2 };
+enum gsis_model { GSIS_SHAKHOV = 0, GSIS_RYKOV = 1 };
+enum gsis_precision { GSIS_F64 = 0, GSIS_F32 = 1 };
+enum gsis_mode { GSIS_MODE_GSIS = 0, GSIS_MODE_DVM = 1 };
+
+/* Structured hexahedral block (spatial finite-volume cells of Section 3.1).
+ * nodes: (ni+1)(nj+1)(nk+1) x 3 doubles (host), node (I,J,K) at index I + (ni+1)(J + (nj+1)K).
+ * This build requires a rectilinear block (node x depends on I only, y on J, z on K,
+ * increasing), else GSIS_E_UNSUPPORTED.
+ * bc[side], side = x-, x+, y-, y+, z-, z+: an axis with one cell must be PERIODIC on both
+ * sides (it then carries no transport); an axis with more cells must be WALL on both sides.
+ * Walls are isothermal and fully diffuse with velocity wall_u[side] (tangential) and
+ * temperature wall_T[side]. */
+typedef struct {
+  int ni, nj, nk;
+  const double *nodes;
+  int bc[6];
+  double wall_u[6][3];
+  double wall_T[6];
+} gsis_mesh;
+
+/* Tensor-product discrete velocity grid (Section 3, velocity-space discretisation):
+ * n[d] nodes x[d][.] with quadrature weights w[d][.] per axis d (host arrays, copied).
+ * The discrete velocity index used by gsis_get_f / gsis_set_f is v = ix + n0 (iy + n1 iz). */
+typedef struct {
+  int n[3];
+  const double *x[3];
+  const double *w[3];
+} gsis_vgrid;
+
+/* Gas model (Section 2): Shakhov (monatomic, Pr = 2/3; the g_0t reference distribution) or
+ * the Rykov-type model with d_r internal degrees of freedom, internal collision number Z_r
+ * and heat-flux relaxation rates A = (Att, Atr, Art, Arr).  omega: viscosity index. */
+typedef struct {
+  int model;
+  double omega;
+  double d_r, Z_r;
+  double A[4];
+} gsis_gas;
+
+/* Device allocator callback: alloc(bytes, stream, ctx) returns device memory or NULL;
+ * free(ptr, stream, ctx) releases it.  Both may be NULL (cudaMalloc / cudaFree are used). */
+typedef void *(*gsis_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*gsis_free_fn)(void *ptr, void *stream, void *ctx);
+
+/* Solver options.  Defaults (gsis_default_options): see the comments. */
+typedef struct {
+  int precision;        /* GSIS_F64 | GSIS_F32: VDF storage and kinetic arithmetic (default F32).
+                           Moments, synthetic solve, correction and residual are FP64 always. */
+  int mode;             /* GSIS_MODE_GSIS (default) or GSIS_MODE_DVM (plain kinetic iteration) */
+  int n_sweeps;         /* colour-ordered point-implicit passes per kinetic step (default 1) */
+  int macro_steps;      /* inner synthetic steps per outer step (default 300, Algorithm 1) */
+  int macro_sweeps;     /* red-black LU-SGS passes per inner step (default 4, Algorithm 2) */
+  double macro_cfl;     /* pseudo-time CFL of the synthetic solve (default 100) */
+  double macro_tol;     /* inner early exit on the relative increment (default 1e-10) */
+  double kin_inv_dt;    /* 1/dt of the kinetic delta form (default 0: steady) */
+  double venkat_K;      /* Venkatakrishnan constant, eps^2 = (K V^(1/3))^3 (default 1) */
+  int kinetic_presteps; /* plain kinetic steps before the GSIS loop (default 10, Algorithm 1) */
+  const double *init_W; /* optional host array, per cell rho, ux, uy, uz, Tt, Tr; f0 = Maxwellian.
+                           NULL: rho = 1, u = 0, Tt = Tr = 1. */
+  void *stream;         /* cudaStream_t, NULL = default stream */
+  gsis_alloc_fn alloc;
+  gsis_free_fn free;
+  void *alloc_ctx;
+} gsis_options;
+
+typedef struct gsis_solver *gsis_handle;
+
+/* Fill *opt with the defaults listed above. */
+void gsis_default_options(gsis_options *opt);
+
+/* Device bytes a solver of this size would hold (admission by memory footprint).
+ * Returns GSIS_OK and writes *bytes, or GSIS_E_INVALID / GSIS_E_UNSUPPORTED. */
+int gsis_footprint_bytes(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const gsis_gas *gas,
+                         const gsis_options *opt, size_t *bytes);
+
+/* Build a solver: copy the inputs, build geometry and velocity blocks, allocate device state,
+ * set f0 = Maxwellian(init_W) and run opt->kinetic_presteps plain kinetic steps
+ * (Algorithm 1, first line).  Kn: Knudsen number, mu(T0)/(p0 L) sqrt(pi R T0/2) (Section 2.1).
+ * Ma: reserved for free-stream boundaries (unused by walls; pass 0).
+ * On success *out is a new handle; on failure *out is NULL. */
+int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const gsis_gas *gas, double Kn,
+                double Ma, const gsis_options *opt, gsis_handle *out);
+
+/* Run outer iterations of Algorithm 1 until eps < tol or max_outer iterations.
+ * *outer_done: iterations run by this call; *eps_last: eps of the last one.
+ * Returns GSIS_OK (converged), GSIS_E_NOT_CONVERGED (max_outer reached), or an error. */
+int gsis_iterate(gsis_handle h, int max_outer, double tol, int *outer_done, double *eps_last);
+
+/* Copy per-cell macroscopic fields to host_out (FP64, layout [cell][field], cell index
+ * i + ni (j + nj k)).  field_mask selects, in this order:
+ *   GSIS_F_W    : rho, ux, uy, uz, Tt, Tr of the state used by the next kinetic step (6)
+ *   GSIS_F_HALF : moments of f^{n+1/2} of the last step: rho, u(3), Tt, Tr,
+ *                 sigma(xx,yy,zz,xy,xz,yz), qt(3), qr(3) (18)
+ *   GSIS_F_HOT  : HoT of the last GSIS step: sigma(6), qt(3), qr(3) (12)
+ * out_len: number of doubles available at host_out. */
+#define GSIS_F_W 1u
+#define GSIS_F_HALF 2u
+#define GSIS_F_HOT 4u
+int gsis_moments(gsis_handle h, unsigned field_mask, double *host_out, size_t out_len);
+
+/* eps of Eq. convergence_critertion for the last outer step: eps_by_field[0..2] = rho, u, Tt,
+ * eps_by_field[3] = their maximum (n >= 4). */
+int gsis_residual(gsis_handle h, double *eps_by_field, int n);
+
+/* Per wall face (host arrays of length gsis_nwall): cell index, side, re-emitted density
+ * rho_w of the last kinetic step and the kinetic wall flux (outward, area-integrated: mass,
+ * momentum(3), energy, internal energy). Any pointer may be NULL. */
+int gsis_nwall(gsis_handle h);
+int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, double *flux6);
+
+/* Per cell and side the outward kinetic face flux of the last kinetic step (6 components,
+ * area-integrated, zero for absent faces): host_out holds ncells x 6 x 6 doubles. */
+int gsis_face_flux(gsis_handle h, double *host_out, size_t out_len);
+
+/* VDF transfer, FP64 host arrays [cell][v] (f1 for the Rykov model only, else NULL).
+ * gsis_set_f also resets the per-cell state to the moments of the new f (checkpoint load). */
+int gsis_get_f(gsis_handle h, double *host_f0, double *host_f1);
+int gsis_set_f(gsis_handle h, const double *host_f0, const double *host_f1);
+
+/* Device-time profile of gsis_iterate, from CUDA events recorded on the solver's stream around
+ * each phase of an outer step while enabled.  enable: 1 record from now on, 0 stop.  reset: clear
+ * the accumulators first.  ms[0..4] (n >= 5, may be NULL): accumulated milliseconds of
+ * [0] wall pre-pass, [1] kinetic step, [2] block reduction and moments, [3] synthetic solve,
+ * [4] residual and next state.  *steps: outer steps recorded; *launches: kernels launched by
+ * those steps (either may be NULL). */
+int gsis_profile(gsis_handle h, int enable, int reset, double *ms, int n, int *steps, int *launches);
+
+/* Counters: outer iterations run so far, inner synthetic steps of the last outer step. */
+int gsis_stats(gsis_handle h, int *outer_total, int *macro_iters_last);
+
+/* Release everything held by h.  NULL-safe. */
+int gsis_destroy(gsis_handle h);
+
+/* Message of the last error on h (or of the last failed gsis_create when h is NULL). */
+const char *gsis_last_error(gsis_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,950 @@
+// gsis_host.cpp -- host solver object behind the C ABI of include/gsis.h.
+//
+// Builds the rectilinear geometry, the octant-blocked velocity layout, the colour tables and the
+// wall tables, owns every device buffer, and sequences one outer iteration of Algorithm 1:
+//   wall pre-pass -> fused kinetic step -> block reduction -> moments (+ closed-domain mass
+//   scale) -> [GSIS: FP64 synthetic solve] -> eps -> state of the next step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gsis.h"
+#include "gsis_internal.h"
+
+using namespace gsis;
+
+namespace {
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+}  // namespace
+
+struct gsis_solver {
+  // options
+  gsis_options opt{};
+  int prec = GSIS_F32;
+  double Kn = 0.1, omega = 0.81;
+  gsis_gas gas{};
+  cudaStream_t stream = nullptr;
+  // geometry
+  int n[3] = {1, 1, 1}, nc = 0;
+  std::vector<double> X[3];
+  std::vector<AxisCell<double>> axc[3];
+  std::vector<double> vol;
+  double vsum = 0.0;
+  KinGeom kg{};
+  std::vector<int> col_off, col_cell, pos_of;
+  // velocities
+  int nvc = 0, nslots = 0, nblocks = 0, np = 0;
+  int nv_axis[3] = {0, 0, 0};
+  std::vector<int> slot_canon;
+  std::vector<int8_t> boct;
+  std::vector<double> vel64;
+  // walls
+  int nwall = 0;
+  std::vector<int> wall_cell, wall_side, wall_sides_list;
+  double wall_uT[6][4] = {};
+  int closed = 1;
+  // device
+  std::vector<DevBuf> allocs;
+  void *d_f = nullptr, *d_part = nullptr, *d_stT = nullptr, *d_vel = nullptr;
+  void *d_ax[3] = {nullptr, nullptr, nullptr};
+  AxisCell<double> *d_ax64[3] = {nullptr, nullptr, nullptr};
+  double *d_vel64 = nullptr, *d_st64 = nullptr, *d_rho_w = nullptr, *d_Z0 = nullptr, *d_Zw = nullptr;
+  double *d_wall_uT = nullptr, *d_mom = nullptr, *d_ff = nullptr, *d_wf = nullptr, *d_Mh = nullptr;
+  double *d_hot = nullptr, *d_Wstate = nullptr, *d_Wnew = nullptr, *d_vol = nullptr, *d_mass = nullptr;
+  double *d_scratch = nullptr, *d_eps4 = nullptr;
+  int8_t *d_boct = nullptr;
+  int *d_col_off = nullptr, *d_col_cell = nullptr, *d_pos_of = nullptr, *d_wall_cell = nullptr;
+  int *d_wall_side = nullptr, *d_wall_sides = nullptr, *d_err = nullptr, *d_iters = nullptr;
+  unsigned *d_ticket = nullptr, *d_bar = nullptr;
+  // macro work
+  double *m_W = nullptr, *m_pr = nullptr, *m_gW = nullptr, *m_phW = nullptr, *m_gP = nullptr, *m_mu = nullptr;
+  double *m_R = nullptr, *m_D = nullptr, *m_dW = nullptr, *m_Fc = nullptr, *m_corr = nullptr, *m_gam = nullptr;
+  double *m_feq0 = nullptr, *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr;
+  int macro_grid = 0;
+  int kin_warps = 1;
+  size_t kin_smem = 0;
+  // profiling
+  bool profiling = false;
+  cudaEvent_t ev[6] = {};
+  double phase_ms[5] = {0, 0, 0, 0, 0};
+  int prof_steps = 0, prof_launches = 0;
+  // bookkeeping
+  double mass_ref = 0.0;
+  int outer_total = 0, macro_iters_last = 0;
+  double eps4[4] = {0, 0, 0, 0};
+  std::string last_error;
+
+  int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    last_error = buf;
+    return code;
+  }
+
+  template <typename P>
+  int alloc(P **out, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (opt.alloc) {
+      p = opt.alloc(bytes, (void *)stream, opt.alloc_ctx);
+      if (!p) return fail(GSIS_E_OOM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+      cudaError_t e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess) return fail(GSIS_E_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    allocs.push_back({p, bytes});
+    *out = static_cast<P *>(p);
+    return GSIS_OK;
+  }
+
+  void mark(int k) {
+    if (profiling) cudaEventRecord(ev[k], stream);
+  }
+
+  void release() {
+    if (ev[0])
+      for (auto &e : ev) cudaEventDestroy(e);
+    if (!allocs.empty()) cudaStreamSynchronize(stream);
+    for (auto &b : allocs) {
+      if (opt.free) opt.free(b.p, (void *)stream, opt.alloc_ctx);
+      else cudaFree(b.p);
+    }
+    allocs.clear();
+  }
+
+  int cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return GSIS_OK;
+    return fail(GSIS_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+
+  template <typename P>
+  int upload(P *dst, const void *src, size_t bytes) {
+    return cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "upload");
+  }
+
+  template <typename T>
+  KinArgs<T> kin_args() const {
+    KinArgs<T> a{};
+    a.g = kg;
+    for (int d = 0; d < 3; ++d) a.ax[d] = static_cast<const AxisCell<T> *>(d_ax[d]);
+    a.vel = static_cast<const T *>(d_vel);
+    a.boct = d_boct;
+    a.col_off = d_col_off;
+    a.col_cell = d_col_cell;
+    a.pos_of = d_pos_of;
+    a.st = static_cast<const T *>(d_stT);
+    a.rho_w = d_rho_w;
+    a.wall_uT = d_wall_uT;
+    a.f = static_cast<T *>(d_f);
+    a.part = static_cast<T *>(d_part);
+    a.np = np;
+    return a;
+  }
+
+  int check_err() {
+    int herr = 0;
+    int rc = cuda(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream), "read error flag");
+    if (rc) return rc;
+    rc = cuda(cudaStreamSynchronize(stream), "synchronize");
+    if (rc) return rc;
+    if (herr == GSIS_ERR_DIVERGED) return fail(GSIS_E_DIVERGED, "non-finite or non-positive density/temperature");
+    if (herr == GSIS_ERR_TIMEOUT) return fail(GSIS_E_TIMEOUT, "a bounded device wait timed out");
+    if (herr != 0) return fail(GSIS_E_CUDA, "device error flag %d", herr);
+    return GSIS_OK;
+  }
+
+  // moments of the current (corrected) f -> Mh, using a state whose velocity is st64[0..2]
+  template <typename T>
+  int reduce_and_finalize(bool closed_scale) {
+    int rc = cuda(launch_reduce<T>(static_cast<const T *>(d_part), np, d_boct, nblocks, kg, d_wall_cell, d_wall_side,
+                                   nwall, d_rho_w, d_Zw, d_mom, d_ff, d_wf, stream),
+                  "reduce");
+    if (rc) return rc;
+    FinalizeArgs fa{};
+    fa.g = kg;
+    fa.mom = d_mom;
+    fa.st64 = d_st64;
+    fa.vol = d_vol;
+    fa.mass_ref = mass_ref;
+    fa.closed = closed_scale ? closed : 0;
+    fa.Mh = d_Mh;
+    fa.mass_scale = d_mass;
+    fa.scratch = d_scratch;
+    fa.ticket = d_ticket;
+    fa.err = d_err;
+    return cuda(launch_finalize(fa, stream), "finalize");
+  }
+
+  int write_state(const double *Wn) {
+    StateArgs sa{};
+    sa.g = kg;
+    sa.Wn = Wn;
+    sa.Mh = d_Mh;
+    sa.mass_scale_ptr = d_mass;
+    sa.Kn = Kn;
+    sa.omega = omega;
+    sa.kin_inv_dt = opt.kin_inv_dt;
+    sa.st64 = d_st64;
+    sa.stT = d_stT;
+    sa.is_float = prec == GSIS_F32;
+    return cuda(launch_state(sa, stream), "state");
+  }
+
+  // state <- moments of the current f (after init or set_f); also sets mass_ref
+  template <typename T>
+  int state_from_f() {
+    // neutral state: corrected f = f_raw, moments about u = 0
+    std::vector<double> st0((size_t)nc * NST, 0.0);
+    for (int c = 0; c < nc; ++c) st0[(size_t)c * NST + 10] = 1.0;
+    std::vector<T> st0T(st0.begin(), st0.end());
+    int rc = upload(d_st64, st0.data(), st0.size() * sizeof(double));
+    if (!rc) rc = upload(d_stT, st0T.data(), st0T.size() * sizeof(T));
+    if (!rc) rc = cuda(launch_moments_only<T>(kin_args<T>(), nblocks, stream), "moments");
+    if (!rc) rc = reduce_and_finalize<T>(false);
+    if (rc) return rc;
+    double m2[2];
+    rc = cuda(cudaMemcpyAsync(m2, d_mass, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream), "mass");
+    if (!rc) rc = cuda(cudaStreamSynchronize(stream), "sync");
+    if (rc) return rc;
+    mass_ref = m2[1];
+    double one = 1.0;
+    rc = upload(d_mass, &one, sizeof(double));
+    if (!rc) rc = cuda(cudaMemcpy2DAsync(d_Wstate, 6 * sizeof(double), d_Mh, 18 * sizeof(double), 6 * sizeof(double),
+                                         nc, cudaMemcpyDeviceToDevice, stream),
+                       "copy W");
+    if (!rc) rc = write_state(d_Wstate);
+    if (!rc) rc = check_err();
+    return rc;
+  }
+
+  template <typename T>
+  int step_impl(int mode) {
+    int launches = 0;
+    mark(0);
+    int rc = cuda(launch_wall_prepass<T>(kin_args<T>(), d_wall_cell, d_wall_side, nwall, d_Z0, d_rho_w, nslots, stream),
+                  "wall pre-pass");
+    if (rc) return rc;
+    launches += nwall > 0;
+    mark(1);
+    rc = cuda(launch_kinetic<T>(kin_args<T>(), nblocks, kin_warps, kin_smem, stream), "kinetic");
+    if (rc) return rc;
+    mark(2);
+    rc = reduce_and_finalize<T>(true);
+    if (rc) return rc;
+    launches += 1 + 1 + 2;
+    mark(3);
+    if (mode == GSIS_MODE_GSIS) {
+      MacroArgs m{};
+      m.g = kg;
+      for (int d = 0; d < 3; ++d) m.ax[d] = d_ax64[d];
+      m.Kn = Kn;
+      m.omega = omega;
+      m.cfl = opt.macro_cfl;
+      m.tol = opt.macro_tol;
+      m.model = gas.model;
+      m.nW = gas.model == GSIS_RYKOV ? 6 : 5;
+      m.steps = opt.macro_steps;
+      m.sweeps = opt.macro_sweeps;
+      m.d_r = gas.d_r;
+      m.Z_r = gas.Z_r;
+      for (int k = 0; k < 4; ++k) m.A[k] = gas.A[k];
+      m.mass_ref = mass_ref;
+      m.closed = closed;
+      m.Mh = d_Mh;
+      m.ffk = d_ff;
+      m.wfk = d_wf;
+      m.wall_cell = d_wall_cell;
+      m.wall_side = d_wall_side;
+      m.nwall = nwall;
+      m.wall_uT = d_wall_uT;
+      m.W = m_W; m.pr = m_pr; m.gW = m_gW; m.phW = m_phW; m.gP = m_gP; m.mu = m_mu; m.R = m_R; m.D = m_D;
+      m.dW = m_dW; m.Fc = m_Fc; m.corr = m_corr; m.gam = m_gam; m.feq0 = m_feq0; m.red = m_red; m.Ffc = m_Ffc;
+      m.wfl = m_wfl;
+      m.Wout = d_Wnew;
+      m.bar = d_bar;
+      m.err = d_err;
+      m.iters = d_iters;
+      if (opt.macro_steps > 0) {
+        rc = cuda(launch_macro(m, macro_grid, macro_block_size(), stream), "synthetic solve");
+        if (rc) return rc;
+        ++launches;
+      } else {
+        rc = cuda(cudaMemcpy2DAsync(d_Wnew, 6 * sizeof(double), d_Mh, 18 * sizeof(double), 6 * sizeof(double), nc,
+                                    cudaMemcpyDeviceToDevice, stream),
+                  "copy W");
+        if (rc) return rc;
+      }
+    } else {
+      rc = cuda(cudaMemcpy2DAsync(d_Wnew, 6 * sizeof(double), d_Mh, 18 * sizeof(double), 6 * sizeof(double), nc,
+                                  cudaMemcpyDeviceToDevice, stream),
+                "copy W");
+      if (rc) return rc;
+    }
+    mark(4);
+    EpsArgs ea{};
+    ea.nc = nc;
+    ea.vsum = vsum;
+    ea.Wn = d_Wnew;
+    ea.Wo = d_Wstate;
+    ea.vol = d_vol;
+    ea.scratch = d_scratch;
+    ea.ticket = d_ticket + 1;
+    ea.eps4 = d_eps4;
+    rc = cuda(launch_eps(ea, stream), "eps");
+    if (!rc) rc = write_state(d_Wnew);
+    if (rc) return rc;
+    launches += 2;
+    mark(5);
+    std::swap(d_Wstate, d_Wnew);
+    int iters = 0;
+    rc = cuda(cudaMemcpyAsync(eps4, d_eps4, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), "eps");
+    if (!rc && mode == GSIS_MODE_GSIS && opt.macro_steps > 0)
+      rc = cuda(cudaMemcpyAsync(&iters, d_iters, sizeof(int), cudaMemcpyDeviceToHost, stream), "iters");
+    if (!rc) rc = check_err();
+    if (rc) return rc;
+    macro_iters_last = iters;
+    ++outer_total;
+    if (profiling) {
+      for (int k = 0; k < 5; ++k) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+        phase_ms[k] += t;
+      }
+      ++prof_steps;
+      prof_launches += launches;
+    }
+    return GSIS_OK;
+  }
+
+  int step(int mode) { return prec == GSIS_F32 ? step_impl<float>(mode) : step_impl<double>(mode); }
+};
+
+// ---------------------------------------------------------------------------------------------
+
+extern "C" void gsis_default_options(gsis_options *o) {
+  std::memset(o, 0, sizeof *o);
+  o->precision = GSIS_F32;
+  o->mode = GSIS_MODE_GSIS;
+  o->n_sweeps = 1;
+  o->macro_steps = 300;
+  o->macro_sweeps = 4;
+  o->macro_cfl = 100.0;
+  o->macro_tol = 1e-10;
+  o->kin_inv_dt = 0.0;
+  o->venkat_K = 1.0;
+  o->kinetic_presteps = 10;
+}
+
+namespace {
+
+int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double Kn, const gsis_options *o,
+             std::string &why) {
+  if (!m || !vg || !g || !o || !m->nodes) { why = "NULL argument"; return GSIS_E_INVALID; }
+  if (m->ni < 1 || m->nj < 1 || m->nk < 1 || m->ni > 1023 || m->nj > 1023 || m->nk > 1023) {
+    why = "cell counts must be in [1, 1023]";
+    return GSIS_E_INVALID;
+  }
+  for (int d = 0; d < 3; ++d)
+    if (vg->n[d] < 1 || !vg->x[d] || !vg->w[d]) { why = "bad velocity grid"; return GSIS_E_INVALID; }
+  if (!(Kn > 0)) { why = "Kn must be positive"; return GSIS_E_INVALID; }
+  if (!(o->venkat_K > 0)) { why = "venkat_K must be positive"; return GSIS_E_INVALID; }
+  if (o->precision != GSIS_F32 && o->precision != GSIS_F64) { why = "bad precision"; return GSIS_E_INVALID; }
+  if (o->mode != GSIS_MODE_GSIS && o->mode != GSIS_MODE_DVM) { why = "bad mode"; return GSIS_E_INVALID; }
+  if (g->model == GSIS_RYKOV) { why = "Rykov model is not implemented on the GPU yet"; return GSIS_E_UNSUPPORTED; }
+  if (g->model != GSIS_SHAKHOV) { why = "bad model"; return GSIS_E_INVALID; }
+  if (o->n_sweeps != 1) { why = "rectilinear colour sweeps are exact in one pass: n_sweeps must be 1"; return GSIS_E_UNSUPPORTED; }
+  const int n[3] = {m->ni, m->nj, m->nk};
+  bool seen_inactive = false;
+  for (int a = 0; a < 3; ++a) {
+    const bool active = n[a] > 1;
+    if (!active) {
+      if (m->bc[2 * a] != GSIS_BC_PERIODIC || m->bc[2 * a + 1] != GSIS_BC_PERIODIC) {
+        why = "an axis with one cell must be periodic on both sides";
+        return GSIS_E_INVALID;
+      }
+      seen_inactive = true;
+    } else {
+      if (seen_inactive) { why = "active axes must come first (x, then y, then z)"; return GSIS_E_UNSUPPORTED; }
+      if (m->bc[2 * a] != GSIS_BC_WALL || m->bc[2 * a + 1] != GSIS_BC_WALL) {
+        why = "only wall boundaries on axes with more than one cell";
+        return GSIS_E_UNSUPPORTED;
+      }
+    }
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 2; ++s)
+      if (m->bc[2 * a + s] == GSIS_BC_WALL && !(m->wall_T[2 * a + s] > 0)) { why = "wall temperature must be positive"; return GSIS_E_INVALID; }
+  // rectilinear check
+  const int N0 = m->ni + 1, N1 = m->nj + 1, N2 = m->nk + 1;
+  auto node = [&](int I, int J, int K, int d) { return m->nodes[3 * ((size_t)I + (size_t)N0 * ((size_t)J + (size_t)N1 * K)) + d]; };
+  for (int K = 0; K < N2; ++K)
+    for (int J = 0; J < N1; ++J)
+      for (int I = 0; I < N0; ++I) {
+        if (node(I, J, K, 0) != node(I, 0, 0, 0) || node(I, J, K, 1) != node(0, J, 0, 1) || node(I, J, K, 2) != node(0, 0, K, 2)) {
+          why = "mesh is not rectilinear";
+          return GSIS_E_UNSUPPORTED;
+        }
+      }
+  for (int I = 1; I < N0; ++I) if (!(node(I, 0, 0, 0) > node(I - 1, 0, 0, 0))) { why = "x nodes must increase"; return GSIS_E_INVALID; }
+  for (int J = 1; J < N1; ++J) if (!(node(0, J, 0, 1) > node(0, J - 1, 0, 1))) { why = "y nodes must increase"; return GSIS_E_INVALID; }
+  for (int K = 1; K < N2; ++K) if (!(node(0, 0, K, 2) > node(0, 0, K - 1, 2))) { why = "z nodes must increase"; return GSIS_E_INVALID; }
+  return GSIS_OK;
+}
+
+// Velocity slots: velocities grouped by octant (sign of each component, 0 counted +), each
+// octant padded to a multiple of VB with weight-0 copies of its first velocity.
+void build_slots(const gsis_vgrid *vg, std::vector<int> &slot_canon, std::vector<int8_t> &boct,
+                 std::vector<double> &vel64) {
+  const int nx = vg->n[0], ny = vg->n[1], nz = vg->n[2];
+  slot_canon.clear();
+  boct.clear();
+  vel64.clear();
+  for (int oct = 0; oct < 8; ++oct) {
+    std::vector<int> list;
+    for (int iz = 0; iz < nz; ++iz)
+      for (int iy = 0; iy < ny; ++iy)
+        for (int ix = 0; ix < nx; ++ix) {
+          const double x = vg->x[0][ix], y = vg->x[1][iy], z = vg->x[2][iz];
+          const int o = (x < 0 ? 1 : 0) | (y < 0 ? 2 : 0) | (z < 0 ? 4 : 0);
+          if (o == oct) list.push_back(ix + nx * (iy + ny * iz));
+        }
+    if (list.empty()) continue;
+    const size_t padded = (list.size() + VB - 1) / VB * VB;
+    for (size_t t = 0; t < padded; ++t) {
+      const bool real = t < list.size();
+      const int v = real ? list[t] : list[0];
+      const int ix = v % nx, iy = (v / nx) % ny, iz = v / (nx * ny);
+      slot_canon.push_back(v);
+      vel64.push_back(vg->x[0][ix]);
+      vel64.push_back(vg->x[1][iy]);
+      vel64.push_back(vg->x[2][iz]);
+      vel64.push_back(real ? vg->w[0][ix] * vg->w[1][iy] * vg->w[2][iz] : 0.0);
+    }
+    for (size_t b = 0; b < padded / VB; ++b) boct.push_back((int8_t)oct);
+  }
+}
+
+template <typename T>
+std::vector<AxisCell<T>> cast_axis(const std::vector<AxisCell<double>> &in) {
+  std::vector<AxisCell<T>> out(in.size());
+  for (size_t i = 0; i < in.size(); ++i)
+    out[i] = {(T)in[i].invh, (T)in[i].rlo, (T)in[i].rhi, (T)in[i].clo, (T)in[i].chi, (T)in[i].h};
+  return out;
+}
+
+}  // namespace
+
+static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
+  s->n[0] = m->ni;
+  s->n[1] = m->nj;
+  s->n[2] = m->nk;
+  s->nc = m->ni * m->nj * m->nk;
+  const int N0 = m->ni + 1, N1 = m->nj + 1;
+  for (int a = 0; a < 3; ++a) {
+    s->X[a].resize(s->n[a] + 1);
+    for (int I = 0; I <= s->n[a]; ++I) {
+      const size_t idx = a == 0 ? (size_t)I : (a == 1 ? (size_t)N0 * I : (size_t)N0 * N1 * I);
+      s->X[a][I] = m->nodes[3 * idx + a];
+    }
+    const int na = s->n[a];
+    std::vector<double> xc(na), h(na);
+    for (int i = 0; i < na; ++i) {
+      xc[i] = 0.5 * (s->X[a][i] + s->X[a][i + 1]);
+      h[i] = s->X[a][i + 1] - s->X[a][i];
+    }
+    s->axc[a].resize(na);
+    for (int i = 0; i < na; ++i) {
+      AxisCell<double> c{};
+      c.h = h[i];
+      c.invh = 1.0 / h[i];
+      c.rlo = s->X[a][i] - xc[i];
+      c.rhi = s->X[a][i + 1] - xc[i];
+      // unweighted least squares over the axis neighbours inside the domain
+      const double dlo = i > 0 ? xc[i - 1] - xc[i] : 0.0, dhi = i < na - 1 ? xc[i + 1] - xc[i] : 0.0;
+      const double den = dlo * dlo + dhi * dhi;
+      c.clo = den > 0 ? dlo / den : 0.0;
+      c.chi = den > 0 ? dhi / den : 0.0;
+      s->axc[a][i] = c;
+    }
+  }
+  s->vol.resize(s->nc);
+  s->vsum = 0.0;
+  for (int k = 0; k < s->n[2]; ++k)
+    for (int j = 0; j < s->n[1]; ++j)
+      for (int i = 0; i < s->n[0]; ++i) {
+        const double V = s->axc[0][i].h * s->axc[1][j].h * s->axc[2][k].h;
+        s->vol[i + s->n[0] * (j + s->n[1] * k)] = V;
+        s->vsum += V;
+      }
+  KinGeom &g = s->kg;
+  g = KinGeom{};
+  g.nc = s->nc;
+  g.nact = 0;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = s->n[a];
+    g.act[a] = s->n[a] > 1;
+    g.nact += g.act[a];
+  }
+  g.ntrans[0] = g.act[0] ? s->n[1] * s->n[2] : 0;
+  g.ntrans[1] = g.act[1] ? s->n[0] * s->n[2] : 0;
+  g.ntrans[2] = g.act[2] ? s->n[0] * s->n[1] : 0;
+  g.K3 = s->opt.venkat_K * s->opt.venkat_K * s->opt.venkat_K;
+  // colour tables: hyperplanes i'+j'+k' of the transformed (upwind-first) coordinates
+  g.ncol = s->n[0] + s->n[1] + s->n[2] - 2;
+  s->col_off.assign(g.ncol + 1, 0);
+  s->col_cell.resize(s->nc);
+  s->pos_of.resize(s->nc);
+  std::vector<std::vector<int>> lists(g.ncol);
+  for (int k = 0; k < s->n[2]; ++k)
+    for (int j = 0; j < s->n[1]; ++j)
+      for (int i = 0; i < s->n[0]; ++i) lists[i + j + k].push_back(i | (j << 10) | (k << 20));
+  g.maxcol = 0;
+  for (int c = 0; c < g.ncol; ++c) {
+    s->col_off[c + 1] = s->col_off[c] + (int)lists[c].size();
+    g.maxcol = std::max(g.maxcol, (int)lists[c].size());
+    for (size_t p = 0; p < lists[c].size(); ++p) {
+      const int tp = lists[c][p];
+      s->col_cell[s->col_off[c] + p] = tp;
+      const int i = tp & 1023, j = (tp >> 10) & 1023, k = tp >> 20;
+      s->pos_of[i + s->n[0] * (j + s->n[1] * k)] = (int)p;
+    }
+  }
+  // walls
+  s->nwall = 0;
+  s->wall_cell.clear();
+  s->wall_side.clear();
+  s->wall_sides_list.clear();
+  s->closed = 1;
+  for (int side = 0; side < 6; ++side) {
+    const int a = side / 2;
+    g.wall_base[side] = -1;
+    for (int d = 0; d < 3; ++d) s->wall_uT[side][d] = m->wall_u[side][d];
+    s->wall_uT[side][3] = m->wall_T[side];
+    if (m->bc[side] != GSIS_BC_WALL) continue;
+    g.wall_base[side] = s->nwall;
+    s->wall_sides_list.push_back(side);
+    const int fixed = (side & 1) ? s->n[a] - 1 : 0;
+    const int ntr = a == 0 ? s->n[1] * s->n[2] : (a == 1 ? s->n[0] * s->n[2] : s->n[0] * s->n[1]);
+    for (int t = 0; t < ntr; ++t) {
+      int nat[3];
+      if (a == 0) { nat[0] = fixed; nat[1] = t % s->n[1]; nat[2] = t / s->n[1]; }
+      else if (a == 1) { nat[1] = fixed; nat[0] = t % s->n[0]; nat[2] = t / s->n[0]; }
+      else { nat[2] = fixed; nat[0] = t % s->n[0]; nat[1] = t / s->n[0]; }
+      s->wall_cell.push_back(nat[0] + s->n[0] * (nat[1] + s->n[1] * nat[2]));
+      s->wall_side.push_back(side);
+    }
+    s->nwall += ntr;
+  }
+  // velocities
+  s->nv_axis[0] = vg->n[0];
+  s->nv_axis[1] = vg->n[1];
+  s->nv_axis[2] = vg->n[2];
+  s->nvc = vg->n[0] * vg->n[1] * vg->n[2];
+  build_slots(vg, s->slot_canon, s->boct, s->vel64);
+  s->nslots = (int)s->slot_canon.size();
+  s->nblocks = s->nslots / VB;
+  s->np = NMOM + NFF * g.nact;
+  return GSIS_OK;
+}
+
+static size_t footprint(const gsis_solver *s) {
+  const size_t T = s->prec == GSIS_F32 ? 4 : 8;
+  const size_t nc = s->nc;
+  size_t b = 0;
+  b += (size_t)s->nslots * nc * T;            // f
+  b += (size_t)s->nblocks * nc * s->np * T;   // partials
+  b += nc * NST * (T + 8);                    // states
+  b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
+  b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 18 + 18 + 3 + 18) * 8;  // synthetic-solve work
+  b += (size_t)s->nslots * 4 * (T + 8) + (size_t)s->nwall * 32 * 8 + 3 * nc * 4 + (1 << 20);
+  return b;
+}
+
+template <typename T>
+static int allocate_and_upload(gsis_solver *s) {
+  const size_t nc = s->nc;
+  int rc = 0;
+#define A(ptr, bytes) \
+  if (!rc) rc = s->alloc(&(ptr), (bytes))
+  A(s->d_f, (size_t)s->nslots * nc * sizeof(T));
+  A(s->d_part, (size_t)s->nblocks * nc * s->np * sizeof(T));
+  A(s->d_stT, nc * NST * sizeof(T));
+  A(s->d_st64, nc * NST * sizeof(double));
+  A(s->d_vel, (size_t)s->nslots * 4 * sizeof(T));
+  A(s->d_vel64, (size_t)s->nslots * 4 * sizeof(double));
+  for (int a = 0; a < 3; ++a) {
+    A(s->d_ax[a], s->axc[a].size() * sizeof(AxisCell<T>));
+    A(s->d_ax64[a], s->axc[a].size() * sizeof(AxisCell<double>));
+  }
+  A(s->d_boct, s->boct.size());
+  A(s->d_col_off, s->col_off.size() * sizeof(int));
+  A(s->d_col_cell, nc * sizeof(int));
+  A(s->d_pos_of, nc * sizeof(int));
+  A(s->d_rho_w, (size_t)(s->nwall + 1) * sizeof(double));
+  A(s->d_Z0, 6 * sizeof(double));
+  A(s->d_Zw, 36 * sizeof(double));
+  A(s->d_wall_uT, 24 * sizeof(double));
+  A(s->d_wall_cell, (size_t)(s->nwall + 1) * sizeof(int));
+  A(s->d_wall_side, (size_t)(s->nwall + 1) * sizeof(int));
+  A(s->d_wall_sides, 6 * sizeof(int));
+  A(s->d_mom, nc * NMOM * sizeof(double));
+  A(s->d_ff, nc * 18 * sizeof(double));
+  A(s->d_wf, (size_t)(s->nwall + 1) * 6 * sizeof(double));
+  A(s->d_Mh, nc * 18 * sizeof(double));
+  A(s->d_hot, nc * 12 * sizeof(double));
+  A(s->d_Wstate, nc * 6 * sizeof(double));
+  A(s->d_Wnew, nc * 6 * sizeof(double));
+  A(s->d_vol, nc * sizeof(double));
+  A(s->d_mass, 2 * sizeof(double));
+  A(s->d_scratch, 8192 * sizeof(double));
+  A(s->d_eps4, 4 * sizeof(double));
+  A(s->d_ticket, 4 * sizeof(unsigned));
+  A(s->d_bar, 2 * sizeof(unsigned));
+  A(s->d_err, sizeof(int));
+  A(s->d_iters, sizeof(int));
+  A(s->m_W, nc * 6 * sizeof(double));
+  A(s->m_pr, nc * 6 * sizeof(double));
+  A(s->m_gW, nc * 18 * sizeof(double));
+  A(s->m_phW, nc * 6 * sizeof(double));
+  A(s->m_gP, nc * 15 * sizeof(double));
+  A(s->m_mu, nc * sizeof(double));
+  A(s->m_R, nc * 6 * sizeof(double));
+  A(s->m_D, nc * 6 * sizeof(double));
+  A(s->m_dW, nc * 6 * sizeof(double));
+  A(s->m_Fc, nc * 18 * sizeof(double));
+  A(s->m_corr, nc * 18 * sizeof(double));
+  A(s->m_gam, nc * 3 * sizeof(double));
+  A(s->m_feq0, (size_t)(s->nwall + 1) * 6 * sizeof(double));
+  A(s->m_Ffc, nc * 18 * sizeof(double));
+  A(s->m_wfl, (size_t)(s->nwall + 1) * 6 * sizeof(double));
+#undef A
+  if (rc) return rc;
+  rc = s->cuda(macro_max_grid(&s->macro_grid), "occupancy");
+  if (rc) return rc;
+  const int want = (int)((nc + 255) / 256);
+  if (want < s->macro_grid) s->macro_grid = std::max(1, want);
+  rc = s->alloc(&s->m_red, (size_t)s->macro_grid * 16 * sizeof(double));
+  if (rc) return rc;
+  std::vector<T> velT(s->vel64.begin(), s->vel64.end());
+  rc = s->upload(s->d_vel, velT.data(), velT.size() * sizeof(T));
+  if (!rc) rc = s->upload(s->d_vel64, s->vel64.data(), s->vel64.size() * sizeof(double));
+  for (int a = 0; a < 3 && !rc; ++a) {
+    auto cv = cast_axis<T>(s->axc[a]);
+    rc = s->upload(s->d_ax[a], cv.data(), cv.size() * sizeof(AxisCell<T>));
+    if (!rc) rc = s->upload(s->d_ax64[a], s->axc[a].data(), s->axc[a].size() * sizeof(AxisCell<double>));
+  }
+  if (!rc) rc = s->upload(s->d_boct, s->boct.data(), s->boct.size());
+  if (!rc) rc = s->upload(s->d_col_off, s->col_off.data(), s->col_off.size() * sizeof(int));
+  if (!rc) rc = s->upload(s->d_col_cell, s->col_cell.data(), nc * sizeof(int));
+  if (!rc) rc = s->upload(s->d_pos_of, s->pos_of.data(), nc * sizeof(int));
+  if (!rc && s->nwall) rc = s->upload(s->d_wall_cell, s->wall_cell.data(), s->nwall * sizeof(int));
+  if (!rc && s->nwall) rc = s->upload(s->d_wall_side, s->wall_side.data(), s->nwall * sizeof(int));
+  if (!rc && !s->wall_sides_list.empty())
+    rc = s->upload(s->d_wall_sides, s->wall_sides_list.data(), s->wall_sides_list.size() * sizeof(int));
+  if (!rc) rc = s->upload(s->d_wall_uT, &s->wall_uT[0][0], 24 * sizeof(double));
+  if (!rc) rc = s->upload(s->d_vol, s->vol.data(), nc * sizeof(double));
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_ticket, 0, 4 * sizeof(unsigned), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(unsigned), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_rho_w, 0, (s->nwall + 1) * sizeof(double), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_ff, 0, nc * 18 * sizeof(double), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_wf, 0, (s->nwall + 1) * 6 * sizeof(double), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_hot, 0, nc * 12 * sizeof(double), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_Z0, 0, 6 * sizeof(double), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_Zw, 0, 36 * sizeof(double), s->stream), "memset");
+  if (!rc)
+    rc = s->cuda(launch_wall_constants(s->d_vel64, s->nslots, s->d_wall_uT, s->d_wall_sides,
+                                       (int)s->wall_sides_list.size(), s->d_Z0, s->d_Zw, 0.0, s->stream),
+                 "wall constants");
+  if (rc) return rc;
+  // kinetic launch shape: one warp per cell of a colour, up to 16 warps, within the register file
+  s->kin_smem = kinetic_smem_bytes<T>(s->kg);
+  int dev = 0, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (s->kin_smem > (size_t)smem_optin)
+    return s->fail(GSIS_E_UNSUPPORTED, "largest colour needs %zu bytes of shared memory (limit %d)", s->kin_smem, smem_optin);
+  s->kin_warps = std::max(1, std::min(16, s->kg.maxcol / 4));
+  if (sizeof(T) == 8) s->kin_warps = std::min(s->kin_warps, 8);
+  return GSIS_OK;
+}
+
+extern "C" int gsis_footprint_bytes(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const gsis_gas *gas,
+                                    const gsis_options *opt, size_t *bytes) {
+  std::string why;
+  gsis_options o;
+  if (opt) o = *opt;
+  else gsis_default_options(&o);
+  int rc = validate(mesh, vgrid, gas, 1.0, &o, why);
+  if (rc) return rc;
+  gsis_solver tmp;
+  tmp.opt = o;
+  tmp.prec = o.precision;
+  setup(&tmp, mesh, vgrid);
+  *bytes = footprint(&tmp);
+  return GSIS_OK;
+}
+
+static int init_state(gsis_solver *s) {
+  const size_t nc = s->nc;
+  std::vector<double> W0(nc * 6);
+  for (size_t c = 0; c < nc; ++c) {
+    if (s->opt.init_W) {
+      for (int k = 0; k < 6; ++k) W0[c * 6 + k] = s->opt.init_W[c * 6 + k];
+    } else {
+      W0[c * 6 + 0] = 1.0;
+      W0[c * 6 + 1] = W0[c * 6 + 2] = W0[c * 6 + 3] = 0.0;
+      W0[c * 6 + 4] = W0[c * 6 + 5] = 1.0;
+    }
+    if (!(W0[c * 6] > 0) || !(W0[c * 6 + 4] > 0)) return s->fail(GSIS_E_INVALID, "initial state must have rho, T > 0");
+  }
+  double *dW0 = nullptr;
+  int rc = s->cuda(cudaMalloc(&dW0, nc * 6 * sizeof(double)), "temporary");
+  if (rc) return rc;
+  rc = s->upload(dW0, W0.data(), nc * 6 * sizeof(double));
+  if (!rc) {
+    if (s->prec == GSIS_F32) rc = s->cuda(launch_init_maxwellian<float>(s->kin_args<float>(), dW0, s->nblocks, s->stream), "init f");
+    else rc = s->cuda(launch_init_maxwellian<double>(s->kin_args<double>(), dW0, s->nblocks, s->stream), "init f");
+  }
+  if (!rc) rc = s->cuda(cudaStreamSynchronize(s->stream), "sync");
+  cudaFree(dW0);
+  if (rc) return rc;
+  return s->prec == GSIS_F32 ? s->state_from_f<float>() : s->state_from_f<double>();
+}
+
+extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const gsis_gas *gas, double Kn, double Ma,
+                           const gsis_options *opt, gsis_handle *out) {
+  (void)Ma;
+  if (out) *out = nullptr;
+  if (!out) { g_create_error = "out is NULL"; return GSIS_E_INVALID; }
+  gsis_options o;
+  if (opt) o = *opt;
+  else gsis_default_options(&o);
+  std::string why;
+  int rc = validate(mesh, vgrid, gas, Kn, &o, why);
+  if (rc) { g_create_error = why; return rc; }
+  gsis_solver *s = new (std::nothrow) gsis_solver();
+  if (!s) { g_create_error = "out of host memory"; return GSIS_E_OOM; }
+  s->opt = o;
+  s->prec = o.precision;
+  s->Kn = Kn;
+  s->omega = gas->omega;
+  s->gas = *gas;
+  s->stream = (cudaStream_t)o.stream;
+  setup(s, mesh, vgrid);
+  rc = s->prec == GSIS_F32 ? allocate_and_upload<float>(s) : allocate_and_upload<double>(s);
+  if (!rc) rc = init_state(s);
+  for (int t = 0; !rc && t < o.kinetic_presteps; ++t) rc = s->step(GSIS_MODE_DVM);
+  if (rc) {
+    g_create_error = s->last_error;
+    s->release();
+    delete s;
+    return rc;
+  }
+  s->outer_total = 0;
+  *out = s;
+  return GSIS_OK;
+}
+
+extern "C" int gsis_iterate(gsis_handle h, int max_outer, double tol, int *outer_done, double *eps_last) {
+  if (!h) return GSIS_E_INVALID;
+  if (outer_done) *outer_done = 0;
+  for (int t = 0; t < max_outer; ++t) {
+    int rc = h->step(h->opt.mode);
+    if (rc) return rc;
+    if (outer_done) *outer_done = t + 1;
+    if (eps_last) *eps_last = h->eps4[3];
+    if (h->eps4[3] < tol) return GSIS_OK;
+  }
+  return max_outer > 0 ? GSIS_E_NOT_CONVERGED : GSIS_OK;
+}
+
+extern "C" int gsis_moments(gsis_handle h, unsigned mask, double *host_out, size_t out_len) {
+  if (!h || !host_out) return GSIS_E_INVALID;
+  const size_t nc = h->nc;
+  size_t per = 0;
+  if (mask & GSIS_F_W) per += 6;
+  if (mask & GSIS_F_HALF) per += 18;
+  if (mask & GSIS_F_HOT) per += 12;
+  if (per == 0 || out_len < per * nc) return h->fail(GSIS_E_INVALID, "out_len too small");
+  std::vector<double> W(nc * 6), M(nc * 18), H(nc * 12);
+  int rc = 0;
+  if (mask & GSIS_F_HOT) {
+    CellFieldArgs c{};
+    c.g = h->kg;
+    for (int d = 0; d < 3; ++d) c.ax[d] = h->d_ax64[d];
+    c.Kn = h->Kn;
+    c.omega = h->omega;
+    c.model = h->gas.model;
+    c.d_r = h->gas.d_r;
+    c.Z_r = h->gas.Z_r;
+    for (int k = 0; k < 4; ++k) c.A[k] = h->gas.A[k];
+    rc = h->cuda(launch_hot(c, h->d_Mh, h->d_hot, h->stream), "hot");
+  }
+  if (!rc) rc = h->cuda(cudaMemcpyAsync(W.data(), h->d_Wstate, nc * 6 * 8, cudaMemcpyDeviceToHost, h->stream), "W");
+  if (!rc) rc = h->cuda(cudaMemcpyAsync(M.data(), h->d_Mh, nc * 18 * 8, cudaMemcpyDeviceToHost, h->stream), "Mh");
+  if (!rc) rc = h->cuda(cudaMemcpyAsync(H.data(), h->d_hot, nc * 12 * 8, cudaMemcpyDeviceToHost, h->stream), "hot");
+  if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return rc;
+  for (size_t c = 0; c < nc; ++c) {
+    double *o = host_out + c * per;
+    if (mask & GSIS_F_W) { std::memcpy(o, &W[c * 6], 6 * 8); o += 6; }
+    if (mask & GSIS_F_HALF) { std::memcpy(o, &M[c * 18], 18 * 8); o += 18; }
+    if (mask & GSIS_F_HOT) { std::memcpy(o, &H[c * 12], 12 * 8); o += 12; }
+  }
+  return GSIS_OK;
+}
+
+extern "C" int gsis_residual(gsis_handle h, double *eps, int n) {
+  if (!h || !eps || n < 4) return GSIS_E_INVALID;
+  for (int k = 0; k < 4; ++k) eps[k] = h->eps4[k];
+  return GSIS_OK;
+}
+
+extern "C" int gsis_nwall(gsis_handle h) { return h ? h->nwall : 0; }
+
+static double face_area(const gsis_solver *s, int cell, int a) {
+  const int nat[3] = {cell % s->n[0], (cell / s->n[0]) % s->n[1], cell / (s->n[0] * s->n[1])};
+  return s->vol[cell] / s->axc[a][nat[a]].h;
+}
+
+extern "C" int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, double *flux6) {
+  if (!h) return GSIS_E_INVALID;
+  const int nw = h->nwall;
+  std::vector<double> rw(nw + 1), wf((size_t)(nw + 1) * 6);
+  int rc = h->cuda(cudaMemcpyAsync(rw.data(), h->d_rho_w, (nw + 1) * 8, cudaMemcpyDeviceToHost, h->stream), "rho_w");
+  if (!rc) rc = h->cuda(cudaMemcpyAsync(wf.data(), h->d_wf, (nw + 1) * 48, cudaMemcpyDeviceToHost, h->stream), "wf");
+  if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return rc;
+  for (int w = 0; w < nw; ++w) {
+    if (cell) cell[w] = h->wall_cell[w];
+    if (side) side[w] = h->wall_side[w];
+    if (rho_w) rho_w[w] = rw[w];
+    if (flux6) {
+      const double A = face_area(h, h->wall_cell[w], h->wall_side[w] / 2);
+      for (int k = 0; k < 6; ++k) flux6[6 * w + k] = wf[6 * w + k] * A;
+    }
+  }
+  return GSIS_OK;
+}
+
+extern "C" int gsis_face_flux(gsis_handle h, double *out, size_t out_len) {
+  if (!h || !out) return GSIS_E_INVALID;
+  const size_t nc = h->nc;
+  if (out_len < nc * 36) return h->fail(GSIS_E_INVALID, "out_len too small");
+  std::vector<double> ff(nc * 18), wf((size_t)(h->nwall + 1) * 6);
+  int rc = h->cuda(cudaMemcpyAsync(ff.data(), h->d_ff, nc * 18 * 8, cudaMemcpyDeviceToHost, h->stream), "ff");
+  if (!rc) rc = h->cuda(cudaMemcpyAsync(wf.data(), h->d_wf, (h->nwall + 1) * 48, cudaMemcpyDeviceToHost, h->stream), "wf");
+  if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return rc;
+  std::memset(out, 0, nc * 36 * sizeof(double));
+  const int cs[3] = {1, h->n[0], h->n[0] * h->n[1]};
+  for (size_t c = 0; c < nc; ++c) {
+    const int nat[3] = {(int)c % h->n[0], ((int)c / h->n[0]) % h->n[1], (int)c / (h->n[0] * h->n[1])};
+    for (int a = 0; a < 3; ++a) {
+      if (h->n[a] == 1) continue;
+      const double A = face_area(h, (int)c, a);
+      const int trn = a == 0 ? nat[1] + h->n[1] * nat[2] : (a == 1 ? nat[0] + h->n[0] * nat[2] : nat[0] + h->n[0] * nat[1]);
+      for (int k = 0; k < 6; ++k) {
+        // + side
+        double vplus = nat[a] < h->n[a] - 1 ? ff[c * 18 + a * 6 + k] : wf[(size_t)(h->kg.wall_base[2 * a + 1] + trn) * 6 + k];
+        // - side (outward = -e_a)
+        double vminus = nat[a] > 0 ? -ff[(c - cs[a]) * 18 + a * 6 + k] : wf[(size_t)(h->kg.wall_base[2 * a] + trn) * 6 + k];
+        out[c * 36 + (2 * a + 1) * 6 + k] = vplus * A;
+        out[c * 36 + (2 * a) * 6 + k] = vminus * A;
+      }
+    }
+  }
+  return GSIS_OK;
+}
+
+extern "C" int gsis_get_f(gsis_handle h, double *f0, double *f1) {
+  (void)f1;
+  if (!h || !f0) return GSIS_E_INVALID;
+  const size_t bytes = (size_t)h->nc * h->nvc * sizeof(double);
+  double *tmp = nullptr;
+  int *canon = nullptr;
+  int rc = h->cuda(cudaMalloc(&tmp, bytes), "temporary");
+  if (!rc) rc = h->cuda(cudaMalloc(&canon, h->nslots * sizeof(int)), "temporary");
+  if (!rc) rc = h->upload(canon, h->slot_canon.data(), h->nslots * sizeof(int));
+  if (!rc) {
+    if (h->prec == GSIS_F32) rc = h->cuda(launch_export_f<float>(h->kin_args<float>(), canon, h->nslots, h->nvc, tmp, h->stream), "export");
+    else rc = h->cuda(launch_export_f<double>(h->kin_args<double>(), canon, h->nslots, h->nvc, tmp, h->stream), "export");
+  }
+  if (!rc) rc = h->cuda(cudaMemcpyAsync(f0, tmp, bytes, cudaMemcpyDeviceToHost, h->stream), "copy f");
+  if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  cudaFree(tmp);
+  cudaFree(canon);
+  return rc;
+}
+
+extern "C" int gsis_set_f(gsis_handle h, const double *f0, const double *f1) {
+  (void)f1;
+  if (!h || !f0) return GSIS_E_INVALID;
+  const size_t bytes = (size_t)h->nc * h->nvc * sizeof(double);
+  double *tmp = nullptr;
+  int *canon = nullptr;
+  int rc = h->cuda(cudaMalloc(&tmp, bytes), "temporary");
+  if (!rc) rc = h->cuda(cudaMalloc(&canon, h->nslots * sizeof(int)), "temporary");
+  if (!rc) rc = h->upload(canon, h->slot_canon.data(), h->nslots * sizeof(int));
+  if (!rc) rc = h->upload(tmp, f0, bytes);
+  if (!rc) {
+    if (h->prec == GSIS_F32) rc = h->cuda(launch_import_f<float>(h->kin_args<float>(), canon, h->nslots, h->nvc, tmp, h->stream), "import");
+    else rc = h->cuda(launch_import_f<double>(h->kin_args<double>(), canon, h->nslots, h->nvc, tmp, h->stream), "import");
+  }
+  if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  cudaFree(tmp);
+  cudaFree(canon);
+  if (rc) return rc;
+  return h->prec == GSIS_F32 ? h->state_from_f<float>() : h->state_from_f<double>();
+}
+
+extern "C" int gsis_profile(gsis_handle h, int enable, int reset, double *ms, int n, int *steps, int *launches) {
+  if (!h) return GSIS_E_INVALID;
+  if (!h->ev[0])
+    for (auto &e : h->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return h->fail(GSIS_E_CUDA, "cudaEventCreate");
+  if (reset) {
+    for (double &t : h->phase_ms) t = 0.0;
+    h->prof_steps = h->prof_launches = 0;
+  }
+  if (ms)
+    for (int k = 0; k < n && k < 5; ++k) ms[k] = h->phase_ms[k];
+  if (steps) *steps = h->prof_steps;
+  if (launches) *launches = h->prof_launches;
+  h->profiling = enable != 0;
+  return GSIS_OK;
+}
+
+extern "C" int gsis_stats(gsis_handle h, int *outer_total, int *macro_iters_last) {
+  if (!h) return GSIS_E_INVALID;
+  if (outer_total) *outer_total = h->outer_total;
+  if (macro_iters_last) *macro_iters_last = h->macro_iters_last;
+  return GSIS_OK;
+}
+
+extern "C" int gsis_destroy(gsis_handle h) {
+  if (!h) return GSIS_OK;
+  h->release();
+  delete h;
+  return GSIS_OK;
+}
+
+extern "C" const char *gsis_last_error(gsis_handle h) {
+  if (!h) return g_create_error.c_str();
+  return h->last_error.c_str();
+}

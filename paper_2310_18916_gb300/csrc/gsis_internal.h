@@ -1,0 +1,169 @@
+// gsis_internal.h -- structures shared by the host solver object and the CUDA kernels.
+// Not part of the public ABI (include/gsis.h is).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gsis {
+
+constexpr int VB = 32;          // discrete velocities per block (one per lane)
+constexpr int NMOM = 13;        // raw moments about the state velocity: 1, c(3), cc(6), |c|^2 c(3)
+constexpr int NFF = 5;          // face-flux moments: 1, xi(3), |xi|^2/2
+constexpr int NST = 20;         // per-cell kinetic state values (see CellState layout)
+constexpr int MAXNP = 13 + 3 * NFF;
+constexpr int GSIS_ERR_DIVERGED = -4;  // same values as GSIS_E_DIVERGED / GSIS_E_TIMEOUT
+constexpr int GSIS_ERR_TIMEOUT = -5;
+
+// Per-axis geometry of one cell of a rectilinear block (natural orientation).
+//   gradient along the axis: g = clo (q[i-1] - q[i]) + chi (q[i+1] - q[i])  (missing neighbour: 0)
+//   face offsets from the cell centre: rlo = X[i] - xc[i] < 0, rhi = X[i+1] - xc[i] > 0
+template <typename T>
+struct AxisCell {
+  T invh, rlo, rhi, clo, chi, h;
+};
+
+// Per-cell kinetic state (values in the precision of the kinetic kernel):
+//  [0..2] un       velocity of the state W^n (reference distribution, correction, moments)
+//  [3]    invTn    1/Tt of W^n
+//  [4]    Cn       rho (pi Tt)^(-3/2) of W^n
+//  [5..7] uo       velocity of W^{n-1/2} (the moments the pending correction removes)
+//  [8]    invTo
+//  [9]    Co
+//  [10]   s        closed-domain mass scale of the stored f
+//  [11]   invtau   1/tau(W^n)
+//  [12..14] Aq     8/(15 rho Tt^2) q_t (Shakhov heat-flux coefficient times q)
+//  [15]   D0       1/dt + 1/tau
+//  [16..19] reserved
+// The stored f is f_raw; the VDF the step starts from is
+//   f^n = s f_raw + Cn exp(-|xi-un|^2 invTn) - Co exp(-|xi-uo|^2 invTo)   (Eq. updatef, lazily).
+
+struct KinGeom {
+  int n[3];
+  int nc;
+  int act[3];
+  int nact;
+  int ncol, maxcol;
+  int ntrans[3];        // transverse face count per axis (0 if inactive)
+  int wall_base[6];     // first wall-face id of each side, -1 if not a wall
+  double K3;            // venkat K^3: eps^2 = K^3 V
+};
+
+template <typename T>
+struct KinArgs {
+  KinGeom g;
+  const AxisCell<T> *ax[3];
+  const T *vel;          // [slot][4]: xi_x, xi_y, xi_z, w
+  const int8_t *boct;    // octant of each block: bit a set => xi_a < 0
+  const int *col_off;    // [ncol+1]
+  const int *col_cell;   // transformed coords packed i' | j' << 10 | k' << 20
+  const int *pos_of;     // position of a transformed cell inside its colour
+  const T *st;           // [cell][NST]
+  const double *rho_w;   // [nwall]
+  const double *wall_uT; // [6][4]: u_w(3), T_w
+  T *f;                  // [block][cell][VB] f_raw, updated in place
+  T *part;               // [block][cell][np] partial moments
+  int np;
+};
+
+// ---- launchers (defined in the .cu files) ----
+template <typename T>
+cudaError_t launch_kinetic(const KinArgs<T> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s);
+template <typename T>
+size_t kinetic_smem_bytes(const KinGeom &g);
+template <typename T>
+cudaError_t launch_wall_prepass(const KinArgs<T> &a, const int *wall_cell, const int *wall_side, int nwall,
+                                const double *Z0, double *rho_w, int nslots, cudaStream_t s);
+template <typename T>
+cudaError_t launch_moments_only(const KinArgs<T> &a, int nblocks, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init_maxwellian(const KinArgs<T> &a, const double *W0, int nblocks, cudaStream_t s);
+template <typename T>
+cudaError_t launch_export_f(const KinArgs<T> &a, const int *slot_canon, int nslots, int nv, double *out,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_import_f(const KinArgs<T> &a, const int *slot_canon, int nslots, int nv, const double *in,
+                            cudaStream_t s);
+
+cudaError_t launch_wall_constants(const double *vel64, int nslots, const double *wall_uT, const int *sides,
+                                  int nsides, double *Z0, double *Zw, double d_r, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_reduce(const T *part, int np, const int8_t *boct, int nblocks, const KinGeom &g,
+                          const int *wall_cell, const int *wall_side, int nwall, const double *rho_w,
+                          const double *Zw, double *mom, double *ff, double *wf, cudaStream_t s);
+
+struct FinalizeArgs {
+  KinGeom g;
+  const double *mom;     // [cell][NMOM] raw moments about the state velocity
+  const double *st64;    // [cell][NST] FP64 copy of the state (un at [0..2])
+  const double *vol;     // [cell]
+  double mass_ref;
+  int closed;
+  double *Mh;            // out [cell][18]
+  double *mass_scale;    // out [1]
+  double *scratch;       // >= 2 * nblocks doubles
+  unsigned *ticket;      // zero-initialised counter
+  int *err;
+};
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s);
+
+struct CellFieldArgs {
+  KinGeom g;
+  const AxisCell<double> *ax[3];
+  double Kn, omega;
+  int model;
+  double d_r, Z_r, A[4];
+};
+// HoT (Eq. full_constitutive) for reporting, per cell from Mh
+cudaError_t launch_hot(const CellFieldArgs &c, const double *Mh, double *hot, cudaStream_t s);
+
+struct StateArgs {
+  KinGeom g;
+  const double *Wn;       // [cell][6] prim state for the next step
+  const double *Mh;       // [cell][18] moments of f^{n+1/2} (after mass scaling)
+  double mass_scale;      // device value read inside via pointer below
+  const double *mass_scale_ptr;
+  double Kn, omega, kin_inv_dt;
+  double *st64;           // out FP64 state
+  void *stT;              // out state in kernel precision
+  int is_float;
+};
+cudaError_t launch_state(const StateArgs &a, cudaStream_t s);
+
+struct EpsArgs {
+  int nc;
+  double vsum;                  // total volume
+  const double *Wn, *Wo, *vol;  // prim [cell][6]
+  double *scratch;              // >= 7 * nblocks
+  unsigned *ticket;
+  double *eps4;                 // out: rho, u, Tt, max
+};
+cudaError_t launch_eps(const EpsArgs &a, cudaStream_t s);
+
+struct MacroArgs {
+  KinGeom g;
+  const AxisCell<double> *ax[3];
+  double Kn, omega, cfl, tol;
+  int model, nW, steps, sweeps;
+  double d_r, Z_r, A[4];
+  double mass_ref;
+  int closed;
+  const double *Mh;        // [cell][18] initial state W^{n+1/2}
+  const double *ffk;       // [cell][3][NFF+1] kinetic + face flux per unit area (natural +e_a)
+  const double *wfk;       // [nwall][6] kinetic wall flux, outward, per unit area
+  const int *wall_cell, *wall_side;
+  int nwall;
+  const double *wall_uT;   // [6][4]
+  // work (device, sized by the host)
+  double *W, *pr, *gW, *phW, *gP, *mu, *R, *D, *dW, *Fc, *corr, *gam, *feq0, *red, *Ffc, *wfl;
+  double *Wout;            // [cell][6] prim W^{n+1}
+  unsigned *bar;           // [2] barrier counter, generation
+  int *err;
+  int *iters;              // out
+};
+cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s);
+int macro_block_size();
+cudaError_t macro_max_grid(int *grid);
+
+}  // namespace gsis

@@ -1,0 +1,502 @@
+// kinetic.cu -- the mesoscopic kinetic step of GSIS on sm_103a (Section 3.1 of arXiv 2310.18916).
+//
+// One CTA owns one block of VB = 32 discrete velocities of a single octant (one per lane) and
+// marches through the spatial cells colour by colour, the colours being the hyperplanes
+// i' + j' + k' = const in the upwind order of that octant.  For each cell and velocity it
+//   - applies the pending VDF correction of Eq. updatef (and the closed-domain mass scale)
+//     while staging f^n into a three-colour shared-memory ring,
+//   - builds the reference distribution g (Shakhov g_0t, Section 2.2),
+//   - takes the LSQ gradient and the Venkatakrishnan limiter, reconstructs the outflow face
+//     value (second-order upwind, Section 3.1),
+//   - solves the point-implicit delta form with the first-order upwind implicit operator,
+//     taking the inflow value "face value + upwind increment" from the previous colour
+//     (exact in one pass on a rectilinear grid: every inflow neighbour has a lower colour),
+//   - writes f^{n+1/2} in place and reduces, over its 32 velocities, the 13 raw moments about
+//     the state velocity and the moments of its outflow face fluxes.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "gsis_internal.h"
+
+namespace gsis {
+
+__device__ __forceinline__ float dexp(float x) { return __expf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float ddiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
+
+template <typename T>
+__device__ __forceinline__ T wall_maxwellian(const double *uT, T x, T y, T z) {
+  const T ux = (T)uT[0], uy = (T)uT[1], uz = (T)uT[2], Tw = (T)uT[3];
+  const T cx = x - ux, cy = y - uy, cz = z - uz;
+  const T norm = (T)pow((double)(3.14159265358979323846 * uT[3]), -1.5);
+  return norm * dexp(-(cx * cx + cy * cy + cz * cz) / Tw);
+}
+
+// f^n = s f_raw + Cn M(un, Tn) - Co M(uo, To)   (Eq. updatef applied on load)
+template <typename T>
+__device__ __forceinline__ T corrected(T fraw, const T *st, T x, T y, T z) {
+  T cx = x - st[0], cy = y - st[1], cz = z - st[2];
+  T mn = st[4] * dexp(-(cx * cx + cy * cy + cz * cz) * st[3]);
+  cx = x - st[5]; cy = y - st[6]; cz = z - st[7];
+  T mo = st[9] * dexp(-(cx * cx + cy * cy + cz * cz) * st[8]);
+  return st[10] * fraw + mn - mo;
+}
+
+// Venkatakrishnan limiter of one cell: min over its faces (and 1) of
+//   (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
+// the face function with numerator and denominator divided by D2; both are positive, so
+// the minimum is taken by cross-multiplication and divided once.
+template <typename T, int NACT>
+__device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const T *rlo, const T *rhi, T eps2) {
+  T bn = (T)1, bd = (T)1;
+#pragma unroll
+  for (int a = 0; a < NACT; ++a) {
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const T d2 = gr[a] * (sd ? rhi[a] : rlo[a]);
+      const T dm = d2 > (T)0 ? fmax - fi : (d2 < (T)0 ? fmin - fi : (T)0);
+      const T n = dm * dm + eps2 + (T)2 * d2 * dm;
+      const T d = dm * dm + (T)2 * d2 * d2 + dm * d2 + eps2;
+      if (n * bd < bn * d) { bn = n; bd = d; }
+    }
+  }
+  return ddiv(bn, bd);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_state(const T *__restrict__ src, T *st) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) st[q] = __ldg(src + q);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, int NACT>
+__global__ void kinetic_kernel(const KinArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const KinGeom &G = A.g;
+  T *ring = reinterpret_cast<T *>(smem_raw);
+  T *ebuf[3];
+  {
+    T *p = ring + (size_t)3 * G.maxcol * VB;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ebuf[a] = p;
+      p += (size_t)G.ntrans[a] * VB;
+    }
+  }
+  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int oct = A.boct[b];
+  const int sg[3] = {oct & 1 ? -1 : 1, oct & 2 ? -1 : 1, oct & 4 ? -1 : 1};
+  const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
+  const T xi[3] = {vp[0], vp[1], vp[2]};
+  const T wv = vp[3];
+  const T e2 = (T)0.5 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+  T axi[3], Mw[3];
+  int upside[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    axi[a] = fabs(xi[a]);
+    upside[a] = 2 * a + (sg[a] > 0 ? 0 : 1);
+    Mw[a] = (T)0;
+    if (a < NACT && G.wall_base[upside[a]] >= 0)
+      Mw[a] = wall_maxwellian<T>(A.wall_uT + 4 * upside[a], xi[0], xi[1], xi[2]);
+  }
+  const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+  const int tstride[3] = {1, n0, n0 * n1};
+  T *F = A.f + (size_t)b * G.nc * VB;
+  T *P = A.part + (size_t)b * G.nc * A.np;
+  const T K3 = (T)G.K3;
+
+  auto decode = [&](int tp, int *tc, int *nat) {
+    tc[0] = tp & 1023;
+    tc[1] = (tp >> 10) & 1023;
+    tc[2] = tp >> 20;
+    nat[0] = sg[0] > 0 ? tc[0] : n0 - 1 - tc[0];
+    nat[1] = sg[1] > 0 ? tc[1] : n1 - 1 - tc[1];
+    nat[2] = sg[2] > 0 ? tc[2] : n2 - 1 - tc[2];
+  };
+
+  auto stage = [&](int c) {
+    const int off = A.col_off[c], cnt = A.col_off[c + 1] - off;
+    T *slot = ring + (size_t)(c % 3) * G.maxcol * VB;
+    for (int p = warp; p < cnt; p += nw) {
+      int tc[3], nat[3];
+      decode(A.col_cell[off + p], tc, nat);
+      const int cell = nat[0] + n0 * (nat[1] + n1 * nat[2]);
+      T st[16];
+      load_state(A.st + (size_t)cell * NST, st);
+      slot[p * VB + lane] = corrected(F[(size_t)cell * VB + lane], st, xi[0], xi[1], xi[2]);
+    }
+  };
+
+  stage(0);
+  for (int c = 0; c < G.ncol; ++c) {
+    if (c + 1 < G.ncol) stage(c + 1);
+    __syncthreads();
+    const T *slotm = ring + (size_t)((c + 2) % 3) * G.maxcol * VB;
+    const T *slot0 = ring + (size_t)(c % 3) * G.maxcol * VB;
+    const T *slotp = ring + (size_t)((c + 1) % 3) * G.maxcol * VB;
+    const int off = A.col_off[c], cnt = A.col_off[c + 1] - off;
+    for (int p = warp; p < cnt; p += nw) {
+      int tc[3], nat[3];
+      decode(A.col_cell[off + p], tc, nat);
+      const int cell = nat[0] + n0 * (nat[1] + n1 * nat[2]);
+      const int t = tc[0] + n0 * (tc[1] + n1 * tc[2]);
+      const T fi = slot0[p * VB + lane];
+      T st[16];
+      load_state(A.st + (size_t)cell * NST, st);
+      // gradient (LSQ, decoupled per axis on a rectilinear grid) and bounds
+      T gr[3], rlo[3], rhi[3], invh[3];
+      T fmax = fi, fmin = fi;
+      T V = (T)1;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const AxisCell<T> gc = A.ax[a][nat[a]];
+        V *= gc.h;
+        gr[a] = (T)0;
+        if (a < NACT) {
+          const int na = G.n[a];
+          T fup = fi, fdn = fi;
+          if (tc[a] > 0) {
+            fup = slotm[A.pos_of[t - tstride[a]] * VB + lane];
+            fmax = fmax > fup ? fmax : fup;
+            fmin = fmin < fup ? fmin : fup;
+          }
+          if (tc[a] < na - 1) {
+            fdn = slotp[A.pos_of[t + tstride[a]] * VB + lane];
+            fmax = fmax > fdn ? fmax : fdn;
+            fmin = fmin < fdn ? fmin : fdn;
+          }
+          const T flo = sg[a] > 0 ? fup : fdn, fhi = sg[a] > 0 ? fdn : fup;
+          gr[a] = gc.clo * (flo - fi) + gc.chi * (fhi - fi);
+          rlo[a] = gc.rlo;
+          rhi[a] = gc.rhi;
+          invh[a] = gc.invh;
+        }
+      }
+      const T phi = venkat_phi<T, NACT>(fi, fmax, fmin, gr, rlo, rhi, K3 * V);
+      // reference distribution g_0t of the state W^n
+      const T cx = xi[0] - st[0], cy = xi[1] - st[1], cz = xi[2] - st[2];
+      const T c2 = cx * cx + cy * cy + cz * cz;
+      const T g = st[4] * dexp(-c2 * st[3]) * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
+      T acc = (g - fi) * st[11];
+      T D = st[15];
+      T fout[3], tr[3];
+#pragma unroll
+      for (int a = 0; a < NACT; ++a) {
+        fout[a] = fi + phi * gr[a] * (sg[a] > 0 ? rhi[a] : rlo[a]);
+        const int trn = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
+        tr[a] = (T)0;
+        T ein;
+        if (tc[a] > 0) ein = ebuf[a][trn * VB + lane];
+        else ein = (T)A.rho_w[G.wall_base[upside[a]] + trn] * Mw[a];
+        const T k = axi[a] * invh[a];
+        D += k;
+        acc -= k * (fout[a] - ein);
+      }
+      const T df = ddiv(acc, D);
+      const T fnew = fi + df;
+      F[(size_t)cell * VB + lane] = fnew;
+      // moments of f^{n+1/2} about the state velocity, and of the outflow face fluxes
+      const T wf = wv * fnew;
+      T vals[MAXNP];
+      vals[0] = wf;
+      vals[1] = wf * cx;
+      vals[2] = wf * cy;
+      vals[3] = wf * cz;
+      vals[4] = wf * cx * cx;
+      vals[5] = wf * cy * cy;
+      vals[6] = wf * cz * cz;
+      vals[7] = wf * cx * cy;
+      vals[8] = wf * cx * cz;
+      vals[9] = wf * cy * cz;
+      vals[10] = wf * c2 * cx;
+      vals[11] = wf * c2 * cy;
+      vals[12] = wf * c2 * cz;
+#pragma unroll
+      for (int a = 0; a < NACT; ++a) {
+        const int trn = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
+        const T eout = fout[a] + df;
+        ebuf[a][trn * VB + lane] = eout;
+        const T fl = wv * xi[a] * eout;
+        vals[13 + 5 * a + 0] = fl;
+        vals[13 + 5 * a + 1] = fl * xi[0];
+        vals[13 + 5 * a + 2] = fl * xi[1];
+        vals[13 + 5 * a + 3] = fl * xi[2];
+        vals[13 + 5 * a + 4] = fl * e2;
+      }
+      T outv = (T)0;
+#pragma unroll
+      for (int k = 0; k < 13 + 5 * NACT; ++k) {
+        const T s = warp_sum(vals[k]);
+        if (lane == k) outv = s;
+      }
+      if (lane < 13 + 5 * NACT) P[(size_t)cell * A.np + lane] = outv;
+      (void)tr;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+size_t kinetic_smem_bytes(const KinGeom &g) {
+  size_t n = (size_t)3 * g.maxcol * VB;
+  for (int a = 0; a < 3; ++a) n += (size_t)g.ntrans[a] * VB;
+  return n * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_kinetic(const KinArgs<T> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s) {
+  void (*k)(const KinArgs<T>) = nullptr;
+  if (a.g.nact == 1) k = kinetic_kernel<T, 1>;
+  else if (a.g.nact == 2) k = kinetic_kernel<T, 2>;
+  else k = kinetic_kernel<T, 3>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<nblocks, nwarps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Diffuse-wall pre-pass: rho_w of each wall face balances the mass flux of the molecules that
+// reach the wall, whose face values are the wall cell's limited reconstruction of f^n.
+
+template <typename T, int NACT>
+__global__ void wall_prepass_kernel(const KinArgs<T> A, const int *wall_cell, const int *wall_side,
+                                    const double *Z0, double *rho_w, int nslots) {
+  const KinGeom &G = A.g;
+  const int wf = blockIdx.x;
+  const int cell = wall_cell[wf], side = wall_side[wf], axn = side / 2;
+  const double dir = (side & 1) ? 1.0 : -1.0;
+  const int n0 = G.n[0], n1 = G.n[1];
+  const int nat[3] = {cell % n0, (cell / n0) % n1, cell / (n0 * n1)};
+  const int stride[3] = {1, n0, n0 * n1};
+  T st[16], stn[3][2][16];
+  load_state(A.st + (size_t)cell * NST, st);
+  bool has[3][2];
+#pragma unroll
+  for (int a = 0; a < NACT; ++a) {
+    has[a][0] = nat[a] > 0;
+    has[a][1] = nat[a] < G.n[a] - 1;
+    if (has[a][0]) load_state(A.st + (size_t)(cell - stride[a]) * NST, stn[a][0]);
+    if (has[a][1]) load_state(A.st + (size_t)(cell + stride[a]) * NST, stn[a][1]);
+  }
+  AxisCell<T> gc[3];
+  T V = (T)1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gc[a] = A.ax[a][nat[a]];
+    V *= gc[a].h;
+  }
+  double acc = 0.0;
+  for (int v = threadIdx.x; v < nslots; v += blockDim.x) {
+    const T *vp = A.vel + (size_t)v * 4;
+    const T x = vp[0], y = vp[1], z = vp[2], w = vp[3];
+    const T xa = axn == 0 ? x : (axn == 1 ? y : z);
+    if (!(w > (T)0) || !((double)xa * dir > 0.0)) continue;
+    const int blk = v / VB, ln = v % VB;
+    const T *Fb = A.f + (size_t)blk * G.nc * VB;
+    const T fi = corrected(Fb[(size_t)cell * VB + ln], st, x, y, z);
+    T gr[3], rlo[3], rhi[3], fmax = fi, fmin = fi;
+#pragma unroll
+    for (int a = 0; a < NACT; ++a) {
+      T flo = fi, fhi = fi;
+      if (has[a][0]) flo = corrected(Fb[(size_t)(cell - stride[a]) * VB + ln], stn[a][0], x, y, z);
+      if (has[a][1]) fhi = corrected(Fb[(size_t)(cell + stride[a]) * VB + ln], stn[a][1], x, y, z);
+      if (has[a][0]) { fmax = fmax > flo ? fmax : flo; fmin = fmin < flo ? fmin : flo; }
+      if (has[a][1]) { fmax = fmax > fhi ? fmax : fhi; fmin = fmin < fhi ? fmin : fhi; }
+      gr[a] = gc[a].clo * (flo - fi) + gc[a].chi * (fhi - fi);
+      rlo[a] = gc[a].rlo;
+      rhi[a] = gc[a].rhi;
+    }
+    const T phi = venkat_phi<T, NACT>(fi, fmax, fmin, gr, rlo, rhi, (T)G.K3 * V);
+    const T r = (side & 1) ? rhi[axn] : rlo[axn];
+    const T face = fi + phi * gr[axn] * r;
+    acc += (double)w * fabs((double)xa) * (double)face;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rho_w[wf] = red[0] / Z0[side];
+}
+
+template <typename T>
+cudaError_t launch_wall_prepass(const KinArgs<T> &a, const int *wall_cell, const int *wall_side, int nwall,
+                                const double *Z0, double *rho_w, int nslots, cudaStream_t s) {
+  if (nwall == 0) return cudaSuccess;
+  if (a.g.nact == 1) wall_prepass_kernel<T, 1><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
+  else if (a.g.nact == 2) wall_prepass_kernel<T, 2><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
+  else wall_prepass_kernel<T, 3><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Wall constants: for each wall side, over the velocities leaving the wall into the gas,
+//   Z0 = sum w |xi_n| M_w  and  Zw[m] = sum w xi_a phi_m M_w (signed, +e_a direction),
+// phi = 1, xi(3), |xi|^2/2 and the internal-energy factor d_r T_w / 4 (Rykov).
+__global__ void wall_constants_kernel(const double *vel64, int nslots, const double *wall_uT, const int *sides,
+                                      double *Z0, double *Zw, double d_r) {
+  const int side = sides[blockIdx.x], a = side / 2;
+  const double dir = (side & 1) ? 1.0 : -1.0;
+  const double *uT = wall_uT + 4 * side;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int v = threadIdx.x; v < nslots; v += blockDim.x) {
+    const double x = vel64[4 * v], y = vel64[4 * v + 1], z = vel64[4 * v + 2], w = vel64[4 * v + 3];
+    const double xa = a == 0 ? x : (a == 1 ? y : z);
+    if (!(w > 0.0) || !(xa * dir < 0.0)) continue;
+    const double cx = x - uT[0], cy = y - uT[1], cz = z - uT[2];
+    const double M = pow(3.14159265358979323846 * uT[3], -1.5) * exp(-(cx * cx + cy * cy + cz * cz) / uT[3]);
+    const double fl = w * xa * M;
+    acc[0] += w * fabs(xa) * M;
+    acc[1] += fl;
+    acc[2] += fl * x;
+    acc[3] += fl * y;
+    acc[4] += fl * z;
+    acc[5] += fl * (0.5 * (x * x + y * y + z * z) + d_r * uT[3] / 4.0);
+    acc[6] += fl * d_r * uT[3] / 4.0;
+  }
+  __shared__ double red[7][256];
+  for (int q = 0; q < 7; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 7; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Z0[side] = red[0][0];
+    for (int q = 0; q < 6; ++q) Zw[6 * side + q] = red[1 + q][0];
+  }
+}
+
+cudaError_t launch_wall_constants(const double *vel64, int nslots, const double *wall_uT, const int *sides,
+                                  int nsides, double *Z0, double *Zw, double d_r, cudaStream_t s) {
+  if (nsides == 0) return cudaSuccess;
+  wall_constants_kernel<<<nsides, 256, 0, s>>>(vel64, nslots, wall_uT, sides, Z0, Zw, d_r);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Raw moments (about the state velocity) of the current corrected f, without a kinetic step.
+template <typename T>
+__global__ void moments_only_kernel(const KinArgs<T> A) {
+  const KinGeom &G = A.g;
+  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
+  const T x = vp[0], y = vp[1], z = vp[2], w = vp[3];
+  const T *F = A.f + (size_t)b * G.nc * VB;
+  T *P = A.part + (size_t)b * G.nc * A.np;
+  for (int cell = warp; cell < G.nc; cell += nw) {
+    T st[16];
+    load_state(A.st + (size_t)cell * NST, st);
+    const T f = corrected(F[(size_t)cell * VB + lane], st, x, y, z);
+    const T cx = x - st[0], cy = y - st[1], cz = z - st[2], c2 = cx * cx + cy * cy + cz * cz, wf = w * f;
+    T vals[13] = {wf, wf * cx, wf * cy, wf * cz, wf * cx * cx, wf * cy * cy, wf * cz * cz,
+                  wf * cx * cy, wf * cx * cz, wf * cy * cz, wf * c2 * cx, wf * c2 * cy, wf * c2 * cz};
+    T outv = (T)0;
+#pragma unroll
+    for (int k = 0; k < 13; ++k) {
+      const T s = warp_sum(vals[k]);
+      if (lane == k) outv = s;
+    }
+    if (lane < A.np) P[(size_t)cell * A.np + lane] = lane < 13 ? outv : (T)0;
+  }
+}
+
+template <typename T>
+cudaError_t launch_moments_only(const KinArgs<T> &a, int nblocks, cudaStream_t s) {
+  moments_only_kernel<T><<<nblocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// f_raw = Maxwellian(W0) of each cell at each slot velocity (computed in FP64).
+template <typename T>
+__global__ void init_maxwellian_kernel(const KinArgs<T> A, const double *W0) {
+  const KinGeom &G = A.g;
+  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
+  const double x = vp[0], y = vp[1], z = vp[2];
+  T *F = A.f + (size_t)b * G.nc * VB;
+  for (int cell = warp; cell < G.nc; cell += nw) {
+    const double *w0 = W0 + 6 * (size_t)cell;
+    const double cx = x - w0[1], cy = y - w0[2], cz = z - w0[3];
+    F[(size_t)cell * VB + lane] =
+        (T)(w0[0] * pow(3.14159265358979323846 * w0[4], -1.5) * exp(-(cx * cx + cy * cy + cz * cz) / w0[4]));
+  }
+}
+
+template <typename T>
+cudaError_t launch_init_maxwellian(const KinArgs<T> &a, const double *W0, int nblocks, cudaStream_t s) {
+  init_maxwellian_kernel<T><<<nblocks, 256, 0, s>>>(a, W0);
+  return cudaGetLastError();
+}
+
+// Canonical [cell][v] FP64 <-> internal [block][cell][lane].  Export applies the pending
+// correction (the returned f is the VDF the next kinetic step starts from).
+template <typename T>
+__global__ void export_f_kernel(const KinArgs<T> A, const int *slot_canon, int nslots, int nv, double *out) {
+  const size_t n = (size_t)A.g.nc * nslots;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(idx % nslots);
+    const int cell = (int)(idx / nslots);
+    const T *vp = A.vel + (size_t)slot * 4;
+    if (!(vp[3] > (T)0)) continue;
+    T st[16];
+    load_state(A.st + (size_t)cell * NST, st);
+    const int blk = slot / VB, ln = slot % VB;
+    const T f = corrected(A.f[((size_t)blk * A.g.nc + cell) * VB + ln], st, vp[0], vp[1], vp[2]);
+    out[(size_t)cell * nv + slot_canon[slot]] = (double)f;
+  }
+}
+
+template <typename T>
+__global__ void import_f_kernel(const KinArgs<T> A, const int *slot_canon, int nslots, int nv, const double *in) {
+  const size_t n = (size_t)A.g.nc * nslots;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(idx % nslots);
+    const int cell = (int)(idx / nslots);
+    const int blk = slot / VB, ln = slot % VB;
+    A.f[((size_t)blk * A.g.nc + cell) * VB + ln] = (T)in[(size_t)cell * nv + slot_canon[slot]];
+  }
+}
+
+template <typename T>
+cudaError_t launch_export_f(const KinArgs<T> &a, const int *slot_canon, int nslots, int nv, double *out,
+                            cudaStream_t s) {
+  export_f_kernel<T><<<1024, 256, 0, s>>>(a, slot_canon, nslots, nv, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_import_f(const KinArgs<T> &a, const int *slot_canon, int nslots, int nv, const double *in,
+                            cudaStream_t s) {
+  import_f_kernel<T><<<1024, 256, 0, s>>>(a, slot_canon, nslots, nv, in);
+  return cudaGetLastError();
+}
+
+#define GSIS_INST(T)                                                                                            \
+  template cudaError_t launch_kinetic<T>(const KinArgs<T> &, int, int, size_t, cudaStream_t);                  \
+  template size_t kinetic_smem_bytes<T>(const KinGeom &);                                                       \
+  template cudaError_t launch_wall_prepass<T>(const KinArgs<T> &, const int *, const int *, int, const double *, \
+                                              double *, int, cudaStream_t);                                     \
+  template cudaError_t launch_moments_only<T>(const KinArgs<T> &, int, cudaStream_t);                           \
+  template cudaError_t launch_init_maxwellian<T>(const KinArgs<T> &, const double *, int, cudaStream_t);        \
+  template cudaError_t launch_export_f<T>(const KinArgs<T> &, const int *, int, int, double *, cudaStream_t);   \
+  template cudaError_t launch_import_f<T>(const KinArgs<T> &, const int *, int, int, const double *, cudaStream_t);
+GSIS_INST(float)
+GSIS_INST(double)
+
+}  // namespace gsis

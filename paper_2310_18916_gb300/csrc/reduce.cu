@@ -1,0 +1,348 @@
+// reduce.cu -- deterministic reductions and per-cell FP64 kernels of one GSIS outer step:
+// block partials -> moments (Eq. getmoment) and kinetic face fluxes, moment shift to the mean
+// velocity, closed-domain mass scale, HoT (Eq. full_constitutive), the per-cell state of the
+// next kinetic step (Eq. updatef applied lazily) and eps (Eq. convergence_critertion).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "gsis_internal.h"
+
+namespace gsis {
+
+namespace {
+constexpr double kPi = 3.14159265358979323846;
+
+// Compensated (Kahan) accumulator in the kinetic precision; FP64 partials add plainly.
+template <typename T>
+struct Acc {
+  T s = 0, c = 0;
+  __device__ void add(T x) {
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ double get() const { return (double)s - (double)c; }
+};
+template <>
+struct Acc<double> {
+  double s = 0;
+  __device__ void add(double x) { s += x; }
+  __device__ double get() const { return s; }
+};
+
+__device__ __forceinline__ int trans_index(const KinGeom &g, int a, const int *nat) {
+  return a == 0 ? nat[1] + g.n[1] * nat[2] : (a == 1 ? nat[0] + g.n[0] * nat[2] : nat[0] + g.n[0] * nat[1]);
+}
+}  // namespace
+
+// partials [block][cell][np] -> mom [cell][13] (raw, about the state velocity),
+// ff [cell][3][6] flux through the + face along +e_a (interior faces, per unit area),
+// wf [wall][6] outward kinetic wall flux per unit area (outgoing half from the partials,
+// re-emitted half rho_w Zw).
+template <typename T>
+__global__ void reduce_kernel(const T *part, int np, const int8_t *boct, int nblocks, KinGeom g, const double *rho_w,
+                              const double *Zw, double *mom, double *ff, double *wf) {
+  const size_t n = (size_t)g.nc * np;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int cell = (int)(idx / np), k = (int)(idx % np);
+    if (k < NMOM) {
+      Acc<T> acc;
+      for (int b = 0; b < nblocks; ++b) acc.add(part[((size_t)b * g.nc + cell) * np + k]);
+      mom[(size_t)cell * NMOM + k] = acc.get();
+      continue;
+    }
+    const int a = (k - NMOM) / NFF, m = (k - NMOM) % NFF;
+    const int nat[3] = {cell % g.n[0], (cell / g.n[0]) % g.n[1], cell / (g.n[0] * g.n[1])};
+    const int stride = a == 0 ? 1 : (a == 1 ? g.n[0] : g.n[0] * g.n[1]);
+    const bool last = nat[a] == g.n[a] - 1;
+    Acc<T> plus, minus, nxt;
+    for (int b = 0; b < nblocks; ++b) {
+      const bool neg = (boct[b] >> a) & 1;
+      const T v = part[((size_t)b * g.nc + cell) * np + k];
+      if (neg) minus.add(v);
+      else plus.add(v);
+      if (neg && !last) nxt.add(part[((size_t)b * g.nc + cell + stride) * np + k]);
+    }
+    ff[((size_t)cell * 3 + a) * 6 + m] = last ? 0.0 : plus.get() + nxt.get();
+    const int trn = trans_index(g, a, nat);
+    if (nat[a] == 0 && g.wall_base[2 * a] >= 0) {
+      const int wid = g.wall_base[2 * a] + trn;
+      wf[(size_t)wid * 6 + m] = -(minus.get() + rho_w[wid] * Zw[6 * (2 * a) + m]);
+    }
+    if (last && g.wall_base[2 * a + 1] >= 0) {
+      const int wid = g.wall_base[2 * a + 1] + trn;
+      wf[(size_t)wid * 6 + m] = plus.get() + rho_w[wid] * Zw[6 * (2 * a + 1) + m];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_reduce(const T *part, int np, const int8_t *boct, int nblocks, const KinGeom &g,
+                          const int *wall_cell, const int *wall_side, int nwall, const double *rho_w,
+                          const double *Zw, double *mom, double *ff, double *wf, cudaStream_t s) {
+  (void)wall_cell;
+  (void)wall_side;
+  (void)nwall;
+  const size_t n = (size_t)g.nc * np;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 152 * 32) grid = 152 * 32;
+  reduce_kernel<T><<<grid, 256, 0, s>>>(part, np, boct, nblocks, g, rho_w, Zw, mom, ff, wf);
+  return cudaGetLastError();
+}
+template cudaError_t launch_reduce<float>(const float *, int, const int8_t *, int, const KinGeom &, const int *,
+                                          const int *, int, const double *, const double *, double *, double *,
+                                          double *, cudaStream_t);
+template cudaError_t launch_reduce<double>(const double *, int, const int8_t *, int, const KinGeom &, const int *,
+                                           const int *, int, const double *, const double *, double *, double *,
+                                           double *, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
+// Raw moments about the state velocity un -> rho, u, Tt, sigma, q about the mean velocity.
+// With d = S1/rho (u = un + d):  P = S2 - rho d d^T,  Tt = 2 tr P / (3 rho),
+//   q = 1/2 [S3 - tr(S2) d - 2 S2 d + 2 rho |d|^2 d].
+// Then the closed-domain mass scale s = mass_ref / sum(rho V) (the last block computes it
+// from the per-block partial masses in block order).
+__global__ void finalize_kernel(FinalizeArgs a) {
+  __shared__ double red[256];
+  double mloc = 0.0;
+  const int nc = a.g.nc;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < nc; cell += gridDim.x * blockDim.x) {
+    const double *S = a.mom + (size_t)cell * NMOM;
+    const double *un = a.st64 + (size_t)cell * NST;
+    const double rho = S[0];
+    const double d[3] = {S[1] / rho, S[2] / rho, S[3] / rho};
+    const double S2[3][3] = {{S[4], S[7], S[8]}, {S[7], S[5], S[9]}, {S[8], S[9], S[6]}};
+    double P[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) P[i][j] = S2[i][j] - rho * d[i] * d[j];
+    const double trP = P[0][0] + P[1][1] + P[2][2];
+    const double trS2 = S2[0][0] + S2[1][1] + S2[2][2];
+    const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double *M = a.Mh + (size_t)cell * 18;
+    M[0] = rho;
+    for (int i = 0; i < 3; ++i) M[1 + i] = un[i] + d[i];
+    M[4] = 2.0 * trP / (3.0 * rho);
+    M[5] = M[4];
+    M[6] = P[0][0] - trP / 3.0;
+    M[7] = P[1][1] - trP / 3.0;
+    M[8] = P[2][2] - trP / 3.0;
+    M[9] = P[0][1];
+    M[10] = P[0][2];
+    M[11] = P[1][2];
+    for (int i = 0; i < 3; ++i) {
+      const double S2d = S2[i][0] * d[0] + S2[i][1] * d[1] + S2[i][2] * d[2];
+      M[12 + i] = 0.5 * (S[10 + i] - trS2 * d[i] - 2.0 * S2d + 2.0 * rho * dd * d[i]);
+      M[15 + i] = 0.0;
+    }
+    if (!(rho > 0.0) || !(M[4] > 0.0) || !isfinite(M[12]) || !isfinite(M[13]) || !isfinite(M[14])) atomicCAS(a.err, 0, GSIS_ERR_DIVERGED);
+    mloc += rho * a.vol[cell];
+  }
+  red[threadIdx.x] = mloc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  __shared__ bool lastb;
+  if (threadIdx.x == 0) {
+    a.scratch[blockIdx.x] = red[0];
+    __threadfence();
+    const unsigned t = atomicAdd(a.ticket, 1u);
+    lastb = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (lastb && threadIdx.x == 0) {
+    __threadfence();
+    double tot = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) tot += ((volatile double *)a.scratch)[b];
+    a.mass_scale[0] = a.closed ? a.mass_ref / tot : 1.0;
+    a.mass_scale[1] = tot;
+    *a.ticket = 0u;
+  }
+}
+
+__global__ void scale_kernel(int nc, double *Mh, const double *mass_scale) {
+  const double s = mass_scale[0];
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < nc; cell += gridDim.x * blockDim.x) {
+    double *M = Mh + (size_t)cell * 18;
+    M[0] *= s;
+    for (int q = 6; q < 18; ++q) M[q] *= s;
+  }
+}
+
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
+  int grid = (a.g.nc + 255) / 256;
+  if (grid > 1024) grid = 1024;
+  finalize_kernel<<<grid, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  scale_kernel<<<grid, 256, 0, s>>>(a.g.nc, a.Mh, a.mass_scale);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// LSQ gradient of a cell field (stride floats apart) on the rectilinear block.
+__device__ __forceinline__ void grad_field(const KinGeom &g, const AxisCell<double> *const *ax, const double *q,
+                                           int stride, int cell, double *gr) {
+  const int nat[3] = {cell % g.n[0], (cell / g.n[0]) % g.n[1], cell / (g.n[0] * g.n[1])};
+  const int cs[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  const double qi = q[(size_t)cell * stride];
+  for (int a = 0; a < 3; ++a) {
+    gr[a] = 0.0;
+    if (!g.act[a]) continue;
+    const AxisCell<double> c = ax[a][nat[a]];
+    const double lo = nat[a] > 0 ? q[(size_t)(cell - cs[a]) * stride] : qi;
+    const double hi = nat[a] < g.n[a] - 1 ? q[(size_t)(cell + cs[a]) * stride] : qi;
+    gr[a] = c.clo * (lo - qi) + c.chi * (hi - qi);
+  }
+}
+
+__device__ __forceinline__ void conductivities(const CellFieldArgs &c, double mu, double *kt, double *kr) {
+  // Eq. mu_kappa with R = 1/2: (kt, kr) = (mu/4) A^{-1} (5, d_r); Shakhov: A_tt = 2/3, d_r = 0.
+  if (c.model == 0) {
+    *kt = mu * 15.0 / 8.0;
+    *kr = 0.0;
+    return;
+  }
+  const double det = c.A[0] * c.A[3] - c.A[1] * c.A[2];
+  *kt = mu / 4.0 * (c.A[3] * 5.0 - c.A[1] * c.d_r) / det;
+  *kr = mu / 4.0 * (-c.A[2] * 5.0 + c.A[0] * c.d_r) / det;
+}
+
+__global__ void hot_kernel(CellFieldArgs c, const double *Mh, double *hot) {
+  const int nc = c.g.nc;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < nc; cell += gridDim.x * blockDim.x) {
+    double G[3][3], gT[3], gTr[3];
+    for (int i = 0; i < 3; ++i) grad_field(c.g, c.ax, Mh + 1 + i, 18, cell, G[i]);
+    grad_field(c.g, c.ax, Mh + 4, 18, cell, gT);
+    grad_field(c.g, c.ax, Mh + 5, 18, cell, gTr);
+    const double *M = Mh + (size_t)cell * 18;
+    const double mu = c.Kn / sqrt(kPi) * pow(M[4], c.omega);
+    double kt, kr;
+    conductivities(c, mu, &kt, &kr);
+    const double div = G[0][0] + G[1][1] + G[2][2];
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    double *h = hot + (size_t)cell * 12;
+    for (int t = 0; t < 6; ++t) {
+      const int i = ia[t], j = ib[t];
+      h[t] = M[6 + t] + mu * (G[i][j] + G[j][i] - (i == j ? 2.0 / 3.0 * div : 0.0));
+    }
+    for (int i = 0; i < 3; ++i) {
+      h[6 + i] = M[12 + i] + kt * gT[i];
+      h[9 + i] = c.model == 1 ? M[15 + i] + kr * gTr[i] : 0.0;
+    }
+  }
+}
+
+cudaError_t launch_hot(const CellFieldArgs &c, const double *Mh, double *hot, cudaStream_t s) {
+  int grid = (c.g.nc + 255) / 256;
+  if (grid > 1024) grid = 1024;
+  hot_kernel<<<grid, 256, 0, s>>>(c, Mh, hot);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// State of the next kinetic step: reference distribution and collision rate from W^{n+1}
+// (heat flux from the kinetic moments of f^{n+1/2}); pending correction
+//   f^{n+1} = s f_raw + M(W^{n+1}) - M(W^{n+1/2})   (Eq. updatef).
+template <typename T>
+__global__ void state_kernel(StateArgs a) {
+  const int nc = a.g.nc;
+  const double s = a.mass_scale_ptr ? a.mass_scale_ptr[0] : a.mass_scale;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < nc; cell += gridDim.x * blockDim.x) {
+    const double *W = a.Wn + (size_t)cell * 6;
+    const double *M = a.Mh + (size_t)cell * 18;
+    double *st = a.st64 + (size_t)cell * NST;
+    const double rho = W[0], Tt = W[4];
+    st[0] = W[1];
+    st[1] = W[2];
+    st[2] = W[3];
+    st[3] = 1.0 / Tt;
+    st[4] = rho * pow(kPi * Tt, -1.5);
+    st[5] = M[1];
+    st[6] = M[2];
+    st[7] = M[3];
+    st[8] = 1.0 / M[4];
+    st[9] = M[0] * pow(kPi * M[4], -1.5);
+    st[10] = s;
+    const double invtau = rho * sqrt(kPi) / (2.0 * a.Kn) * pow(Tt, 1.0 - a.omega);
+    st[11] = invtau;
+    const double A = 8.0 / (15.0 * rho * Tt * Tt);
+    st[12] = A * M[12];
+    st[13] = A * M[13];
+    st[14] = A * M[14];
+    st[15] = a.kin_inv_dt + invtau;
+    for (int q = 16; q < NST; ++q) st[q] = 0.0;
+    T *out = reinterpret_cast<T *>(a.stT) + (size_t)cell * NST;
+    for (int q = 0; q < NST; ++q) out[q] = (T)st[q];
+  }
+}
+
+cudaError_t launch_state(const StateArgs &a, cudaStream_t s) {
+  int grid = (a.g.nc + 255) / 256;
+  if (grid > 1024) grid = 1024;
+  if (a.is_float) state_kernel<float><<<grid, 256, 0, s>>>(a);
+  else state_kernel<double><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// eps over rho, u (as a vector) and Tt; fields whose RMS is below 1e-12 count as zero.
+__global__ void eps_kernel(EpsArgs a) {
+  __shared__ double red[6][256];
+  double loc[6] = {0, 0, 0, 0, 0, 0};
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < a.nc; cell += gridDim.x * blockDim.x) {
+    const double *n = a.Wn + (size_t)cell * 6, *o = a.Wo + (size_t)cell * 6;
+    const double V = a.vol[cell];
+    loc[0] += (n[0] - o[0]) * (n[0] - o[0]) * V;
+    loc[1] += o[0] * o[0] * V;
+    for (int d = 1; d <= 3; ++d) {
+      loc[2] += (n[d] - o[d]) * (n[d] - o[d]) * V;
+      loc[3] += o[d] * o[d] * V;
+    }
+    loc[4] += (n[4] - o[4]) * (n[4] - o[4]) * V;
+    loc[5] += o[4] * o[4] * V;
+  }
+  for (int q = 0; q < 6; ++q) red[q][threadIdx.x] = loc[q];
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off)
+      for (int q = 0; q < 6; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + off];
+    __syncthreads();
+  }
+  __shared__ bool lastb;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 6; ++q) a.scratch[7 * blockIdx.x + q] = red[q][0];
+    __threadfence();
+    lastb = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (lastb && threadIdx.x == 0) {
+    __threadfence();
+    double tot[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < (int)gridDim.x; ++b)
+      for (int q = 0; q < 6; ++q) tot[q] += ((volatile double *)a.scratch)[7 * b + q];
+    const double vsum = a.vsum;
+    double mx = 0.0;
+    for (int f = 0; f < 3; ++f) {
+      double e = 0.0;
+      if (tot[2 * f + 1] > 1e-24 * vsum) e = sqrt(tot[2 * f] / tot[2 * f + 1]);
+      a.eps4[f] = e;
+      mx = e > mx ? e : mx;
+    }
+    a.eps4[3] = mx;
+    *a.ticket = 0u;
+  }
+}
+
+cudaError_t launch_eps(const EpsArgs &a, cudaStream_t s) {
+  int grid = (a.nc + 255) / 256;
+  if (grid > 256) grid = 256;
+  eps_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace gsis
