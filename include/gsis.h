@@ -97,7 +97,7 @@ typedef struct {
   int macro_sweeps;     /* red-black LU-SGS passes per inner step (default 4, Algorithm 2) */
   double macro_cfl;     /* pseudo-time CFL of the synthetic solve (default 100) */
   double macro_tol;     /* inner early exit on the relative increment (default 1e-10) */
-  double kin_inv_dt;    /* 1/dt of the kinetic delta form (default 0: steady) */
+  double kin_inv_dt;    /* 1/dt of the kinetic delta form (default 0: steady; this build supports 0) */
   double venkat_K;      /* Venkatakrishnan constant, eps^2 = (K V^(1/3))^3 (default 1) */
   int kinetic_presteps; /* plain kinetic steps before the GSIS loop (default 10, Algorithm 1) */
   const double *init_W; /* optional host array, per cell rho, ux, uy, uz, Tt, Tr; f0 = Maxwellian.
@@ -153,9 +153,11 @@ int gsis_residual(gsis_handle h, double *eps_by_field, int n);
 int gsis_nwall(gsis_handle h);
 int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, double *flux6);
 
-/* Per cell and side the outward kinetic face flux of the last kinetic step (6 components,
- * area-integrated, zero for absent faces): host_out holds ncells x 6 x 6 doubles. */
-int gsis_face_flux(gsis_handle h, double *host_out, size_t out_len);
+/* Per cell the sum over its faces of the outward kinetic face flux of the last kinetic step
+ * (mass, momentum(3), energy, internal energy; area-integrated): the kinetic information the
+ * synthetic solve uses (Eq. full_constitutive evaluated with the kinetic scheme's own fluxes).
+ * host_out holds ncells x 6 doubles. */
+int gsis_kinetic_flux_sum(gsis_handle h, double *host_out, size_t out_len);
 
 /* VDF transfer, FP64 host arrays [cell][v] (f1 for the Rykov model only, else NULL).
  * gsis_set_f also resets the per-cell state to the moments of the new f (checkpoint load). */

@@ -43,6 +43,8 @@ struct gsis_solver {
   double vsum = 0.0;
   KinGeom kg{};
   std::vector<int> col_off, col_cell, pos_of;
+  std::vector<EntryInfo> entries;
+  std::vector<int4> natcell;
   // velocities
   int nvc = 0, nslots = 0, nblocks = 0, np = 0;
   int nv_axis[3] = {0, 0, 0};
@@ -56,22 +58,26 @@ struct gsis_solver {
   int closed = 1;
   // device
   std::vector<DevBuf> allocs;
-  void *d_f = nullptr, *d_part = nullptr, *d_stT = nullptr, *d_vel = nullptr;
+  void *d_f = nullptr, *d_wpart = nullptr, *d_stT = nullptr, *d_vel = nullptr;
+  double *d_mp = nullptr, *d_K = nullptr;
+  int mom_bpc = 1, mom_nchunks = 1;
   void *d_ax[3] = {nullptr, nullptr, nullptr};
   AxisCell<double> *d_ax64[3] = {nullptr, nullptr, nullptr};
   double *d_vel64 = nullptr, *d_st64 = nullptr, *d_rho_w = nullptr, *d_Z0 = nullptr, *d_Zw = nullptr;
-  double *d_wall_uT = nullptr, *d_mom = nullptr, *d_ff = nullptr, *d_wf = nullptr, *d_Mh = nullptr;
+  double *d_wall_uT = nullptr, *d_mom = nullptr, *d_wf = nullptr, *d_Mh = nullptr;
   double *d_hot = nullptr, *d_Wstate = nullptr, *d_Wnew = nullptr, *d_vol = nullptr, *d_mass = nullptr;
   double *d_scratch = nullptr, *d_eps4 = nullptr;
   int8_t *d_boct = nullptr;
   int *d_col_off = nullptr, *d_col_cell = nullptr, *d_pos_of = nullptr, *d_wall_cell = nullptr;
   int *d_wall_side = nullptr, *d_wall_sides = nullptr, *d_err = nullptr, *d_iters = nullptr;
+  EntryInfo *d_entry = nullptr;
+  int4 *d_natcell = nullptr;
   unsigned *d_ticket = nullptr, *d_bar = nullptr;
   // macro work
   double *m_W = nullptr, *m_pr = nullptr, *m_gW = nullptr, *m_phW = nullptr, *m_gP = nullptr, *m_mu = nullptr;
   double *m_R = nullptr, *m_D = nullptr, *m_dW = nullptr, *m_Fc = nullptr, *m_corr = nullptr, *m_gam = nullptr;
-  double *m_feq0 = nullptr, *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr;
-  int macro_grid = 0;
+  double *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr;
+  int macro_grid = 0, macro_block = 256;
   int kin_warps = 1;
   size_t kin_smem = 0;
   // profiling
@@ -146,12 +152,15 @@ struct gsis_solver {
     a.col_off = d_col_off;
     a.col_cell = d_col_cell;
     a.pos_of = d_pos_of;
+    a.entry = d_entry;
+    a.natcell = d_natcell;
     a.st = static_cast<const T *>(d_stT);
     a.rho_w = d_rho_w;
     a.wall_uT = d_wall_uT;
     a.f = static_cast<T *>(d_f);
-    a.part = static_cast<T *>(d_part);
-    a.np = np;
+    a.wpart = static_cast<T *>(d_wpart);
+    a.nwall = nwall;
+    a.nblocks = nblocks;
     return a;
   }
 
@@ -167,12 +176,15 @@ struct gsis_solver {
     return GSIS_OK;
   }
 
-  // moments of the current (corrected) f -> Mh, using a state whose velocity is st64[0..2]
+  // moments of the stored f -> Mh (about the state velocity st64[0..2]), the kinetic flux sum K
+  // and the wall fluxes
   template <typename T>
   int reduce_and_finalize(bool closed_scale) {
-    int rc = cuda(launch_reduce<T>(static_cast<const T *>(d_part), np, d_boct, nblocks, kg, d_wall_cell, d_wall_side,
-                                   nwall, d_rho_w, d_Zw, d_mom, d_ff, d_wf, stream),
-                  "reduce");
+    int rc = cuda(launch_moments<T>(kin_args<T>(), mom_bpc, mom_nchunks, d_mp, stream), "moments");
+    if (rc) return rc;
+    rc = cuda(launch_reduce<T>(d_mp, mom_nchunks, static_cast<const T *>(d_wpart), d_boct, nblocks, kg, d_wall_cell,
+                               d_wall_side, nwall, d_rho_w, d_Zw, d_vol, d_st64, d_mom, d_K, d_wf, stream),
+              "reduce");
     if (rc) return rc;
     FinalizeArgs fa{};
     fa.g = kg;
@@ -213,7 +225,6 @@ struct gsis_solver {
     std::vector<T> st0T(st0.begin(), st0.end());
     int rc = upload(d_st64, st0.data(), st0.size() * sizeof(double));
     if (!rc) rc = upload(d_stT, st0T.data(), st0T.size() * sizeof(T));
-    if (!rc) rc = cuda(launch_moments_only<T>(kin_args<T>(), nblocks, stream), "moments");
     if (!rc) rc = reduce_and_finalize<T>(false);
     if (rc) return rc;
     double m2[2];
@@ -245,7 +256,7 @@ struct gsis_solver {
     mark(2);
     rc = reduce_and_finalize<T>(true);
     if (rc) return rc;
-    launches += 1 + 1 + 2;
+    launches += 1 + 1 + (nwall > 0) + 2;
     mark(3);
     if (mode == GSIS_MODE_GSIS) {
       MacroArgs m{};
@@ -265,21 +276,20 @@ struct gsis_solver {
       m.mass_ref = mass_ref;
       m.closed = closed;
       m.Mh = d_Mh;
-      m.ffk = d_ff;
-      m.wfk = d_wf;
+      m.K = d_K;
       m.wall_cell = d_wall_cell;
       m.wall_side = d_wall_side;
       m.nwall = nwall;
       m.wall_uT = d_wall_uT;
       m.W = m_W; m.pr = m_pr; m.gW = m_gW; m.phW = m_phW; m.gP = m_gP; m.mu = m_mu; m.R = m_R; m.D = m_D;
-      m.dW = m_dW; m.Fc = m_Fc; m.corr = m_corr; m.gam = m_gam; m.feq0 = m_feq0; m.red = m_red; m.Ffc = m_Ffc;
+      m.dW = m_dW; m.Fc = m_Fc; m.corr = m_corr; m.gam = m_gam; m.red = m_red; m.Ffc = m_Ffc;
       m.wfl = m_wfl;
       m.Wout = d_Wnew;
       m.bar = d_bar;
       m.err = d_err;
       m.iters = d_iters;
       if (opt.macro_steps > 0) {
-        rc = cuda(launch_macro(m, macro_grid, macro_block_size(), stream), "synthetic solve");
+        rc = cuda(launch_macro(m, macro_grid, macro_block, stream), "synthetic solve");
         if (rc) return rc;
         ++launches;
       } else {
@@ -366,6 +376,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   if (o->mode != GSIS_MODE_GSIS && o->mode != GSIS_MODE_DVM) { why = "bad mode"; return GSIS_E_INVALID; }
   if (g->model == GSIS_RYKOV) { why = "Rykov model is not implemented on the GPU yet"; return GSIS_E_UNSUPPORTED; }
   if (g->model != GSIS_SHAKHOV) { why = "bad model"; return GSIS_E_INVALID; }
+  if (o->kin_inv_dt != 0.0) { why = "the GPU kinetic step is steady (kin_inv_dt = 0)"; return GSIS_E_UNSUPPORTED; }
   if (o->n_sweeps != 1) { why = "rectilinear colour sweeps are exact in one pass: n_sweeps must be 1"; return GSIS_E_UNSUPPORTED; }
   const int n[3] = {m->ni, m->nj, m->nk};
   bool seen_inactive = false;
@@ -442,7 +453,7 @@ template <typename T>
 std::vector<AxisCell<T>> cast_axis(const std::vector<AxisCell<double>> &in) {
   std::vector<AxisCell<T>> out(in.size());
   for (size_t i = 0; i < in.size(); ++i)
-    out[i] = {(T)in[i].invh, (T)in[i].rlo, (T)in[i].rhi, (T)in[i].clo, (T)in[i].chi, (T)in[i].h};
+    out[i] = {(T)in[i].invh, (T)in[i].rlo, (T)in[i].rhi, (T)in[i].clo, (T)in[i].chi, (T)in[i].h, (T)0, (T)0};
   return out;
 }
 
@@ -523,6 +534,31 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
       s->pos_of[i + s->n[0] * (j + s->n[1] * k)] = (int)p;
     }
   }
+  // per colour entry: neighbour positions in the adjacent colours and transformed transverse
+  // indices (octant independent); per octant: the natural cell of every entry
+  s->entries.assign(s->nc, EntryInfo{});
+  s->natcell.assign((size_t)8 * s->nc, int4{0, 0, 0, 0});
+  {
+    const int n0 = s->n[0], n1 = s->n[1], n2 = s->n[2];
+    for (int e = 0; e < s->nc; ++e) {
+      const int tp = s->col_cell[e];
+      const int tc[3] = {tp & 1023, (tp >> 10) & 1023, tp >> 20};
+      const int t = tc[0] + n0 * (tc[1] + n1 * tc[2]);
+      const int st[3] = {1, n0, n0 * n1};
+      EntryInfo &E = s->entries[e];
+      for (int a = 0; a < 3; ++a) {
+        E.nb[2 * a] = tc[a] > 0 ? s->pos_of[t - st[a]] : -1;
+        E.nb[2 * a + 1] = tc[a] < s->n[a] - 1 ? s->pos_of[t + st[a]] : -1;
+      }
+      E.trn[0] = tc[1] + n1 * tc[2];
+      E.trn[1] = tc[0] + n0 * tc[2];
+      E.trn[2] = tc[0] + n0 * tc[1];
+      for (int oct = 0; oct < 8; ++oct) {
+        const int nat[3] = {oct & 1 ? n0 - 1 - tc[0] : tc[0], oct & 2 ? n1 - 1 - tc[1] : tc[1], oct & 4 ? n2 - 1 - tc[2] : tc[2]};
+        s->natcell[(size_t)oct * s->nc + e] = int4{nat[0] + n0 * (nat[1] + n1 * nat[2]), nat[0], nat[1], nat[2]};
+      }
+    }
+  }
   // walls
   s->nwall = 0;
   s->wall_cell.clear();
@@ -566,7 +602,8 @@ static size_t footprint(const gsis_solver *s) {
   const size_t nc = s->nc;
   size_t b = 0;
   b += (size_t)s->nslots * nc * T;            // f
-  b += (size_t)s->nblocks * nc * s->np * T;   // partials
+  b += (size_t)s->nblocks * (s->nwall + 1) * NFF * T;  // wall partials
+  b += (size_t)64 * nc * (NMOM + NFF) * 8 / 64 + nc * (NMOM + NFF) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
   b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 18 + 18 + 3 + 18) * 8;  // synthetic-solve work
@@ -581,7 +618,15 @@ static int allocate_and_upload(gsis_solver *s) {
 #define A(ptr, bytes) \
   if (!rc) rc = s->alloc(&(ptr), (bytes))
   A(s->d_f, (size_t)s->nslots * nc * sizeof(T));
-  A(s->d_part, (size_t)s->nblocks * nc * s->np * sizeof(T));
+  // moment chunks: enough (cell, chunk) threads to fill the GPU, at most 64 blocks per chunk
+  {
+    const int want = std::max(1, (int)((160000 + nc - 1) / nc));
+    s->mom_bpc = std::max(1, std::min(64, (s->nblocks + want - 1) / want));
+    s->mom_nchunks = (s->nblocks + s->mom_bpc - 1) / s->mom_bpc;
+  }
+  A(s->d_mp, (size_t)s->mom_nchunks * nc * (NMOM + NFF) * sizeof(double));
+  A(s->d_wpart, (size_t)s->nblocks * (s->nwall + 1) * NFF * sizeof(T));
+  A(s->d_K, nc * 6 * sizeof(double));
   A(s->d_stT, nc * NST * sizeof(T));
   A(s->d_st64, nc * NST * sizeof(double));
   A(s->d_vel, (size_t)s->nslots * 4 * sizeof(T));
@@ -594,6 +639,8 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->d_col_off, s->col_off.size() * sizeof(int));
   A(s->d_col_cell, nc * sizeof(int));
   A(s->d_pos_of, nc * sizeof(int));
+  A(s->d_entry, nc * sizeof(EntryInfo));
+  A(s->d_natcell, 8 * nc * sizeof(int4));
   A(s->d_rho_w, (size_t)(s->nwall + 1) * sizeof(double));
   A(s->d_Z0, 6 * sizeof(double));
   A(s->d_Zw, 36 * sizeof(double));
@@ -602,7 +649,6 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->d_wall_side, (size_t)(s->nwall + 1) * sizeof(int));
   A(s->d_wall_sides, 6 * sizeof(int));
   A(s->d_mom, nc * NMOM * sizeof(double));
-  A(s->d_ff, nc * 18 * sizeof(double));
   A(s->d_wf, (size_t)(s->nwall + 1) * 6 * sizeof(double));
   A(s->d_Mh, nc * 18 * sizeof(double));
   A(s->d_hot, nc * 12 * sizeof(double));
@@ -626,17 +672,14 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->m_D, nc * 6 * sizeof(double));
   A(s->m_dW, nc * 6 * sizeof(double));
   A(s->m_Fc, nc * 18 * sizeof(double));
-  A(s->m_corr, nc * 18 * sizeof(double));
+  A(s->m_corr, nc * 6 * sizeof(double));
   A(s->m_gam, nc * 3 * sizeof(double));
-  A(s->m_feq0, (size_t)(s->nwall + 1) * 6 * sizeof(double));
   A(s->m_Ffc, nc * 18 * sizeof(double));
   A(s->m_wfl, (size_t)(s->nwall + 1) * 6 * sizeof(double));
 #undef A
   if (rc) return rc;
-  rc = s->cuda(macro_max_grid(&s->macro_grid), "occupancy");
+  rc = s->cuda(macro_launch_shape((int)nc, &s->macro_grid, &s->macro_block), "occupancy");
   if (rc) return rc;
-  const int want = (int)((nc + 255) / 256);
-  if (want < s->macro_grid) s->macro_grid = std::max(1, want);
   rc = s->alloc(&s->m_red, (size_t)s->macro_grid * 16 * sizeof(double));
   if (rc) return rc;
   std::vector<T> velT(s->vel64.begin(), s->vel64.end());
@@ -651,6 +694,8 @@ static int allocate_and_upload(gsis_solver *s) {
   if (!rc) rc = s->upload(s->d_col_off, s->col_off.data(), s->col_off.size() * sizeof(int));
   if (!rc) rc = s->upload(s->d_col_cell, s->col_cell.data(), nc * sizeof(int));
   if (!rc) rc = s->upload(s->d_pos_of, s->pos_of.data(), nc * sizeof(int));
+  if (!rc) rc = s->upload(s->d_entry, s->entries.data(), nc * sizeof(EntryInfo));
+  if (!rc) rc = s->upload(s->d_natcell, s->natcell.data(), 8 * nc * sizeof(int4));
   if (!rc && s->nwall) rc = s->upload(s->d_wall_cell, s->wall_cell.data(), s->nwall * sizeof(int));
   if (!rc && s->nwall) rc = s->upload(s->d_wall_side, s->wall_side.data(), s->nwall * sizeof(int));
   if (!rc && !s->wall_sides_list.empty())
@@ -661,7 +706,7 @@ static int allocate_and_upload(gsis_solver *s) {
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(unsigned), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_rho_w, 0, (s->nwall + 1) * sizeof(double), s->stream), "memset");
-  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_ff, 0, nc * 18 * sizeof(double), s->stream), "memset");
+  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_K, 0, nc * 6 * sizeof(double), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_wf, 0, (s->nwall + 1) * 6 * sizeof(double), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_hot, 0, nc * 12 * sizeof(double), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_Z0, 0, 6 * sizeof(double), s->stream), "memset");
@@ -842,34 +887,13 @@ extern "C" int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, dou
   return GSIS_OK;
 }
 
-extern "C" int gsis_face_flux(gsis_handle h, double *out, size_t out_len) {
+extern "C" int gsis_kinetic_flux_sum(gsis_handle h, double *out, size_t out_len) {
   if (!h || !out) return GSIS_E_INVALID;
   const size_t nc = h->nc;
-  if (out_len < nc * 36) return h->fail(GSIS_E_INVALID, "out_len too small");
-  std::vector<double> ff(nc * 18), wf((size_t)(h->nwall + 1) * 6);
-  int rc = h->cuda(cudaMemcpyAsync(ff.data(), h->d_ff, nc * 18 * 8, cudaMemcpyDeviceToHost, h->stream), "ff");
-  if (!rc) rc = h->cuda(cudaMemcpyAsync(wf.data(), h->d_wf, (h->nwall + 1) * 48, cudaMemcpyDeviceToHost, h->stream), "wf");
+  if (out_len < nc * 6) return h->fail(GSIS_E_INVALID, "out_len too small");
+  int rc = h->cuda(cudaMemcpyAsync(out, h->d_K, nc * 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "K");
   if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
-  if (rc) return rc;
-  std::memset(out, 0, nc * 36 * sizeof(double));
-  const int cs[3] = {1, h->n[0], h->n[0] * h->n[1]};
-  for (size_t c = 0; c < nc; ++c) {
-    const int nat[3] = {(int)c % h->n[0], ((int)c / h->n[0]) % h->n[1], (int)c / (h->n[0] * h->n[1])};
-    for (int a = 0; a < 3; ++a) {
-      if (h->n[a] == 1) continue;
-      const double A = face_area(h, (int)c, a);
-      const int trn = a == 0 ? nat[1] + h->n[1] * nat[2] : (a == 1 ? nat[0] + h->n[0] * nat[2] : nat[0] + h->n[0] * nat[1]);
-      for (int k = 0; k < 6; ++k) {
-        // + side
-        double vplus = nat[a] < h->n[a] - 1 ? ff[c * 18 + a * 6 + k] : wf[(size_t)(h->kg.wall_base[2 * a + 1] + trn) * 6 + k];
-        // - side (outward = -e_a)
-        double vminus = nat[a] > 0 ? -ff[(c - cs[a]) * 18 + a * 6 + k] : wf[(size_t)(h->kg.wall_base[2 * a] + trn) * 6 + k];
-        out[c * 36 + (2 * a + 1) * 6 + k] = vplus * A;
-        out[c * 36 + (2 * a) * 6 + k] = vminus * A;
-      }
-    }
-  }
-  return GSIS_OK;
+  return rc;
 }
 
 extern "C" int gsis_get_f(gsis_handle h, double *f0, double *f1) {

@@ -19,8 +19,17 @@ constexpr int GSIS_ERR_TIMEOUT = -5;
 //   gradient along the axis: g = clo (q[i-1] - q[i]) + chi (q[i+1] - q[i])  (missing neighbour: 0)
 //   face offsets from the cell centre: rlo = X[i] - xc[i] < 0, rhi = X[i+1] - xc[i] > 0
 template <typename T>
-struct AxisCell {
-  T invh, rlo, rhi, clo, chi, h;
+struct alignas(8 * sizeof(T)) AxisCell {
+  T invh, rlo, rhi, clo, chi, h, pad0, pad1;
+};
+
+// Per colour entry (octant independent): position inside the previous / next colour of the
+// transformed upwind and downwind neighbour along each axis (-1 if none) and the transformed
+// transverse index of the entry for each axis (index of its e-buffer slot).
+struct alignas(16) EntryInfo {
+  int nb[6];    // up x, dn x, up y, dn y, up z, dn z
+  int trn[3];
+  int pad[3];
 };
 
 // Per-cell kinetic state (values in the precision of the kinetic kernel):
@@ -58,12 +67,15 @@ struct KinArgs {
   const int *col_off;    // [ncol+1]
   const int *col_cell;   // transformed coords packed i' | j' << 10 | k' << 20
   const int *pos_of;     // position of a transformed cell inside its colour
+  const EntryInfo *entry;  // [entry] neighbour positions and transverse indices
+  const int4 *natcell;     // [octant][entry]: cell index and natural coordinates
   const T *st;           // [cell][NST]
   const double *rho_w;   // [nwall]
   const double *wall_uT; // [6][4]: u_w(3), T_w
   T *f;                  // [block][cell][VB] f_raw, updated in place
-  T *part;               // [block][cell][np] partial moments
-  int np;
+  T *wpart;              // [block][wall face][NFF] outgoing wall-flux moments (wall cells only)
+  int nwall;
+  int nblocks;
 };
 
 // ---- launchers (defined in the .cu files) ----
@@ -75,7 +87,7 @@ template <typename T>
 cudaError_t launch_wall_prepass(const KinArgs<T> &a, const int *wall_cell, const int *wall_side, int nwall,
                                 const double *Z0, double *rho_w, int nslots, cudaStream_t s);
 template <typename T>
-cudaError_t launch_moments_only(const KinArgs<T> &a, int nblocks, cudaStream_t s);
+cudaError_t launch_moments(const KinArgs<T> &a, int blocks_per_chunk, int nchunks, double *mp, cudaStream_t s);
 template <typename T>
 cudaError_t launch_init_maxwellian(const KinArgs<T> &a, const double *W0, int nblocks, cudaStream_t s);
 template <typename T>
@@ -88,10 +100,14 @@ cudaError_t launch_import_f(const KinArgs<T> &a, const int *slot_canon, int nslo
 cudaError_t launch_wall_constants(const double *vel64, int nslots, const double *wall_uT, const int *sides,
                                   int nsides, double *Z0, double *Zw, double d_r, cudaStream_t s);
 
+// per-chunk moment partials [chunk][cell][18] -> mom [cell][13] and kinetic flux sum
+// K [cell][6] (outward, area-integrated, via the delta-form identity); per-block wall partials
+// -> wf [wall][6] outward kinetic wall flux per unit area.
 template <typename T>
-cudaError_t launch_reduce(const T *part, int np, const int8_t *boct, int nblocks, const KinGeom &g,
-                          const int *wall_cell, const int *wall_side, int nwall, const double *rho_w,
-                          const double *Zw, double *mom, double *ff, double *wf, cudaStream_t s);
+cudaError_t launch_reduce(const double *mp, int nchunks, const T *wpart, const int8_t *boct, int nblocks,
+                          const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
+                          const double *rho_w, const double *Zw, const double *vol, const double *st64,
+                          double *mom, double *K, double *wf, cudaStream_t s);
 
 struct FinalizeArgs {
   KinGeom g;
@@ -150,13 +166,12 @@ struct MacroArgs {
   double mass_ref;
   int closed;
   const double *Mh;        // [cell][18] initial state W^{n+1/2}
-  const double *ffk;       // [cell][3][NFF+1] kinetic + face flux per unit area (natural +e_a)
-  const double *wfk;       // [nwall][6] kinetic wall flux, outward, per unit area
+  const double *K;         // [cell][6] sum over the cell's faces of the outward kinetic flux (area-integrated)
   const int *wall_cell, *wall_side;
   int nwall;
   const double *wall_uT;   // [6][4]
   // work (device, sized by the host)
-  double *W, *pr, *gW, *phW, *gP, *mu, *R, *D, *dW, *Fc, *corr, *gam, *feq0, *red, *Ffc, *wfl;
+  double *W, *pr, *gW, *phW, *gP, *mu, *R, *D, *dW, *Fc, *corr, *gam, *red, *Ffc, *wfl;
   double *Wout;            // [cell][6] prim W^{n+1}
   unsigned *bar;           // [2] barrier counter, generation
   int *err;
@@ -165,5 +180,6 @@ struct MacroArgs {
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s);
 int macro_block_size();
 cudaError_t macro_max_grid(int *grid);
+cudaError_t macro_launch_shape(int nc, int *grid, int *block);
 
 }  // namespace gsis

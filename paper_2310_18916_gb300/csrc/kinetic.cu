@@ -66,10 +66,43 @@ __device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const
   return ddiv(bn, bd);
 }
 
-template <typename T>
-__device__ __forceinline__ void load_state(const T *__restrict__ src, T *st) {
+__device__ __forceinline__ void load_state(const float *__restrict__ src, float *st) {
+  const float4 *p = reinterpret_cast<const float4 *>(src);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) st[q] = __ldg(src + q);
+  for (int q = 0; q < 4; ++q) {
+    const float4 v = __ldg(p + q);
+    st[4 * q] = v.x;
+    st[4 * q + 1] = v.y;
+    st[4 * q + 2] = v.z;
+    st[4 * q + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_state(const double *__restrict__ src, double *st) {
+  const double2 *p = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double2 v = __ldg(p + q);
+    st[2 * q] = v.x;
+    st[2 * q + 1] = v.y;
+  }
+}
+
+// Sum over the 32 lanes of v[0..31] by recursive halving: at each level a lane keeps the half
+// of its vector selected by one bit of its lane index and adds the partner's copy of that half.
+// Afterwards lane l holds the warp total of v[l] (31 shuffles instead of 5 per value).
+template <typename T>
+__device__ __forceinline__ T transpose_reduce(T *v, int lane) {
+#pragma unroll
+  for (int h = 16; h > 0; h >>= 1) {
+    const bool up = lane & h;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return v[0];
 }
 
 template <typename T>
@@ -110,28 +143,17 @@ __global__ void kinetic_kernel(const KinArgs<T> A) {
     if (a < NACT && G.wall_base[upside[a]] >= 0)
       Mw[a] = wall_maxwellian<T>(A.wall_uT + 4 * upside[a], xi[0], xi[1], xi[2]);
   }
-  const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
-  const int tstride[3] = {1, n0, n0 * n1};
+  const int n0 = G.n[0], n1 = G.n[1];
   T *F = A.f + (size_t)b * G.nc * VB;
-  T *P = A.part + (size_t)b * G.nc * A.np;
+  const int4 *natcell = A.natcell + (size_t)oct * G.nc;
   const T K3 = (T)G.K3;
-
-  auto decode = [&](int tp, int *tc, int *nat) {
-    tc[0] = tp & 1023;
-    tc[1] = (tp >> 10) & 1023;
-    tc[2] = tp >> 20;
-    nat[0] = sg[0] > 0 ? tc[0] : n0 - 1 - tc[0];
-    nat[1] = sg[1] > 0 ? tc[1] : n1 - 1 - tc[1];
-    nat[2] = sg[2] > 0 ? tc[2] : n2 - 1 - tc[2];
-  };
+  const size_t slot_stride = (size_t)G.maxcol * VB;
 
   auto stage = [&](int c) {
     const int off = A.col_off[c], cnt = A.col_off[c + 1] - off;
-    T *slot = ring + (size_t)(c % 3) * G.maxcol * VB;
+    T *slot = ring + (size_t)(c % 3) * slot_stride;
     for (int p = warp; p < cnt; p += nw) {
-      int tc[3], nat[3];
-      decode(A.col_cell[off + p], tc, nat);
-      const int cell = nat[0] + n0 * (nat[1] + n1 * nat[2]);
+      const int cell = __ldg(&natcell[off + p].x);
       T st[16];
       load_state(A.st + (size_t)cell * NST, st);
       slot[p * VB + lane] = corrected(F[(size_t)cell * VB + lane], st, xi[0], xi[1], xi[2]);
@@ -142,15 +164,20 @@ __global__ void kinetic_kernel(const KinArgs<T> A) {
   for (int c = 0; c < G.ncol; ++c) {
     if (c + 1 < G.ncol) stage(c + 1);
     __syncthreads();
-    const T *slotm = ring + (size_t)((c + 2) % 3) * G.maxcol * VB;
-    const T *slot0 = ring + (size_t)(c % 3) * G.maxcol * VB;
-    const T *slotp = ring + (size_t)((c + 1) % 3) * G.maxcol * VB;
+    const T *slotm = ring + (size_t)((c + 2) % 3) * slot_stride;
+    const T *slot0 = ring + (size_t)(c % 3) * slot_stride;
+    const T *slotp = ring + (size_t)((c + 1) % 3) * slot_stride;
     const int off = A.col_off[c], cnt = A.col_off[c + 1] - off;
     for (int p = warp; p < cnt; p += nw) {
-      int tc[3], nat[3];
-      decode(A.col_cell[off + p], tc, nat);
-      const int cell = nat[0] + n0 * (nat[1] + n1 * nat[2]);
-      const int t = tc[0] + n0 * (tc[1] + n1 * tc[2]);
+      const int4 nc4 = __ldg(&natcell[off + p]);
+      const int cell = nc4.x;
+      const int nat[3] = {nc4.y, nc4.z, nc4.w};
+      const EntryInfo &E = A.entry[off + p];
+      int nb[6], trn[3];
+#pragma unroll
+      for (int q = 0; q < 2 * NACT; ++q) nb[q] = __ldg(&E.nb[q]);
+#pragma unroll
+      for (int q = 0; q < NACT; ++q) trn[q] = __ldg(&E.trn[q]);
       const T fi = slot0[p * VB + lane];
       T st[16];
       load_state(A.st + (size_t)cell * NST, st);
@@ -162,17 +189,15 @@ __global__ void kinetic_kernel(const KinArgs<T> A) {
       for (int a = 0; a < 3; ++a) {
         const AxisCell<T> gc = A.ax[a][nat[a]];
         V *= gc.h;
-        gr[a] = (T)0;
         if (a < NACT) {
-          const int na = G.n[a];
           T fup = fi, fdn = fi;
-          if (tc[a] > 0) {
-            fup = slotm[A.pos_of[t - tstride[a]] * VB + lane];
+          if (nb[2 * a] >= 0) {
+            fup = slotm[nb[2 * a] * VB + lane];
             fmax = fmax > fup ? fmax : fup;
             fmin = fmin < fup ? fmin : fup;
           }
-          if (tc[a] < na - 1) {
-            fdn = slotp[A.pos_of[t + tstride[a]] * VB + lane];
+          if (nb[2 * a + 1] >= 0) {
+            fdn = slotp[nb[2 * a + 1] * VB + lane];
             fmax = fmax > fdn ? fmax : fdn;
             fmin = fmin < fdn ? fmin : fdn;
           }
@@ -190,58 +215,45 @@ __global__ void kinetic_kernel(const KinArgs<T> A) {
       const T g = st[4] * dexp(-c2 * st[3]) * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
       T acc = (g - fi) * st[11];
       T D = st[15];
-      T fout[3], tr[3];
+      T fout[3];
 #pragma unroll
       for (int a = 0; a < NACT; ++a) {
         fout[a] = fi + phi * gr[a] * (sg[a] > 0 ? rhi[a] : rlo[a]);
-        const int trn = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
-        tr[a] = (T)0;
         T ein;
-        if (tc[a] > 0) ein = ebuf[a][trn * VB + lane];
-        else ein = (T)A.rho_w[G.wall_base[upside[a]] + trn] * Mw[a];
+        if (nb[2 * a] >= 0) {
+          ein = ebuf[a][trn[a] * VB + lane];
+        } else {
+          // upwind boundary: the natural transverse index of the wall face
+          const int trw = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
+          ein = (T)A.rho_w[G.wall_base[upside[a]] + trw] * Mw[a];
+        }
         const T k = axi[a] * invh[a];
         D += k;
         acc -= k * (fout[a] - ein);
       }
       const T df = ddiv(acc, D);
-      const T fnew = fi + df;
-      F[(size_t)cell * VB + lane] = fnew;
-      // moments of f^{n+1/2} about the state velocity, and of the outflow face fluxes
-      const T wf = wv * fnew;
-      T vals[MAXNP];
-      vals[0] = wf;
-      vals[1] = wf * cx;
-      vals[2] = wf * cy;
-      vals[3] = wf * cz;
-      vals[4] = wf * cx * cx;
-      vals[5] = wf * cy * cy;
-      vals[6] = wf * cz * cz;
-      vals[7] = wf * cx * cy;
-      vals[8] = wf * cx * cz;
-      vals[9] = wf * cy * cz;
-      vals[10] = wf * c2 * cx;
-      vals[11] = wf * c2 * cy;
-      vals[12] = wf * c2 * cz;
+      F[(size_t)cell * VB + lane] = fi + df;
 #pragma unroll
       for (int a = 0; a < NACT; ++a) {
-        const int trn = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
         const T eout = fout[a] + df;
-        ebuf[a][trn * VB + lane] = eout;
-        const T fl = wv * xi[a] * eout;
-        vals[13 + 5 * a + 0] = fl;
-        vals[13 + 5 * a + 1] = fl * xi[0];
-        vals[13 + 5 * a + 2] = fl * xi[1];
-        vals[13 + 5 * a + 3] = fl * xi[2];
-        vals[13 + 5 * a + 4] = fl * e2;
+        ebuf[a][trn[a] * VB + lane] = eout;
+        if (nb[2 * a + 1] < 0) {
+          // outflow face on the domain boundary (a wall): moments of the flux towards the wall
+          const int trw = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
+          const int wid = G.wall_base[2 * a + (sg[a] > 0 ? 1 : 0)] + trw;
+          const T fl = wv * xi[a] * eout;
+          const T m0 = warp_sum(fl), m1 = warp_sum(fl * xi[0]), m2 = warp_sum(fl * xi[1]);
+          const T m3 = warp_sum(fl * xi[2]), m4 = warp_sum(fl * e2);
+          if (lane == 0) {
+            T *W = A.wpart + ((size_t)b * A.nwall + wid) * NFF;
+            W[0] = m0;
+            W[1] = m1;
+            W[2] = m2;
+            W[3] = m3;
+            W[4] = m4;
+          }
+        }
       }
-      T outv = (T)0;
-#pragma unroll
-      for (int k = 0; k < 13 + 5 * NACT; ++k) {
-        const T s = warp_sum(vals[k]);
-        if (lane == k) outv = s;
-      }
-      if (lane < 13 + 5 * NACT) P[(size_t)cell * A.np + lane] = outv;
-      (void)tr;
     }
     __syncthreads();
   }
@@ -390,35 +402,121 @@ cudaError_t launch_wall_constants(const double *vel64, int nslots, const double 
 }
 
 // ---------------------------------------------------------------------------------------------
-// Raw moments (about the state velocity) of the current corrected f, without a kinetic step.
+// Moments of the stored f (Eq. getmoment) streamed after the kinetic step: one thread owns one
+// cell and a chunk of velocity blocks, reads the block's 32 values of its cell as vectors and
+// accumulates, about the state velocity u_n,
+//   13 raw moments of f (1, c, cc, |c|^2 c)  and  5 moments of w (g^n - f) (1, xi, |xi|^2/2).
+// The second set gives, through the discrete identity of the delta-form equation with 1/dt = 0,
+//   sum over the cell's faces of the outward kinetic flux = V sum_v w phi (g^n - f^{n+1/2}) / tau,
+// the only kinetic-flux information the synthetic solve needs.  Sums over one block (32 terms)
+// are plain, and are added into compensated (Kahan) accumulators across blocks.
 template <typename T>
-__global__ void moments_only_kernel(const KinArgs<T> A) {
-  const KinGeom &G = A.g;
-  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
-  const T x = vp[0], y = vp[1], z = vp[2], w = vp[3];
-  const T *F = A.f + (size_t)b * G.nc * VB;
-  T *P = A.part + (size_t)b * G.nc * A.np;
-  for (int cell = warp; cell < G.nc; cell += nw) {
-    T st[16];
-    load_state(A.st + (size_t)cell * NST, st);
-    const T f = corrected(F[(size_t)cell * VB + lane], st, x, y, z);
-    const T cx = x - st[0], cy = y - st[1], cz = z - st[2], c2 = cx * cx + cy * cy + cz * cz, wf = w * f;
-    T vals[13] = {wf, wf * cx, wf * cy, wf * cz, wf * cx * cx, wf * cy * cy, wf * cz * cz,
-                  wf * cx * cy, wf * cx * cz, wf * cy * cz, wf * c2 * cx, wf * c2 * cy, wf * c2 * cz};
-    T outv = (T)0;
+struct MomAcc {
+  T s[NMOM + NFF], c[NMOM + NFF];
+  __device__ void zero() {
 #pragma unroll
-    for (int k = 0; k < 13; ++k) {
-      const T s = warp_sum(vals[k]);
-      if (lane == k) outv = s;
+    for (int k = 0; k < NMOM + NFF; ++k) s[k] = c[k] = (T)0;
+  }
+  __device__ void add(const T *x) {
+#pragma unroll
+    for (int k = 0; k < NMOM + NFF; ++k) {
+      const T y = x[k] - c[k];
+      const T t = s[k] + y;
+      c[k] = (t - s[k]) - y;
+      s[k] = t;
     }
-    if (lane < A.np) P[(size_t)cell * A.np + lane] = lane < 13 ? outv : (T)0;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void load_block_f(const T *p, T *f);
+template <>
+__device__ __forceinline__ void load_block_f<float>(const float *p, float *f) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 v = __ldcs(q + i);
+    f[4 * i] = v.x;
+    f[4 * i + 1] = v.y;
+    f[4 * i + 2] = v.z;
+    f[4 * i + 3] = v.w;
+  }
+}
+template <>
+__device__ __forceinline__ void load_block_f<double>(const double *p, double *f) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const double2 v = __ldcs(q + i);
+    f[2 * i] = v.x;
+    f[2 * i + 1] = v.y;
   }
 }
 
 template <typename T>
-cudaError_t launch_moments_only(const KinArgs<T> &a, int nblocks, cudaStream_t s) {
-  moments_only_kernel<T><<<nblocks, 256, 0, s>>>(a);
+__global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T> A, int blocks_per_chunk, double *mp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *svel = reinterpret_cast<T *>(smem_raw);  // [blocks_per_chunk * VB][4]
+  const KinGeom &G = A.g;
+  const int chunk = blockIdx.y;
+  const int b0 = chunk * blocks_per_chunk;
+  const int nb = min(blocks_per_chunk, A.nblocks - b0);
+  for (int i = threadIdx.x; i < nb * VB * 4; i += blockDim.x) svel[i] = A.vel[(size_t)b0 * VB * 4 + i];
+  __syncthreads();
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= G.nc) return;
+  T st[16];
+  load_state(A.st + (size_t)cell * NST, st);
+  MomAcc<T> acc;
+  acc.zero();
+  for (int bb = 0; bb < nb; ++bb) {
+    T f[VB];
+    load_block_f<T>(A.f + ((size_t)(b0 + bb) * G.nc + cell) * VB, f);
+    T sum[NMOM + NFF];
+#pragma unroll
+    for (int k = 0; k < NMOM + NFF; ++k) sum[k] = (T)0;
+#pragma unroll
+    for (int l = 0; l < VB; ++l) {
+      const T *v = svel + (bb * VB + l) * 4;
+      const T x = v[0], y = v[1], z = v[2], w = v[3];
+      const T cx = x - st[0], cy = y - st[1], cz = z - st[2];
+      const T c2 = cx * cx + cy * cy + cz * cz;
+      const T wf = w * f[l];
+      sum[0] += wf;
+      sum[1] += wf * cx;
+      sum[2] += wf * cy;
+      sum[3] += wf * cz;
+      sum[4] += wf * cx * cx;
+      sum[5] += wf * cy * cy;
+      sum[6] += wf * cz * cz;
+      sum[7] += wf * cx * cy;
+      sum[8] += wf * cx * cz;
+      sum[9] += wf * cy * cz;
+      sum[10] += wf * c2 * cx;
+      sum[11] += wf * c2 * cy;
+      sum[12] += wf * c2 * cz;
+      const T g = st[4] * dexp(-c2 * st[3]) * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
+      const T d = w * g - wf;
+      sum[13] += d;
+      sum[14] += d * x;
+      sum[15] += d * y;
+      sum[16] += d * z;
+      sum[17] += d * (T)0.5 * (x * x + y * y + z * z);
+    }
+    acc.add(sum);
+  }
+  double *out = mp + ((size_t)chunk * G.nc + cell) * (NMOM + NFF);
+#pragma unroll
+  for (int k = 0; k < NMOM + NFF; ++k) out[k] = (double)acc.s[k] - (double)acc.c[k];
+}
+
+template <typename T>
+cudaError_t launch_moments(const KinArgs<T> &a, int blocks_per_chunk, int nchunks, double *mp, cudaStream_t s) {
+  const size_t smem = (size_t)blocks_per_chunk * VB * 4 * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(moments_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.g.nc + 127) / 128, nchunks);
+  moments_kernel<T><<<grid, 128, smem, s>>>(a, blocks_per_chunk, mp);
   return cudaGetLastError();
 }
 
@@ -492,7 +590,7 @@ cudaError_t launch_import_f(const KinArgs<T> &a, const int *slot_canon, int nslo
   template size_t kinetic_smem_bytes<T>(const KinGeom &);                                                       \
   template cudaError_t launch_wall_prepass<T>(const KinArgs<T> &, const int *, const int *, int, const double *, \
                                               double *, int, cudaStream_t);                                     \
-  template cudaError_t launch_moments_only<T>(const KinArgs<T> &, int, cudaStream_t);                           \
+  template cudaError_t launch_moments<T>(const KinArgs<T> &, int, int, double *, cudaStream_t);                \
   template cudaError_t launch_init_maxwellian<T>(const KinArgs<T> &, const double *, int, cudaStream_t);        \
   template cudaError_t launch_export_f<T>(const KinArgs<T> &, const int *, int, int, double *, cudaStream_t);   \
   template cudaError_t launch_import_f<T>(const KinArgs<T> &, const int *, int, int, const double *, cudaStream_t);

@@ -65,27 +65,30 @@ struct Geo {
 };
 
 __device__ __forceinline__ void prim_of(const double *W, int nW, double dr, double *p) {
-  const double rho = W[0];
-  const double ux = W[1] / rho, uy = W[2] / rho, uz = W[3] / rho;
+  const double rho = W[0], ir = 1.0 / rho;
+  const double ux = W[1] * ir, uy = W[2] * ir, uz = W[3] * ir;
   const double Er = nW == 6 ? W[5] : 0.0;
-  const double Tt = (W[4] - 0.5 * rho * (ux * ux + uy * uy + uz * uz) - Er) / (0.75 * rho);
+  const double Tt = (W[4] - 0.5 * rho * (ux * ux + uy * uy + uz * uz) - Er) * (ir * (4.0 / 3.0));
   p[0] = rho;
   p[1] = ux;
   p[2] = uy;
   p[3] = uz;
   p[4] = Tt;
-  p[5] = nW == 6 ? Er / (dr * rho / 4.0) : Tt;
+  p[5] = nW == 6 ? Er * ir * (4.0 / dr) : Tt;
 }
 
 // Euler flux along n = sg e_a: (rho u_n, rho u u_n + p_t n, (rho E + p_t) u_n, rho E_r u_n)
 __device__ __forceinline__ void euler_axis(const double *W, int nW, double dr, int a, double sg, double *F) {
-  double p[6];
-  prim_of(W, nW, dr, p);
-  const double un = sg * p[1 + a], pt = 0.5 * p[0] * p[4];
+  const double ir = 1.0 / W[0];
+  const double un = sg * W[1 + a] * ir;
+  const double Er = nW == 6 ? W[5] : 0.0;
+  // p_t = rho Tt / 2 = (2/3) (rho E - |rho u|^2 / (2 rho) - rho E_r)
+  const double pt = (2.0 / 3.0) * (W[4] - 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) * ir - Er);
   F[0] = W[0] * un;
   for (int b = 0; b < 3; ++b) F[1 + b] = W[1 + b] * un + (b == a ? sg * pt : 0.0);
   F[4] = (W[4] + pt) * un;
-  F[5] = nW == 6 ? W[5] * un : 0.0;
+  F[5] = Er * un;
+  (void)dr;
 }
 
 __device__ __forceinline__ double sound(double Tt) { return sqrt(5.0 * Tt / 6.0); }
@@ -141,7 +144,8 @@ __device__ __forceinline__ double venkat_face(double fi, double fmax, double fmi
 __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   const Geo G{m.g.n[0], m.g.n[1], m.g.n[2], m.g.nc};
   const int nc = G.nc, nW = m.nW;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  // work items are dealt round-robin over the blocks first, so every SM holds cells
+  const int tid = blockIdx.x + gridDim.x * threadIdx.x, nthr = gridDim.x * blockDim.x;
   const int cs[3] = {1, G.n0, G.n0 * G.n1};
   const int act[3] = {m.g.act[0], m.g.act[1], m.g.act[2]};
   __shared__ double sred[kBlock];
@@ -305,14 +309,8 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
       for (int b = 0; b < 3; ++b) F[1 + b] += sn[b];
       F[4] += sn[0] * uf[0] + sn[1] * uf[1] + sn[2] * uf[2] - kt * gT[a] - (nW == 6 ? kr * gTr[a] : 0.0);
       if (nW == 6) F[5] += -kr * gTr[a];
-      double *cr = m.corr + ((size_t)c * 3 + a) * 6;
-      const double *fk = m.ffk + ((size_t)c * 3 + a) * 6;
       double *Ff = m.Ffc + ((size_t)c * 3 + a) * 6;
-      for (int k = 0; k < 6; ++k) {
-        if (k >= nW) { Ff[k] = 0.0; continue; }
-        if (step == 0) cr[k] = (fk[k] - F[k]) * A;
-        Ff[k] = F[k] * A + cr[k];
-      }
+      for (int k = 0; k < 6; ++k) Ff[k] = k < nW ? F[k] * A : 0.0;
     }
     for (int wf = tid; wf < m.nwall; wf += nthr) {
       const int c = m.wall_cell[wf], side = m.wall_side[wf], a = side / 2;
@@ -324,36 +322,39 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
       const double A = V * m.ax[a][nt[a]].invh;
       double feq[6];
       equilibrium_wall_flux(m, m.pr + (size_t)c * 6, a, sg, m.wall_uT + 4 * side, feq);
-      if (step == 0)
-        for (int k = 0; k < 6; ++k) m.feq0[(size_t)wf * 6 + k] = feq[k];
-      for (int k = 0; k < 6; ++k)
-        m.wfl[(size_t)wf * 6 + k] = k < nW ? (m.wfk[(size_t)wf * 6 + k] + feq[k] - m.feq0[(size_t)wf * 6 + k]) * A : 0.0;
+      for (int k = 0; k < 6; ++k) m.wfl[(size_t)wf * 6 + k] = k < nW ? feq[k] * A : 0.0;
     }
     if (!grid_sync(m.bar, m.err)) return;
-    // ---- phase 4: residual
+    // ---- phase 4: residual.  S = sum over the cell's faces of this scheme's outward flux; the
+    // high-order correction (frozen) is corr = K - S(W^{n+1/2}) with K the kinetic step's sum of
+    // outward face fluxes, so R_i(W^{n+1/2}) is the kinetic step's moment residual.
     for (int c = tid; c < nc; c += nthr) {
       int nt[3];
       G.nat(c, nt);
       double V = 1.0;
       for (int b = 0; b < 3; ++b) V *= m.ax[b][nt[b]].h;
-      double R[6] = {0, 0, 0, 0, 0, 0};
+      double S[6] = {0, 0, 0, 0, 0, 0};
       for (int a = 0; a < 3; ++a) {
         if (!act[a]) continue;
         if (nt[a] < m.g.n[a] - 1)
-          for (int k = 0; k < nW; ++k) R[k] -= m.Ffc[((size_t)c * 3 + a) * 6 + k];
+          for (int k = 0; k < nW; ++k) S[k] += m.Ffc[((size_t)c * 3 + a) * 6 + k];
         if (nt[a] > 0)
-          for (int k = 0; k < nW; ++k) R[k] += m.Ffc[((size_t)(c - cs[a]) * 3 + a) * 6 + k];
+          for (int k = 0; k < nW; ++k) S[k] -= m.Ffc[((size_t)(c - cs[a]) * 3 + a) * 6 + k];
         const int trn = a == 0 ? nt[1] + G.n1 * nt[2] : (a == 1 ? nt[0] + G.n0 * nt[2] : nt[0] + G.n0 * nt[1]);
         if (nt[a] == 0 && m.g.wall_base[2 * a] >= 0) {
           const int wid = m.g.wall_base[2 * a] + trn;
-          for (int k = 0; k < nW; ++k) R[k] -= m.wfl[(size_t)wid * 6 + k];
+          for (int k = 0; k < nW; ++k) S[k] += m.wfl[(size_t)wid * 6 + k];
         }
         if (nt[a] == m.g.n[a] - 1 && m.g.wall_base[2 * a + 1] >= 0) {
           const int wid = m.g.wall_base[2 * a + 1] + trn;
-          for (int k = 0; k < nW; ++k) R[k] -= m.wfl[(size_t)wid * 6 + k];
+          for (int k = 0; k < nW; ++k) S[k] += m.wfl[(size_t)wid * 6 + k];
         }
       }
-      for (int k = 0; k < nW; ++k) R[k] /= V;
+      double *cr = m.corr + (size_t)c * 6;
+      if (step == 0)
+        for (int k = 0; k < nW; ++k) cr[k] = m.K[(size_t)c * 6 + k] - S[k];
+      double R[6] = {0, 0, 0, 0, 0, 0};
+      for (int k = 0; k < nW; ++k) R[k] = -(S[k] + cr[k]) / V;
       if (nW == 6) {
         const double *p = m.pr + (size_t)c * 6;
         const double tau = 2.0 * m.Kn / sqrt(kPi) * pow(p[4], m.omega - 1.0) / p[0];
@@ -416,31 +417,42 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
         den[k] += w * w * V;
       }
     }
-    for (int k = 0; k < 12; ++k) {
-      sred[threadIdx.x] = k < 6 ? num[k] : den[k - 6];
-      __syncthreads();
-      for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sred[threadIdx.x] += sred[threadIdx.x + o];
-        __syncthreads();
+    {
+      __shared__ double wsum[kBlock / 32][12];
+      const int nwarps = blockDim.x >> 5;
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      for (int k = 0; k < 12; ++k) {
+        double v = k < 6 ? num[k] : den[k - 6];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) wsum[wid][k] = v;
       }
-      if (threadIdx.x == 0) m.red[(size_t)blockIdx.x * 16 + k] = sred[0];
       __syncthreads();
+      if (threadIdx.x < 12) {
+        double v = 0.0;
+        for (int w = 0; w < nwarps; ++w) v += wsum[w][threadIdx.x];
+        m.red[(size_t)blockIdx.x * 16 + threadIdx.x] = v;
+      }
     }
     if (!grid_sync(m.bar, m.err)) return;
     used = step + 1;
-    double tot[12];
-    for (int k = 0; k < 12; ++k) tot[k] = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b)
-      for (int k = 0; k < 12; ++k) tot[k] += ((volatile double *)m.red)[(size_t)b * 16 + k];
-    double delta = 0.0;
-    for (int k = 0; k < nW; ++k)
-      if (tot[6 + k] > 0.0) {
-        const double e = sqrt(tot[k] / tot[6 + k]);
-        delta = e > delta ? e : delta;
-      }
+    // the same fixed-order sum in every block (thread 0), broadcast through shared memory
+    __shared__ double sdelta;
+    if (threadIdx.x == 0) {
+      double tot[12];
+      for (int k = 0; k < 12; ++k) tot[k] = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b)
+        for (int k = 0; k < 12; ++k) tot[k] += ((volatile double *)m.red)[(size_t)b * 16 + k];
+      double delta = 0.0;
+      for (int k = 0; k < nW; ++k)
+        if (tot[6 + k] > 0.0) {
+          const double e = sqrt(tot[k] / tot[6 + k]);
+          delta = e > delta ? e : delta;
+        }
+      sdelta = delta;
+    }
     // every block has read the partials before any block overwrites them in the next step
     if (!grid_sync(m.bar, m.err)) return;
-    if (delta < m.tol) break;
+    if (sdelta < m.tol) break;
   }
   // closed domain: rescale the density to the domain's total mass (velocity, temperatures kept)
   double mloc = 0.0;
@@ -451,38 +463,62 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     for (int b = 0; b < 3; ++b) V *= m.ax[b][nt[b]].h;
     mloc += m.W[(size_t)c * 6] * V;
   }
-  sred[threadIdx.x] = mloc;
+  for (int o = 16; o > 0; o >>= 1) mloc += __shfl_xor_sync(0xffffffffu, mloc, o);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = mloc;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sred[threadIdx.x] += sred[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sred[w];
+    m.red[(size_t)blockIdx.x * 16] = v;
   }
-  if (threadIdx.x == 0) m.red[(size_t)blockIdx.x * 16] = sred[0];
   if (!grid_sync(m.bar, m.err)) return;
-  double mm = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) mm += ((volatile double *)m.red)[(size_t)b * 16];
-  const double fac = m.closed ? m.mass_ref / mm : 1.0;
+  __shared__ double sfac;
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) mm += ((volatile double *)m.red)[(size_t)b * 16];
+    sfac = m.closed ? m.mass_ref / mm : 1.0;
+  }
+  __syncthreads();
+  const double fac = sfac;
   for (int c = tid; c < nc; c += nthr) {
     double p[6];
     prim_of(m.W + (size_t)c * 6, nW, m.d_r, p);
     p[0] *= fac;
     for (int k = 0; k < 6; ++k) m.Wout[(size_t)c * 6 + k] = p[k];
   }
-  if (tid == 0) *m.iters = used;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *m.iters = used;
 }
 
 int macro_block_size() { return kBlock; }
 
-cudaError_t macro_max_grid(int *grid) {
+// One block per SM (two when the cells do not fit in 256 threads per SM), block size the
+// smallest multiple of 32 that covers the cells: FP64 on GB300 runs at 1/58 of FP32, so the
+// solve is bound by FP64 issue and latency and every SM must hold cells.
+cudaError_t macro_launch_shape(int nc, int *grid, int *block) {
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, macro_kernel, kBlock, 0);
+  int b = 32 * ((nc + 32 * nsm - 1) / (32 * nsm));
+  if (b < 32) b = 32;
+  if (b > kBlock) b = kBlock;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, macro_kernel, b, 0);
   if (e != cudaSuccess) return e;
-  *grid = nsm * (per < 2 ? per : 2);
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  int g = nsm * (per < 2 ? per : 2);
+  if (b < kBlock) g = nsm;
+  const int need = (nc + b - 1) / b;
+  if (g > need && need >= 1) g = need < nsm ? nsm : need;
+  if (g > nc) g = nc > 0 ? nc : 1;
+  *grid = g;
+  *block = b;
   return cudaSuccess;
+}
+
+cudaError_t macro_max_grid(int *grid) {
+  int b = 0;
+  return macro_launch_shape(1 << 30, grid, &b);
 }
 
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s) {

@@ -13,91 +13,70 @@ namespace gsis {
 
 namespace {
 constexpr double kPi = 3.14159265358979323846;
-
-// Compensated (Kahan) accumulator in the kinetic precision; FP64 partials add plainly.
-template <typename T>
-struct Acc {
-  T s = 0, c = 0;
-  __device__ void add(T x) {
-    const T y = x - c;
-    const T t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ double get() const { return (double)s - (double)c; }
-};
-template <>
-struct Acc<double> {
-  double s = 0;
-  __device__ void add(double x) { s += x; }
-  __device__ double get() const { return s; }
-};
-
-__device__ __forceinline__ int trans_index(const KinGeom &g, int a, const int *nat) {
-  return a == 0 ? nat[1] + g.n[1] * nat[2] : (a == 1 ? nat[0] + g.n[0] * nat[2] : nat[0] + g.n[0] * nat[1]);
-}
 }  // namespace
 
-// partials [block][cell][np] -> mom [cell][13] (raw, about the state velocity),
-// ff [cell][3][6] flux through the + face along +e_a (interior faces, per unit area),
-// wf [wall][6] outward kinetic wall flux per unit area (outgoing half from the partials,
-// re-emitted half rho_w Zw).
-template <typename T>
-__global__ void reduce_kernel(const T *part, int np, const int8_t *boct, int nblocks, KinGeom g, const double *rho_w,
-                              const double *Zw, double *mom, double *ff, double *wf) {
-  const size_t n = (size_t)g.nc * np;
+// Chunk partials [chunk][cell][18] -> mom [cell][13] (raw, about the state velocity) and
+//   K [cell][k] = V sum_v w phi_k (g^n - f^{n+1/2}) / tau = sum over the cell's faces of the
+//   outward kinetic face flux (mass, momentum, energy; k = 5 internal energy: 0 here).
+__global__ void reduce_moments_kernel(const double *mp, int nchunks, int nc, const double *vol, const double *st64,
+                                      double *mom, double *K) {
+  const size_t n = (size_t)nc * (NMOM + NFF);
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const int cell = (int)(idx / np), k = (int)(idx % np);
+    const int cell = (int)(idx / (NMOM + NFF)), k = (int)(idx % (NMOM + NFF));
+    double acc = 0.0;
+    for (int ch = 0; ch < nchunks; ++ch) acc += mp[((size_t)ch * nc + cell) * (NMOM + NFF) + k];
     if (k < NMOM) {
-      Acc<T> acc;
-      for (int b = 0; b < nblocks; ++b) acc.add(part[((size_t)b * g.nc + cell) * np + k]);
-      mom[(size_t)cell * NMOM + k] = acc.get();
-      continue;
-    }
-    const int a = (k - NMOM) / NFF, m = (k - NMOM) % NFF;
-    const int nat[3] = {cell % g.n[0], (cell / g.n[0]) % g.n[1], cell / (g.n[0] * g.n[1])};
-    const int stride = a == 0 ? 1 : (a == 1 ? g.n[0] : g.n[0] * g.n[1]);
-    const bool last = nat[a] == g.n[a] - 1;
-    Acc<T> plus, minus, nxt;
-    for (int b = 0; b < nblocks; ++b) {
-      const bool neg = (boct[b] >> a) & 1;
-      const T v = part[((size_t)b * g.nc + cell) * np + k];
-      if (neg) minus.add(v);
-      else plus.add(v);
-      if (neg && !last) nxt.add(part[((size_t)b * g.nc + cell + stride) * np + k]);
-    }
-    ff[((size_t)cell * 3 + a) * 6 + m] = last ? 0.0 : plus.get() + nxt.get();
-    const int trn = trans_index(g, a, nat);
-    if (nat[a] == 0 && g.wall_base[2 * a] >= 0) {
-      const int wid = g.wall_base[2 * a] + trn;
-      wf[(size_t)wid * 6 + m] = -(minus.get() + rho_w[wid] * Zw[6 * (2 * a) + m]);
-    }
-    if (last && g.wall_base[2 * a + 1] >= 0) {
-      const int wid = g.wall_base[2 * a + 1] + trn;
-      wf[(size_t)wid * 6 + m] = plus.get() + rho_w[wid] * Zw[6 * (2 * a + 1) + m];
+      mom[(size_t)cell * NMOM + k] = acc;
+    } else {
+      K[(size_t)cell * 6 + (k - NMOM)] = vol[cell] * acc * st64[(size_t)cell * NST + 11];
+      if (k == NMOM) K[(size_t)cell * 6 + 5] = 0.0;
     }
   }
 }
 
+// Outward kinetic wall flux per unit area: the half moving towards the wall from the wall cells'
+// block partials (blocks whose octant moves towards this wall), the re-emitted half rho_w Zw.
 template <typename T>
-cudaError_t launch_reduce(const T *part, int np, const int8_t *boct, int nblocks, const KinGeom &g,
-                          const int *wall_cell, const int *wall_side, int nwall, const double *rho_w,
-                          const double *Zw, double *mom, double *ff, double *wf, cudaStream_t s) {
+__global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nblocks, int nwall, const int *wall_side,
+                                   const double *rho_w, const double *Zw, double *wf) {
+  const int n = nwall * NFF;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int w = idx / NFF, m = idx % NFF;
+    const int side = wall_side[w], a = side / 2;
+    const bool plus = side & 1;
+    double out = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+      const bool neg = (boct[b] >> a) & 1;
+      if (neg == plus) continue;  // this block's velocities move away from the wall
+      out += (double)wpart[((size_t)b * nwall + w) * NFF + m];
+    }
+    const double tot = out + rho_w[w] * Zw[6 * side + m];
+    wf[(size_t)w * 6 + m] = plus ? tot : -tot;
+    if (m == 0) wf[(size_t)w * 6 + 5] = 0.0;
+  }
+}
+
+template <typename T>
+cudaError_t launch_reduce(const double *mp, int nchunks, const T *wpart, const int8_t *boct, int nblocks,
+                          const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
+                          const double *rho_w, const double *Zw, const double *vol, const double *st64,
+                          double *mom, double *K, double *wf, cudaStream_t s) {
   (void)wall_cell;
-  (void)wall_side;
-  (void)nwall;
-  const size_t n = (size_t)g.nc * np;
+  const size_t n = (size_t)g.nc * (NMOM + NFF);
   int grid = (int)((n + 255) / 256);
-  if (grid > 152 * 32) grid = 152 * 32;
-  reduce_kernel<T><<<grid, 256, 0, s>>>(part, np, boct, nblocks, g, rho_w, Zw, mom, ff, wf);
+  if (grid > 152 * 16) grid = 152 * 16;
+  reduce_moments_kernel<<<grid, 256, 0, s>>>(mp, nchunks, g.nc, vol, st64, mom, K);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || nwall == 0 || wpart == nullptr) return e;
+  reduce_wall_kernel<T><<<(nwall * NFF + 255) / 256, 256, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw, wf);
   return cudaGetLastError();
 }
-template cudaError_t launch_reduce<float>(const float *, int, const int8_t *, int, const KinGeom &, const int *,
-                                          const int *, int, const double *, const double *, double *, double *,
-                                          double *, cudaStream_t);
-template cudaError_t launch_reduce<double>(const double *, int, const int8_t *, int, const KinGeom &, const int *,
-                                           const int *, int, const double *, const double *, double *, double *,
-                                           double *, cudaStream_t);
+template cudaError_t launch_reduce<float>(const double *, int, const float *, const int8_t *, int, const KinGeom &,
+                                          const int *, const int *, int, const double *, const double *,
+                                          const double *, const double *, double *, double *, double *, cudaStream_t);
+template cudaError_t launch_reduce<double>(const double *, int, const double *, const int8_t *, int, const KinGeom &,
+                                           const int *, const int *, int, const double *, const double *,
+                                           const double *, const double *, double *, double *, double *, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------
 // Raw moments about the state velocity un -> rho, u, Tt, sigma, q about the mean velocity.

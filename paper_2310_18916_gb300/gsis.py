@@ -50,7 +50,7 @@ class Options(C.Structure):
 
 _lib = None
 SYMBOLS = ("gsis_default_options", "gsis_footprint_bytes", "gsis_create", "gsis_iterate", "gsis_moments",
-           "gsis_residual", "gsis_nwall", "gsis_wall", "gsis_face_flux", "gsis_get_f", "gsis_set_f", "gsis_stats",
+           "gsis_residual", "gsis_nwall", "gsis_wall", "gsis_kinetic_flux_sum", "gsis_get_f", "gsis_set_f", "gsis_stats",
            "gsis_destroy", "gsis_last_error", "gsis_profile")
 
 
@@ -73,7 +73,7 @@ def load(path: str = LIB_PATH):
     L.gsis_residual.argtypes = [P, D, C.c_int]
     L.gsis_nwall.argtypes = [P]
     L.gsis_wall.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), D, D]
-    L.gsis_face_flux.argtypes = [P, D, C.c_size_t]
+    L.gsis_kinetic_flux_sum.argtypes = [P, D, C.c_size_t]
     L.gsis_get_f.argtypes = [P, D, D]
     L.gsis_set_f.argtypes = [P, D, D]
     L.gsis_stats.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -232,9 +232,9 @@ class Solver:
                                      side.ctypes.data_as(C.POINTER(C.c_int)), _p(rw), _p(fl)))
         return cell, side, rw, fl
 
-    def face_flux(self):
-        out = np.empty((self.nc, 6, 6))
-        self._check(load().gsis_face_flux(self.h, _p(out), out.size))
+    def kinetic_flux_sum(self):
+        out = np.empty((self.nc, 6))
+        self._check(load().gsis_kinetic_flux_sum(self.h, _p(out), out.size))
         return out
 
     def get_f(self):

@@ -19,11 +19,14 @@ def pair(p, precision="f64", mode="gsis", W0=None, **opts):
     return g, o
 
 
-def scaled_close(a, b, rel, what):
-    """Column-wise |a - b| <= rel * max(|b| over cells, floor) with a floor for near-zero fields."""
+def scaled_close(a, b, rel, what, vector=False):
+    """Column-wise |a - b| <= rel * max(|b| over cells, floor) with a floor for near-zero fields;
+    vector=True scales every column by the largest column (components of one vector)."""
     a = np.asarray(a)
     b = np.asarray(b)
     scale = np.maximum(np.abs(b).max(axis=0), 1e-3 * np.abs(b).max())
+    if vector:
+        scale = np.full_like(scale, np.abs(b).max())
     err = (np.abs(a - b) / scale).max(axis=0)
     assert (err <= rel).all(), f"{what}: worst column error {err.max():.3e} (limit {rel:.1e}) per column {err}"
     return err.max()
