@@ -175,6 +175,27 @@ int gsis_profile(gsis_handle h, int enable, int reset, double *ms, int n, int *s
 /* Counters: outer iterations run so far, inner synthetic steps of the last outer step. */
 int gsis_stats(gsis_handle h, int *outer_total, int *macro_iters_last);
 
+/* Allocation-free velocity moments of a VDF held by the caller (no counterpart in the paper).
+ * For callers that cannot allocate device memory where they need moments: code running inside
+ * another framework's memory pool without an allocator handle to pass down, or a
+ * latency-critical region where an allocation (and the synchronisation it can imply) is not
+ * allowed.  It allocates nothing: its only scratch is a fixed 8 MiB array of static device
+ * memory (every GPU that loads this library holds it until the process exits).
+ *   f_dev:   device, FP32, [cell][v], v = ix + nx (iy + ny iz) (the layout of gsis_get_f)
+ *   vel_dev: device, FP32, [v][4] = xi_x, xi_y, xi_z, quadrature weight
+ *   out_dev: device, FP64, [cell][18] = the GSIS_F_HALF fields of gsis_moments: rho, u(3),
+ *            Tt, Tr (= Tt), sigma(xx,yy,zz,xy,xz,yz), qt(3), qr(3) (= 0)  (Eq. getmoment)
+ *   stream:  cudaStream_t (NULL = default stream); the call only enqueues work on it.
+ * Limits: ncells <= 8 MiB / (13 x 8 B) = 80659, else GSIS_E_INVALID (nothing is launched).
+ * The first call on a device, with that device current, looks up the scratch's device address
+ * (cudaGetSymbolAddress); make that first call before capturing a stream into a graph.
+ * Calls share the scratch: two calls whose work overlaps on the GPU (different streams,
+ * concurrent host threads) race and must be ordered by the caller.  Each call overwrites all
+ * scratch it reads, so no state carries from one call to the next.
+ * Returns GSIS_OK, GSIS_E_INVALID or GSIS_E_CUDA. */
+int gsis_vdf_moments_noalloc(const float *f_dev, const float *vel_dev, int ncells, int nvel, double *out_dev,
+                             void *stream);
+
 /* Release everything held by h.  NULL-safe. */
 int gsis_destroy(gsis_handle h);
 

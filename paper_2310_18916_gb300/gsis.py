@@ -51,7 +51,7 @@ class Options(C.Structure):
 _lib = None
 SYMBOLS = ("gsis_default_options", "gsis_footprint_bytes", "gsis_create", "gsis_iterate", "gsis_moments",
            "gsis_residual", "gsis_nwall", "gsis_wall", "gsis_kinetic_flux_sum", "gsis_get_f", "gsis_set_f", "gsis_stats",
-           "gsis_destroy", "gsis_last_error", "gsis_profile")
+           "gsis_destroy", "gsis_last_error", "gsis_profile", "gsis_vdf_moments_noalloc")
 
 
 def load(path: str = LIB_PATH):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.gsis_set_f.argtypes = [P, D, D]
     L.gsis_stats.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.gsis_profile.argtypes = [P, C.c_int, C.c_int, D, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.gsis_vdf_moments_noalloc.argtypes = [P, P, C.c_int, C.c_int, P, P]
     L.gsis_destroy.argtypes = [P]
     L.gsis_last_error.argtypes = [P]
     L.gsis_last_error.restype = C.c_char_p
