@@ -74,8 +74,11 @@ struct gsis_solver {
   int4 *d_natcell = nullptr;
   unsigned *d_ticket = nullptr, *d_bar = nullptr;
   // macro work
-  double *m_W = nullptr, *m_pr = nullptr, *m_gW = nullptr, *m_phW = nullptr, *m_gP = nullptr, *m_mu = nullptr;
-  double *m_R = nullptr, *m_D = nullptr, *m_dW = nullptr, *m_Fc = nullptr, *m_corr = nullptr, *m_gam = nullptr;
+  double *m_W = nullptr, *m_pr = nullptr, *m_gW = nullptr, *m_phW = nullptr, *m_gP = nullptr, *m_aux = nullptr;
+  double *m_R = nullptr, *m_invD = nullptr, *m_dW = nullptr, *m_Fc = nullptr, *m_corr = nullptr, *m_gam = nullptr;
+  int *d_colcells = nullptr;
+  int ncol0 = 0;
+  std::vector<int> colcells;
   double *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr;
   int macro_grid = 0, macro_block = 256;
   int kin_warps = 1;
@@ -281,7 +284,9 @@ struct gsis_solver {
       m.wall_side = d_wall_side;
       m.nwall = nwall;
       m.wall_uT = d_wall_uT;
-      m.W = m_W; m.pr = m_pr; m.gW = m_gW; m.phW = m_phW; m.gP = m_gP; m.mu = m_mu; m.R = m_R; m.D = m_D;
+      m.colcells = d_colcells;
+      m.ncol0 = ncol0;
+      m.W = m_W; m.pr = m_pr; m.gW = m_gW; m.phW = m_phW; m.gP = m_gP; m.aux = m_aux; m.R = m_R; m.invD = m_invD;
       m.dW = m_dW; m.Fc = m_Fc; m.corr = m_corr; m.gam = m_gam; m.red = m_red; m.Ffc = m_Ffc;
       m.wfl = m_wfl;
       m.Wout = d_Wnew;
@@ -453,7 +458,7 @@ template <typename T>
 std::vector<AxisCell<T>> cast_axis(const std::vector<AxisCell<double>> &in) {
   std::vector<AxisCell<T>> out(in.size());
   for (size_t i = 0; i < in.size(); ++i)
-    out[i] = {(T)in[i].invh, (T)in[i].rlo, (T)in[i].rhi, (T)in[i].clo, (T)in[i].chi, (T)in[i].h, (T)0, (T)0};
+    out[i] = {(T)in[i].invh, (T)in[i].rlo, (T)in[i].rhi, (T)in[i].clo, (T)in[i].chi, (T)in[i].h, (T)in[i].pad0, (T)0};
   return out;
 }
 
@@ -489,6 +494,8 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
       const double den = dlo * dlo + dhi * dhi;
       c.clo = den > 0 ? dlo / den : 0.0;
       c.chi = den > 0 ? dhi / den : 0.0;
+      c.pad0 = i < na - 1 ? 1.0 / (xc[i + 1] - xc[i]) : 0.0;
+      c.pad1 = 0.0;
       s->axc[a][i] = c;
     }
   }
@@ -585,6 +592,15 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
     }
     s->nwall += ntr;
   }
+  // red/black cell lists of the synthetic solve's sweeps
+  s->colcells.clear();
+  for (int col = 0; col < 2; ++col) {
+    for (int c = 0; c < s->nc; ++c) {
+      const int i = c % s->n[0], j = (c / s->n[0]) % s->n[1], k = c / (s->n[0] * s->n[1]);
+      if (((i + j + k) & 1) == col) s->colcells.push_back(c);
+    }
+    if (col == 0) s->ncol0 = (int)s->colcells.size();
+  }
   // velocities
   s->nv_axis[0] = vg->n[0];
   s->nv_axis[1] = vg->n[1];
@@ -667,9 +683,10 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->m_gW, nc * 18 * sizeof(double));
   A(s->m_phW, nc * 6 * sizeof(double));
   A(s->m_gP, nc * 15 * sizeof(double));
-  A(s->m_mu, nc * sizeof(double));
+  A(s->m_aux, nc * 8 * sizeof(double));
+  A(s->d_colcells, nc * sizeof(int));
   A(s->m_R, nc * 6 * sizeof(double));
-  A(s->m_D, nc * 6 * sizeof(double));
+  A(s->m_invD, nc * 6 * sizeof(double));
   A(s->m_dW, nc * 6 * sizeof(double));
   A(s->m_Fc, nc * 18 * sizeof(double));
   A(s->m_corr, nc * 6 * sizeof(double));
@@ -680,7 +697,7 @@ static int allocate_and_upload(gsis_solver *s) {
   if (rc) return rc;
   rc = s->cuda(macro_launch_shape((int)nc, &s->macro_grid, &s->macro_block), "occupancy");
   if (rc) return rc;
-  rc = s->alloc(&s->m_red, (size_t)s->macro_grid * 16 * sizeof(double));
+  rc = s->alloc(&s->m_red, (size_t)3 * s->macro_grid * 16 * sizeof(double));
   if (rc) return rc;
   std::vector<T> velT(s->vel64.begin(), s->vel64.end());
   rc = s->upload(s->d_vel, velT.data(), velT.size() * sizeof(T));
@@ -702,6 +719,7 @@ static int allocate_and_upload(gsis_solver *s) {
     rc = s->upload(s->d_wall_sides, s->wall_sides_list.data(), s->wall_sides_list.size() * sizeof(int));
   if (!rc) rc = s->upload(s->d_wall_uT, &s->wall_uT[0][0], 24 * sizeof(double));
   if (!rc) rc = s->upload(s->d_vol, s->vol.data(), nc * sizeof(double));
+  if (!rc) rc = s->upload(s->d_colcells, s->colcells.data(), nc * sizeof(int));
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_ticket, 0, 4 * sizeof(unsigned), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(unsigned), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream), "memset");

@@ -18,6 +18,7 @@ constexpr int GSIS_ERR_TIMEOUT = -5;
 // Per-axis geometry of one cell of a rectilinear block (natural orientation).
 //   gradient along the axis: g = clo (q[i-1] - q[i]) + chi (q[i+1] - q[i])  (missing neighbour: 0)
 //   face offsets from the cell centre: rlo = X[i] - xc[i] < 0, rhi = X[i+1] - xc[i] > 0
+//   pad0 = 1 / (xc[i+1] - xc[i]) (0 for the last cell), pad1 unused
 template <typename T>
 struct alignas(8 * sizeof(T)) AxisCell {
   T invh, rlo, rhi, clo, chi, h, pad0, pad1;
@@ -171,7 +172,9 @@ struct MacroArgs {
   int nwall;
   const double *wall_uT;   // [6][4]
   // work (device, sized by the host)
-  double *W, *pr, *gW, *phW, *gP, *mu, *R, *D, *dW, *Fc, *corr, *gam, *red, *Ffc, *wfl;
+  const int *colcells;     // red cells (i+j+k even) then black cells
+  int ncol0;               // number of red cells
+  double *W, *pr, *aux, *gW, *phW, *gP, *R, *invD, *dW, *Fc, *corr, *gam, *red, *Ffc, *wfl;
   double *Wout;            // [cell][6] prim W^{n+1}
   unsigned *bar;           // [2] barrier counter, generation
   int *err;

@@ -520,19 +520,23 @@ cudaError_t launch_moments(const KinArgs<T> &a, int blocks_per_chunk, int nchunk
   return cudaGetLastError();
 }
 
-// f_raw = Maxwellian(W0) of each cell at each slot velocity (computed in FP64).
+// f_raw = Maxwellian(W0) of each cell at each slot velocity, in the storage precision (the
+// per-cell factor rho (pi T)^(-3/2) and 1/T in FP64, the exponential in T).
+__device__ __forceinline__ float accurate_exp(float x) { return expf(x); }
+__device__ __forceinline__ double accurate_exp(double x) { return exp(x); }
+
 template <typename T>
 __global__ void init_maxwellian_kernel(const KinArgs<T> A, const double *W0) {
   const KinGeom &G = A.g;
   const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
-  const double x = vp[0], y = vp[1], z = vp[2];
+  const T x = vp[0], y = vp[1], z = vp[2];
   T *F = A.f + (size_t)b * G.nc * VB;
   for (int cell = warp; cell < G.nc; cell += nw) {
     const double *w0 = W0 + 6 * (size_t)cell;
-    const double cx = x - w0[1], cy = y - w0[2], cz = z - w0[3];
-    F[(size_t)cell * VB + lane] =
-        (T)(w0[0] * pow(3.14159265358979323846 * w0[4], -1.5) * exp(-(cx * cx + cy * cy + cz * cz) / w0[4]));
+    const T C = (T)(w0[0] * pow(3.14159265358979323846 * w0[4], -1.5)), invT = (T)(1.0 / w0[4]);
+    const T cx = x - (T)w0[1], cy = y - (T)w0[2], cz = z - (T)w0[3];
+    F[(size_t)cell * VB + lane] = C * accurate_exp(-(cx * cx + cy * cy + cz * cz) * invT);
   }
 }
 
