@@ -622,7 +622,7 @@ static size_t footprint(const gsis_solver *s) {
   b += (size_t)64 * nc * (NMOM + NFF) * 8 / 64 + nc * (NMOM + NFF) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
-  b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 18 + 18 + 3 + 18) * 8;  // synthetic-solve work
+  b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 36 + 18 + 3 + 18 + 8) * 8;  // synthetic-solve work
   b += (size_t)s->nslots * 4 * (T + 8) + (size_t)s->nwall * 32 * 8 + 3 * nc * 4 + (1 << 20);
   return b;
 }
@@ -688,7 +688,7 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->m_R, nc * 6 * sizeof(double));
   A(s->m_invD, nc * 6 * sizeof(double));
   A(s->m_dW, nc * 6 * sizeof(double));
-  A(s->m_Fc, nc * 18 * sizeof(double));
+  A(s->m_Fc, nc * 36 * sizeof(double));  // two buffers: start and end of an inner step
   A(s->m_corr, nc * 6 * sizeof(double));
   A(s->m_gam, nc * 3 * sizeof(double));
   A(s->m_Ffc, nc * 18 * sizeof(double));

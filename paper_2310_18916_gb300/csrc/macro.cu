@@ -3,14 +3,17 @@
 // One persistent cooperative kernel runs all inner steps (Algorithm 2 body).  FP64 on GB300 is
 // 1/58 of the FP32 rate and the problem has O(10^4) cells, so the solve is bound by FP64
 // latency: every phase is split into many short work items (per cell and field, per face, per
-// cell and neighbour) dealt out warp by warp over all SMs, and per-cell quantities every phase
-// needs are computed once per inner step.
-//   A (with the update)  primitives, mu, nu = mu/rho, sound speed, |u_a| + c_s, axis Euler fluxes
+// cell and face) dealt out warp by warp over all SMs, and per-cell quantities every phase
+// needs are computed once per inner step.  Per inner step:
 //   B  per (cell, field): LSQ gradients, Venkatakrishnan limiters; per cell: time step, diagonal
 //   C  per face: Rusanov convective + NSF viscous flux; wall faces: equilibrium wall flux
-//   D  per cell: residual R_i (Eq. delta_Macroscopic_equations)
-//   E  red / black point-implicit sweeps (Eq. res_macro), one lane per (cell, neighbour)
-//   F  update, inner residual, then A for the next step
+//   E  red / black point-implicit sweeps (Eq. res_macro), one lane per (cell, face).  The first
+//      pass of each colour also sums the cell's face fluxes into the residual R_i
+//      (Eq. delta_Macroscopic_equations); the last one applies the update W += dW, adds to the
+//      inner residual and recomputes the cell's primitives, mu, nu, sound speed, |u_a| + c_s and
+//      axis Euler fluxes (into the second of two flux buffers: the other colour still reads the
+//      fluxes at the start of the step)
+// so ten grid barriers per inner step with the default four sweeps.
 // The high-order terms of Eq. full_constitutive enter through a per-cell frozen correction
 // corr = K - S(W^{n+1/2}), K the kinetic step's sum of outward face fluxes and S this scheme's,
 // so the residual at W^{n+1/2} is the kinetic step's moment residual.  Wall faces use the
@@ -18,6 +21,8 @@
 // boundary-flux modification of Section 3.2; its value at W^{n+1/2} cancels in corr).
 // Phases are separated by a grid barrier whose spin is bounded: on time-out it raises an error
 // flag and every block returns.
+// Per-cell arrays are indexed only by compile-time constants (the field count NW is a template
+// parameter, per-axis values are selected, not indexed), so they stay in registers.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -71,33 +76,41 @@ struct Items {
   }
 };
 
+template <typename T>
+__device__ __forceinline__ T pick3(int a, T x, T y, T z) { return a == 0 ? x : (a == 1 ? y : z); }
+
 __device__ __forceinline__ void nat_of(const KinGeom &g, int c, int *v) {
   v[0] = c % g.n[0];
   v[1] = (c / g.n[0]) % g.n[1];
   v[2] = c / (g.n[0] * g.n[1]);
 }
 
-__device__ __forceinline__ void prim_of(const double *W, int nW, double dr, double *p) {
+template <int NW>
+__device__ __forceinline__ void prim_of(const double *W, double dr, double *p) {
   const double rho = W[0], ir = 1.0 / rho;
   const double ux = W[1] * ir, uy = W[2] * ir, uz = W[3] * ir;
-  const double Er = nW == 6 ? W[5] : 0.0;
+  const double Er = NW == 6 ? W[5] : 0.0;
   const double Tt = (W[4] - 0.5 * rho * (ux * ux + uy * uy + uz * uz) - Er) * (ir * (4.0 / 3.0));
   p[0] = rho;
   p[1] = ux;
   p[2] = uy;
   p[3] = uz;
   p[4] = Tt;
-  p[5] = nW == 6 ? Er * ir * (4.0 / dr) : Tt;
+  p[5] = NW == 6 ? Er * ir * (4.0 / dr) : Tt;
 }
 
+__device__ __forceinline__ bool physical(const double *p) { return p[0] > 0.0 && p[4] > 0.0 && p[5] > 0.0; }
+
 // Euler flux along n = sg e_a: (rho u_n, rho u u_n + p_t n, (rho E + p_t) u_n, rho E_r u_n)
-__device__ __forceinline__ void euler_axis(const double *W, int nW, int a, double sg, double *F) {
+template <int NW>
+__device__ __forceinline__ void euler_axis(const double *W, int a, double sg, double *F) {
   const double ir = 1.0 / W[0];
-  const double un = sg * W[1 + a] * ir;
-  const double Er = nW == 6 ? W[5] : 0.0;
+  const double un = sg * pick3(a, W[1], W[2], W[3]) * ir;
+  const double Er = NW == 6 ? W[5] : 0.0;
   // p_t = rho Tt / 2 = (2/3) (rho E - |rho u|^2 / (2 rho) - rho E_r)
   const double pt = (2.0 / 3.0) * (W[4] - 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) * ir - Er);
   F[0] = W[0] * un;
+#pragma unroll
   for (int b = 0; b < 3; ++b) F[1 + b] = W[1 + b] * un + (b == a ? sg * pt : 0.0);
   F[4] = (W[4] + pt) * un;
   F[5] = Er * un;
@@ -119,9 +132,10 @@ __device__ __forceinline__ void kappas(const MacroArgs &m, double mu, double *kt
 // Outward wall flux per unit area of local equilibrium at the cell state p meeting the diffuse
 // wall (u_w, T_w): half-range moments J_k of N(u_n, T/2) for the half moving into the wall,
 // re-emission rho_w M(u_w, T_w) with zero net mass flux.  n = sg e_a.
+template <int NW>
 __device__ void equilibrium_wall_flux(const MacroArgs &m, const double *p, int a, double sg, const double *uT,
                                       double *F) {
-  const double rho = p[0], T = p[4], un = sg * p[1 + a], Tw = uT[3];
+  const double rho = p[0], T = p[4], un = sg * pick3(a, p[1], p[2], p[3]), Tw = uT[3];
   const double sr = un / sqrt(T);
   const double phi0 = exp(-sr * sr) / sqrt(kPi * T);
   const double J0 = 0.5 * erfc(-sr);
@@ -131,6 +145,7 @@ __device__ void equilibrium_wall_flux(const MacroArgs &m, const double *p, int a
   const double K1 = -sqrt(Tw) / (2.0 * sqrt(kPi)), K2 = Tw / 4.0, K3 = Tw * K1;
   const double rw = -rho * J1 / K1;
   double ut[3], uwt[3];
+#pragma unroll
   for (int b = 0; b < 3; ++b) {
     ut[b] = b == a ? 0.0 : p[1 + b];
     uwt[b] = b == a ? 0.0 : uT[b];
@@ -138,9 +153,10 @@ __device__ void equilibrium_wall_flux(const MacroArgs &m, const double *p, int a
   const double ut2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
   const double uw2 = uwt[0] * uwt[0] + uwt[1] * uwt[1] + uwt[2] * uwt[2];
   F[0] = rho * J1 + rw * K1;
+#pragma unroll
   for (int b = 0; b < 3; ++b) F[1 + b] = (b == a ? sg : 0.0) * (rho * J2 + rw * K2) + rho * J1 * ut[b] + rw * K1 * uwt[b];
-  const double rin = m.nW == 6 ? m.d_r * p[5] / 4.0 * rho * J1 : 0.0;
-  const double rout = m.nW == 6 ? m.d_r * Tw / 4.0 * rw * K1 : 0.0;
+  const double rin = NW == 6 ? m.d_r * p[5] / 4.0 * rho * J1 : 0.0;
+  const double rout = NW == 6 ? m.d_r * Tw / 4.0 * rw * K1 : 0.0;
   F[4] = 0.5 * rho * (J3 + J1 * (ut2 + T)) + 0.5 * rw * (K3 + K1 * (uw2 + Tw)) + rin + rout;
   F[5] = rin + rout;
 }
@@ -149,313 +165,418 @@ __device__ __forceinline__ double cell_volume(const MacroArgs &m, const int *nt)
   return m.ax[0][nt[0]].h * m.ax[1][nt[1]].h * m.ax[2][nt[2]].h;
 }
 
-// A: primitives and the per-cell quantities the later phases read
-__device__ void cell_aux(const MacroArgs &m, int c) {
-  double *p = m.pr + (size_t)c * 6;
-  const double *W = m.W + (size_t)c * 6;
-  prim_of(W, m.nW, m.d_r, p);
-  if (!(p[0] > 0.0) || !(p[4] > 0.0) || !(p[5] > 0.0)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
+__device__ __forceinline__ const AxisCell<double> *axis_cells(const MacroArgs &m, int a) {
+  return pick3(a, m.ax[0], m.ax[1], m.ax[2]);
+}
+
+// Primitives and the per-cell quantities the later phases read (everything but the fluxes)
+template <int NW>
+__device__ void cell_prims(const MacroArgs &m, int c, const double *W) {
+  double p[6];
+  prim_of<NW>(W, m.d_r, p);
+  if (!physical(p)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) m.pr[(size_t)c * 6 + k] = p[k];
   double *x = m.aux + (size_t)c * NAUX;
   const double mu = m.Kn / sqrt(kPi) * pow(p[4], m.omega);
   const double cs = sound(p[4]);
   x[0] = mu;
   x[1] = mu / p[0];
   x[2] = cs;
+  x[3] = fabs(p[1]) + cs;
+  x[4] = fabs(p[2]) + cs;
+  x[5] = fabs(p[3]) + cs;
+}
+
+// B, one item: LSQ gradient of field k (limited conservative field for k < NW, else primitive
+// k - NW + 1) with its Venkatakrishnan limiter, or (k = NW + 5) the local time step and diagonal.
+template <int NW>
+__device__ void gradient_item(const MacroArgs &m, const int *cs, int c, int k) {
+  const KinGeom &g = m.g;
+  int nt[3];
+  nat_of(g, c, nt);
+  if (k < NW + 5) {
+    const bool lim = k < NW;
+    const double *q = lim ? m.W + k : m.pr + 1 + (k - NW);
+    const double qi = q[(size_t)c * 6];
+    double gr[3] = {0, 0, 0}, qmax = qi, qmin = qi, V = 1.0;
+    AxisCell<double> gc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      gc[a] = m.ax[a][nt[a]];
+      V *= gc[a].h;
+      if (!g.act[a]) continue;
+      double lo = qi, hi = qi;
+      if (nt[a] > 0) { lo = q[(size_t)(c - cs[a]) * 6]; qmax = fmax(qmax, lo); qmin = fmin(qmin, lo); }
+      if (nt[a] < g.n[a] - 1) { hi = q[(size_t)(c + cs[a]) * 6]; qmax = fmax(qmax, hi); qmin = fmin(qmin, hi); }
+      gr[a] = gc[a].clo * (lo - qi) + gc[a].chi * (hi - qi);
+    }
+    if (lim) {
+      // Venkatakrishnan: min over the faces (and 1) of (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
+      // compared by cross-multiplication and divided once
+      const double eps2 = g.K3 * V;
+      double bn = 1.0, bd = 1.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (!g.act[a]) continue;
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          const double d2 = gr[a] * (sd ? gc[a].rhi : gc[a].rlo);
+          const double dm = d2 > 0.0 ? qmax - qi : (d2 < 0.0 ? qmin - qi : 0.0);
+          const double nn = dm * dm + eps2 + 2.0 * d2 * dm, dd = dm * dm + 2.0 * d2 * d2 + dm * d2 + eps2;
+          if (nn * bd < bn * dd) { bn = nn; bd = dd; }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) m.gW[((size_t)c * 6 + k) * 3 + a] = gr[a];
+      m.phW[(size_t)c * 6 + k] = bn / bd;
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) m.gP[((size_t)c * 5 + (k - NW)) * 3 + a] = gr[a];
+    }
+    return;
+  }
+  // local time step and diagonal D_i = 1/dt_i + (1/2V_i) sum_f Gamma_f A_f (- dQ/dW)
+  const double *xi = m.aux + (size_t)c * NAUX;
+  const double V = cell_volume(m, nt);
+  double lsum = 0.0, gsum = 0.0;
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    x[3 + a] = fabs(p[1 + a]) + cs;
-    euler_axis(W, m.nW, a, 1.0, m.Fc + ((size_t)c * 3 + a) * 6);
+    if (!g.act[a]) continue;
+    const AxisCell<double> ga = m.ax[a][nt[a]];
+    const double A = V * ga.invh, li = xi[3 + a];
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const bool inside = sd ? nt[a] < g.n[a] - 1 : nt[a] > 0;
+      lsum += li * A;
+      double gam;
+      if (inside) {
+        const int j = c + (sd ? cs[a] : -cs[a]);
+        const double *xj = m.aux + (size_t)j * NAUX;
+        const double idx = sd ? ga.pad0 : m.ax[a][nt[a] - 1].pad0;  // 1 / centre distance
+        gam = fmax(li, xj[3 + a]) + 2.0 * fmax(xi[1], xj[1]) * idx;
+        if (sd) m.gam[(size_t)c * 3 + a] = gam;
+      } else {
+        gam = li + 2.0 * xi[1] * (2.0 * ga.invh);  // wall at half a cell width
+      }
+      gsum += gam * A;
+    }
+  }
+  const double inv_dt = lsum / (m.cfl * V);
+  double srcdiag = 0.0;
+  if (NW == 6) {
+    const double *p = m.pr + (size_t)c * 6;
+    const double tau = 2.0 * m.Kn / sqrt(kPi) * pow(p[4], m.omega - 1.0) / p[0];
+    srcdiag = 1.0 / (m.Z_r * tau);
+  }
+  const double Dt = inv_dt + gsum / (2.0 * V), iD = 1.0 / Dt;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) m.invD[(size_t)c * 6 + q] = iD;
+  m.invD[(size_t)c * 6 + 5] = NW == 6 ? 1.0 / (Dt + srcdiag) : iD;
+}
+
+// C, one item: Rusanov convective + NSF viscous flux (area-integrated) through the + face of
+// cell c along axis a, from the limited linear reconstructions of both sides.
+template <int NW>
+__device__ void face_item(const MacroArgs &m, const int *cs, int c, int a) {
+  const KinGeom &g = m.g;
+  int nt[3];
+  nat_of(g, c, nt);
+  const int na = pick3(a, nt[0], nt[1], nt[2]);
+  if (na >= pick3(a, g.n[0], g.n[1], g.n[2]) - 1) return;
+  const int j = c + pick3(a, cs[0], cs[1], cs[2]);
+  const AxisCell<double> *axa = axis_cells(m, a);
+  const double rhi = axa[na].rhi, rlo = axa[na + 1].rlo;
+  const double A = cell_volume(m, nt) * axa[na].invh;
+  double WL[6], WR[6], pL[6], pR[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    WL[k] = m.W[(size_t)c * 6 + k];
+    WR[k] = m.W[(size_t)j * 6 + k];
+  }
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    WL[k] += m.phW[(size_t)c * 6 + k] * m.gW[((size_t)c * 6 + k) * 3 + a] * rhi;
+    WR[k] += m.phW[(size_t)j * 6 + k] * m.gW[((size_t)j * 6 + k) * 3 + a] * rlo;
+  }
+  prim_of<NW>(WL, m.d_r, pL);
+  prim_of<NW>(WR, m.d_r, pR);
+  if (!physical(pL)) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) WL[k] = m.W[(size_t)c * 6 + k];
+    prim_of<NW>(WL, m.d_r, pL);
+  }
+  if (!physical(pR)) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) WR[k] = m.W[(size_t)j * 6 + k];
+    prim_of<NW>(WR, m.d_r, pR);
+  }
+  double FL[6], FR[6], F[6];
+  euler_axis<NW>(WL, a, 1.0, FL);
+  euler_axis<NW>(WR, a, 1.0, FR);
+  const double lam = fmax(fabs(pick3(a, pL[1], pL[2], pL[3])) + sound(pL[4]),
+                          fabs(pick3(a, pR[1], pR[2], pR[3])) + sound(pR[4]));
+#pragma unroll
+  for (int k = 0; k < 6; ++k) F[k] = k < NW ? 0.5 * (FL[k] + FR[k]) - 0.5 * lam * (WR[k] - WL[k]) : 0.0;
+  // NSF viscous and conductive flux, face gradients = mean of the cells' gradients
+  const double *gPc = m.gP + (size_t)c * 15, *gPj = m.gP + (size_t)j * 15;
+  double G3[3][3], Ga[3], uf[3];  // G3[b][d] = d u_b / dx_d, Ga[b] = d u_a / dx_b
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) G3[b][d] = 0.5 * (gPc[b * 3 + d] + gPj[b * 3 + d]);
+    uf[b] = 0.5 * (m.pr[(size_t)c * 6 + 1 + b] + m.pr[(size_t)j * 6 + 1 + b]);
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) Ga[b] = pick3(a, G3[0][b], G3[1][b], G3[2][b]);
+  const double gTa = 0.5 * (gPc[9 + a] + gPj[9 + a]);
+  const double gTra = 0.5 * (gPc[12 + a] + gPj[12 + a]);
+  const double muf = 0.5 * (m.aux[(size_t)c * NAUX] + m.aux[(size_t)j * NAUX]);
+  double kt, kr;
+  kappas(m, muf, &kt, &kr);
+  const double div = G3[0][0] + G3[1][1] + G3[2][2];
+  double sn[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+    sn[b] = -muf * (pick3(a, G3[b][0], G3[b][1], G3[b][2]) + Ga[b] - (a == b ? 2.0 / 3.0 * div : 0.0));
+#pragma unroll
+  for (int b = 0; b < 3; ++b) F[1 + b] += sn[b];
+  F[4] += sn[0] * uf[0] + sn[1] * uf[1] + sn[2] * uf[2] - kt * gTa - (NW == 6 ? kr * gTra : 0.0);
+  if (NW == 6) F[5] += -kr * gTra;
+  double *Ff = m.Ffc + ((size_t)c * 3 + a) * 6;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Ff[k] = F[k] * A;
+}
+
+// C, one wall item: equilibrium wall flux (area-integrated) of wall face wf
+template <int NW>
+__device__ void wall_item(const MacroArgs &m, int wf) {
+  const int c = m.wall_cell[wf], side = m.wall_side[wf], a = side / 2;
+  int nt[3];
+  nat_of(m.g, c, nt);
+  const double A = cell_volume(m, nt) * axis_cells(m, a)[pick3(a, nt[0], nt[1], nt[2])].invh;
+  double p[6], feq[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = m.pr[(size_t)c * 6 + k];
+  equilibrium_wall_flux<NW>(m, p, a, (side & 1) ? 1.0 : -1.0, m.wall_uT + 4 * side, feq);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) m.wfl[(size_t)wf * 6 + k] = k < NW ? feq[k] * A : 0.0;
+}
+
+// E, one lane: the face on side sd of axis a of cell c.  With nb_term it adds the face's
+// off-diagonal term (1/2V) A [Delta F_j(n) - Gamma dW_j] to acc, the neighbour state being
+// W_j + dW_j, or W_j alone once the neighbour has been updated in place; in the first pass it
+// puts the face's outward flux into S.
+template <int NW>
+__device__ __forceinline__ void sweep_face(const MacroArgs &m, const double *Fc, const int *cs, int c,
+                                           const int *nt, int a, int sd, bool nb_term, bool nb_updated, bool first,
+                                           double *acc, double *S) {
+  const KinGeom &g = m.g;
+  const int na = pick3(a, nt[0], nt[1], nt[2]);
+  const bool inside = sd ? na < pick3(a, g.n[0], g.n[1], g.n[2]) - 1 : na > 0;
+  if (inside) {
+    const int csa = pick3(a, cs[0], cs[1], cs[2]);
+    const int j = sd ? c + csa : c - csa;
+    if (nb_term) {
+      const double sg = sd ? 1.0 : -1.0;
+      const double gam = m.gam[(size_t)(sd ? c : j) * 3 + a];
+      const double half_AoV = 0.5 * axis_cells(m, a)[na].invh;  // A / (2 V) on a rectilinear cell
+      double Wn[6], dWj[6], F1[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        dWj[k] = m.dW[(size_t)j * 6 + k];
+        Wn[k] = nb_updated ? m.W[(size_t)j * 6 + k] : m.W[(size_t)j * 6 + k] + dWj[k];
+      }
+      euler_axis<NW>(Wn, a, sg, F1);
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        const double dF = F1[k] - sg * Fc[((size_t)j * 3 + a) * 6 + k];
+        acc[k] = (dF - gam * dWj[k]) * half_AoV;
+      }
+    }
+    if (first)
+#pragma unroll
+      for (int k = 0; k < NW; ++k) S[k] = sd ? m.Ffc[((size_t)c * 3 + a) * 6 + k] : -m.Ffc[((size_t)j * 3 + a) * 6 + k];
+  } else if (first) {
+    const int wb = g.wall_base[2 * a + sd];
+    if (wb >= 0) {
+      const int trn = pick3(a, nt[1] + g.n[1] * nt[2], nt[0] + g.n[0] * nt[2], nt[0] + g.n[0] * nt[1]);
+#pragma unroll
+      for (int k = 0; k < NW; ++k) S[k] = m.wfl[(size_t)(wb + trn) * 6 + k];
+    }
   }
 }
 }  // namespace
 
+template <int NW>
 __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   const KinGeom &g = m.g;
-  const int nc = g.nc, nW = m.nW;
+  const int nc = g.nc, nact = g.nact;
   const Items it;
   const int cs[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  static_assert(kBlock >= 12 * 32, "one warp per reduced field");
   __shared__ double wsum[kBlock / 32][12];
   __shared__ double sdelta;
 
-  // initial conservative state from the moments of f^{n+1/2}, then A
+  // initial conservative state from the moments of f^{n+1/2}, its primitives and axis fluxes
   for (int c = it.first; c < nc; c += it.stride) {
     const double *M = m.Mh + (size_t)c * 18;
-    double *W = m.W + (size_t)c * 6;
+    double W[6];
     const double rho = M[0];
     W[0] = rho;
     W[1] = rho * M[1];
     W[2] = rho * M[2];
     W[3] = rho * M[3];
-    const double Er = nW == 6 ? m.d_r * rho * M[5] / 4.0 : 0.0;
+    const double Er = NW == 6 ? m.d_r * rho * M[5] / 4.0 : 0.0;
     W[4] = 0.5 * rho * (M[1] * M[1] + M[2] * M[2] + M[3] * M[3]) + 0.75 * rho * M[4] + Er;
     W[5] = Er;
-    cell_aux(m, c);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) m.W[(size_t)c * 6 + k] = W[k];
+    cell_prims<NW>(m, c, W);
+    for (int a = 0; a < nact; ++a) euler_axis<NW>(W, a, 1.0, m.Fc + ((size_t)c * 3 + a) * 6);
   }
   if (!grid_sync(m.bar, m.err)) return;
 
-  const int nB = nW + 6;  // phase-B items per cell: nW limited fields, 5 primitive gradients, 1 diagonal
-  const int G = 2 * g.nact <= 2 ? 2 : (2 * g.nact <= 4 ? 4 : 8);  // lanes per cell in the sweeps
+  const int lgG = 2 * nact <= 2 ? 1 : (2 * nact <= 4 ? 2 : 3);  // lanes per cell in the sweeps: one per face
+  const int G = 1 << lgG;
   int used = 0;
   for (int step = 0; step < m.steps; ++step) {
+    // axis fluxes at the start of this step, and the buffer for those at its end
+    const double *Fc = m.Fc + (size_t)(step & 1) * nc * 18;
+    double *Fn = m.Fc + (size_t)((step + 1) & 1) * nc * 18;
     // ---- B: gradients and limiters per (cell, field); time step and diagonal per cell
-    for (int t = it.first; t < nc * nB; t += it.stride) {
-      const int c = t / nB, k = t % nB;
-      int nt[3];
-      nat_of(g, c, nt);
-      if (k < nW + 5) {
-        const bool lim = k < nW;
-        const double *q = lim ? m.W + k : m.pr + 1 + (k - nW);
-        const double qi = q[(size_t)c * 6];
-        double gr[3] = {0, 0, 0}, qmax = qi, qmin = qi, V = 1.0;
-        AxisCell<double> gc[3];
-        for (int a = 0; a < 3; ++a) {
-          gc[a] = m.ax[a][nt[a]];
-          V *= gc[a].h;
-          if (!g.act[a]) continue;
-          double lo = qi, hi = qi;
-          if (nt[a] > 0) { lo = q[(size_t)(c - cs[a]) * 6]; qmax = fmax(qmax, lo); qmin = fmin(qmin, lo); }
-          if (nt[a] < g.n[a] - 1) { hi = q[(size_t)(c + cs[a]) * 6]; qmax = fmax(qmax, hi); qmin = fmin(qmin, hi); }
-          gr[a] = gc[a].clo * (lo - qi) + gc[a].chi * (hi - qi);
-        }
-        if (lim) {
-          // Venkatakrishnan: min over the faces (and 1) of (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
-          // compared by cross-multiplication and divided once
-          const double eps2 = g.K3 * V;
-          double bn = 1.0, bd = 1.0;
-          for (int a = 0; a < 3; ++a) {
-            if (!g.act[a]) continue;
-            for (int sd = 0; sd < 2; ++sd) {
-              const double d2 = gr[a] * (sd ? gc[a].rhi : gc[a].rlo);
-              const double dm = d2 > 0.0 ? qmax - qi : (d2 < 0.0 ? qmin - qi : 0.0);
-              const double nn = dm * dm + eps2 + 2.0 * d2 * dm, dd = dm * dm + 2.0 * d2 * d2 + dm * d2 + eps2;
-              if (nn * bd < bn * dd) { bn = nn; bd = dd; }
-            }
-          }
-          for (int a = 0; a < 3; ++a) m.gW[((size_t)c * 6 + k) * 3 + a] = gr[a];
-          m.phW[(size_t)c * 6 + k] = bn / bd;
-        } else {
-          for (int a = 0; a < 3; ++a) m.gP[((size_t)c * 5 + (k - nW)) * 3 + a] = gr[a];
-        }
-      } else {
-        // local time step and diagonal D_i = 1/dt_i + (1/2V_i) sum_f Gamma_f A_f (- dQ/dW)
-        const double *xi = m.aux + (size_t)c * NAUX;
-        const double V = cell_volume(m, nt);
-        double lsum = 0.0, gsum = 0.0;
-        for (int a = 0; a < 3; ++a) {
-          if (!g.act[a]) continue;
-          const AxisCell<double> ga = m.ax[a][nt[a]];
-          const double A = V * ga.invh, li = xi[3 + a];
-          for (int sd = 0; sd < 2; ++sd) {
-            const bool inside = sd ? nt[a] < g.n[a] - 1 : nt[a] > 0;
-            lsum += li * A;
-            double gam;
-            if (inside) {
-              const int j = c + (sd ? cs[a] : -cs[a]);
-              const double *xj = m.aux + (size_t)j * NAUX;
-              const double idx = sd ? ga.pad0 : m.ax[a][nt[a] - 1].pad0;  // 1 / centre distance
-              gam = fmax(li, xj[3 + a]) + 2.0 * fmax(xi[1], xj[1]) * idx;
-              if (sd) m.gam[(size_t)c * 3 + a] = gam;
-            } else {
-              gam = li + 2.0 * xi[1] * (2.0 * ga.invh);  // wall at half a cell width
-            }
-            gsum += gam * A;
-          }
-        }
-        const double inv_dt = lsum / (m.cfl * V);
-        double srcdiag = 0.0;
-        if (nW == 6) {
-          const double *p = m.pr + (size_t)c * 6;
-          const double tau = 2.0 * m.Kn / sqrt(kPi) * pow(p[4], m.omega - 1.0) / p[0];
-          srcdiag = 1.0 / (m.Z_r * tau);
-        }
-        const double Dt = inv_dt + gsum / (2.0 * V);
-        for (int q = 0; q < 6; ++q) m.invD[(size_t)c * 6 + q] = 1.0 / (Dt + (q == 5 ? srcdiag : 0.0));
-      }
+    const int nB = NW + 6;
+    for (int t = it.first; t < nc * nB; t += it.stride) gradient_item<NW>(m, cs, t / nB, t % nB);
+    if (!grid_sync(m.bar, m.err)) return;
+    // ---- C: interior + faces of the active axes, then the wall faces
+    for (int t = it.first; t < nact * nc + m.nwall; t += it.stride) {
+      if (t >= nact * nc)
+        wall_item<NW>(m, t - nact * nc);
+      else
+        face_item<NW>(m, cs, t / nact, t % nact);
     }
     if (!grid_sync(m.bar, m.err)) return;
-    // ---- C: interior + faces (Rusanov + NSF) and wall faces (equilibrium wall flux)
-    for (int t = it.first; t < 3 * nc + m.nwall; t += it.stride) {
-      if (t >= 3 * nc) {
-        const int wf = t - 3 * nc;
-        const int c = m.wall_cell[wf], side = m.wall_side[wf], a = side / 2;
-        int nt[3];
-        nat_of(g, c, nt);
-        const double A = cell_volume(m, nt) * m.ax[a][nt[a]].invh;
-        double feq[6];
-        equilibrium_wall_flux(m, m.pr + (size_t)c * 6, a, (side & 1) ? 1.0 : -1.0, m.wall_uT + 4 * side, feq);
-        for (int k = 0; k < 6; ++k) m.wfl[(size_t)wf * 6 + k] = k < nW ? feq[k] * A : 0.0;
-        continue;
-      }
-      const int c = t / 3, a = t % 3;
-      if (!g.act[a]) continue;
-      int nt[3];
-      nat_of(g, c, nt);
-      if (nt[a] >= g.n[a] - 1) continue;
-      const int j = c + cs[a];
-      const AxisCell<double> gi = m.ax[a][nt[a]], gj = m.ax[a][nt[a] + 1];
-      const double A = cell_volume(m, nt) * gi.invh;
-      double WL[6], WR[6], pL[6], pR[6];
-      for (int k = 0; k < 6; ++k) {
-        WL[k] = m.W[(size_t)c * 6 + k];
-        WR[k] = m.W[(size_t)j * 6 + k];
-      }
-      for (int k = 0; k < nW; ++k) {
-        WL[k] += m.phW[(size_t)c * 6 + k] * m.gW[((size_t)c * 6 + k) * 3 + a] * gi.rhi;
-        WR[k] += m.phW[(size_t)j * 6 + k] * m.gW[((size_t)j * 6 + k) * 3 + a] * gj.rlo;
-      }
-      prim_of(WL, nW, m.d_r, pL);
-      prim_of(WR, nW, m.d_r, pR);
-      if (!(pL[0] > 0.0) || !(pL[4] > 0.0) || !(pL[5] > 0.0)) {
-        for (int k = 0; k < 6; ++k) WL[k] = m.W[(size_t)c * 6 + k];
-        prim_of(WL, nW, m.d_r, pL);
-      }
-      if (!(pR[0] > 0.0) || !(pR[4] > 0.0) || !(pR[5] > 0.0)) {
-        for (int k = 0; k < 6; ++k) WR[k] = m.W[(size_t)j * 6 + k];
-        prim_of(WR, nW, m.d_r, pR);
-      }
-      double FL[6], FR[6], F[6];
-      euler_axis(WL, nW, a, 1.0, FL);
-      euler_axis(WR, nW, a, 1.0, FR);
-      const double lam = fmax(fabs(pL[1 + a]) + sound(pL[4]), fabs(pR[1 + a]) + sound(pR[4]));
-      for (int k = 0; k < 6; ++k) F[k] = k < nW ? 0.5 * (FL[k] + FR[k]) - 0.5 * lam * (WR[k] - WL[k]) : 0.0;
-      // NSF viscous and conductive flux, face gradients = mean of the cells' gradients
-      double G3[3][3], gT[3], gTr[3], uf[3];
-      for (int b = 0; b < 3; ++b) {
-        for (int d = 0; d < 3; ++d) G3[b][d] = 0.5 * (m.gP[((size_t)c * 5 + b) * 3 + d] + m.gP[((size_t)j * 5 + b) * 3 + d]);
-        gT[b] = 0.5 * (m.gP[((size_t)c * 5 + 3) * 3 + b] + m.gP[((size_t)j * 5 + 3) * 3 + b]);
-        gTr[b] = 0.5 * (m.gP[((size_t)c * 5 + 4) * 3 + b] + m.gP[((size_t)j * 5 + 4) * 3 + b]);
-        uf[b] = 0.5 * (m.pr[(size_t)c * 6 + 1 + b] + m.pr[(size_t)j * 6 + 1 + b]);
-      }
-      const double muf = 0.5 * (m.aux[(size_t)c * NAUX] + m.aux[(size_t)j * NAUX]);
-      double kt, kr;
-      kappas(m, muf, &kt, &kr);
-      const double div = G3[0][0] + G3[1][1] + G3[2][2];
-      double sn[3];
-      for (int b = 0; b < 3; ++b) sn[b] = -muf * (G3[b][a] + G3[a][b] - (a == b ? 2.0 / 3.0 * div : 0.0));
-      for (int b = 0; b < 3; ++b) F[1 + b] += sn[b];
-      F[4] += sn[0] * uf[0] + sn[1] * uf[1] + sn[2] * uf[2] - kt * gT[a] - (nW == 6 ? kr * gTr[a] : 0.0);
-      if (nW == 6) F[5] += -kr * gTr[a];
-      double *Ff = m.Ffc + ((size_t)c * 3 + a) * 6;
-      for (int k = 0; k < 6; ++k) Ff[k] = F[k] * A;
-    }
-    if (!grid_sync(m.bar, m.err)) return;
-    // ---- D: residual.  S = sum over the cell's faces of this scheme's outward flux; the frozen
-    // correction corr = K - S(W^{n+1/2}) makes R_i(W^{n+1/2}) the kinetic moment residual.
-    for (int c = it.first; c < nc; c += it.stride) {
-      int nt[3];
-      nat_of(g, c, nt);
-      const double V = cell_volume(m, nt);
-      double S[6] = {0, 0, 0, 0, 0, 0};
-      for (int a = 0; a < 3; ++a) {
-        if (!g.act[a]) continue;
-        if (nt[a] < g.n[a] - 1)
-          for (int k = 0; k < nW; ++k) S[k] += m.Ffc[((size_t)c * 3 + a) * 6 + k];
-        if (nt[a] > 0)
-          for (int k = 0; k < nW; ++k) S[k] -= m.Ffc[((size_t)(c - cs[a]) * 3 + a) * 6 + k];
-        const int trn = a == 0 ? nt[1] + g.n[1] * nt[2] : (a == 1 ? nt[0] + g.n[0] * nt[2] : nt[0] + g.n[0] * nt[1]);
-        if (nt[a] == 0 && g.wall_base[2 * a] >= 0)
-          for (int k = 0; k < nW; ++k) S[k] += m.wfl[(size_t)(g.wall_base[2 * a] + trn) * 6 + k];
-        if (nt[a] == g.n[a] - 1 && g.wall_base[2 * a + 1] >= 0)
-          for (int k = 0; k < nW; ++k) S[k] += m.wfl[(size_t)(g.wall_base[2 * a + 1] + trn) * 6 + k];
-      }
-      double *cr = m.corr + (size_t)c * 6;
-      if (step == 0)
-        for (int k = 0; k < nW; ++k) cr[k] = m.K[(size_t)c * 6 + k] - S[k];
-      double R[6] = {0, 0, 0, 0, 0, 0};
-      for (int k = 0; k < nW; ++k) R[k] = -(S[k] + cr[k]) / V;
-      if (nW == 6) {
-        const double *p = m.pr + (size_t)c * 6;
-        const double tau = 2.0 * m.Kn / sqrt(kPi) * pow(p[4], m.omega - 1.0) / p[0];
-        const double T = (3.0 * p[4] + m.d_r * p[5]) / (3.0 + m.d_r);
-        R[5] += m.d_r * p[0] * (T - p[5]) / (4.0 * m.Z_r * tau);
-      }
-      for (int k = 0; k < 6; ++k) {
-        m.R[(size_t)c * 6 + k] = R[k];
-        m.dW[(size_t)c * 6 + k] = 0.0;
-      }
-    }
-    if (!grid_sync(m.bar, m.err)) return;
-    // ---- E: red/black point-implicit sweeps, G lanes per cell (one per neighbour)
+    // ---- E: red/black point-implicit sweeps, G lanes per cell (one per face)
+    double num[NW], den[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) num[k] = den[k] = 0.0;
     for (int sw = 0; sw < m.sweeps; ++sw) {
+      const bool first = sw == 0, last = sw == m.sweeps - 1;
       for (int col = 0; col < 2; ++col) {
         const int off = col ? m.ncol0 : 0, cnt = col ? nc - m.ncol0 : m.ncol0;
-        // all lanes of a group loop together so the group shuffle is converged
-        const int nitems = ((cnt * G + 31) / 32) * 32;
+        // in the first red pass every increment is still zero; in the last black pass the red
+        // neighbours hold W + dW already
+        const bool nb_term = !(first && col == 0), nb_updated = last && col == 1;
+        // all lanes of a group loop together so the group shuffles are converged
+        const int nitems = (((cnt << lgG) + 31) / 32) * 32;
         for (int t = it.first; t < nitems; t += it.stride) {
-          const int q = t / G, gl = t % G;
+          const int q = t >> lgG, gl = t & (G - 1);
           const bool live = q < cnt;
           const int c = live ? m.colcells[off + q] : 0;
-          double acc[6] = {0, 0, 0, 0, 0, 0};
+          int nt[3];
+          nat_of(g, c, nt);
+          double acc[NW], S[NW];
+#pragma unroll
+          for (int k = 0; k < NW; ++k) acc[k] = S[k] = 0.0;
           const int a = gl >> 1, sd = gl & 1;
-          if (live && a < 3 && g.act[a]) {
-            int nt[3];
-            nat_of(g, c, nt);
-            const bool inside = sd ? nt[a] < g.n[a] - 1 : nt[a] > 0;
-            if (inside) {
-              const int j = c + (sd ? cs[a] : -cs[a]);
-              const double sg = sd ? 1.0 : -1.0;
-              const double gam = sd ? m.gam[(size_t)c * 3 + a] : m.gam[(size_t)j * 3 + a];
-              const double half_AoV = 0.5 * m.ax[a][nt[a]].invh;  // A / (2 V) on a rectilinear cell
-              double Wn[6], F1[6];
-              for (int k = 0; k < 6; ++k) Wn[k] = m.W[(size_t)j * 6 + k] + m.dW[(size_t)j * 6 + k];
-              euler_axis(Wn, nW, a, sg, F1);
-              for (int k = 0; k < nW; ++k) {
-                const double dF = F1[k] - sg * m.Fc[((size_t)j * 3 + a) * 6 + k];
-                acc[k] = (dF - gam * m.dW[(size_t)j * 6 + k]) * half_AoV;
+          if (live && a < nact) sweep_face<NW>(m, Fc, cs, c, nt, a, sd, nb_term, nb_updated, first, acc, S);
+          for (int o = 1; o < G; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+              acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o, G);
+              if (first) S[k] += __shfl_xor_sync(0xffffffffu, S[k], o, G);
+            }
+          }
+          double Wnew[6];
+          if (live && gl == 0) {
+            const double V = cell_volume(m, nt);
+            double R[NW];
+            if (first) {
+              // residual R_i = -(S + corr) / V, corr frozen at the first inner step
+              double *cr = m.corr + (size_t)c * 6;
+              if (step == 0)
+#pragma unroll
+                for (int k = 0; k < NW; ++k) cr[k] = m.K[(size_t)c * 6 + k] - S[k];
+#pragma unroll
+              for (int k = 0; k < NW; ++k) R[k] = -(S[k] + cr[k]) / V;
+              if (NW == 6) {
+                const double *p = m.pr + (size_t)c * 6;
+                const double tau = 2.0 * m.Kn / sqrt(kPi) * pow(p[4], m.omega - 1.0) / p[0];
+                const double T = (3.0 * p[4] + m.d_r * p[5]) / (3.0 + m.d_r);
+                R[NW - 1] += m.d_r * p[0] * (T - p[5]) / (4.0 * m.Z_r * tau);
+              }
+              if (!last)
+#pragma unroll
+                for (int k = 0; k < NW; ++k) m.R[(size_t)c * 6 + k] = R[k];
+            } else {
+#pragma unroll
+              for (int k = 0; k < NW; ++k) R[k] = m.R[(size_t)c * 6 + k];
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Wnew[k] = m.W[(size_t)c * 6 + k];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+              const double d = (R[k] - acc[k]) * m.invD[(size_t)c * 6 + k];
+              m.dW[(size_t)c * 6 + k] = d;
+              if (last) {
+                const double w = Wnew[k] + d;
+                if (!isfinite(w)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
+                Wnew[k] = w;
+                m.W[(size_t)c * 6 + k] = w;
+                num[k] += d * d * V;
+                den[k] += w * w * V;
               }
             }
           }
-          for (int o = 1; o < G; o <<= 1)
-            for (int k = 0; k < 6; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o, G);
-          if (live && gl == 0)
-            for (int k = 0; k < nW; ++k)
-              m.dW[(size_t)c * 6 + k] = (m.R[(size_t)c * 6 + k] - acc[k]) * m.invD[(size_t)c * 6 + k];
+          if (last) {
+            // the group's odd lanes recompute the axis fluxes of the updated cell, lane 0 the rest
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Wnew[k] = __shfl_sync(0xffffffffu, Wnew[k], 0, G);
+            if (live && gl == 0) cell_prims<NW>(m, c, Wnew);
+            if (live && sd == 1 && a < nact) euler_axis<NW>(Wnew, a, 1.0, Fn + ((size_t)c * 3 + a) * 6);
+          }
+        }
+        if (last && col == 1) {
+          // block partials of the inner residual, double buffered by step
+          double *red = m.red + (size_t)(step & 1) * gridDim.x * 16;
+          const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            const int f = k < 6 ? k : k - 6;
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < NW; ++q)
+              if (q == f) v = k < 6 ? num[q] : den[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) wsum[wid][k] = v;
+          }
+          __syncthreads();
+          if (threadIdx.x < 12) {
+            double v = 0.0;
+            for (int w = 0; w < nwarps; ++w) v += wsum[w][threadIdx.x];
+            red[(size_t)blockIdx.x * 16 + threadIdx.x] = v;
+          }
         }
         if (!grid_sync(m.bar, m.err)) return;
       }
     }
-    // ---- F: update, inner residual partials (double buffered), then A for the next step
-    double num[6] = {0, 0, 0, 0, 0, 0}, den[6] = {0, 0, 0, 0, 0, 0};
-    for (int c = it.first; c < nc; c += it.stride) {
-      int nt[3];
-      nat_of(g, c, nt);
-      const double V = cell_volume(m, nt);
-      for (int k = 0; k < nW; ++k) {
-        double &w = m.W[(size_t)c * 6 + k];
-        const double d = m.dW[(size_t)c * 6 + k];
-        w += d;
-        if (!isfinite(w)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
-        num[k] += d * d * V;
-        den[k] += w * w * V;
-      }
-      cell_aux(m, c);
-    }
-    double *red = m.red + (size_t)(step & 1) * gridDim.x * 16;
-    {
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-      for (int k = 0; k < 12; ++k) {
-        double v = k < 6 ? num[k] : den[k - 6];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) wsum[wid][k] = v;
-      }
-      __syncthreads();
-      if (threadIdx.x < 12) {
-        double v = 0.0;
-        for (int w = 0; w < nwarps; ++w) v += wsum[w][threadIdx.x];
-        red[(size_t)blockIdx.x * 16 + threadIdx.x] = v;
-      }
-    }
-    if (!grid_sync(m.bar, m.err)) return;
     used = step + 1;
-    // the same fixed-order sum in every block; the partials of this step are not overwritten
-    // before two more barriers, so no barrier is needed after reading them
+    // every block sums the partials in the same fixed order: warp k < 12 adds up field k, lane l
+    // over the blocks l, l + 32, ..., then a butterfly over the lanes (the partials of this step
+    // are not overwritten before two more barriers, so no barrier is needed after reading them)
+    const double *red = m.red + (size_t)(step & 1) * gridDim.x * 16;
+    if ((threadIdx.x >> 5) < 12) {
+      const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      double v = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(red + (size_t)b * 16 + k);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) wsum[0][k] = v;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double tot[12];
-      for (int k = 0; k < 12; ++k) tot[k] = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b)
-        for (int k = 0; k < 12; ++k) tot[k] += ((volatile double *)red)[(size_t)b * 16 + k];
       double delta = 0.0;
-      for (int k = 0; k < nW; ++k)
-        if (tot[6 + k] > 0.0) delta = fmax(delta, sqrt(tot[k] / tot[6 + k]));
+      for (int k = 0; k < NW; ++k)
+        if (wsum[0][6 + k] > 0.0) delta = fmax(delta, sqrt(wsum[0][k] / wsum[0][6 + k]));
       sdelta = delta;
     }
     __syncthreads();
@@ -480,17 +601,19 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   }
   if (!grid_sync(m.bar, m.err)) return;
   __shared__ double sfac;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     double mm = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) mm += ((volatile double *)red)[b];
-    sfac = m.closed ? m.mass_ref / mm : 1.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) mm += __ldcg(red + b);
+    for (int o = 16; o > 0; o >>= 1) mm += __shfl_xor_sync(0xffffffffu, mm, o);
+    if (threadIdx.x == 0) sfac = m.closed ? m.mass_ref / mm : 1.0;
   }
   __syncthreads();
   const double fac = sfac;
   for (int c = it.first; c < nc; c += it.stride) {
     double p[6];
-    prim_of(m.W + (size_t)c * 6, nW, m.d_r, p);
+    prim_of<NW>(m.W + (size_t)c * 6, m.d_r, p);
     p[0] *= fac;
+#pragma unroll
     for (int k = 0; k < 6; ++k) m.Wout[(size_t)c * 6 + k] = p[k];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *m.iters = used;
@@ -502,14 +625,16 @@ int macro_block_size() { return kBlock; }
 // must hold some.  The cooperative launch guarantees the blocks are co-resident.
 cudaError_t macro_launch_shape(int nc, int *grid, int *block) {
   (void)nc;
-  int dev = 0, nsm = 0, per = 0;
+  int dev = 0, nsm = 0, per5 = 0, per6 = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, macro_kernel, kBlock, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per5, macro_kernel<5>, kBlock, 0);
   if (e != cudaSuccess) return e;
-  if (per < 1) return cudaErrorInvalidConfiguration;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per6, macro_kernel<6>, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per5 < 1 || per6 < 1) return cudaErrorInvalidConfiguration;
   *grid = nsm;
   *block = kBlock;
   return cudaSuccess;
@@ -523,7 +648,8 @@ cudaError_t macro_max_grid(int *grid) {
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s) {
   MacroArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel((void *)macro_kernel, dim3(grid), dim3(block), args, 0, s);
+  void *fn = a.nW == 6 ? (void *)macro_kernel<6> : (void *)macro_kernel<5>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s);
 }
 
 }  // namespace gsis
