@@ -79,7 +79,7 @@ struct gsis_solver {
   int *d_colcells = nullptr;
   int ncol0 = 0;
   std::vector<int> colcells;
-  double *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr;
+  double *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr, *m_dF = nullptr;
   int macro_grid = 0, macro_block = 256;
   int kin_warps = 1;
   size_t kin_smem = 0;
@@ -289,11 +289,14 @@ struct gsis_solver {
       m.W = m_W; m.pr = m_pr; m.gW = m_gW; m.phW = m_phW; m.gP = m_gP; m.aux = m_aux; m.R = m_R; m.invD = m_invD;
       m.dW = m_dW; m.Fc = m_Fc; m.corr = m_corr; m.gam = m_gam; m.red = m_red; m.Ffc = m_Ffc;
       m.wfl = m_wfl;
+      m.dF = m_dF;
       m.Wout = d_Wnew;
       m.bar = d_bar;
       m.err = d_err;
       m.iters = d_iters;
       if (opt.macro_steps > 0) {
+        rc = cuda(cudaMemsetAsync(d_bar, 0, MACRO_BAR_WORDS * sizeof(unsigned), stream), "memset");
+        if (rc) return rc;
         rc = cuda(launch_macro(m, macro_grid, macro_block, stream), "synthetic solve");
         if (rc) return rc;
         ++launches;
@@ -622,7 +625,7 @@ static size_t footprint(const gsis_solver *s) {
   b += (size_t)64 * nc * (NMOM + NFF) * 8 / 64 + nc * (NMOM + NFF) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
-  b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 36 + 18 + 3 + 18 + 8) * 8;  // synthetic-solve work
+  b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 36 + 18 + 3 + 18 + 8 + 18) * 8;  // synthetic-solve work
   b += (size_t)s->nslots * 4 * (T + 8) + (size_t)s->nwall * 32 * 8 + 3 * nc * 4 + (1 << 20);
   return b;
 }
@@ -675,7 +678,7 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->d_scratch, 8192 * sizeof(double));
   A(s->d_eps4, 4 * sizeof(double));
   A(s->d_ticket, 4 * sizeof(unsigned));
-  A(s->d_bar, 2 * sizeof(unsigned));
+  A(s->d_bar, MACRO_BAR_WORDS * sizeof(unsigned));
   A(s->d_err, sizeof(int));
   A(s->d_iters, sizeof(int));
   A(s->m_W, nc * 6 * sizeof(double));
@@ -692,6 +695,7 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->m_corr, nc * 6 * sizeof(double));
   A(s->m_gam, nc * 3 * sizeof(double));
   A(s->m_Ffc, nc * 18 * sizeof(double));
+  A(s->m_dF, nc * 18 * sizeof(double));
   A(s->m_wfl, (size_t)(s->nwall + 1) * 6 * sizeof(double));
 #undef A
   if (rc) return rc;
@@ -721,7 +725,6 @@ static int allocate_and_upload(gsis_solver *s) {
   if (!rc) rc = s->upload(s->d_vol, s->vol.data(), nc * sizeof(double));
   if (!rc) rc = s->upload(s->d_colcells, s->colcells.data(), nc * sizeof(int));
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_ticket, 0, 4 * sizeof(unsigned), s->stream), "memset");
-  if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(unsigned), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_rho_w, 0, (s->nwall + 1) * sizeof(double), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_K, 0, nc * 6 * sizeof(double), s->stream), "memset");

@@ -175,11 +175,14 @@ struct MacroArgs {
   const int *colcells;     // red cells (i+j+k even) then black cells
   int ncol0;               // number of red cells
   double *W, *pr, *aux, *gW, *phW, *gP, *R, *invD, *dW, *Fc, *corr, *gam, *red, *Ffc, *wfl;
+  double *dF;              // [cell][3][6] axis-flux increment F(W + dW) - F(W) of the last update
   double *Wout;            // [cell][6] prim W^{n+1}
-  unsigned *bar;           // [2] barrier counter, generation
+  unsigned *bar;           // barrier counter, generation; zero at launch
   int *err;
   int *iters;              // out
 };
+constexpr int MACRO_MAX_GRID = 512;  // blocks of the synthetic-solve kernel at most
+constexpr int MACRO_BAR_WORDS = 512;  // barrier words, cleared before each launch
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s);
 int macro_block_size();
 cudaError_t macro_max_grid(int *grid);

@@ -7,12 +7,13 @@
 // needs are computed once per inner step.  Per inner step:
 //   B  per (cell, field): LSQ gradients, Venkatakrishnan limiters; per cell: time step, diagonal
 //   C  per face: Rusanov convective + NSF viscous flux; wall faces: equilibrium wall flux
-//   E  red / black point-implicit sweeps (Eq. res_macro), one lane per (cell, face).  The first
-//      pass of each colour also sums the cell's face fluxes into the residual R_i
-//      (Eq. delta_Macroscopic_equations); the last one applies the update W += dW, adds to the
-//      inner residual and recomputes the cell's primitives, mu, nu, sound speed, |u_a| + c_s and
-//      axis Euler fluxes (into the second of two flux buffers: the other colour still reads the
-//      fluxes at the start of the step)
+//   E  red / black point-implicit sweeps (Eq. res_macro), one lane per (cell, face).  A cell
+//      updated in a pass evaluates its own axis-flux increments F(W + dW) - F(W) once, for the
+//      other colour's next pass.  The first pass of each colour also sums the cell's face fluxes
+//      into the residual R_i (Eq. delta_Macroscopic_equations); the last one applies the update
+//      W += dW, adds to the inner residual and recomputes the cell's primitives, mu, nu, sound
+//      speed, |u_a| + c_s and axis Euler fluxes (into the second of two flux buffers: the other
+//      colour still reads the fluxes at the start of the step)
 // so ten grid barriers per inner step with the default four sweeps.
 // The high-order terms of Eq. full_constitutive enter through a per-cell frozen correction
 // corr = K - S(W^{n+1/2}), K the kinetic step's sum of outward face fluxes and S this scheme's,
@@ -85,8 +86,9 @@ __device__ __forceinline__ void nat_of(const KinGeom &g, int c, int *v) {
   v[2] = c / (g.n[0] * g.n[1]);
 }
 
+// primitives (rho, u, Tt, Tr) of the conservative state W; returns 1 / rho
 template <int NW>
-__device__ __forceinline__ void prim_of(const double *W, double dr, double *p) {
+__device__ __forceinline__ double prim_of(const double *W, double dr, double *p) {
   const double rho = W[0], ir = 1.0 / rho;
   const double ux = W[1] * ir, uy = W[2] * ir, uz = W[3] * ir;
   const double Er = NW == 6 ? W[5] : 0.0;
@@ -97,6 +99,7 @@ __device__ __forceinline__ void prim_of(const double *W, double dr, double *p) {
   p[3] = uz;
   p[4] = Tt;
   p[5] = NW == 6 ? Er * ir * (4.0 / dr) : Tt;
+  return ir;
 }
 
 __device__ __forceinline__ bool physical(const double *p) { return p[0] > 0.0 && p[4] > 0.0 && p[5] > 0.0; }
@@ -116,7 +119,22 @@ __device__ __forceinline__ void euler_axis(const double *W, int a, double sg, do
   F[5] = Er * un;
 }
 
+// The same flux from W and its primitives p (no division): u_n = u_a, p_t = rho Tt / 2
+template <int NW>
+__device__ __forceinline__ void euler_axis_prim(const double *W, const double *p, int a, double *F) {
+  const double un = pick3(a, p[1], p[2], p[3]);
+  const double pt = 0.5 * p[0] * p[4];
+  F[0] = W[0] * un;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) F[1 + b] = W[1 + b] * un + (b == a ? pt : 0.0);
+  F[4] = (W[4] + pt) * un;
+  F[5] = (NW == 6 ? W[5] : 0.0) * un;
+}
+
 __device__ __forceinline__ double sound(double Tt) { return sqrt(5.0 * Tt / 6.0); }
+
+// T^e for T > 0 as exp(e log T)
+__device__ __forceinline__ double power(double T, double e) { return exp(e * log(T)); }
 
 __device__ __forceinline__ void kappas(const MacroArgs &m, double mu, double *kt, double *kr) {
   if (m.model == 0) {
@@ -165,6 +183,10 @@ __device__ __forceinline__ double cell_volume(const MacroArgs &m, const int *nt)
   return m.ax[0][nt[0]].h * m.ax[1][nt[1]].h * m.ax[2][nt[2]].h;
 }
 
+__device__ __forceinline__ double cell_inv_volume(const MacroArgs &m, const int *nt) {
+  return m.ax[0][nt[0]].invh * m.ax[1][nt[1]].invh * m.ax[2][nt[2]].invh;
+}
+
 __device__ __forceinline__ const AxisCell<double> *axis_cells(const MacroArgs &m, int a) {
   return pick3(a, m.ax[0], m.ax[1], m.ax[2]);
 }
@@ -173,15 +195,15 @@ __device__ __forceinline__ const AxisCell<double> *axis_cells(const MacroArgs &m
 template <int NW>
 __device__ void cell_prims(const MacroArgs &m, int c, const double *W) {
   double p[6];
-  prim_of<NW>(W, m.d_r, p);
+  const double ir = prim_of<NW>(W, m.d_r, p);
   if (!physical(p)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
 #pragma unroll
   for (int k = 0; k < 6; ++k) m.pr[(size_t)c * 6 + k] = p[k];
   double *x = m.aux + (size_t)c * NAUX;
-  const double mu = m.Kn / sqrt(kPi) * pow(p[4], m.omega);
+  const double mu = m.Kn / sqrt(kPi) * power(p[4], m.omega);
   const double cs = sound(p[4]);
   x[0] = mu;
-  x[1] = mu / p[0];
+  x[1] = mu * ir;
   x[2] = cs;
   x[3] = fabs(p[1]) + cs;
   x[4] = fabs(p[2]) + cs;
@@ -191,7 +213,7 @@ __device__ void cell_prims(const MacroArgs &m, int c, const double *W) {
 // B, one item: LSQ gradient of field k (limited conservative field for k < NW, else primitive
 // k - NW + 1) with its Venkatakrishnan limiter, or (k = NW + 5) the local time step and diagonal.
 template <int NW>
-__device__ void gradient_item(const MacroArgs &m, const int *cs, int c, int k) {
+__device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl, int c, int k) {
   const KinGeom &g = m.g;
   int nt[3];
   nat_of(g, c, nt);
@@ -238,7 +260,7 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, int c, int k) {
   }
   // local time step and diagonal D_i = 1/dt_i + (1/2V_i) sum_f Gamma_f A_f (- dQ/dW)
   const double *xi = m.aux + (size_t)c * NAUX;
-  const double V = cell_volume(m, nt);
+  const double V = cell_volume(m, nt), iV = cell_inv_volume(m, nt);
   double lsum = 0.0, gsum = 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -262,14 +284,14 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, int c, int k) {
       gsum += gam * A;
     }
   }
-  const double inv_dt = lsum / (m.cfl * V);
+  const double inv_dt = lsum * iV * inv_cfl;
   double srcdiag = 0.0;
   if (NW == 6) {
     const double *p = m.pr + (size_t)c * 6;
-    const double tau = 2.0 * m.Kn / sqrt(kPi) * pow(p[4], m.omega - 1.0) / p[0];
+    const double tau = 2.0 * m.Kn / sqrt(kPi) * power(p[4], m.omega - 1.0) / p[0];
     srcdiag = 1.0 / (m.Z_r * tau);
   }
-  const double Dt = inv_dt + gsum / (2.0 * V), iD = 1.0 / Dt;
+  const double Dt = inv_dt + gsum * 0.5 * iV, iD = 1.0 / Dt;
 #pragma unroll
   for (int q = 0; q < 5; ++q) m.invD[(size_t)c * 6 + q] = iD;
   m.invD[(size_t)c * 6 + 5] = NW == 6 ? 1.0 / (Dt + srcdiag) : iD;
@@ -312,8 +334,8 @@ __device__ void face_item(const MacroArgs &m, const int *cs, int c, int a) {
     prim_of<NW>(WR, m.d_r, pR);
   }
   double FL[6], FR[6], F[6];
-  euler_axis<NW>(WL, a, 1.0, FL);
-  euler_axis<NW>(WR, a, 1.0, FR);
+  euler_axis_prim<NW>(WL, pL, a, FL);
+  euler_axis_prim<NW>(WR, pR, a, FR);
   const double lam = fmax(fabs(pick3(a, pL[1], pL[2], pL[3])) + sound(pL[4]),
                           fabs(pick3(a, pR[1], pR[2], pR[3])) + sound(pR[4]));
 #pragma unroll
@@ -364,13 +386,12 @@ __device__ void wall_item(const MacroArgs &m, int wf) {
 }
 
 // E, one lane: the face on side sd of axis a of cell c.  With nb_term it adds the face's
-// off-diagonal term (1/2V) A [Delta F_j(n) - Gamma dW_j] to acc, the neighbour state being
-// W_j + dW_j, or W_j alone once the neighbour has been updated in place; in the first pass it
-// puts the face's outward flux into S.
+// off-diagonal term (1/2V) A [Delta F_j(n) - Gamma dW_j] to acc, Delta F_j(n) = sg dF_j along
+// the axis (the neighbour stored F(W_j + dW_j) - F(W_j) when it was updated); in the first pass
+// it puts the face's outward flux into S.
 template <int NW>
-__device__ __forceinline__ void sweep_face(const MacroArgs &m, const double *Fc, const int *cs, int c,
-                                           const int *nt, int a, int sd, bool nb_term, bool nb_updated, bool first,
-                                           double *acc, double *S) {
+__device__ __forceinline__ void sweep_face(const MacroArgs &m, const int *cs, int c, const int *nt, int a, int sd,
+                                           bool nb_term, bool first, double *acc, double *S) {
   const KinGeom &g = m.g;
   const int na = pick3(a, nt[0], nt[1], nt[2]);
   const bool inside = sd ? na < pick3(a, g.n[0], g.n[1], g.n[2]) - 1 : na > 0;
@@ -381,18 +402,9 @@ __device__ __forceinline__ void sweep_face(const MacroArgs &m, const double *Fc,
       const double sg = sd ? 1.0 : -1.0;
       const double gam = m.gam[(size_t)(sd ? c : j) * 3 + a];
       const double half_AoV = 0.5 * axis_cells(m, a)[na].invh;  // A / (2 V) on a rectilinear cell
-      double Wn[6], dWj[6], F1[6];
+      const double *dFj = m.dF + ((size_t)j * 3 + a) * 6;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        dWj[k] = m.dW[(size_t)j * 6 + k];
-        Wn[k] = nb_updated ? m.W[(size_t)j * 6 + k] : m.W[(size_t)j * 6 + k] + dWj[k];
-      }
-      euler_axis<NW>(Wn, a, sg, F1);
-#pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        const double dF = F1[k] - sg * Fc[((size_t)j * 3 + a) * 6 + k];
-        acc[k] = (dF - gam * dWj[k]) * half_AoV;
-      }
+      for (int k = 0; k < NW; ++k) acc[k] = (sg * dFj[k] - gam * m.dW[(size_t)j * 6 + k]) * half_AoV;
     }
     if (first)
 #pragma unroll
@@ -414,6 +426,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   const int nc = g.nc, nact = g.nact;
   const Items it;
   const int cs[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  const double inv_cfl = 1.0 / m.cfl;
   static_assert(kBlock >= 12 * 32, "one warp per reduced field");
   __shared__ double wsum[kBlock / 32][12];
   __shared__ double sdelta;
@@ -444,9 +457,9 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     // axis fluxes at the start of this step, and the buffer for those at its end
     const double *Fc = m.Fc + (size_t)(step & 1) * nc * 18;
     double *Fn = m.Fc + (size_t)((step + 1) & 1) * nc * 18;
-    // ---- B: gradients and limiters per (cell, field); time step and diagonal per cell
-    const int nB = NW + 6;
-    for (int t = it.first; t < nc * nB; t += it.stride) gradient_item<NW>(m, cs, t / nB, t % nB);
+    // ---- B: gradients and limiters per (cell, field); time step and diagonal per cell.  Items
+    // are field-major so the lanes of a warp take the same branch.
+    for (int t = it.first; t < nc * (NW + 6); t += it.stride) gradient_item<NW>(m, cs, inv_cfl, t % nc, t / nc);
     if (!grid_sync(m.bar, m.err)) return;
     // ---- C: interior + faces of the active axes, then the wall faces
     for (int t = it.first; t < nact * nc + m.nwall; t += it.stride) {
@@ -464,9 +477,8 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
       const bool first = sw == 0, last = sw == m.sweeps - 1;
       for (int col = 0; col < 2; ++col) {
         const int off = col ? m.ncol0 : 0, cnt = col ? nc - m.ncol0 : m.ncol0;
-        // in the first red pass every increment is still zero; in the last black pass the red
-        // neighbours hold W + dW already
-        const bool nb_term = !(first && col == 0), nb_updated = last && col == 1;
+        // in the first red pass every increment is still zero
+        const bool nb_term = !(first && col == 0);
         // all lanes of a group loop together so the group shuffles are converged
         const int nitems = (((cnt << lgG) + 31) / 32) * 32;
         for (int t = it.first; t < nitems; t += it.stride) {
@@ -479,7 +491,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
 #pragma unroll
           for (int k = 0; k < NW; ++k) acc[k] = S[k] = 0.0;
           const int a = gl >> 1, sd = gl & 1;
-          if (live && a < nact) sweep_face<NW>(m, Fc, cs, c, nt, a, sd, nb_term, nb_updated, first, acc, S);
+          if (live && a < nact) sweep_face<NW>(m, cs, c, nt, a, sd, nb_term, first, acc, S);
           for (int o = 1; o < G; o <<= 1) {
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
@@ -487,7 +499,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
               if (first) S[k] += __shfl_xor_sync(0xffffffffu, S[k], o, G);
             }
           }
-          double Wnew[6];
+          double Wnew[6] = {0, 0, 0, 0, 0, 0};  // W + dW of the cell, in every lane of the group after the broadcast
           if (live && gl == 0) {
             const double V = cell_volume(m, nt);
             double R[NW];
@@ -497,11 +509,12 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
               if (step == 0)
 #pragma unroll
                 for (int k = 0; k < NW; ++k) cr[k] = m.K[(size_t)c * 6 + k] - S[k];
+              const double iV = cell_inv_volume(m, nt);
 #pragma unroll
-              for (int k = 0; k < NW; ++k) R[k] = -(S[k] + cr[k]) / V;
+              for (int k = 0; k < NW; ++k) R[k] = -(S[k] + cr[k]) * iV;
               if (NW == 6) {
                 const double *p = m.pr + (size_t)c * 6;
-                const double tau = 2.0 * m.Kn / sqrt(kPi) * pow(p[4], m.omega - 1.0) / p[0];
+                const double tau = 2.0 * m.Kn / sqrt(kPi) * power(p[4], m.omega - 1.0) / p[0];
                 const double T = (3.0 * p[4] + m.d_r * p[5]) / (3.0 + m.d_r);
                 R[NW - 1] += m.d_r * p[0] * (T - p[5]) / (4.0 * m.Z_r * tau);
               }
@@ -517,24 +530,34 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
               const double d = (R[k] - acc[k]) * m.invD[(size_t)c * 6 + k];
+              const double w = Wnew[k] + d;
               m.dW[(size_t)c * 6 + k] = d;
+              Wnew[k] = w;
               if (last) {
-                const double w = Wnew[k] + d;
                 if (!isfinite(w)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
-                Wnew[k] = w;
                 m.W[(size_t)c * 6 + k] = w;
                 num[k] += d * d * V;
                 den[k] += w * w * V;
               }
             }
           }
-          if (last) {
-            // the group's odd lanes recompute the axis fluxes of the updated cell, lane 0 the rest
+          // the group's odd lanes evaluate the axis fluxes at W + dW: the increment over the
+          // step's start for the other colour's next pass (none follows the last black pass)
+          // and, in the last sweep, the fluxes of the next step; lane 0 the cell's primitives
 #pragma unroll
-            for (int k = 0; k < 6; ++k) Wnew[k] = __shfl_sync(0xffffffffu, Wnew[k], 0, G);
-            if (live && gl == 0) cell_prims<NW>(m, c, Wnew);
-            if (live && sd == 1 && a < nact) euler_axis<NW>(Wnew, a, 1.0, Fn + ((size_t)c * 3 + a) * 6);
+          for (int k = 0; k < 6; ++k) Wnew[k] = __shfl_sync(0xffffffffu, Wnew[k], 0, G);
+          if (live && sd == 1 && a < nact) {
+            double F[6];
+            euler_axis<NW>(Wnew, a, 1.0, F);
+            const size_t o = ((size_t)c * 3 + a) * 6;
+            if (last)
+#pragma unroll
+              for (int k = 0; k < 6; ++k) Fn[o + k] = F[k];
+            if (!(last && col == 1))
+#pragma unroll
+              for (int k = 0; k < NW; ++k) m.dF[o + k] = F[k] - Fc[o + k];
           }
+          if (last && live && gl == 0) cell_prims<NW>(m, c, Wnew);
         }
         if (last && col == 1) {
           // block partials of the inner residual, double buffered by step
@@ -635,7 +658,7 @@ cudaError_t macro_launch_shape(int nc, int *grid, int *block) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per6, macro_kernel<6>, kBlock, 0);
   if (e != cudaSuccess) return e;
   if (per5 < 1 || per6 < 1) return cudaErrorInvalidConfiguration;
-  *grid = nsm;
+  *grid = nsm < MACRO_MAX_GRID ? nsm : MACRO_MAX_GRID;
   *block = kBlock;
   return cudaSuccess;
 }
