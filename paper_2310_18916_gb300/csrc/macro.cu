@@ -38,31 +38,42 @@ constexpr int kBlock = 512;
 constexpr long long kSpinLimit = 1LL << 31;  // ~1 s of clock64 cycles at 2 GHz
 constexpr int NAUX = 8;                      // mu, nu, c_s, lam_x, lam_y, lam_z
 
-__device__ __forceinline__ unsigned ld_volatile(const unsigned *p) { return *(volatile const unsigned *)p; }
+constexpr int kBarGroups = 8, kBarStride = 32;  // arrival counters, 128 bytes apart
+constexpr int kListCap = 2048;                  // cells per block and last pass evaluated compacted
+static_assert(kBarGroups * kBarStride <= MACRO_BAR_WORDS, "barrier words");
 
-// Sense-reversing grid barrier with a bounded spin.  Returns false when any block has flagged an
-// error (including a time-out here), so every caller leaves the kernel together.
-__device__ bool grid_sync(unsigned *bar, int *err) {
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned x) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
+
+// Grid barrier on kBarGroups monotonic arrival counters, each in its own 128-byte line and zero
+// at launch.  Block b adds 1 to counter b % kBarGroups with release semantics (publishing the
+// block's writes); thread g < kBarGroups of every block waits, with acquire loads, until counter
+// g has reached the barrier's epoch (1, 2, ...) times its group size.  Spreading the arrivals
+// keeps same-address atomics from serialising on one line.  The spin is bounded: on time-out
+// it raises the error flag.  Returns false when any block has flagged an error, so every caller
+// leaves the kernel together.
+__device__ bool grid_sync(unsigned *bar, unsigned &epoch, int *err) {
+  ++epoch;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned gen = ld_volatile(bar + 1);
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (ld_volatile(bar + 1) == gen) {
-        if (clock64() - t0 > kSpinLimit || *(volatile int *)err != 0) {
-          atomicCAS(err, 0, GSIS_ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(20);
+  if (threadIdx.x == 0) red_release_add(bar + kBarStride * (blockIdx.x % kBarGroups), 1u);
+  if (threadIdx.x < kBarGroups) {
+    const unsigned g = threadIdx.x, gsize = (gridDim.x - g + kBarGroups - 1) / kBarGroups;
+    const unsigned target = epoch * gsize;
+    const long long t0 = clock64();
+    for (unsigned i = 0; ld_acquire(bar + kBarStride * g) < target; ++i) {
+      if ((i & 15u) == 15u && (clock64() - t0 > kSpinLimit || *(volatile int *)err != 0)) {
+        atomicCAS(err, 0, GSIS_ERR_TIMEOUT);
+        break;
       }
+      __nanosleep(32);
     }
-    __threadfence();
   }
   __syncthreads();
   return *(volatile int *)err == 0;
@@ -427,9 +438,15 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   const Items it;
   const int cs[3] = {1, g.n[0], g.n[0] * g.n[1]};
   const double inv_cfl = 1.0 / m.cfl;
+  unsigned ep = 0;  // grid barriers passed
   static_assert(kBlock >= 12 * 32, "one warp per reduced field");
   __shared__ double wsum[kBlock / 32][12];
-  __shared__ double sdelta;
+  __shared__ int sdone;
+  // cells this block updated in a last pass, for the compacted evaluation of their primitives
+  // and fluxes (overflow entries are evaluated in place)
+  __shared__ int slist[kListCap];
+  __shared__ int scount;
+  if (threadIdx.x == 0) scount = 0;
 
   // initial conservative state from the moments of f^{n+1/2}, its primitives and axis fluxes
   for (int c = it.first; c < nc; c += it.stride) {
@@ -448,7 +465,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     cell_prims<NW>(m, c, W);
     for (int a = 0; a < nact; ++a) euler_axis<NW>(W, a, 1.0, m.Fc + ((size_t)c * 3 + a) * 6);
   }
-  if (!grid_sync(m.bar, m.err)) return;
+  if (!grid_sync(m.bar, ep, m.err)) return;
 
   const int lgG = 2 * nact <= 2 ? 1 : (2 * nact <= 4 ? 2 : 3);  // lanes per cell in the sweeps: one per face
   const int G = 1 << lgG;
@@ -460,7 +477,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     // ---- B: gradients and limiters per (cell, field); time step and diagonal per cell.  Items
     // are field-major so the lanes of a warp take the same branch.
     for (int t = it.first; t < nc * (NW + 6); t += it.stride) gradient_item<NW>(m, cs, inv_cfl, t % nc, t / nc);
-    if (!grid_sync(m.bar, m.err)) return;
+    if (!grid_sync(m.bar, ep, m.err)) return;
     // ---- C: interior + faces of the active axes, then the wall faces
     for (int t = it.first; t < nact * nc + m.nwall; t += it.stride) {
       if (t >= nact * nc)
@@ -468,7 +485,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
       else
         face_item<NW>(m, cs, t / nact, t % nact);
     }
-    if (!grid_sync(m.bar, m.err)) return;
+    if (!grid_sync(m.bar, ep, m.err)) return;
     // ---- E: red/black point-implicit sweeps, G lanes per cell (one per face)
     double num[NW], den[NW];
 #pragma unroll
@@ -491,6 +508,28 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
 #pragma unroll
           for (int k = 0; k < NW; ++k) acc[k] = S[k] = 0.0;
           const int a = gl >> 1, sd = gl & 1;
+          const bool upd = live && gl == 0, flx = live && sd == 1 && a < nact;
+          // the cell's own data, loaded before the neighbours' so that both are in flight together:
+          // lane 0 (the update) W, the inverse diagonal and R (first pass: K at the first inner
+          // step, else corr); the flux lanes the axis flux at the start of the step
+          double Wc[6], iDc[NW], Rc[NW], Fco[NW];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) Wc[k] = 0.0;
+#pragma unroll
+          for (int k = 0; k < NW; ++k) iDc[k] = Rc[k] = Fco[k] = 0.0;
+          if (upd) {
+            const double *src = first ? (step == 0 ? m.K : m.corr) : m.R;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Wc[k] = m.W[(size_t)c * 6 + k];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+              iDc[k] = m.invD[(size_t)c * 6 + k];
+              Rc[k] = src[(size_t)c * 6 + k];
+            }
+          }
+          if (flx)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) Fco[k] = Fc[((size_t)c * 3 + a) * 6 + k];
           if (live && a < nact) sweep_face<NW>(m, cs, c, nt, a, sd, nb_term, first, acc, S);
           for (int o = 1; o < G; o <<= 1) {
 #pragma unroll
@@ -500,18 +539,20 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
             }
           }
           double Wnew[6] = {0, 0, 0, 0, 0, 0};  // W + dW of the cell, in every lane of the group after the broadcast
-          if (live && gl == 0) {
+          if (upd) {
             const double V = cell_volume(m, nt);
             double R[NW];
             if (first) {
-              // residual R_i = -(S + corr) / V, corr frozen at the first inner step
-              double *cr = m.corr + (size_t)c * 6;
+              // residual R_i = -(S + corr) / V, corr = K - S frozen at the first inner step
               if (step == 0)
 #pragma unroll
-                for (int k = 0; k < NW; ++k) cr[k] = m.K[(size_t)c * 6 + k] - S[k];
+                for (int k = 0; k < NW; ++k) {
+                  Rc[k] -= S[k];
+                  m.corr[(size_t)c * 6 + k] = Rc[k];
+                }
               const double iV = cell_inv_volume(m, nt);
 #pragma unroll
-              for (int k = 0; k < NW; ++k) R[k] = -(S[k] + cr[k]) * iV;
+              for (int k = 0; k < NW; ++k) R[k] = -(S[k] + Rc[k]) * iV;
               if (NW == 6) {
                 const double *p = m.pr + (size_t)c * 6;
                 const double tau = 2.0 * m.Kn / sqrt(kPi) * power(p[4], m.omega - 1.0) / p[0];
@@ -523,13 +564,13 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
                 for (int k = 0; k < NW; ++k) m.R[(size_t)c * 6 + k] = R[k];
             } else {
 #pragma unroll
-              for (int k = 0; k < NW; ++k) R[k] = m.R[(size_t)c * 6 + k];
+              for (int k = 0; k < NW; ++k) R[k] = Rc[k];
             }
 #pragma unroll
-            for (int k = 0; k < 6; ++k) Wnew[k] = m.W[(size_t)c * 6 + k];
+            for (int k = 0; k < 6; ++k) Wnew[k] = Wc[k];
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
-              const double d = (R[k] - acc[k]) * m.invD[(size_t)c * 6 + k];
+              const double d = (R[k] - acc[k]) * iDc[k];
               const double w = Wnew[k] + d;
               m.dW[(size_t)c * 6 + k] = d;
               Wnew[k] = w;
@@ -542,11 +583,22 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
             }
           }
           // the group's odd lanes evaluate the axis fluxes at W + dW: the increment over the
-          // step's start for the other colour's next pass (none follows the last black pass)
-          // and, in the last sweep, the fluxes of the next step; lane 0 the cell's primitives
+          // step's start for the other colour's next pass.  In the last sweep the cell instead
+          // joins the block's list, and its primitives, the fluxes of the next step and the
+          // increment (last red pass) are evaluated after the loop by the block's threads packed
+          // one item per lane.
+          int here = !last;
+          if (last && upd) {
+            const int slot = atomicAdd(&scount, 1);
+            if (slot < kListCap)
+              slist[slot] = c;
+            else
+              here = 1;
+          }
+          here = __shfl_sync(0xffffffffu, here, 0, G);
 #pragma unroll
           for (int k = 0; k < 6; ++k) Wnew[k] = __shfl_sync(0xffffffffu, Wnew[k], 0, G);
-          if (live && sd == 1 && a < nact) {
+          if (flx && here) {
             double F[6];
             euler_axis<NW>(Wnew, a, 1.0, F);
             const size_t o = ((size_t)c * 3 + a) * 6;
@@ -555,9 +607,36 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
               for (int k = 0; k < 6; ++k) Fn[o + k] = F[k];
             if (!(last && col == 1))
 #pragma unroll
-              for (int k = 0; k < NW; ++k) m.dF[o + k] = F[k] - Fc[o + k];
+              for (int k = 0; k < NW; ++k) m.dF[o + k] = F[k] - Fco[k];
           }
-          if (last && live && gl == 0) cell_prims<NW>(m, c, Wnew);
+          if (last && upd && here) cell_prims<NW>(m, c, Wnew);
+        }
+        if (last) {
+          // compacted evaluation for the listed cells: items [0, n) primitives, then (cell, axis)
+          // fluxes; the block's own W writes are visible after the barrier
+          __syncthreads();
+          const int n = min(scount, kListCap);
+          for (int t = threadIdx.x; t < n * (1 + nact); t += blockDim.x) {
+            const int c = slist[t < n ? t : (t - n) / nact];
+            double Wl[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Wl[k] = m.W[(size_t)c * 6 + k];
+            if (t < n) {
+              cell_prims<NW>(m, c, Wl);
+            } else {
+              const int a = (t - n) % nact;
+              double F[6];
+              euler_axis<NW>(Wl, a, 1.0, F);
+              const size_t o = ((size_t)c * 3 + a) * 6;
+#pragma unroll
+              for (int k = 0; k < 6; ++k) Fn[o + k] = F[k];
+              if (col == 0)
+#pragma unroll
+                for (int k = 0; k < NW; ++k) m.dF[o + k] = F[k] - Fc[o + k];
+            }
+          }
+          __syncthreads();
+          if (threadIdx.x == 0) scount = 0;
         }
         if (last && col == 1) {
           // block partials of the inner residual, double buffered by step
@@ -580,7 +659,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
             red[(size_t)blockIdx.x * 16 + threadIdx.x] = v;
           }
         }
-        if (!grid_sync(m.bar, m.err)) return;
+        if (!grid_sync(m.bar, ep, m.err)) return;
       }
     }
     used = step + 1;
@@ -596,17 +675,19 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
       if (lane == 0) wsum[0][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double delta = 0.0;
-      for (int k = 0; k < NW; ++k)
-        if (wsum[0][6 + k] > 0.0) delta = fmax(delta, sqrt(wsum[0][k] / wsum[0][6 + k]));
-      sdelta = delta;
+    // stop when max_k sqrt(num_k / den_k) < tol, tested as num_k < tol^2 den_k
+    if (threadIdx.x < 32) {
+      const int k = threadIdx.x;
+      bool done = m.tol > 0.0;
+      if (k < NW && wsum[0][6 + k] > 0.0) done = done && wsum[0][k] < m.tol * m.tol * wsum[0][6 + k];
+      done = __all_sync(0xffffffffu, done);
+      if (k == 0) sdone = done;
     }
     __syncthreads();
-    if (sdelta < m.tol) break;
+    if (sdone) break;
   }
   // closed domain: rescale the density to the domain's total mass (velocity, temperatures kept)
-  if (!grid_sync(m.bar, m.err)) return;
+  if (!grid_sync(m.bar, ep, m.err)) return;
   double mloc = 0.0;
   for (int c = it.first; c < nc; c += it.stride) {
     int nt[3];
@@ -622,7 +703,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += wsum[w][0];
     red[blockIdx.x] = v;
   }
-  if (!grid_sync(m.bar, m.err)) return;
+  if (!grid_sync(m.bar, ep, m.err)) return;
   __shared__ double sfac;
   if (threadIdx.x < 32) {
     double mm = 0.0;
