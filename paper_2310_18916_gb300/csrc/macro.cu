@@ -7,7 +7,7 @@
 // needs are computed once per inner step.  Per inner step:
 //   B  per (cell, field): LSQ gradients, Venkatakrishnan limiters; per cell: time step, diagonal
 //   C  per face: Rusanov convective + NSF viscous flux; wall faces: equilibrium wall flux
-//   E  red / black point-implicit sweeps (Eq. res_macro), one lane per (cell, face).  A cell
+//   E  red / black point-implicit sweeps (Eq. res_macro), two lanes per cell.  A cell
 //      updated in a pass evaluates its own axis-flux increments F(W + dW) - F(W) once, for the
 //      other colour's next pass.  The first pass of each colour also sums the cell's face fluxes
 //      into the residual R_i (Eq. delta_Macroscopic_equations); the last one applies the update
@@ -396,10 +396,10 @@ __device__ void wall_item(const MacroArgs &m, int wf) {
   for (int k = 0; k < 6; ++k) m.wfl[(size_t)wf * 6 + k] = k < NW ? feq[k] * A : 0.0;
 }
 
-// E, one lane: the face on side sd of axis a of cell c.  With nb_term it adds the face's
-// off-diagonal term (1/2V) A [Delta F_j(n) - Gamma dW_j] to acc, Delta F_j(n) = sg dF_j along
-// the axis (the neighbour stored F(W_j + dW_j) - F(W_j) when it was updated); in the first pass
-// it puts the face's outward flux into S.
+// E, the face on side sd of axis a of cell c.  With nb_term it adds the face's off-diagonal term
+// (1/2V) A [Delta F_j(n) - Gamma dW_j] to acc, Delta F_j(n) = sg dF_j along the axis (the
+// neighbour stored F(W_j + dW_j) - F(W_j) when it was updated); in the first pass it adds the
+// face's outward flux to S.
 template <int NW>
 __device__ __forceinline__ void sweep_face(const MacroArgs &m, const int *cs, int c, const int *nt, int a, int sd,
                                            bool nb_term, bool first, double *acc, double *S) {
@@ -415,17 +415,17 @@ __device__ __forceinline__ void sweep_face(const MacroArgs &m, const int *cs, in
       const double half_AoV = 0.5 * axis_cells(m, a)[na].invh;  // A / (2 V) on a rectilinear cell
       const double *dFj = m.dF + ((size_t)j * 3 + a) * 6;
 #pragma unroll
-      for (int k = 0; k < NW; ++k) acc[k] = (sg * dFj[k] - gam * m.dW[(size_t)j * 6 + k]) * half_AoV;
+      for (int k = 0; k < NW; ++k) acc[k] += (sg * dFj[k] - gam * m.dW[(size_t)j * 6 + k]) * half_AoV;
     }
     if (first)
 #pragma unroll
-      for (int k = 0; k < NW; ++k) S[k] = sd ? m.Ffc[((size_t)c * 3 + a) * 6 + k] : -m.Ffc[((size_t)j * 3 + a) * 6 + k];
+      for (int k = 0; k < NW; ++k) S[k] += sd ? m.Ffc[((size_t)c * 3 + a) * 6 + k] : -m.Ffc[((size_t)j * 3 + a) * 6 + k];
   } else if (first) {
     const int wb = g.wall_base[2 * a + sd];
     if (wb >= 0) {
       const int trn = pick3(a, nt[1] + g.n[1] * nt[2], nt[0] + g.n[0] * nt[2], nt[0] + g.n[0] * nt[1]);
 #pragma unroll
-      for (int k = 0; k < NW; ++k) S[k] = m.wfl[(size_t)(wb + trn) * 6 + k];
+      for (int k = 0; k < NW; ++k) S[k] += m.wfl[(size_t)(wb + trn) * 6 + k];
     }
   }
 }
@@ -467,8 +467,6 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   }
   if (!grid_sync(m.bar, ep, m.err)) return;
 
-  const int lgG = 2 * nact <= 2 ? 1 : (2 * nact <= 4 ? 2 : 3);  // lanes per cell in the sweeps: one per face
-  const int G = 1 << lgG;
   int used = 0;
   for (int step = 0; step < m.steps; ++step) {
     // axis fluxes at the start of this step, and the buffer for those at its end
@@ -486,8 +484,9 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
         face_item<NW>(m, cs, t / nact, t % nact);
     }
     if (!grid_sync(m.bar, ep, m.err)) return;
-    // ---- E: red/black point-implicit sweeps, G lanes per cell (one per face)
-    double num[NW], den[NW];
+    // ---- E: red/black point-implicit sweeps, a pair of lanes per cell: lane sd takes the faces
+    // on side sd of every active axis and the axis fluxes of axes sd, sd + 2
+    double num[NW], den[NW];  // inner residual partials of this thread
 #pragma unroll
     for (int k = 0; k < NW; ++k) num[k] = den[k] = 0.0;
     for (int sw = 0; sw < m.sweeps; ++sw) {
@@ -496,22 +495,17 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
         const int off = col ? m.ncol0 : 0, cnt = col ? nc - m.ncol0 : m.ncol0;
         // in the first red pass every increment is still zero
         const bool nb_term = !(first && col == 0);
-        // all lanes of a group loop together so the group shuffles are converged
-        const int nitems = (((cnt << lgG) + 31) / 32) * 32;
+        // both lanes of a pair loop together so the pair shuffles are converged
+        const int nitems = ((2 * cnt + 31) / 32) * 32;
         for (int t = it.first; t < nitems; t += it.stride) {
-          const int q = t >> lgG, gl = t & (G - 1);
-          const bool live = q < cnt;
+          const int q = t >> 1, sd = t & 1;
+          const bool live = q < cnt, upd = live && sd == 0;
           const int c = live ? m.colcells[off + q] : 0;
           int nt[3];
           nat_of(g, c, nt);
-          double acc[NW], S[NW];
-#pragma unroll
-          for (int k = 0; k < NW; ++k) acc[k] = S[k] = 0.0;
-          const int a = gl >> 1, sd = gl & 1;
-          const bool upd = live && gl == 0, flx = live && sd == 1 && a < nact;
           // the cell's own data, loaded before the neighbours' so that both are in flight together:
           // lane 0 (the update) W, the inverse diagonal and R (first pass: K at the first inner
-          // step, else corr); the flux lanes the axis flux at the start of the step
+          // step, else corr); both lanes the start-of-step flux of axis sd
           double Wc[6], iDc[NW], Rc[NW], Fco[NW];
 #pragma unroll
           for (int k = 0; k < 6; ++k) Wc[k] = 0.0;
@@ -527,20 +521,24 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
               Rc[k] = src[(size_t)c * 6 + k];
             }
           }
-          if (flx)
+          if (live && !last && sd < nact)
 #pragma unroll
-            for (int k = 0; k < NW; ++k) Fco[k] = Fc[((size_t)c * 3 + a) * 6 + k];
-          if (live && a < nact) sweep_face<NW>(m, cs, c, nt, a, sd, nb_term, first, acc, S);
-          for (int o = 1; o < G; o <<= 1) {
+            for (int k = 0; k < NW; ++k) Fco[k] = Fc[((size_t)c * 3 + sd) * 6 + k];
+          double acc[NW], S[NW];
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-              acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o, G);
-              if (first) S[k] += __shfl_xor_sync(0xffffffffu, S[k], o, G);
-            }
+          for (int k = 0; k < NW; ++k) acc[k] = S[k] = 0.0;
+          if (live)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+              if (a < nact) sweep_face<NW>(m, cs, c, nt, a, sd, nb_term, first, acc, S);
+#pragma unroll
+          for (int k = 0; k < NW; ++k) {
+            acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
+            if (first) S[k] += __shfl_xor_sync(0xffffffffu, S[k], 1);
           }
-          double Wnew[6] = {0, 0, 0, 0, 0, 0};  // W + dW of the cell, in every lane of the group after the broadcast
+          double Wnew[6] = {0, 0, 0, 0, 0, 0};  // W + dW of the cell, in both lanes after the broadcast
+          int here = !last;  // evaluate the axis fluxes (last sweep: and primitives) in this loop
           if (upd) {
-            const double V = cell_volume(m, nt);
             double R[NW];
             if (first) {
               // residual R_i = -(S + corr) / V, corr = K - S frozen at the first inner step
@@ -566,54 +564,66 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
 #pragma unroll
               for (int k = 0; k < NW; ++k) R[k] = Rc[k];
             }
+            double d[NW];
 #pragma unroll
             for (int k = 0; k < 6; ++k) Wnew[k] = Wc[k];
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
-              const double d = (R[k] - acc[k]) * iDc[k];
-              const double w = Wnew[k] + d;
-              m.dW[(size_t)c * 6 + k] = d;
-              Wnew[k] = w;
-              if (last) {
-                if (!isfinite(w)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
-                m.W[(size_t)c * 6 + k] = w;
-                num[k] += d * d * V;
-                den[k] += w * w * V;
+              d[k] = (R[k] - acc[k]) * iDc[k];
+              Wnew[k] += d[k];
+              m.dW[(size_t)c * 6 + k] = d[k];
+            }
+            if (last) {
+              // the new state; the cell joins the block's list for the compacted evaluation of
+              // its primitives, its fluxes for the next step, its increment (last red pass) and
+              // its inner-residual terms after the loop, one item per lane
+#pragma unroll
+              for (int k = 0; k < NW; ++k) {
+                if (!isfinite(Wnew[k])) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
+                m.W[(size_t)c * 6 + k] = Wnew[k];
+              }
+              const int slot = atomicAdd(&scount, 1);
+              if (slot < kListCap) {
+                slist[slot] = c;
+              } else {
+                here = 1;
+                const double V = cell_volume(m, nt);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                  num[k] += d[k] * d[k] * V;
+                  den[k] += Wnew[k] * Wnew[k] * V;
+                }
               }
             }
           }
-          // the group's odd lanes evaluate the axis fluxes at W + dW: the increment over the
-          // step's start for the other colour's next pass.  In the last sweep the cell instead
-          // joins the block's list, and its primitives, the fluxes of the next step and the
-          // increment (last red pass) are evaluated after the loop by the block's threads packed
-          // one item per lane.
-          int here = !last;
-          if (last && upd) {
-            const int slot = atomicAdd(&scount, 1);
-            if (slot < kListCap)
-              slist[slot] = c;
-            else
-              here = 1;
+          // both lanes evaluate the axis fluxes at W + dW of their axes: the increment over the
+          // step's start for the other colour's next pass and, in the last sweep when the block's
+          // list is full, the fluxes of the next step
+          here = __shfl_sync(0xffffffffu, here, t & 30u);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) Wnew[k] = __shfl_sync(0xffffffffu, Wnew[k], t & 30u);
+          if (live && here) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int a = sd + 2 * h;
+              if (a >= nact) continue;
+              double F[6];
+              euler_axis<NW>(Wnew, a, 1.0, F);
+              const size_t o = ((size_t)c * 3 + a) * 6;
+              if (last)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) Fn[o + k] = F[k];
+              if (!(last && col == 1))
+#pragma unroll
+                for (int k = 0; k < NW; ++k) m.dF[o + k] = F[k] - (last || h ? Fc[o + k] : Fco[k]);
+            }
+            if (last && upd) cell_prims<NW>(m, c, Wnew);
           }
-          here = __shfl_sync(0xffffffffu, here, 0, G);
-#pragma unroll
-          for (int k = 0; k < 6; ++k) Wnew[k] = __shfl_sync(0xffffffffu, Wnew[k], 0, G);
-          if (flx && here) {
-            double F[6];
-            euler_axis<NW>(Wnew, a, 1.0, F);
-            const size_t o = ((size_t)c * 3 + a) * 6;
-            if (last)
-#pragma unroll
-              for (int k = 0; k < 6; ++k) Fn[o + k] = F[k];
-            if (!(last && col == 1))
-#pragma unroll
-              for (int k = 0; k < NW; ++k) m.dF[o + k] = F[k] - Fco[k];
-          }
-          if (last && upd && here) cell_prims<NW>(m, c, Wnew);
         }
         if (last) {
-          // compacted evaluation for the listed cells: items [0, n) primitives, then (cell, axis)
-          // fluxes; the block's own W writes are visible after the barrier
+          // compacted evaluation for the listed cells: items [0, n) primitives and inner-residual
+          // terms, then (cell, axis) fluxes; the block's own W, dW writes are visible after the
+          // barrier
           __syncthreads();
           const int n = min(scount, kListCap);
           for (int t = threadIdx.x; t < n * (1 + nact); t += blockDim.x) {
@@ -623,6 +633,15 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
             for (int k = 0; k < 6; ++k) Wl[k] = m.W[(size_t)c * 6 + k];
             if (t < n) {
               cell_prims<NW>(m, c, Wl);
+              int nt[3];
+              nat_of(g, c, nt);
+              const double V = cell_volume(m, nt);
+#pragma unroll
+              for (int k = 0; k < NW; ++k) {
+                const double d = m.dW[(size_t)c * 6 + k];
+                num[k] += d * d * V;
+                den[k] += Wl[k] * Wl[k] * V;
+              }
             } else {
               const int a = (t - n) % nact;
               double F[6];
@@ -639,18 +658,27 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
           if (threadIdx.x == 0) scount = 0;
         }
         if (last && col == 1) {
-          // block partials of the inner residual, double buffered by step
+          // block partials of the inner residual, double buffered by step.  Only the threads that
+          // evaluated listed (or overflowing) cells hold nonzero terms: warps without any skip
+          // the FP64 butterfly.
           double *red = m.red + (size_t)(step & 1) * gridDim.x * 16;
           const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+          bool nz = false;
 #pragma unroll
-          for (int k = 0; k < 12; ++k) {
-            const int f = k < 6 ? k : k - 6;
-            double v = 0.0;
+          for (int k = 0; k < NW; ++k) nz = nz || num[k] != 0.0 || den[k] != 0.0;
+          if (__any_sync(0xffffffffu, nz)) {
 #pragma unroll
-            for (int q = 0; q < NW; ++q)
-              if (q == f) v = k < 6 ? num[q] : den[q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) wsum[wid][k] = v;
+            for (int k = 0; k < 12; ++k) {
+              const int f = k < 6 ? k : k - 6;
+              double v = 0.0;
+#pragma unroll
+              for (int q = 0; q < NW; ++q)
+                if (q == f) v = k < 6 ? num[q] : den[q];
+              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+              if (lane == 0) wsum[wid][k] = v;
+            }
+          } else if (lane < 12) {
+            wsum[wid][lane] = 0.0;
           }
           __syncthreads();
           if (threadIdx.x < 12) {
