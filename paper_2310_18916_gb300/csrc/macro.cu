@@ -100,7 +100,7 @@ __device__ __forceinline__ void nat_of(const KinGeom &g, int c, int *v) {
 // primitives (rho, u, Tt, Tr) of the conservative state W; returns 1 / rho
 template <int NW>
 __device__ __forceinline__ double prim_of(const double *W, double dr, double *p) {
-  const double rho = W[0], ir = 1.0 / rho;
+  const double rho = W[0], ir = __drcp_rn(rho);  // = 1.0 / rho, correctly rounded
   const double ux = W[1] * ir, uy = W[2] * ir, uz = W[3] * ir;
   const double Er = NW == 6 ? W[5] : 0.0;
   const double Tt = (W[4] - 0.5 * rho * (ux * ux + uy * uy + uz * uz) - Er) * (ir * (4.0 / 3.0));
@@ -118,7 +118,7 @@ __device__ __forceinline__ bool physical(const double *p) { return p[0] > 0.0 &&
 // Euler flux along n = sg e_a: (rho u_n, rho u u_n + p_t n, (rho E + p_t) u_n, rho E_r u_n)
 template <int NW>
 __device__ __forceinline__ void euler_axis(const double *W, int a, double sg, double *F) {
-  const double ir = 1.0 / W[0];
+  const double ir = __drcp_rn(W[0]);
   const double un = sg * pick3(a, W[1], W[2], W[3]) * ir;
   const double Er = NW == 6 ? W[5] : 0.0;
   // p_t = rho Tt / 2 = (2/3) (rho E - |rho u|^2 / (2 rho) - rho E_r)
@@ -302,7 +302,7 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl,
     const double tau = 2.0 * m.Kn / sqrt(kPi) * power(p[4], m.omega - 1.0) / p[0];
     srcdiag = 1.0 / (m.Z_r * tau);
   }
-  const double Dt = inv_dt + gsum * 0.5 * iV, iD = 1.0 / Dt;
+  const double Dt = inv_dt + gsum * 0.5 * iV, iD = __drcp_rn(Dt);
 #pragma unroll
   for (int q = 0; q < 5; ++q) m.invD[(size_t)c * 6 + q] = iD;
   m.invD[(size_t)c * 6 + 5] = NW == 6 ? 1.0 / (Dt + srcdiag) : iD;
@@ -410,12 +410,14 @@ __device__ __forceinline__ void sweep_face(const MacroArgs &m, const int *cs, in
     const int csa = pick3(a, cs[0], cs[1], cs[2]);
     const int j = sd ? c + csa : c - csa;
     if (nb_term) {
-      const double sg = sd ? 1.0 : -1.0;
       const double gam = m.gam[(size_t)(sd ? c : j) * 3 + a];
       const double half_AoV = 0.5 * axis_cells(m, a)[na].invh;  // A / (2 V) on a rectilinear cell
       const double *dFj = m.dF + ((size_t)j * 3 + a) * 6;
 #pragma unroll
-      for (int k = 0; k < NW; ++k) acc[k] += (sg * dFj[k] - gam * m.dW[(size_t)j * 6 + k]) * half_AoV;
+      for (int k = 0; k < NW; ++k) {
+        const double df = sd ? dFj[k] : -dFj[k];  // Delta F_j(n) = sg dF_j, sg = +-1
+        acc[k] = fma(fma(-gam, m.dW[(size_t)j * 6 + k], df), half_AoV, acc[k]);
+      }
     }
     if (first)
 #pragma unroll
