@@ -365,12 +365,13 @@ __global__ void wall_constants_kernel(const double *vel64, int nslots, const dou
   const double dir = (side & 1) ? 1.0 : -1.0;
   const double *uT = wall_uT + 4 * side;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  const double norm = pow(3.14159265358979323846 * uT[3], -1.5);
   for (int v = threadIdx.x; v < nslots; v += blockDim.x) {
     const double x = vel64[4 * v], y = vel64[4 * v + 1], z = vel64[4 * v + 2], w = vel64[4 * v + 3];
     const double xa = a == 0 ? x : (a == 1 ? y : z);
     if (!(w > 0.0) || !(xa * dir < 0.0)) continue;
     const double cx = x - uT[0], cy = y - uT[1], cz = z - uT[2];
-    const double M = pow(3.14159265358979323846 * uT[3], -1.5) * exp(-(cx * cx + cy * cy + cz * cz) / uT[3]);
+    const double M = norm * exp(-(cx * cx + cy * cy + cz * cz) / uT[3]);
     const double fl = w * xa * M;
     acc[0] += w * fabs(xa) * M;
     acc[1] += fl;
@@ -525,24 +526,30 @@ cudaError_t launch_moments(const KinArgs<T> &a, int blocks_per_chunk, int nchunk
 __device__ __forceinline__ float accurate_exp(float x) { return expf(x); }
 __device__ __forceinline__ double accurate_exp(double x) { return exp(x); }
 
+// One warp per cell: the per-cell factors once (FP64 is scarce on this GPU), then every
+// velocity block of the cell, one 128-byte line per block.
 template <typename T>
 __global__ void init_maxwellian_kernel(const KinArgs<T> A, const double *W0) {
   const KinGeom &G = A.g;
-  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
-  const T x = vp[0], y = vp[1], z = vp[2];
-  T *F = A.f + (size_t)b * G.nc * VB;
-  for (int cell = warp; cell < G.nc; cell += nw) {
-    const double *w0 = W0 + 6 * (size_t)cell;
-    const T C = (T)(w0[0] * pow(3.14159265358979323846 * w0[4], -1.5)), invT = (T)(1.0 / w0[4]);
-    const T cx = x - (T)w0[1], cy = y - (T)w0[2], cz = z - (T)w0[3];
-    F[(size_t)cell * VB + lane] = C * accurate_exp(-(cx * cx + cy * cy + cz * cz) * invT);
+  const int lane = threadIdx.x & 31;
+  const int cell = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (cell >= G.nc) return;
+  const double *w0 = W0 + 6 * (size_t)cell;
+  const T C = (T)(w0[0] * pow(3.14159265358979323846 * w0[4], -1.5)), invT = (T)(1.0 / w0[4]);
+  const T ux = (T)w0[1], uy = (T)w0[2], uz = (T)w0[3];
+  for (int b = 0; b < A.nblocks; ++b) {
+    const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
+    const T cx = vp[0] - ux, cy = vp[1] - uy, cz = vp[2] - uz;
+    A.f[((size_t)b * G.nc + cell) * VB + lane] = C * accurate_exp(-(cx * cx + cy * cy + cz * cz) * invT);
   }
 }
 
 template <typename T>
 cudaError_t launch_init_maxwellian(const KinArgs<T> &a, const double *W0, int nblocks, cudaStream_t s) {
-  init_maxwellian_kernel<T><<<nblocks, 256, 0, s>>>(a, W0);
+  (void)nblocks;
+  const int threads = 256;
+  const size_t grid = ((size_t)a.g.nc * 32 + threads - 1) / threads;
+  init_maxwellian_kernel<T><<<(unsigned)grid, threads, 0, s>>>(a, W0);
   return cudaGetLastError();
 }
 
