@@ -153,6 +153,19 @@ int gsis_residual(gsis_handle h, double *eps_by_field, int n);
 int gsis_nwall(gsis_handle h);
 int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, double *flux6);
 
+/* Wall loads (drag and heat-flux coefficients, a10) from the kinetic wall fluxes of the last
+ * kinetic step, summed over the wall faces of the sides selected by side_mask (bit s = side s:
+ * 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z).  Writes 6 host doubles to out6:
+ *   out6[0..2] force on the walls = sum of the outward (gas -> wall) momentum fluxes,
+ *   out6[3]    energy flux into the walls,
+ *   out6[4]    C_D = (force . dir) / (1/2 rho_ref U_ref^2 A_ref),
+ *   out6[5]    C_H = energy flux / (1/2 rho_ref U_ref^3 A_ref),
+ * in the solver's units (lengths of the mesh, velocities in sqrt(2RT0), density rho0).
+ * dir: 3 host doubles, the reference direction (not normalised by the call).  rho_ref, U_ref,
+ * A_ref > 0, else GSIS_E_INVALID.  Synchronises the solver's stream. */
+int gsis_wall_loads(gsis_handle h, unsigned side_mask, const double *dir, double rho_ref, double U_ref, double A_ref,
+                    double *out6);
+
 /* Per cell the sum over its faces of the outward kinetic face flux of the last kinetic step
  * (mass, momentum(3), energy, internal energy; area-integrated): the kinetic information the
  * synthetic solve uses (Eq. full_constitutive evaluated with the kinetic scheme's own fluxes).

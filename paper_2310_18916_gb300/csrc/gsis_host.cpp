@@ -908,6 +908,32 @@ extern "C" int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, dou
   return GSIS_OK;
 }
 
+extern "C" int gsis_wall_loads(gsis_handle h, unsigned side_mask, const double *dir, double rho_ref, double U_ref,
+                               double A_ref, double *out6) {
+  if (!h || !dir || !out6) return GSIS_E_INVALID;
+  if (!(rho_ref > 0.0) || !(U_ref > 0.0) || !(A_ref > 0.0) || (side_mask & ~63u) != 0)
+    return h->fail(GSIS_E_INVALID, "wall loads need rho_ref, U_ref, A_ref > 0 and a 6-bit side mask");
+  WallLoadArgs a{};
+  a.wf = h->d_wf;
+  a.wall_cell = h->d_wall_cell;
+  a.wall_side = h->d_wall_side;
+  a.nwall = h->nwall;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = h->n[d];
+    a.ax[d] = h->d_ax64[d];
+    a.dir[d] = dir[d];
+  }
+  a.mask = side_mask;
+  a.rho_ref = rho_ref;
+  a.U_ref = U_ref;
+  a.A_ref = A_ref;
+  a.out = h->d_scratch;
+  int rc = h->cuda(launch_wall_loads(a, h->stream), "wall loads");
+  if (!rc) rc = h->cuda(cudaMemcpyAsync(out6, h->d_scratch, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "out");
+  if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  return rc;
+}
+
 extern "C" int gsis_kinetic_flux_sum(gsis_handle h, double *out, size_t out_len) {
   if (!h || !out) return GSIS_E_INVALID;
   const size_t nc = h->nc;

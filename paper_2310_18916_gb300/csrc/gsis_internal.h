@@ -158,6 +158,18 @@ struct EpsArgs {
 };
 cudaError_t launch_eps(const EpsArgs &a, cudaStream_t s);
 
+struct WallLoadArgs {
+  const double *wf;            // [wall face][6] kinetic wall flux per unit area (outward)
+  const int *wall_cell, *wall_side;
+  int nwall;
+  int n[3];
+  const AxisCell<double> *ax[3];
+  unsigned mask;               // bit s selects wall side s
+  double dir[3], rho_ref, U_ref, A_ref;
+  double *out;                 // [6] force(3), energy flux, C_D, C_H
+};
+cudaError_t launch_wall_loads(const WallLoadArgs &a, cudaStream_t s);
+
 struct MacroArgs {
   KinGeom g;
   const AxisCell<double> *ax[3];

@@ -324,4 +324,43 @@ cudaError_t launch_eps(const EpsArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Wall loads (a10): sums over the wall faces of the selected sides of the kinetic wall flux of
+// the last kinetic step (per unit area in wf, times the face area): force on the walls
+// (outward momentum flux), energy flux into the walls, and the coefficients
+// C_D = F.dir / (1/2 rho U^2 A), C_H = Q / (1/2 rho U^3 A).  One block; each thread sums a fixed
+// strided subset, then a fixed-order tree, so the result does not depend on timing.
+__global__ void wall_loads_kernel(WallLoadArgs a) {
+  constexpr int NT = 256;
+  __shared__ double red[4][NT];
+  double acc[4] = {0, 0, 0, 0};
+  for (int w = threadIdx.x; w < a.nwall; w += NT) {
+    const int side = a.wall_side[w];
+    if (!((a.mask >> side) & 1u)) continue;
+    const int c = a.wall_cell[w], ax = side / 2;
+    const int nat[3] = {c % a.n[0], (c / a.n[0]) % a.n[1], c / (a.n[0] * a.n[1])};
+    const double area = a.ax[0][nat[0]].h * a.ax[1][nat[1]].h * a.ax[2][nat[2]].h * a.ax[ax][nat[ax]].invh;
+    for (int k = 0; k < 4; ++k) acc[k] += a.wf[(size_t)w * 6 + 1 + k] * area;
+  }
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int o = NT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double F[3] = {red[0][0], red[1][0], red[2][0]}, Q = red[3][0];
+    for (int k = 0; k < 3; ++k) a.out[k] = F[k];
+    a.out[3] = Q;
+    a.out[4] = (F[0] * a.dir[0] + F[1] * a.dir[1] + F[2] * a.dir[2]) / (0.5 * a.rho_ref * a.U_ref * a.U_ref * a.A_ref);
+    a.out[5] = Q / (0.5 * a.rho_ref * a.U_ref * a.U_ref * a.U_ref * a.A_ref);
+  }
+}
+
+cudaError_t launch_wall_loads(const WallLoadArgs &a, cudaStream_t s) {
+  wall_loads_kernel<<<1, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace gsis

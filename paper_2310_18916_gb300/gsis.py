@@ -50,7 +50,7 @@ class Options(C.Structure):
 
 _lib = None
 SYMBOLS = ("gsis_default_options", "gsis_footprint_bytes", "gsis_create", "gsis_iterate", "gsis_moments",
-           "gsis_residual", "gsis_nwall", "gsis_wall", "gsis_kinetic_flux_sum", "gsis_get_f", "gsis_set_f", "gsis_stats",
+           "gsis_residual", "gsis_nwall", "gsis_wall", "gsis_wall_loads", "gsis_kinetic_flux_sum", "gsis_get_f", "gsis_set_f", "gsis_stats",
            "gsis_destroy", "gsis_last_error", "gsis_profile", "gsis_vdf_moments_noalloc")
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     L.gsis_residual.argtypes = [P, D, C.c_int]
     L.gsis_nwall.argtypes = [P]
     L.gsis_wall.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), D, D]
+    L.gsis_wall_loads.argtypes = [P, C.c_uint, D, C.c_double, C.c_double, C.c_double, D]
     L.gsis_kinetic_flux_sum.argtypes = [P, D, C.c_size_t]
     L.gsis_get_f.argtypes = [P, D, D]
     L.gsis_set_f.argtypes = [P, D, D]
@@ -232,6 +233,16 @@ class Solver:
         self._check(load().gsis_wall(self.h, cell.ctypes.data_as(C.POINTER(C.c_int)),
                                      side.ctypes.data_as(C.POINTER(C.c_int)), _p(rw), _p(fl)))
         return cell, side, rw, fl
+
+    def wall_loads(self, sides, direction, rho_ref, U_ref, A_ref):
+        """Force (3), energy flux, C_D, C_H on the walls of the given sides (0 -x .. 5 +z)."""
+        mask = 0
+        for sd in sides:
+            mask |= 1 << int(sd)
+        d = np.ascontiguousarray(direction, dtype=np.float64)
+        out = np.empty(6)
+        self._check(load().gsis_wall_loads(self.h, mask, _p(d), float(rho_ref), float(U_ref), float(A_ref), _p(out)))
+        return out
 
     def kinetic_flux_sum(self):
         out = np.empty((self.nc, 6))

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from gpu_common import pair, scaled_close
+from paper_2310_18916_gb300 import gsis
 from paper_2310_18916_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -77,3 +78,29 @@ def test_cavity_fp32_per_iteration(mode):
         scaled_close(hg[:, :12], ho[:, :12], 2e-5, f"half moments, step {it}")
         scaled_close(hg[:, 12:15], ho[:, 12:15], 2e-4, f"heat flux, step {it}", vector=True)
         scaled_close(g.W(), o.W(), 2e-5, f"W, step {it}")
+
+
+def test_wall_loads_match_oracle_wall_fluxes():
+    """a10: force, energy flux and the drag / heat-flux coefficients on chosen walls, from the
+    kinetic wall fluxes of the last step, against the same sums of the oracle's per-face wall
+    fluxes (FP64 path, three GSIS steps)."""
+    p = wl.cavity(n=12, nv=16, Kn=0.1, lid=0.16)
+    g, o = pair(p, "f64", "gsis", macro_steps=50)
+    for _ in range(3):
+        g.step()
+        o.step()
+    _, side, _, fl = o.wall()
+    rho, U, A = 1.0, 0.16, 1.0
+    for sides, d in (([3], (1.0, 0.0, 0.0)), ([0, 1, 2, 3], (0.0, 1.0, 0.0)), ([2], (0.6, 0.8, 0.0))):
+        sel = np.isin(side, sides)
+        F = fl[sel, 1:4].sum(axis=0)
+        Q = fl[sel, 4].sum()
+        ref = np.array([F[0], F[1], F[2], Q, F @ np.array(d) / (0.5 * rho * U ** 2 * A), Q / (0.5 * rho * U ** 3 * A)])
+        out = g.wall_loads(sides, d, rho, U, A)
+        fs = np.abs(F).max()
+        scale = np.array([fs, fs, fs, max(abs(Q), fs * U), fs / (0.5 * rho * U ** 2 * A),
+                          max(abs(Q), fs * U) / (0.5 * rho * U ** 3 * A)])
+        err = np.abs(out - ref) / scale
+        assert err.max() < 1e-10, f"sides {sides}: {err}"
+    with pytest.raises(gsis.GsisError):
+        g.wall_loads([3], (1.0, 0.0, 0.0), 0.0, U, A)

@@ -73,6 +73,35 @@ def test_free_molecular_couette_discrete_closed_form():
     assert T == pytest.approx(1 + 2 * U ** 2 / 3, rel=1e-6)
 
 
+def test_free_molecular_couette_wall_loads():
+    """Wall loads (a10) from the oracle's kinetic wall fluxes: with Kn -> inf the momentum flux
+    is the same on every plane x = const, so the outward y-momentum flux through each wall face
+    per unit area is +P_xy at x = 1 and -P_xy at x = 0 (P_xy the discrete sum of the test above),
+    and the wall faces carry no net mass flux."""
+    U = 0.2
+    p = wl.couette(n_cells=8, nv=24, Kn=1e7, U=U)
+    o = Oracle(p, mode=1)
+    converge(o, 1e-13, 60)
+    x, y, z, w = _disc(p)
+    m0 = w @ _m(x, y, z, (0, 0, 0), 1.0)
+    ML, MR = _m(x, y, z, (0, -U, 0), 1.0), _m(x, y, z, (0, U, 0), 1.0)
+    shape = np.where(x > 0, ML, MR)
+    f = m0 / (w @ shape) * shape
+    Pxy = w @ (x * y * f)  # u_x = 0 and the mean u_y is 0 by symmetry
+    Efx = w @ (x * 0.5 * (x ** 2 + y ** 2 + z ** 2) * f)
+    cell, side, rho_w, flux = o.wall()
+    vol, xc, S, xf = o.geometry()
+    area = np.array([np.linalg.norm(S[c, sd]) for c, sd in zip(cell, side)])
+    per_area = flux / area[:, None]
+    sign = np.where(side == 1, 1.0, -1.0)
+    np.testing.assert_allclose(per_area[:, 2], sign * Pxy, rtol=2e-6)
+    np.testing.assert_allclose(per_area[:, 4], sign * Efx, rtol=2e-6, atol=1e-9)
+    assert np.abs(per_area[:, 0]).max() < 1e-9
+    # drag coefficient of the moving wall at x = 1 along +y: C_D = 2 P_xy / (rho U^2) -> -2/(U sqrt(pi))
+    cd = 2 * flux[side == 1, 2].sum() / area[side == 1].sum() / (m0 * U ** 2)
+    assert cd == pytest.approx(-2 / (U * math.sqrt(math.pi)), rel=0.02)
+
+
 def test_free_molecular_fourier_heat_flux():
     """Plates at rest at T1 and T2: half-range Maxwellians with zero net mass flux.
     Continuum: q_x = rho sqrt(T1 T2) (T1 - T2) / (sqrt(pi) (sqrt(T1) + sqrt(T2)))."""
