@@ -167,7 +167,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16"],
+                    help="VDF storage (kinetic arithmetic is FP32 for f32 and bf16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=CFG["n"], help="cells per side (profiling cases use 64)")
     ap.add_argument("--nv", type=int, default=CFG["nv"], help="velocities per axis")
@@ -246,7 +247,7 @@ def main():
             dist.destroy_process_group()
         return 0
     peak, peak_kind, sm_mhz = measured_peaks()
-    sbytes = 4 if args.precision == "f32" else 8
+    sbytes = {"f32": 4, "f64": 8, "bf16": 2}[args.precision]
     alg_bytes = 2 * sbytes * pts
     achieved = alg_bytes / (kin_ms / 1e3) / 1e9
     macro_ms = phase[3] / max(nsteps, 1)
@@ -258,7 +259,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
         "config": {"workload": workload_name(), "precision": f"{args.precision} VDF, f64 synthetic solve",
                    "cells": p.ncells, "velocities": p.nvel, "points": pts, "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": f"inputs larger than L2 (VDF {vdf_gb:.2f} GB)" if vdf_gb > 0.129 else

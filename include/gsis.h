@@ -44,7 +44,7 @@ extern "C" {
 
 enum gsis_bc_type { GSIS_BC_WALL = 1, GSIS_BC_PERIODIC = 2 };
 enum gsis_model { GSIS_SHAKHOV = 0, GSIS_RYKOV = 1 };
-enum gsis_precision { GSIS_F64 = 0, GSIS_F32 = 1 };
+enum gsis_precision { GSIS_F64 = 0, GSIS_F32 = 1, GSIS_BF16 = 2 };
 enum gsis_mode { GSIS_MODE_GSIS = 0, GSIS_MODE_DVM = 1 };
 
 /* Structured hexahedral block (spatial finite-volume cells of Section 3.1).
@@ -89,8 +89,11 @@ typedef void (*gsis_free_fn)(void *ptr, void *stream, void *ctx);
 
 /* Solver options.  Defaults (gsis_default_options): see the comments. */
 typedef struct {
-  int precision;        /* GSIS_F64 | GSIS_F32: VDF storage and kinetic arithmetic (default F32).
-                           Moments, synthetic solve, correction and residual are FP64 always. */
+  int precision;        /* VDF storage / kinetic arithmetic (default F32): GSIS_F64 (FP64 / FP64),
+                           GSIS_F32 (FP32 / FP32), GSIS_BF16 (BF16, rounded to nearest even on
+                           store / FP32).  FP32 and BF16 accumulate moments in FP32 with
+                           compensated sums.  The synthetic solve, the correction state and the
+                           residual are FP64 always. */
   int mode;             /* GSIS_MODE_GSIS (default) or GSIS_MODE_DVM (plain kinetic iteration) */
   int n_sweeps;         /* colour-ordered point-implicit passes per kinetic step (default 1) */
   int macro_steps;      /* inner synthetic steps per outer step (default 300, Algorithm 1) */

@@ -4,6 +4,7 @@
 // wall tables, owns every device buffer, and sequences one outer iteration of Algorithm 1:
 //   wall pre-pass -> fused kinetic step -> block reduction -> moments (+ closed-domain mass
 //   scale) -> [GSIS: FP64 synthetic solve] -> eps -> state of the next step.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +17,13 @@
 
 #include "../../include/gsis.h"
 #include "gsis_internal.h"
+
+// Evaluates EXPR with T (kinetic arithmetic) and S (VDF storage) bound to the types of the
+// precision PREC: F64 -> double/double, F32 -> float/float, BF16 -> float/__nv_bfloat16.
+#define GSIS_DISPATCH(PREC, EXPR)                                                          \
+  ((PREC) == GSIS_F64    ? [&] { using T = double; using S = double; return EXPR; }()        \
+   : (PREC) == GSIS_BF16 ? [&] { using T = float; using S = __nv_bfloat16; return EXPR; }()  \
+                         : [&] { using T = float; using S = float; return EXPR; }())
 
 using namespace gsis;
 
@@ -145,9 +153,9 @@ struct gsis_solver {
     return cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "upload");
   }
 
-  template <typename T>
-  KinArgs<T> kin_args() const {
-    KinArgs<T> a{};
+  template <typename T, typename S = T>
+  KinArgs<T, S> kin_args() const {
+    KinArgs<T, S> a{};
     a.g = kg;
     for (int d = 0; d < 3; ++d) a.ax[d] = static_cast<const AxisCell<T> *>(d_ax[d]);
     a.vel = static_cast<const T *>(d_vel);
@@ -160,7 +168,7 @@ struct gsis_solver {
     a.st = static_cast<const T *>(d_stT);
     a.rho_w = d_rho_w;
     a.wall_uT = d_wall_uT;
-    a.f = static_cast<T *>(d_f);
+    a.f = static_cast<S *>(d_f);
     a.wpart = static_cast<T *>(d_wpart);
     a.nwall = nwall;
     a.nblocks = nblocks;
@@ -181,9 +189,9 @@ struct gsis_solver {
 
   // moments of the stored f -> Mh (about the state velocity st64[0..2]), the kinetic flux sum K
   // and the wall fluxes
-  template <typename T>
+  template <typename T, typename S>
   int reduce_and_finalize(bool closed_scale) {
-    int rc = cuda(launch_moments<T>(kin_args<T>(), mom_bpc, mom_nchunks, d_mp, stream), "moments");
+    int rc = cuda(launch_moments<T, S>(kin_args<T, S>(), mom_bpc, mom_nchunks, d_mp, stream), "moments");
     if (rc) return rc;
     rc = cuda(launch_reduce<T>(d_mp, mom_nchunks, static_cast<const T *>(d_wpart), d_boct, nblocks, kg, d_wall_cell,
                                d_wall_side, nwall, d_rho_w, d_Zw, d_vol, d_st64, d_mom, d_K, d_wf, stream),
@@ -215,20 +223,33 @@ struct gsis_solver {
     sa.kin_inv_dt = opt.kin_inv_dt;
     sa.st64 = d_st64;
     sa.stT = d_stT;
-    sa.is_float = prec == GSIS_F32;
+    sa.is_float = prec != GSIS_F64;
     return cuda(launch_state(sa, stream), "state");
   }
 
-  // state <- moments of the current f (after init or set_f); also sets mass_ref
-  template <typename T>
-  int state_from_f() {
-    // neutral state: corrected f = f_raw, moments about u = 0
+  // state <- moments of the current f (after init or set_f); also sets mass_ref.  W0: the
+  // initial state when f was just initialised to its Maxwellian (BF16 storage holds f relative
+  // to it), else nullptr.
+  template <typename T, typename S>
+  int state_from_f(const double *W0 = nullptr) {
+    // neutral state: corrected f = f_raw, moments about u = 0; with relative storage after
+    // initialisation, f_raw = M(W0) is formed from the state's W^n Maxwellian slot
     std::vector<double> st0((size_t)nc * NST, 0.0);
     for (int c = 0; c < nc; ++c) st0[(size_t)c * NST + 10] = 1.0;
+    if (W0 && prec == GSIS_BF16)
+      for (int c = 0; c < nc; ++c) {
+        const double *w = W0 + (size_t)c * 6;
+        double *st = st0.data() + (size_t)c * NST;
+        st[0] = w[1];
+        st[1] = w[2];
+        st[2] = w[3];
+        st[3] = 1.0 / w[4];
+        st[4] = w[0] * std::pow(3.14159265358979323846 * w[4], -1.5);
+      }
     std::vector<T> st0T(st0.begin(), st0.end());
     int rc = upload(d_st64, st0.data(), st0.size() * sizeof(double));
     if (!rc) rc = upload(d_stT, st0T.data(), st0T.size() * sizeof(T));
-    if (!rc) rc = reduce_and_finalize<T>(false);
+    if (!rc) rc = reduce_and_finalize<T, S>(false);
     if (rc) return rc;
     double m2[2];
     rc = cuda(cudaMemcpyAsync(m2, d_mass, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream), "mass");
@@ -245,19 +266,19 @@ struct gsis_solver {
     return rc;
   }
 
-  template <typename T>
+  template <typename T, typename S>
   int step_impl(int mode) {
     int launches = 0;
     mark(0);
-    int rc = cuda(launch_wall_prepass<T>(kin_args<T>(), d_wall_cell, d_wall_side, nwall, d_Z0, d_rho_w, nslots, stream),
+    int rc = cuda(launch_wall_prepass<T, S>(kin_args<T, S>(), d_wall_cell, d_wall_side, nwall, d_Z0, d_rho_w, nslots, stream),
                   "wall pre-pass");
     if (rc) return rc;
     launches += nwall > 0;
     mark(1);
-    rc = cuda(launch_kinetic<T>(kin_args<T>(), nblocks, kin_warps, kin_smem, stream), "kinetic");
+    rc = cuda(launch_kinetic<T, S>(kin_args<T, S>(), nblocks, kin_warps, kin_smem, stream), "kinetic");
     if (rc) return rc;
     mark(2);
-    rc = reduce_and_finalize<T>(true);
+    rc = reduce_and_finalize<T, S>(true);
     if (rc) return rc;
     launches += 1 + 1 + (nwall > 0) + 2;
     mark(3);
@@ -348,7 +369,7 @@ struct gsis_solver {
     return GSIS_OK;
   }
 
-  int step(int mode) { return prec == GSIS_F32 ? step_impl<float>(mode) : step_impl<double>(mode); }
+  int step(int mode) { return GSIS_DISPATCH(prec, (step_impl<T, S>(mode))); }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -380,7 +401,10 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     if (vg->n[d] < 1 || !vg->x[d] || !vg->w[d]) { why = "bad velocity grid"; return GSIS_E_INVALID; }
   if (!(Kn > 0)) { why = "Kn must be positive"; return GSIS_E_INVALID; }
   if (!(o->venkat_K > 0)) { why = "venkat_K must be positive"; return GSIS_E_INVALID; }
-  if (o->precision != GSIS_F32 && o->precision != GSIS_F64) { why = "bad precision"; return GSIS_E_INVALID; }
+  if (o->precision != GSIS_F32 && o->precision != GSIS_F64 && o->precision != GSIS_BF16) {
+    why = "bad precision";
+    return GSIS_E_INVALID;
+  }
   if (o->mode != GSIS_MODE_GSIS && o->mode != GSIS_MODE_DVM) { why = "bad mode"; return GSIS_E_INVALID; }
   if (g->model == GSIS_RYKOV) { why = "Rykov model is not implemented on the GPU yet"; return GSIS_E_UNSUPPORTED; }
   if (g->model != GSIS_SHAKHOV) { why = "bad model"; return GSIS_E_INVALID; }
@@ -617,10 +641,11 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
 }
 
 static size_t footprint(const gsis_solver *s) {
-  const size_t T = s->prec == GSIS_F32 ? 4 : 8;
+  const size_t T = s->prec == GSIS_F64 ? 8 : 4;                             // kinetic arithmetic
+  const size_t Sb = s->prec == GSIS_F64 ? 8 : (s->prec == GSIS_BF16 ? 2 : 4);  // VDF storage
   const size_t nc = s->nc;
   size_t b = 0;
-  b += (size_t)s->nslots * nc * T;            // f
+  b += (size_t)s->nslots * nc * Sb;           // f
   b += (size_t)s->nblocks * (s->nwall + 1) * NFF * T;  // wall partials
   b += (size_t)64 * nc * (NMOM + NFF) * 8 / 64 + nc * (NMOM + NFF) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
@@ -630,13 +655,13 @@ static size_t footprint(const gsis_solver *s) {
   return b;
 }
 
-template <typename T>
+template <typename T, typename S>
 static int allocate_and_upload(gsis_solver *s) {
   const size_t nc = s->nc;
   int rc = 0;
 #define A(ptr, bytes) \
   if (!rc) rc = s->alloc(&(ptr), (bytes))
-  A(s->d_f, (size_t)s->nslots * nc * sizeof(T));
+  A(s->d_f, (size_t)s->nslots * nc * sizeof(S));
   // moment chunks: enough (cell, chunk) threads to fill the GPU, at most 64 blocks per chunk
   {
     const int want = std::max(1, (int)((160000 + nc - 1) / nc));
@@ -782,14 +807,13 @@ static int init_state(gsis_solver *s) {
   int rc = s->cuda(cudaMalloc(&dW0, nc * 6 * sizeof(double)), "temporary");
   if (rc) return rc;
   rc = s->upload(dW0, W0.data(), nc * 6 * sizeof(double));
-  if (!rc) {
-    if (s->prec == GSIS_F32) rc = s->cuda(launch_init_maxwellian<float>(s->kin_args<float>(), dW0, s->nblocks, s->stream), "init f");
-    else rc = s->cuda(launch_init_maxwellian<double>(s->kin_args<double>(), dW0, s->nblocks, s->stream), "init f");
-  }
+  if (!rc)
+    rc = GSIS_DISPATCH(s->prec, (s->cuda(launch_init_maxwellian<T, S>(s->kin_args<T, S>(), dW0, s->nblocks, s->stream),
+                                         "init f")));
   if (!rc) rc = s->cuda(cudaStreamSynchronize(s->stream), "sync");
   cudaFree(dW0);
   if (rc) return rc;
-  return s->prec == GSIS_F32 ? s->state_from_f<float>() : s->state_from_f<double>();
+  return GSIS_DISPATCH(s->prec, (s->state_from_f<T, S>(W0.data())));
 }
 
 extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const gsis_gas *gas, double Kn, double Ma,
@@ -812,7 +836,7 @@ extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const
   s->gas = *gas;
   s->stream = (cudaStream_t)o.stream;
   setup(s, mesh, vgrid);
-  rc = s->prec == GSIS_F32 ? allocate_and_upload<float>(s) : allocate_and_upload<double>(s);
+  rc = GSIS_DISPATCH(s->prec, (allocate_and_upload<T, S>(s)));
   if (!rc) rc = init_state(s);
   for (int t = 0; !rc && t < o.kinetic_presteps; ++t) rc = s->step(GSIS_MODE_DVM);
   if (rc) {
@@ -952,10 +976,10 @@ extern "C" int gsis_get_f(gsis_handle h, double *f0, double *f1) {
   int rc = h->cuda(cudaMalloc(&tmp, bytes), "temporary");
   if (!rc) rc = h->cuda(cudaMalloc(&canon, h->nslots * sizeof(int)), "temporary");
   if (!rc) rc = h->upload(canon, h->slot_canon.data(), h->nslots * sizeof(int));
-  if (!rc) {
-    if (h->prec == GSIS_F32) rc = h->cuda(launch_export_f<float>(h->kin_args<float>(), canon, h->nslots, h->nvc, tmp, h->stream), "export");
-    else rc = h->cuda(launch_export_f<double>(h->kin_args<double>(), canon, h->nslots, h->nvc, tmp, h->stream), "export");
-  }
+  if (!rc)
+    rc = GSIS_DISPATCH(h->prec, (h->cuda(launch_export_f<T, S>(h->kin_args<T, S>(), canon, h->nslots, h->nvc, tmp,
+                                                                 h->stream),
+                                         "export")));
   if (!rc) rc = h->cuda(cudaMemcpyAsync(f0, tmp, bytes, cudaMemcpyDeviceToHost, h->stream), "copy f");
   if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
   cudaFree(tmp);
@@ -973,15 +997,15 @@ extern "C" int gsis_set_f(gsis_handle h, const double *f0, const double *f1) {
   if (!rc) rc = h->cuda(cudaMalloc(&canon, h->nslots * sizeof(int)), "temporary");
   if (!rc) rc = h->upload(canon, h->slot_canon.data(), h->nslots * sizeof(int));
   if (!rc) rc = h->upload(tmp, f0, bytes);
-  if (!rc) {
-    if (h->prec == GSIS_F32) rc = h->cuda(launch_import_f<float>(h->kin_args<float>(), canon, h->nslots, h->nvc, tmp, h->stream), "import");
-    else rc = h->cuda(launch_import_f<double>(h->kin_args<double>(), canon, h->nslots, h->nvc, tmp, h->stream), "import");
-  }
+  if (!rc)
+    rc = GSIS_DISPATCH(h->prec, (h->cuda(launch_import_f<T, S>(h->kin_args<T, S>(), canon, h->nslots, h->nvc, tmp,
+                                                                 h->stream),
+                                         "import")));
   if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
   cudaFree(tmp);
   cudaFree(canon);
   if (rc) return rc;
-  return h->prec == GSIS_F32 ? h->state_from_f<float>() : h->state_from_f<double>();
+  return GSIS_DISPATCH(h->prec, (h->state_from_f<T, S>()));
 }
 
 extern "C" int gsis_profile(gsis_handle h, int enable, int reset, double *ms, int n, int *steps, int *launches) {

@@ -10,7 +10,12 @@ namespace gsis {
 constexpr int VB = 32;          // discrete velocities per block (one per lane)
 constexpr int NMOM = 13;        // raw moments about the state velocity: 1, c(3), cc(6), |c|^2 c(3)
 constexpr int NFF = 5;          // face-flux moments: 1, xi(3), |xi|^2/2
-constexpr int NST = 20;         // per-cell kinetic state values (see CellState layout)
+constexpr int NST = 24;         // per-cell kinetic state values:
+                                //  [0..2] u_n, [3] 1/T_n, [4] rho_n (pi T_n)^-3/2 (Maxwellian of W^n),
+                                //  [5..7] u_o, [8] 1/T_o, [9] rho_o (pi T_o)^-3/2 (of W^{n+1/2}),
+                                //  [10] mass scale s, [11] 1/tau, [12..14] Shakhov heat-flux factor,
+                                //  [15] diagonal, [16..18] u_r, [19] 1/T_r, [20] rho_r (pi T_r)^-3/2:
+                                //  the Maxwellian a BF16 VDF is stored relative to, [21..23] unused
 constexpr int MAXNP = 13 + 3 * NFF;
 constexpr int GSIS_ERR_DIVERGED = -4;  // same values as GSIS_E_DIVERGED / GSIS_E_TIMEOUT
 constexpr int GSIS_ERR_TIMEOUT = -5;
@@ -59,7 +64,8 @@ struct KinGeom {
   double K3;            // venkat K^3: eps^2 = K^3 V
 };
 
-template <typename T>
+// T: kinetic arithmetic (float or double); S: VDF storage (T, or __nv_bfloat16 with T = float)
+template <typename T, typename S = T>
 struct KinArgs {
   KinGeom g;
   const AxisCell<T> *ax[3];
@@ -73,29 +79,29 @@ struct KinArgs {
   const T *st;           // [cell][NST]
   const double *rho_w;   // [nwall]
   const double *wall_uT; // [6][4]: u_w(3), T_w
-  T *f;                  // [block][cell][VB] f_raw, updated in place
+  S *f;                  // [block][cell][VB] f_raw, updated in place
   T *wpart;              // [block][wall face][NFF] outgoing wall-flux moments (wall cells only)
   int nwall;
   int nblocks;
 };
 
 // ---- launchers (defined in the .cu files) ----
-template <typename T>
-cudaError_t launch_kinetic(const KinArgs<T> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s);
+template <typename T, typename S>
+cudaError_t launch_kinetic(const KinArgs<T, S> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s);
 template <typename T>
 size_t kinetic_smem_bytes(const KinGeom &g);
-template <typename T>
-cudaError_t launch_wall_prepass(const KinArgs<T> &a, const int *wall_cell, const int *wall_side, int nwall,
+template <typename T, typename S>
+cudaError_t launch_wall_prepass(const KinArgs<T, S> &a, const int *wall_cell, const int *wall_side, int nwall,
                                 const double *Z0, double *rho_w, int nslots, cudaStream_t s);
-template <typename T>
-cudaError_t launch_moments(const KinArgs<T> &a, int blocks_per_chunk, int nchunks, double *mp, cudaStream_t s);
-template <typename T>
-cudaError_t launch_init_maxwellian(const KinArgs<T> &a, const double *W0, int nblocks, cudaStream_t s);
-template <typename T>
-cudaError_t launch_export_f(const KinArgs<T> &a, const int *slot_canon, int nslots, int nv, double *out,
+template <typename T, typename S>
+cudaError_t launch_moments(const KinArgs<T, S> &a, int blocks_per_chunk, int nchunks, double *mp, cudaStream_t s);
+template <typename T, typename S>
+cudaError_t launch_init_maxwellian(const KinArgs<T, S> &a, const double *W0, int nblocks, cudaStream_t s);
+template <typename T, typename S>
+cudaError_t launch_export_f(const KinArgs<T, S> &a, const int *slot_canon, int nslots, int nv, double *out,
                             cudaStream_t s);
-template <typename T>
-cudaError_t launch_import_f(const KinArgs<T> &a, const int *slot_canon, int nslots, int nv, const double *in,
+template <typename T, typename S>
+cudaError_t launch_import_f(const KinArgs<T, S> &a, const int *slot_canon, int nslots, int nv, const double *in,
                             cudaStream_t s);
 
 cudaError_t launch_wall_constants(const double *vel64, int nslots, const double *wall_uT, const int *sides,

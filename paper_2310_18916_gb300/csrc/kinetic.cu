@@ -13,14 +13,29 @@
 //     (exact in one pass on a rectilinear grid: every inflow neighbour has a lower colour),
 //   - writes f^{n+1/2} in place and reduces, over its 32 velocities, the 13 raw moments about
 //     the state velocity and the moments of its outflow face fluxes.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "gsis_internal.h"
 
 namespace gsis {
+
+// VDF element load / store between the storage type S and the arithmetic type T: plain for
+// S = T; BF16 storage widens exactly to FP32 on load and rounds to nearest even on store.
+template <typename T, typename S>
+struct Fio {
+  static __device__ __forceinline__ T ld(const S *p) { return *p; }
+  static __device__ __forceinline__ void st(S *p, T v) { *p = v; }
+};
+template <>
+struct Fio<float, __nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
 
 __device__ __forceinline__ float dexp(float x) { return __expf(x); }
 __device__ __forceinline__ double dexp(double x) { return exp(x); }
@@ -45,6 +60,28 @@ __device__ __forceinline__ T corrected(T fraw, const T *st, T x, T y, T z) {
   return st[10] * fraw + mn - mo;
 }
 
+// BF16 storage keeps f_raw relative to a per-cell Maxwellian, the Maxwellian of W^n of the
+// kinetic step that stored it (state values 16..20): the stored deviation is small next to f,
+// and so is its round-off.  FP32 and FP64 store f_raw itself.
+template <typename S>
+struct StoredRelative : std::false_type {};
+template <>
+struct StoredRelative<__nv_bfloat16> : std::true_type {};
+
+// state values a loader of stored f needs: 16, or 24 with the storage reference
+template <typename S>
+__host__ __device__ constexpr int state_len() { return StoredRelative<S>::value ? 24 : 16; }
+
+// f^n from a stored value: f_raw = stored (+ M_r for relative storage), then Eq. updatef
+template <typename T, typename S>
+__device__ __forceinline__ T corrected_stored(T stored, const T *st, T x, T y, T z) {
+  if constexpr (StoredRelative<S>::value) {
+    const T cx = x - st[16], cy = y - st[17], cz = z - st[18];
+    stored += st[20] * dexp(-(cx * cx + cy * cy + cz * cz) * st[19]);
+  }
+  return corrected(stored, st, x, y, z);
+}
+
 // Venkatakrishnan limiter of one cell: min over its faces (and 1) of
 //   (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
 // the face function with numerator and denominator divided by D2; both are positive, so
@@ -66,10 +103,11 @@ __device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const
   return ddiv(bn, bd);
 }
 
+template <int N = 16>
 __device__ __forceinline__ void load_state(const float *__restrict__ src, float *st) {
   const float4 *p = reinterpret_cast<const float4 *>(src);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < N / 4; ++q) {
     const float4 v = __ldg(p + q);
     st[4 * q] = v.x;
     st[4 * q + 1] = v.y;
@@ -77,10 +115,11 @@ __device__ __forceinline__ void load_state(const float *__restrict__ src, float 
     st[4 * q + 3] = v.w;
   }
 }
+template <int N = 16>
 __device__ __forceinline__ void load_state(const double *__restrict__ src, double *st) {
   const double2 *p = reinterpret_cast<const double2 *>(src);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < N / 2; ++q) {
     const double2 v = __ldg(p + q);
     st[2 * q] = v.x;
     st[2 * q + 1] = v.y;
@@ -112,8 +151,8 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-template <typename T, int NACT>
-__global__ void kinetic_kernel(const KinArgs<T> A) {
+template <typename T, typename S, int NACT>
+__global__ void kinetic_kernel(const KinArgs<T, S> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const KinGeom &G = A.g;
   T *ring = reinterpret_cast<T *>(smem_raw);
@@ -144,7 +183,7 @@ __global__ void kinetic_kernel(const KinArgs<T> A) {
       Mw[a] = wall_maxwellian<T>(A.wall_uT + 4 * upside[a], xi[0], xi[1], xi[2]);
   }
   const int n0 = G.n[0], n1 = G.n[1];
-  T *F = A.f + (size_t)b * G.nc * VB;
+  S *F = A.f + (size_t)b * G.nc * VB;
   const int4 *natcell = A.natcell + (size_t)oct * G.nc;
   const T K3 = (T)G.K3;
   const size_t slot_stride = (size_t)G.maxcol * VB;
@@ -154,9 +193,9 @@ __global__ void kinetic_kernel(const KinArgs<T> A) {
     T *slot = ring + (size_t)(c % 3) * slot_stride;
     for (int p = warp; p < cnt; p += nw) {
       const int cell = __ldg(&natcell[off + p].x);
-      T st[16];
-      load_state(A.st + (size_t)cell * NST, st);
-      slot[p * VB + lane] = corrected(F[(size_t)cell * VB + lane], st, xi[0], xi[1], xi[2]);
+      T st[state_len<S>()];
+      load_state<state_len<S>()>(A.st + (size_t)cell * NST, st);
+      slot[p * VB + lane] = corrected_stored<T, S>(Fio<T, S>::ld(F + (size_t)cell * VB + lane), st, xi[0], xi[1], xi[2]);
     }
   };
 
@@ -212,7 +251,8 @@ __global__ void kinetic_kernel(const KinArgs<T> A) {
       // reference distribution g_0t of the state W^n
       const T cx = xi[0] - st[0], cy = xi[1] - st[1], cz = xi[2] - st[2];
       const T c2 = cx * cx + cy * cy + cz * cz;
-      const T g = st[4] * dexp(-c2 * st[3]) * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
+      const T mw = st[4] * dexp(-c2 * st[3]);  // Maxwellian of W^n
+      const T g = mw * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
       T acc = (g - fi) * st[11];
       T D = st[15];
       T fout[3];
@@ -232,7 +272,7 @@ __global__ void kinetic_kernel(const KinArgs<T> A) {
         acc -= k * (fout[a] - ein);
       }
       const T df = ddiv(acc, D);
-      F[(size_t)cell * VB + lane] = fi + df;
+      Fio<T, S>::st(F + (size_t)cell * VB + lane, StoredRelative<S>::value ? fi + df - mw : fi + df);
 #pragma unroll
       for (int a = 0; a < NACT; ++a) {
         const T eout = fout[a] + df;
@@ -266,12 +306,12 @@ size_t kinetic_smem_bytes(const KinGeom &g) {
   return n * sizeof(T);
 }
 
-template <typename T>
-cudaError_t launch_kinetic(const KinArgs<T> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s) {
-  void (*k)(const KinArgs<T>) = nullptr;
-  if (a.g.nact == 1) k = kinetic_kernel<T, 1>;
-  else if (a.g.nact == 2) k = kinetic_kernel<T, 2>;
-  else k = kinetic_kernel<T, 3>;
+template <typename T, typename S>
+cudaError_t launch_kinetic(const KinArgs<T, S> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s) {
+  void (*k)(const KinArgs<T, S>) = nullptr;
+  if (a.g.nact == 1) k = kinetic_kernel<T, S, 1>;
+  else if (a.g.nact == 2) k = kinetic_kernel<T, S, 2>;
+  else k = kinetic_kernel<T, S, 3>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<nblocks, nwarps * 32, smem, s>>>(a);
@@ -282,8 +322,8 @@ cudaError_t launch_kinetic(const KinArgs<T> &a, int nblocks, int nwarps, size_t 
 // Diffuse-wall pre-pass: rho_w of each wall face balances the mass flux of the molecules that
 // reach the wall, whose face values are the wall cell's limited reconstruction of f^n.
 
-template <typename T, int NACT>
-__global__ void wall_prepass_kernel(const KinArgs<T> A, const int *wall_cell, const int *wall_side,
+template <typename T, typename S, int NACT>
+__global__ void wall_prepass_kernel(const KinArgs<T, S> A, const int *wall_cell, const int *wall_side,
                                     const double *Z0, double *rho_w, int nslots) {
   const KinGeom &G = A.g;
   const int wf = blockIdx.x;
@@ -292,15 +332,16 @@ __global__ void wall_prepass_kernel(const KinArgs<T> A, const int *wall_cell, co
   const int n0 = G.n[0], n1 = G.n[1];
   const int nat[3] = {cell % n0, (cell / n0) % n1, cell / (n0 * n1)};
   const int stride[3] = {1, n0, n0 * n1};
-  T st[16], stn[3][2][16];
-  load_state(A.st + (size_t)cell * NST, st);
+  constexpr int SL = state_len<S>();
+  T st[SL], stn[3][2][SL];
+  load_state<SL>(A.st + (size_t)cell * NST, st);
   bool has[3][2];
 #pragma unroll
   for (int a = 0; a < NACT; ++a) {
     has[a][0] = nat[a] > 0;
     has[a][1] = nat[a] < G.n[a] - 1;
-    if (has[a][0]) load_state(A.st + (size_t)(cell - stride[a]) * NST, stn[a][0]);
-    if (has[a][1]) load_state(A.st + (size_t)(cell + stride[a]) * NST, stn[a][1]);
+    if (has[a][0]) load_state<SL>(A.st + (size_t)(cell - stride[a]) * NST, stn[a][0]);
+    if (has[a][1]) load_state<SL>(A.st + (size_t)(cell + stride[a]) * NST, stn[a][1]);
   }
   AxisCell<T> gc[3];
   T V = (T)1;
@@ -316,14 +357,14 @@ __global__ void wall_prepass_kernel(const KinArgs<T> A, const int *wall_cell, co
     const T xa = axn == 0 ? x : (axn == 1 ? y : z);
     if (!(w > (T)0) || !((double)xa * dir > 0.0)) continue;
     const int blk = v / VB, ln = v % VB;
-    const T *Fb = A.f + (size_t)blk * G.nc * VB;
-    const T fi = corrected(Fb[(size_t)cell * VB + ln], st, x, y, z);
+    const S *Fb = A.f + (size_t)blk * G.nc * VB;
+    const T fi = corrected_stored<T, S>(Fio<T, S>::ld(Fb + (size_t)cell * VB + ln), st, x, y, z);
     T gr[3], rlo[3], rhi[3], fmax = fi, fmin = fi;
 #pragma unroll
     for (int a = 0; a < NACT; ++a) {
       T flo = fi, fhi = fi;
-      if (has[a][0]) flo = corrected(Fb[(size_t)(cell - stride[a]) * VB + ln], stn[a][0], x, y, z);
-      if (has[a][1]) fhi = corrected(Fb[(size_t)(cell + stride[a]) * VB + ln], stn[a][1], x, y, z);
+      if (has[a][0]) flo = corrected_stored<T, S>(Fio<T, S>::ld(Fb + (size_t)(cell - stride[a]) * VB + ln), stn[a][0], x, y, z);
+      if (has[a][1]) fhi = corrected_stored<T, S>(Fio<T, S>::ld(Fb + (size_t)(cell + stride[a]) * VB + ln), stn[a][1], x, y, z);
       if (has[a][0]) { fmax = fmax > flo ? fmax : flo; fmin = fmin < flo ? fmin : flo; }
       if (has[a][1]) { fmax = fmax > fhi ? fmax : fhi; fmin = fmin < fhi ? fmin : fhi; }
       gr[a] = gc[a].clo * (flo - fi) + gc[a].chi * (fhi - fi);
@@ -345,13 +386,13 @@ __global__ void wall_prepass_kernel(const KinArgs<T> A, const int *wall_cell, co
   if (threadIdx.x == 0) rho_w[wf] = red[0] / Z0[side];
 }
 
-template <typename T>
-cudaError_t launch_wall_prepass(const KinArgs<T> &a, const int *wall_cell, const int *wall_side, int nwall,
+template <typename T, typename S>
+cudaError_t launch_wall_prepass(const KinArgs<T, S> &a, const int *wall_cell, const int *wall_side, int nwall,
                                 const double *Z0, double *rho_w, int nslots, cudaStream_t s) {
   if (nwall == 0) return cudaSuccess;
-  if (a.g.nact == 1) wall_prepass_kernel<T, 1><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
-  else if (a.g.nact == 2) wall_prepass_kernel<T, 2><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
-  else wall_prepass_kernel<T, 3><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
+  if (a.g.nact == 1) wall_prepass_kernel<T, S, 1><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
+  else if (a.g.nact == 2) wall_prepass_kernel<T, S, 2><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
+  else wall_prepass_kernel<T, S, 3><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, Z0, rho_w, nslots);
   return cudaGetLastError();
 }
 
@@ -429,10 +470,10 @@ struct MomAcc {
   }
 };
 
-template <typename T>
-__device__ __forceinline__ void load_block_f(const T *p, T *f);
+template <typename T, typename S>
+__device__ __forceinline__ void load_block_f(const S *p, T *f);
 template <>
-__device__ __forceinline__ void load_block_f<float>(const float *p, float *f) {
+__device__ __forceinline__ void load_block_f<float, float>(const float *p, float *f) {
   const float4 *q = reinterpret_cast<const float4 *>(p);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -444,7 +485,23 @@ __device__ __forceinline__ void load_block_f<float>(const float *p, float *f) {
   }
 }
 template <>
-__device__ __forceinline__ void load_block_f<double>(const double *p, double *f) {
+__device__ __forceinline__ void load_block_f<float, __nv_bfloat16>(const __nv_bfloat16 *p, float *f) {
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint4 v = __ldcs(q + i);
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      // a 32-bit word holds two BF16 values, the lower-addressed one in the low half; a BF16
+      // value is the upper 16 bits of the FP32 value it widens to
+      f[8 * i + 2 * j] = __uint_as_float(w[j] << 16);
+      f[8 * i + 2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+    }
+  }
+}
+template <>
+__device__ __forceinline__ void load_block_f<double, double>(const double *p, double *f) {
   const double2 *q = reinterpret_cast<const double2 *>(p);
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
@@ -454,8 +511,8 @@ __device__ __forceinline__ void load_block_f<double>(const double *p, double *f)
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T> A, int blocks_per_chunk, double *mp) {
+template <typename T, typename S>
+__global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T, S> A, int blocks_per_chunk, double *mp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *svel = reinterpret_cast<T *>(smem_raw);  // [blocks_per_chunk * VB][4]
   const KinGeom &G = A.g;
@@ -472,7 +529,7 @@ __global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T> A, int bl
   acc.zero();
   for (int bb = 0; bb < nb; ++bb) {
     T f[VB];
-    load_block_f<T>(A.f + ((size_t)(b0 + bb) * G.nc + cell) * VB, f);
+    load_block_f<T, S>(A.f + ((size_t)(b0 + bb) * G.nc + cell) * VB, f);
     T sum[NMOM + NFF];
 #pragma unroll
     for (int k = 0; k < NMOM + NFF; ++k) sum[k] = (T)0;
@@ -482,7 +539,8 @@ __global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T> A, int bl
       const T x = v[0], y = v[1], z = v[2], w = v[3];
       const T cx = x - st[0], cy = y - st[1], cz = z - st[2];
       const T c2 = cx * cx + cy * cy + cz * cz;
-      const T wf = w * f[l];
+      const T mw = st[4] * dexp(-c2 * st[3]);  // Maxwellian of W^n, the storage reference of this step
+      const T wf = w * (StoredRelative<S>::value ? f[l] + mw : f[l]);
       sum[0] += wf;
       sum[1] += wf * cx;
       sum[2] += wf * cy;
@@ -496,7 +554,7 @@ __global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T> A, int bl
       sum[10] += wf * c2 * cx;
       sum[11] += wf * c2 * cy;
       sum[12] += wf * c2 * cz;
-      const T g = st[4] * dexp(-c2 * st[3]) * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
+      const T g = mw * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
       const T d = w * g - wf;
       sum[13] += d;
       sum[14] += d * x;
@@ -511,25 +569,26 @@ __global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T> A, int bl
   for (int k = 0; k < NMOM + NFF; ++k) out[k] = (double)acc.s[k] - (double)acc.c[k];
 }
 
-template <typename T>
-cudaError_t launch_moments(const KinArgs<T> &a, int blocks_per_chunk, int nchunks, double *mp, cudaStream_t s) {
+template <typename T, typename S>
+cudaError_t launch_moments(const KinArgs<T, S> &a, int blocks_per_chunk, int nchunks, double *mp, cudaStream_t s) {
   const size_t smem = (size_t)blocks_per_chunk * VB * 4 * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(moments_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(moments_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.nc + 127) / 128, nchunks);
-  moments_kernel<T><<<grid, 128, smem, s>>>(a, blocks_per_chunk, mp);
+  moments_kernel<T, S><<<grid, 128, smem, s>>>(a, blocks_per_chunk, mp);
   return cudaGetLastError();
 }
 
 // f_raw = Maxwellian(W0) of each cell at each slot velocity, in the storage precision (the
-// per-cell factor rho (pi T)^(-3/2) and 1/T in FP64, the exponential in T).
+// per-cell factor rho (pi T)^(-3/2) and 1/T in FP64, the exponential in T).  Relative (BF16)
+// storage writes zero deviations from M(W0), which the initial state names as the reference.
 __device__ __forceinline__ float accurate_exp(float x) { return expf(x); }
 __device__ __forceinline__ double accurate_exp(double x) { return exp(x); }
 
 // One warp per cell: the per-cell factors once (FP64 is scarce on this GPU), then every
 // velocity block of the cell, one 128-byte line per block.
-template <typename T>
-__global__ void init_maxwellian_kernel(const KinArgs<T> A, const double *W0) {
+template <typename T, typename S>
+__global__ void init_maxwellian_kernel(const KinArgs<T, S> A, const double *W0) {
   const KinGeom &G = A.g;
   const int lane = threadIdx.x & 31;
   const int cell = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -540,72 +599,78 @@ __global__ void init_maxwellian_kernel(const KinArgs<T> A, const double *W0) {
   for (int b = 0; b < A.nblocks; ++b) {
     const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
     const T cx = vp[0] - ux, cy = vp[1] - uy, cz = vp[2] - uz;
-    A.f[((size_t)b * G.nc + cell) * VB + lane] = C * accurate_exp(-(cx * cx + cy * cy + cz * cz) * invT);
+    // relative storage: f is exactly the reference Maxwellian M(W0), stored as a zero deviation
+    const T f = StoredRelative<S>::value ? (T)0 : C * accurate_exp(-(cx * cx + cy * cy + cz * cz) * invT);
+    Fio<T, S>::st(A.f + ((size_t)b * G.nc + cell) * VB + lane, f);
   }
 }
 
-template <typename T>
-cudaError_t launch_init_maxwellian(const KinArgs<T> &a, const double *W0, int nblocks, cudaStream_t s) {
+template <typename T, typename S>
+cudaError_t launch_init_maxwellian(const KinArgs<T, S> &a, const double *W0, int nblocks, cudaStream_t s) {
   (void)nblocks;
   const int threads = 256;
   const size_t grid = ((size_t)a.g.nc * 32 + threads - 1) / threads;
-  init_maxwellian_kernel<T><<<(unsigned)grid, threads, 0, s>>>(a, W0);
+  init_maxwellian_kernel<T, S><<<(unsigned)grid, threads, 0, s>>>(a, W0);
   return cudaGetLastError();
 }
 
 // Canonical [cell][v] FP64 <-> internal [block][cell][lane].  Export applies the pending
 // correction (the returned f is the VDF the next kinetic step starts from).
-template <typename T>
-__global__ void export_f_kernel(const KinArgs<T> A, const int *slot_canon, int nslots, int nv, double *out) {
+template <typename T, typename S>
+__global__ void export_f_kernel(const KinArgs<T, S> A, const int *slot_canon, int nslots, int nv, double *out) {
   const size_t n = (size_t)A.g.nc * nslots;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
     const int slot = (int)(idx % nslots);
     const int cell = (int)(idx / nslots);
     const T *vp = A.vel + (size_t)slot * 4;
     if (!(vp[3] > (T)0)) continue;
-    T st[16];
-    load_state(A.st + (size_t)cell * NST, st);
+    T st[state_len<S>()];
+    load_state<state_len<S>()>(A.st + (size_t)cell * NST, st);
     const int blk = slot / VB, ln = slot % VB;
-    const T f = corrected(A.f[((size_t)blk * A.g.nc + cell) * VB + ln], st, vp[0], vp[1], vp[2]);
+    const T f = corrected_stored<T, S>(Fio<T, S>::ld(A.f + ((size_t)blk * A.g.nc + cell) * VB + ln), st, vp[0], vp[1], vp[2]);
     out[(size_t)cell * nv + slot_canon[slot]] = (double)f;
   }
 }
 
-template <typename T>
-__global__ void import_f_kernel(const KinArgs<T> A, const int *slot_canon, int nslots, int nv, const double *in) {
+template <typename T, typename S>
+__global__ void import_f_kernel(const KinArgs<T, S> A, const int *slot_canon, int nslots, int nv, const double *in) {
   const size_t n = (size_t)A.g.nc * nslots;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
     const int slot = (int)(idx % nslots);
     const int cell = (int)(idx / nslots);
     const int blk = slot / VB, ln = slot % VB;
-    A.f[((size_t)blk * A.g.nc + cell) * VB + ln] = (T)in[(size_t)cell * nv + slot_canon[slot]];
+    Fio<T, S>::st(A.f + ((size_t)blk * A.g.nc + cell) * VB + ln, (T)in[(size_t)cell * nv + slot_canon[slot]]);
   }
 }
 
-template <typename T>
-cudaError_t launch_export_f(const KinArgs<T> &a, const int *slot_canon, int nslots, int nv, double *out,
+template <typename T, typename S>
+cudaError_t launch_export_f(const KinArgs<T, S> &a, const int *slot_canon, int nslots, int nv, double *out,
                             cudaStream_t s) {
-  export_f_kernel<T><<<1024, 256, 0, s>>>(a, slot_canon, nslots, nv, out);
+  export_f_kernel<T, S><<<1024, 256, 0, s>>>(a, slot_canon, nslots, nv, out);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_import_f(const KinArgs<T> &a, const int *slot_canon, int nslots, int nv, const double *in,
+template <typename T, typename S>
+cudaError_t launch_import_f(const KinArgs<T, S> &a, const int *slot_canon, int nslots, int nv, const double *in,
                             cudaStream_t s) {
-  import_f_kernel<T><<<1024, 256, 0, s>>>(a, slot_canon, nslots, nv, in);
+  import_f_kernel<T, S><<<1024, 256, 0, s>>>(a, slot_canon, nslots, nv, in);
   return cudaGetLastError();
 }
 
-#define GSIS_INST(T)                                                                                            \
-  template cudaError_t launch_kinetic<T>(const KinArgs<T> &, int, int, size_t, cudaStream_t);                  \
-  template size_t kinetic_smem_bytes<T>(const KinGeom &);                                                       \
-  template cudaError_t launch_wall_prepass<T>(const KinArgs<T> &, const int *, const int *, int, const double *, \
-                                              double *, int, cudaStream_t);                                     \
-  template cudaError_t launch_moments<T>(const KinArgs<T> &, int, int, double *, cudaStream_t);                \
-  template cudaError_t launch_init_maxwellian<T>(const KinArgs<T> &, const double *, int, cudaStream_t);        \
-  template cudaError_t launch_export_f<T>(const KinArgs<T> &, const int *, int, int, double *, cudaStream_t);   \
-  template cudaError_t launch_import_f<T>(const KinArgs<T> &, const int *, int, int, const double *, cudaStream_t);
-GSIS_INST(float)
-GSIS_INST(double)
+#define GSIS_INST(T, S)                                                                                         \
+  template cudaError_t launch_kinetic<T, S>(const KinArgs<T, S> &, int, int, size_t, cudaStream_t);             \
+  template cudaError_t launch_wall_prepass<T, S>(const KinArgs<T, S> &, const int *, const int *, int,           \
+                                                 const double *, double *, int, cudaStream_t);                   \
+  template cudaError_t launch_moments<T, S>(const KinArgs<T, S> &, int, int, double *, cudaStream_t);           \
+  template cudaError_t launch_init_maxwellian<T, S>(const KinArgs<T, S> &, const double *, int, cudaStream_t);   \
+  template cudaError_t launch_export_f<T, S>(const KinArgs<T, S> &, const int *, int, int, double *,            \
+                                             cudaStream_t);                                                      \
+  template cudaError_t launch_import_f<T, S>(const KinArgs<T, S> &, const int *, int, int, const double *,      \
+                                             cudaStream_t);
+GSIS_INST(float, float)
+GSIS_INST(double, double)
+GSIS_INST(float, __nv_bfloat16)
+template size_t kinetic_smem_bytes<float>(const KinGeom &);
+template size_t kinetic_smem_bytes<double>(const KinGeom &);
 
 }  // namespace gsis

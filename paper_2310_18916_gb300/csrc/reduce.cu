@@ -235,6 +235,8 @@ __global__ void state_kernel(StateArgs a) {
     const double *W = a.Wn + (size_t)cell * 6;
     const double *M = a.Mh + (size_t)cell * 18;
     double *st = a.st64 + (size_t)cell * NST;
+    // the Maxwellian of the step that just stored f becomes the storage reference of BF16 VDFs
+    for (int q = 0; q < 5; ++q) st[16 + q] = st[q];
     const double rho = W[0], Tt = W[4];
     st[0] = W[1];
     st[1] = W[2];
@@ -254,7 +256,7 @@ __global__ void state_kernel(StateArgs a) {
     st[13] = A * M[13];
     st[14] = A * M[14];
     st[15] = a.kin_inv_dt + invtau;
-    for (int q = 16; q < NST; ++q) st[q] = 0.0;
+    for (int q = 21; q < NST; ++q) st[q] = 0.0;
     T *out = reinterpret_cast<T *>(a.stT) + (size_t)cell * NST;
     for (int q = 0; q < NST; ++q) out[q] = (T)st[q];
   }

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libgsis.so")
 
 D = C.POINTER(C.c_double)
 GSIS_OK, GSIS_E_NOT_CONVERGED = 0, -6
-F64, F32 = 0, 1
+F64, F32, BF16 = 0, 1, 2
+PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16}
 MODE_GSIS, MODE_DVM = 0, 1
 F_W, F_HALF, F_HOT = 1, 2, 4
 ERRORS = {-1: "GSIS_E_INVALID", -2: "GSIS_E_OOM", -3: "GSIS_E_CUDA", -4: "GSIS_E_DIVERGED", -5: "GSIS_E_TIMEOUT",
@@ -127,7 +128,8 @@ def build_structs(problem, keep):
 class Solver:
     """GSIS solver on one GPU for a workloads.Problem.
 
-    precision: "f32" or "f64" (VDF storage and kinetic arithmetic; the synthetic solve is FP64).
+    precision: "f32", "f64" or "bf16" (VDF storage; kinetic arithmetic is FP32 for f32 and bf16,
+    FP64 for f64; the synthetic solve is FP64).
     mode: "gsis" or "dvm".  Other keyword arguments map onto gsis_options.
     """
 
@@ -142,7 +144,7 @@ class Solver:
         m, vg, g = build_structs(problem, self._keep)
         o = Options()
         L.gsis_default_options(C.byref(o))
-        o.precision = F32 if precision == "f32" else F64
+        o.precision = PRECISIONS[precision]
         o.mode = MODE_GSIS if mode == "gsis" else MODE_DVM
         for k, v in opts.items():
             if not hasattr(o, k):
@@ -277,7 +279,7 @@ def footprint_bytes(problem, precision="f32"):
     m, vg, g = build_structs(problem, keep)
     o = Options()
     L.gsis_default_options(C.byref(o))
-    o.precision = F32 if precision == "f32" else F64
+    o.precision = PRECISIONS[precision]
     out = C.c_size_t()
     rc = L.gsis_footprint_bytes(C.byref(m), C.byref(vg), C.byref(g), C.byref(o), C.byref(out))
     if rc != 0:

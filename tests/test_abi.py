@@ -53,3 +53,6 @@ def test_default_options_and_footprint_without_gpu(lib):
     # footprint of the 128^2 x 32^3 cavity: f (4 B/point) dominates
     b = gsis.footprint_bytes(wl.cavity(n=128, nv=32), "f32")
     assert 4 * 128 * 128 * 32 ** 3 < b < 8 * 128 * 128 * 32 ** 3
+    # BF16 storage halves the VDF: the footprints differ by 2 B per stored point
+    pts = 128 * 128 * 32 ** 3
+    assert b - gsis.footprint_bytes(wl.cavity(n=128, nv=32), "bf16") == 2 * pts
