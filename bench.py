@@ -138,6 +138,55 @@ def oracle_sample(c=CFG, nv_sample=16, macro_sample=100):
     return est, desc, (t2 - t0)
 
 
+def run_time_to_steady(args):
+    """Wall time from solver creation (host inputs) to eps < tol, per VDF precision, on one GPU,
+    with the accuracy of the FP32 / BF16 solutions against the plain FP64 one.  Each precision
+    stops at the first of eps < tol, a stall of eps (its storage round-off floor: 20 steps
+    without a new minimum) or max_steps."""
+    import numpy as np
+    import torch
+
+    from paper_2310_18916_gb300 import gsis
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    p = problem()
+    vol = np.full(p.ncells, 1.0 / p.ncells)
+    out, ref = [], None
+    for prec in ("f64", "f32", "bf16"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = gsis.Solver(p, precision=prec, mode="gsis")
+        best, since, hist = float("inf"), 0, []
+        for k in range(args.tts_max_steps):
+            e = s.step()
+            hist.append(e)
+            if e < best:
+                best, since = e, 0
+            else:
+                since += 1
+            if e < args.tts_tol or since >= 20:
+                break
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        W = s.W()
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        rec = {"precision": prec, "tol": args.tts_tol, "reached": hist[-1] < args.tts_tol, "steps": len(hist),
+               "seconds": sec, "eps_last": hist[-1], "eps_min": min(hist)}
+        if prec == "f64":
+            ref = W
+        else:
+            rl2 = lambda a, b: float(np.sqrt(((a - b) ** 2 * vol).sum() / (b ** 2 * vol).sum()))
+            rec["rel_l2_vs_f64"] = {"rho": rl2(W[:, 0], ref[:, 0]), "T": rl2(W[:, 4], ref[:, 4]),
+                                    "u_max_abs_over_max": float(np.abs(W[:, 1:3] - ref[:, 1:3]).max()
+                                                                / np.abs(ref[:, 1:3]).max())}
+        out.append(rec)
+    print(json.dumps({"metric": "time to steady state (GSIS, 2D cavity, from host inputs)", "unit": "s",
+                      "higher_is_better": False, "config": {"workload": workload_name()}, "results": out}))
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -173,10 +222,16 @@ def main():
     ap.add_argument("--n", type=int, default=CFG["n"], help="cells per side (profiling cases use 64)")
     ap.add_argument("--nv", type=int, default=CFG["nv"], help="velocities per axis")
     ap.add_argument("--kn", type=float, default=CFG["Kn"])
+    ap.add_argument("--time-to-steady", action="store_true",
+                    help="instead of the throughput line: wall time to eps < --tts-tol for FP64, FP32, BF16")
+    ap.add_argument("--tts-tol", type=float, default=1e-6)
+    ap.add_argument("--tts-max-steps", type=int, default=400)
     args = ap.parse_args()
     CFG.update(n=args.n, nv=args.nv, Kn=args.kn)
     if args.impl == "reference":
         return run_reference(args)
+    if args.time_to_steady:
+        return run_time_to_steady(args)
 
     import numpy as np
     import torch
