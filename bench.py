@@ -37,7 +37,7 @@ FP64_LANES_PER_SM = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # 64^2 cavity with 32^3 velocities, scaled by 4 to 128^2 (both grow with the cells); None once the
 # kernel has changed since the capture
-DRAM_BYTES_PER_LAUNCH = {"kinetic_kernel": 4 * 1018.6e6, "macro_kernel": 4 * 4.06e6}
+DRAM_BYTES_PER_LAUNCH = {"kinetic_kernel": None, "macro_kernel": 4 * 4.06e6}
 
 
 def workload_name(c=CFG):
@@ -187,6 +187,48 @@ def run_time_to_steady(args):
     return 0
 
 
+def run_serve(args):
+    """Configuration 5 scaled to minutes: a seeded Poisson stream of steady cavity solves (sizes,
+    velocity counts and arrival gaps scaled down, Kn log-uniform in [1e-3, 1], lid Mach number in
+    [0.1, 1]) served with continuous batching in FP32, against the same requests solved one at a
+    time in FP32 and in plain FP64."""
+    import torch
+
+    from paper_2310_18916_gb300 import serving
+    from paper_2310_18916_gb300 import workloads as wl
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = serving.poisson_requests(args.serve_requests, args.serve_gap, 0,
+                                    lambda rng: wl.serving_cavity(rng, sizes=(32, 48, 64), nvs=(16, 20, 24)),
+                                    tol=1e-6, max_steps=150)
+    budget = int(0.5 * torch.cuda.mem_get_info()[0])
+    lines = {}
+    for name, slots, prec, arrivals in (("batched_f32", args.serve_slots, "f32", True),
+                                        ("sequential_f32", 1, "f32", False), ("sequential_f64", 1, "f64", False)):
+        rs = reqs if arrivals else [serving.Request(r.rid, r.problem, 0.0, r.tol, r.max_steps, r.stall_steps)
+                                    for r in reqs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = serving.Server(budget, slots=slots, precision=prec).run(rs)
+        wall = time.perf_counter() - t0
+        summ = serving.summary(res, wall)
+        summ["slots"] = slots
+        summ["precision"] = prec
+        lines[name] = summ
+    b = lines["batched_f32"]
+    print(json.dumps({"metric": "steady-solve serving (GSIS, cavity stream)", "unit": "s",
+                      "p50_latency_s": b["p50_latency_s"], "p99_latency_s": b["p99_latency_s"],
+                      "solves_per_hour": b["solves_per_hour"], "higher_is_better": False,
+                      "config": {"requests": len(reqs), "mean_gap_s": args.serve_gap, "slots": args.serve_slots,
+                                 "sizes": "32^2, 48^2, 64^2 cells; 16^3, 20^3, 24^3 velocities",
+                                 "kn": "log-uniform [1e-3, 1]", "lid_mach": "[0.1, 1]", "tol": 1e-6,
+                                 "memory_budget_bytes": budget},
+                      "runs": lines,
+                      "throughput_vs_sequential_f64": b["solves_per_hour"] / lines["sequential_f64"]["solves_per_hour"],
+                      "throughput_vs_sequential_f32": b["solves_per_hour"] / lines["sequential_f32"]["solves_per_hour"]}))
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -226,12 +268,18 @@ def main():
                     help="instead of the throughput line: wall time to eps < --tts-tol for FP64, FP32, BF16")
     ap.add_argument("--tts-tol", type=float, default=1e-6)
     ap.add_argument("--tts-max-steps", type=int, default=400)
+    ap.add_argument("--serve", action="store_true", help="instead of the throughput line: the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-gap", type=float, default=0.25, help="mean arrival gap, seconds")
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     CFG.update(n=args.n, nv=args.nv, Kn=args.kn)
     if args.impl == "reference":
         return run_reference(args)
     if args.time_to_steady:
         return run_time_to_steady(args)
+    if args.serve:
+        return run_serve(args)
 
     import numpy as np
     import torch
@@ -331,7 +379,8 @@ def main():
                      "launch_ms": macro_ms, "share_of_step": macro_ms / ms},
         "roofline_kinetic": {"kernel": "kinetic_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                             "traffic": DRAM_BYTES_PER_LAUNCH["kinetic_kernel"] if args.n == 128 and args.precision == "f32" else None,
+                             "traffic": DRAM_BYTES_PER_LAUNCH["kinetic_kernel"]
+                             if args.n == 128 and args.precision == "f32" else None,
                              "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": kin_ms, "share_of_step": kin_ms / ms},
         "e2e": {"value": args.steps * pts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h, "seconds": e2e_s, "includes": "create from host inputs, steps, per-step state read, destroy"},

@@ -109,6 +109,9 @@ typedef struct {
   gsis_alloc_fn alloc;
   gsis_free_fn free;
   void *alloc_ctx;
+  int macro_sms;        /* SMs the synthetic solve may occupy (default 0: all).  Its blocks hold a
+                           whole SM each, so solves that run at the same time on one GPU (serving)
+                           each take a share. */
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;
@@ -149,6 +152,17 @@ int gsis_moments(gsis_handle h, unsigned field_mask, double *host_out, size_t ou
 /* eps of Eq. convergence_critertion for the last outer step: eps_by_field[0..2] = rho, u, Tt,
  * eps_by_field[3] = their maximum (n >= 4). */
 int gsis_residual(gsis_handle h, double *eps_by_field, int n);
+
+/* One outer step enqueued on the handle's stream without waiting for it (GSIS or DVM as
+ * opt.mode), so steps of several handles on different streams overlap on the device.  At most
+ * one step may be pending: gsis_step_wait must follow before the next gsis_step_async or any
+ * other call on the handle (GSIS_E_INVALID otherwise). */
+int gsis_step_async(gsis_handle h);
+
+/* Waits for the pending step of gsis_step_async and returns its status (the same codes as
+ * gsis_iterate for one step); *eps_last (may be NULL) receives its eps (maximum over fields).
+ * GSIS_E_INVALID when no step is pending. */
+int gsis_step_wait(gsis_handle h, double *eps_last);
 
 /* Per wall face (host arrays of length gsis_nwall): cell index, side, re-emitted density
  * rho_w of the last kinetic step and the kinetic wall flux (outward, area-integrated: mass,

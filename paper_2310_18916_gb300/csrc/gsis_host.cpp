@@ -89,6 +89,15 @@ struct gsis_solver {
   std::vector<int> colcells;
   double *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr, *m_dF = nullptr;
   int macro_grid = 0, macro_block = 256;
+  // pinned host words the step's results are copied into, so a step can be enqueued without
+  // the host waiting (pageable read-backs would block)
+  struct Readback {
+    double eps4[4];
+    int iters, err;
+  };
+  Readback *pin = nullptr;
+  bool pending = false;
+  int pending_mode = 0, pending_launches = 0;
   int kin_warps = 1;
   size_t kin_smem = 0;
   // profiling
@@ -133,6 +142,10 @@ struct gsis_solver {
   }
 
   void release() {
+    if (pin) {
+      cudaFreeHost(pin);
+      pin = nullptr;
+    }
     if (ev[0])
       for (auto &e : ev) cudaEventDestroy(e);
     if (!allocs.empty()) cudaStreamSynchronize(stream);
@@ -236,7 +249,7 @@ struct gsis_solver {
     // initialisation, f_raw = M(W0) is formed from the state's W^n Maxwellian slot
     std::vector<double> st0((size_t)nc * NST, 0.0);
     for (int c = 0; c < nc; ++c) st0[(size_t)c * NST + 10] = 1.0;
-    if (W0 && prec == GSIS_BF16)
+    if (W0 && prec != GSIS_F64)
       for (int c = 0; c < nc; ++c) {
         const double *w = W0 + (size_t)c * 6;
         double *st = st0.data() + (size_t)c * NST;
@@ -349,13 +362,29 @@ struct gsis_solver {
     launches += 2;
     mark(5);
     std::swap(d_Wstate, d_Wnew);
-    int iters = 0;
-    rc = cuda(cudaMemcpyAsync(eps4, d_eps4, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), "eps");
+    pin->iters = 0;
+    rc = cuda(cudaMemcpyAsync(pin->eps4, d_eps4, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream), "eps");
     if (!rc && mode == GSIS_MODE_GSIS && opt.macro_steps > 0)
-      rc = cuda(cudaMemcpyAsync(&iters, d_iters, sizeof(int), cudaMemcpyDeviceToHost, stream), "iters");
-    if (!rc) rc = check_err();
+      rc = cuda(cudaMemcpyAsync(&pin->iters, d_iters, sizeof(int), cudaMemcpyDeviceToHost, stream), "iters");
+    if (!rc) rc = cuda(cudaMemcpyAsync(&pin->err, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream), "error flag");
     if (rc) return rc;
-    macro_iters_last = iters;
+    pending = true;
+    pending_mode = mode;
+    pending_launches = launches;
+    return GSIS_OK;
+  }
+
+  // waits for the enqueued step and takes over its results
+  int finish_step() {
+    if (!pending) return fail(GSIS_E_INVALID, "no step is pending");
+    pending = false;
+    int rc = cuda(cudaStreamSynchronize(stream), "synchronize");
+    if (rc) return rc;
+    if (pin->err == GSIS_ERR_DIVERGED) return fail(GSIS_E_DIVERGED, "non-finite or non-positive density/temperature");
+    if (pin->err == GSIS_ERR_TIMEOUT) return fail(GSIS_E_TIMEOUT, "a bounded device wait timed out");
+    if (pin->err != 0) return fail(GSIS_E_CUDA, "device error flag %d", pin->err);
+    for (int k = 0; k < 4; ++k) eps4[k] = pin->eps4[k];
+    macro_iters_last = pin->iters;
     ++outer_total;
     if (profiling) {
       for (int k = 0; k < 5; ++k) {
@@ -364,12 +393,19 @@ struct gsis_solver {
         phase_ms[k] += t;
       }
       ++prof_steps;
-      prof_launches += launches;
+      prof_launches += pending_launches;
     }
     return GSIS_OK;
   }
 
-  int step(int mode) { return GSIS_DISPATCH(prec, (step_impl<T, S>(mode))); }
+  int enqueue_step(int mode) {
+    if (pending) return fail(GSIS_E_INVALID, "a step is pending: call gsis_step_wait first");
+    return GSIS_DISPATCH(prec, (step_impl<T, S>(mode)));
+  }
+  int step(int mode) {
+    int rc = enqueue_step(mode);
+    return rc ? rc : finish_step();
+  }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -705,6 +741,8 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->d_ticket, 4 * sizeof(unsigned));
   A(s->d_bar, MACRO_BAR_WORDS * sizeof(unsigned));
   A(s->d_err, sizeof(int));
+  if (!rc && cudaHostAlloc((void **)&s->pin, sizeof(gsis_solver::Readback), cudaHostAllocDefault) != cudaSuccess)
+    rc = s->fail(GSIS_E_OOM, "pinned host read-back words");
   A(s->d_iters, sizeof(int));
   A(s->m_W, nc * 6 * sizeof(double));
   A(s->m_pr, nc * 6 * sizeof(double));
@@ -724,7 +762,7 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->m_wfl, (size_t)(s->nwall + 1) * 6 * sizeof(double));
 #undef A
   if (rc) return rc;
-  rc = s->cuda(macro_launch_shape((int)nc, &s->macro_grid, &s->macro_block), "occupancy");
+  rc = s->cuda(macro_launch_shape((int)nc, s->opt.macro_sms, &s->macro_grid, &s->macro_block), "occupancy");
   if (rc) return rc;
   rc = s->alloc(&s->m_red, (size_t)3 * s->macro_grid * 16 * sizeof(double));
   if (rc) return rc;
@@ -850,8 +888,24 @@ extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const
   return GSIS_OK;
 }
 
+#define GSIS_NOT_PENDING(h) \
+  if ((h)->pending) return (h)->fail(GSIS_E_INVALID, "a step is pending: call gsis_step_wait first")
+
+extern "C" int gsis_step_async(gsis_handle h) {
+  if (!h) return GSIS_E_INVALID;
+  return h->enqueue_step(h->opt.mode);
+}
+
+extern "C" int gsis_step_wait(gsis_handle h, double *eps_last) {
+  if (!h) return GSIS_E_INVALID;
+  const int rc = h->finish_step();
+  if (!rc && eps_last) *eps_last = h->eps4[3];
+  return rc;
+}
+
 extern "C" int gsis_iterate(gsis_handle h, int max_outer, double tol, int *outer_done, double *eps_last) {
   if (!h) return GSIS_E_INVALID;
+  GSIS_NOT_PENDING(h);
   if (outer_done) *outer_done = 0;
   for (int t = 0; t < max_outer; ++t) {
     int rc = h->step(h->opt.mode);
@@ -865,6 +919,7 @@ extern "C" int gsis_iterate(gsis_handle h, int max_outer, double tol, int *outer
 
 extern "C" int gsis_moments(gsis_handle h, unsigned mask, double *host_out, size_t out_len) {
   if (!h || !host_out) return GSIS_E_INVALID;
+  GSIS_NOT_PENDING(h);
   const size_t nc = h->nc;
   size_t per = 0;
   if (mask & GSIS_F_W) per += 6;
@@ -901,6 +956,7 @@ extern "C" int gsis_moments(gsis_handle h, unsigned mask, double *host_out, size
 
 extern "C" int gsis_residual(gsis_handle h, double *eps, int n) {
   if (!h || !eps || n < 4) return GSIS_E_INVALID;
+  GSIS_NOT_PENDING(h);
   for (int k = 0; k < 4; ++k) eps[k] = h->eps4[k];
   return GSIS_OK;
 }
@@ -914,6 +970,7 @@ static double face_area(const gsis_solver *s, int cell, int a) {
 
 extern "C" int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, double *flux6) {
   if (!h) return GSIS_E_INVALID;
+  GSIS_NOT_PENDING(h);
   const int nw = h->nwall;
   std::vector<double> rw(nw + 1), wf((size_t)(nw + 1) * 6);
   int rc = h->cuda(cudaMemcpyAsync(rw.data(), h->d_rho_w, (nw + 1) * 8, cudaMemcpyDeviceToHost, h->stream), "rho_w");
@@ -935,6 +992,7 @@ extern "C" int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, dou
 extern "C" int gsis_wall_loads(gsis_handle h, unsigned side_mask, const double *dir, double rho_ref, double U_ref,
                                double A_ref, double *out6) {
   if (!h || !dir || !out6) return GSIS_E_INVALID;
+  GSIS_NOT_PENDING(h);
   if (!(rho_ref > 0.0) || !(U_ref > 0.0) || !(A_ref > 0.0) || (side_mask & ~63u) != 0)
     return h->fail(GSIS_E_INVALID, "wall loads need rho_ref, U_ref, A_ref > 0 and a 6-bit side mask");
   WallLoadArgs a{};
@@ -960,6 +1018,7 @@ extern "C" int gsis_wall_loads(gsis_handle h, unsigned side_mask, const double *
 
 extern "C" int gsis_kinetic_flux_sum(gsis_handle h, double *out, size_t out_len) {
   if (!h || !out) return GSIS_E_INVALID;
+  GSIS_NOT_PENDING(h);
   const size_t nc = h->nc;
   if (out_len < nc * 6) return h->fail(GSIS_E_INVALID, "out_len too small");
   int rc = h->cuda(cudaMemcpyAsync(out, h->d_K, nc * 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "K");
@@ -970,6 +1029,7 @@ extern "C" int gsis_kinetic_flux_sum(gsis_handle h, double *out, size_t out_len)
 extern "C" int gsis_get_f(gsis_handle h, double *f0, double *f1) {
   (void)f1;
   if (!h || !f0) return GSIS_E_INVALID;
+  GSIS_NOT_PENDING(h);
   const size_t bytes = (size_t)h->nc * h->nvc * sizeof(double);
   double *tmp = nullptr;
   int *canon = nullptr;
@@ -990,6 +1050,7 @@ extern "C" int gsis_get_f(gsis_handle h, double *f0, double *f1) {
 extern "C" int gsis_set_f(gsis_handle h, const double *f0, const double *f1) {
   (void)f1;
   if (!h || !f0) return GSIS_E_INVALID;
+  GSIS_NOT_PENDING(h);
   const size_t bytes = (size_t)h->nc * h->nvc * sizeof(double);
   double *tmp = nullptr;
   int *canon = nullptr;

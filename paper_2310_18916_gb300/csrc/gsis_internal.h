@@ -204,6 +204,6 @@ constexpr int MACRO_BAR_WORDS = 512;  // barrier words, cleared before each laun
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s);
 int macro_block_size();
 cudaError_t macro_max_grid(int *grid);
-cudaError_t macro_launch_shape(int nc, int *grid, int *block);
+cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block);
 
 }  // namespace gsis

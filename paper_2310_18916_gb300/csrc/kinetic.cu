@@ -60,13 +60,16 @@ __device__ __forceinline__ T corrected(T fraw, const T *st, T x, T y, T z) {
   return st[10] * fraw + mn - mo;
 }
 
-// BF16 storage keeps f_raw relative to a per-cell Maxwellian, the Maxwellian of W^n of the
-// kinetic step that stored it (state values 16..20): the stored deviation is small next to f,
-// and so is its round-off.  FP32 and FP64 store f_raw itself.
+// BF16 and FP32 storage keep f_raw relative to a per-cell Maxwellian, the Maxwellian of W^n of
+// the kinetic step that stored it (state values 16..20): the stored deviation is small next to
+// f, and so is its round-off.  FP64 stores f_raw itself (an FP64 exponential per point costs
+// more than its round-off is worth).
 template <typename S>
 struct StoredRelative : std::false_type {};
 template <>
 struct StoredRelative<__nv_bfloat16> : std::true_type {};
+template <>
+struct StoredRelative<float> : std::true_type {};
 
 // state values a loader of stored f needs: 16, or 24 with the storage reference
 template <typename S>
@@ -554,8 +557,10 @@ __global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T, S> A, int
       sum[10] += wf * c2 * cx;
       sum[11] += wf * c2 * cy;
       sum[12] += wf * c2 * cz;
-      const T g = mw * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
-      const T d = w * g - wf;
+      const T shak = (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5);
+      // w (g - f): with relative storage g - f = M shak - (f - M) needs no difference of O(1)
+      // values (the sum is multiplied by 1/tau, which at small Kn would amplify that round-off)
+      const T d = StoredRelative<S>::value ? w * (mw * shak - f[l]) : w * (mw * ((T)1 + shak)) - wf;
       sum[13] += d;
       sum[14] += d * x;
       sum[15] += d * y;
@@ -580,8 +585,9 @@ cudaError_t launch_moments(const KinArgs<T, S> &a, int blocks_per_chunk, int nch
 }
 
 // f_raw = Maxwellian(W0) of each cell at each slot velocity, in the storage precision (the
-// per-cell factor rho (pi T)^(-3/2) and 1/T in FP64, the exponential in T).  Relative (BF16)
-// storage writes zero deviations from M(W0), which the initial state names as the reference.
+// per-cell factor rho (pi T)^(-3/2) and 1/T in FP64, the exponential in T).  Relative (BF16,
+// FP32) storage writes zero deviations from M(W0), which the initial state names as the
+// reference.
 __device__ __forceinline__ float accurate_exp(float x) { return expf(x); }
 __device__ __forceinline__ double accurate_exp(double x) { return exp(x); }
 

@@ -757,7 +757,7 @@ int macro_block_size() { return kBlock; }
 
 // One block of 512 threads per SM: the phases have many short FP64 work items and every SM
 // must hold some.  The cooperative launch guarantees the blocks are co-resident.
-cudaError_t macro_launch_shape(int nc, int *grid, int *block) {
+cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block) {
   (void)nc;
   int dev = 0, nsm = 0, per5 = 0, per6 = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -769,6 +769,7 @@ cudaError_t macro_launch_shape(int nc, int *grid, int *block) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per6, macro_kernel<6>, kBlock, 0);
   if (e != cudaSuccess) return e;
   if (per5 < 1 || per6 < 1) return cudaErrorInvalidConfiguration;
+  if (max_sms > 0 && max_sms < nsm) nsm = max_sms;
   *grid = nsm < MACRO_MAX_GRID ? nsm : MACRO_MAX_GRID;
   *block = kBlock;
   return cudaSuccess;
@@ -776,7 +777,7 @@ cudaError_t macro_launch_shape(int nc, int *grid, int *block) {
 
 cudaError_t macro_max_grid(int *grid) {
   int b = 0;
-  return macro_launch_shape(0, grid, &b);
+  return macro_launch_shape(0, 0, grid, &b);
 }
 
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s) {

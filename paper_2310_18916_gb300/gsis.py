@@ -46,11 +46,12 @@ class Options(C.Structure):
                 ("macro_sweeps", C.c_int), ("macro_cfl", C.c_double), ("macro_tol", C.c_double),
                 ("kin_inv_dt", C.c_double), ("venkat_K", C.c_double), ("kinetic_presteps", C.c_int),
                 ("init_W", D), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("alloc_ctx", C.c_void_p), ("macro_sms", C.c_int)]
 
 
 _lib = None
-SYMBOLS = ("gsis_default_options", "gsis_footprint_bytes", "gsis_create", "gsis_iterate", "gsis_moments",
+SYMBOLS = ("gsis_default_options", "gsis_footprint_bytes", "gsis_create", "gsis_iterate", "gsis_step_async",
+           "gsis_step_wait", "gsis_moments",
            "gsis_residual", "gsis_nwall", "gsis_wall", "gsis_wall_loads", "gsis_kinetic_flux_sum", "gsis_get_f", "gsis_set_f", "gsis_stats",
            "gsis_destroy", "gsis_last_error", "gsis_profile", "gsis_vdf_moments_noalloc")
 
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH):
     L.gsis_create.argtypes = [C.POINTER(Mesh), C.POINTER(Vgrid), C.POINTER(Gas), C.c_double, C.c_double,
                               C.POINTER(Options), C.POINTER(P)]
     L.gsis_iterate.argtypes = [P, C.c_int, C.c_double, C.POINTER(C.c_int), D]
+    L.gsis_step_async.argtypes = [P]
+    L.gsis_step_wait.argtypes = [P, D]
     L.gsis_moments.argtypes = [P, C.c_uint, D, C.c_size_t]
     L.gsis_residual.argtypes = [P, D, C.c_int]
     L.gsis_nwall.argtypes = [P]
@@ -205,6 +208,15 @@ class Solver:
 
     def step(self):
         return self.iterate(1, 0.0)[1]
+
+    def step_async(self):
+        """Enqueue one outer step on the solver's stream; step_wait() returns its eps."""
+        self._check(load().gsis_step_async(self.h))
+
+    def step_wait(self):
+        eps = C.c_double()
+        self._check(load().gsis_step_wait(self.h, C.byref(eps)))
+        return eps.value
 
     def moments(self, mask=F_W):
         per = (6 if mask & F_W else 0) + (18 if mask & F_HALF else 0) + (12 if mask & F_HOT else 0)

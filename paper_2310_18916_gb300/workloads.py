@@ -108,6 +108,22 @@ def cavity(n=128, nv=32, vmax=5.0, lid=0.16, Kn=0.1, omega=0.81, stretch=0.0) ->
                    W0=_uniform_state(n * n), name=f"cavity{n}^2x{nv}^3_Kn{Kn:g}")
 
 
+def serving_cavity(rng, sizes=(32, 48, 64), nvs=(16, 20, 24), kn=(1e-3, 1.0), ma=(0.1, 1.0)) -> Problem:
+    """One request of the serving stream: a lid-driven cavity with the spatial size and velocity
+    count drawn from the lists, Kn log-uniform in kn, lid Mach number uniform in ma (lid speed
+    Ma sqrt(gamma/2) in sqrt(2RT0) units, gamma = 5/3), and a velocity box of half-width
+    max(5, lid + 5 sqrt(T_stag / 2)) with T_stag = 1 + (gamma - 1) Ma^2 / 2."""
+    n = int(rng.choice(sizes))
+    nv = int(rng.choice(nvs))
+    Kn = float(np.exp(rng.uniform(np.log(kn[0]), np.log(kn[1]))))
+    Ma = float(rng.uniform(ma[0], ma[1]))
+    gamma = 5.0 / 3.0
+    lid = Ma * np.sqrt(gamma / 2.0)
+    t_stag = 1.0 + 0.5 * (gamma - 1.0) * Ma * Ma
+    vmax = max(5.0, lid + 5.0 * np.sqrt(t_stag / 2.0))
+    return cavity(n=n, nv=nv, vmax=vmax, lid=lid, Kn=Kn)
+
+
 def box3d(ni=6, nj=5, nk=4, nv=12, vmax=5.0, Kn=0.1, omega=0.81, wall_speed=0.2) -> Problem:
     """Small closed 3D box with one moving wall (z+ moves along x); all walls diffuse at T = 1."""
     nodes = box_nodes(np.linspace(0, 1, ni + 1), np.linspace(0, 0.8, nj + 1), np.linspace(0, 0.6, nk + 1))

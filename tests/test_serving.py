@@ -1,0 +1,111 @@
+"""Scheduling logic of the serving loop on the CPU, with fake solvers and a fake clock:
+first-in first-out admission by footprint and slots, rejection of requests larger than the
+whole budget, results and latencies, percentiles."""
+import numpy as np
+import pytest
+
+from paper_2310_18916_gb300 import serving
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+class FakeSolver:
+    """eps halves every step; every step_wait advances the clock by dt."""
+
+    log = []
+
+    def __init__(self, problem, clock, dt):
+        self.p, self.clock, self.dt, self.k = problem, clock, dt, 0
+        self.pending = False
+        FakeSolver.log.append(("create", problem["name"], clock()))
+
+    def step_async(self):
+        assert not self.pending
+        self.pending = True
+
+    def step_wait(self):
+        assert self.pending
+        self.pending = False
+        self.k += 1
+        self.clock.t += self.dt
+        return 0.5 ** self.k
+
+    def W(self):
+        return np.full((2, 6), float(self.k))
+
+    def close(self):
+        FakeSolver.log.append(("close", self.p["name"], self.clock()))
+
+
+def make_server(budget, slots, clock, dt=0.01):
+    return serving.Server(budget, slots=slots, nsm=152,
+                          make_solver=lambda p, prec, sms, st: FakeSolver(p, clock, dt),
+                          footprint=lambda p, prec: p["bytes"], new_stream=lambda: None, clock=clock,
+                          idle=lambda s: setattr(clock, "t", clock.t + max(s, 1e-3)))
+
+
+def test_fifo_admission_by_footprint_and_slots():
+    FakeSolver.log = []
+    clock = FakeClock()
+    reqs = [serving.Request(i, {"name": f"r{i}", "bytes": b}, a, tol=1.5 * 2 ** -5)
+            for i, (b, a) in enumerate([(60, 0.0), (50, 0.0), (30, 0.0), (10, 0.5), (200, 0.6)])]
+    srv = make_server(100, slots=2, clock=clock)
+    assert srv.macro_sms == 76
+    res = srv.run(reqs)
+    # r0 (60) runs first; r1 (50) does not fit next to it and blocks r2 behind it (FIFO)
+    creates = [name for kind, name, _ in FakeSolver.log if kind == "create"]
+    assert creates == ["r0", "r1", "r2", "r3"]
+    t = {name: tt for kind, name, tt in FakeSolver.log if kind == "create"}
+    c = {name: tt for kind, name, tt in FakeSolver.log if kind == "close"}
+    assert t["r1"] >= c["r0"]
+    assert res[4] is None  # larger than the whole budget
+    for r in res[:4]:
+        assert r.converged and r.steps == 5 and r.eps == 2 ** -5
+        assert r.latency >= r.steps * 0.01 - 1e-12
+        assert r.admitted >= r.arrival
+        assert (r.W == 5.0).all()
+
+
+def test_a_stalled_eps_stops_at_the_precision_floor():
+    class Flat(FakeSolver):
+        def step_wait(self):
+            super().step_wait()
+            return 1e-3  # never improves after the first step
+    clock = FakeClock()
+    srv = serving.Server(10, slots=1, nsm=152, make_solver=lambda p, prec, sms, st: Flat(p, clock, 0.01),
+                         footprint=lambda p, prec: 1, new_stream=lambda: None, clock=clock)
+    res = srv.run([serving.Request(0, {"name": "f"}, 0.0, tol=1e-6, max_steps=100, stall_steps=7)])
+    assert res[0].steps == 8 and res[0].floor and not res[0].converged
+    assert serving.summary(res, clock.t)["at_precision_floor"] == 1
+
+
+def test_idle_until_next_arrival_and_summary():
+    FakeSolver.log = []
+    clock = FakeClock()
+    reqs = [serving.Request(0, {"name": "a", "bytes": 1}, 2.0, tol=0.3)]
+    res = make_server(10, slots=4, clock=clock).run(reqs)
+    assert res[0].admitted >= 2.0
+    s = serving.summary(res, wall_seconds=clock.t)
+    assert s["served"] == 1 and s["converged"] == 1
+    assert s["p50_latency_s"] == pytest.approx(res[0].latency)
+
+
+def test_percentile_matches_numpy():
+    x = np.random.default_rng(1).exponential(1.0, 37)
+    for q in (0, 50, 90, 99, 100):
+        assert serving.percentile(x, q) == pytest.approx(np.percentile(x, q))
+
+
+def test_poisson_requests_are_seeded():
+    mk = lambda rng: {"n": int(rng.integers(10))}
+    a = serving.poisson_requests(20, 2.0, 0, mk)
+    b = serving.poisson_requests(20, 2.0, 0, mk)
+    assert [r.arrival for r in a] == [r.arrival for r in b]
+    gaps = np.diff([0.0] + [r.arrival for r in a])
+    assert (gaps > 0).all() and abs(gaps.mean() - 2.0) < 1.2
