@@ -40,6 +40,7 @@ struct gsis_solver {
   // options
   gsis_options opt{};
   int prec = GSIS_F32;
+  int nvdf = 1;  // reduced VDFs: 1 (Shakhov) or 2 (Rykov)
   double Kn = 0.1, omega = 0.81;
   gsis_gas gas{};
   cudaStream_t stream = nullptr;
@@ -182,6 +183,9 @@ struct gsis_solver {
     a.rho_w = d_rho_w;
     a.wall_uT = d_wall_uT;
     a.f = static_cast<S *>(d_f);
+    a.f1 = nvdf == 2 ? static_cast<S *>(d_f) + (size_t)nslots * nc : nullptr;
+    a.nvdf = nvdf;
+    a.d_r = gas.d_r;
     a.wpart = static_cast<T *>(d_wpart);
     a.nwall = nwall;
     a.nblocks = nblocks;
@@ -206,11 +210,13 @@ struct gsis_solver {
   int reduce_and_finalize(bool closed_scale) {
     int rc = cuda(launch_moments<T, S>(kin_args<T, S>(), mom_bpc, mom_nchunks, d_mp, stream), "moments");
     if (rc) return rc;
-    rc = cuda(launch_reduce<T>(d_mp, mom_nchunks, static_cast<const T *>(d_wpart), d_boct, nblocks, kg, d_wall_cell,
+    rc = cuda(launch_reduce<T>(d_mp, mom_nchunks, nvdf, static_cast<const T *>(d_wpart), d_boct, nblocks, kg, d_wall_cell,
                                d_wall_side, nwall, d_rho_w, d_Zw, d_vol, d_st64, d_mom, d_K, d_wf, stream),
               "reduce");
     if (rc) return rc;
     FinalizeArgs fa{};
+    fa.nvdf = nvdf;
+    fa.d_r = gas.d_r;
     fa.g = kg;
     fa.mom = d_mom;
     fa.st64 = d_st64;
@@ -227,6 +233,10 @@ struct gsis_solver {
 
   int write_state(const double *Wn) {
     StateArgs sa{};
+    sa.nvdf = nvdf;
+    sa.d_r = gas.d_r;
+    sa.Z_r = gas.Z_r;
+    for (int k = 0; k < 4; ++k) sa.A[k] = gas.A[k];
     sa.g = kg;
     sa.Wn = Wn;
     sa.Mh = d_Mh;
@@ -258,6 +268,7 @@ struct gsis_solver {
         st[2] = w[3];
         st[3] = 1.0 / w[4];
         st[4] = w[0] * std::pow(3.14159265358979323846 * w[4], -1.5);
+        if (nvdf == 2) st[29] = gas.d_r * w[5] / 4.0;  // f1 = (d_r Tr / 4) M
       }
     std::vector<T> st0T(st0.begin(), st0.end());
     int rc = upload(d_st64, st0.data(), st0.size() * sizeof(double));
@@ -442,8 +453,11 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     return GSIS_E_INVALID;
   }
   if (o->mode != GSIS_MODE_GSIS && o->mode != GSIS_MODE_DVM) { why = "bad mode"; return GSIS_E_INVALID; }
-  if (g->model == GSIS_RYKOV) { why = "Rykov model is not implemented on the GPU yet"; return GSIS_E_UNSUPPORTED; }
-  if (g->model != GSIS_SHAKHOV) { why = "bad model"; return GSIS_E_INVALID; }
+  if (g->model == GSIS_RYKOV && (!(g->d_r > 0) || !(g->Z_r > 0))) {
+    why = "Rykov needs d_r > 0 and Z_r > 0";
+    return GSIS_E_INVALID;
+  }
+  if (g->model != GSIS_SHAKHOV && g->model != GSIS_RYKOV) { why = "bad model"; return GSIS_E_INVALID; }
   if (o->kin_inv_dt != 0.0) { why = "the GPU kinetic step is steady (kin_inv_dt = 0)"; return GSIS_E_UNSUPPORTED; }
   if (o->n_sweeps != 1) { why = "rectilinear colour sweeps are exact in one pass: n_sweeps must be 1"; return GSIS_E_UNSUPPORTED; }
   const int n[3] = {m->ni, m->nj, m->nk};
@@ -681,9 +695,9 @@ static size_t footprint(const gsis_solver *s) {
   const size_t Sb = s->prec == GSIS_F64 ? 8 : (s->prec == GSIS_BF16 ? 2 : 4);  // VDF storage
   const size_t nc = s->nc;
   size_t b = 0;
-  b += (size_t)s->nslots * nc * Sb;           // f
-  b += (size_t)s->nblocks * (s->nwall + 1) * NFF * T;  // wall partials
-  b += (size_t)64 * nc * (NMOM + NFF) * 8 / 64 + nc * (NMOM + NFF) * 8 * 16;  // moment chunks (bounded)
+  b += (size_t)s->nvdf * s->nslots * nc * Sb;  // f (f0, f1)
+  b += (size_t)s->nblocks * (s->nwall + 1) * NWF * T;  // wall partials
+  b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
   b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 36 + 18 + 3 + 18 + 8 + 18) * 8;  // synthetic-solve work
@@ -697,15 +711,15 @@ static int allocate_and_upload(gsis_solver *s) {
   int rc = 0;
 #define A(ptr, bytes) \
   if (!rc) rc = s->alloc(&(ptr), (bytes))
-  A(s->d_f, (size_t)s->nslots * nc * sizeof(S));
+  A(s->d_f, (size_t)s->nvdf * s->nslots * nc * sizeof(S));
   // moment chunks: enough (cell, chunk) threads to fill the GPU, at most 64 blocks per chunk
   {
     const int want = std::max(1, (int)((160000 + nc - 1) / nc));
     s->mom_bpc = std::max(1, std::min(64, (s->nblocks + want - 1) / want));
     s->mom_nchunks = (s->nblocks + s->mom_bpc - 1) / s->mom_bpc;
   }
-  A(s->d_mp, (size_t)s->mom_nchunks * nc * (NMOM + NFF) * sizeof(double));
-  A(s->d_wpart, (size_t)s->nblocks * (s->nwall + 1) * NFF * sizeof(T));
+  A(s->d_mp, (size_t)s->mom_nchunks * nc * moment_len(s->nvdf) * sizeof(double));
+  A(s->d_wpart, (size_t)s->nblocks * (s->nwall + 1) * NWF * sizeof(T));
   A(s->d_K, nc * 6 * sizeof(double));
   A(s->d_stT, nc * NST * sizeof(T));
   A(s->d_st64, nc * NST * sizeof(double));
@@ -728,7 +742,7 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->d_wall_cell, (size_t)(s->nwall + 1) * sizeof(int));
   A(s->d_wall_side, (size_t)(s->nwall + 1) * sizeof(int));
   A(s->d_wall_sides, 6 * sizeof(int));
-  A(s->d_mom, nc * NMOM * sizeof(double));
+  A(s->d_mom, nc * MOM_STRIDE * sizeof(double));
   A(s->d_wf, (size_t)(s->nwall + 1) * 6 * sizeof(double));
   A(s->d_Mh, nc * 18 * sizeof(double));
   A(s->d_hot, nc * 12 * sizeof(double));
@@ -797,11 +811,12 @@ static int allocate_and_upload(gsis_solver *s) {
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_Zw, 0, 36 * sizeof(double), s->stream), "memset");
   if (!rc)
     rc = s->cuda(launch_wall_constants(s->d_vel64, s->nslots, s->d_wall_uT, s->d_wall_sides,
-                                       (int)s->wall_sides_list.size(), s->d_Z0, s->d_Zw, 0.0, s->stream),
+                                       (int)s->wall_sides_list.size(), s->d_Z0, s->d_Zw,
+                                       s->nvdf == 2 ? s->gas.d_r : 0.0, s->stream),
                  "wall constants");
   if (rc) return rc;
   // kinetic launch shape: one warp per cell of a colour, up to 16 warps, within the register file
-  s->kin_smem = kinetic_smem_bytes<T>(s->kg);
+  s->kin_smem = kinetic_smem_bytes<T>(s->kg, s->nvdf);
   int dev = 0, smem_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -809,6 +824,10 @@ static int allocate_and_upload(gsis_solver *s) {
     return s->fail(GSIS_E_UNSUPPORTED, "largest colour needs %zu bytes of shared memory (limit %d)", s->kin_smem, smem_optin);
   s->kin_warps = std::max(1, std::min(16, s->kg.maxcol / 4));
   if (sizeof(T) == 8) s->kin_warps = std::min(s->kin_warps, 8);
+  int max_warps = 0;
+  rc = s->cuda(kinetic_max_warps<T, S>(s->kg, s->nvdf, &max_warps), "kinetic shape");
+  if (rc) return rc;
+  s->kin_warps = std::max(1, std::min(s->kin_warps, max_warps));
   return GSIS_OK;
 }
 
@@ -823,6 +842,7 @@ extern "C" int gsis_footprint_bytes(const gsis_mesh *mesh, const gsis_vgrid *vgr
   gsis_solver tmp;
   tmp.opt = o;
   tmp.prec = o.precision;
+  tmp.nvdf = gas->model == GSIS_RYKOV ? 2 : 1;
   setup(&tmp, mesh, vgrid);
   *bytes = footprint(&tmp);
   return GSIS_OK;
@@ -869,6 +889,7 @@ extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const
   if (!s) { g_create_error = "out of host memory"; return GSIS_E_OOM; }
   s->opt = o;
   s->prec = o.precision;
+  s->nvdf = gas->model == GSIS_RYKOV ? 2 : 1;
   s->Kn = Kn;
   s->omega = gas->omega;
   s->gas = *gas;
@@ -1027,7 +1048,6 @@ extern "C" int gsis_kinetic_flux_sum(gsis_handle h, double *out, size_t out_len)
 }
 
 extern "C" int gsis_get_f(gsis_handle h, double *f0, double *f1) {
-  (void)f1;
   if (!h || !f0) return GSIS_E_INVALID;
   GSIS_NOT_PENDING(h);
   const size_t bytes = (size_t)h->nc * h->nvc * sizeof(double);
@@ -1036,19 +1056,21 @@ extern "C" int gsis_get_f(gsis_handle h, double *f0, double *f1) {
   int rc = h->cuda(cudaMalloc(&tmp, bytes), "temporary");
   if (!rc) rc = h->cuda(cudaMalloc(&canon, h->nslots * sizeof(int)), "temporary");
   if (!rc) rc = h->upload(canon, h->slot_canon.data(), h->nslots * sizeof(int));
-  if (!rc)
-    rc = GSIS_DISPATCH(h->prec, (h->cuda(launch_export_f<T, S>(h->kin_args<T, S>(), canon, h->nslots, h->nvc, tmp,
+  double *outs[2] = {f0, h->nvdf == 2 ? f1 : nullptr};
+  for (int q = 0; q < 2 && !rc; ++q) {
+    if (!outs[q]) continue;
+    rc = GSIS_DISPATCH(h->prec, (h->cuda(launch_export_f<T, S>(h->kin_args<T, S>(), q, canon, h->nslots, h->nvc, tmp,
                                                                  h->stream),
                                          "export")));
-  if (!rc) rc = h->cuda(cudaMemcpyAsync(f0, tmp, bytes, cudaMemcpyDeviceToHost, h->stream), "copy f");
-  if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+    if (!rc) rc = h->cuda(cudaMemcpyAsync(outs[q], tmp, bytes, cudaMemcpyDeviceToHost, h->stream), "copy f");
+    if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  }
   cudaFree(tmp);
   cudaFree(canon);
   return rc;
 }
 
 extern "C" int gsis_set_f(gsis_handle h, const double *f0, const double *f1) {
-  (void)f1;
   if (!h || !f0) return GSIS_E_INVALID;
   GSIS_NOT_PENDING(h);
   const size_t bytes = (size_t)h->nc * h->nvc * sizeof(double);
@@ -1057,12 +1079,16 @@ extern "C" int gsis_set_f(gsis_handle h, const double *f0, const double *f1) {
   int rc = h->cuda(cudaMalloc(&tmp, bytes), "temporary");
   if (!rc) rc = h->cuda(cudaMalloc(&canon, h->nslots * sizeof(int)), "temporary");
   if (!rc) rc = h->upload(canon, h->slot_canon.data(), h->nslots * sizeof(int));
-  if (!rc) rc = h->upload(tmp, f0, bytes);
-  if (!rc)
-    rc = GSIS_DISPATCH(h->prec, (h->cuda(launch_import_f<T, S>(h->kin_args<T, S>(), canon, h->nslots, h->nvc, tmp,
-                                                                 h->stream),
-                                         "import")));
-  if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  const double *ins[2] = {f0, f1};
+  for (int q = 0; q < h->nvdf && !rc; ++q) {
+    if (ins[q]) rc = h->upload(tmp, ins[q], bytes);
+    else rc = h->cuda(cudaMemsetAsync(tmp, 0, bytes, h->stream), "memset");  // f1 = 0 when not given
+    if (!rc)
+      rc = GSIS_DISPATCH(h->prec, (h->cuda(launch_import_f<T, S>(h->kin_args<T, S>(), q, canon, h->nslots, h->nvc,
+                                                                   tmp, h->stream),
+                                           "import")));
+    if (!rc) rc = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+  }
   cudaFree(tmp);
   cudaFree(canon);
   if (rc) return rc;

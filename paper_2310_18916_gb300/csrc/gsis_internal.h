@@ -8,14 +8,25 @@
 namespace gsis {
 
 constexpr int VB = 32;          // discrete velocities per block (one per lane)
-constexpr int NMOM = 13;        // raw moments about the state velocity: 1, c(3), cc(6), |c|^2 c(3)
-constexpr int NFF = 5;          // face-flux moments: 1, xi(3), |xi|^2/2
-constexpr int NST = 24;         // per-cell kinetic state values:
+constexpr int NMOM = 13;        // raw moments of f0 about the state velocity: 1, c(3), cc(6), |c|^2 c(3)
+constexpr int NMOM1 = 4;        // raw moments of f1 (Rykov) about the state velocity: 1, c(3)
+constexpr int NFF = 5;          // kinetic flux sums: mass, momentum(3), energy (with f1)
+constexpr int NWF = 6;          // wall-flux moments: NFF and the internal energy (f1; 0 for Shakhov)
+// per-cell moment vector of the moments kernel: f0 moments, flux sums, then for Rykov the f1
+// flux sum and the f1 moments
+__host__ __device__ constexpr int moment_len(int nvdf) { return nvdf == 2 ? NMOM + NFF + 1 + NMOM1 : NMOM + NFF; }
+constexpr int NST = 48;         // per-cell kinetic state values:
                                 //  [0..2] u_n, [3] 1/T_n, [4] rho_n (pi T_n)^-3/2 (Maxwellian of W^n),
                                 //  [5..7] u_o, [8] 1/T_o, [9] rho_o (pi T_o)^-3/2 (of W^{n+1/2}),
                                 //  [10] mass scale s, [11] 1/tau, [12..14] Shakhov heat-flux factor,
                                 //  [15] diagonal, [16..18] u_r, [19] 1/T_r, [20] rho_r (pi T_r)^-3/2:
-                                //  the Maxwellian a BF16 VDF is stored relative to, [21..23] unused
+                                //  the Maxwellian an FP32/BF16 VDF is stored relative to,
+                                //  [21] d_r T_r,r / 4 (the f1 reference factor), [22..23] unused,
+                                //  Rykov: [24] 1/T, [25] rho (pi T)^-3/2 with T = (3Tt + d_r Tr)/(3 + d_r),
+                                //  [26..28] 8 q0 / (15 rho T^2), [29] d_r Tr_n / 4, [30] d_r T / 4,
+                                //  [31..33] 2 (pi Tt)^-3/2 qr / Tt, [34..36] 2 (pi T)^-3/2 q1 / T,
+                                //  [37] 1 - 1/Z_r, [38] 1/Z_r, [39] d_r Tr_o / 4, [40..47] unused
+constexpr int NST_RYKOV = 40;   // state values a Rykov kinetic step reads
 constexpr int MAXNP = 13 + 3 * NFF;
 constexpr int GSIS_ERR_DIVERGED = -4;  // same values as GSIS_E_DIVERGED / GSIS_E_TIMEOUT
 constexpr int GSIS_ERR_TIMEOUT = -5;
@@ -80,7 +91,10 @@ struct KinArgs {
   const double *rho_w;   // [nwall]
   const double *wall_uT; // [6][4]: u_w(3), T_w
   S *f;                  // [block][cell][VB] f_raw, updated in place
-  T *wpart;              // [block][wall face][NFF] outgoing wall-flux moments (wall cells only)
+  S *f1;                 // Rykov: the second reduced VDF, same layout (nullptr for Shakhov)
+  int nvdf;              // 1 (Shakhov) or 2 (Rykov)
+  double d_r;            // rotational degrees of freedom (Rykov)
+  T *wpart;              // [block][wall face][NWF] outgoing wall-flux moments (wall cells only)
   int nwall;
   int nblocks;
 };
@@ -89,7 +103,7 @@ struct KinArgs {
 template <typename T, typename S>
 cudaError_t launch_kinetic(const KinArgs<T, S> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s);
 template <typename T>
-size_t kinetic_smem_bytes(const KinGeom &g);
+size_t kinetic_smem_bytes(const KinGeom &g, int nvdf);
 template <typename T, typename S>
 cudaError_t launch_wall_prepass(const KinArgs<T, S> &a, const int *wall_cell, const int *wall_side, int nwall,
                                 const double *Z0, double *rho_w, int nslots, cudaStream_t s);
@@ -98,11 +112,14 @@ cudaError_t launch_moments(const KinArgs<T, S> &a, int blocks_per_chunk, int nch
 template <typename T, typename S>
 cudaError_t launch_init_maxwellian(const KinArgs<T, S> &a, const double *W0, int nblocks, cudaStream_t s);
 template <typename T, typename S>
-cudaError_t launch_export_f(const KinArgs<T, S> &a, const int *slot_canon, int nslots, int nv, double *out,
+cudaError_t launch_export_f(const KinArgs<T, S> &a, int q, const int *slot_canon, int nslots, int nv, double *out,
                             cudaStream_t s);
 template <typename T, typename S>
-cudaError_t launch_import_f(const KinArgs<T, S> &a, const int *slot_canon, int nslots, int nv, const double *in,
+cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon, int nslots, int nv, const double *in,
                             cudaStream_t s);
+// largest block (in warps) the kinetic kernel of this shape launches with (its registers)
+template <typename T, typename S>
+cudaError_t kinetic_max_warps(const KinGeom &g, int nvdf, int *warps);
 
 cudaError_t launch_wall_constants(const double *vel64, int nslots, const double *wall_uT, const int *sides,
                                   int nsides, double *Z0, double *Zw, double d_r, cudaStream_t s);
@@ -111,14 +128,17 @@ cudaError_t launch_wall_constants(const double *vel64, int nslots, const double 
 // K [cell][6] (outward, area-integrated, via the delta-form identity); per-block wall partials
 // -> wf [wall][6] outward kinetic wall flux per unit area.
 template <typename T>
-cudaError_t launch_reduce(const double *mp, int nchunks, const T *wpart, const int8_t *boct, int nblocks,
+cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpart, const int8_t *boct, int nblocks,
                           const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
                           const double *rho_w, const double *Zw, const double *vol, const double *st64,
                           double *mom, double *K, double *wf, cudaStream_t s);
+constexpr int MOM_STRIDE = NMOM + NMOM1;  // per-cell raw moments: f0 then f1
 
 struct FinalizeArgs {
   KinGeom g;
-  const double *mom;     // [cell][NMOM] raw moments about the state velocity
+  const double *mom;     // [cell][MOM_STRIDE] raw moments about the state velocity
+  int nvdf;
+  double d_r;
   const double *st64;    // [cell][NST] FP64 copy of the state (un at [0..2])
   const double *vol;     // [cell]
   double mass_ref;
@@ -151,6 +171,8 @@ struct StateArgs {
   double *st64;           // out FP64 state
   void *stT;              // out state in kernel precision
   int is_float;
+  int nvdf;               // Rykov (2): the state carries the Rykov values
+  double d_r, Z_r, A[4];
 };
 cudaError_t launch_state(const StateArgs &a, cudaStream_t s);
 

@@ -85,6 +85,55 @@ __device__ __forceinline__ T corrected_stored(T stored, const T *st, T x, T y, T
   return corrected(stored, st, x, y, z);
 }
 
+// f^n of the NV reduced VDFs from their stored values, sharing the Maxwellians: f0 as above;
+// f1 (Rykov) carries the internal-energy factor d_r T_r / 4 of each Maxwellian (state values
+// 21, 29, 39), in its storage reference and in Eq. updatef alike.
+template <typename T, typename S, int NV>
+__device__ __forceinline__ void corrected_all(const T *stored, const T *st, T x, T y, T z, T *f) {
+  T cx = x - st[0], cy = y - st[1], cz = z - st[2];
+  const T mn = st[4] * dexp(-(cx * cx + cy * cy + cz * cz) * st[3]);
+  cx = x - st[5]; cy = y - st[6]; cz = z - st[7];
+  const T mo = st[9] * dexp(-(cx * cx + cy * cy + cz * cz) * st[8]);
+  T raw[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) raw[q] = stored[q];
+  if constexpr (StoredRelative<S>::value) {
+    cx = x - st[16]; cy = y - st[17]; cz = z - st[18];
+    const T mr = st[20] * dexp(-(cx * cx + cy * cy + cz * cz) * st[19]);
+    raw[0] += mr;
+    if constexpr (NV == 2) raw[1] += st[21] * mr;
+  }
+  f[0] = st[10] * raw[0] + mn - mo;
+  if constexpr (NV == 2) f[1] = st[10] * raw[1] + st[29] * mn - st[39] * mo;
+}
+
+// Reference distributions of the state W^n (Section 2.2), c = xi - u_n, c2 = |c|^2:
+//   Shakhov: g0 = M_t [1 + A q_t.c (c^2/T_t - 5/2)];
+//   Rykov:   g_q = (1 - 1/Z_r) g_qt + g_qr / Z_r with the translational (T_t) and equilibrium
+//            (T) Maxwellians, heat fluxes q0, q1 and the internal-energy factors (state 24..38).
+// mw returns M_t, the Maxwellian relative storage refers to.
+template <typename T, int NV>
+__device__ __forceinline__ void reference(const T *st, T cx, T cy, T cz, T c2, T &mw, T *g) {
+  const T et = dexp(-c2 * st[3]);
+  mw = st[4] * et;
+  const T g0t = mw * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
+  if constexpr (NV == 1) {
+    g[0] = g0t;
+  } else {
+    const T eT = dexp(-c2 * st[24]);
+    const T g0r = st[25] * eT * ((T)1 + (st[26] * cx + st[27] * cy + st[28] * cz) * (c2 * st[24] - (T)2.5));
+    const T g1t = st[29] * g0t + (st[31] * cx + st[32] * cy + st[33] * cz) * et;
+    const T g1r = st[30] * g0r + (st[34] * cx + st[35] * cy + st[36] * cz) * eT;
+    g[0] = st[37] * g0t + st[38] * g0r;
+    g[1] = st[37] * g1t + st[38] * g1r;
+  }
+}
+
+// state values the kinetic kernels read: Rykov 40; Shakhov 16 (24 with relative storage for
+// the loaders of stored f)
+template <typename S, int NV>
+__host__ __device__ constexpr int stage_state_len() { return NV == 2 ? NST_RYKOV : state_len<S>(); }
+
 // Venkatakrishnan limiter of one cell: min over its faces (and 1) of
 //   (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
 // the face function with numerator and denominator divided by D2; both are positive, so
@@ -154,18 +203,18 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-template <typename T, typename S, int NACT>
+template <typename T, typename S, int NACT, int NV>
 __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const KinGeom &G = A.g;
   T *ring = reinterpret_cast<T *>(smem_raw);
   T *ebuf[3];
   {
-    T *p = ring + (size_t)3 * G.maxcol * VB;
+    T *p = ring + (size_t)3 * G.maxcol * NV * VB;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       ebuf[a] = p;
-      p += (size_t)G.ntrans[a] * VB;
+      p += (size_t)G.ntrans[a] * NV * VB;
     }
   }
   const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -175,30 +224,41 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   const T xi[3] = {vp[0], vp[1], vp[2]};
   const T wv = vp[3];
   const T e2 = (T)0.5 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
-  T axi[3], Mw[3];
+  T axi[3], Mw[3], Mw1[3];
   int upside[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     axi[a] = fabs(xi[a]);
     upside[a] = 2 * a + (sg[a] > 0 ? 0 : 1);
-    Mw[a] = (T)0;
-    if (a < NACT && G.wall_base[upside[a]] >= 0)
+    Mw[a] = Mw1[a] = (T)0;
+    if (a < NACT && G.wall_base[upside[a]] >= 0) {
       Mw[a] = wall_maxwellian<T>(A.wall_uT + 4 * upside[a], xi[0], xi[1], xi[2]);
+      // re-emitted f1 = (d_r T_w / 4) f0 at the wall
+      if constexpr (NV == 2) Mw1[a] = (T)(A.d_r * A.wall_uT[4 * upside[a] + 3] / 4.0) * Mw[a];
+    }
   }
   const int n0 = G.n[0], n1 = G.n[1];
-  S *F = A.f + (size_t)b * G.nc * VB;
+  S *F[NV];
+  F[0] = A.f + (size_t)b * G.nc * VB;
+  if constexpr (NV == 2) F[NV - 1] = A.f1 + (size_t)b * G.nc * VB;
   const int4 *natcell = A.natcell + (size_t)oct * G.nc;
   const T K3 = (T)G.K3;
-  const size_t slot_stride = (size_t)G.maxcol * VB;
+  const size_t slot_stride = (size_t)G.maxcol * NV * VB;
+  constexpr int SL = stage_state_len<S, NV>();
 
   auto stage = [&](int c) {
     const int off = A.col_off[c], cnt = A.col_off[c + 1] - off;
     T *slot = ring + (size_t)(c % 3) * slot_stride;
     for (int p = warp; p < cnt; p += nw) {
       const int cell = __ldg(&natcell[off + p].x);
-      T st[state_len<S>()];
-      load_state<state_len<S>()>(A.st + (size_t)cell * NST, st);
-      slot[p * VB + lane] = corrected_stored<T, S>(Fio<T, S>::ld(F + (size_t)cell * VB + lane), st, xi[0], xi[1], xi[2]);
+      T st[SL];
+      load_state<SL>(A.st + (size_t)cell * NST, st);
+      T stored[NV], f[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(F[q] + (size_t)cell * VB + lane);
+      corrected_all<T, S, NV>(stored, st, xi[0], xi[1], xi[2], f);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) slot[(p * NV + q) * VB + lane] = f[q];
     }
   };
 
@@ -220,80 +280,107 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
       for (int q = 0; q < 2 * NACT; ++q) nb[q] = __ldg(&E.nb[q]);
 #pragma unroll
       for (int q = 0; q < NACT; ++q) trn[q] = __ldg(&E.trn[q]);
-      const T fi = slot0[p * VB + lane];
-      T st[16];
-      load_state(A.st + (size_t)cell * NST, st);
-      // gradient (LSQ, decoupled per axis on a rectilinear grid) and bounds
-      T gr[3], rlo[3], rhi[3], invh[3];
-      T fmax = fi, fmin = fi;
+      T fi[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) fi[q] = slot0[(p * NV + q) * VB + lane];
+      constexpr int CL = NV == 2 ? NST_RYKOV : 16;
+      T st[CL];
+      load_state<CL>(A.st + (size_t)cell * NST, st);
+      // gradient (LSQ, decoupled per axis on a rectilinear grid) and bounds, per VDF
+      T gr[NV][3], rlo[3], rhi[3], invh[3];
+      T fmax[NV], fmin[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) fmax[q] = fmin[q] = fi[q];
       T V = (T)1;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const AxisCell<T> gc = A.ax[a][nat[a]];
         V *= gc.h;
         if (a < NACT) {
-          T fup = fi, fdn = fi;
-          if (nb[2 * a] >= 0) {
-            fup = slotm[nb[2 * a] * VB + lane];
-            fmax = fmax > fup ? fmax : fup;
-            fmin = fmin < fup ? fmin : fup;
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            T fup = fi[q], fdn = fi[q];
+            if (nb[2 * a] >= 0) {
+              fup = slotm[(nb[2 * a] * NV + q) * VB + lane];
+              fmax[q] = fmax[q] > fup ? fmax[q] : fup;
+              fmin[q] = fmin[q] < fup ? fmin[q] : fup;
+            }
+            if (nb[2 * a + 1] >= 0) {
+              fdn = slotp[(nb[2 * a + 1] * NV + q) * VB + lane];
+              fmax[q] = fmax[q] > fdn ? fmax[q] : fdn;
+              fmin[q] = fmin[q] < fdn ? fmin[q] : fdn;
+            }
+            const T flo = sg[a] > 0 ? fup : fdn, fhi = sg[a] > 0 ? fdn : fup;
+            gr[q][a] = gc.clo * (flo - fi[q]) + gc.chi * (fhi - fi[q]);
           }
-          if (nb[2 * a + 1] >= 0) {
-            fdn = slotp[nb[2 * a + 1] * VB + lane];
-            fmax = fmax > fdn ? fmax : fdn;
-            fmin = fmin < fdn ? fmin : fdn;
-          }
-          const T flo = sg[a] > 0 ? fup : fdn, fhi = sg[a] > 0 ? fdn : fup;
-          gr[a] = gc.clo * (flo - fi) + gc.chi * (fhi - fi);
           rlo[a] = gc.rlo;
           rhi[a] = gc.rhi;
           invh[a] = gc.invh;
         }
       }
-      const T phi = venkat_phi<T, NACT>(fi, fmax, fmin, gr, rlo, rhi, K3 * V);
-      // reference distribution g_0t of the state W^n
+      T phi[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) phi[q] = venkat_phi<T, NACT>(fi[q], fmax[q], fmin[q], gr[q], rlo, rhi, K3 * V);
+      // reference distributions of the state W^n
       const T cx = xi[0] - st[0], cy = xi[1] - st[1], cz = xi[2] - st[2];
       const T c2 = cx * cx + cy * cy + cz * cz;
-      const T mw = st[4] * dexp(-c2 * st[3]);  // Maxwellian of W^n
-      const T g = mw * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
-      T acc = (g - fi) * st[11];
+      T mw, g[NV];  // mw: Maxwellian of W^n
+      reference<T, NV>(st, cx, cy, cz, c2, mw, g);
+      T acc[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) acc[q] = (g[q] - fi[q]) * st[11];
       T D = st[15];
-      T fout[3];
+      T fout[NV][3];
 #pragma unroll
       for (int a = 0; a < NACT; ++a) {
-        fout[a] = fi + phi * gr[a] * (sg[a] > 0 ? rhi[a] : rlo[a]);
-        T ein;
-        if (nb[2 * a] >= 0) {
-          ein = ebuf[a][trn[a] * VB + lane];
-        } else {
-          // upwind boundary: the natural transverse index of the wall face
-          const int trw = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
-          ein = (T)A.rho_w[G.wall_base[upside[a]] + trw] * Mw[a];
-        }
         const T k = axi[a] * invh[a];
         D += k;
-        acc -= k * (fout[a] - ein);
+        T rho_w = (T)0;
+        if (nb[2 * a] < 0) {
+          // upwind boundary: the natural transverse index of the wall face
+          const int trw = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
+          rho_w = (T)A.rho_w[G.wall_base[upside[a]] + trw];
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          fout[q][a] = fi[q] + phi[q] * gr[q][a] * (sg[a] > 0 ? rhi[a] : rlo[a]);
+          const T ein = nb[2 * a] >= 0 ? ebuf[a][(trn[a] * NV + q) * VB + lane] : rho_w * (q == 0 ? Mw[a] : Mw1[a]);
+          acc[q] -= k * (fout[q][a] - ein);
+        }
       }
-      const T df = ddiv(acc, D);
-      Fio<T, S>::st(F + (size_t)cell * VB + lane, StoredRelative<S>::value ? fi + df - mw : fi + df);
+      T df[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        df[q] = ddiv(acc[q], D);
+        // relative storage keeps the deviation from the reference: M_t for f0, (d_r Tr_n / 4) M_t for f1
+        const T ref = q == 0 ? mw : st[NV == 2 ? 29 : 0] * mw;
+        Fio<T, S>::st(F[q] + (size_t)cell * VB + lane, StoredRelative<S>::value ? fi[q] + df[q] - ref : fi[q] + df[q]);
+      }
 #pragma unroll
       for (int a = 0; a < NACT; ++a) {
-        const T eout = fout[a] + df;
-        ebuf[a][trn[a] * VB + lane] = eout;
+        T eout[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          eout[q] = fout[q][a] + df[q];
+          ebuf[a][(trn[a] * NV + q) * VB + lane] = eout[q];
+        }
         if (nb[2 * a + 1] < 0) {
           // outflow face on the domain boundary (a wall): moments of the flux towards the wall
           const int trw = a == 0 ? nat[1] + n1 * nat[2] : (a == 1 ? nat[0] + n0 * nat[2] : nat[0] + n0 * nat[1]);
           const int wid = G.wall_base[2 * a + (sg[a] > 0 ? 1 : 0)] + trw;
-          const T fl = wv * xi[a] * eout;
+          const T fl = wv * xi[a] * eout[0];
+          const T e1 = NV == 2 ? wv * xi[a] * eout[NV - 1] : (T)0;
           const T m0 = warp_sum(fl), m1 = warp_sum(fl * xi[0]), m2 = warp_sum(fl * xi[1]);
-          const T m3 = warp_sum(fl * xi[2]), m4 = warp_sum(fl * e2);
+          const T m3 = warp_sum(fl * xi[2]), m4 = warp_sum(fl * e2 + e1);
+          const T m5 = NV == 2 ? warp_sum(e1) : (T)0;
           if (lane == 0) {
-            T *W = A.wpart + ((size_t)b * A.nwall + wid) * NFF;
+            T *W = A.wpart + ((size_t)b * A.nwall + wid) * NWF;
             W[0] = m0;
             W[1] = m1;
             W[2] = m2;
             W[3] = m3;
             W[4] = m4;
+            W[5] = m5;
           }
         }
       }
@@ -303,18 +390,30 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
 }
 
 template <typename T>
-size_t kinetic_smem_bytes(const KinGeom &g) {
+size_t kinetic_smem_bytes(const KinGeom &g, int nvdf) {
   size_t n = (size_t)3 * g.maxcol * VB;
   for (int a = 0; a < 3; ++a) n += (size_t)g.ntrans[a] * VB;
-  return n * sizeof(T);
+  return n * nvdf * sizeof(T);
+}
+
+template <typename T, typename S>
+static void (*kinetic_fn(int nact, int nvdf))(const KinArgs<T, S>) {
+  if (nvdf == 2)
+    return nact == 1 ? kinetic_kernel<T, S, 1, 2> : (nact == 2 ? kinetic_kernel<T, S, 2, 2> : kinetic_kernel<T, S, 3, 2>);
+  return nact == 1 ? kinetic_kernel<T, S, 1, 1> : (nact == 2 ? kinetic_kernel<T, S, 2, 1> : kinetic_kernel<T, S, 3, 1>);
+}
+
+template <typename T, typename S>
+cudaError_t kinetic_max_warps(const KinGeom &g, int nvdf, int *warps) {
+  cudaFuncAttributes attr;
+  cudaError_t e = cudaFuncGetAttributes(&attr, kinetic_fn<T, S>(g.nact, nvdf));
+  if (e == cudaSuccess) *warps = attr.maxThreadsPerBlock / 32;
+  return e;
 }
 
 template <typename T, typename S>
 cudaError_t launch_kinetic(const KinArgs<T, S> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s) {
-  void (*k)(const KinArgs<T, S>) = nullptr;
-  if (a.g.nact == 1) k = kinetic_kernel<T, S, 1>;
-  else if (a.g.nact == 2) k = kinetic_kernel<T, S, 2>;
-  else k = kinetic_kernel<T, S, 3>;
+  void (*k)(const KinArgs<T, S>) = kinetic_fn<T, S>(a.g.nact, a.nvdf);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<nblocks, nwarps * 32, smem, s>>>(a);
@@ -455,16 +554,16 @@ cudaError_t launch_wall_constants(const double *vel64, int nslots, const double 
 //   sum over the cell's faces of the outward kinetic flux = V sum_v w phi (g^n - f^{n+1/2}) / tau,
 // the only kinetic-flux information the synthetic solve needs.  Sums over one block (32 terms)
 // are plain, and are added into compensated (Kahan) accumulators across blocks.
-template <typename T>
+template <typename T, int N>
 struct MomAcc {
-  T s[NMOM + NFF], c[NMOM + NFF];
+  T s[N], c[N];
   __device__ void zero() {
 #pragma unroll
-    for (int k = 0; k < NMOM + NFF; ++k) s[k] = c[k] = (T)0;
+    for (int k = 0; k < N; ++k) s[k] = c[k] = (T)0;
   }
   __device__ void add(const T *x) {
 #pragma unroll
-    for (int k = 0; k < NMOM + NFF; ++k) {
+    for (int k = 0; k < N; ++k) {
       const T y = x[k] - c[k];
       const T t = s[k] + y;
       c[k] = (t - s[k]) - y;
@@ -514,8 +613,9 @@ __device__ __forceinline__ void load_block_f<double, double>(const double *p, do
   }
 }
 
-template <typename T, typename S>
+template <typename T, typename S, int NV>
 __global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T, S> A, int blocks_per_chunk, double *mp) {
+  constexpr int NP = moment_len(NV);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *svel = reinterpret_cast<T *>(smem_raw);  // [blocks_per_chunk * VB][4]
   const KinGeom &G = A.g;
@@ -526,23 +626,30 @@ __global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T, S> A, int
   __syncthreads();
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= G.nc) return;
-  T st[16];
-  load_state(A.st + (size_t)cell * NST, st);
-  MomAcc<T> acc;
+  constexpr int CL = NV == 2 ? NST_RYKOV : 16;
+  T st[CL];
+  load_state<CL>(A.st + (size_t)cell * NST, st);
+  MomAcc<T, NP> acc;
   acc.zero();
   for (int bb = 0; bb < nb; ++bb) {
-    T f[VB];
+    T f[VB], f1[NV == 2 ? VB : 1];
     load_block_f<T, S>(A.f + ((size_t)(b0 + bb) * G.nc + cell) * VB, f);
-    T sum[NMOM + NFF];
+    if constexpr (NV == 2) load_block_f<T, S>(A.f1 + ((size_t)(b0 + bb) * G.nc + cell) * VB, f1);
+    T sum[NP];
 #pragma unroll
-    for (int k = 0; k < NMOM + NFF; ++k) sum[k] = (T)0;
+    for (int k = 0; k < NP; ++k) sum[k] = (T)0;
 #pragma unroll
     for (int l = 0; l < VB; ++l) {
       const T *v = svel + (bb * VB + l) * 4;
       const T x = v[0], y = v[1], z = v[2], w = v[3];
       const T cx = x - st[0], cy = y - st[1], cz = z - st[2];
       const T c2 = cx * cx + cy * cy + cz * cz;
-      const T mw = st[4] * dexp(-c2 * st[3]);  // Maxwellian of W^n, the storage reference of this step
+      T mw, g[NV];  // Maxwellian of W^n (the storage reference of this step) and the reference
+      if constexpr (NV == 1) {
+        mw = st[4] * dexp(-c2 * st[3]);
+      } else {
+        reference<T, NV>(st, cx, cy, cz, c2, mw, g);
+      }
       const T wf = w * (StoredRelative<S>::value ? f[l] + mw : f[l]);
       sum[0] += wf;
       sum[1] += wf * cx;
@@ -557,30 +664,43 @@ __global__ void __launch_bounds__(128) moments_kernel(const KinArgs<T, S> A, int
       sum[10] += wf * c2 * cx;
       sum[11] += wf * c2 * cy;
       sum[12] += wf * c2 * cz;
-      const T shak = (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5);
-      // w (g - f): with relative storage g - f = M shak - (f - M) needs no difference of O(1)
-      // values (the sum is multiplied by 1/tau, which at small Kn would amplify that round-off)
-      const T d = StoredRelative<S>::value ? w * (mw * shak - f[l]) : w * (mw * ((T)1 + shak)) - wf;
+      T d, d1 = (T)0;
+      if constexpr (NV == 1) {
+        const T shak = (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5);
+        // w (g - f): with relative storage g - f = M shak - (f - M) needs no difference of O(1)
+        // values (the sum is multiplied by 1/tau, which at small Kn would amplify that round-off)
+        d = StoredRelative<S>::value ? w * (mw * shak - f[l]) : w * (mw * ((T)1 + shak)) - wf;
+      } else {
+        const T wf1 = w * (StoredRelative<S>::value ? f1[l] + st[29] * mw : f1[l]);
+        d = w * g[0] - wf;
+        d1 = w * g[NV - 1] - wf1;
+        sum[NMOM + NFF + 1] += wf1;
+        sum[NMOM + NFF + 2] += wf1 * cx;
+        sum[NMOM + NFF + 3] += wf1 * cy;
+        sum[NMOM + NFF + 4] += wf1 * cz;
+        sum[NMOM + NFF] += d1;
+      }
       sum[13] += d;
       sum[14] += d * x;
       sum[15] += d * y;
       sum[16] += d * z;
-      sum[17] += d * (T)0.5 * (x * x + y * y + z * z);
+      sum[17] += d * (T)0.5 * (x * x + y * y + z * z) + d1;
     }
     acc.add(sum);
   }
-  double *out = mp + ((size_t)chunk * G.nc + cell) * (NMOM + NFF);
+  double *out = mp + ((size_t)chunk * G.nc + cell) * NP;
 #pragma unroll
-  for (int k = 0; k < NMOM + NFF; ++k) out[k] = (double)acc.s[k] - (double)acc.c[k];
+  for (int k = 0; k < NP; ++k) out[k] = (double)acc.s[k] - (double)acc.c[k];
 }
 
 template <typename T, typename S>
 cudaError_t launch_moments(const KinArgs<T, S> &a, int blocks_per_chunk, int nchunks, double *mp, cudaStream_t s) {
   const size_t smem = (size_t)blocks_per_chunk * VB * 4 * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(moments_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto k = a.nvdf == 2 ? moments_kernel<T, S, 2> : moments_kernel<T, S, 1>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.nc + 127) / 128, nchunks);
-  moments_kernel<T, S><<<grid, 128, smem, s>>>(a, blocks_per_chunk, mp);
+  k<<<grid, 128, smem, s>>>(a, blocks_per_chunk, mp);
   return cudaGetLastError();
 }
 
@@ -602,12 +722,14 @@ __global__ void init_maxwellian_kernel(const KinArgs<T, S> A, const double *W0) 
   const double *w0 = W0 + 6 * (size_t)cell;
   const T C = (T)(w0[0] * pow(3.14159265358979323846 * w0[4], -1.5)), invT = (T)(1.0 / w0[4]);
   const T ux = (T)w0[1], uy = (T)w0[2], uz = (T)w0[3];
+  const T c1 = (T)(A.d_r * w0[5] / 4.0);  // f1 = (d_r Tr / 4) f0 (Rykov)
   for (int b = 0; b < A.nblocks; ++b) {
     const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
     const T cx = vp[0] - ux, cy = vp[1] - uy, cz = vp[2] - uz;
     // relative storage: f is exactly the reference Maxwellian M(W0), stored as a zero deviation
     const T f = StoredRelative<S>::value ? (T)0 : C * accurate_exp(-(cx * cx + cy * cy + cz * cz) * invT);
     Fio<T, S>::st(A.f + ((size_t)b * G.nc + cell) * VB + lane, f);
+    if (A.nvdf == 2) Fio<T, S>::st(A.f1 + ((size_t)b * G.nc + cell) * VB + lane, c1 * f);
   }
 }
 
@@ -623,60 +745,68 @@ cudaError_t launch_init_maxwellian(const KinArgs<T, S> &a, const double *W0, int
 // Canonical [cell][v] FP64 <-> internal [block][cell][lane].  Export applies the pending
 // correction (the returned f is the VDF the next kinetic step starts from).
 template <typename T, typename S>
-__global__ void export_f_kernel(const KinArgs<T, S> A, const int *slot_canon, int nslots, int nv, double *out) {
+__global__ void export_f_kernel(const KinArgs<T, S> A, int q, const int *slot_canon, int nslots, int nv, double *out) {
   const size_t n = (size_t)A.g.nc * nslots;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
     const int slot = (int)(idx % nslots);
     const int cell = (int)(idx / nslots);
     const T *vp = A.vel + (size_t)slot * 4;
     if (!(vp[3] > (T)0)) continue;
-    T st[state_len<S>()];
-    load_state<state_len<S>()>(A.st + (size_t)cell * NST, st);
+    T st[NST_RYKOV];
+    load_state<NST_RYKOV>(A.st + (size_t)cell * NST, st);
     const int blk = slot / VB, ln = slot % VB;
-    const T f = corrected_stored<T, S>(Fio<T, S>::ld(A.f + ((size_t)blk * A.g.nc + cell) * VB + ln), st, vp[0], vp[1], vp[2]);
-    out[(size_t)cell * nv + slot_canon[slot]] = (double)f;
+    const size_t at = ((size_t)blk * A.g.nc + cell) * VB + ln;
+    T stored[2] = {Fio<T, S>::ld(A.f + at), (T)0}, f[2];
+    if (A.nvdf == 2) {
+      stored[1] = Fio<T, S>::ld(A.f1 + at);
+      corrected_all<T, S, 2>(stored, st, vp[0], vp[1], vp[2], f);
+    } else {
+      corrected_all<T, S, 1>(stored, st, vp[0], vp[1], vp[2], f);
+    }
+    out[(size_t)cell * nv + slot_canon[slot]] = (double)f[q];
   }
 }
 
 template <typename T, typename S>
-__global__ void import_f_kernel(const KinArgs<T, S> A, const int *slot_canon, int nslots, int nv, const double *in) {
+__global__ void import_f_kernel(const KinArgs<T, S> A, int q, const int *slot_canon, int nslots, int nv, const double *in) {
   const size_t n = (size_t)A.g.nc * nslots;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
     const int slot = (int)(idx % nslots);
     const int cell = (int)(idx / nslots);
     const int blk = slot / VB, ln = slot % VB;
-    Fio<T, S>::st(A.f + ((size_t)blk * A.g.nc + cell) * VB + ln, (T)in[(size_t)cell * nv + slot_canon[slot]]);
+    Fio<T, S>::st((q ? A.f1 : A.f) + ((size_t)blk * A.g.nc + cell) * VB + ln, (T)in[(size_t)cell * nv + slot_canon[slot]]);
   }
 }
 
 template <typename T, typename S>
-cudaError_t launch_export_f(const KinArgs<T, S> &a, const int *slot_canon, int nslots, int nv, double *out,
+cudaError_t launch_export_f(const KinArgs<T, S> &a, int q, const int *slot_canon, int nslots, int nv, double *out,
                             cudaStream_t s) {
-  export_f_kernel<T, S><<<1024, 256, 0, s>>>(a, slot_canon, nslots, nv, out);
+  export_f_kernel<T, S><<<1024, 256, 0, s>>>(a, q, slot_canon, nslots, nv, out);
   return cudaGetLastError();
 }
 
 template <typename T, typename S>
-cudaError_t launch_import_f(const KinArgs<T, S> &a, const int *slot_canon, int nslots, int nv, const double *in,
+cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon, int nslots, int nv, const double *in,
                             cudaStream_t s) {
-  import_f_kernel<T, S><<<1024, 256, 0, s>>>(a, slot_canon, nslots, nv, in);
+  import_f_kernel<T, S><<<1024, 256, 0, s>>>(a, q, slot_canon, nslots, nv, in);
   return cudaGetLastError();
 }
 
 #define GSIS_INST(T, S)                                                                                         \
   template cudaError_t launch_kinetic<T, S>(const KinArgs<T, S> &, int, int, size_t, cudaStream_t);             \
+  template cudaError_t kinetic_max_warps<T, S>(const KinGeom &, int, int *);                                     \
   template cudaError_t launch_wall_prepass<T, S>(const KinArgs<T, S> &, const int *, const int *, int,           \
                                                  const double *, double *, int, cudaStream_t);                   \
   template cudaError_t launch_moments<T, S>(const KinArgs<T, S> &, int, int, double *, cudaStream_t);           \
   template cudaError_t launch_init_maxwellian<T, S>(const KinArgs<T, S> &, const double *, int, cudaStream_t);   \
-  template cudaError_t launch_export_f<T, S>(const KinArgs<T, S> &, const int *, int, int, double *,            \
+  template cudaError_t launch_export_f<T, S>(const KinArgs<T, S> &, int, const int *, int, int, double *,       \
                                              cudaStream_t);                                                      \
-  template cudaError_t launch_import_f<T, S>(const KinArgs<T, S> &, const int *, int, int, const double *,      \
+  template cudaError_t launch_import_f<T, S>(const KinArgs<T, S> &, int, const int *, int, int, const double *, \
                                              cudaStream_t);
 GSIS_INST(float, float)
 GSIS_INST(double, double)
 GSIS_INST(float, __nv_bfloat16)
-template size_t kinetic_smem_bytes<float>(const KinGeom &);
-template size_t kinetic_smem_bytes<double>(const KinGeom &);
+template size_t kinetic_smem_bytes<float>(const KinGeom &, int);
+template size_t kinetic_smem_bytes<double>(const KinGeom &, int);
 
 }  // namespace gsis

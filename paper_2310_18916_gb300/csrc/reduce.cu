@@ -15,21 +15,27 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 }  // namespace
 
-// Chunk partials [chunk][cell][18] -> mom [cell][13] (raw, about the state velocity) and
+// Chunk partials [chunk][cell][np] -> mom [cell][MOM_STRIDE] (raw, about the state velocity:
+// f0 then, Rykov, f1) and
 //   K [cell][k] = V sum_v w phi_k (g^n - f^{n+1/2}) / tau = sum over the cell's faces of the
-//   outward kinetic face flux (mass, momentum, energy; k = 5 internal energy: 0 here).
-__global__ void reduce_moments_kernel(const double *mp, int nchunks, int nc, const double *vol, const double *st64,
-                                      double *mom, double *K) {
-  const size_t n = (size_t)nc * (NMOM + NFF);
+//   outward kinetic face flux (mass, momentum, energy, internal energy; the last 0 for Shakhov).
+__global__ void reduce_moments_kernel(const double *mp, int nchunks, int nc, int np, const double *vol,
+                                      const double *st64, double *mom, double *K) {
+  const size_t n = (size_t)nc * np;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const int cell = (int)(idx / (NMOM + NFF)), k = (int)(idx % (NMOM + NFF));
+    const int cell = (int)(idx / np), k = (int)(idx % np);
     double acc = 0.0;
-    for (int ch = 0; ch < nchunks; ++ch) acc += mp[((size_t)ch * nc + cell) * (NMOM + NFF) + k];
+    for (int ch = 0; ch < nchunks; ++ch) acc += mp[((size_t)ch * nc + cell) * np + k];
+    const double kf = vol[cell] * st64[(size_t)cell * NST + 11];
     if (k < NMOM) {
-      mom[(size_t)cell * NMOM + k] = acc;
+      mom[(size_t)cell * MOM_STRIDE + k] = acc;
+    } else if (k < NMOM + NFF) {
+      K[(size_t)cell * 6 + (k - NMOM)] = kf * acc;
+      if (k == NMOM && np == NMOM + NFF) K[(size_t)cell * 6 + 5] = 0.0;
+    } else if (k == NMOM + NFF) {
+      K[(size_t)cell * 6 + 5] = kf * acc;
     } else {
-      K[(size_t)cell * 6 + (k - NMOM)] = vol[cell] * acc * st64[(size_t)cell * NST + 11];
-      if (k == NMOM) K[(size_t)cell * 6 + 5] = 0.0;
+      mom[(size_t)cell * MOM_STRIDE + NMOM + (k - NMOM - NFF - 1)] = acc;
     }
   }
 }
@@ -39,44 +45,45 @@ __global__ void reduce_moments_kernel(const double *mp, int nchunks, int nc, con
 template <typename T>
 __global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nblocks, int nwall, const int *wall_side,
                                    const double *rho_w, const double *Zw, double *wf) {
-  const int n = nwall * NFF;
+  const int n = nwall * NWF;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int w = idx / NFF, m = idx % NFF;
+    const int w = idx / NWF, m = idx % NWF;
     const int side = wall_side[w], a = side / 2;
     const bool plus = side & 1;
     double out = 0.0;
     for (int b = 0; b < nblocks; ++b) {
       const bool neg = (boct[b] >> a) & 1;
       if (neg == plus) continue;  // this block's velocities move away from the wall
-      out += (double)wpart[((size_t)b * nwall + w) * NFF + m];
+      out += (double)wpart[((size_t)b * nwall + w) * NWF + m];
     }
     const double tot = out + rho_w[w] * Zw[6 * side + m];
     wf[(size_t)w * 6 + m] = plus ? tot : -tot;
-    if (m == 0) wf[(size_t)w * 6 + 5] = 0.0;
   }
 }
 
 template <typename T>
-cudaError_t launch_reduce(const double *mp, int nchunks, const T *wpart, const int8_t *boct, int nblocks,
+cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpart, const int8_t *boct, int nblocks,
                           const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
                           const double *rho_w, const double *Zw, const double *vol, const double *st64,
                           double *mom, double *K, double *wf, cudaStream_t s) {
   (void)wall_cell;
-  const size_t n = (size_t)g.nc * (NMOM + NFF);
+  const int np = moment_len(nvdf);
+  const size_t n = (size_t)g.nc * np;
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 16) grid = 152 * 16;
-  reduce_moments_kernel<<<grid, 256, 0, s>>>(mp, nchunks, g.nc, vol, st64, mom, K);
+  reduce_moments_kernel<<<grid, 256, 0, s>>>(mp, nchunks, g.nc, np, vol, st64, mom, K);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nwall == 0 || wpart == nullptr) return e;
-  reduce_wall_kernel<T><<<(nwall * NFF + 255) / 256, 256, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw, wf);
+  reduce_wall_kernel<T><<<(nwall * NWF + 255) / 256, 256, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw, wf);
   return cudaGetLastError();
 }
-template cudaError_t launch_reduce<float>(const double *, int, const float *, const int8_t *, int, const KinGeom &,
+template cudaError_t launch_reduce<float>(const double *, int, int, const float *, const int8_t *, int, const KinGeom &,
                                           const int *, const int *, int, const double *, const double *,
                                           const double *, const double *, double *, double *, double *, cudaStream_t);
-template cudaError_t launch_reduce<double>(const double *, int, const double *, const int8_t *, int, const KinGeom &,
-                                           const int *, const int *, int, const double *, const double *,
-                                           const double *, const double *, double *, double *, double *, cudaStream_t);
+template cudaError_t launch_reduce<double>(const double *, int, int, const double *, const int8_t *, int,
+                                           const KinGeom &, const int *, const int *, int, const double *,
+                                           const double *, const double *, const double *, double *, double *,
+                                           double *, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------
 // Raw moments about the state velocity un -> rho, u, Tt, sigma, q about the mean velocity.
@@ -89,7 +96,7 @@ __global__ void finalize_kernel(FinalizeArgs a) {
   double mloc = 0.0;
   const int nc = a.g.nc;
   for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < nc; cell += gridDim.x * blockDim.x) {
-    const double *S = a.mom + (size_t)cell * NMOM;
+    const double *S = a.mom + (size_t)cell * MOM_STRIDE;
     const double *un = a.st64 + (size_t)cell * NST;
     const double rho = S[0];
     const double d[3] = {S[1] / rho, S[2] / rho, S[3] / rho};
@@ -104,7 +111,8 @@ __global__ void finalize_kernel(FinalizeArgs a) {
     M[0] = rho;
     for (int i = 0; i < 3; ++i) M[1 + i] = un[i] + d[i];
     M[4] = 2.0 * trP / (3.0 * rho);
-    M[5] = M[4];
+    // Rykov: (d_r / 2) rho R Tr = sum w f1, qr = sum w (c - d) f1 about the mean velocity
+    M[5] = a.nvdf == 2 ? S[NMOM] / (a.d_r * rho / 4.0) : M[4];
     M[6] = P[0][0] - trP / 3.0;
     M[7] = P[1][1] - trP / 3.0;
     M[8] = P[2][2] - trP / 3.0;
@@ -114,9 +122,10 @@ __global__ void finalize_kernel(FinalizeArgs a) {
     for (int i = 0; i < 3; ++i) {
       const double S2d = S2[i][0] * d[0] + S2[i][1] * d[1] + S2[i][2] * d[2];
       M[12 + i] = 0.5 * (S[10 + i] - trS2 * d[i] - 2.0 * S2d + 2.0 * rho * dd * d[i]);
-      M[15 + i] = 0.0;
+      M[15 + i] = a.nvdf == 2 ? S[NMOM + 1 + i] - d[i] * S[NMOM] : 0.0;
     }
-    if (!(rho > 0.0) || !(M[4] > 0.0) || !isfinite(M[12]) || !isfinite(M[13]) || !isfinite(M[14])) atomicCAS(a.err, 0, GSIS_ERR_DIVERGED);
+    if (!(rho > 0.0) || !(M[4] > 0.0) || !(M[5] > 0.0) || !isfinite(M[12]) || !isfinite(M[13]) || !isfinite(M[14]))
+      atomicCAS(a.err, 0, GSIS_ERR_DIVERGED);
     mloc += rho * a.vol[cell];
   }
   red[threadIdx.x] = mloc;
@@ -235,8 +244,10 @@ __global__ void state_kernel(StateArgs a) {
     const double *W = a.Wn + (size_t)cell * 6;
     const double *M = a.Mh + (size_t)cell * 18;
     double *st = a.st64 + (size_t)cell * NST;
-    // the Maxwellian of the step that just stored f becomes the storage reference of BF16 VDFs
+    // the Maxwellian of the step that just stored f becomes the storage reference of relative
+    // VDF storage (f1: times its internal-energy factor)
     for (int q = 0; q < 5; ++q) st[16 + q] = st[q];
+    st[21] = st[29];
     const double rho = W[0], Tt = W[4];
     st[0] = W[1];
     st[1] = W[2];
@@ -256,7 +267,30 @@ __global__ void state_kernel(StateArgs a) {
     st[13] = A * M[13];
     st[14] = A * M[14];
     st[15] = a.kin_inv_dt + invtau;
-    for (int q = 21; q < NST; ++q) st[q] = 0.0;
+    for (int q = 22; q < NST; ++q) st[q] = 0.0;
+    if (a.nvdf == 2) {
+      // Rykov (Section 2.2): equilibrium temperature T, heat fluxes q0, q1 from the kinetic
+      // qt, qr through the A matrix and Z_r, internal-energy factors d_r T / 4
+      const double dr = a.d_r, Zr = a.Z_r, Tr = W[5];
+      const double Teq = (3.0 * Tt + dr * Tr) / (3.0 + dr);
+      const double *qt = M + 12, *qr = M + 15;
+      const double At = 2.0 * pow(kPi * Tt, -1.5) / Tt, AT = 2.0 * pow(kPi * Teq, -1.5) / Teq;
+      st[24] = 1.0 / Teq;
+      st[25] = rho * pow(kPi * Teq, -1.5);
+      const double A0 = 8.0 / (15.0 * rho * Teq * Teq);
+      for (int k = 0; k < 3; ++k) {
+        const double q0 = ((2.0 - 3.0 * a.A[0]) * Zr + 1.0) * qt[k] - 3.0 * a.A[1] * Zr * qr[k];
+        const double q1 = -a.A[2] * Zr * qt[k] + (-a.A[3] * Zr + 1.0) * qr[k];
+        st[26 + k] = A0 * q0;
+        st[31 + k] = At * qr[k];
+        st[34 + k] = AT * q1;
+      }
+      st[29] = dr * Tr / 4.0;
+      st[30] = dr * Teq / 4.0;
+      st[37] = 1.0 - 1.0 / Zr;
+      st[38] = 1.0 / Zr;
+      st[39] = dr * M[5] / 4.0;
+    }
     T *out = reinterpret_cast<T *>(a.stT) + (size_t)cell * NST;
     for (int q = 0; q < NST; ++q) out[q] = (T)st[q];
   }

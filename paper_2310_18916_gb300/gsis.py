@@ -263,14 +263,17 @@ class Solver:
         self._check(load().gsis_kinetic_flux_sum(self.h, _p(out), out.size))
         return out
 
-    def get_f(self):
+    def get_f(self, both=False):
+        """f0 [cell][v]; with both=True (Rykov) the pair (f0, f1)."""
         f0 = np.empty((self.nc, self.nv))
-        self._check(load().gsis_get_f(self.h, _p(f0), None))
-        return f0
+        f1 = np.empty((self.nc, self.nv)) if both else None
+        self._check(load().gsis_get_f(self.h, _p(f0), _p(f1) if both else None))
+        return (f0, f1) if both else f0
 
-    def set_f(self, f0):
+    def set_f(self, f0, f1=None):
         f0 = np.ascontiguousarray(f0, dtype=np.float64)
-        self._check(load().gsis_set_f(self.h, _p(f0), None))
+        f1 = None if f1 is None else np.ascontiguousarray(f1, dtype=np.float64)
+        self._check(load().gsis_set_f(self.h, _p(f0), None if f1 is None else _p(f1)))
 
     def profile(self, enable=True, reset=False):
         """Per-phase device milliseconds (wall, kinetic, reduce, synthetic, state), steps, launches."""
