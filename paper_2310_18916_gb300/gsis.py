@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgsis.so")
 
 D = C.POINTER(C.c_double)
-GSIS_OK, GSIS_E_NOT_CONVERGED = 0, -6
+GSIS_OK, GSIS_E_NOT_CONVERGED, GSIS_E_UNSUPPORTED = 0, -6, -7
 F64, F32, BF16 = 0, 1, 2
 PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16}
 MODE_GSIS, MODE_DVM = 0, 1

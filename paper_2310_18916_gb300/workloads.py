@@ -90,22 +90,25 @@ def couette(n_cells=100, nv=24, vmax=5.0, U=0.2, Kn=0.1, omega=0.81, Tw=(1.0, 1.
                    W0=_uniform_state(n_cells), name=f"couette{n_cells}x{nv}^3")
 
 
-def cavity(n=128, nv=32, vmax=5.0, lid=0.16, Kn=0.1, omega=0.81, stretch=0.0) -> Problem:
-    """Lid-driven square cavity [0,1]^2: lid y = 1 moves at +lid along x, all walls at T = 1.
+def cavity(n=128, nv=32, vmax=5.0, lid=0.16, Kn=0.1, omega=0.81, stretch=0.0, ny=None) -> Problem:
+    """Lid-driven cavity [0,1] x [0, ny/n]: lid y = top moves at +lid along x, all walls at T = 1
+    (square with n x n cells unless ny is given).
 
     stretch > 0 clusters cells towards the walls (tanh spacing); 0 gives a uniform grid.
     """
+    ny = n if ny is None else ny
     s = np.linspace(0.0, 1.0, n + 1)
     if stretch > 0:
         s = 0.5 * (1.0 + np.tanh(stretch * (2.0 * s - 1.0)) / np.tanh(stretch))
+    sy = s if ny == n else np.linspace(0.0, ny / n, ny + 1)
     dz = 1.0 / n
-    nodes = box_nodes(s, s, [0.0, dz])
+    nodes = box_nodes(s, sy, [0.0, dz])
     v, w = midpoint_grid(nv, -vmax, vmax)
     wall_u = np.zeros((6, 3))
     wall_u[3, 0] = lid
-    return Problem(n, n, 1, nodes, [WALL, WALL, WALL, WALL, PERIODIC, PERIODIC], wall_u, np.ones(6),
+    return Problem(n, ny, 1, nodes, [WALL, WALL, WALL, WALL, PERIODIC, PERIODIC], wall_u, np.ones(6),
                    v, v.copy(), v.copy(), w, w.copy(), w.copy(), SHAKHOV, omega, Kn,
-                   W0=_uniform_state(n * n), name=f"cavity{n}^2x{nv}^3_Kn{Kn:g}")
+                   W0=_uniform_state(n * ny), name=f"cavity{n}x{ny}x{nv}^3_Kn{Kn:g}")
 
 
 def serving_cavity(rng, sizes=(32, 48, 64), nvs=(16, 20, 24), kn=(1e-3, 1.0), ma=(0.1, 1.0)) -> Problem:
