@@ -34,10 +34,10 @@ MACRO_FLOPS_PER_CELL_STEP_2D = 1556
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA lanes per clock
 # x 2 flops x the maximum SM clock
 FP64_LANES_PER_SM = 2
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# 64^2 cavity with 32^3 velocities, scaled by 4 to 128^2 (both grow with the cells); None once the
-# kernel has changed since the capture
-DRAM_BYTES_PER_LAUNCH = {"kinetic_kernel": None, "macro_kernel": 4 * 4.06e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the 128^2 cavity with
+# 32^3 velocities in FP32, from one ncu pass over the benchmark itself; None once the kernel has
+# changed since the capture
+DRAM_BYTES_PER_LAUNCH = {"kinetic_kernel": 2184.08e6 + 2092.71e6, "macro_kernel": 12.67e6 + 21.91e6}
 
 
 def workload_name(c=CFG):

@@ -444,6 +444,10 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     why = "cell counts must be in [1, 1023]";
     return GSIS_E_INVALID;
   }
+  if ((double)m->ni * m->nj * m->nk * NST >= 4294967296.0) {  // 32-bit state offsets in the kernels
+    why = "too many cells";
+    return GSIS_E_UNSUPPORTED;
+  }
   for (int d = 0; d < 3; ++d)
     if (vg->n[d] < 1 || !vg->x[d] || !vg->w[d]) { why = "bad velocity grid"; return GSIS_E_INVALID; }
   if (!(Kn > 0)) { why = "Kn must be positive"; return GSIS_E_INVALID; }

@@ -42,11 +42,14 @@ __device__ __forceinline__ double dexp(double x) { return exp(x); }
 __device__ __forceinline__ float ddiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
 
+// Wall Maxwellian M(xi; u_w, T_w) with unit density, in the arithmetic type (an FP64 pow per
+// lane would cost FP64-rate time on this GPU in every CTA's set-up)
 template <typename T>
 __device__ __forceinline__ T wall_maxwellian(const double *uT, T x, T y, T z) {
   const T ux = (T)uT[0], uy = (T)uT[1], uz = (T)uT[2], Tw = (T)uT[3];
   const T cx = x - ux, cy = y - uy, cz = z - uz;
-  const T norm = (T)pow((double)(3.14159265358979323846 * uT[3]), -1.5);
+  const T pT = (T)3.14159265358979323846 * Tw;
+  const T norm = (T)1 / (pT * sqrt(pT));  // (pi T_w)^(-3/2)
   return norm * dexp(-(cx * cx + cy * cy + cz * cz) / Tw);
 }
 
@@ -155,6 +158,17 @@ __device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const
   return ddiv(bn, bd);
 }
 
+// Per-cell state and colour-entry addresses from 32-bit offsets: a 64-bit multiply by a
+// non-power-of-two stride would run at the FP64 rate on this GPU (cells * NST < 2^32 is checked
+// at creation).
+template <typename T>
+__device__ __forceinline__ const T *state_of(const T *st, int cell) {
+  return st + (unsigned)cell * (unsigned)NST;
+}
+__device__ __forceinline__ const EntryInfo &entry_of(const EntryInfo *e, int i) {
+  return *reinterpret_cast<const EntryInfo *>(reinterpret_cast<const char *>(e) + (unsigned)i * (unsigned)sizeof(EntryInfo));
+}
+
 template <int N = 16>
 __device__ __forceinline__ void load_state(const float *__restrict__ src, float *st) {
   const float4 *p = reinterpret_cast<const float4 *>(src);
@@ -252,7 +266,7 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
     for (int p = warp; p < cnt; p += nw) {
       const int cell = __ldg(&natcell[off + p].x);
       T st[SL];
-      load_state<SL>(A.st + (size_t)cell * NST, st);
+      load_state<SL>(state_of(A.st, cell), st);
       T stored[NV], f[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(F[q] + (size_t)cell * VB + lane);
@@ -274,7 +288,7 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
       const int4 nc4 = __ldg(&natcell[off + p]);
       const int cell = nc4.x;
       const int nat[3] = {nc4.y, nc4.z, nc4.w};
-      const EntryInfo &E = A.entry[off + p];
+      const EntryInfo &E = entry_of(A.entry, off + p);
       int nb[6], trn[3];
 #pragma unroll
       for (int q = 0; q < 2 * NACT; ++q) nb[q] = __ldg(&E.nb[q]);
@@ -285,7 +299,7 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
       for (int q = 0; q < NV; ++q) fi[q] = slot0[(p * NV + q) * VB + lane];
       constexpr int CL = NV == 2 ? NST_RYKOV : 16;
       T st[CL];
-      load_state<CL>(A.st + (size_t)cell * NST, st);
+      load_state<CL>(state_of(A.st, cell), st);
       // gradient (LSQ, decoupled per axis on a rectilinear grid) and bounds, per VDF
       T gr[NV][3], rlo[3], rhi[3], invh[3];
       T fmax[NV], fmin[NV];
