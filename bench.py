@@ -269,6 +269,9 @@ def main():
     ap.add_argument("--tts-tol", type=float, default=1e-6)
     ap.add_argument("--tts-max-steps", type=int, default=400)
     ap.add_argument("--serve", action="store_true", help="instead of the throughput line: the serving stream")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: one solve sharded over the ranks' velocities (strong scaling) "
+                         "instead of a replica per rank")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-gap", type=float, default=0.25, help="mean arrival gap, seconds")
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -302,7 +305,12 @@ def main():
 
     p = problem()
     pts = p.ncells * p.nvel
-    s = gsis.Solver(p, precision=args.precision, mode="gsis")
+    sharded = args.shard and world > 1
+    shard_kw = {}
+    if sharded:
+        from paper_2310_18916_gb300 import sharding
+        shard_kw = dict(shard=(rank, world), allreduce=sharding.dist_allreduce())
+    s = gsis.Solver(p, precision=args.precision, mode="gsis", **shard_kw)
     for _ in range(args.warmup):
         s.step()
     s.profile(True, reset=True)
@@ -324,7 +332,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
     ms = ms_total / args.steps
-    value = world * pts * args.steps / (ms_total / 1e3)
+    value = (1 if sharded else world) * pts * args.steps / (ms_total / 1e3)
     kin_ms = phase[1] / max(nsteps, 1)
     s.close()
     del s
@@ -334,7 +342,7 @@ def main():
     # device->host read of the state, destroy
     barrier()
     t0 = time.perf_counter()
-    s2 = gsis.Solver(p, precision=args.precision, mode="gsis", kinetic_presteps=0)
+    s2 = gsis.Solver(p, precision=args.precision, mode="gsis", kinetic_presteps=0, **shard_kw)
     for _ in range(args.steps):
         s2.step()
         W = s2.W()
@@ -361,10 +369,12 @@ def main():
     vdf_gb = p.ncells * p.nvel * sbytes / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
         "config": {"workload": workload_name(), "precision": f"{args.precision} VDF, f64 synthetic solve",
-                   "cells": p.ncells, "velocities": p.nvel, "points": pts, "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "cells": p.ncells, "velocities": p.nvel, "points": pts,
+                   "parallelism": f"velocity shards x{world}" if sharded else ("replicas" if world > 1 else "1 GPU"),
                    "l2": f"inputs larger than L2 (VDF {vdf_gb:.2f} GB)" if vdf_gb > 0.129 else
                          f"VDF {vdf_gb:.3f} GB fits in L2 (profiling size)", "macro_inner_steps": macro_iters, "eps_last": eps},
         "phase_ms_per_step": {k: v / max(nsteps, 1) for k, v in zip(
@@ -382,7 +392,8 @@ def main():
                              "traffic": DRAM_BYTES_PER_LAUNCH["kinetic_kernel"]
                              if args.n == 128 and args.precision == "f32" else None,
                              "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": kin_ms, "share_of_step": kin_ms / ms},
-        "e2e": {"value": args.steps * pts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+        "e2e": {"value": (1 if sharded else world) * args.steps * pts / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h, "seconds": e2e_s, "includes": "create from host inputs, steps, per-step state read, destroy"},
         "gpu_launches": launches,
         "clocks": clk.summary(),

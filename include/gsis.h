@@ -87,6 +87,12 @@ typedef struct {
 typedef void *(*gsis_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*gsis_free_fn)(void *ptr, void *stream, void *ctx);
 
+/* Sum-all-reduce across the shards of a velocity-sharded solve (see shard_count): replace the
+ * count FP64 values at device pointer dev by their sum over all shards, in the order of work on
+ * stream (e.g. an NCCL all-reduce on that stream, or a host-synchronising exchange).  Every
+ * shard calls it with the same count at the same points of a step; returns 0 on success. */
+typedef int (*gsis_allreduce_fn)(double *dev, size_t count, void *stream, void *ctx);
+
 /* Solver options.  Defaults (gsis_default_options): see the comments. */
 typedef struct {
   int precision;        /* VDF storage / kinetic arithmetic (default F32): GSIS_F64 (FP64 / FP64),
@@ -112,6 +118,18 @@ typedef struct {
   int macro_sms;        /* SMs the synthetic solve may occupy (default 0: all).  Its blocks hold a
                            whole SM each, so solves that run at the same time on one GPU (serving)
                            each take a share. */
+  int shard_count;      /* velocity sharding (the N_v decomposition of Section 4): the discrete
+                           velocities, in blocks of 32 of one octant, are split into shard_count
+                           contiguous ranges; this handle owns range shard_index and stores f only
+                           there (default 1: unsharded).  Per step three partial sums are
+                           all-reduced through allreduce: the wall re-emission densities before
+                           the kinetic sweeps, the per-cell moments and kinetic flux sums, and the
+                           wall fluxes.  Everything after them (the synthetic solve included) is
+                           repeated identically on every shard.  gsis_get_f / gsis_set_f then
+                           transfer only this shard's velocities (others untouched / ignored). */
+  int shard_index;
+  gsis_allreduce_fn allreduce;  /* required when shard_count > 1 */
+  void *allreduce_ctx;
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;

@@ -59,7 +59,9 @@ struct gsis_solver {
   int nv_axis[3] = {0, 0, 0};
   std::vector<int> slot_canon;
   std::vector<int8_t> boct;
-  std::vector<double> vel64;
+  std::vector<double> vel64;      // this shard's slots [slot][4]
+  std::vector<double> vel64_all;  // every slot (wall constants integrate over all velocities)
+  int nslots_all = 0;
   // walls
   int nwall = 0;
   std::vector<int> wall_cell, wall_side, wall_sides_list;
@@ -192,6 +194,14 @@ struct gsis_solver {
     return a;
   }
 
+  // sum over the velocity shards (no-op unsharded)
+  int exchange(double *dev, size_t count, const char *what) {
+    if (opt.shard_count <= 1 || count == 0) return GSIS_OK;
+    if (opt.allreduce(dev, count, (void *)stream, opt.allreduce_ctx) != 0)
+      return fail(GSIS_E_CUDA, "allreduce of %s failed", what);
+    return GSIS_OK;
+  }
+
   int check_err() {
     int herr = 0;
     int rc = cuda(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream), "read error flag");
@@ -211,8 +221,12 @@ struct gsis_solver {
     int rc = cuda(launch_moments<T, S>(kin_args<T, S>(), mom_bpc, mom_nchunks, d_mp, stream), "moments");
     if (rc) return rc;
     rc = cuda(launch_reduce<T>(d_mp, mom_nchunks, nvdf, static_cast<const T *>(d_wpart), d_boct, nblocks, kg, d_wall_cell,
-                               d_wall_side, nwall, d_rho_w, d_Zw, d_vol, d_st64, d_mom, d_K, d_wf, stream),
+                               d_wall_side, nwall, d_rho_w, d_Zw, opt.shard_count <= 1 || opt.shard_index == 0,
+                               d_vol, d_st64, d_mom, d_K, d_wf, stream),
               "reduce");
+    if (!rc) rc = exchange(d_mom, (size_t)nc * MOM_STRIDE, "moments");
+    if (!rc) rc = exchange(d_K, (size_t)nc * 6, "kinetic flux sums");
+    if (!rc) rc = exchange(d_wf, (size_t)nwall * 6, "wall fluxes");
     if (rc) return rc;
     FinalizeArgs fa{};
     fa.nvdf = nvdf;
@@ -296,6 +310,7 @@ struct gsis_solver {
     mark(0);
     int rc = cuda(launch_wall_prepass<T, S>(kin_args<T, S>(), d_wall_cell, d_wall_side, nwall, d_Z0, d_rho_w, nslots, stream),
                   "wall pre-pass");
+    if (!rc) rc = exchange(d_rho_w, (size_t)nwall, "wall densities");
     if (rc) return rc;
     launches += nwall > 0;
     mark(1);
@@ -457,6 +472,10 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     return GSIS_E_INVALID;
   }
   if (o->mode != GSIS_MODE_GSIS && o->mode != GSIS_MODE_DVM) { why = "bad mode"; return GSIS_E_INVALID; }
+  if (o->shard_count > 1 && (o->shard_index < 0 || o->shard_index >= o->shard_count || !o->allreduce)) {
+    why = "velocity sharding needs 0 <= shard_index < shard_count and an allreduce callback";
+    return GSIS_E_INVALID;
+  }
   if (g->model == GSIS_RYKOV && (!(g->d_r > 0) || !(g->Z_r > 0))) {
     why = "Rykov needs d_r > 0 and Z_r > 0";
     return GSIS_E_INVALID;
@@ -688,6 +707,18 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
   s->nv_axis[2] = vg->n[2];
   s->nvc = vg->n[0] * vg->n[1] * vg->n[2];
   build_slots(vg, s->slot_canon, s->boct, s->vel64);
+  s->vel64_all = s->vel64;
+  s->nslots_all = (int)s->slot_canon.size();
+  const int K = s->opt.shard_count > 1 ? s->opt.shard_count : 1;
+  if (K > 1) {
+    // this shard's contiguous range of velocity blocks
+    const int nb = s->nslots_all / VB, k = s->opt.shard_index;
+    if (K > nb) return s->fail(GSIS_E_INVALID, "%d shards for %d velocity blocks", K, nb);
+    const int b0 = (int)((long long)k * nb / K), b1 = (int)((long long)(k + 1) * nb / K);
+    s->slot_canon = std::vector<int>(s->slot_canon.begin() + (size_t)b0 * VB, s->slot_canon.begin() + (size_t)b1 * VB);
+    s->boct = std::vector<int8_t>(s->boct.begin() + b0, s->boct.begin() + b1);
+    s->vel64 = std::vector<double>(s->vel64.begin() + (size_t)b0 * VB * 4, s->vel64.begin() + (size_t)b1 * VB * 4);
+  }
   s->nslots = (int)s->slot_canon.size();
   s->nblocks = s->nslots / VB;
   s->np = NMOM + NFF * g.nact;
@@ -728,7 +759,7 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->d_stT, nc * NST * sizeof(T));
   A(s->d_st64, nc * NST * sizeof(double));
   A(s->d_vel, (size_t)s->nslots * 4 * sizeof(T));
-  A(s->d_vel64, (size_t)s->nslots * 4 * sizeof(double));
+  A(s->d_vel64, (size_t)s->nslots_all * 4 * sizeof(double));
   for (int a = 0; a < 3; ++a) {
     A(s->d_ax[a], s->axc[a].size() * sizeof(AxisCell<T>));
     A(s->d_ax64[a], s->axc[a].size() * sizeof(AxisCell<double>));
@@ -786,7 +817,7 @@ static int allocate_and_upload(gsis_solver *s) {
   if (rc) return rc;
   std::vector<T> velT(s->vel64.begin(), s->vel64.end());
   rc = s->upload(s->d_vel, velT.data(), velT.size() * sizeof(T));
-  if (!rc) rc = s->upload(s->d_vel64, s->vel64.data(), s->vel64.size() * sizeof(double));
+  if (!rc) rc = s->upload(s->d_vel64, s->vel64_all.data(), s->vel64_all.size() * sizeof(double));
   for (int a = 0; a < 3 && !rc; ++a) {
     auto cv = cast_axis<T>(s->axc[a]);
     rc = s->upload(s->d_ax[a], cv.data(), cv.size() * sizeof(AxisCell<T>));
@@ -814,7 +845,7 @@ static int allocate_and_upload(gsis_solver *s) {
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_Z0, 0, 6 * sizeof(double), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_Zw, 0, 36 * sizeof(double), s->stream), "memset");
   if (!rc)
-    rc = s->cuda(launch_wall_constants(s->d_vel64, s->nslots, s->d_wall_uT, s->d_wall_sides,
+    rc = s->cuda(launch_wall_constants(s->d_vel64, s->nslots_all, s->d_wall_uT, s->d_wall_sides,
                                        (int)s->wall_sides_list.size(), s->d_Z0, s->d_Zw,
                                        s->nvdf == 2 ? s->gas.d_r : 0.0, s->stream),
                  "wall constants");
@@ -847,7 +878,8 @@ extern "C" int gsis_footprint_bytes(const gsis_mesh *mesh, const gsis_vgrid *vgr
   tmp.opt = o;
   tmp.prec = o.precision;
   tmp.nvdf = gas->model == GSIS_RYKOV ? 2 : 1;
-  setup(&tmp, mesh, vgrid);
+  rc = setup(&tmp, mesh, vgrid);
+  if (rc) return rc;
   *bytes = footprint(&tmp);
   return GSIS_OK;
 }
@@ -898,8 +930,8 @@ extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const
   s->omega = gas->omega;
   s->gas = *gas;
   s->stream = (cudaStream_t)o.stream;
-  setup(s, mesh, vgrid);
-  rc = GSIS_DISPATCH(s->prec, (allocate_and_upload<T, S>(s)));
+  rc = setup(s, mesh, vgrid);
+  if (!rc) rc = GSIS_DISPATCH(s->prec, (allocate_and_upload<T, S>(s)));
   if (!rc) rc = init_state(s);
   for (int t = 0; !rc && t < o.kinetic_presteps; ++t) rc = s->step(GSIS_MODE_DVM);
   if (rc) {

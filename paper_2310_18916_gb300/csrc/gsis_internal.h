@@ -130,8 +130,8 @@ cudaError_t launch_wall_constants(const double *vel64, int nslots, const double 
 template <typename T>
 cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpart, const int8_t *boct, int nblocks,
                           const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
-                          const double *rho_w, const double *Zw, const double *vol, const double *st64,
-                          double *mom, double *K, double *wf, cudaStream_t s);
+                          const double *rho_w, const double *Zw, bool emit, const double *vol,
+                          const double *st64, double *mom, double *K, double *wf, cudaStream_t s);
 constexpr int MOM_STRIDE = NMOM + NMOM1;  // per-cell raw moments: f0 then f1
 
 struct FinalizeArgs {

@@ -44,7 +44,7 @@ __global__ void reduce_moments_kernel(const double *mp, int nchunks, int nc, int
 // block partials (blocks whose octant moves towards this wall), the re-emitted half rho_w Zw.
 template <typename T>
 __global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nblocks, int nwall, const int *wall_side,
-                                   const double *rho_w, const double *Zw, double *wf) {
+                                   const double *rho_w, const double *Zw, int emit, double *wf) {
   const int n = nwall * NWF;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     const int w = idx / NWF, m = idx % NWF;
@@ -56,7 +56,8 @@ __global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nbloc
       if (neg == plus) continue;  // this block's velocities move away from the wall
       out += (double)wpart[((size_t)b * nwall + w) * NWF + m];
     }
-    const double tot = out + rho_w[w] * Zw[6 * side + m];
+    // the re-emitted half once per solve: by one shard of a velocity-sharded solve
+    const double tot = out + (emit ? rho_w[w] * Zw[6 * side + m] : 0.0);
     wf[(size_t)w * 6 + m] = plus ? tot : -tot;
   }
 }
@@ -64,7 +65,7 @@ __global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nbloc
 template <typename T>
 cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpart, const int8_t *boct, int nblocks,
                           const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
-                          const double *rho_w, const double *Zw, const double *vol, const double *st64,
+                          const double *rho_w, const double *Zw, bool emit, const double *vol, const double *st64,
                           double *mom, double *K, double *wf, cudaStream_t s) {
   (void)wall_cell;
   const int np = moment_len(nvdf);
@@ -74,15 +75,16 @@ cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpar
   reduce_moments_kernel<<<grid, 256, 0, s>>>(mp, nchunks, g.nc, np, vol, st64, mom, K);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nwall == 0 || wpart == nullptr) return e;
-  reduce_wall_kernel<T><<<(nwall * NWF + 255) / 256, 256, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw, wf);
+  reduce_wall_kernel<T><<<(nwall * NWF + 255) / 256, 256, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw,
+                                                                   emit ? 1 : 0, wf);
   return cudaGetLastError();
 }
 template cudaError_t launch_reduce<float>(const double *, int, int, const float *, const int8_t *, int, const KinGeom &,
-                                          const int *, const int *, int, const double *, const double *,
+                                          const int *, const int *, int, const double *, const double *, bool,
                                           const double *, const double *, double *, double *, double *, cudaStream_t);
 template cudaError_t launch_reduce<double>(const double *, int, int, const double *, const int8_t *, int,
                                            const KinGeom &, const int *, const int *, int, const double *,
-                                           const double *, const double *, const double *, double *, double *,
+                                           const double *, bool, const double *, const double *, double *, double *,
                                            double *, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------

@@ -25,6 +25,7 @@ ERRORS = {-1: "GSIS_E_INVALID", -2: "GSIS_E_OOM", -3: "GSIS_E_CUDA", -4: "GSIS_E
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 
 class Mesh(C.Structure):
@@ -46,7 +47,8 @@ class Options(C.Structure):
                 ("macro_sweeps", C.c_int), ("macro_cfl", C.c_double), ("macro_tol", C.c_double),
                 ("kin_inv_dt", C.c_double), ("venkat_K", C.c_double), ("kinetic_presteps", C.c_int),
                 ("init_W", D), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("macro_sms", C.c_int)]
+                ("alloc_ctx", C.c_void_p), ("macro_sms", C.c_int), ("shard_count", C.c_int),
+                ("shard_index", C.c_int), ("allreduce", ALLREDUCE_FN), ("allreduce_ctx", C.c_void_p)]
 
 
 _lib = None
@@ -134,9 +136,12 @@ class Solver:
     precision: "f32", "f64" or "bf16" (VDF storage; kinetic arithmetic is FP32 for f32 and bf16,
     FP64 for f64; the synthetic solve is FP64).
     mode: "gsis" or "dvm".  Other keyword arguments map onto gsis_options.
+    shard: (index, count) of a velocity-sharded solve, with allreduce(ptr, count, stream_ptr) the
+    sum-all-reduce of count FP64 values at device pointer ptr (see sharding.py).
     """
 
-    def __init__(self, problem, precision="f32", mode="gsis", init_W=None, torch_memory=True, **opts):
+    def __init__(self, problem, precision="f32", mode="gsis", init_W=None, torch_memory=True, shard=None,
+                 allreduce=None, **opts):
         import torch
 
         if not torch.cuda.is_available():
@@ -153,6 +158,22 @@ class Solver:
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")
             setattr(o, k, v)
+        if shard is not None:
+            if allreduce is None:
+                raise TypeError("a sharded solve needs allreduce")
+            o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
+
+            def _allreduce(ptr, count, stream, ctx):
+                try:
+                    allreduce(int(ptr), int(count), int(stream or 0))
+                    return 0
+                except Exception:  # noqa: BLE001 - reported to the library as a failed exchange
+                    import traceback
+                    traceback.print_exc()
+                    return 1
+
+            self._allreduce_cb = ALLREDUCE_FN(_allreduce)
+            o.allreduce = self._allreduce_cb
         W0 = problem.W0 if init_W is None else init_W
         if W0 is not None:
             W0 = np.ascontiguousarray(W0, dtype=np.float64)
@@ -288,13 +309,20 @@ class Solver:
         return a.value, b.value
 
 
-def footprint_bytes(problem, precision="f32"):
+_NO_EXCHANGE = ALLREDUCE_FN(lambda ptr, count, stream, ctx: 1)  # footprints never exchange
+
+
+def footprint_bytes(problem, precision="f32", shard=None):
+    """Device bytes a solver of this problem holds (shard: (index, count) of a sharded solve)."""
     L = load()
     keep = []
     m, vg, g = build_structs(problem, keep)
     o = Options()
     L.gsis_default_options(C.byref(o))
     o.precision = PRECISIONS[precision]
+    if shard is not None:
+        o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
+        o.allreduce = _NO_EXCHANGE
     out = C.c_size_t()
     rc = L.gsis_footprint_bytes(C.byref(m), C.byref(vg), C.byref(g), C.byref(o), C.byref(out))
     if rc != 0:
