@@ -55,7 +55,7 @@ struct gsis_solver {
   std::vector<EntryInfo> entries;
   std::vector<int4> natcell;
   // velocities
-  int nvc = 0, nslots = 0, nblocks = 0, np = 0;
+  int nvc = 0, nslots = 0, nblocks = 0;
   int nv_axis[3] = {0, 0, 0};
   std::vector<int> slot_canon;
   std::vector<int8_t> boct;
@@ -79,7 +79,7 @@ struct gsis_solver {
   double *d_hot = nullptr, *d_Wstate = nullptr, *d_Wnew = nullptr, *d_vol = nullptr, *d_mass = nullptr;
   double *d_scratch = nullptr, *d_eps4 = nullptr;
   int8_t *d_boct = nullptr;
-  int *d_col_off = nullptr, *d_col_cell = nullptr, *d_pos_of = nullptr, *d_wall_cell = nullptr;
+  int *d_col_off = nullptr, *d_wall_cell = nullptr;
   int *d_wall_side = nullptr, *d_wall_sides = nullptr, *d_err = nullptr, *d_iters = nullptr;
   EntryInfo *d_entry = nullptr;
   int4 *d_natcell = nullptr;
@@ -177,8 +177,6 @@ struct gsis_solver {
     a.vel = static_cast<const T *>(d_vel);
     a.boct = d_boct;
     a.col_off = d_col_off;
-    a.col_cell = d_col_cell;
-    a.pos_of = d_pos_of;
     a.entry = d_entry;
     a.natcell = d_natcell;
     a.st = static_cast<const T *>(d_stT);
@@ -721,7 +719,6 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
   }
   s->nslots = (int)s->slot_canon.size();
   s->nblocks = s->nslots / VB;
-  s->np = NMOM + NFF * g.nact;
   return GSIS_OK;
 }
 
@@ -766,8 +763,6 @@ static int allocate_and_upload(gsis_solver *s) {
   }
   A(s->d_boct, s->boct.size());
   A(s->d_col_off, s->col_off.size() * sizeof(int));
-  A(s->d_col_cell, nc * sizeof(int));
-  A(s->d_pos_of, nc * sizeof(int));
   A(s->d_entry, nc * sizeof(EntryInfo));
   A(s->d_natcell, 8 * nc * sizeof(int4));
   A(s->d_rho_w, (size_t)(s->nwall + 1) * sizeof(double));
@@ -825,8 +820,6 @@ static int allocate_and_upload(gsis_solver *s) {
   }
   if (!rc) rc = s->upload(s->d_boct, s->boct.data(), s->boct.size());
   if (!rc) rc = s->upload(s->d_col_off, s->col_off.data(), s->col_off.size() * sizeof(int));
-  if (!rc) rc = s->upload(s->d_col_cell, s->col_cell.data(), nc * sizeof(int));
-  if (!rc) rc = s->upload(s->d_pos_of, s->pos_of.data(), nc * sizeof(int));
   if (!rc) rc = s->upload(s->d_entry, s->entries.data(), nc * sizeof(EntryInfo));
   if (!rc) rc = s->upload(s->d_natcell, s->natcell.data(), 8 * nc * sizeof(int4));
   if (!rc && s->nwall) rc = s->upload(s->d_wall_cell, s->wall_cell.data(), s->nwall * sizeof(int));

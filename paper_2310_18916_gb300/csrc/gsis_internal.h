@@ -27,7 +27,6 @@ constexpr int NST = 48;         // per-cell kinetic state values:
                                 //  [31..33] 2 (pi Tt)^-3/2 qr / Tt, [34..36] 2 (pi T)^-3/2 q1 / T,
                                 //  [37] 1 - 1/Z_r, [38] 1/Z_r, [39] d_r Tr_o / 4, [40..47] unused
 constexpr int NST_RYKOV = 40;   // state values a Rykov kinetic step reads
-constexpr int MAXNP = 13 + 3 * NFF;
 constexpr int GSIS_ERR_DIVERGED = -4;  // same values as GSIS_E_DIVERGED / GSIS_E_TIMEOUT
 constexpr int GSIS_ERR_TIMEOUT = -5;
 
@@ -83,8 +82,6 @@ struct KinArgs {
   const T *vel;          // [slot][4]: xi_x, xi_y, xi_z, w
   const int8_t *boct;    // octant of each block: bit a set => xi_a < 0
   const int *col_off;    // [ncol+1]
-  const int *col_cell;   // transformed coords packed i' | j' << 10 | k' << 20
-  const int *pos_of;     // position of a transformed cell inside its colour
   const EntryInfo *entry;  // [entry] neighbour positions and transverse indices
   const int4 *natcell;     // [octant][entry]: cell index and natural coordinates
   const T *st;           // [cell][NST]
@@ -224,8 +221,6 @@ struct MacroArgs {
 constexpr int MACRO_MAX_GRID = 512;  // blocks of the synthetic-solve kernel at most
 constexpr int MACRO_BAR_WORDS = 512;  // barrier words, cleared before each launch
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s);
-int macro_block_size();
-cudaError_t macro_max_grid(int *grid);
 cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block);
 
 }  // namespace gsis

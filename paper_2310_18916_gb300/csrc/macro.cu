@@ -753,8 +753,6 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *m.iters = used;
 }
 
-int macro_block_size() { return kBlock; }
-
 // One block of 512 threads per SM: the phases have many short FP64 work items and every SM
 // must hold some.  The cooperative launch guarantees the blocks are co-resident.
 cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block) {
@@ -773,11 +771,6 @@ cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block) {
   *grid = nsm < MACRO_MAX_GRID ? nsm : MACRO_MAX_GRID;
   *block = kBlock;
   return cudaSuccess;
-}
-
-cudaError_t macro_max_grid(int *grid) {
-  int b = 0;
-  return macro_launch_shape(0, 0, grid, &b);
 }
 
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s) {
