@@ -808,7 +808,7 @@ static int allocate_and_upload(gsis_solver *s) {
   if (rc) return rc;
   rc = s->cuda(macro_launch_shape((int)nc, s->opt.macro_sms, &s->macro_grid, &s->macro_block), "occupancy");
   if (rc) return rc;
-  rc = s->alloc(&s->m_red, (size_t)3 * s->macro_grid * 16 * sizeof(double));
+  rc = s->alloc(&s->m_red, ((size_t)3 * s->macro_grid * 16 + 32) * sizeof(double));
   if (rc) return rc;
   std::vector<T> velT(s->vel64.begin(), s->vel64.end());
   rc = s->upload(s->d_vel, velT.data(), velT.size() * sizeof(T));

@@ -140,20 +140,26 @@ __host__ __device__ constexpr int stage_state_len() { return NV == 2 ? NST_RYKOV
 // Venkatakrishnan limiter of one cell: min over its faces (and 1) of
 //   (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
 // the face function with numerator and denominator divided by D2; both are positive, so
-// the minimum is taken by cross-multiplication and divided once.
+// the minimum is taken by cross-multiplication and divided once.  Of the two faces of an axis
+// (r_lo < 0 < r_hi) only the one with the smaller y = Dm / D2 >= 0 can give the minimum: with
+// E = e^2 / D2^2 (the same on both faces, |r_lo| = |r_hi|) the function (y^2 + 2y + E) /
+// (y^2 + y + 2 + E) rises while y < 2 + sqrt(8 + E) and exceeds 1 exactly when y > 2.
 template <typename T, int NACT>
 __device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const T *rlo, const T *rhi, T eps2) {
+  const T dp = fmax - fi, dn = fmin - fi;
   T bn = (T)1, bd = (T)1;
 #pragma unroll
   for (int a = 0; a < NACT; ++a) {
-#pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-      const T d2 = gr[a] * (sd ? rhi[a] : rlo[a]);
-      const T dm = d2 > (T)0 ? fmax - fi : (d2 < (T)0 ? fmin - fi : (T)0);
-      const T n = dm * dm + eps2 + (T)2 * d2 * dm;
-      const T d = dm * dm + (T)2 * d2 * d2 + dm * d2 + eps2;
-      if (n * bd < bn * d) { bn = n; bd = d; }
-    }
+    const T dh = gr[a] * rhi[a], dl = gr[a] * rlo[a];
+    const bool pos = gr[a] > (T)0;
+    const T mh = pos ? dp : dn, ml = pos ? dn : dp;
+    const bool hi = fabs(mh) * fabs(dl) <= fabs(ml) * fabs(dh);
+    // (gr = 0: D2 = 0 and the face value is 1, which never lowers the minimum)
+    const T d2 = hi ? dh : dl, dm = hi ? mh : ml;
+    const T dm2 = dm * dm + eps2;
+    const T n = (T)2 * d2 * dm + dm2;
+    const T d = d2 * ((T)2 * d2 + dm) + dm2;
+    if (n * bd < bn * d) { bn = n; bd = d; }
   }
   return ddiv(bn, bd);
 }

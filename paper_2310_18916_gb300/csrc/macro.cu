@@ -79,6 +79,24 @@ __device__ bool grid_sync(unsigned *bar, unsigned &epoch, int *err) {
   return *(volatile int *)err == 0;
 }
 
+// Warp sums of v[0..15] by recursive halving: at each level a lane keeps the half of its vector
+// selected by one bit of its lane index and adds the partner's copy of that half (16 adds instead
+// of 80).  Afterwards lanes 2i and 2i + 1 hold the warp total of v[i].
+__device__ __forceinline__ double transpose_sum16(double *v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 16, n = 8; h > 1; h >>= 1, n >>= 1) {
+    const bool up = lane & h;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const double send = up ? v[i] : v[i + n];
+      const double keep = up ? v[i + n] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // Work items: warp w (dealt round-robin over the blocks) takes items 32 w .. 32 w + 31.
 struct Items {
   int first, stride;
@@ -143,6 +161,25 @@ __device__ __forceinline__ void euler_axis_prim(const double *W, const double *p
 }
 
 __device__ __forceinline__ double sound(double Tt) { return sqrt(5.0 * Tt / 6.0); }
+
+// Venkatakrishnan face function of the two faces of one axis, r_lo < 0 < r_hi.  The increment
+// D2 = g r of the face where it is positive meets the bound dp = qmax - qi, the other face dn =
+// qmin - qi.  As a function of y = Dm / D2 >= 0, (y^2 + 2y + E) / (y^2 + y + 2 + E) with E =
+// e^2 / D2^2 (the same on both faces, |r_lo| = |r_hi|) rises while y < 2 + sqrt(8 + E) and
+// exceeds 1 exactly when y > 2, so the minimum of the two faces and 1 is the face with the
+// smaller y (up to rounding).  Returns that face's numerator and denominator.
+__device__ __forceinline__ void venkat_axis(double g, double rlo, double rhi, double dp, double dn, double eps2,
+                                            double &nn, double &dd) {
+  const double dh = g * rhi, dl = g * rlo;
+  const bool pos = g > 0.0;
+  const double mh = pos ? dp : dn, ml = pos ? dn : dp;
+  const bool hi = fabs(mh) * fabs(dl) <= fabs(ml) * fabs(dh);
+  // (g = 0: D2 = 0 and the face value is 1, which never lowers the minimum)
+  const double d2 = hi ? dh : dl, dm = hi ? mh : ml;
+  const double dm2 = fma(dm, dm, eps2);
+  nn = fma(2.0 * d2, dm, dm2);
+  dd = fma(d2, fma(2.0, d2, dm), dm2);
+}
 
 // T^e for T > 0 as exp(e log T)
 __device__ __forceinline__ double power(double T, double e) { return exp(e * log(T)); }
@@ -246,19 +283,16 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl,
     }
     if (lim) {
       // Venkatakrishnan: min over the faces (and 1) of (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
-      // compared by cross-multiplication and divided once
-      const double eps2 = g.K3 * V;
+      // one face per axis (the one with the smaller |Dm| / |D2|), compared by cross-multiplication
+      // and divided once
+      const double eps2 = g.K3 * V, dp = qmax - qi, dn = qmin - qi;
       double bn = 1.0, bd = 1.0;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (!g.act[a]) continue;
-#pragma unroll
-        for (int sd = 0; sd < 2; ++sd) {
-          const double d2 = gr[a] * (sd ? gc[a].rhi : gc[a].rlo);
-          const double dm = d2 > 0.0 ? qmax - qi : (d2 < 0.0 ? qmin - qi : 0.0);
-          const double nn = dm * dm + eps2 + 2.0 * d2 * dm, dd = dm * dm + 2.0 * d2 * d2 + dm * d2 + eps2;
-          if (nn * bd < bn * dd) { bn = nn; bd = dd; }
-        }
+        double nn, dd;
+        venkat_axis(gr[a], gc[a].rlo, gc[a].rhi, dp, dn, eps2, nn, dd);
+        if (nn * bd < bn * dd) { bn = nn; bd = dd; }
       }
 #pragma unroll
       for (int a = 0; a < 3; ++a) m.gW[((size_t)c * 6 + k) * 3 + a] = gr[a];
@@ -474,18 +508,50 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     // axis fluxes at the start of this step, and the buffer for those at its end
     const double *Fc = m.Fc + (size_t)(step & 1) * nc * 18;
     double *Fn = m.Fc + (size_t)((step + 1) & 1) * nc * 18;
+    // the previous step's inner residual: block k < 12 sums value k (num_k, den_k) of the
+    // blocks' partials in fixed order; every block tests them during C
+    const bool check = m.tol > 0.0 && step > 0;
+    if (check && blockIdx.x < 12 && threadIdx.x < 32) {
+      const double *red = m.red + (size_t)((step - 1) & 1) * gridDim.x * 16;
+      const int lane = threadIdx.x;
+      double v = 0.0;
+#pragma unroll
+      for (int i = 0; i < MACRO_MAX_GRID / 32; ++i) {
+        const int b = lane + 32 * i;
+        if (b < (int)gridDim.x) v += __ldcg(red + (size_t)b * 16 + blockIdx.x);
+      }
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) m.red[(size_t)3 * gridDim.x * 16 + ((step - 1) & 1) * 16 + blockIdx.x] = v;
+    }
     // ---- B: gradients and limiters per (cell, field); time step and diagonal per cell.  Items
-    // are field-major so the lanes of a warp take the same branch.
-    for (int t = it.first; t < nc * (NW + 6); t += it.stride) gradient_item<NW>(m, cs, inv_cfl, t % nc, t / nc);
+    // are field-major so the lanes of a warp take the same branch.  (Shakhov: T_r = T_t, whose
+    // gradient is not taken twice.)
+    constexpr int NB = NW == 6 ? NW + 6 : NW + 5;
+    for (int t = it.first; t < nc * NB; t += it.stride) {
+      const int k = t / nc;
+      gradient_item<NW>(m, cs, inv_cfl, t - k * nc, NW == 5 && k == NW + 4 ? NW + 5 : k);
+    }
     if (!grid_sync(m.bar, ep, m.err)) return;
-    // ---- C: interior + faces of the active axes, then the wall faces
+    // ---- C: interior + faces of the active axes, then the wall faces.  Warp 0 loads the
+    // residual sums before its items and tests them after: stop when max_k sqrt(num_k / den_k) <
+    // tol, tested as num_k < tol^2 den_k (the state is still that of the previous step's end)
+    double rsum = 0.0;
+    if (check && threadIdx.x < 12) rsum = __ldcg(m.red + (size_t)3 * gridDim.x * 16 + ((step - 1) & 1) * 16 + threadIdx.x);
     for (int t = it.first; t < nact * nc + m.nwall; t += it.stride) {
       if (t >= nact * nc)
         wall_item<NW>(m, t - nact * nc);
       else
         face_item<NW>(m, cs, t / nact, t % nact);
     }
+    if (check && threadIdx.x < 32) {
+      const int k = threadIdx.x;
+      const double den = __shfl_sync(0xffffffffu, rsum, (k + 6) & 31);
+      bool done = !(k < NW && den > 0.0 && !(rsum < m.tol * m.tol * den));
+      done = __all_sync(0xffffffffu, done);
+      if (k == 0) sdone = done;
+    }
     if (!grid_sync(m.bar, ep, m.err)) return;
+    if (check && sdone) break;
     // ---- E: red/black point-implicit sweeps, a pair of lanes per cell: lane sd takes the faces
     // on side sd of every active axis and the axis fluxes of axes sd, sd + 2
     double num[NW], den[NW];  // inner residual partials of this thread
@@ -628,24 +694,36 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
           // barrier
           __syncthreads();
           const int n = min(scount, kListCap);
-          for (int t = threadIdx.x; t < n * (1 + nact); t += blockDim.x) {
-            const int c = slist[t < n ? t : (t - n) / nact];
-            double Wl[6];
+          // warp w runs on sub-partition w % 4: the primitives go to the warps of sub-partitions 0
+          // and 1, the axis fluxes to those of 2 and 3, so the two kinds do not share FP64 pipes
+          const int wq = threadIdx.x >> 5, rs = blockDim.x >> 1;
+          const int r = (((wq >> 2) << 1) | (wq & 1)) * 32 + (threadIdx.x & 31);
+          if (!(wq & 2)) {
+            for (int t = r; t < n; t += rs) {
+              const int c = slist[t];
+              double Wl[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) Wl[k] = m.W[(size_t)c * 6 + k];
-            if (t < n) {
+              for (int k = 0; k < 6; ++k) Wl[k] = m.W[(size_t)c * 6 + k];
               cell_prims<NW>(m, c, Wl);
-              int nt[3];
-              nat_of(g, c, nt);
-              const double V = cell_volume(m, nt);
+              if (m.tol > 0.0) {
+                int nt[3];
+                nat_of(g, c, nt);
+                const double V = cell_volume(m, nt);
 #pragma unroll
-              for (int k = 0; k < NW; ++k) {
-                const double d = m.dW[(size_t)c * 6 + k];
-                num[k] += d * d * V;
-                den[k] += Wl[k] * Wl[k] * V;
+                for (int k = 0; k < NW; ++k) {
+                  const double d = m.dW[(size_t)c * 6 + k];
+                  num[k] += d * d * V;
+                  den[k] += Wl[k] * Wl[k] * V;
+                }
               }
-            } else {
-              const int a = (t - n) % nact;
+            }
+          } else {
+            for (int t = r; t < n * nact; t += rs) {
+              const int q = t / nact, a = t - q * nact;
+              const int c = slist[q];
+              double Wl[6];
+#pragma unroll
+              for (int k = 0; k < 6; ++k) Wl[k] = m.W[(size_t)c * 6 + k];
               double F[6];
               euler_axis<NW>(Wl, a, 1.0, F);
               const size_t o = ((size_t)c * 3 + a) * 6;
@@ -659,62 +737,44 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
           __syncthreads();
           if (threadIdx.x == 0) scount = 0;
         }
-        if (last && col == 1) {
-          // block partials of the inner residual, double buffered by step.  Only the threads that
-          // evaluated listed (or overflowing) cells hold nonzero terms: warps without any skip
-          // the FP64 butterfly.
+        if (last && col == 1 && m.tol > 0.0) {
+          // block partials of the inner residual (values 0..5: num_k, 6..11: den_k), double
+          // buffered by step.  Only the threads that evaluated listed (or overflowing) cells hold
+          // nonzero terms: warps without any skip the FP64 reduction.
           double *red = m.red + (size_t)(step & 1) * gridDim.x * 16;
-          const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+          const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
           bool nz = false;
 #pragma unroll
           for (int k = 0; k < NW; ++k) nz = nz || num[k] != 0.0 || den[k] != 0.0;
           if (__any_sync(0xffffffffu, nz)) {
+            double v[16];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-              const int f = k < 6 ? k : k - 6;
-              double v = 0.0;
+            for (int k = 0; k < 16; ++k) v[k] = 0.0;
 #pragma unroll
-              for (int q = 0; q < NW; ++q)
-                if (q == f) v = k < 6 ? num[q] : den[q];
-              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-              if (lane == 0) wsum[wid][k] = v;
+            for (int k = 0; k < NW; ++k) {
+              v[k] = num[k];
+              v[6 + k] = den[k];
             }
+            const double tot = transpose_sum16(v);
+            if (!(lane & 1) && lane < 24) wsum[wid][lane >> 1] = tot;
           } else if (lane < 12) {
             wsum[wid][lane] = 0.0;
           }
           __syncthreads();
-          if (threadIdx.x < 12) {
+          if (threadIdx.x < 24) {
+            // lane 2k + h sums value k over warps 8h .. 8h + 7, then the pair adds up
+            const int k = threadIdx.x >> 1, h = threadIdx.x & 1;
             double v = 0.0;
-            for (int w = 0; w < nwarps; ++w) v += wsum[w][threadIdx.x];
-            red[(size_t)blockIdx.x * 16 + threadIdx.x] = v;
+#pragma unroll
+            for (int w = 0; w < kBlock / 64; ++w) v += wsum[h * (kBlock / 64) + w][k];
+            v += __shfl_xor_sync(0x00ffffffu, v, 1);
+            if (!h) red[(size_t)blockIdx.x * 16 + k] = v;
           }
         }
         if (!grid_sync(m.bar, ep, m.err)) return;
       }
     }
     used = step + 1;
-    // every block sums the partials in the same fixed order: warp k < 12 adds up field k, lane l
-    // over the blocks l, l + 32, ..., then a butterfly over the lanes (the partials of this step
-    // are not overwritten before two more barriers, so no barrier is needed after reading them)
-    const double *red = m.red + (size_t)(step & 1) * gridDim.x * 16;
-    if ((threadIdx.x >> 5) < 12) {
-      const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      double v = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(red + (size_t)b * 16 + k);
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) wsum[0][k] = v;
-    }
-    __syncthreads();
-    // stop when max_k sqrt(num_k / den_k) < tol, tested as num_k < tol^2 den_k
-    if (threadIdx.x < 32) {
-      const int k = threadIdx.x;
-      bool done = m.tol > 0.0;
-      if (k < NW && wsum[0][6 + k] > 0.0) done = done && wsum[0][k] < m.tol * m.tol * wsum[0][6 + k];
-      done = __all_sync(0xffffffffu, done);
-      if (k == 0) sdone = done;
-    }
-    __syncthreads();
-    if (sdone) break;
   }
   // closed domain: rescale the density to the domain's total mass (velocity, temperatures kept)
   if (!grid_sync(m.bar, ep, m.err)) return;
