@@ -90,7 +90,7 @@ struct gsis_solver {
   int *d_colcells = nullptr;
   int ncol0 = 0;
   std::vector<int> colcells;
-  double *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr, *m_dF = nullptr;
+  double *m_red = nullptr, *m_Ffc = nullptr, *m_wfl = nullptr, *m_G = nullptr;
   int macro_grid = 0, macro_block = 256;
   // pinned host words the step's results are copied into, so a step can be enqueued without
   // the host waiting (pageable read-backs would block)
@@ -347,7 +347,7 @@ struct gsis_solver {
       m.W = m_W; m.pr = m_pr; m.gW = m_gW; m.phW = m_phW; m.gP = m_gP; m.aux = m_aux; m.R = m_R; m.invD = m_invD;
       m.dW = m_dW; m.Fc = m_Fc; m.corr = m_corr; m.gam = m_gam; m.red = m_red; m.Ffc = m_Ffc;
       m.wfl = m_wfl;
-      m.dF = m_dF;
+      m.G = m_G;
       m.Wout = d_Wnew;
       m.bar = d_bar;
       m.err = d_err;
@@ -802,7 +802,7 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->m_corr, nc * 6 * sizeof(double));
   A(s->m_gam, nc * 3 * sizeof(double));
   A(s->m_Ffc, nc * 18 * sizeof(double));
-  A(s->m_dF, nc * 18 * sizeof(double));
+  A(s->m_G, nc * 36 * sizeof(double));
   A(s->m_wfl, (size_t)(s->nwall + 1) * 6 * sizeof(double));
 #undef A
   if (rc) return rc;

@@ -212,7 +212,8 @@ struct MacroArgs {
   const int *colcells;     // red cells (i+j+k even) then black cells
   int ncol0;               // number of red cells
   double *W, *pr, *aux, *gW, *phW, *gP, *R, *invD, *dW, *Fc, *corr, *gam, *red, *Ffc, *wfl;
-  double *dF;              // [cell][3][6] axis-flux increment F(W + dW) - F(W) of the last update
+  double *G;               // [cell][3][2][6] off-diagonal terms a cell publishes for its neighbours
+                           // along each axis: [0] for the upper one, [1] for the lower one
   double *Wout;            // [cell][6] prim W^{n+1}
   unsigned *bar;           // barrier counter, generation; zero at launch
   int *err;

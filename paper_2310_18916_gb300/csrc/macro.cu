@@ -40,6 +40,7 @@ constexpr int NAUX = 8;                      // mu, nu, c_s, lam_x, lam_y, lam_z
 
 constexpr int kBarGroups = 8, kBarStride = 32;  // arrival counters, 128 bytes apart
 constexpr int kListCap = 2048;                  // cells per block and last pass evaluated compacted
+constexpr size_t kResidualSmem = 12 * kBlock * sizeof(double);  // per-thread inner-residual partials
 static_assert(kBarGroups * kBarStride <= MACRO_BAR_WORDS, "barrier words");
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
@@ -430,44 +431,33 @@ __device__ void wall_item(const MacroArgs &m, int wf) {
   for (int k = 0; k < 6; ++k) m.wfl[(size_t)wf * 6 + k] = k < NW ? feq[k] * A : 0.0;
 }
 
-// E, the face on side sd of axis a of cell c.  With nb_term it adds the face's off-diagonal term
-// (1/2V) A [Delta F_j(n) - Gamma dW_j] to acc, Delta F_j(n) = sg dF_j along the axis (the
-// neighbour stored F(W_j + dW_j) - F(W_j) when it was updated); in the first pass it adds the
-// face's outward flux to S.
+// E, publishing.  A cell updated in a pass writes, for each of its axes a, the two off-diagonal
+// terms its neighbours along a read in the other colour's next pass: the upper neighbour (face
+// on its low side) reads -dF - Gamma_hi dW, the lower one (face on its high side) +dF - Gamma_lo dW,
+// dF = F_a(W + dW) - F_a(W) and Gamma of the face in question.  A reader then needs one
+// five-vector per face, scaled by A / (2V).
 template <int NW>
-__device__ __forceinline__ void sweep_face(const MacroArgs &m, const int *cs, int c, const int *nt, int a, int sd,
-                                           bool nb_term, bool first, double *acc, double *S) {
-  const KinGeom &g = m.g;
-  const int na = pick3(a, nt[0], nt[1], nt[2]);
-  const bool inside = sd ? na < pick3(a, g.n[0], g.n[1], g.n[2]) - 1 : na > 0;
-  if (inside) {
-    const int csa = pick3(a, cs[0], cs[1], cs[2]);
-    const int j = sd ? c + csa : c - csa;
-    if (nb_term) {
-      const double gam = m.gam[(size_t)(sd ? c : j) * 3 + a];
-      const double half_AoV = 0.5 * axis_cells(m, a)[na].invh;  // A / (2 V) on a rectilinear cell
-      const double *dFj = m.dF + ((size_t)j * 3 + a) * 6;
+__device__ __forceinline__ void publish_terms(const MacroArgs &m, int c, int a, const double *dF, const double *d,
+                                              double gam_lo, double gam_hi) {
+  double *G = m.G + ((size_t)c * 3 + a) * 12;
 #pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        const double df = sd ? dFj[k] : -dFj[k];  // Delta F_j(n) = sg dF_j, sg = +-1
-        acc[k] = fma(fma(-gam, m.dW[(size_t)j * 6 + k], df), half_AoV, acc[k]);
-      }
-    }
-    if (first)
-#pragma unroll
-      for (int k = 0; k < NW; ++k) S[k] += sd ? m.Ffc[((size_t)c * 3 + a) * 6 + k] : -m.Ffc[((size_t)j * 3 + a) * 6 + k];
-  } else if (first) {
-    const int wb = g.wall_base[2 * a + sd];
-    if (wb >= 0) {
-      const int trn = pick3(a, nt[1] + g.n[1] * nt[2], nt[0] + g.n[0] * nt[2], nt[0] + g.n[0] * nt[1]);
-#pragma unroll
-      for (int k = 0; k < NW; ++k) S[k] += m.wfl[(size_t)(wb + trn) * 6 + k];
-    }
+  for (int k = 0; k < NW; ++k) {
+    G[k] = fma(-gam_hi, d[k], -dF[k]);
+    G[6 + k] = fma(-gam_lo, d[k], dF[k]);
   }
+}
+
+// Gamma of the faces below and above cell c along axis a (zero where the face is a boundary)
+__device__ __forceinline__ void face_gammas(const MacroArgs &m, int c, int csa, int na, int n, int a, double &lo,
+                                            double &hi) {
+  lo = na > 0 ? m.gam[(size_t)(c - csa) * 3 + a] : 0.0;
+  hi = na < n - 1 ? m.gam[(size_t)c * 3 + a] : 0.0;
 }
 }  // namespace
 
-template <int NW>
+// NW conservative fields (5 Shakhov, 6 Rykov); MA >= the active axis count bounds the per-face
+// registers of the sweeps (2 for 1D and 2D meshes, 3 for 3D).
+template <int NW, int MA>
 __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   const KinGeom &g = m.g;
   const int nc = g.nc, nact = g.nact;
@@ -481,6 +471,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   // cells this block updated in a last pass, for the compacted evaluation of their primitives
   // and fluxes (overflow entries are evaluated in place)
   __shared__ int slist[kListCap];
+  extern __shared__ double rsd[];  // [12][kBlock] inner-residual partials, value-major
   __shared__ int scount;
   if (threadIdx.x == 0) scount = 0;
 
@@ -503,6 +494,9 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
   }
   if (!grid_sync(m.bar, ep, m.err)) return;
 
+  // the cell of this thread's first sweep item in each colour (the items are the same every pass)
+  const int cell0 = it.first >> 1 < m.ncol0 ? m.colcells[it.first >> 1] : 0;
+  const int cell1 = it.first >> 1 < nc - m.ncol0 ? m.colcells[m.ncol0 + (it.first >> 1)] : 0;
   int used = 0;
   for (int step = 0; step < m.steps; ++step) {
     // axis fluxes at the start of this step, and the buffer for those at its end
@@ -554,9 +548,10 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     if (check && sdone) break;
     // ---- E: red/black point-implicit sweeps, a pair of lanes per cell: lane sd takes the faces
     // on side sd of every active axis and the axis fluxes of axes sd, sd + 2
-    double num[NW], den[NW];  // inner residual partials of this thread
+    // inner residual partials of this thread, in shared memory (registers are the sweeps')
+    double *const num = rsd + threadIdx.x, *const den = rsd + 6 * kBlock + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < NW; ++k) num[k] = den[k] = 0.0;
+    for (int k = 0; k < NW; ++k) num[k * kBlock] = den[k * kBlock] = 0.0;
     for (int sw = 0; sw < m.sweeps; ++sw) {
       const bool first = sw == 0, last = sw == m.sweeps - 1;
       for (int col = 0; col < 2; ++col) {
@@ -568,43 +563,87 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
         for (int t = it.first; t < nitems; t += it.stride) {
           const int q = t >> 1, sd = t & 1;
           const bool live = q < cnt, upd = live && sd == 0;
-          const int c = live ? m.colcells[off + q] : 0;
+          const int c = !live ? 0 : (t == it.first ? (col ? cell1 : cell0) : m.colcells[off + q]);
           int nt[3];
           nat_of(g, c, nt);
-          // the cell's own data, loaded before the neighbours' so that both are in flight together:
-          // lane 0 (the update) W, the inverse diagonal and R (first pass: K at the first inner
-          // step, else corr); both lanes the start-of-step flux of axis sd
-          double Wc[6], iDc[NW], Rc[NW], Fco[NW];
+          // one wave of loads.  The cell's own data: both lanes W, and for the axes they publish
+          // the start-of-step flux and the face Gammas; lane 0 (the update) the inverse diagonal
+          // and R (first pass: K at the first inner step, else corr).  Per face on side sd: the
+          // neighbour's published term (and, in the first pass, the face flux).
+          const bool pub = live && sd < nact && !(last && col == 1);
+          double Wc[6], iDc[NW], Rc[NW], Fco[NW], gl = 0.0, gh = 0.0;
 #pragma unroll
-          for (int k = 0; k < 6; ++k) Wc[k] = 0.0;
+          for (int k = 0; k < 6; ++k) Wc[k] = live ? m.W[(size_t)c * 6 + k] : 0.0;
 #pragma unroll
           for (int k = 0; k < NW; ++k) iDc[k] = Rc[k] = Fco[k] = 0.0;
           if (upd) {
             const double *src = first ? (step == 0 ? m.K : m.corr) : m.R;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) Wc[k] = m.W[(size_t)c * 6 + k];
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
               iDc[k] = m.invD[(size_t)c * 6 + k];
               Rc[k] = src[(size_t)c * 6 + k];
             }
           }
-          if (live && !last && sd < nact)
+          if (pub) {
+            if (!last)
 #pragma unroll
-            for (int k = 0; k < NW; ++k) Fco[k] = Fc[((size_t)c * 3 + sd) * 6 + k];
-          double acc[NW], S[NW];
+              for (int k = 0; k < NW; ++k) Fco[k] = Fc[((size_t)c * 3 + sd) * 6 + k];
+            face_gammas(m, c, pick3(sd, cs[0], cs[1], cs[2]), pick3(sd, nt[0], nt[1], nt[2]),
+                        pick3(sd, g.n[0], g.n[1], g.n[2]), sd, gl, gh);
+          }
+          double Gn[MA][NW], hA[MA], S[NW];
+          bool nbf[MA];
 #pragma unroll
-          for (int k = 0; k < NW; ++k) acc[k] = S[k] = 0.0;
-          if (live)
+          for (int k = 0; k < NW; ++k) S[k] = 0.0;
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-              if (a < nact) sweep_face<NW>(m, cs, c, nt, a, sd, nb_term, first, acc, S);
+          for (int a = 0; a < MA; ++a) {
+            nbf[a] = false;
+            hA[a] = 0.0;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) Gn[a][k] = 0.0;
+            if (!live || a >= nact) continue;
+            const int na = pick3(a, nt[0], nt[1], nt[2]);
+            const bool inside = sd ? na < pick3(a, g.n[0], g.n[1], g.n[2]) - 1 : na > 0;
+            const int csa = pick3(a, cs[0], cs[1], cs[2]);
+            const int j = sd ? c + csa : c - csa;
+            if (inside && nb_term) {
+              nbf[a] = true;
+              hA[a] = 0.5 * axis_cells(m, a)[na].invh;  // A / (2 V) on a rectilinear cell
+              const double *Gj = m.G + ((size_t)j * 3 + a) * 12 + 6 * sd;
+#pragma unroll
+              for (int k = 0; k < NW; ++k) Gn[a][k] = Gj[k];
+            }
+            if (first) {
+              if (inside) {
+#pragma unroll
+                for (int k = 0; k < NW; ++k) S[k] += sd ? m.Ffc[((size_t)c * 3 + a) * 6 + k] : -m.Ffc[((size_t)j * 3 + a) * 6 + k];
+              } else {
+                const int wb = g.wall_base[2 * a + sd];
+                if (wb >= 0) {
+                  const int trn = pick3(a, nt[1] + g.n[1] * nt[2], nt[0] + g.n[0] * nt[2], nt[0] + g.n[0] * nt[1]);
+#pragma unroll
+                  for (int k = 0; k < NW; ++k) S[k] += m.wfl[(size_t)(wb + trn) * 6 + k];
+                }
+              }
+            }
+          }
+          // off-diagonal sum of the lane's faces: (1/2V) A [Delta F_j(n) - Gamma dW_j]
+          double acc[NW];
+#pragma unroll
+          for (int k = 0; k < NW; ++k) acc[k] = 0.0;
+#pragma unroll
+          for (int a = 0; a < MA; ++a)
+            if (nbf[a])
+#pragma unroll
+              for (int k = 0; k < NW; ++k) acc[k] = fma(Gn[a][k], hA[a], acc[k]);
 #pragma unroll
           for (int k = 0; k < NW; ++k) {
             acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
             if (first) S[k] += __shfl_xor_sync(0xffffffffu, S[k], 1);
           }
-          double Wnew[6] = {0, 0, 0, 0, 0, 0};  // W + dW of the cell, in both lanes after the broadcast
+          double d[NW];  // the increment dW, in both lanes after the broadcast
+#pragma unroll
+          for (int k = 0; k < NW; ++k) d[k] = 0.0;
           int here = !last;  // evaluate the axis fluxes (last sweep: and primitives) in this loop
           if (upd) {
             double R[NW];
@@ -632,23 +671,18 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
 #pragma unroll
               for (int k = 0; k < NW; ++k) R[k] = Rc[k];
             }
-            double d[NW];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) Wnew[k] = Wc[k];
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-              d[k] = (R[k] - acc[k]) * iDc[k];
-              Wnew[k] += d[k];
-              m.dW[(size_t)c * 6 + k] = d[k];
-            }
+            for (int k = 0; k < NW; ++k) d[k] = (R[k] - acc[k]) * iDc[k];
             if (last) {
               // the new state; the cell joins the block's list for the compacted evaluation of
-              // its primitives, its fluxes for the next step, its increment (last red pass) and
-              // its inner-residual terms after the loop, one item per lane
+              // its primitives, its fluxes for the next step, its published terms (last red pass)
+              // and its inner-residual terms after the loop, one item per lane
 #pragma unroll
               for (int k = 0; k < NW; ++k) {
-                if (!isfinite(Wnew[k])) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
-                m.W[(size_t)c * 6 + k] = Wnew[k];
+                const double w = Wc[k] + d[k];
+                if (!isfinite(w)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
+                m.W[(size_t)c * 6 + k] = w;
+                m.dW[(size_t)c * 6 + k] = d[k];
               }
               const int slot = atomicAdd(&scount, 1);
               if (slot < kListCap) {
@@ -658,21 +692,24 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
                 const double V = cell_volume(m, nt);
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
-                  num[k] += d[k] * d[k] * V;
-                  den[k] += Wnew[k] * Wnew[k] * V;
+                  num[k * kBlock] += d[k] * d[k] * V;
+                  den[k * kBlock] += (Wc[k] + d[k]) * (Wc[k] + d[k]) * V;
                 }
               }
             }
           }
           // both lanes evaluate the axis fluxes at W + dW of their axes: the increment over the
-          // step's start for the other colour's next pass and, in the last sweep when the block's
-          // list is full, the fluxes of the next step
+          // step's start for the other colour's next pass (published with dW) and, in the last
+          // sweep when the block's list is full, the fluxes of the next step
           here = __shfl_sync(0xffffffffu, here, t & 30u);
 #pragma unroll
-          for (int k = 0; k < 6; ++k) Wnew[k] = __shfl_sync(0xffffffffu, Wnew[k], t & 30u);
+          for (int k = 0; k < NW; ++k) d[k] = __shfl_sync(0xffffffffu, d[k], t & 30u);
           if (live && here) {
+            double Wnew[6];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int k = 0; k < 6; ++k) Wnew[k] = k < NW ? Wc[k] + d[k] : Wc[k];
+#pragma unroll
+            for (int h = 0; h < (MA > 2 ? 2 : 1); ++h) {
               const int a = sd + 2 * h;
               if (a >= nact) continue;
               double F[6];
@@ -681,9 +718,13 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
               if (last)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) Fn[o + k] = F[k];
-              if (!(last && col == 1))
+              if (!(last && col == 1)) {
+                double dF[NW], lo = gl, hi = gh;
 #pragma unroll
-                for (int k = 0; k < NW; ++k) m.dF[o + k] = F[k] - (last || h ? Fc[o + k] : Fco[k]);
+                for (int k = 0; k < NW; ++k) dF[k] = F[k] - (last || h ? Fc[o + k] : Fco[k]);
+                if (h) face_gammas(m, c, pick3(a, cs[0], cs[1], cs[2]), pick3(a, nt[0], nt[1], nt[2]), pick3(a, g.n[0], g.n[1], g.n[2]), a, lo, hi);
+                publish_terms<NW>(m, c, a, dF, d, lo, hi);
+              }
             }
             if (last && upd) cell_prims<NW>(m, c, Wnew);
           }
@@ -712,8 +753,8 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
                   const double d = m.dW[(size_t)c * 6 + k];
-                  num[k] += d * d * V;
-                  den[k] += Wl[k] * Wl[k] * V;
+                  num[k * kBlock] += d * d * V;
+                  den[k * kBlock] += Wl[k] * Wl[k] * V;
                 }
               }
             }
@@ -729,9 +770,19 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
               const size_t o = ((size_t)c * 3 + a) * 6;
 #pragma unroll
               for (int k = 0; k < 6; ++k) Fn[o + k] = F[k];
-              if (col == 0)
+              if (col == 0) {
+                double dF[NW], dl[NW], lo, hi;
 #pragma unroll
-                for (int k = 0; k < NW; ++k) m.dF[o + k] = F[k] - Fc[o + k];
+                for (int k = 0; k < NW; ++k) {
+                  dF[k] = F[k] - Fc[o + k];
+                  dl[k] = m.dW[(size_t)c * 6 + k];
+                }
+                int nt[3];
+                nat_of(g, c, nt);
+                face_gammas(m, c, pick3(a, cs[0], cs[1], cs[2]), pick3(a, nt[0], nt[1], nt[2]), pick3(a, g.n[0], g.n[1], g.n[2]), a,
+                            lo, hi);
+                publish_terms<NW>(m, c, a, dF, dl, lo, hi);
+              }
             }
           }
           __syncthreads();
@@ -745,15 +796,15 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
           const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
           bool nz = false;
 #pragma unroll
-          for (int k = 0; k < NW; ++k) nz = nz || num[k] != 0.0 || den[k] != 0.0;
+          for (int k = 0; k < NW; ++k) nz = nz || num[k * kBlock] != 0.0 || den[k * kBlock] != 0.0;
           if (__any_sync(0xffffffffu, nz)) {
             double v[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) v[k] = 0.0;
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
-              v[k] = num[k];
-              v[6 + k] = den[k];
+              v[k] = num[k * kBlock];
+              v[6 + k] = den[k * kBlock];
             }
             const double tot = transpose_sum16(v);
             if (!(lane & 1) && lane < 24) wsum[wid][lane >> 1] = tot;
@@ -817,16 +868,20 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
 // must hold some.  The cooperative launch guarantees the blocks are co-resident.
 cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block) {
   (void)nc;
-  int dev = 0, nsm = 0, per5 = 0, per6 = 0;
+  int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per5, macro_kernel<5>, kBlock, 0);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per6, macro_kernel<6>, kBlock, 0);
-  if (e != cudaSuccess) return e;
-  if (per5 < 1 || per6 < 1) return cudaErrorInvalidConfiguration;
+  void (*const kernels[])(MacroArgs) = {macro_kernel<5, 2>, macro_kernel<5, 3>, macro_kernel<6, 2>, macro_kernel<6, 3>};
+  for (auto k : kernels) {
+    int per = 0;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResidualSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kBlock, kResidualSmem);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+  }
   if (max_sms > 0 && max_sms < nsm) nsm = max_sms;
   *grid = nsm < MACRO_MAX_GRID ? nsm : MACRO_MAX_GRID;
   *block = kBlock;
@@ -836,8 +891,10 @@ cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block) {
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s) {
   MacroArgs copy = a;
   void *args[] = {&copy};
-  void *fn = a.nW == 6 ? (void *)macro_kernel<6> : (void *)macro_kernel<5>;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s);
+  const bool a3 = a.g.nact > 2;
+  void *fn = a.nW == 6 ? (a3 ? (void *)macro_kernel<6, 3> : (void *)macro_kernel<6, 2>)
+                       : (a3 ? (void *)macro_kernel<5, 3> : (void *)macro_kernel<5, 2>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, kResidualSmem, s);
 }
 
 }  // namespace gsis
