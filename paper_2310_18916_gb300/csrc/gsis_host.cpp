@@ -189,6 +189,7 @@ struct gsis_solver {
     a.wpart = static_cast<T *>(d_wpart);
     a.nwall = nwall;
     a.nblocks = nblocks;
+    a.err = d_err;
     return a;
   }
 
@@ -844,7 +845,7 @@ static int allocate_and_upload(gsis_solver *s) {
                  "wall constants");
   if (rc) return rc;
   // kinetic launch shape: one warp per cell of a colour, up to 16 warps, within the register file
-  s->kin_smem = kinetic_smem_bytes<T>(s->kg, s->nvdf);
+  s->kin_smem = kinetic_smem_bytes<T, S>(s->kg, s->nvdf);
   int dev = 0, smem_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -94,12 +94,13 @@ struct KinArgs {
   T *wpart;              // [block][wall face][NWF] outgoing wall-flux moments (wall cells only)
   int nwall;
   int nblocks;
+  int *err;              // device error flag (a bounded wait that timed out)
 };
 
 // ---- launchers (defined in the .cu files) ----
 template <typename T, typename S>
 cudaError_t launch_kinetic(const KinArgs<T, S> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s);
-template <typename T>
+template <typename T, typename S>
 size_t kinetic_smem_bytes(const KinGeom &g, int nvdf);
 template <typename T, typename S>
 cudaError_t launch_wall_prepass(const KinArgs<T, S> &a, const int *wall_cell, const int *wall_side, int nwall,

@@ -223,20 +223,90 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// ---- bulk asynchronous copies (TMA) into shared memory, completed on an mbarrier ----
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// the one arrival of a phase, announcing the bytes its copies will deliver
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase of the given parity; false on time-out (about a second)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (unsigned i = 0; !mbar_test(bar, parity); ++i)
+    if ((i & 63u) == 63u && clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+
+// global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void load_state_shared(const T *src, T *st, int n) {
+#pragma unroll
+  for (int q = 0; q < 40; ++q)
+    if (q < n) st[q] = src[q];
+}
+
+// shared-memory layout of the kinetic kernel: the three-colour ring and the face buffers (T),
+// the bulk-copy staging area for one colour (stored f in S, then the state rows in T), the
+// mbarrier
+template <typename T, typename S>
+struct KinSmem {
+  size_t ring, ebuf, rawf, rawst, bar, total;
+  __host__ __device__ KinSmem(const KinGeom &g, int nv, int sl) {
+    ring = 0;
+    ebuf = ring + (size_t)3 * g.maxcol * nv * VB * sizeof(T);
+    rawf = ebuf;
+    for (int a = 0; a < 3; ++a) rawf += (size_t)g.ntrans[a] * nv * VB * sizeof(T);
+    rawf = (rawf + 15) & ~(size_t)15;
+    rawst = (rawf + (size_t)g.maxcol * nv * VB * sizeof(S) + 15) & ~(size_t)15;
+    bar = (rawst + (size_t)g.maxcol * sl * sizeof(T) + 15) & ~(size_t)15;
+    total = bar + 16;
+  }
+};
+
 template <typename T, typename S, int NACT, int NV>
 __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const KinGeom &G = A.g;
-  T *ring = reinterpret_cast<T *>(smem_raw);
+  constexpr int SL = stage_state_len<S, NV>();
+  const KinSmem<T, S> L(G, NV, SL);
+  T *ring = reinterpret_cast<T *>(smem_raw + L.ring);
   T *ebuf[3];
   {
-    T *p = ring + (size_t)3 * G.maxcol * NV * VB;
+    T *p = reinterpret_cast<T *>(smem_raw + L.ebuf);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       ebuf[a] = p;
       p += (size_t)G.ntrans[a] * NV * VB;
     }
   }
+  S *rawf = reinterpret_cast<S *>(smem_raw + L.rawf);
+  T *rawst = reinterpret_cast<T *>(smem_raw + L.rawst);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L.bar);
   const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int oct = A.boct[b];
   const int sg[3] = {oct & 1 ? -1 : 1, oct & 2 ? -1 : 1, oct & 4 ? -1 : 1};
@@ -264,28 +334,79 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   const int4 *natcell = A.natcell + (size_t)oct * G.nc;
   const T K3 = (T)G.K3;
   const size_t slot_stride = (size_t)G.maxcol * NV * VB;
-  constexpr int SL = stage_state_len<S, NV>();
-
-  auto stage = [&](int c) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  // Colour c + 2's stored f rows (VB values per cell and VDF) and state rows are copied into the
+  // staging area by bulk copies while colour c is computed; one thread per copy, the cell index
+  // loaded before the wait so that its latency is hidden.
+  constexpr unsigned kRowBytes = VB * sizeof(S), kStBytes = SL * sizeof(T);
+  auto colour_bytes = [&](int c) { return (unsigned)(A.col_off[c + 1] - A.col_off[c]) * (NV * kRowBytes + kStBytes); };
+  auto prefetch_cell = [&](int c) {
+    if (c >= G.ncol) return 0;
     const int off = A.col_off[c], cnt = A.col_off[c + 1] - off;
+    return tid < cnt * (NV + 1) ? __ldg(&natcell[off + tid / (NV + 1)].x) : 0;
+  };
+  auto issue = [&](int c, int cell0) {
+    const int off = A.col_off[c], cnt = A.col_off[c + 1] - off;
+    for (int i = tid; i < cnt * (NV + 1); i += nthr) {
+      const int p = i / (NV + 1), q = i - p * (NV + 1);
+      const int cell = i == tid ? cell0 : __ldg(&natcell[off + p].x);
+      if (q < NV)
+        bulk_copy(rawf + (size_t)(p * NV + q) * VB, F[q] + (size_t)cell * VB, kRowBytes, bar);
+      else
+        bulk_copy(rawst + (size_t)p * SL, state_of(A.st, cell), kStBytes, bar);
+    }
+  };
+  // Each colour is one phase of the mbarrier; on a time-out the block flags the error, waits
+  // once more (bounded) for its copies in flight and leaves.
+  unsigned phase = 0;
+  auto await = [&]() {
+    const bool ok = mbar_wait(bar, phase & 1u);
+    ++phase;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicCAS(A.err, 0, GSIS_ERR_TIMEOUT);
+        mbar_wait(bar, (phase - 1) & 1u);
+      }
+      return false;
+    }
+    return true;
+  };
+  auto stage = [&](int c) {
+    const int cnt = A.col_off[c + 1] - A.col_off[c];
     T *slot = ring + (size_t)(c % 3) * slot_stride;
     for (int p = warp; p < cnt; p += nw) {
-      const int cell = __ldg(&natcell[off + p].x);
       T st[SL];
-      load_state<SL>(state_of(A.st, cell), st);
+      load_state_shared<T>(rawst + (size_t)p * SL, st, SL);
       T stored[NV], f[NV];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(F[q] + (size_t)cell * VB + lane);
+      for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(rawf + (size_t)(p * NV + q) * VB + lane);
       corrected_all<T, S, NV>(stored, st, xi[0], xi[1], xi[2], f);
 #pragma unroll
       for (int q = 0; q < NV; ++q) slot[(p * NV + q) * VB + lane] = f[q];
     }
   };
 
+  if (tid == 0) {
+    mbar_init(bar);
+    mbar_expect(bar, colour_bytes(0));
+  }
+  __syncthreads();
+  issue(0, prefetch_cell(0));
+  int pf = prefetch_cell(1);
+  if (!await()) return;
   stage(0);
+  if (tid == 0 && G.ncol > 1) mbar_expect(bar, colour_bytes(1));
+  __syncthreads();
+  if (G.ncol > 1) issue(1, pf);
   for (int c = 0; c < G.ncol; ++c) {
-    if (c + 1 < G.ncol) stage(c + 1);
+    pf = prefetch_cell(c + 2);
+    if (c + 1 < G.ncol) {
+      if (!await()) return;
+      stage(c + 1);
+      if (tid == 0 && c + 2 < G.ncol) mbar_expect(bar, colour_bytes(c + 2));
+    }
     __syncthreads();
+    if (c + 2 < G.ncol) issue(c + 2, pf);
     const T *slotm = ring + (size_t)((c + 2) % 3) * slot_stride;
     const T *slot0 = ring + (size_t)(c % 3) * slot_stride;
     const T *slotp = ring + (size_t)((c + 1) % 3) * slot_stride;
@@ -409,11 +530,10 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   }
 }
 
-template <typename T>
+template <typename T, typename S>
 size_t kinetic_smem_bytes(const KinGeom &g, int nvdf) {
-  size_t n = (size_t)3 * g.maxcol * VB;
-  for (int a = 0; a < 3; ++a) n += (size_t)g.ntrans[a] * VB;
-  return n * nvdf * sizeof(T);
+  const int sl = nvdf == 2 ? stage_state_len<S, 2>() : stage_state_len<S, 1>();
+  return KinSmem<T, S>(g, nvdf, sl).total;
 }
 
 template <typename T, typename S>
@@ -826,7 +946,8 @@ cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon
 GSIS_INST(float, float)
 GSIS_INST(double, double)
 GSIS_INST(float, __nv_bfloat16)
-template size_t kinetic_smem_bytes<float>(const KinGeom &, int);
-template size_t kinetic_smem_bytes<double>(const KinGeom &, int);
+template size_t kinetic_smem_bytes<float, float>(const KinGeom &, int);
+template size_t kinetic_smem_bytes<double, double>(const KinGeom &, int);
+template size_t kinetic_smem_bytes<float, __nv_bfloat16>(const KinGeom &, int);
 
 }  // namespace gsis
