@@ -733,7 +733,7 @@ static size_t footprint(const gsis_solver *s) {
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
-  b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 36 + 18 + 3 + 18 + 8 + 18) * 8;  // synthetic-solve work
+  b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 36 + 6 + 3 + 18 + 8 + 36) * 8;  // synthetic-solve work
   b += (size_t)s->nslots * 4 * (T + 8) + (size_t)s->nwall * 32 * 8 + 3 * nc * 4 + (1 << 20);
   return b;
 }
