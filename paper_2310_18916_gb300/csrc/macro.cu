@@ -132,7 +132,20 @@ __device__ __forceinline__ double prim_of(const double *W, double dr, double *p)
   return ir;
 }
 
-__device__ __forceinline__ bool physical(const double *p) { return p[0] > 0.0 && p[4] > 0.0 && p[5] > 0.0; }
+// FP64 comparisons, min and max run at the FP64 rate on this GPU (a warp instruction holds a
+// sub-partition's FP64 pipe for ~64 cycles, like an FMA).  Where the operands are known to be
+// non-negative, the order of their bit patterns as integers is their numeric order, so these take
+// the integer pipes and give the same results (no NaN reaches them on a physical state).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// x > 0 exactly as the FP64 comparison: +0 < bits <= +inf (negative values, -0 and NaN fail)
+__device__ __forceinline__ bool gt0(double x) {
+  return (unsigned long long)(dbits(x) - 1) < 0x7ff0000000000000ULL;
+}
+// x < y and max(x, y) for x, y >= 0
+__device__ __forceinline__ bool lt_nn(double x, double y) { return dbits(x) < dbits(y); }
+__device__ __forceinline__ double max_nn(double x, double y) { return dbits(x) < dbits(y) ? y : x; }
+
+__device__ __forceinline__ bool physical(const double *p) { return gt0(p[0]) && gt0(p[4]) && gt0(p[5]); }
 
 // Euler flux along n = sg e_a: (rho u_n, rho u u_n + p_t n, (rho E + p_t) u_n, rho E_r u_n)
 template <int NW>
@@ -172,9 +185,9 @@ __device__ __forceinline__ double sound(double Tt) { return sqrt(5.0 * Tt / 6.0)
 __device__ __forceinline__ void venkat_axis(double g, double rlo, double rhi, double dp, double dn, double eps2,
                                             double &nn, double &dd) {
   const double dh = g * rhi, dl = g * rlo;
-  const bool pos = g > 0.0;
+  const bool pos = gt0(g);
   const double mh = pos ? dp : dn, ml = pos ? dn : dp;
-  const bool hi = fabs(mh) * fabs(dl) <= fabs(ml) * fabs(dh);
+  const bool hi = !lt_nn(fabs(ml) * fabs(dh), fabs(mh) * fabs(dl));
   // (g = 0: D2 = 0 and the face value is 1, which never lowers the minimum)
   const double d2 = hi ? dh : dl, dm = hi ? mh : ml;
   const double dm2 = fma(dm, dm, eps2);
@@ -270,7 +283,12 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl,
     const bool lim = k < NW;
     const double *q = lim ? m.W + k : m.pr + 1 + (k - NW);
     const double qi = q[(size_t)c * 6];
-    double gr[3] = {0, 0, 0}, qmax = qi, qmin = qi, V = 1.0;
+    double gr[3] = {0, 0, 0}, V = 1.0;
+    // bounds qmax - qi, qmin - qi as the largest positive and negative neighbour difference
+    // (rounding is monotonic, so max fl(q - qi) = fl(max q - qi)): bit patterns of the positive
+    // differences and magnitudes of the negative ones, compared as integers; a missing neighbour
+    // gives the difference +0, which changes neither
+    long long pbits = 0, nmag = 0;
     AxisCell<double> gc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -278,22 +296,30 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl,
       V *= gc[a].h;
       if (!g.act[a]) continue;
       double lo = qi, hi = qi;
-      if (nt[a] > 0) { lo = q[(size_t)(c - cs[a]) * 6]; qmax = fmax(qmax, lo); qmin = fmin(qmin, lo); }
-      if (nt[a] < g.n[a] - 1) { hi = q[(size_t)(c + cs[a]) * 6]; qmax = fmax(qmax, hi); qmin = fmin(qmin, hi); }
-      gr[a] = gc[a].clo * (lo - qi) + gc[a].chi * (hi - qi);
+      if (nt[a] > 0) lo = q[(size_t)(c - cs[a]) * 6];
+      if (nt[a] < g.n[a] - 1) hi = q[(size_t)(c + cs[a]) * 6];
+      const double dlo = lo - qi, dhi = hi - qi;
+      gr[a] = gc[a].clo * dlo + gc[a].chi * dhi;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const long long b = dbits(e ? dhi : dlo), mag = b & 0x7fffffffffffffffLL;
+        pbits = b > pbits ? b : pbits;
+        nmag = b < 0 && mag > nmag ? mag : nmag;
+      }
     }
     if (lim) {
       // Venkatakrishnan: min over the faces (and 1) of (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
       // one face per axis (the one with the smaller |Dm| / |D2|), compared by cross-multiplication
       // and divided once
-      const double eps2 = g.K3 * V, dp = qmax - qi, dn = qmin - qi;
+      const double eps2 = g.K3 * V, dp = __longlong_as_double(pbits);
+      const double dn = nmag ? __longlong_as_double(nmag | (long long)0x8000000000000000ULL) : 0.0;
       double bn = 1.0, bd = 1.0;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (!g.act[a]) continue;
         double nn, dd;
         venkat_axis(gr[a], gc[a].rlo, gc[a].rhi, dp, dn, eps2, nn, dd);
-        if (nn * bd < bn * dd) { bn = nn; bd = dd; }
+        if (lt_nn(nn * bd, bn * dd)) { bn = nn; bd = dd; }
       }
 #pragma unroll
       for (int a = 0; a < 3; ++a) m.gW[((size_t)c * 6 + k) * 3 + a] = gr[a];
@@ -322,7 +348,7 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl,
         const int j = c + (sd ? cs[a] : -cs[a]);
         const double *xj = m.aux + (size_t)j * NAUX;
         const double idx = sd ? ga.pad0 : m.ax[a][nt[a] - 1].pad0;  // 1 / centre distance
-        gam = fmax(li, xj[3 + a]) + 2.0 * fmax(xi[1], xj[1]) * idx;
+        gam = max_nn(li, xj[3 + a]) + 2.0 * max_nn(xi[1], xj[1]) * idx;
         if (sd) m.gam[(size_t)c * 3 + a] = gam;
       } else {
         gam = li + 2.0 * xi[1] * (2.0 * ga.invh);  // wall at half a cell width
@@ -382,8 +408,8 @@ __device__ void face_item(const MacroArgs &m, const int *cs, int c, int a) {
   double FL[6], FR[6], F[6];
   euler_axis_prim<NW>(WL, pL, a, FL);
   euler_axis_prim<NW>(WR, pR, a, FR);
-  const double lam = fmax(fabs(pick3(a, pL[1], pL[2], pL[3])) + sound(pL[4]),
-                          fabs(pick3(a, pR[1], pR[2], pR[3])) + sound(pR[4]));
+  const double lam = max_nn(fabs(pick3(a, pL[1], pL[2], pL[3])) + sound(pL[4]),
+                            fabs(pick3(a, pR[1], pR[2], pR[3])) + sound(pR[4]));
 #pragma unroll
   for (int k = 0; k < 6; ++k) F[k] = k < NW ? 0.5 * (FL[k] + FR[k]) - 0.5 * lam * (WR[k] - WL[k]) : 0.0;
   // NSF viscous and conductive flux, face gradients = mean of the cells' gradients
