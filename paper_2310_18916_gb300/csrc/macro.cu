@@ -593,21 +593,24 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
           int nt[3];
           nat_of(g, c, nt);
           // one wave of loads.  The cell's own data: both lanes W, and for the axes they publish
-          // the start-of-step flux and the face Gammas; lane 0 (the update) the inverse diagonal
-          // and R (first pass: K at the first inner step, else corr).  Per face on side sd: the
-          // neighbour's published term (and, in the first pass, the face flux).
+          // the start-of-step flux and the face Gammas; for the update, lane sd takes the
+          // components 3 sd .. 3 sd + 2 (those below NW): their inverse diagonal and R (first pass:
+          // K at the first inner step, else corr).  Per face on side sd: the neighbour's published
+          // term (and, in the first pass, the face flux).
           const bool pub = live && sd < nact && !(last && col == 1);
-          double Wc[6], iDc[NW], Rc[NW], Fco[NW], gl = 0.0, gh = 0.0;
+          const int k0 = 3 * sd;  // first component of this lane's share of the update
+          double Wc[6], iDo[3], Ro[3], Fco[NW], gl = 0.0, gh = 0.0;
 #pragma unroll
           for (int k = 0; k < 6; ++k) Wc[k] = live ? m.W[(size_t)c * 6 + k] : 0.0;
 #pragma unroll
-          for (int k = 0; k < NW; ++k) iDc[k] = Rc[k] = Fco[k] = 0.0;
-          if (upd) {
+          for (int k = 0; k < NW; ++k) Fco[k] = 0.0;
+          {
             const double *src = first ? (step == 0 ? m.K : m.corr) : m.R;
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-              iDc[k] = m.invD[(size_t)c * 6 + k];
-              Rc[k] = src[(size_t)c * 6 + k];
+            for (int j = 0; j < 3; ++j) {
+              const bool ok = live && k0 + j < NW;
+              iDo[j] = ok ? m.invD[(size_t)c * 6 + k0 + j] : 0.0;
+              Ro[j] = ok ? src[(size_t)c * 6 + k0 + j] : 0.0;
             }
           }
           if (pub) {
@@ -662,74 +665,87 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
             if (nbf[a])
 #pragma unroll
               for (int k = 0; k < NW; ++k) acc[k] = fma(Gn[a][k], hA[a], acc[k]);
+          // the pair's totals of this lane's components: its own partial plus the partner's
+          // (a + b = b + a, so both lanes see the sums a single lane would form)
+          auto own = [&](const double *v, int j) { return sd ? (3 + j < NW ? v[3 + j] : 0.0) : v[j]; };
+          auto other = [&](const double *v, int j) { return sd ? v[j] : (3 + j < NW ? v[3 + j] : 0.0); };
+          double acco[3], So[3];
 #pragma unroll
-          for (int k = 0; k < NW; ++k) {
-            acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
-            if (first) S[k] += __shfl_xor_sync(0xffffffffu, S[k], 1);
+          for (int j = 0; j < 3; ++j) {
+            acco[j] = own(acc, j) + __shfl_xor_sync(0xffffffffu, other(acc, j), 1);
+            So[j] = first ? own(S, j) + __shfl_xor_sync(0xffffffffu, other(S, j), 1) : 0.0;
           }
-          double d[NW];  // the increment dW, in both lanes after the broadcast
+          // the update of this lane's components (the point-implicit solve of Eq. res_macro)
+          double Rn[3];
+          if (first) {
+            // residual R_i = -(S + corr) / V, corr = K - S frozen at the first inner step
+            const double iV = cell_inv_volume(m, nt);
 #pragma unroll
-          for (int k = 0; k < NW; ++k) d[k] = 0.0;
+            for (int j = 0; j < 3; ++j) {
+              const bool ok = live && k0 + j < NW;
+              if (step == 0) {
+                Ro[j] -= So[j];
+                if (ok) m.corr[(size_t)c * 6 + k0 + j] = Ro[j];
+              }
+              Rn[j] = -(So[j] + Ro[j]) * iV;
+            }
+            if (NW == 6 && live && sd == 1) {
+              const double *p = m.pr + (size_t)c * 6;
+              const double tau = 2.0 * m.Kn / sqrt(kPi) * power(p[4], m.omega - 1.0) / p[0];
+              const double T = (3.0 * p[4] + m.d_r * p[5]) / (3.0 + m.d_r);
+              Rn[2] += m.d_r * p[0] * (T - p[5]) / (4.0 * m.Z_r * tau);
+            }
+            if (!last)
+#pragma unroll
+              for (int j = 0; j < 3; ++j)
+                if (live && k0 + j < NW) m.R[(size_t)c * 6 + k0 + j] = Rn[j];
+          } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Rn[j] = Ro[j];
+          }
+          double dO[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) dO[j] = (Rn[j] - acco[j]) * iDo[j];
           int here = !last;  // evaluate the axis fluxes (last sweep: and primitives) in this loop
-          if (upd) {
-            double R[NW];
-            if (first) {
-              // residual R_i = -(S + corr) / V, corr = K - S frozen at the first inner step
-              if (step == 0)
+          if (last && live) {
+            // the new state; the cell joins the block's list for the compacted evaluation of its
+            // primitives, its fluxes for the next step, its published terms (last red pass) and
+            // its inner-residual terms after the loop, one item per lane
 #pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                  Rc[k] -= S[k];
-                  m.corr[(size_t)c * 6 + k] = Rc[k];
-                }
-              const double iV = cell_inv_volume(m, nt);
-#pragma unroll
-              for (int k = 0; k < NW; ++k) R[k] = -(S[k] + Rc[k]) * iV;
-              if (NW == 6) {
-                const double *p = m.pr + (size_t)c * 6;
-                const double tau = 2.0 * m.Kn / sqrt(kPi) * power(p[4], m.omega - 1.0) / p[0];
-                const double T = (3.0 * p[4] + m.d_r * p[5]) / (3.0 + m.d_r);
-                R[NW - 1] += m.d_r * p[0] * (T - p[5]) / (4.0 * m.Z_r * tau);
-              }
-              if (!last)
-#pragma unroll
-                for (int k = 0; k < NW; ++k) m.R[(size_t)c * 6 + k] = R[k];
-            } else {
-#pragma unroll
-              for (int k = 0; k < NW; ++k) R[k] = Rc[k];
+            for (int j = 0; j < 3; ++j) {
+              if (k0 + j >= NW) continue;
+              const double w = (sd ? Wc[3 + j] : Wc[j]) + dO[j];
+              if (!isfinite(w)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
+              m.W[(size_t)c * 6 + k0 + j] = w;
+              m.dW[(size_t)c * 6 + k0 + j] = dO[j];
             }
-#pragma unroll
-            for (int k = 0; k < NW; ++k) d[k] = (R[k] - acc[k]) * iDc[k];
-            if (last) {
-              // the new state; the cell joins the block's list for the compacted evaluation of
-              // its primitives, its fluxes for the next step, its published terms (last red pass)
-              // and its inner-residual terms after the loop, one item per lane
-#pragma unroll
-              for (int k = 0; k < NW; ++k) {
-                const double w = Wc[k] + d[k];
-                if (!isfinite(w)) atomicCAS(m.err, 0, GSIS_ERR_DIVERGED);
-                m.W[(size_t)c * 6 + k] = w;
-                m.dW[(size_t)c * 6 + k] = d[k];
-              }
+            if (upd) {
               const int slot = atomicAdd(&scount, 1);
-              if (slot < kListCap) {
-                slist[slot] = c;
-              } else {
-                here = 1;
-                const double V = cell_volume(m, nt);
-#pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                  num[k * kBlock] += d[k] * d[k] * V;
-                  den[k * kBlock] += (Wc[k] + d[k]) * (Wc[k] + d[k]) * V;
-                }
-              }
+              if (slot < kListCap) slist[slot] = c;
+              else here = 1;
             }
           }
-          // both lanes evaluate the axis fluxes at W + dW of their axes: the increment over the
-          // step's start for the other colour's next pass (published with dW) and, in the last
-          // sweep when the block's list is full, the fluxes of the next step
+          // both lanes take the whole increment and evaluate the axis fluxes at W + dW of their
+          // axes: the increment over the step's start for the other colour's next pass
+          // (published with dW) and, in the last sweep when the block's list is full, the fluxes
+          // of the next step
           here = __shfl_sync(0xffffffffu, here, t & 30u);
+          double d[NW];
 #pragma unroll
-          for (int k = 0; k < NW; ++k) d[k] = __shfl_sync(0xffffffffu, d[k], t & 30u);
+          for (int j = 0; j < 3; ++j) {
+            const double x = __shfl_xor_sync(0xffffffffu, dO[j], 1);
+            d[j] = sd ? x : dO[j];
+            if (3 + j < NW) d[3 + j] = sd ? dO[j] : x;
+          }
+          if (last && upd && here) {
+            // list overflow: the inner-residual terms here
+            const double V = cell_volume(m, nt);
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+              num[k * kBlock] += d[k] * d[k] * V;
+              den[k * kBlock] += (Wc[k] + d[k]) * (Wc[k] + d[k]) * V;
+            }
+          }
           if (live && here) {
             double Wnew[6];
 #pragma unroll
