@@ -272,33 +272,42 @@ __device__ void cell_prims(const MacroArgs &m, int c, const double *W) {
   x[5] = fabs(p[3]) + cs;
 }
 
-// B, one item: LSQ gradient of field k (limited conservative field for k < NW, else primitive
-// k - NW + 1) with its Venkatakrishnan limiter, or (k = NW + 5) the local time step and diagonal.
-template <int NW>
-__device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl, int c, int k) {
+// B, one cell's limited fields: LSQ gradients of the conservative fields k < NW with their
+// Venkatakrishnan limiters.  The neighbours' rows are read once for all fields (a missing
+// neighbour reads the cell's own row: difference +0).
+template <int NW, int MA>
+__device__ void limited_cell(const MacroArgs &m, const int *cs, int c) {
   const KinGeom &g = m.g;
   int nt[3];
   nat_of(g, c, nt);
-  if (k < NW + 5) {
-    const bool lim = k < NW;
-    const double *q = lim ? m.W + k : m.pr + 1 + (k - NW);
-    const double qi = q[(size_t)c * 6];
-    double gr[3] = {0, 0, 0}, V = 1.0;
+  AxisCell<double> gc[3];
+  double V = 1.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gc[a] = m.ax[a][nt[a]];
+    V *= gc[a].h;
+  }
+  const double eps2 = g.K3 * V;
+  const double *Wc = m.W + (size_t)c * 6;
+  const double *Wlo[MA], *Whi[MA];
+#pragma unroll
+  for (int a = 0; a < MA; ++a) {
+    const bool act = a < g.nact;
+    Wlo[a] = act && nt[a] > 0 ? m.W + (size_t)(c - cs[a]) * 6 : Wc;
+    Whi[a] = act && nt[a] < g.n[a] - 1 ? m.W + (size_t)(c + cs[a]) * 6 : Wc;
+  }
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    const double qi = Wc[k];
+    double gr[3] = {0, 0, 0};
     // bounds qmax - qi, qmin - qi as the largest positive and negative neighbour difference
     // (rounding is monotonic, so max fl(q - qi) = fl(max q - qi)): bit patterns of the positive
-    // differences and magnitudes of the negative ones, compared as integers; a missing neighbour
-    // gives the difference +0, which changes neither
+    // differences and magnitudes of the negative ones, compared as integers
     long long pbits = 0, nmag = 0;
-    AxisCell<double> gc[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      gc[a] = m.ax[a][nt[a]];
-      V *= gc[a].h;
-      if (!g.act[a]) continue;
-      double lo = qi, hi = qi;
-      if (nt[a] > 0) lo = q[(size_t)(c - cs[a]) * 6];
-      if (nt[a] < g.n[a] - 1) hi = q[(size_t)(c + cs[a]) * 6];
-      const double dlo = lo - qi, dhi = hi - qi;
+    for (int a = 0; a < MA; ++a) {
+      if (a >= g.nact) continue;
+      const double dlo = Wlo[a][k] - qi, dhi = Whi[a][k] - qi;
       gr[a] = gc[a].clo * dlo + gc[a].chi * dhi;
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -307,37 +316,63 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl,
         nmag = b < 0 && mag > nmag ? mag : nmag;
       }
     }
-    if (lim) {
-      // Venkatakrishnan: min over the faces (and 1) of (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
-      // one face per axis (the one with the smaller |Dm| / |D2|), compared by cross-multiplication
-      // and divided once
-      const double eps2 = g.K3 * V, dp = __longlong_as_double(pbits);
-      const double dn = nmag ? __longlong_as_double(nmag | (long long)0x8000000000000000ULL) : 0.0;
-      double bn = 1.0, bd = 1.0;
+    // Venkatakrishnan: min over the faces (and 1) of (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
+    // one face per axis (the one with the smaller |Dm| / |D2|), compared by cross-multiplication
+    // and divided once
+    const double dp = __longlong_as_double(pbits);
+    const double dn = nmag ? __longlong_as_double(nmag | (long long)0x8000000000000000ULL) : 0.0;
+    double bn = 1.0, bd = 1.0;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (!g.act[a]) continue;
-        double nn, dd;
-        venkat_axis(gr[a], gc[a].rlo, gc[a].rhi, dp, dn, eps2, nn, dd);
-        if (lt_nn(nn * bd, bn * dd)) { bn = nn; bd = dd; }
-      }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) m.gW[((size_t)c * 6 + k) * 3 + a] = gr[a];
-      m.phW[(size_t)c * 6 + k] = bn / bd;
-    } else {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) m.gP[((size_t)c * 5 + (k - NW)) * 3 + a] = gr[a];
+    for (int a = 0; a < MA; ++a) {
+      if (a >= g.nact) continue;
+      double nn, dd;
+      venkat_axis(gr[a], gc[a].rlo, gc[a].rhi, dp, dn, eps2, nn, dd);
+      if (lt_nn(nn * bd, bn * dd)) { bn = nn; bd = dd; }
     }
-    return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) m.gW[((size_t)c * 6 + k) * 3 + a] = gr[a];
+    m.phW[(size_t)c * 6 + k] = bn / bd;
   }
-  // local time step and diagonal D_i = 1/dt_i + (1/2V_i) sum_f Gamma_f A_f (- dQ/dW)
+}
+
+// B, one cell's primitive gradients (u, T_t and for Rykov T_r: the NSF stress and heat flux) and
+// its local time step and diagonal D_i = 1/dt_i + (1/2V_i) sum_f Gamma_f A_f (- dQ/dW)
+template <int NW, int MA>
+__device__ void prim_cell(const MacroArgs &m, const int *cs, double inv_cfl, int c) {
+  const KinGeom &g = m.g;
+  int nt[3];
+  nat_of(g, c, nt);
+  constexpr int NP = NW == 6 ? 5 : 4;  // Shakhov: T_r = T_t, whose gradient is not taken twice
+  const double *pc = m.pr + (size_t)c * 6;
+  AxisCell<double> gc[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) gc[a] = m.ax[a][nt[a]];
+  const double *plo[MA], *phi_[MA];
+#pragma unroll
+  for (int a = 0; a < MA; ++a) {
+    const bool act = a < g.nact;
+    plo[a] = act && nt[a] > 0 ? m.pr + (size_t)(c - cs[a]) * 6 : pc;
+    phi_[a] = act && nt[a] < g.n[a] - 1 ? m.pr + (size_t)(c + cs[a]) * 6 : pc;
+  }
+#pragma unroll
+  for (int f = 0; f < NP; ++f) {
+    const double qi = pc[1 + f];
+    double gr[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < MA; ++a) {
+      if (a >= g.nact) continue;
+      gr[a] = gc[a].clo * (plo[a][1 + f] - qi) + gc[a].chi * (phi_[a][1 + f] - qi);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) m.gP[((size_t)c * 5 + f) * 3 + a] = gr[a];
+  }
   const double *xi = m.aux + (size_t)c * NAUX;
-  const double V = cell_volume(m, nt), iV = cell_inv_volume(m, nt);
+  const double V = gc[0].h * gc[1].h * gc[2].h, iV = gc[0].invh * gc[1].invh * gc[2].invh;
   double lsum = 0.0, gsum = 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (!g.act[a]) continue;
-    const AxisCell<double> ga = m.ax[a][nt[a]];
+    const AxisCell<double> ga = gc[a];
     const double A = V * ga.invh, li = xi[3 + a];
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
@@ -359,8 +394,7 @@ __device__ void gradient_item(const MacroArgs &m, const int *cs, double inv_cfl,
   const double inv_dt = lsum * iV * inv_cfl;
   double srcdiag = 0.0;
   if (NW == 6) {
-    const double *p = m.pr + (size_t)c * 6;
-    const double tau = 2.0 * m.Kn / sqrt(kPi) * power(p[4], m.omega - 1.0) / p[0];
+    const double tau = 2.0 * m.Kn / sqrt(kPi) * power(pc[4], m.omega - 1.0) / pc[0];
     srcdiag = 1.0 / (m.Z_r * tau);
   }
   const double Dt = inv_dt + gsum * 0.5 * iV, iD = __drcp_rn(Dt);
@@ -543,13 +577,14 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) m.red[(size_t)3 * gridDim.x * 16 + ((step - 1) & 1) * 16 + blockIdx.x] = v;
     }
-    // ---- B: gradients and limiters per (cell, field); time step and diagonal per cell.  Items
-    // are field-major so the lanes of a warp take the same branch.  (Shakhov: T_r = T_t, whose
-    // gradient is not taken twice.)
-    constexpr int NB = NW == 6 ? NW + 6 : NW + 5;
-    for (int t = it.first; t < nc * NB; t += it.stride) {
-      const int k = t / nc;
-      gradient_item<NW>(m, cs, inv_cfl, t - k * nc, NW == 5 && k == NW + 4 ? NW + 5 : k);
+    // ---- B: per cell, the limited fields' gradients and limiters (items [0, nc)), then the
+    // primitive gradients, time step and diagonal (items [nc, 2 nc)): one round of items over
+    // the GPU, each reading its neighbours' rows once
+    for (int t = it.first; t < 2 * nc; t += it.stride) {
+      if (t < nc)
+        limited_cell<NW, MA>(m, cs, t);
+      else
+        prim_cell<NW, MA>(m, cs, inv_cfl, t - nc);
     }
     if (!grid_sync(m.bar, ep, m.err)) return;
     // ---- C: interior + faces of the active axes, then the wall faces.  Warp 0 loads the
