@@ -325,6 +325,7 @@ struct gsis_solver {
       m.g = kg;
       for (int d = 0; d < 3; ++d) m.ax[d] = d_ax64[d];
       m.Kn = Kn;
+      m.mu0 = Kn / std::sqrt(3.14159265358979323846);
       m.omega = omega;
       m.cfl = opt.macro_cfl;
       m.tol = opt.macro_tol;

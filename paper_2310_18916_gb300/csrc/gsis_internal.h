@@ -200,6 +200,7 @@ struct MacroArgs {
   KinGeom g;
   const AxisCell<double> *ax[3];
   double Kn, omega, cfl, tol;
+  double mu0;              // Kn / sqrt(pi): mu = mu0 T^omega
   int model, nW, steps, sweeps;
   double d_r, Z_r, A[4];
   double mass_ref;

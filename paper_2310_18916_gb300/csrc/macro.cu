@@ -174,7 +174,7 @@ __device__ __forceinline__ void euler_axis_prim(const double *W, const double *p
   F[5] = (NW == 6 ? W[5] : 0.0) * un;
 }
 
-__device__ __forceinline__ double sound(double Tt) { return sqrt(5.0 * Tt / 6.0); }
+__device__ __forceinline__ double sound(double Tt) { return sqrt(Tt * (5.0 / 6.0)); }
 
 // Venkatakrishnan face function of the two faces of one axis, r_lo < 0 < r_hi.  The increment
 // D2 = g r of the face where it is positive meets the bound dp = qmax - qi, the other face dn =
@@ -262,7 +262,7 @@ __device__ void cell_prims(const MacroArgs &m, int c, const double *W) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) m.pr[(size_t)c * 6 + k] = p[k];
   double *x = m.aux + (size_t)c * NAUX;
-  const double mu = m.Kn / sqrt(kPi) * power(p[4], m.omega);
+  const double mu = m.mu0 * power(p[4], m.omega);
   const double cs = sound(p[4]);
   x[0] = mu;
   x[1] = mu * ir;
@@ -394,7 +394,7 @@ __device__ void prim_cell(const MacroArgs &m, const int *cs, double inv_cfl, int
   const double inv_dt = lsum * iV * inv_cfl;
   double srcdiag = 0.0;
   if (NW == 6) {
-    const double tau = 2.0 * m.Kn / sqrt(kPi) * power(pc[4], m.omega - 1.0) / pc[0];
+    const double tau = 2.0 * m.mu0 * power(pc[4], m.omega - 1.0) / pc[0];
     srcdiag = 1.0 / (m.Z_r * tau);
   }
   const double Dt = inv_dt + gsum * 0.5 * iV, iD = __drcp_rn(Dt);
@@ -415,7 +415,9 @@ __device__ void face_item(const MacroArgs &m, const int *cs, int c, int a) {
   const int j = c + pick3(a, cs[0], cs[1], cs[2]);
   const AxisCell<double> *axa = axis_cells(m, a);
   const double rhi = axa[na].rhi, rlo = axa[na + 1].rlo;
-  const double A = cell_volume(m, nt) * axa[na].invh;
+  // face area: the product of the cell's widths along the two other axes
+  const double h0 = m.ax[0][nt[0]].h, h1 = m.ax[1][nt[1]].h, h2 = m.ax[2][nt[2]].h;
+  const double A = a == 0 ? h1 * h2 : (a == 1 ? h0 * h2 : h0 * h1);
   double WL[6], WR[6], pL[6], pR[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
@@ -444,36 +446,39 @@ __device__ void face_item(const MacroArgs &m, const int *cs, int c, int a) {
   euler_axis_prim<NW>(WR, pR, a, FR);
   const double lam = max_nn(fabs(pick3(a, pL[1], pL[2], pL[3])) + sound(pL[4]),
                             fabs(pick3(a, pR[1], pR[2], pR[3])) + sound(pR[4]));
+  // area-integrated Rusanov flux (A/2) [F_L + F_R - lam (W_R - W_L)]
+  const double hA = 0.5 * A;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) F[k] = k < NW ? 0.5 * (FL[k] + FR[k]) - 0.5 * lam * (WR[k] - WL[k]) : 0.0;
-  // NSF viscous and conductive flux, face gradients = mean of the cells' gradients
+  for (int k = 0; k < 6; ++k) F[k] = k < NW ? hA * fma(-lam, WR[k] - WL[k], FL[k] + FR[k]) : 0.0;
+  // NSF viscous and conductive flux with the face gradients, velocity and viscosity the means of
+  // the two cells' values: the sums are taken here and the halves folded into q = A mu_f / 2
+  // (stress -mu_f (G + G^T - 2/3 div G) with G = S / 2) and the conductivities (linear in mu)
   const double *gPc = m.gP + (size_t)c * 15, *gPj = m.gP + (size_t)j * 15;
-  double G3[3][3], Ga[3], uf[3];  // G3[b][d] = d u_b / dx_d, Ga[b] = d u_a / dx_b
+  double S3[3][3], us[3];  // S3[b][d] = sum of the cells' d u_b / dx_d
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) G3[b][d] = 0.5 * (gPc[b * 3 + d] + gPj[b * 3 + d]);
-    uf[b] = 0.5 * (m.pr[(size_t)c * 6 + 1 + b] + m.pr[(size_t)j * 6 + 1 + b]);
+    for (int d = 0; d < 3; ++d) S3[b][d] = gPc[b * 3 + d] + gPj[b * 3 + d];
+    us[b] = m.pr[(size_t)c * 6 + 1 + b] + m.pr[(size_t)j * 6 + 1 + b];
   }
-#pragma unroll
-  for (int b = 0; b < 3; ++b) Ga[b] = pick3(a, G3[0][b], G3[1][b], G3[2][b]);
-  const double gTa = 0.5 * (gPc[9 + a] + gPj[9 + a]);
-  const double gTra = 0.5 * (gPc[12 + a] + gPj[12 + a]);
-  const double muf = 0.5 * (m.aux[(size_t)c * NAUX] + m.aux[(size_t)j * NAUX]);
-  double kt, kr;
-  kappas(m, muf, &kt, &kr);
-  const double div = G3[0][0] + G3[1][1] + G3[2][2];
+  const double gTs = gPc[9 + a] + gPj[9 + a];
+  const double gTrs = NW == 6 ? gPc[12 + a] + gPj[12 + a] : 0.0;
+  const double q = 0.25 * A * (m.aux[(size_t)c * NAUX] + m.aux[(size_t)j * NAUX]);
+  double qt, qr;  // conductivities at viscosity q: the heat fluxes' coefficients of the gradient sums
+  kappas(m, q, &qt, &qr);
+  const double divs = S3[0][0] + S3[1][1] + S3[2][2];
   double sn[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b)
-    sn[b] = -muf * (pick3(a, G3[b][0], G3[b][1], G3[b][2]) + Ga[b] - (a == b ? 2.0 / 3.0 * div : 0.0));
+    sn[b] = -q * (pick3(a, S3[b][0], S3[b][1], S3[b][2]) + pick3(a, S3[0][b], S3[1][b], S3[2][b]) -
+                  (a == b ? (2.0 / 3.0) * divs : 0.0));
 #pragma unroll
   for (int b = 0; b < 3; ++b) F[1 + b] += sn[b];
-  F[4] += sn[0] * uf[0] + sn[1] * uf[1] + sn[2] * uf[2] - kt * gTa - (NW == 6 ? kr * gTra : 0.0);
-  if (NW == 6) F[5] += -kr * gTra;
+  F[4] += fma(0.5, sn[0] * us[0] + sn[1] * us[1] + sn[2] * us[2], -qt * gTs) - (NW == 6 ? qr * gTrs : 0.0);
+  if (NW == 6) F[5] += -qr * gTrs;
   double *Ff = m.Ffc + ((size_t)c * 3 + a) * 6;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) Ff[k] = F[k] * A;
+  for (int k = 0; k < 6; ++k) Ff[k] = F[k];
 }
 
 // C, one wall item: equilibrium wall flux (area-integrated) of wall face wf
@@ -565,9 +570,10 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     // the previous step's inner residual: block k < 12 sums value k (num_k, den_k) of the
     // blocks' partials in fixed order; every block tests them during C
     const bool check = m.tol > 0.0 && step > 0;
-    if (check && blockIdx.x < 12 && threadIdx.x < 32) {
+    if (check && blockIdx.x < 12 && (threadIdx.x >> 5) == kBlock / 32 - 1) {
+      // (the block's last warp, the last one dealt B items)
       const double *red = m.red + (size_t)((step - 1) & 1) * gridDim.x * 16;
-      const int lane = threadIdx.x;
+      const int lane = threadIdx.x & 31;
       double v = 0.0;
 #pragma unroll
       for (int i = 0; i < MACRO_MAX_GRID / 32; ++i) {
@@ -726,7 +732,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
             }
             if (NW == 6 && live && sd == 1) {
               const double *p = m.pr + (size_t)c * 6;
-              const double tau = 2.0 * m.Kn / sqrt(kPi) * power(p[4], m.omega - 1.0) / p[0];
+              const double tau = 2.0 * m.mu0 * power(p[4], m.omega - 1.0) / p[0];
               const double T = (3.0 * p[4] + m.d_r * p[5]) / (3.0 + m.d_r);
               Rn[2] += m.d_r * p[0] * (T - p[5]) / (4.0 * m.Z_r * tau);
             }
