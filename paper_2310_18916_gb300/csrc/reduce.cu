@@ -45,17 +45,20 @@ __global__ void reduce_moments_kernel(const double *mp, int nchunks, int nc, int
 template <typename T>
 __global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nblocks, int nwall, const int *wall_side,
                                    const double *rho_w, const double *Zw, int emit, double *wf) {
-  const int n = nwall * NWF;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int w = idx / NWF, m = idx % NWF;
-    const int side = wall_side[w], a = side / 2;
-    const bool plus = side & 1;
-    double out = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-      const bool neg = (boct[b] >> a) & 1;
-      if (neg == plus) continue;  // this block's velocities move away from the wall
-      out += (double)wpart[((size_t)b * nwall + w) * NWF + m];
-    }
+  // one block per wall face, warp m < NWF for moment m: lane l sums the blocks l, l + 32, ... in
+  // order, then a fixed butterfly over the lanes
+  const int w = blockIdx.x, m = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w >= nwall || m >= NWF) return;
+  const int side = wall_side[w], a = side / 2;
+  const bool plus = side & 1;
+  double out = 0.0;
+  for (int b = lane; b < nblocks; b += 32) {
+    const bool neg = (boct[b] >> a) & 1;
+    if (neg == plus) continue;  // this block's velocities move away from the wall
+    out += (double)wpart[((size_t)b * nwall + w) * NWF + m];
+  }
+  for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
+  if (lane == 0) {
     // the re-emitted half once per solve: by one shard of a velocity-sharded solve
     const double tot = out + (emit ? rho_w[w] * Zw[6 * side + m] : 0.0);
     wf[(size_t)w * 6 + m] = plus ? tot : -tot;
@@ -75,8 +78,7 @@ cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpar
   reduce_moments_kernel<<<grid, 256, 0, s>>>(mp, nchunks, g.nc, np, vol, st64, mom, K);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nwall == 0 || wpart == nullptr) return e;
-  reduce_wall_kernel<T><<<(nwall * NWF + 255) / 256, 256, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw,
-                                                                   emit ? 1 : 0, wf);
+  reduce_wall_kernel<T><<<nwall, 32 * NWF, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw, emit ? 1 : 0, wf);
   return cudaGetLastError();
 }
 template cudaError_t launch_reduce<float>(const double *, int, int, const float *, const int8_t *, int, const KinGeom &,
