@@ -597,7 +597,9 @@ __global__ void wall_prepass_kernel(const KinArgs<T, S> A, const int *wall_cell,
     const T *vp = A.vel + (size_t)v * 4;
     const T x = vp[0], y = vp[1], z = vp[2], w = vp[3];
     const T xa = axn == 0 ? x : (axn == 1 ? y : z);
-    if (!(w > (T)0) || !((double)xa * dir > 0.0)) continue;
+    // (the direction test and the product in the arithmetic type: FP64 conversions, compares
+    // and products per velocity would run at the FP64 rate; dir = +-1 keeps them exact)
+    if (!(w > (T)0) || !(xa * (T)dir > (T)0)) continue;
     const int blk = v / VB, ln = v % VB;
     const S *Fb = A.f + (size_t)blk * G.nc * VB;
     const T fi = corrected_stored<T, S>(Fio<T, S>::ld(Fb + (size_t)cell * VB + ln), st, x, y, z);
@@ -616,7 +618,7 @@ __global__ void wall_prepass_kernel(const KinArgs<T, S> A, const int *wall_cell,
     const T phi = venkat_phi<T, NACT>(fi, fmax, fmin, gr, rlo, rhi, (T)G.K3 * V);
     const T r = (side & 1) ? rhi[axn] : rlo[axn];
     const T face = fi + phi * gr[axn] * r;
-    acc += (double)w * fabs((double)xa) * (double)face;
+    acc += (double)(w * fabs(xa) * face);
   }
   __shared__ double red[256];
   red[threadIdx.x] = acc;
