@@ -250,6 +250,15 @@ int gsis_destroy(gsis_handle h);
 /* Message of the last error on h (or of the last failed gsis_create when h is NULL). */
 const char *gsis_last_error(gsis_handle h);
 
+/* Self-test of the bounded device waits, on the current device: which = 0 runs the synthetic
+ * solve's grid barrier with one of its two blocks leaving without arriving; which = 1 waits on an
+ * mbarrier phase that nothing completes (the kinetic kernel's staging wait).  Each wait gives up
+ * after ~2^24 clock cycles (a few ms) and raises the device error flag, which is returned in
+ * *device_status (GSIS_E_TIMEOUT when the wait ran out as designed, GSIS_OK if it did not).  The
+ * context stays usable.  Uses its own cudaMalloc'd scratch (freed before returning).
+ * Returns GSIS_OK, GSIS_E_INVALID (bad which / NULL) or GSIS_E_CUDA. */
+int gsis_selftest_wait_timeout(int which, int *device_status);
+
 #ifdef __cplusplus
 }
 #endif

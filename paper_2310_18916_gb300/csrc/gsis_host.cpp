@@ -1161,3 +1161,23 @@ extern "C" const char *gsis_last_error(gsis_handle h) {
   if (!h) return g_create_error.c_str();
   return h->last_error.c_str();
 }
+
+extern "C" int gsis_selftest_wait_timeout(int which, int *device_status) {
+  if ((which != 0 && which != 1) || !device_status) return GSIS_E_INVALID;
+  unsigned *bar = nullptr;
+  int *err = nullptr;
+  cudaError_t e = cudaMalloc(&bar, MACRO_BAR_WORDS * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(bar, 0, MACRO_BAR_WORDS * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+  const long long limit = 1LL << 24;
+  if (e == cudaSuccess) e = which == 0 ? probe_barrier_timeout(bar, err, limit, nullptr) : probe_mbarrier_timeout(err, limit, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (bar) cudaFree(bar);
+  if (err) cudaFree(err);
+  if (e != cudaSuccess) return GSIS_E_CUDA;
+  *device_status = h;
+  return GSIS_OK;
+}

@@ -224,6 +224,9 @@ struct MacroArgs {
 constexpr int MACRO_MAX_GRID = 512;  // blocks of the synthetic-solve kernel at most
 constexpr int MACRO_BAR_WORDS = 512;  // barrier words, cleared before each launch
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s);
+// self-tests of the bounded device waits (each raises GSIS_ERR_TIMEOUT in *err after `limit` cycles)
+cudaError_t probe_barrier_timeout(unsigned *bar, int *err, long long limit, cudaStream_t s);
+cudaError_t probe_mbarrier_timeout(int *err, long long limit, cudaStream_t s);
 cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block);
 
 }  // namespace gsis

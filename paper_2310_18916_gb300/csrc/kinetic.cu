@@ -248,11 +248,26 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity) {
 }
 
 // bounded wait for the phase of the given parity; false on time-out (about a second)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit = 1LL << 31) {
   const long long t0 = clock64();
   for (unsigned i = 0; !mbar_test(bar, parity); ++i)
-    if ((i & 63u) == 63u && clock64() - t0 > (1LL << 31)) return false;
+    if ((i & 63u) == 63u && clock64() - t0 > limit) return false;
   return true;
+}
+
+// Self-test of the bounded mbarrier wait: a phase that no arrival and no copy completes, so the
+// wait runs out after `limit` cycles and raises GSIS_ERR_TIMEOUT.
+__global__ void mbarrier_timeout_probe(int *err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u, limit);
+  if (!ok && threadIdx.x == 0) atomicCAS(err, 0, GSIS_ERR_TIMEOUT);
+}
+
+cudaError_t probe_mbarrier_timeout(int *err, long long limit, cudaStream_t s) {
+  mbarrier_timeout_probe<<<1, 32, 0, s>>>(err, limit);
+  return cudaGetLastError();
 }
 
 // global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)

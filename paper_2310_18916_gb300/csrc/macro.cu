@@ -60,7 +60,7 @@ __device__ __forceinline__ void red_release_add(unsigned *p, unsigned x) {
 // keeps same-address atomics from serialising on one line.  The spin is bounded: on time-out
 // it raises the error flag.  Returns false when any block has flagged an error, so every caller
 // leaves the kernel together.
-__device__ bool grid_sync(unsigned *bar, unsigned &epoch, int *err) {
+__device__ bool grid_sync(unsigned *bar, unsigned &epoch, int *err, long long limit = kSpinLimit) {
   ++epoch;
   __syncthreads();
   if (threadIdx.x == 0) red_release_add(bar + kBarStride * (blockIdx.x % kBarGroups), 1u);
@@ -69,7 +69,7 @@ __device__ bool grid_sync(unsigned *bar, unsigned &epoch, int *err) {
     const unsigned target = epoch * gsize;
     const long long t0 = clock64();
     for (unsigned i = 0; ld_acquire(bar + kBarStride * g) < target; ++i) {
-      if ((i & 15u) == 15u && (clock64() - t0 > kSpinLimit || *(volatile int *)err != 0)) {
+      if ((i & 15u) == 15u && (clock64() - t0 > limit || *(volatile int *)err != 0)) {
         atomicCAS(err, 0, GSIS_ERR_TIMEOUT);
         break;
       }
@@ -969,6 +969,19 @@ cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block) {
   *grid = nsm < MACRO_MAX_GRID ? nsm : MACRO_MAX_GRID;
   *block = kBlock;
   return cudaSuccess;
+}
+
+// Self-test of the bounded grid barrier: block 1 of two co-resident blocks leaves without
+// arriving, so block 0's wait runs out after `limit` cycles and raises GSIS_ERR_TIMEOUT.
+__global__ void barrier_timeout_probe(unsigned *bar, int *err, long long limit) {
+  if (blockIdx.x == 1) return;
+  unsigned ep = 0;
+  grid_sync(bar, ep, err, limit);
+}
+
+cudaError_t probe_barrier_timeout(unsigned *bar, int *err, long long limit, cudaStream_t s) {
+  void *args[] = {&bar, &err, &limit};
+  return cudaLaunchCooperativeKernel((void *)barrier_timeout_probe, dim3(2), dim3(32), args, 0, s);
 }
 
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s) {

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgsis.so")
 
 D = C.POINTER(C.c_double)
-GSIS_OK, GSIS_E_NOT_CONVERGED, GSIS_E_UNSUPPORTED = 0, -6, -7
+GSIS_OK, GSIS_E_TIMEOUT, GSIS_E_NOT_CONVERGED, GSIS_E_UNSUPPORTED = 0, -5, -6, -7
 F64, F32, BF16 = 0, 1, 2
 PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16}
 MODE_GSIS, MODE_DVM = 0, 1
@@ -55,7 +55,7 @@ _lib = None
 SYMBOLS = ("gsis_default_options", "gsis_footprint_bytes", "gsis_create", "gsis_iterate", "gsis_step_async",
            "gsis_step_wait", "gsis_moments",
            "gsis_residual", "gsis_nwall", "gsis_wall", "gsis_wall_loads", "gsis_kinetic_flux_sum", "gsis_get_f", "gsis_set_f", "gsis_stats",
-           "gsis_destroy", "gsis_last_error", "gsis_profile", "gsis_vdf_moments_noalloc")
+           "gsis_destroy", "gsis_last_error", "gsis_profile", "gsis_vdf_moments_noalloc", "gsis_selftest_wait_timeout")
 
 
 def load(path: str = LIB_PATH):
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
     L.gsis_destroy.argtypes = [P]
     L.gsis_last_error.argtypes = [P]
     L.gsis_last_error.restype = C.c_char_p
+    L.gsis_selftest_wait_timeout.argtypes = [C.c_int, C.POINTER(C.c_int)]
     _lib = L
     return L
 
@@ -310,6 +311,21 @@ class Solver:
 
 
 _NO_EXCHANGE = ALLREDUCE_FN(lambda ptr, count, stream, ctx: 1)  # footprints never exchange
+
+
+def selftest_wait_timeout(which):
+    """Run a bounded device wait that cannot complete (0: the grid barrier of the synthetic
+    solve, 1: the kinetic kernel's mbarrier wait) and return the device error status it raised
+    (GSIS_E_TIMEOUT when the wait ran out as designed)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("the GSIS library needs a CUDA GPU")
+    st = C.c_int()
+    rc = load().gsis_selftest_wait_timeout(int(which), C.byref(st))
+    if rc != GSIS_OK:
+        raise GsisError(rc, "self-test launch failed")
+    return st.value
 
 
 def footprint_bytes(problem, precision="f32", shard=None):
