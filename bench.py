@@ -17,6 +17,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -60,7 +61,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples (the JSON line carries their summary); CLOCKS_DIR keeps them elsewhere
+        self.path = os.path.join(os.environ.get("CLOCKS_DIR", tempfile.gettempdir()), f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:

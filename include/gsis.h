@@ -40,7 +40,7 @@ extern "C" {
 #define GSIS_E_DIVERGED (-4)      /* non-finite or non-positive density / temperature */
 #define GSIS_E_TIMEOUT (-5)       /* a bounded device-side wait gave up */
 #define GSIS_E_NOT_CONVERGED (-6) /* max_outer reached above tol; results are valid */
-#define GSIS_E_UNSUPPORTED (-7)   /* valid input outside what this build implements */
+#define GSIS_E_UNSUPPORTED (-7)   /* valid input outside what the library implements */
 
 enum gsis_bc_type { GSIS_BC_WALL = 1, GSIS_BC_PERIODIC = 2 };
 enum gsis_model { GSIS_SHAKHOV = 0, GSIS_RYKOV = 1 };
@@ -49,7 +49,7 @@ enum gsis_mode { GSIS_MODE_GSIS = 0, GSIS_MODE_DVM = 1 };
 
 /* Structured hexahedral block (spatial finite-volume cells of Section 3.1).
  * nodes: (ni+1)(nj+1)(nk+1) x 3 doubles (host), node (I,J,K) at index I + (ni+1)(J + (nj+1)K).
- * This build requires a rectilinear block (node x depends on I only, y on J, z on K,
+ * The library requires a rectilinear block (node x depends on I only, y on J, z on K,
  * increasing), else GSIS_E_UNSUPPORTED.
  * bc[side], side = x-, x+, y-, y+, z-, z+: an axis with one cell must be PERIODIC on both
  * sides (it then carries no transport); an axis with more cells must be WALL on both sides.
@@ -106,7 +106,7 @@ typedef struct {
   int macro_sweeps;     /* red-black LU-SGS passes per inner step (default 4, Algorithm 2) */
   double macro_cfl;     /* pseudo-time CFL of the synthetic solve (default 100) */
   double macro_tol;     /* inner early exit on the relative increment (default 1e-10) */
-  double kin_inv_dt;    /* 1/dt of the kinetic delta form (default 0: steady; this build supports 0) */
+  double kin_inv_dt;    /* 1/dt of the kinetic delta form (default 0: steady; only 0 is supported) */
   double venkat_K;      /* Venkatakrishnan constant, eps^2 = (K V^(1/3))^3 (default 1) */
   int kinetic_presteps; /* plain kinetic steps before the GSIS loop (default 10, Algorithm 1) */
   const double *init_W; /* optional host array, per cell rho, ux, uy, uz, Tt, Tr; f0 = Maxwellian.

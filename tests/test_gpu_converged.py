@@ -42,7 +42,7 @@ def test_couette_config1_fp64_converged_matches_oracle():
     print(f"config 1: GPU {done} steps {tg:.2f} s, oracle {len(ho)} steps {to:.2f} s, P_xy {Pg.mean():.6f}")
 
 
-def test_cavity_fp32_converged_within_north_star_tolerance():
+def test_cavity_fp32_converged_within_fp32_tolerance():
     """FP32 VDF storage: converged density and temperature within rel-L2 1e-4 of the FP64 oracle.
     FP32 storage leaves eps a floor near 1e-6 (the step-to-step change of f rounded to 6e-8 of f,
     amplified by the condition of the iteration), so the GPU stops at 1e-5 and is compared with
