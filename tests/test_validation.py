@@ -1,0 +1,74 @@
+"""Input validation at the boundary, without a GPU: gsis_footprint_bytes runs the same checks and
+set-up as gsis_create, so every rejected input returns its documented error code and nothing is
+allocated or launched."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2310_18916_gb300 import gsis
+from paper_2310_18916_gb300 import workloads as wl
+
+GSIS_E_INVALID = -1
+
+
+def code(problem, **kw):
+    try:
+        gsis.footprint_bytes(problem, **kw)
+    except gsis.GsisError as e:
+        return e.code
+    return gsis.GSIS_OK
+
+
+def test_valid_problems_pass():
+    for p in (wl.couette(n_cells=12, nv=8), wl.cavity(n=8, nv=8), wl.box3d(ni=4, nj=3, nk=3, nv=8),
+              wl.as_rykov(wl.cavity(n=6, nv=8))):
+        assert code(p) == gsis.GSIS_OK, p.name
+
+
+def test_curved_mesh_is_unsupported():
+    p = wl.cavity(n=8, nv=8)
+    nodes = p.nodes.copy()
+    nodes[..., 0] += 0.01 * nodes[..., 1]  # x depends on J: not rectilinear
+    assert code(dataclasses.replace(p, nodes=nodes)) == gsis.GSIS_E_UNSUPPORTED
+
+
+def test_non_increasing_nodes_are_rejected():
+    p = wl.cavity(n=8, nv=8)
+    nodes = p.nodes.copy()
+    nodes[..., 3, 0] = nodes[..., 2, 0]  # a zero-width cell along x
+    assert code(dataclasses.replace(p, nodes=nodes)) == GSIS_E_INVALID
+
+
+def test_boundary_conditions_must_match_the_axis():
+    p = wl.cavity(n=8, nv=8)
+    bc = list(p.bc)
+    bc[0] = wl.PERIODIC  # periodic axes with several cells are not implemented
+    assert code(dataclasses.replace(p, bc=bc)) == gsis.GSIS_E_UNSUPPORTED
+    bc = list(p.bc)
+    bc[4] = wl.WALL  # an axis with one cell must be PERIODIC on both sides
+    assert code(dataclasses.replace(p, bc=bc)) == GSIS_E_INVALID
+
+
+def test_inactive_axis_before_an_active_one_is_unsupported():
+    dx = 1.0 / 8
+    nodes = wl.box_nodes(np.linspace(0, 1, 9), [0.0, dx], np.linspace(0, 1, 9))
+    p = wl.cavity(n=8, nv=8)
+    q = dataclasses.replace(p, nj=1, nk=8, nodes=nodes,
+                            bc=[wl.WALL, wl.WALL, wl.PERIODIC, wl.PERIODIC, wl.WALL, wl.WALL],
+                            W0=np.tile(p.W0[:1], (64, 1)))
+    assert code(q) == gsis.GSIS_E_UNSUPPORTED
+
+
+def test_bad_velocity_grid_and_gas_are_rejected():
+    p = wl.cavity(n=6, nv=8)
+    assert code(dataclasses.replace(p, vx=p.vx[:0], wx=p.wx[:0])) == GSIS_E_INVALID
+    r = wl.as_rykov(p)
+    assert code(dataclasses.replace(r, d_r=0.0)) == GSIS_E_INVALID
+    assert code(dataclasses.replace(r, Z_r=-1.0)) == GSIS_E_INVALID
+
+
+def test_bad_shard_options_are_rejected():
+    p = wl.cavity(n=6, nv=8)
+    assert code(p, shard=(2, 2)) == GSIS_E_INVALID   # index outside [0, count)
+    assert code(p, shard=(0, 10 ** 6)) == GSIS_E_INVALID  # more shards than velocity blocks
