@@ -23,7 +23,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CFG = dict(n=128, nv=32, vmax=5.0, Kn=0.1, lid=0.16)
+CFG = dict(n=128, nv=32, vmax=5.0, Kn=0.1, lid=0.16, model="shakhov")
 CFG_DEFAULT_KN = CFG["Kn"]
 METRIC = "phase-space updates/s (GSIS outer step, 2D cavity)"
 UNIT = "updates/s"
@@ -43,12 +43,15 @@ DRAM_BYTES_PER_LAUNCH = {"kinetic_kernel": 2186.25e6 + 2092.57e6, "macro_kernel"
 
 
 def workload_name(c=CFG):
-    return f"2D lid-driven cavity {c['n']}x{c['n']} cells, {c['nv']}^3 velocities on [-{c['vmax']},{c['vmax']}]^3, Kn={c['Kn']}, lid {c['lid']}"
+    gas = "" if c["model"] == "shakhov" else ", Rykov N2-like gas (two reduced VDFs)"
+    return (f"2D lid-driven cavity {c['n']}x{c['n']} cells, {c['nv']}^3 velocities on [-{c['vmax']},{c['vmax']}]^3, "
+            f"Kn={c['Kn']}, lid {c['lid']}{gas}")
 
 
 def problem(c=CFG):
     from paper_2310_18916_gb300 import workloads as wl
-    return wl.cavity(n=c["n"], nv=c["nv"], vmax=c["vmax"], Kn=c["Kn"], lid=c["lid"])
+    p = wl.cavity(n=c["n"], nv=c["nv"], vmax=c["vmax"], Kn=c["Kn"], lid=c["lid"])
+    return wl.as_rykov(p) if c["model"] == "rykov" else p
 
 
 class ClockSampler:
@@ -125,6 +128,8 @@ def oracle_sample(c=CFG, nv_sample=16, macro_sample=100):
     from paper_2310_18916_gb300 import workloads as wl
 
     p = wl.cavity(n=c["n"], nv=nv_sample, vmax=c["vmax"], Kn=c["Kn"], lid=c["lid"])
+    if c["model"] == "rykov":
+        p = wl.as_rykov(p)
     o = Oracle(p, mode=0, macro_steps=macro_sample, macro_tol=0.0)
     t0 = time.perf_counter()
     o.wall_prepass()
@@ -132,11 +137,11 @@ def oracle_sample(c=CFG, nv_sample=16, macro_sample=100):
     t1 = time.perf_counter()
     o.macro_from_current()
     t2 = time.perf_counter()
-    full_pts = c["n"] ** 2 * c["nv"] ** 3
+    full_pts = c["n"] ** 2 * c["nv"] ** 3 * (2 if c["model"] == "rykov" else 1)
     kin_scale = c["nv"] ** 3 / o.nv
     est = (t1 - t0) * kin_scale + (t2 - t1) * (300.0 / macro_sample)
     desc = (f"oracle kinetic step on the {c['n']}^2 mesh with {nv_sample}^3 velocities ({t1 - t0:.2f} s, scaled x"
-            f"{kin_scale:.0f} to 32^3) + moments and {macro_sample} of 300 synthetic inner steps ({t2 - t1:.2f} s, "
+            f"{kin_scale:.0f} to {c['nv']}^3) + moments and {macro_sample} of 300 synthetic inner steps ({t2 - t1:.2f} s, "
             f"scaled x{300.0 / macro_sample:.0f}); {full_pts} points per full step")
     return est, desc, (t2 - t0)
 
@@ -331,6 +336,8 @@ def main():
     ap.add_argument("--n", type=int, default=CFG["n"], help="cells per side (profiling cases use 64)")
     ap.add_argument("--nv", type=int, default=CFG["nv"], help="velocities per axis")
     ap.add_argument("--kn", type=float, default=CFG["Kn"])
+    ap.add_argument("--model", default="shakhov", choices=["shakhov", "rykov"],
+                    help="gas model (rykov: two reduced VDFs; a phase-space update counts each VDF's point)")
     ap.add_argument("--time-to-steady", action="store_true",
                     help="instead of the throughput line: wall time to eps < --tts-tol for FP64, FP32, BF16")
     ap.add_argument("--tts-tol", type=float, default=1e-6)
@@ -345,7 +352,7 @@ def main():
     ap.add_argument("--serve-gap", type=float, default=0.25, help="mean arrival gap, seconds")
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
-    CFG.update(n=args.n, nv=args.nv, Kn=args.kn)
+    CFG.update(n=args.n, nv=args.nv, Kn=args.kn, model=args.model)
     if args.impl == "reference":
         return run_reference(args)
     if args.time_to_steady:
@@ -375,7 +382,8 @@ def main():
         torch.cuda.synchronize()
 
     p = problem()
-    pts = p.ncells * p.nvel
+    nvdf = 2 if args.model == "rykov" else 1
+    pts = p.ncells * p.nvel * nvdf
     sharded = args.shard and world > 1
     shard_kw = {}
     if sharded:
@@ -435,8 +443,9 @@ def main():
     macro_ms = phase[3] / max(nsteps, 1)
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     fp64_peak = nsm * FP64_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    macro_flops = MACRO_FLOPS_PER_CELL_STEP_2D * p.ncells * macro_iters
-    macro_tflops = macro_flops / (macro_ms / 1e3) / 1e12
+    # (the flop tally is the five-field Shakhov solve's; the Rykov solve has no tally: no frac)
+    macro_flops = MACRO_FLOPS_PER_CELL_STEP_2D * p.ncells * macro_iters if nvdf == 1 else None
+    macro_tflops = macro_flops / (macro_ms / 1e3) / 1e12 if macro_flops else None
     vdf_gb = p.ncells * p.nvel * sbytes / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -454,14 +463,14 @@ def main():
         # the dominant kernel: the FP64 synthetic solve (one persistent launch per step)
         "roofline": {"kernel": "macro_kernel", "bound": "alu", "achieved": macro_tflops, "peak": fp64_peak,
                      "peak_kind": "derived FP64 peak: SMs x 2 FP64 FMA lanes x 2 flops x max SM clock",
-                     "unit": "TFLOP/s", "frac": macro_tflops / fp64_peak,
-                     "traffic": DRAM_BYTES_PER_LAUNCH["macro_kernel"] if args.n == 128 else None,
+                     "unit": "TFLOP/s", "frac": macro_tflops / fp64_peak if macro_tflops else None,
+                     "traffic": DRAM_BYTES_PER_LAUNCH["macro_kernel"] if args.n == 128 and nvdf == 1 else None,
                      "algorithmic_flops_per_launch": macro_flops, "flops_per_cell_inner_step": MACRO_FLOPS_PER_CELL_STEP_2D,
                      "launch_ms": macro_ms, "share_of_step": macro_ms / ms},
         "roofline_kinetic": {"kernel": "kinetic_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                              "traffic": DRAM_BYTES_PER_LAUNCH["kinetic_kernel"]
-                             if args.n == 128 and args.precision == "f32" else None,
+                             if args.n == 128 and args.precision == "f32" and nvdf == 1 else None,
                              "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": kin_ms, "share_of_step": kin_ms / ms},
         "e2e": {"value": (1 if sharded else world) * args.steps * pts / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps,
