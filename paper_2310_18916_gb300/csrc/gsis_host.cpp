@@ -102,7 +102,9 @@ struct gsis_solver {
   bool pending = false;
   int pending_mode = 0, pending_launches = 0;
   int kin_warps = 1;
-  size_t kin_smem = 0;
+  size_t kin_smem = 0;     // dynamic shared memory of the kinetic kernel (0 with a global ring)
+  size_t kin_gstride = 0;  // bytes of global ring scratch per velocity block (0: shared memory)
+  void *d_kscratch = nullptr;
   // profiling
   bool profiling = false;
   cudaEvent_t ev[6] = {};
@@ -190,6 +192,8 @@ struct gsis_solver {
     a.nwall = nwall;
     a.nblocks = nblocks;
     a.err = d_err;
+    a.gscratch = static_cast<unsigned char *>(d_kscratch);
+    a.gstride = kin_gstride;
     return a;
   }
 
@@ -472,6 +476,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     return GSIS_E_INVALID;
   }
   if (o->mode != GSIS_MODE_GSIS && o->mode != GSIS_MODE_DVM) { why = "bad mode"; return GSIS_E_INVALID; }
+  if (o->kinetic_ring != 0 && o->kinetic_ring != 1) { why = "kinetic_ring must be 0 or 1"; return GSIS_E_INVALID; }
   if (o->shard_count > 1 && (o->shard_index < 0 || o->shard_index >= o->shard_count || !o->allreduce)) {
     why = "velocity sharding needs 0 <= shard_index < shard_count and an allreduce callback";
     return GSIS_E_INVALID;
@@ -724,6 +729,40 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
   return GSIS_OK;
 }
 
+// Kinetic launch shape and ring placement.  One warp per cell of a colour, up to 16 warps (8 in
+// FP64), within the register file.  The ring stays in shared memory unless the largest colour
+// does not fit there, or the global-scratch kernel keeps at least twice as many blocks resident
+// per SM (3D meshes: a colour ring of ~100 KB or more leaves room for one block per SM, and the
+// scratch stays in L2).  Without a device (footprint queries on a host with no GPU) the
+// placement follows the shared-memory limit of the sm_100 family, 227 KB.
+template <typename T, typename S>
+static int plan_kinetic(gsis_solver *s) {
+  const size_t smem = kinetic_smem_bytes<T, S>(s->kg, s->nvdf);
+  const size_t gstride = kinetic_gscratch_stride<T, S>(s->kg, s->nvdf);
+  int want = std::max(1, std::min(16, s->kg.maxcol / 4));
+  if (sizeof(T) == 8) want = std::min(want, 8);
+  int dev = 0, optin = 0;
+  const bool have_dev = cudaGetDevice(&dev) == cudaSuccess &&
+                        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess;
+  if (!have_dev) {
+    cudaGetLastError();
+    optin = 227 * 1024;
+  }
+  bool gm = s->opt.kinetic_ring == 1 || smem > (size_t)optin;
+  int warps_sh = want, warps_gm = want;
+  if (have_dev) {
+    int occ_sh = 0, occ_gm = 0;
+    int rc = s->cuda(kinetic_shape<T, S>(s->kg, s->nvdf, true, want, 0, &warps_gm, &occ_gm), "kinetic shape");
+    if (!rc && !gm) rc = s->cuda(kinetic_shape<T, S>(s->kg, s->nvdf, false, want, smem, &warps_sh, &occ_sh), "kinetic shape");
+    if (rc) return rc;
+    if (!gm && occ_gm >= 2 * occ_sh) gm = true;
+  }
+  s->kin_smem = gm ? 0 : smem;
+  s->kin_gstride = gm ? gstride : 0;
+  s->kin_warps = gm ? warps_gm : warps_sh;
+  return GSIS_OK;
+}
+
 static size_t footprint(const gsis_solver *s) {
   const size_t T = s->prec == GSIS_F64 ? 8 : 4;                             // kinetic arithmetic
   const size_t Sb = s->prec == GSIS_F64 ? 8 : (s->prec == GSIS_BF16 ? 2 : 4);  // VDF storage
@@ -731,6 +770,7 @@ static size_t footprint(const gsis_solver *s) {
   size_t b = 0;
   b += (size_t)s->nvdf * s->nslots * nc * Sb;  // f (f0, f1)
   b += (size_t)s->nblocks * (s->nwall + 1) * NWF * T;  // wall partials
+  b += (size_t)s->nblocks * s->kin_gstride;           // kinetic ring in global memory
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
@@ -754,6 +794,7 @@ static int allocate_and_upload(gsis_solver *s) {
   }
   A(s->d_mp, (size_t)s->mom_nchunks * nc * moment_len(s->nvdf) * sizeof(double));
   A(s->d_wpart, (size_t)s->nblocks * (s->nwall + 1) * NWF * sizeof(T));
+  if (s->kin_gstride) A(s->d_kscratch, (size_t)s->nblocks * s->kin_gstride);
   A(s->d_K, nc * 6 * sizeof(double));
   A(s->d_stT, nc * NST * sizeof(T));
   A(s->d_st64, nc * NST * sizeof(double));
@@ -845,19 +886,6 @@ static int allocate_and_upload(gsis_solver *s) {
                                        s->nvdf == 2 ? s->gas.d_r : 0.0, s->stream),
                  "wall constants");
   if (rc) return rc;
-  // kinetic launch shape: one warp per cell of a colour, up to 16 warps, within the register file
-  s->kin_smem = kinetic_smem_bytes<T, S>(s->kg, s->nvdf);
-  int dev = 0, smem_optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (s->kin_smem > (size_t)smem_optin)
-    return s->fail(GSIS_E_UNSUPPORTED, "largest colour needs %zu bytes of shared memory (limit %d)", s->kin_smem, smem_optin);
-  s->kin_warps = std::max(1, std::min(16, s->kg.maxcol / 4));
-  if (sizeof(T) == 8) s->kin_warps = std::min(s->kin_warps, 8);
-  int max_warps = 0;
-  rc = s->cuda(kinetic_max_warps<T, S>(s->kg, s->nvdf, &max_warps), "kinetic shape");
-  if (rc) return rc;
-  s->kin_warps = std::max(1, std::min(s->kin_warps, max_warps));
   return GSIS_OK;
 }
 
@@ -874,6 +902,7 @@ extern "C" int gsis_footprint_bytes(const gsis_mesh *mesh, const gsis_vgrid *vgr
   tmp.prec = o.precision;
   tmp.nvdf = gas->model == GSIS_RYKOV ? 2 : 1;
   rc = setup(&tmp, mesh, vgrid);
+  if (!rc) rc = GSIS_DISPATCH(tmp.prec, (plan_kinetic<T, S>(&tmp)));
   if (rc) return rc;
   *bytes = footprint(&tmp);
   return GSIS_OK;
@@ -926,6 +955,7 @@ extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const
   s->gas = *gas;
   s->stream = (cudaStream_t)o.stream;
   rc = setup(s, mesh, vgrid);
+  if (!rc) rc = GSIS_DISPATCH(s->prec, (plan_kinetic<T, S>(s)));
   if (!rc) rc = GSIS_DISPATCH(s->prec, (allocate_and_upload<T, S>(s)));
   if (!rc) rc = init_state(s);
   for (int t = 0; !rc && t < o.kinetic_presteps; ++t) rc = s->step(GSIS_MODE_DVM);

@@ -95,6 +95,8 @@ struct KinArgs {
   int nwall;
   int nblocks;
   int *err;              // device error flag (a bounded wait that timed out)
+  unsigned char *gscratch;  // ring and face buffers in global memory (nullptr: shared memory)
+  size_t gstride;           // bytes of gscratch per velocity block
 };
 
 // ---- launchers (defined in the .cu files) ----
@@ -102,6 +104,9 @@ template <typename T, typename S>
 cudaError_t launch_kinetic(const KinArgs<T, S> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s);
 template <typename T, typename S>
 size_t kinetic_smem_bytes(const KinGeom &g, int nvdf);
+// bytes of global scratch per velocity block when the ring and face buffers live there
+template <typename T, typename S>
+size_t kinetic_gscratch_stride(const KinGeom &g, int nvdf);
 template <typename T, typename S>
 cudaError_t launch_wall_prepass(const KinArgs<T, S> &a, const int *wall_cell, const int *wall_side, int nwall,
                                 const double *Z0, double *rho_w, int nslots, cudaStream_t s);
@@ -115,9 +120,11 @@ cudaError_t launch_export_f(const KinArgs<T, S> &a, int q, const int *slot_canon
 template <typename T, typename S>
 cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon, int nslots, int nv, const double *in,
                             cudaStream_t s);
-// largest block (in warps) the kinetic kernel of this shape launches with (its registers)
+// launch shape of the kinetic kernel (gm: ring in global scratch): warps = want_warps capped by
+// the kernel's registers, and the blocks of that size and dynamic shared memory an SM holds
 template <typename T, typename S>
-cudaError_t kinetic_max_warps(const KinGeom &g, int nvdf, int *warps);
+cudaError_t kinetic_shape(const KinGeom &g, int nvdf, bool gm, int want_warps, size_t smem, int *warps,
+                          int *ctas_per_sm);
 
 cudaError_t launch_wall_constants(const double *vel64, int nslots, const double *wall_uT, const int *sides,
                                   int nsides, double *Z0, double *Zw, double d_r, cudaStream_t s);

@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <type_traits>
@@ -303,12 +304,17 @@ struct KinSmem {
   }
 };
 
-template <typename T, typename S, int NACT, int NV>
+// GM: the colour ring and face buffers of a velocity block too large for shared memory (3D
+// meshes: a colour of n^3 cells has O(n^2) cells) live in the block's own slice of a global
+// scratch (L2-resident where it fits), and each colour is staged with plain loads.  The
+// arithmetic and the order of every cell's inputs are those of the shared-memory kernel.
+template <typename T, typename S, int NACT, int NV, bool GM>
 __global__ void kinetic_kernel(const KinArgs<T, S> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
   const KinGeom &G = A.g;
   constexpr int SL = stage_state_len<S, NV>();
   const KinSmem<T, S> L(G, NV, SL);
+  unsigned char *smem_raw = GM ? A.gscratch + (size_t)blockIdx.x * A.gstride : smem_dyn;
   T *ring = reinterpret_cast<T *>(smem_raw + L.ring);
   T *ebuf[3];
   {
@@ -387,20 +393,29 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
     return true;
   };
   auto stage = [&](int c) {
-    const int cnt = A.col_off[c + 1] - A.col_off[c];
+    const int off = A.col_off[c], cnt = A.col_off[c + 1] - off;
     T *slot = ring + (size_t)(c % 3) * slot_stride;
     for (int p = warp; p < cnt; p += nw) {
-      T st[SL];
-      load_state_shared<T>(rawst + (size_t)p * SL, st, SL);
-      T stored[NV], f[NV];
+      T st[SL], stored[NV], f[NV];
+      if constexpr (GM) {
+        const int cell = __ldg(&natcell[off + p].x);
+        load_state<SL>(state_of(A.st, cell), st);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(rawf + (size_t)(p * NV + q) * VB + lane);
+        for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(F[q] + (size_t)cell * VB + lane);
+      } else {
+        load_state_shared<T>(rawst + (size_t)p * SL, st, SL);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(rawf + (size_t)(p * NV + q) * VB + lane);
+      }
       corrected_all<T, S, NV>(stored, st, xi[0], xi[1], xi[2], f);
 #pragma unroll
       for (int q = 0; q < NV; ++q) slot[(p * NV + q) * VB + lane] = f[q];
     }
   };
 
+  if constexpr (GM) {
+    stage(0);
+  } else {
   if (tid == 0) {
     mbar_init(bar);
     mbar_expect(bar, colour_bytes(0));
@@ -413,7 +428,13 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   if (tid == 0 && G.ncol > 1) mbar_expect(bar, colour_bytes(1));
   __syncthreads();
   if (G.ncol > 1) issue(1, pf);
+  }
+  int pf = 0;
   for (int c = 0; c < G.ncol; ++c) {
+    if constexpr (GM) {
+      if (c + 1 < G.ncol) stage(c + 1);
+      __syncthreads();
+    } else {
     pf = prefetch_cell(c + 2);
     if (c + 1 < G.ncol) {
       if (!await()) return;
@@ -422,6 +443,7 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
     }
     __syncthreads();
     if (c + 2 < G.ncol) issue(c + 2, pf);
+    }
     const T *slotm = ring + (size_t)((c + 2) % 3) * slot_stride;
     const T *slot0 = ring + (size_t)(c % 3) * slot_stride;
     const T *slotp = ring + (size_t)((c + 1) % 3) * slot_stride;
@@ -551,24 +573,44 @@ size_t kinetic_smem_bytes(const KinGeom &g, int nvdf) {
   return KinSmem<T, S>(g, nvdf, sl).total;
 }
 
+// the ring and face buffers only (the bulk-copy staging area is not used from global memory),
+// rounded to 256 bytes so that every block's slice starts on an aligned boundary
 template <typename T, typename S>
-static void (*kinetic_fn(int nact, int nvdf))(const KinArgs<T, S>) {
+size_t kinetic_gscratch_stride(const KinGeom &g, int nvdf) {
+  const int sl = nvdf == 2 ? stage_state_len<S, 2>() : stage_state_len<S, 1>();
+  return (KinSmem<T, S>(g, nvdf, sl).rawf + 255) & ~(size_t)255;
+}
+
+template <typename T, typename S, bool GM>
+static void (*kinetic_fn_gm(int nact, int nvdf))(const KinArgs<T, S>) {
   if (nvdf == 2)
-    return nact == 1 ? kinetic_kernel<T, S, 1, 2> : (nact == 2 ? kinetic_kernel<T, S, 2, 2> : kinetic_kernel<T, S, 3, 2>);
-  return nact == 1 ? kinetic_kernel<T, S, 1, 1> : (nact == 2 ? kinetic_kernel<T, S, 2, 1> : kinetic_kernel<T, S, 3, 1>);
+    return nact == 1 ? kinetic_kernel<T, S, 1, 2, GM>
+                     : (nact == 2 ? kinetic_kernel<T, S, 2, 2, GM> : kinetic_kernel<T, S, 3, 2, GM>);
+  return nact == 1 ? kinetic_kernel<T, S, 1, 1, GM>
+                   : (nact == 2 ? kinetic_kernel<T, S, 2, 1, GM> : kinetic_kernel<T, S, 3, 1, GM>);
 }
 
 template <typename T, typename S>
-cudaError_t kinetic_max_warps(const KinGeom &g, int nvdf, int *warps) {
+static void (*kinetic_fn(int nact, int nvdf, bool gm))(const KinArgs<T, S>) {
+  return gm ? kinetic_fn_gm<T, S, true>(nact, nvdf) : kinetic_fn_gm<T, S, false>(nact, nvdf);
+}
+
+template <typename T, typename S>
+cudaError_t kinetic_shape(const KinGeom &g, int nvdf, bool gm, int want_warps, size_t smem, int *warps,
+                          int *ctas_per_sm) {
+  void (*k)(const KinArgs<T, S>) = kinetic_fn<T, S>(g.nact, nvdf, gm);
   cudaFuncAttributes attr;
-  cudaError_t e = cudaFuncGetAttributes(&attr, kinetic_fn<T, S>(g.nact, nvdf));
-  if (e == cudaSuccess) *warps = attr.maxThreadsPerBlock / 32;
-  return e;
+  cudaError_t e = cudaFuncGetAttributes(&attr, k);
+  if (e != cudaSuccess) return e;
+  *warps = std::max(1, std::min(want_warps, attr.maxThreadsPerBlock / 32));
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, *warps * 32, smem);
 }
 
 template <typename T, typename S>
 cudaError_t launch_kinetic(const KinArgs<T, S> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s) {
-  void (*k)(const KinArgs<T, S>) = kinetic_fn<T, S>(a.g.nact, a.nvdf);
+  void (*k)(const KinArgs<T, S>) = kinetic_fn<T, S>(a.g.nact, a.nvdf, a.gscratch != nullptr);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<nblocks, nwarps * 32, smem, s>>>(a);
@@ -951,7 +993,7 @@ cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon
 
 #define GSIS_INST(T, S)                                                                                         \
   template cudaError_t launch_kinetic<T, S>(const KinArgs<T, S> &, int, int, size_t, cudaStream_t);             \
-  template cudaError_t kinetic_max_warps<T, S>(const KinGeom &, int, int *);                                     \
+  template cudaError_t kinetic_shape<T, S>(const KinGeom &, int, bool, int, size_t, int *, int *);                                       \
   template cudaError_t launch_wall_prepass<T, S>(const KinArgs<T, S> &, const int *, const int *, int,           \
                                                  const double *, double *, int, cudaStream_t);                   \
   template cudaError_t launch_moments<T, S>(const KinArgs<T, S> &, int, int, double *, cudaStream_t);           \
@@ -966,5 +1008,8 @@ GSIS_INST(float, __nv_bfloat16)
 template size_t kinetic_smem_bytes<float, float>(const KinGeom &, int);
 template size_t kinetic_smem_bytes<double, double>(const KinGeom &, int);
 template size_t kinetic_smem_bytes<float, __nv_bfloat16>(const KinGeom &, int);
+template size_t kinetic_gscratch_stride<float, float>(const KinGeom &, int);
+template size_t kinetic_gscratch_stride<double, double>(const KinGeom &, int);
+template size_t kinetic_gscratch_stride<float, __nv_bfloat16>(const KinGeom &, int);
 
 }  // namespace gsis

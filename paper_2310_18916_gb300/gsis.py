@@ -48,7 +48,8 @@ class Options(C.Structure):
                 ("kin_inv_dt", C.c_double), ("venkat_K", C.c_double), ("kinetic_presteps", C.c_int),
                 ("init_W", D), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("macro_sms", C.c_int), ("shard_count", C.c_int),
-                ("shard_index", C.c_int), ("allreduce", ALLREDUCE_FN), ("allreduce_ctx", C.c_void_p)]
+                ("shard_index", C.c_int), ("allreduce", ALLREDUCE_FN), ("allreduce_ctx", C.c_void_p),
+                ("kinetic_ring", C.c_int)]
 
 
 _lib = None
@@ -328,14 +329,19 @@ def selftest_wait_timeout(which):
     return st.value
 
 
-def footprint_bytes(problem, precision="f32", shard=None):
-    """Device bytes a solver of this problem holds (shard: (index, count) of a sharded solve)."""
+def footprint_bytes(problem, precision="f32", shard=None, **opts):
+    """Device bytes a solver of this problem holds (shard: (index, count) of a sharded solve;
+    other keyword arguments map onto gsis_options)."""
     L = load()
     keep = []
     m, vg, g = build_structs(problem, keep)
     o = Options()
     L.gsis_default_options(C.byref(o))
     o.precision = PRECISIONS[precision]
+    for k, v in opts.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
     if shard is not None:
         o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
         o.allreduce = _NO_EXCHANGE

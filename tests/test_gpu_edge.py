@@ -1,6 +1,7 @@
 """Edge cases of the GPU path against the FP64 oracle: a 3D box (three active axes), odd
 velocity counts (a xi = 0 node on every axis, ragged octants padded with weight-0 slots),
-rectangular grids, the rest state, colours too large for shared memory, and one kinetic step of
+rectangular grids, the rest state, colour rings in device scratch (bit-identical to shared memory;
+3D boxes too large for it against the oracle), and one kinetic step of
 the full benchmark workload (128^2 cells x 32^3 velocities) compared cell by cell."""
 import os
 
@@ -74,13 +75,39 @@ def test_rest_state_stays_at_rest():
     # threshold, and its relative change is of order one)
 
 
-def test_colours_beyond_shared_memory_are_rejected():
-    """A 1023 x 1023 grid has 1023 cells in its largest colour: its ring does not fit in shared
-    memory, and creation fails with GSIS_E_UNSUPPORTED (no kernel runs)."""
-    p = wl.cavity(n=1023, nv=4, Kn=0.1)
-    with pytest.raises(gsis.GsisError) as e:
-        gsis.Solver(p, precision="f64", mode="gsis", kinetic_presteps=0)
-    assert e.value.code == gsis.GSIS_E_UNSUPPORTED
+@pytest.mark.parametrize("precision,rykov", [("f32", False), ("bf16", False), ("f64", True)])
+def test_global_ring_is_bit_identical(precision, rykov):
+    """kinetic_ring = 1 keeps the sweep's colour ring and wall face values in device scratch
+    instead of shared memory. The arithmetic and its order are the same, so the VDF after GSIS
+    steps is bit-identical to the shared-memory kernel's."""
+    p = wl.box3d(ni=6, nj=5, nk=4, nv=10, Kn=0.2, wall_speed=0.25)
+    if rykov:
+        p = wl.as_rykov(p)
+    W = wl.perturbed_state(p, seed=31, amp=0.04)
+    runs = []
+    for ring in (0, 1):
+        g = gsis.Solver(p, precision=precision, mode="gsis", init_W=W, kinetic_presteps=2, macro_steps=40,
+                        kinetic_ring=ring)
+        for _ in range(2):
+            g.step()
+        runs.append((g.get_f(), g.W()))
+        g.close()
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+@pytest.mark.parametrize("precision,n,rel", [("f64", 16, 1e-10), ("f32", 18, 2e-5)])
+def test_box3d_beyond_shared_memory(precision, n, rel):
+    """A 3D box whose largest colour does not fit in shared memory (16^3 cells in FP64, 18^3 in
+    FP32): the ring moves to device scratch by itself, and GSIS steps match the oracle."""
+    p = wl.box3d(ni=n, nj=n, nk=n, nv=8, Kn=0.2, wall_speed=0.25)
+    assert gsis.footprint_bytes(p, precision) == gsis.footprint_bytes(p, precision, kinetic_ring=1)
+    W = wl.perturbed_state(p, seed=33, amp=0.04)
+    g, o = pair(p, precision, "gsis", W0=W, macro_steps=60)
+    for it in range(2):
+        g.step()
+        o.step()
+        scaled_close(g.W(), o.W(), rel, f"{n}^3 box W, step {it}")
 
 
 def test_benchmark_workload_one_kinetic_step_cell_by_cell():

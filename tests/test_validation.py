@@ -72,3 +72,14 @@ def test_bad_shard_options_are_rejected():
     p = wl.cavity(n=6, nv=8)
     assert code(p, shard=(2, 2)) == GSIS_E_INVALID   # index outside [0, count)
     assert code(p, shard=(0, 10 ** 6)) == GSIS_E_INVALID  # more shards than velocity blocks
+
+
+def test_kinetic_ring_placement():
+    """The kinetic sweep's colour ring moves to a device scratch (counted in the footprint) only
+    when the largest colour does not fit in shared memory, or when asked to."""
+    small = wl.box3d(ni=8, nj=8, nk=8, nv=8)
+    f_auto, f_global = gsis.footprint_bytes(small), gsis.footprint_bytes(small, kinetic_ring=1)
+    assert f_global > f_auto
+    for p, prec in ((wl.box3d(ni=20, nj=20, nk=20, nv=8), "f32"), (wl.box3d(ni=16, nj=16, nk=16, nv=8), "f64")):
+        assert gsis.footprint_bytes(p, prec) == gsis.footprint_bytes(p, prec, kinetic_ring=1), p.name
+    assert code(small, kinetic_ring=2) == GSIS_E_INVALID
