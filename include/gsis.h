@@ -132,11 +132,12 @@ typedef struct {
   void *allreduce_ctx;
   int kinetic_ring;     /* where the kinetic sweep keeps the three colours it works on and the
                            face values along walls, per block of 32 velocities (Section 4's
-                           colour-ordered sweep): 0 (default) in shared memory when the largest
-                           colour fits there, else in a device scratch of the solver's own
-                           (3D meshes beyond about 16^3 cells in FP32 and BF16, 11^3 in FP64;
-                           counted by gsis_footprint_bytes); 1 always in the device scratch.
-                           Results are bit-identical either way. */
+                           colour-ordered sweep).  0 (default): in shared memory, unless the
+                           largest colour does not fit there (3D meshes from about 18^3 cells in
+                           FP32 and BF16, 12^3 in FP64) or the other placement keeps at least
+                           twice as many blocks resident per SM; else in a device scratch of the
+                           solver's own, counted by gsis_footprint_bytes.  1: always in the
+                           device scratch.  Results are bit-identical either way. */
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;
