@@ -16,7 +16,8 @@
  *   geometry, LSQ gradient, Venkatakrishnan limiter, moments, reference
  *   distributions, tau, conductivities, collision conservation, uniform
  *   equilibrium, free-molecular Couette, wall mass balance, NSF limit,
- *   refinement, GSIS-vs-DVM fixed point: pinned.
+ *   refinement, GSIS-vs-DVM fixed point, O-grid geometry (wrapped azimuth, pole faces),
+ *   far field (uniform free stream, collisionless reservoir against a wall): pinned.
  *   Macro-solver details the paper leaves to its references (face gradient,
  *   Gamma, time step): pinned only through the fixed point (kinetic/GSIS agree).
  */
@@ -44,7 +45,9 @@ struct orc_solver {
   double *vx, *vy, *vz, *wx, *wy, *wz;
   /* geometry */
   double *vol, *xc, *S, *xf, *eps2;
-  int *nb;               /* per cell and side: >=0 neighbour, -1 wall, -2 absent (inactive axis) */
+  int *nb;               /* per cell and side: >=0 neighbour, -1 wall, -2 absent (inactive axis),
+                            -3 axis (zero area), -4 far field */
+  int open;              /* a far-field side exists: mass is not conserved by the domain */
   int *wid;              /* per cell and side: wall face id or -1 */
   int nwall;
   int *wcell, *wside;
@@ -157,12 +160,21 @@ static void quad(const double p[4][3], double S[3], double x[3]) {
 
 static int build_geometry(orc_solver *s, const orc_mesh *m) {
   int n[3] = {s->ni, s->nj, s->nk};
+  s->open = 0;
   for (int a = 0; a < 3; ++a) {
+    int lo = m->bc[2 * a], hi = m->bc[2 * a + 1];
     s->active[a] = n[a] > 1;
     if (!s->active[a]) {
-      if (m->bc[2 * a] != ORC_BC_PERIODIC || m->bc[2 * a + 1] != ORC_BC_PERIODIC) return ORC_E_INVALID;
-    } else {
-      if (m->bc[2 * a] != ORC_BC_WALL || m->bc[2 * a + 1] != ORC_BC_WALL) return ORC_E_INVALID;
+      if (lo != ORC_BC_PERIODIC || hi != ORC_BC_PERIODIC) return ORC_E_INVALID;
+    } else if ((lo == ORC_BC_PERIODIC) != (hi == ORC_BC_PERIODIC)) {
+      return ORC_E_INVALID;
+    } else if (lo == ORC_BC_PERIODIC && n[a] < 3) {
+      return ORC_E_INVALID;  /* a wrapped axis needs distinct neighbours on both sides */
+    }
+    for (int t = 0; t < 2; ++t) {
+      int b = m->bc[2 * a + t];
+      if (b < ORC_BC_WALL || b > ORC_BC_AXIS) return ORC_E_INVALID;
+      if (b == ORC_BC_FARFIELD) s->open = 1;
     }
   }
   s->nwall = 0;
@@ -208,6 +220,11 @@ static int build_geometry(orc_solver *s, const orc_mesh *m) {
           s->wid[6 * c + side] = -1;
           if (!s->active[a]) nbr = -2;
           else if (idx[a] >= 0 && idx[a] < n[a]) nbr = cid(s, idx[0], idx[1], idx[2]);
+          else if (m->bc[side] == ORC_BC_PERIODIC) {
+            idx[a] = (idx[a] + n[a]) % n[a];
+            nbr = cid(s, idx[0], idx[1], idx[2]);
+          } else if (m->bc[side] == ORC_BC_AXIS) nbr = -3;
+          else if (m->bc[side] == ORC_BC_FARFIELD) nbr = -4;
           else { nbr = -1; s->wid[6 * c + side] = s->nwall++; }
           s->nb[6 * c + side] = nbr;
         }
@@ -282,7 +299,7 @@ static double venkat_cell(const orc_solver *s, int i, const double *q, int strid
   }
   double phi = 1.0;
   for (int side = 0; side < 6; ++side) {
-    if (s->nb[6 * i + side] == -2) continue;
+    if (s->nb[6 * i + side] == -2 || s->nb[6 * i + side] == -3) continue;
     const double *xf = s->xf + 18 * i + 3 * side, *xc = s->xc + 3 * i;
     double r[3] = {xf[0] - xc[0], xf[1] - xc[1], xf[2] - xc[2]};
     double d2 = dot3(g, r);
@@ -342,6 +359,25 @@ typedef struct {
   double *fl;            /* this velocity's outward face fluxes [cell][side][6] */
 } kin_work;
 
+/* Face values (f, and f1 for Rykov) entering the domain through the boundary face (i, side)
+   for velocity xi: at a wall the re-emitted rho_w M_w (f1 = (d_r T_w / 4) f); at a far field
+   the free-stream Maxwellian where the free stream does not leave through the face
+   (U_inf . S <= 0), else the cell's own face values own[] (zero gradient). */
+static void boundary_in(const orc_solver *s, int i, int side, const double *xi, const double own[2], double e[2]) {
+  if (s->nb[6 * i + side] == -1) {
+    double M = s->rho_w[s->wid[6 * i + side]] * wall_maxwellian(s, side, xi);
+    e[0] = M;
+    e[1] = s->g.d_r * s->wall_T[side] / 4.0 * M;
+  } else if (dot3(s->wall_u[side], s->S + 18 * i + 3 * side) <= 0.0) {
+    double M = maxwellian(1.0, s->wall_u[side], s->wall_T[side], xi);
+    e[0] = M;
+    e[1] = s->g.d_r * s->wall_T[side] / 4.0 * M;
+  } else {
+    e[0] = own[0];
+    e[1] = own[1];
+  }
+}
+
 static int colour_of(const orc_solver *s, int c, const int sgn[3]) {
   int i = c % s->ni, j = (c / s->ni) % s->nj, k = c / (s->ni * s->nj);
   int a = sgn[0] >= 0 ? i : s->ni - 1 - i;
@@ -380,7 +416,7 @@ static void kinetic_velocity(orc_solver *s, int v, kin_work *wk) {
     double flux[2] = {0.0, 0.0};
     for (int side = 0; side < 6; ++side) {
       int j = s->nb[6 * i + side];
-      if (j == -2) continue;
+      if (j == -2 || j == -3) continue;
       double sn = dot3(xi, s->S + 18 * i + 3 * side);
       if (sn > 0) {
         D += sn / s->vol[i];
@@ -390,9 +426,10 @@ static void kinetic_velocity(orc_solver *s, int v, kin_work *wk) {
           int opp = side ^ 1;
           for (int q = 0; q < s->nvdf; ++q) flux[q] += sn * wk->ff[((size_t)q * nc + j) * 6 + opp];
         } else {
-          double M = s->rho_w[s->wid[6 * i + side]] * wall_maxwellian(s, side, xi);
-          flux[0] += sn * M;
-          if (s->nvdf == 2) flux[1] += sn * s->g.d_r * s->wall_T[side] / 4.0 * M;
+          double own[2] = {0.0, 0.0}, e[2];
+          for (int q = 0; q < s->nvdf; ++q) own[q] = wk->ff[((size_t)q * nc + i) * 6 + side];
+          boundary_in(s, i, side, xi, own, e);
+          for (int q = 0; q < s->nvdf; ++q) flux[q] += sn * e[q];
         }
       }
     }
@@ -425,7 +462,7 @@ static void kinetic_velocity(orc_solver *s, int v, kin_work *wk) {
         double *out = wk->fl + (size_t)36 * i + 6 * side;
         for (int k = 0; k < 6; ++k) out[k] = 0.0;
         int j = s->nb[6 * i + side];
-        if (j == -2) continue;
+        if (j == -2 || j == -3) continue;
         double sn = dot3(xi, s->S + 18 * i + 3 * side), e[2] = {0.0, 0.0};
         if (sn > 0) {
           for (int q = 0; q < s->nvdf; ++q)
@@ -435,9 +472,10 @@ static void kinetic_velocity(orc_solver *s, int v, kin_work *wk) {
             for (int q = 0; q < s->nvdf; ++q)
               e[q] = wk->ff[((size_t)q * nc + j) * 6 + (side ^ 1)] + wk->df[(size_t)q * nc + j];
           } else {
-            double M = s->rho_w[s->wid[6 * i + side]] * wall_maxwellian(s, side, xi);
-            e[0] = M;
-            if (s->nvdf == 2) e[1] = s->g.d_r * s->wall_T[side] / 4.0 * M;
+            double own[2] = {0.0, 0.0};
+            for (int q = 0; q < s->nvdf; ++q) own[q] = wk->ff[((size_t)q * nc + i) * 6 + side];
+            boundary_in(s, i, side, xi, own, e);
+            if (s->nvdf == 1) e[1] = 0.0;
           }
         }
         out[0] = w * sn * e[0];
@@ -691,6 +729,42 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
           }
           continue;
         }
+        if (j == -2 || j == -3) continue;
+        if (j == -4) {
+          /* far field: Rusanov flux between the cell's face state and the free stream (a
+             dissipative, well-posed weak imposition on inflow and outflow faces alike; at the
+             fixed point the high-order correction makes the face flux the kinetic one anyway),
+             the NSF part from the cell's own gradients, the correction as on interior faces */
+          double WL[6], WR[6], FL[6], FR[6], F[6], pL[6], pR[6];
+          const double *xci = s->xc + 3 * i;
+          double ri[3] = {xf[0] - xci[0], xf[1] - xci[1], xf[2] - xci[2]};
+          for (int k = 0; k < nW; ++k) WL[k] = W[6 * i + k] + m.phW[6 * i + k] * dot3(m.gW + 18 * i + 3 * k, ri);
+          prim_of(s, WL, pL);
+          if (!(pL[0] > 0) || !(pL[4] > 0) || !(pL[5] > 0)) { memcpy(WL, W + 6 * i, sizeof WL); prim_of(s, WL, pL); }
+          double pinf[6] = {1.0, s->wall_u[side][0], s->wall_u[side][1], s->wall_u[side][2], s->wall_T[side],
+                            s->wall_T[side]};
+          cons_of(s, pinf, WR);
+          prim_of(s, WR, pR);
+          euler_flux(s, WL, n, FL);
+          euler_flux(s, WR, n, FR);
+          double lL = fabs(dot3(pL + 1, n)) + sound(pL[4]), lR = fabs(dot3(pR + 1, n)) + sound(pR[4]);
+          double lam = lL > lR ? lL : lR;
+          for (int k = 0; k < nW; ++k) F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * lam * (WR[k] - WL[k]);
+          if (!euler) {
+            double nsf[12], sn[3];
+            face_nsf(s, &m, i, i, nsf);
+            const int map[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+            for (int a = 0; a < 3; ++a) sn[a] = nsf[map[a][0]] * n[0] + nsf[map[a][1]] * n[1] + nsf[map[a][2]] * n[2];
+            for (int a = 0; a < 3; ++a) F[1 + a] += sn[a];
+            F[4] += dot3(sn, m.pr + 6 * i + 1) + dot3(nsf + 6, n) + (nW == 6 ? dot3(nsf + 9, n) : 0.0);
+            if (nW == 6) F[5] += dot3(nsf + 9, n);
+          }
+          double *cr = corr + 36 * i + 6 * side;
+          if (step == 0)
+            for (int k = 0; k < nW; ++k) cr[k] = euler ? 0.0 : fkin[36 * i + 6 * side + k] - F[k] * A;
+          for (int k = 0; k < nW; ++k) m.R[6 * i + k] -= F[k] * A + cr[k];
+          continue;
+        }
         if (j < i) continue;  /* each interior face once, from its lower-index cell */
         double WL[6], WR[6], FL[6], FR[6], F[6];
         const double *xci = s->xc + 3 * i, *xcj = s->xc + 3 * j;
@@ -747,7 +821,7 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
       double lsum = 0.0, gsum = 0.0;
       for (int side = 0; side < 6; ++side) {
         int j = s->nb[6 * i + side];
-        if (j == -2) continue;
+        if (j == -2 || j == -3) continue;
         const double *S = s->S + 18 * i + 3 * side;
         double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
         double li = fabs(dot3(pr + 1, n)) + sound(pr[4]);
@@ -906,6 +980,10 @@ static double total_mass(const orc_solver *s) {
    so the wall only balances the mass flux once f stops changing; the step therefore
    rescales f^{n+1/2} to the domain's total mass (a factor that tends to 1). */
 static int conserve_mass(orc_solver *s) {
+  if (s->open) {  /* mass leaves and enters through the far field */
+    s->mass_scale = 1.0;
+    return ORC_OK;
+  }
   double fac = s->mass_ref / total_mass(s);
   s->mass_scale = fac;
   size_t n = (size_t)s->nc * s->nv;
@@ -935,13 +1013,14 @@ static int run_step(orc_solver *s, int mode) {
     for (int i = 0; i < nc; ++i) cons_of(s, s->Mh + 18 * i, Wc + 6 * i);
     rc = macro_solve(s, Wc, s->fkin, 0, s->o.macro_steps, s->o.macro_tol, &s->macro_iters);
     if (rc) { free(Wc); free(Wold); free(Wnew); return rc; }
-    /* Closed domain: the synthetic solve fixes the density only up to a constant and its
+    /* Closed domain (no far field): the synthetic solve fixes the density only up to a constant and its
        local-time-step iteration does not conserve mass, so its density is rescaled to the
        domain's total mass (velocity and temperatures unchanged). */
     double mk = s->mass_ref, mm = 0.0;
     for (int i = 0; i < nc; ++i) mm += Wc[6 * i] * s->vol[i];
     for (int i = 0; i < nc; ++i) prim_of(s, Wc + 6 * i, Wnew + 6 * i);
-    for (int i = 0; i < nc; ++i) Wnew[6 * i] *= mk / mm;
+    if (!s->open)
+      for (int i = 0; i < nc; ++i) Wnew[6 * i] *= mk / mm;
     free(Wc);
     /* Eq. updatef: keep the non-equilibrium part, replace the equilibrium */
 #pragma omp parallel for num_threads(s->o.nthreads > 0 ? s->o.nthreads : 1)

@@ -16,7 +16,12 @@
 extern "C" {
 #endif
 
-enum { ORC_BC_WALL = 1, ORC_BC_PERIODIC = 2 };
+/* Side conditions.  WALL: diffuse isothermal wall (wall_u, wall_T).  PERIODIC: both sides of
+   an axis; with several cells the axis wraps onto itself (a closed mesh such as the azimuth of
+   an O-grid, whose geometry already joins the two ends).  FARFIELD: free stream rho = 1,
+   u = wall_u, T_t = T_r = wall_T.  AXIS: a degenerate side of zero area (the pole of a
+   spherical grid): no flux, no neighbour. */
+enum { ORC_BC_WALL = 1, ORC_BC_PERIODIC = 2, ORC_BC_FARFIELD = 3, ORC_BC_AXIS = 4 };
 enum { ORC_SHAKHOV = 0, ORC_RYKOV = 1 };
 enum { ORC_GSIS = 0, ORC_DVM = 1 };
 enum { ORC_SCHED_COLOUR = 0, ORC_SCHED_LEXSGS = 1 };
@@ -25,7 +30,7 @@ enum { ORC_OK = 0, ORC_E_INVALID = -1, ORC_E_OOM = -2, ORC_E_DIVERGED = -4 };
 typedef struct {
   int ni, nj, nk;
   const double *nodes;  /* (ni+1)(nj+1)(nk+1) x 3, node (I,J,K) at I + (ni+1)(J + (nj+1)K) */
-  int bc[6];            /* sides x-, x+, y-, y+, z-, z+ */
+  int bc[6];            /* sides x-, x+, y-, y+, z-, z+ (index space: i-, i+, j-, j+, k-, k+) */
   double wall_u[6][3];
   double wall_T[6];
 } orc_mesh;

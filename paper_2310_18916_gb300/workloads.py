@@ -14,7 +14,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-WALL, PERIODIC = 1, 2
+# Side conditions: WALL (diffuse, wall_u / wall_T), PERIODIC (both sides of an axis; with
+# several cells the axis closes on itself, as the azimuth of an O-grid), FARFIELD (free stream
+# rho = 1, u = wall_u, T_t = T_r = wall_T), AXIS (a side of zero area: the pole of a sphere).
+WALL, PERIODIC, FARFIELD, AXIS = 1, 2, 3, 4
 SHAKHOV, RYKOV = 0, 1
 # Nitrogen relaxation data of Section 5 (d_r = 2, omega = 0.74, A = Att, Atr, Art, Arr).
 N2_A = (0.786, -0.201, -0.059, 0.842)
@@ -125,6 +128,103 @@ def serving_cavity(rng, sizes=(32, 48, 64), nvs=(16, 20, 24), kn=(1e-3, 1.0), ma
     t_stag = 1.0 + 0.5 * (gamma - 1.0) * Ma * Ma
     vmax = max(5.0, lid + 5.0 * np.sqrt(t_stag / 2.0))
     return cavity(n=n, nv=nv, vmax=vmax, lid=lid, Kn=Kn)
+
+
+def radial_nodes(n_r, R, R_out, first=None):
+    """n_r + 1 radii from R to R_out: uniform, or geometric with first spacing `first`."""
+    if first is None:
+        return np.linspace(R, R_out, n_r + 1)
+    lo, hi = 1.0 + 1e-12, 10.0
+    for _ in range(200):  # growth ratio q with first (q^n - 1) / (q - 1) = R_out - R
+        q = 0.5 * (lo + hi)
+        if first * (q ** n_r - 1.0) / (q - 1.0) > R_out - R:
+            hi = q
+        else:
+            lo = q
+    r = R + first * np.concatenate([[0.0], np.cumsum(q ** np.arange(n_r))])
+    r[-1] = R_out
+    return r
+
+
+def velocity_box(U, T_stag, vmax_min=5.0):
+    """Half-width of a velocity box holding the free stream and the stagnation gas."""
+    return max(vmax_min, float(U) + 5.0 * np.sqrt(T_stag / 2.0))
+
+
+def cylinder(n_r=16, n_theta=24, nv=16, R=0.5, R_out=5.0, first=None, Ma=0.5, Kn=0.1, omega=0.81, T_w=1.0,
+             vmax=None) -> Problem:
+    """Circular cylinder of radius R in a cross flow along +x: a 2D O-grid, i radial (wall at
+    r = R, far field at R_out), j azimuthal (closed, PERIODIC), k the inactive span.  Free-stream
+    speed Ma sqrt(gamma / 2) (gamma = 5/3), T = 1; midpoint velocity grid of half-width vmax
+    (default: the velocity box of the free stream and its stagnation temperature)."""
+    gamma = 5.0 / 3.0
+    U = Ma * np.sqrt(gamma / 2.0)
+    r = radial_nodes(n_r, R, R_out, first)
+    th = 2.0 * np.pi * np.arange(n_theta + 1) / n_theta
+    c, sn = np.cos(th), np.sin(th)
+    c[-1], sn[-1] = c[0], sn[0]  # the closing node is the first one
+    dz = float(r[1] - r[0])
+    nodes = np.zeros((2, n_theta + 1, n_r + 1, 3))
+    for k, z in enumerate((0.0, dz)):
+        nodes[k, :, :, 0] = c[:, None] * r[None, :]
+        nodes[k, :, :, 1] = sn[:, None] * r[None, :]
+        nodes[k, :, :, 2] = z
+    if vmax is None:
+        vmax = velocity_box(U, 1.0 + 0.5 * (gamma - 1.0) * Ma * Ma)
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[1, 0] = U
+    wall_T = np.ones(6)
+    wall_T[0] = T_w
+    return Problem(n_r, n_theta, 1, nodes, [WALL, FARFIELD, PERIODIC, PERIODIC, PERIODIC, PERIODIC], wall_u, wall_T,
+                   v, v.copy(), v.copy(), w, w.copy(), w.copy(), SHAKHOV, omega, Kn,
+                   W0=_uniform_state(n_r * n_theta, u=(U, 0.0, 0.0)), name=f"cylinder{n_r}x{n_theta}x{nv}^3_Ma{Ma:g}")
+
+
+def sphere(n_r=8, n_pol=6, n_az=8, nv=12, R=0.5, R_out=5.0, first=None, Ma=0.5, Kn=0.1, omega=0.81, T_w=1.0,
+           vmax=None) -> Problem:
+    """Sphere of radius R in a flow along +x: a spherical O-grid, i radial (wall at r = R, far
+    field at R_out), j polar angle from the +x axis (both ends AXIS: faces of zero area), k
+    azimuth (closed, PERIODIC).  Free stream and velocity grid as for `cylinder`."""
+    gamma = 5.0 / 3.0
+    U = Ma * np.sqrt(gamma / 2.0)
+    r = radial_nodes(n_r, R, R_out, first)
+    th = np.pi * np.arange(n_pol + 1) / n_pol
+    ct, st = np.cos(th), np.sin(th)
+    ct[0], st[0], ct[-1], st[-1] = 1.0, 0.0, -1.0, 0.0  # the poles are single points
+    ph = 2.0 * np.pi * np.arange(n_az + 1) / n_az
+    cp, sp = np.cos(ph), np.sin(ph)
+    cp[-1], sp[-1] = cp[0], sp[0]
+    nodes = np.zeros((n_az + 1, n_pol + 1, n_r + 1, 3))
+    nodes[..., 0] = ct[None, :, None] * r[None, None, :]
+    nodes[..., 1] = (st[None, :, None] * cp[:, None, None]) * r[None, None, :]
+    nodes[..., 2] = (st[None, :, None] * sp[:, None, None]) * r[None, None, :]
+    if vmax is None:
+        vmax = velocity_box(U, 1.0 + 0.5 * (gamma - 1.0) * Ma * Ma)
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[1, 0] = U
+    wall_T = np.ones(6)
+    wall_T[0] = T_w
+    nc = n_r * n_pol * n_az
+    return Problem(n_r, n_pol, n_az, nodes, [WALL, FARFIELD, AXIS, AXIS, PERIODIC, PERIODIC], wall_u, wall_T,
+                   v, v.copy(), v.copy(), w, w.copy(), w.copy(), SHAKHOV, omega, Kn,
+                   W0=_uniform_state(nc, u=(U, 0.0, 0.0)), name=f"sphere{n_r}x{n_pol}x{n_az}x{nv}^3_Ma{Ma:g}")
+
+
+def reservoir_wall(n_cells=10, nv=16, vmax=5.0, U=(0.0, 0.3, 0.0), T_inf=1.0, T_w=2.0, Kn=1e7) -> Problem:
+    """1D slab x in [0, 1]: a far field (free stream rho = 1, U, T_inf) at x = 0 and a diffuse
+    wall at rest at T_w at x = 1."""
+    dx = 1.0 / n_cells
+    nodes = box_nodes(np.linspace(0.0, 1.0, n_cells + 1), [0.0, dx], [0.0, dx])
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[0] = U
+    wall_T = np.ones(6)
+    wall_T[0], wall_T[1] = T_inf, T_w
+    return Problem(n_cells, 1, 1, nodes, [FARFIELD, WALL, PERIODIC, PERIODIC, PERIODIC, PERIODIC], wall_u, wall_T,
+                   v, v.copy(), v.copy(), w, w.copy(), w.copy(), SHAKHOV, 0.81, Kn,
+                   W0=_uniform_state(n_cells, u=U, Tt=T_inf, Tr=T_inf), name=f"reservoir{n_cells}x{nv}^3")
 
 
 def box3d(ni=6, nj=5, nk=4, nv=12, vmax=5.0, Kn=0.1, omega=0.81, wall_speed=0.2) -> Problem:
