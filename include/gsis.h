@@ -42,19 +42,29 @@ extern "C" {
 #define GSIS_E_NOT_CONVERGED (-6) /* max_outer reached above tol; results are valid */
 #define GSIS_E_UNSUPPORTED (-7)   /* valid input outside what the library implements */
 
-enum gsis_bc_type { GSIS_BC_WALL = 1, GSIS_BC_PERIODIC = 2 };
+enum gsis_bc_type { GSIS_BC_WALL = 1, GSIS_BC_PERIODIC = 2, GSIS_BC_FARFIELD = 3, GSIS_BC_AXIS = 4 };
 enum gsis_model { GSIS_SHAKHOV = 0, GSIS_RYKOV = 1 };
 enum gsis_precision { GSIS_F64 = 0, GSIS_F32 = 1, GSIS_BF16 = 2 };
 enum gsis_mode { GSIS_MODE_GSIS = 0, GSIS_MODE_DVM = 1 };
 
 /* Structured hexahedral block (spatial finite-volume cells of Section 3.1).
  * nodes: (ni+1)(nj+1)(nk+1) x 3 doubles (host), node (I,J,K) at index I + (ni+1)(J + (nj+1)K).
- * The library requires a rectilinear block (node x depends on I only, y on J, z on K,
- * increasing), else GSIS_E_UNSUPPORTED.
- * bc[side], side = x-, x+, y-, y+, z-, z+: an axis with one cell must be PERIODIC on both
- * sides (it then carries no transport); an axis with more cells must be WALL on both sides.
- * Walls are isothermal and fully diffuse with velocity wall_u[side] (tangential) and
- * temperature wall_T[side]. */
+ * bc[side], side = i-, i+, j-, j+, k-, k+ (x-, x+, ... on a rectilinear block):
+ *   WALL      isothermal, fully diffuse wall with velocity wall_u[side] (tangential) and
+ *             temperature wall_T[side];
+ *   PERIODIC  on both sides of an axis.  An axis with one cell must be PERIODIC (it then carries
+ *             no transport); with at least 3 cells the axis closes on itself, the two ends being
+ *             neighbours (the azimuth of an O-grid: the mesh geometry already joins them);
+ *   FARFIELD  free stream of density 1, velocity wall_u[side] and temperature wall_T[side]:
+ *             molecules entering through a face carry its Maxwellian where the free stream does
+ *             not leave through the face, else the cell's own face value;
+ *   AXIS      a degenerate side of zero area (the pole of a spherical grid): no flux.
+ * Axes with one cell come after the others.  A rectilinear block (node x depends on I only,
+ * y on J, z on K, increasing) with WALL sides and one-cell periodic axes runs every mode; any
+ * other block (curvilinear, far field, pole or wrapped sides) runs the kinetic iteration
+ * (GSIS_MODE_DVM) on one device, with n_sweeps colour passes per step; the synthetic solve and
+ * velocity sharding on such blocks return GSIS_E_UNSUPPORTED.  Cells must have positive
+ * volume, else GSIS_E_INVALID. */
 typedef struct {
   int ni, nj, nk;
   const double *nodes;
@@ -101,7 +111,9 @@ typedef struct {
                            compensated sums.  The synthetic solve, the correction state and the
                            residual are FP64 always. */
   int mode;             /* GSIS_MODE_GSIS (default) or GSIS_MODE_DVM (plain kinetic iteration) */
-  int n_sweeps;         /* colour-ordered point-implicit passes per kinetic step (default 1) */
+  int n_sweeps;         /* colour-ordered point-implicit passes per kinetic step (default 1; a
+                           rectilinear block is solved exactly by 1 and takes only 1; general
+                           blocks take 1..64) */
   int macro_steps;      /* inner synthetic steps per outer step (default 300, Algorithm 1) */
   int macro_sweeps;     /* red-black LU-SGS passes per inner step (default 4, Algorithm 2) */
   double macro_cfl;     /* pseudo-time CFL of the synthetic solve (default 100) */

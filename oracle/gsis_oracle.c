@@ -359,6 +359,13 @@ typedef struct {
   double *fl;            /* this velocity's outward face fluxes [cell][side][6] */
 } kin_work;
 
+/* A far-field face lets the free stream in unless the stream leaves through it: U_inf . S <= 0,
+   with faces tangential to the stream (|U_inf . S| at rounding level) counted as inflow. */
+static int far_inflow(const orc_solver *s, int i, int side) {
+  const double *U = s->wall_u[side], *S = s->S + 18 * i + 3 * side;
+  return dot3(U, S) <= 1e-12 * sqrt(dot3(U, U) * dot3(S, S));
+}
+
 /* Face values (f, and f1 for Rykov) entering the domain through the boundary face (i, side)
    for velocity xi: at a wall the re-emitted rho_w M_w (f1 = (d_r T_w / 4) f); at a far field
    the free-stream Maxwellian where the free stream does not leave through the face
@@ -368,7 +375,7 @@ static void boundary_in(const orc_solver *s, int i, int side, const double *xi, 
     double M = s->rho_w[s->wid[6 * i + side]] * wall_maxwellian(s, side, xi);
     e[0] = M;
     e[1] = s->g.d_r * s->wall_T[side] / 4.0 * M;
-  } else if (dot3(s->wall_u[side], s->S + 18 * i + 3 * side) <= 0.0) {
+  } else if (far_inflow(s, i, side)) {
     double M = maxwellian(1.0, s->wall_u[side], s->wall_T[side], xi);
     e[0] = M;
     e[1] = s->g.d_r * s->wall_T[side] / 4.0 * M;

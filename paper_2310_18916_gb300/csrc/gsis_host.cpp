@@ -67,6 +67,19 @@ struct gsis_solver {
   std::vector<int> wall_cell, wall_side, wall_sides_list;
   double wall_uT[6][4] = {};
   int closed = 1;
+  // general (curvilinear) meshes: per-cell geometry, neighbour codes, wall-face ids, far-field
+  // inflow sides, wall-face areas; the kinetic kernel's persistent grid
+  bool general = false;
+  std::vector<GenCell<double>> gen64;
+  std::vector<int> gnb, gwid;
+  std::vector<unsigned char> gin;
+  std::vector<double> wall_area;
+  void *d_gen = nullptr;
+  int *d_gnb = nullptr, *d_gwid = nullptr;
+  unsigned char *d_gin = nullptr;
+  double *d_wall_area = nullptr;
+  int kin_grid = 0;
+  size_t kin_scratch_bytes = 0;
   // device
   std::vector<DevBuf> allocs;
   void *d_f = nullptr, *d_wpart = nullptr, *d_stT = nullptr, *d_vel = nullptr;
@@ -194,6 +207,11 @@ struct gsis_solver {
     a.err = d_err;
     a.gscratch = static_cast<unsigned char *>(d_kscratch);
     a.gstride = kin_gstride;
+    a.gen = static_cast<const GenCell<T> *>(d_gen);
+    a.gnb = d_gnb;
+    a.gwid = d_gwid;
+    a.gin = d_gin;
+    a.n_sweeps = opt.n_sweeps;
     return a;
   }
 
@@ -225,7 +243,7 @@ struct gsis_solver {
     if (rc) return rc;
     rc = cuda(launch_reduce<T>(d_mp, mom_nchunks, nvdf, static_cast<const T *>(d_wpart), d_boct, nblocks, kg, d_wall_cell,
                                d_wall_side, nwall, d_rho_w, d_Zw, opt.shard_count <= 1 || opt.shard_index == 0,
-                               d_vol, d_st64, d_mom, d_K, d_wf, stream),
+                               general, d_vol, d_st64, d_mom, d_K, d_wf, stream),
               "reduce");
     if (!rc) rc = exchange(d_mom, (size_t)nc * MOM_STRIDE, "moments");
     if (!rc) rc = exchange(d_K, (size_t)nc * 6, "kinetic flux sums");
@@ -311,13 +329,18 @@ struct gsis_solver {
   int step_impl(int mode) {
     int launches = 0;
     mark(0);
-    int rc = cuda(launch_wall_prepass<T, S>(kin_args<T, S>(), d_wall_cell, d_wall_side, nwall, d_Z0, d_rho_w, nslots, stream),
-                  "wall pre-pass");
+    int rc = general ? cuda(launch_wall_prepass_general<T, S>(kin_args<T, S>(), d_wall_cell, d_wall_side, nwall, d_rho_w,
+                                                              stream),
+                            "wall pre-pass")
+                     : cuda(launch_wall_prepass<T, S>(kin_args<T, S>(), d_wall_cell, d_wall_side, nwall, d_Z0, d_rho_w,
+                                                      nslots, stream),
+                            "wall pre-pass");
     if (!rc) rc = exchange(d_rho_w, (size_t)nwall, "wall densities");
     if (rc) return rc;
     launches += nwall > 0;
     mark(1);
-    rc = cuda(launch_kinetic<T, S>(kin_args<T, S>(), nblocks, kin_warps, kin_smem, stream), "kinetic");
+    rc = general ? cuda(launch_kinetic_general<T, S>(kin_args<T, S>(), kin_grid, stream), "kinetic")
+                 : cuda(launch_kinetic<T, S>(kin_args<T, S>(), nblocks, kin_warps, kin_smem, stream), "kinetic");
     if (rc) return rc;
     mark(2);
     rc = reduce_and_finalize<T, S>(true);
@@ -456,6 +479,28 @@ extern "C" void gsis_default_options(gsis_options *o) {
 
 namespace {
 
+// A mesh takes the general (curvilinear) path when its nodes are not a rectilinear product or
+// a side is a far field, a pole, or a wrapped axis with several cells.
+bool rectilinear_nodes(const gsis_mesh *m) {
+  const int N0 = m->ni + 1, N1 = m->nj + 1, N2 = m->nk + 1;
+  auto node = [&](int I, int J, int K, int d) { return m->nodes[3 * ((size_t)I + (size_t)N0 * ((size_t)J + (size_t)N1 * K)) + d]; };
+  for (int K = 0; K < N2; ++K)
+    for (int J = 0; J < N1; ++J)
+      for (int I = 0; I < N0; ++I)
+        if (node(I, J, K, 0) != node(I, 0, 0, 0) || node(I, J, K, 1) != node(0, J, 0, 1) || node(I, J, K, 2) != node(0, 0, K, 2))
+          return false;
+  return true;
+}
+
+bool needs_general(const gsis_mesh *m) {
+  const int n[3] = {m->ni, m->nj, m->nk};
+  for (int side = 0; side < 6; ++side) {
+    const int b = m->bc[side];
+    if (b == GSIS_BC_FARFIELD || b == GSIS_BC_AXIS || (b == GSIS_BC_PERIODIC && n[side / 2] > 1)) return true;
+  }
+  return !rectilinear_nodes(m);
+}
+
 int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double Kn, const gsis_options *o,
              std::string &why) {
   if (!m || !vg || !g || !o || !m->nodes) { why = "NULL argument"; return GSIS_E_INVALID; }
@@ -487,39 +532,50 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   }
   if (g->model != GSIS_SHAKHOV && g->model != GSIS_RYKOV) { why = "bad model"; return GSIS_E_INVALID; }
   if (o->kin_inv_dt != 0.0) { why = "the GPU kinetic step is steady (kin_inv_dt = 0)"; return GSIS_E_UNSUPPORTED; }
-  if (o->n_sweeps != 1) { why = "rectilinear colour sweeps are exact in one pass: n_sweeps must be 1"; return GSIS_E_UNSUPPORTED; }
+  const bool general = needs_general(m);
+  if (!general && o->n_sweeps != 1) {
+    why = "rectilinear colour sweeps are exact in one pass: n_sweeps must be 1";
+    return GSIS_E_UNSUPPORTED;
+  }
+  if (general && (o->n_sweeps < 1 || o->n_sweeps > 64)) { why = "n_sweeps must be in [1, 64]"; return GSIS_E_INVALID; }
   const int n[3] = {m->ni, m->nj, m->nk};
   bool seen_inactive = false;
   for (int a = 0; a < 3; ++a) {
     const bool active = n[a] > 1;
+    const int lo = m->bc[2 * a], hi = m->bc[2 * a + 1];
+    for (int t = 0; t < 2; ++t)
+      if (m->bc[2 * a + t] < GSIS_BC_WALL || m->bc[2 * a + t] > GSIS_BC_AXIS) { why = "bad boundary condition"; return GSIS_E_INVALID; }
     if (!active) {
-      if (m->bc[2 * a] != GSIS_BC_PERIODIC || m->bc[2 * a + 1] != GSIS_BC_PERIODIC) {
+      if (lo != GSIS_BC_PERIODIC || hi != GSIS_BC_PERIODIC) {
         why = "an axis with one cell must be periodic on both sides";
         return GSIS_E_INVALID;
       }
       seen_inactive = true;
     } else {
       if (seen_inactive) { why = "active axes must come first (x, then y, then z)"; return GSIS_E_UNSUPPORTED; }
-      if (m->bc[2 * a] != GSIS_BC_WALL || m->bc[2 * a + 1] != GSIS_BC_WALL) {
-        why = "only wall boundaries on axes with more than one cell";
-        return GSIS_E_UNSUPPORTED;
+      if ((lo == GSIS_BC_PERIODIC) != (hi == GSIS_BC_PERIODIC)) {
+        why = "a periodic axis is periodic on both sides";
+        return GSIS_E_INVALID;
       }
+      if (lo == GSIS_BC_PERIODIC && n[a] < 3) { why = "a wrapped axis needs at least 3 cells"; return GSIS_E_INVALID; }
     }
   }
-  for (int a = 0; a < 3; ++a)
-    for (int s = 0; s < 2; ++s)
-      if (m->bc[2 * a + s] == GSIS_BC_WALL && !(m->wall_T[2 * a + s] > 0)) { why = "wall temperature must be positive"; return GSIS_E_INVALID; }
-  // rectilinear check
+  for (int s = 0; s < 6; ++s)
+    if ((m->bc[s] == GSIS_BC_WALL || m->bc[s] == GSIS_BC_FARFIELD) && !(m->wall_T[s] > 0)) {
+      why = "wall and free-stream temperatures must be positive";
+      return GSIS_E_INVALID;
+    }
+  if (general) {
+    if (o->mode == GSIS_MODE_GSIS) {
+      why = "the synthetic solve is built for rectilinear meshes only: use GSIS_MODE_DVM on general meshes";
+      return GSIS_E_UNSUPPORTED;
+    }
+    if (o->shard_count > 1) { why = "velocity sharding is built for rectilinear meshes only"; return GSIS_E_UNSUPPORTED; }
+    return GSIS_OK;  // volumes are checked when the geometry is built
+  }
   const int N0 = m->ni + 1, N1 = m->nj + 1, N2 = m->nk + 1;
   auto node = [&](int I, int J, int K, int d) { return m->nodes[3 * ((size_t)I + (size_t)N0 * ((size_t)J + (size_t)N1 * K)) + d]; };
-  for (int K = 0; K < N2; ++K)
-    for (int J = 0; J < N1; ++J)
-      for (int I = 0; I < N0; ++I) {
-        if (node(I, J, K, 0) != node(I, 0, 0, 0) || node(I, J, K, 1) != node(0, J, 0, 1) || node(I, J, K, 2) != node(0, 0, K, 2)) {
-          why = "mesh is not rectilinear";
-          return GSIS_E_UNSUPPORTED;
-        }
-      }
+  (void)N2;
   for (int I = 1; I < N0; ++I) if (!(node(I, 0, 0, 0) > node(I - 1, 0, 0, 0))) { why = "x nodes must increase"; return GSIS_E_INVALID; }
   for (int J = 1; J < N1; ++J) if (!(node(0, J, 0, 1) > node(0, J - 1, 0, 1))) { why = "y nodes must increase"; return GSIS_E_INVALID; }
   for (int K = 1; K < N2; ++K) if (!(node(0, 0, K, 2) > node(0, 0, K - 1, 2))) { why = "z nodes must increase"; return GSIS_E_INVALID; }
@@ -560,6 +616,24 @@ void build_slots(const gsis_vgrid *vg, std::vector<int> &slot_canon, std::vector
 }
 
 template <typename T>
+std::vector<GenCell<T>> cast_gen(const std::vector<GenCell<double>> &in) {
+  std::vector<GenCell<T>> out(in.size());
+  for (size_t c = 0; c < in.size(); ++c) {
+    for (int s = 0; s < 6; ++s) {
+      for (int d = 0; d < 3; ++d) {
+        out[c].f[s].S[d] = (T)in[c].f[s].S[d];
+        out[c].f[s].r[d] = (T)in[c].f[s].r[d];
+        out[c].f[s].w[d] = (T)in[c].f[s].w[d];
+      }
+      out[c].f[s].invA = (T)in[c].f[s].invA;
+    }
+    out[c].invV = (T)in[c].invV;
+    out[c].eps2 = (T)in[c].eps2;
+  }
+  return out;
+}
+
+template <typename T>
 std::vector<AxisCell<T>> cast_axis(const std::vector<AxisCell<double>> &in) {
   std::vector<AxisCell<T>> out(in.size());
   for (size_t i = 0; i < in.size(); ++i)
@@ -568,6 +642,142 @@ std::vector<AxisCell<T>> cast_axis(const std::vector<AxisCell<double>> &in) {
 }
 
 }  // namespace
+
+// Finite-volume geometry of a general structured block (Section 3.1): a face's area vector is
+// half the cross product of its diagonals, oriented out of the cell; its centre the mean of its
+// corners; a cell's centre the mean of its 8 corners and its volume (1/3) sum x_f . S_f
+// (divergence theorem with F = x / 3).  Least squares: the unweighted normal equations over
+// the in-domain neighbours, with the components of one-cell axes fixed to zero, inverted once
+// per cell into per-side weights.  Wall faces are numbered cell by cell, side by side.
+static int build_general(gsis_solver *s, const gsis_mesh *m) {
+  const int n[3] = {m->ni, m->nj, m->nk}, nc = s->nc;
+  const int N0 = m->ni + 1, N1 = m->nj + 1;
+  auto P = [&](int I, int J, int K, double *p) {
+    const double *q = m->nodes + 3 * ((size_t)I + (size_t)N0 * ((size_t)J + (size_t)N1 * K));
+    p[0] = q[0];
+    p[1] = q[1];
+    p[2] = q[2];
+  };
+  s->gen64.assign(nc, GenCell<double>{});
+  s->gnb.assign((size_t)6 * nc, NB_ABSENT);
+  s->gwid.assign((size_t)6 * nc, -1);
+  s->gin.assign((size_t)6 * nc, 0);
+  s->vol.assign(nc, 0.0);
+  std::vector<double> xc((size_t)3 * nc);
+  s->vsum = 0.0;
+  s->nwall = 0;
+  s->wall_cell.clear();
+  s->wall_side.clear();
+  s->wall_area.clear();
+  s->closed = 1;
+  for (int side = 0; side < 6; ++side)
+    if (m->bc[side] == GSIS_BC_FARFIELD) s->closed = 0;
+  const double K3 = s->opt.venkat_K * s->opt.venkat_K * s->opt.venkat_K;
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        const int c = i + n[0] * (j + n[1] * k);
+        double cen[3] = {0, 0, 0}, p[3];
+        for (int t = 0; t < 8; ++t) {
+          P(i + (t & 1), j + ((t >> 1) & 1), k + (t >> 2), p);
+          for (int d = 0; d < 3; ++d) cen[d] += p[d] / 8.0;
+        }
+        for (int d = 0; d < 3; ++d) xc[3 * (size_t)c + d] = cen[d];
+        GenCell<double> &g = s->gen64[c];
+        double V = 0.0;
+        for (int side = 0; side < 6; ++side) {
+          const int a = side / 2, hi = side & 1;
+          // the face's corners in cyclic order: the two tangential index directions
+          const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+          double q[4][3];
+          for (int t = 0; t < 4; ++t) {
+            int idx[3] = {i, j, k};
+            idx[a] += hi;
+            idx[t1] += (t == 1 || t == 2);
+            idx[t2] += (t >= 2);
+            P(idx[0], idx[1], idx[2], q[t]);
+          }
+          double d1[3], d2[3], S[3], xf[3];
+          for (int d = 0; d < 3; ++d) {
+            d1[d] = q[2][d] - q[0][d];
+            d2[d] = q[3][d] - q[1][d];
+            xf[d] = 0.25 * (q[0][d] + q[1][d] + q[2][d] + q[3][d]);
+          }
+          S[0] = 0.5 * (d1[1] * d2[2] - d1[2] * d2[1]);
+          S[1] = 0.5 * (d1[2] * d2[0] - d1[0] * d2[2]);
+          S[2] = 0.5 * (d1[0] * d2[1] - d1[1] * d2[0]);
+          double r[3] = {xf[0] - cen[0], xf[1] - cen[1], xf[2] - cen[2]};
+          if (S[0] * r[0] + S[1] * r[1] + S[2] * r[2] < 0)
+            for (int d = 0; d < 3; ++d) S[d] = -S[d];
+          V += (xf[0] * S[0] + xf[1] * S[1] + xf[2] * S[2]) / 3.0;
+          const double A = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+          for (int d = 0; d < 3; ++d) {
+            g.f[side].S[d] = S[d];
+            g.f[side].r[d] = r[d];
+          }
+          g.f[side].invA = A > 0 ? 1.0 / A : 0.0;
+          int idx[3] = {i, j, k};
+          idx[a] += hi ? 1 : -1;
+          int nb;
+          const int b = m->bc[side];
+          if (n[a] == 1) nb = NB_ABSENT;
+          else if (idx[a] >= 0 && idx[a] < n[a]) nb = idx[0] + n[0] * (idx[1] + n[1] * idx[2]);
+          else if (b == GSIS_BC_PERIODIC) {
+            idx[a] = (idx[a] + n[a]) % n[a];
+            nb = idx[0] + n[0] * (idx[1] + n[1] * idx[2]);
+          } else if (b == GSIS_BC_AXIS) nb = NB_AXIS;
+          else if (b == GSIS_BC_FARFIELD) {
+            nb = NB_FAR;
+            // the free stream enters unless it leaves through the face (tangential faces enter)
+            const double *U = m->wall_u[side];
+            const double un = U[0] * S[0] + U[1] * S[1] + U[2] * S[2];
+            const double Un = std::sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+            s->gin[6 * (size_t)c + side] = un <= 1e-12 * Un * A;
+          } else {
+            nb = NB_WALL;
+            s->gwid[6 * (size_t)c + side] = s->nwall++;
+            s->wall_cell.push_back(c);
+            s->wall_side.push_back(side);
+            s->wall_area.push_back(A);
+          }
+          s->gnb[6 * (size_t)c + side] = nb;
+        }
+        if (!(V > 0)) return s->fail(GSIS_E_INVALID, "cell %d has volume %g", c, V);
+        s->vol[c] = V;
+        s->vsum += V;
+        g.invV = 1.0 / V;
+        g.eps2 = K3 * V;
+      }
+  // least-squares weights
+  for (int c = 0; c < nc; ++c) {
+    GenCell<double> &g = s->gen64[c];
+    double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, dv[6][3];
+    for (int side = 0; side < 6; ++side) {
+      const int nb = s->gnb[6 * (size_t)c + side];
+      for (int d = 0; d < 3; ++d) dv[side][d] = nb >= 0 ? xc[3 * (size_t)nb + d] - xc[3 * (size_t)c + d] : 0.0;
+      for (int a = 0; a < 3; ++a)
+        if (n[a] == 1) dv[side][a] = 0.0;
+      for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) A[r][q] += dv[side][r] * dv[side][q];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (n[a] == 1) A[a][a] = 1.0;
+    const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                       A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (!(std::fabs(det) > 0)) return s->fail(GSIS_E_INVALID, "cell %d: singular least-squares system", c);
+    double inv[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) {
+        // adjugate / det: cofactor of (q, r)
+        const int r1 = (q + 1) % 3, r2 = (q + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+        inv[r][q] = (A[r1][c1] * A[r2][c2] - A[r1][c2] * A[r2][c1]) / det;
+      }
+    for (int side = 0; side < 6; ++side)
+      for (int r = 0; r < 3; ++r)
+        g.f[side].w[r] = inv[r][0] * dv[side][0] + inv[r][1] * dv[side][1] + inv[r][2] * dv[side][2];
+  }
+  return GSIS_OK;
+}
 
 static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
   s->n[0] = m->ni;
@@ -697,6 +907,12 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
     }
     s->nwall += ntr;
   }
+  s->general = needs_general(m);
+  if (s->general) {
+    for (int side = 0; side < 6; ++side) g.wall_base[side] = -1;
+    const int rc = build_general(s, m);
+    if (rc) return rc;
+  }
   // red/black cell lists of the synthetic solve's sweeps
   s->colcells.clear();
   for (int col = 0; col < 2; ++col) {
@@ -737,6 +953,23 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
 // placement follows the shared-memory limit of the sm_100 family, 227 KB.
 template <typename T, typename S>
 static int plan_kinetic(gsis_solver *s) {
+  if (s->general) {
+    // persistent grid of 8-warp CTAs over the velocity blocks, at most 2 per SM: each holds
+    // whole-mesh work arrays for its block of 32 velocities
+    s->kin_smem = 0;
+    s->kin_warps = 8;
+    s->kin_gstride = kinetic_general_stride<T, S>(s->nc, s->nvdf);
+    int dev = 0, sms = 152, occ = 2;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+      const int rc = s->cuda(kinetic_general_shape<T, S>(s->nvdf, &occ), "kinetic shape");
+      if (rc) return rc;
+    } else {
+      cudaGetLastError();
+    }
+    s->kin_grid = std::max(1, std::min(s->nblocks, std::max(1, std::min(occ, 2)) * sms));
+    s->kin_scratch_bytes = (size_t)s->kin_grid * s->kin_gstride;
+    return GSIS_OK;
+  }
   const size_t smem = kinetic_smem_bytes<T, S>(s->kg, s->nvdf);
   const size_t gstride = kinetic_gscratch_stride<T, S>(s->kg, s->nvdf);
   int want = std::max(1, std::min(16, s->kg.maxcol / 4));
@@ -760,6 +993,7 @@ static int plan_kinetic(gsis_solver *s) {
   s->kin_smem = gm ? 0 : smem;
   s->kin_gstride = gm ? gstride : 0;
   s->kin_warps = gm ? warps_gm : warps_sh;
+  s->kin_scratch_bytes = (size_t)s->nblocks * s->kin_gstride;
   return GSIS_OK;
 }
 
@@ -770,7 +1004,8 @@ static size_t footprint(const gsis_solver *s) {
   size_t b = 0;
   b += (size_t)s->nvdf * s->nslots * nc * Sb;  // f (f0, f1)
   b += (size_t)s->nblocks * (s->nwall + 1) * NWF * T;  // wall partials
-  b += (size_t)s->nblocks * s->kin_gstride;           // kinetic ring in global memory
+  b += s->kin_scratch_bytes;                          // kinetic ring or work arrays in global memory
+  if (s->general) b += nc * (sizeof(GenCell<double>) + 6 * (2 * sizeof(int) + 1)) + (size_t)s->nwall * 8;
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
@@ -794,7 +1029,14 @@ static int allocate_and_upload(gsis_solver *s) {
   }
   A(s->d_mp, (size_t)s->mom_nchunks * nc * moment_len(s->nvdf) * sizeof(double));
   A(s->d_wpart, (size_t)s->nblocks * (s->nwall + 1) * NWF * sizeof(T));
-  if (s->kin_gstride) A(s->d_kscratch, (size_t)s->nblocks * s->kin_gstride);
+  if (s->kin_scratch_bytes) A(s->d_kscratch, s->kin_scratch_bytes);
+  if (s->general) {
+    A(s->d_gen, nc * sizeof(GenCell<T>));
+    A(s->d_gnb, 6 * nc * sizeof(int));
+    A(s->d_gwid, 6 * nc * sizeof(int));
+    A(s->d_gin, 6 * nc);
+    A(s->d_wall_area, (size_t)(s->nwall + 1) * sizeof(double));
+  }
   A(s->d_K, nc * 6 * sizeof(double));
   A(s->d_stT, nc * NST * sizeof(T));
   A(s->d_st64, nc * NST * sizeof(double));
@@ -872,6 +1114,14 @@ static int allocate_and_upload(gsis_solver *s) {
   if (!rc) rc = s->upload(s->d_wall_uT, &s->wall_uT[0][0], 24 * sizeof(double));
   if (!rc) rc = s->upload(s->d_vol, s->vol.data(), nc * sizeof(double));
   if (!rc) rc = s->upload(s->d_colcells, s->colcells.data(), nc * sizeof(int));
+  if (!rc && s->general) {
+    const std::vector<GenCell<T>> gT = cast_gen<T>(s->gen64);
+    rc = s->upload(s->d_gen, gT.data(), nc * sizeof(GenCell<T>));
+    if (!rc) rc = s->upload(s->d_gnb, s->gnb.data(), 6 * nc * sizeof(int));
+    if (!rc) rc = s->upload(s->d_gwid, s->gwid.data(), 6 * nc * sizeof(int));
+    if (!rc) rc = s->upload(s->d_gin, s->gin.data(), 6 * nc);
+    if (!rc && s->nwall) rc = s->upload(s->d_wall_area, s->wall_area.data(), s->nwall * sizeof(double));
+  }
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_ticket, 0, 4 * sizeof(unsigned), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_rho_w, 0, (s->nwall + 1) * sizeof(double), s->stream), "memset");
@@ -1064,7 +1314,7 @@ extern "C" int gsis_wall(gsis_handle h, int *cell, int *side, double *rho_w, dou
     if (side) side[w] = h->wall_side[w];
     if (rho_w) rho_w[w] = rw[w];
     if (flux6) {
-      const double A = face_area(h, h->wall_cell[w], h->wall_side[w] / 2);
+      const double A = h->general ? h->wall_area[w] : face_area(h, h->wall_cell[w], h->wall_side[w] / 2);
       for (int k = 0; k < 6; ++k) flux6[6 * w + k] = wf[6 * w + k] * A;
     }
   }
@@ -1082,6 +1332,7 @@ extern "C" int gsis_wall_loads(gsis_handle h, unsigned side_mask, const double *
   a.wall_cell = h->d_wall_cell;
   a.wall_side = h->d_wall_side;
   a.nwall = h->nwall;
+  a.area = h->general ? h->d_wall_area : nullptr;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = h->n[d];
     a.ax[d] = h->d_ax64[d];

@@ -74,6 +74,21 @@ struct KinGeom {
   double K3;            // venkat K^3: eps^2 = K^3 V
 };
 
+// General (curvilinear) structured meshes.  Per cell and side: the outward area vector S, the
+// vector r from the cell centre to the face centre, the least-squares weight w (gradient =
+// sum over the in-domain neighbours of w (q_j - q_i)) and 1/|S|; per cell 1/V and the
+// Venkatakrishnan eps^2 = (K V^(1/3))^3.  Neighbour codes: >= 0 a cell, or one of the NB_*.
+template <typename T>
+struct GenFace {
+  T S[3], r[3], w[3], invA;
+};
+template <typename T>
+struct GenCell {
+  GenFace<T> f[6];
+  T invV, eps2;
+};
+constexpr int NB_WALL = -1, NB_ABSENT = -2, NB_AXIS = -3, NB_FAR = -4;
+
 // T: kinetic arithmetic (float or double); S: VDF storage (T, or __nv_bfloat16 with T = float)
 template <typename T, typename S = T>
 struct KinArgs {
@@ -95,8 +110,15 @@ struct KinArgs {
   int nwall;
   int nblocks;
   int *err;              // device error flag (a bounded wait that timed out)
-  unsigned char *gscratch;  // ring and face buffers in global memory (nullptr: shared memory)
-  size_t gstride;           // bytes of gscratch per velocity block
+  unsigned char *gscratch;  // ring and face buffers in global memory (nullptr: shared memory);
+                            // general meshes: the per-CTA work arrays of the kinetic kernel
+  size_t gstride;           // bytes of gscratch per velocity block (general meshes: per CTA)
+  // general meshes (nullptr otherwise)
+  const GenCell<T> *gen;    // [cell]
+  const int *gnb;           // [cell][6] neighbour codes
+  const int *gwid;          // [cell][6] wall-face id, -1 if the side is not a wall
+  const unsigned char *gin; // [cell][6] far-field sides: 1 where the free stream enters
+  int n_sweeps;             // point-implicit passes over the colours
 };
 
 // ---- launchers (defined in the .cu files) ----
@@ -120,6 +142,18 @@ cudaError_t launch_export_f(const KinArgs<T, S> &a, int q, const int *slot_canon
 template <typename T, typename S>
 cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon, int nslots, int nv, const double *in,
                             cudaStream_t s);
+// general meshes: the kinetic step as a persistent kernel over the velocity blocks (grid CTAs of
+// 8 warps, each with gstride bytes of work arrays), and the wall pre-pass
+template <typename T, typename S>
+cudaError_t launch_kinetic_general(const KinArgs<T, S> &a, int grid, cudaStream_t s);
+template <typename T, typename S>
+cudaError_t kinetic_general_shape(int nvdf, int *ctas_per_sm);
+template <typename T, typename S>
+size_t kinetic_general_stride(int nc, int nvdf);
+template <typename T, typename S>
+cudaError_t launch_wall_prepass_general(const KinArgs<T, S> &a, const int *wall_cell, const int *wall_side, int nwall,
+                                        double *rho_w, cudaStream_t s);
+
 // launch shape of the kinetic kernel (gm: ring in global scratch): warps = want_warps capped by
 // the kernel's registers, and the blocks of that size and dynamic shared memory an SM holds
 template <typename T, typename S>
@@ -135,7 +169,7 @@ cudaError_t launch_wall_constants(const double *vel64, int nslots, const double 
 template <typename T>
 cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpart, const int8_t *boct, int nblocks,
                           const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
-                          const double *rho_w, const double *Zw, bool emit, const double *vol,
+                          const double *rho_w, const double *Zw, bool emit, bool general, const double *vol,
                           const double *st64, double *mom, double *K, double *wf, cudaStream_t s);
 constexpr int MOM_STRIDE = NMOM + NMOM1;  // per-cell raw moments: f0 then f1
 
@@ -197,6 +231,7 @@ struct WallLoadArgs {
   int nwall;
   int n[3];
   const AxisCell<double> *ax[3];
+  const double *area;          // general meshes: [wall face] area (nullptr: from ax)
   unsigned mask;               // bit s selects wall side s
   double dir[3], rho_ref, U_ref, A_ref;
   double *out;                 // [6] force(3), energy flux, C_D, C_H

@@ -991,6 +991,347 @@ cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// General (curvilinear) structured meshes: O-grids with far-field, pole and wrapped sides.
+//
+// On a curved mesh the upwind side of a face changes with the velocity, so the colour sweeps are
+// no longer exact in one pass; the kernel therefore keeps whole-mesh work arrays for its block
+// of 32 velocities (in its own slice of a device scratch) and runs the steps of Section 3.1 one
+// after another: f^n with the pending correction, the limited LSQ gradient, the second-order
+// upwind residual with the implicit diagonal, n_sweeps point-implicit passes over the colours
+// of the octant (a cell's inflow increments are the neighbours' latest), the update.  A
+// persistent grid walks the velocity blocks, one block per CTA at a time.
+
+template <typename T>
+__device__ __forceinline__ T dot_xi(const T *S, T x, T y, T z) {
+  return x * S[0] + y * S[1] + z * S[2];
+}
+
+// Venkatakrishnan factor of one cell from its unlimited gradient gr and neighbour bounds: the
+// minimum over its faces (not the absent or pole sides) of
+//   (Dm^2 + e^2 + 2 D2 Dm) / (Dm^2 + 2 D2^2 + D2 Dm + e^2),  D2 = gr . r,
+// Dm the bound on the side of D2; faces with D2 = 0 give 1.  Both parts are positive, so the
+// minimum is found by cross-multiplication and divided once.
+template <typename T>
+__device__ __forceinline__ T venkat_general(const GenCell<T> &g, const int *nb, T fi, T fmax, T fmin, const T *gr) {
+  T bn = (T)1, bd = (T)1;
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    if (nb[s] == NB_ABSENT || nb[s] == NB_AXIS) continue;
+    const T d2 = gr[0] * g.f[s].r[0] + gr[1] * g.f[s].r[1] + gr[2] * g.f[s].r[2];
+    if (d2 == (T)0) continue;
+    const T dm = d2 > (T)0 ? fmax - fi : fmin - fi;
+    const T dm2 = dm * dm + g.eps2;
+    const T n = dm2 + (T)2 * d2 * dm;
+    const T d = dm2 + d2 * ((T)2 * d2 + dm);
+    if (n * bd < bn * d) {
+      bn = n;
+      bd = d;
+    }
+  }
+  return ddiv(bn, bd);
+}
+
+template <typename T, typename S, int NV>
+__global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S> A) {
+  const KinGeom &G = A.g;
+  const int nc = G.nc, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int SL = stage_state_len<S, NV>();
+  constexpr int CL = NV == 2 ? NST_RYKOV : 16;
+  // work arrays of this CTA: f^n, limited gradient, residual, increment [cell][q][VB];
+  // diagonal and M_t of W^n [cell][VB]
+  T *fc = reinterpret_cast<T *>(A.gscratch + (size_t)blockIdx.x * A.gstride);
+  T *gs = fc + (size_t)nc * NV * VB;
+  T *rs = gs + (size_t)nc * NV * 3 * VB;
+  T *dfs = rs + (size_t)nc * NV * VB;
+  T *ds = dfs + (size_t)nc * NV * VB;
+  T *ms = ds + (size_t)nc * VB;
+  auto FC = [&](int c, int q) -> T & { return fc[((size_t)c * NV + q) * VB + lane]; };
+  auto GS = [&](int c, int q, int k) -> T & { return gs[(((size_t)c * NV + q) * 3 + k) * VB + lane]; };
+  for (int b = blockIdx.x; b < A.nblocks; b += gridDim.x) {
+    const int oct = A.boct[b];
+    const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
+    const T x = vp[0], y = vp[1], z = vp[2], wv = vp[3];
+    const T e2 = (T)0.5 * (x * x + y * y + z * z);
+    S *F[NV];
+    F[0] = A.f + (size_t)b * nc * VB;
+    if constexpr (NV == 2) F[NV - 1] = A.f1 + (size_t)b * nc * VB;
+    // f^n of every cell (Eq. updatef applied on load)
+    for (int c = warp; c < nc; c += nw) {
+      T st[SL], stored[NV], f[NV];
+      load_state<SL>(state_of(A.st, c), st);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(F[q] + (size_t)c * VB + lane);
+      corrected_all<T, S, NV>(stored, st, x, y, z, f);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) FC(c, q) = f[q];
+    }
+    __syncthreads();
+    // limited least-squares gradient
+    for (int c = warp; c < nc; c += nw) {
+      const GenCell<T> &g = A.gen[c];
+      int nb[6];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) nb[s] = __ldg(A.gnb + 6 * c + s);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const T fi = FC(c, q);
+        T gr[3] = {(T)0, (T)0, (T)0}, fmax = fi, fmin = fi;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+          if (nb[s] < 0) continue;
+          const T fj = FC(nb[s], q), d = fj - fi;
+          gr[0] += g.f[s].w[0] * d;
+          gr[1] += g.f[s].w[1] * d;
+          gr[2] += g.f[s].w[2] * d;
+          fmax = fmax > fj ? fmax : fj;
+          fmin = fmin < fj ? fmin : fj;
+        }
+        const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) GS(c, q, k) = phi * gr[k];
+      }
+    }
+    __syncthreads();
+    // residual r = (g - f)/tau - (1/V) sum_faces (xi . S) f_face and the implicit diagonal
+    for (int c = warp; c < nc; c += nw) {
+      const GenCell<T> &g = A.gen[c];
+      T st[CL];
+      load_state<CL>(state_of(A.st, c), st);
+      const T cx = x - st[0], cy = y - st[1], cz = z - st[2];
+      T mw, gq[NV], fi[NV], acc[NV];
+      reference<T, NV>(st, cx, cy, cz, cx * cx + cy * cy + cz * cz, mw, gq);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        fi[q] = FC(c, q);
+        acc[q] = (gq[q] - fi[q]) * st[11];
+      }
+      T D = st[15];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        const int nb = __ldg(A.gnb + 6 * c + s);
+        if (nb == NB_ABSENT || nb == NB_AXIS) continue;
+        const GenFace<T> &fa = g.f[s];
+        const T sn = dot_xi(fa.S, x, y, z), k = sn * g.invV;
+        T e[NV];
+        if (sn > (T)0) {
+          D += k;
+#pragma unroll
+          for (int q = 0; q < NV; ++q)
+            e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2];
+        } else if (sn < (T)0) {
+          if (nb >= 0) {
+            const GenFace<T> &fb = A.gen[nb].f[s ^ 1];
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+              e[q] = FC(nb, q) + GS(nb, q, 0) * fb.r[0] + GS(nb, q, 1) * fb.r[1] + GS(nb, q, 2) * fb.r[2];
+          } else if (nb == NB_WALL || A.gin[6 * c + s]) {
+            // the wall's re-emission rho_w M_w, or the free stream entering (f1: (d_r T / 4) M)
+            const double *uT = A.wall_uT + 4 * s;
+            const T M = wall_maxwellian<T>(uT, x, y, z) * (nb == NB_WALL ? (T)A.rho_w[__ldg(A.gwid + 6 * c + s)] : (T)1);
+            e[0] = M;
+            if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
+          } else {
+            // far field where the free stream leaves: the cell's own face value
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+              e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2];
+          }
+        } else {
+          continue;
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] -= k * e[q];
+      }
+#pragma unroll
+      for (int q = 0; q < NV; ++q) rs[((size_t)c * NV + q) * VB + lane] = acc[q];
+      ds[(size_t)c * VB + lane] = D;
+      ms[(size_t)c * VB + lane] = mw;
+    }
+    // point-implicit passes over the colours of this octant
+    for (int c = threadIdx.x; c < nc * NV * VB; c += blockDim.x) dfs[c] = (T)0;
+    __syncthreads();
+    const int4 *natcell = A.natcell + (size_t)oct * nc;
+    for (int pass = 0; pass < A.n_sweeps; ++pass) {
+      for (int col = 0; col < G.ncol; ++col) {
+        const int e0 = A.col_off[col], e1 = A.col_off[col + 1];
+        for (int e = e0 + warp; e < e1; e += nw) {
+          const int c = __ldg(&natcell[e].x);
+          const GenCell<T> &g = A.gen[c];
+          T acc[NV];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) acc[q] = rs[((size_t)c * NV + q) * VB + lane];
+#pragma unroll
+          for (int s = 0; s < 6; ++s) {
+            const int nb = __ldg(A.gnb + 6 * c + s);
+            if (nb < 0) continue;  // boundary increments are lagged (zero)
+            const T sn = dot_xi(g.f[s].S, x, y, z);
+            if (sn < (T)0) {
+#pragma unroll
+              for (int q = 0; q < NV; ++q) acc[q] += -sn * g.invV * dfs[((size_t)nb * NV + q) * VB + lane];
+            }
+          }
+          const T D = ds[(size_t)c * VB + lane];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) dfs[((size_t)c * NV + q) * VB + lane] = ddiv(acc[q], D);
+        }
+        __syncthreads();
+      }
+    }
+    // f^{n+1/2} = f^n + df (stored relative to M_t of W^n for FP32 / BF16) and the outward flux
+    // moments of the wall faces, per unit area
+    for (int c = warp; c < nc; c += nw) {
+      const GenCell<T> &g = A.gen[c];
+      T fi[NV], df[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        fi[q] = FC(c, q);
+        df[q] = dfs[((size_t)c * NV + q) * VB + lane];
+      }
+      if constexpr (StoredRelative<S>::value) {
+        const T mw = ms[(size_t)c * VB + lane];
+        const T r1 = NV == 2 ? state_of(A.st, c)[29] : (T)0;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) Fio<T, S>::st(F[q] + (size_t)c * VB + lane, fi[q] + df[q] - (q == 0 ? mw : r1 * mw));
+      } else {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) Fio<T, S>::st(F[q] + (size_t)c * VB + lane, fi[q] + df[q]);
+      }
+      for (int s = 0; s < 6; ++s) {
+        const int wid = __ldg(A.gwid + 6 * c + s);
+        if (wid < 0) continue;
+        const GenFace<T> &fa = g.f[s];
+        const T sn = dot_xi(fa.S, x, y, z);
+        T e[NV];
+        if (sn > (T)0) {
+#pragma unroll
+          for (int q = 0; q < NV; ++q)
+            e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2] + df[q];
+        } else {
+          const double *uT = A.wall_uT + 4 * s;
+          const T M = sn < (T)0 ? wall_maxwellian<T>(uT, x, y, z) * (T)A.rho_w[wid] : (T)0;
+          e[0] = M;
+          if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
+        }
+        const T fl = wv * sn * fa.invA * e[0];
+        const T e1 = NV == 2 ? wv * sn * fa.invA * e[NV - 1] : (T)0;
+        const T m0 = warp_sum(fl), m1 = warp_sum(fl * x), m2 = warp_sum(fl * y), m3 = warp_sum(fl * z);
+        const T m4 = warp_sum(fl * e2 + e1), m5 = NV == 2 ? warp_sum(e1) : (T)0;
+        if (lane == 0) {
+          T *W = A.wpart + ((size_t)b * A.nwall + wid) * NWF;
+          W[0] = m0;
+          W[1] = m1;
+          W[2] = m2;
+          W[3] = m3;
+          W[4] = m4;
+          W[5] = m5;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Wall pre-pass on general meshes: rho_w of each wall face balances the mass flux of the
+// molecules reaching it (the wall cell's limited reconstruction of f^n) against the re-emitted
+// flux of M(u_w, T_w) through the face.  One CTA per wall face; warps over velocity blocks,
+// FP64 sums in a fixed order.
+template <typename T, typename S, int NV>
+__global__ void __launch_bounds__(256) wall_prepass_general_kernel(const KinArgs<T, S> A, const int *wall_cell,
+                                                                  const int *wall_side, double *rho_w) {
+  __shared__ double red[2][8];
+  const int w = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int c = wall_cell[w], side = wall_side[w], nc = A.g.nc;
+  constexpr int SL = stage_state_len<S, NV>();
+  const GenCell<T> &g = A.gen[c];
+  int nb[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) nb[s] = __ldg(A.gnb + 6 * c + s);
+  const GenFace<T> &fa = g.f[side];
+  const double *uT = A.wall_uT + 4 * side;
+  double num = 0.0, den = 0.0;
+  for (int b = warp; b < A.nblocks; b += nw) {
+    const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
+    const T x = vp[0], y = vp[1], z = vp[2], wv = vp[3];
+    const T sn = dot_xi(fa.S, x, y, z);
+    if (sn > (T)0) {
+      auto fn = [&](int cell) {
+        T st[SL], stored[NV], f[NV];
+        load_state<SL>(state_of(A.st, cell), st);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld((q == 0 ? A.f : A.f1) + ((size_t)b * nc + cell) * VB + lane);
+        corrected_all<T, S, NV>(stored, st, x, y, z, f);
+        return f[0];
+      };
+      const T fi = fn(c);
+      T gr[3] = {(T)0, (T)0, (T)0}, fmax = fi, fmin = fi;
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        if (nb[s] < 0) continue;
+        const T fj = fn(nb[s]), d = fj - fi;
+        gr[0] += g.f[s].w[0] * d;
+        gr[1] += g.f[s].w[1] * d;
+        gr[2] += g.f[s].w[2] * d;
+        fmax = fmax > fj ? fmax : fj;
+        fmin = fmin < fj ? fmin : fj;
+      }
+      const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
+      const T ff = fi + (phi * gr[0]) * fa.r[0] + (phi * gr[1]) * fa.r[1] + (phi * gr[2]) * fa.r[2];
+      num += (double)(wv * sn * ff);
+    } else if (sn < (T)0) {
+      den += (double)(wv * -sn * wall_maxwellian<T>(uT, x, y, z));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = num;
+    red[1][warp] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double n = 0.0, d = 0.0;
+    for (int k = 0; k < nw; ++k) {
+      n += red[0][k];
+      d += red[1][k];
+    }
+    rho_w[w] = n / d;
+  }
+}
+
+template <typename T, typename S>
+size_t kinetic_general_stride(int nc, int nvdf) {
+  return (((size_t)nc * VB * (6 * nvdf + 2)) * sizeof(T) + 255) & ~(size_t)255;
+}
+
+template <typename T, typename S>
+cudaError_t kinetic_general_shape(int nvdf, int *ctas_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      ctas_per_sm, nvdf == 2 ? kinetic_general_kernel<T, S, 2> : kinetic_general_kernel<T, S, 1>, 256, 0);
+}
+
+template <typename T, typename S>
+cudaError_t launch_kinetic_general(const KinArgs<T, S> &a, int grid, cudaStream_t s) {
+  if (a.nvdf == 2)
+    kinetic_general_kernel<T, S, 2><<<grid, 256, 0, s>>>(a);
+  else
+    kinetic_general_kernel<T, S, 1><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, typename S>
+cudaError_t launch_wall_prepass_general(const KinArgs<T, S> &a, const int *wall_cell, const int *wall_side, int nwall,
+                                        double *rho_w, cudaStream_t s) {
+  if (nwall == 0) return cudaSuccess;
+  if (a.nvdf == 2)
+    wall_prepass_general_kernel<T, S, 2><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, rho_w);
+  else
+    wall_prepass_general_kernel<T, S, 1><<<nwall, 256, 0, s>>>(a, wall_cell, wall_side, rho_w);
+  return cudaGetLastError();
+}
+
 #define GSIS_INST(T, S)                                                                                         \
   template cudaError_t launch_kinetic<T, S>(const KinArgs<T, S> &, int, int, size_t, cudaStream_t);             \
   template cudaError_t kinetic_shape<T, S>(const KinGeom &, int, bool, int, size_t, int *, int *);                                       \
@@ -1001,7 +1342,12 @@ cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon
   template cudaError_t launch_export_f<T, S>(const KinArgs<T, S> &, int, const int *, int, int, double *,       \
                                              cudaStream_t);                                                      \
   template cudaError_t launch_import_f<T, S>(const KinArgs<T, S> &, int, const int *, int, int, const double *, \
-                                             cudaStream_t);
+                                             cudaStream_t);                                                      \
+  template cudaError_t launch_kinetic_general<T, S>(const KinArgs<T, S> &, int, cudaStream_t);                   \
+  template cudaError_t kinetic_general_shape<T, S>(int, int *);                                                  \
+  template size_t kinetic_general_stride<T, S>(int, int);                                                        \
+  template cudaError_t launch_wall_prepass_general<T, S>(const KinArgs<T, S> &, const int *, const int *, int,   \
+                                                         double *, cudaStream_t);
 GSIS_INST(float, float)
 GSIS_INST(double, double)
 GSIS_INST(float, __nv_bfloat16)

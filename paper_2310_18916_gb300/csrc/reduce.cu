@@ -42,9 +42,11 @@ __global__ void reduce_moments_kernel(const double *mp, int nchunks, int nc, int
 
 // Outward kinetic wall flux per unit area: the half moving towards the wall from the wall cells'
 // block partials (blocks whose octant moves towards this wall), the re-emitted half rho_w Zw.
+// General meshes (general = 1): every block's partial already holds both halves along the
+// face's outward normal.
 template <typename T>
 __global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nblocks, int nwall, const int *wall_side,
-                                   const double *rho_w, const double *Zw, int emit, double *wf) {
+                                   const double *rho_w, const double *Zw, int emit, int general, double *wf) {
   // one block per wall face, warp m < NWF for moment m: lane l sums the blocks l, l + 32, ... in
   // order, then a fixed butterfly over the lanes
   const int w = blockIdx.x, m = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -54,12 +56,16 @@ __global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nbloc
   double out = 0.0;
   for (int b = lane; b < nblocks; b += 32) {
     const bool neg = (boct[b] >> a) & 1;
-    if (neg == plus) continue;  // this block's velocities move away from the wall
+    if (!general && neg == plus) continue;  // this block's velocities move away from the wall
     out += (double)wpart[((size_t)b * nwall + w) * NWF + m];
   }
   for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
   if (lane == 0) {
     // the re-emitted half once per solve: by one shard of a velocity-sharded solve
+    if (general) {
+      wf[(size_t)w * 6 + m] = out;
+      return;
+    }
     const double tot = out + (emit ? rho_w[w] * Zw[6 * side + m] : 0.0);
     wf[(size_t)w * 6 + m] = plus ? tot : -tot;
   }
@@ -68,8 +74,8 @@ __global__ void reduce_wall_kernel(const T *wpart, const int8_t *boct, int nbloc
 template <typename T>
 cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpart, const int8_t *boct, int nblocks,
                           const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
-                          const double *rho_w, const double *Zw, bool emit, const double *vol, const double *st64,
-                          double *mom, double *K, double *wf, cudaStream_t s) {
+                          const double *rho_w, const double *Zw, bool emit, bool general, const double *vol,
+                          const double *st64, double *mom, double *K, double *wf, cudaStream_t s) {
   (void)wall_cell;
   const int np = moment_len(nvdf);
   const size_t n = (size_t)g.nc * np;
@@ -78,16 +84,17 @@ cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpar
   reduce_moments_kernel<<<grid, 256, 0, s>>>(mp, nchunks, g.nc, np, vol, st64, mom, K);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nwall == 0 || wpart == nullptr) return e;
-  reduce_wall_kernel<T><<<nwall, 32 * NWF, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw, emit ? 1 : 0, wf);
+  reduce_wall_kernel<T><<<nwall, 32 * NWF, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw, emit ? 1 : 0,
+                                                   general ? 1 : 0, wf);
   return cudaGetLastError();
 }
 template cudaError_t launch_reduce<float>(const double *, int, int, const float *, const int8_t *, int, const KinGeom &,
-                                          const int *, const int *, int, const double *, const double *, bool,
+                                          const int *, const int *, int, const double *, const double *, bool, bool,
                                           const double *, const double *, double *, double *, double *, cudaStream_t);
 template cudaError_t launch_reduce<double>(const double *, int, int, const double *, const int8_t *, int,
                                            const KinGeom &, const int *, const int *, int, const double *,
-                                           const double *, bool, const double *, const double *, double *, double *,
-                                           double *, cudaStream_t);
+                                           const double *, bool, bool, const double *, const double *, double *,
+                                           double *, double *, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------------
 // Raw moments about the state velocity un -> rho, u, Tt, sigma, q about the mean velocity.
@@ -379,7 +386,8 @@ __global__ void wall_loads_kernel(WallLoadArgs a) {
     if (!((a.mask >> side) & 1u)) continue;
     const int c = a.wall_cell[w], ax = side / 2;
     const int nat[3] = {c % a.n[0], (c / a.n[0]) % a.n[1], c / (a.n[0] * a.n[1])};
-    const double area = a.ax[0][nat[0]].h * a.ax[1][nat[1]].h * a.ax[2][nat[2]].h * a.ax[ax][nat[ax]].invh;
+    const double area = a.area ? a.area[w]
+                               : a.ax[0][nat[0]].h * a.ax[1][nat[1]].h * a.ax[2][nat[2]].h * a.ax[ax][nat[ax]].invh;
     for (int k = 0; k < 4; ++k) acc[k] += a.wf[(size_t)w * 6 + 1 + k] * area;
   }
   for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = acc[k];

@@ -1,0 +1,120 @@
+"""General (curvilinear) structured meshes on the GPU against the FP64 oracle: the kinetic
+iteration on a cylinder O-grid (wall inside, far field outside, wrapped azimuth) and a sphere
+O-grid (pole sides of zero area), with several colour passes per step; FP64 element by element,
+FP32 within its rounding; the Rykov model; wall fluxes and loads; the collisionless reservoir
+slab against its exact discrete solution."""
+import numpy as np
+import pytest
+
+from gpu_common import scaled_close
+from oracle.oracle import Oracle
+from paper_2310_18916_gb300 import gsis
+from paper_2310_18916_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pair(p, precision, steps, n_sweeps, W0=None, f0=None):
+    g = gsis.Solver(p, precision=precision, mode="dvm", init_W=W0, kinetic_presteps=0, n_sweeps=n_sweeps)
+    o = Oracle(p, W0=W0, mode=1, n_sweeps=n_sweeps)
+    if f0 is not None:
+        g.set_f(f0)
+        o.set_f(f0)
+    out = []
+    for _ in range(steps):
+        g.step()
+        o.step()
+        out.append((g.W(), o.W()))
+    return g, o, out
+
+
+def wall_match(g, o, rel):
+    cg, sg, rg, flg = g.wall()
+    co, so, ro, flo = o.wall()
+    assert np.array_equal(cg, co) and np.array_equal(sg, so)
+    np.testing.assert_allclose(rg, ro, rtol=rel)
+    scaled_close(flg, flo, rel * 10, "wall flux")
+
+
+@pytest.mark.parametrize("n_sweeps", [1, 3])
+def test_cylinder_ogrid_fp64(n_sweeps):
+    p = wl.cylinder(n_r=6, n_theta=12, nv=12, R=0.5, R_out=3.0, first=0.15, Ma=0.5, Kn=0.2, T_w=1.5)
+    W = wl.perturbed_state(p, seed=41, amp=0.04)
+    f0, _ = wl.random_vdf(p, seed=42, amp=0.2, W=W)
+    g, o, out = run_pair(p, "f64", 3, n_sweeps, W0=W, f0=f0)
+    for it, (Wg, Wo) in enumerate(out):
+        scaled_close(Wg, Wo, 1e-11, f"cylinder W, step {it}")
+    fg, fo = g.get_f(), o.get_f()[0]
+    assert np.abs(fg - fo).max() <= 1e-11 * np.abs(fo).max()
+    wall_match(g, o, 1e-11)
+
+
+def test_sphere_ogrid_fp64():
+    p = wl.sphere(n_r=4, n_pol=5, n_az=8, nv=10, R=0.5, R_out=3.0, Ma=0.6, Kn=0.3)
+    W = wl.perturbed_state(p, seed=43, amp=0.04)
+    g, o, out = run_pair(p, "f64", 3, 2, W0=W)
+    for it, (Wg, Wo) in enumerate(out):
+        scaled_close(Wg, Wo, 1e-11, f"sphere W, step {it}")
+    fg, fo = g.get_f(), o.get_f()[0]
+    assert np.abs(fg - fo).max() <= 1e-11 * np.abs(fo).max()
+    wall_match(g, o, 1e-11)
+
+
+def test_cylinder_rykov_fp64():
+    p = wl.as_rykov(wl.cylinder(n_r=5, n_theta=10, nv=10, R=0.5, R_out=3.0, Ma=0.5, Kn=0.2, T_w=1.3))
+    W = wl.perturbed_state(p, seed=44, amp=0.04)
+    g, o, out = run_pair(p, "f64", 2, 2, W0=W)
+    for it, (Wg, Wo) in enumerate(out):
+        scaled_close(Wg, Wo, 1e-11, f"Rykov cylinder W, step {it}")
+    fg, fo = g.get_f(both=True), o.get_f()
+    assert np.abs(fg[0] - fo[0]).max() <= 1e-11 * np.abs(fo[0]).max()
+    assert np.abs(fg[1] - fo[1]).max() <= 1e-11 * np.abs(fo[1]).max()
+
+
+@pytest.mark.parametrize("precision,rel", [("f32", 2e-5), ("bf16", 2e-3)])
+def test_cylinder_ogrid_reduced_precision(precision, rel):
+    p = wl.cylinder(n_r=6, n_theta=12, nv=16, R=0.5, R_out=3.0, Ma=0.5, Kn=0.2)
+    g, o, out = run_pair(p, precision, 3, 2)
+    for it, (Wg, Wo) in enumerate(out):
+        scaled_close(Wg, Wo, rel, f"{precision} cylinder W, step {it}")
+
+
+def test_cylinder_wall_loads_match_oracle():
+    """a10 on a curved body: force and drag coefficient on the cylinder from the wall fluxes."""
+    p = wl.cylinder(n_r=6, n_theta=16, nv=12, R=0.5, R_out=3.0, Ma=0.5, Kn=0.3)
+    g, o, _ = run_pair(p, "f64", 3, 2)
+    _, side, _, fl = o.wall()
+    U = p.wall_u[1][0]
+    F = fl[side == 0, 1:4].sum(axis=0)
+    out = g.wall_loads([0], (1.0, 0.0, 0.0), 1.0, U, 1.0)
+    np.testing.assert_allclose(out[:3], F, rtol=1e-10, atol=1e-12 * np.abs(F).max())
+    assert out[4] == pytest.approx(F[0] / (0.5 * U * U), rel=1e-10)
+
+
+def test_reservoir_wall_exact_on_gpu():
+    U = (0.0, 0.3, 0.0)
+    p = wl.reservoir_wall(n_cells=8, nv=16, U=U, T_inf=1.0, T_w=2.0, Kn=1e9)
+    W0 = np.tile([0.5, 0.0, 0.0, 0.0, 1.5, 1.5], (p.ncells, 1))
+    g = gsis.Solver(p, precision="f64", mode="dvm", init_W=W0, kinetic_presteps=0)
+    for _ in range(4):
+        g.step()
+    f = g.get_f()
+    X, Y, Z = np.meshgrid(p.vx, p.vy, p.vz, indexing="ij")
+
+    def M(rho, u, T):
+        return (rho * (np.pi * T) ** -1.5 * np.exp(-((X - u[0]) ** 2 + (Y - u[1]) ** 2 + (Z - u[2]) ** 2) / T)).transpose(2, 1, 0).ravel()
+
+    vx = X.transpose(2, 1, 0).ravel()
+    w = np.multiply.outer(np.multiply.outer(p.wx, p.wy), p.wz).transpose(2, 1, 0).ravel()
+    Minf, Mw = M(1.0, U, 1.0), M(1.0, (0, 0, 0), 2.0)
+    up, dn = vx > 0, vx < 0
+    rho_w = (w[up] * vx[up] * Minf[up]).sum() / (w[dn] * -vx[dn] * Mw[dn]).sum()
+    exact = np.where(up, Minf, rho_w * Mw)
+    assert np.abs(f - exact[None, :]).max() < 1e-6 * np.abs(exact).max()
+
+
+def test_general_mesh_gsis_mode_is_unsupported():
+    p = wl.cylinder(n_r=4, n_theta=8, nv=8)
+    with pytest.raises(gsis.GsisError) as e:
+        gsis.Solver(p, precision="f32", mode="gsis")
+    assert e.value.code == gsis.GSIS_E_UNSUPPORTED

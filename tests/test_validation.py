@@ -26,11 +26,12 @@ def test_valid_problems_pass():
         assert code(p) == gsis.GSIS_OK, p.name
 
 
-def test_curved_mesh_is_unsupported():
+def test_curved_mesh_runs_the_kinetic_iteration_only():
     p = wl.cavity(n=8, nv=8)
     nodes = p.nodes.copy()
     nodes[..., 0] += 0.01 * nodes[..., 1]  # x depends on J: not rectilinear
     assert code(dataclasses.replace(p, nodes=nodes)) == gsis.GSIS_E_UNSUPPORTED
+    assert code(dataclasses.replace(p, nodes=nodes), mode=gsis.MODE_DVM) == gsis.GSIS_OK
 
 
 def test_non_increasing_nodes_are_rejected():
@@ -43,11 +44,31 @@ def test_non_increasing_nodes_are_rejected():
 def test_boundary_conditions_must_match_the_axis():
     p = wl.cavity(n=8, nv=8)
     bc = list(p.bc)
-    bc[0] = wl.PERIODIC  # periodic axes with several cells are not implemented
+    bc[0] = wl.PERIODIC  # a periodic axis is periodic on both sides
+    assert code(dataclasses.replace(p, bc=bc)) == GSIS_E_INVALID
+    bc[1] = wl.PERIODIC  # a wrapped axis takes the general path: kinetic iteration only
     assert code(dataclasses.replace(p, bc=bc)) == gsis.GSIS_E_UNSUPPORTED
+    assert code(dataclasses.replace(p, bc=bc), mode=gsis.MODE_DVM) == gsis.GSIS_OK
     bc = list(p.bc)
     bc[4] = wl.WALL  # an axis with one cell must be PERIODIC on both sides
     assert code(dataclasses.replace(p, bc=bc)) == GSIS_E_INVALID
+    bc = list(p.bc)
+    bc[1] = 7  # not a boundary condition
+    assert code(dataclasses.replace(p, bc=bc), mode=gsis.MODE_DVM) == GSIS_E_INVALID
+
+
+def test_general_meshes_run_the_kinetic_iteration():
+    """O-grids (far field, pole and wrapped sides) are accepted in DVM mode on one device, with
+    several colour passes; the synthetic solve and sharding on them are not built."""
+    for p in (wl.cylinder(n_r=6, n_theta=12, nv=8), wl.sphere(n_r=4, n_pol=4, n_az=6, nv=8),
+              wl.reservoir_wall(n_cells=6, nv=8)):
+        assert code(p, mode=gsis.MODE_DVM, n_sweeps=3) == gsis.GSIS_OK, p.name
+        assert code(p) == gsis.GSIS_E_UNSUPPORTED, p.name
+        assert code(p, mode=gsis.MODE_DVM, n_sweeps=0) == GSIS_E_INVALID, p.name
+    p = wl.cylinder(n_r=6, n_theta=12, nv=8)
+    nodes = p.nodes.copy()
+    nodes[:, :, 0, :] = nodes[:, :, 1, :]  # the first ring of cells collapses to zero volume
+    assert code(dataclasses.replace(p, nodes=nodes), mode=gsis.MODE_DVM) == GSIS_E_INVALID
 
 
 def test_inactive_axis_before_an_active_one_is_unsupported():
