@@ -118,7 +118,9 @@ typedef struct {
   int macro_sweeps;     /* red-black LU-SGS passes per inner step (default 4, Algorithm 2) */
   double macro_cfl;     /* pseudo-time CFL of the synthetic solve (default 100) */
   double macro_tol;     /* inner early exit on the relative increment (default 1e-10) */
-  double kin_inv_dt;    /* 1/dt of the kinetic delta form (default 0: steady; only 0 is supported) */
+  double kin_inv_dt;    /* 1/dt of the kinetic delta form (default 0: steady).  A pseudo-time step
+                           (> 0) damps the kinetic iteration after an impulsive start; only
+                           GSIS_MODE_DVM takes it (the synthetic solve needs a steady step). */
   double venkat_K;      /* Venkatakrishnan constant, eps^2 = (K V^(1/3))^3 (default 1) */
   int kinetic_presteps; /* plain kinetic steps before the GSIS loop (default 10, Algorithm 1) */
   const double *init_W; /* optional host array, per cell rho, ux, uy, uz, Tt, Tr; f0 = Maxwellian.

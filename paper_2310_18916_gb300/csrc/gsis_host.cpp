@@ -531,7 +531,11 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     return GSIS_E_INVALID;
   }
   if (g->model != GSIS_SHAKHOV && g->model != GSIS_RYKOV) { why = "bad model"; return GSIS_E_INVALID; }
-  if (o->kin_inv_dt != 0.0) { why = "the GPU kinetic step is steady (kin_inv_dt = 0)"; return GSIS_E_UNSUPPORTED; }
+  if (!(o->kin_inv_dt >= 0.0) || !std::isfinite(o->kin_inv_dt)) { why = "kin_inv_dt must be finite and >= 0"; return GSIS_E_INVALID; }
+  if (o->kin_inv_dt != 0.0 && o->mode == GSIS_MODE_GSIS) {
+    why = "the synthetic solve takes the face fluxes of a steady kinetic step: kin_inv_dt must be 0 in GSIS mode";
+    return GSIS_E_UNSUPPORTED;
+  }
   const bool general = needs_general(m);
   if (!general && o->n_sweeps != 1) {
     why = "rectilinear colour sweeps are exact in one pass: n_sweeps must be 1";

@@ -79,6 +79,17 @@ def test_cylinder_ogrid_reduced_precision(precision, rel):
         scaled_close(Wg, Wo, rel, f"{precision} cylinder W, step {it}")
 
 
+def test_cylinder_pseudo_time_step_fp64():
+    """kin_inv_dt > 0 (the delta form with 1/dt on the diagonal) against the oracle."""
+    p = wl.cylinder(n_r=6, n_theta=12, nv=12, R=0.5, R_out=3.0, Ma=1.5, Kn=0.1)
+    g = gsis.Solver(p, precision="f64", mode="dvm", kinetic_presteps=0, n_sweeps=2, kin_inv_dt=5.0)
+    o = Oracle(p, mode=1, n_sweeps=2, kin_inv_dt=5.0)
+    for it in range(3):
+        g.step()
+        o.step()
+        scaled_close(g.W(), o.W(), 1e-11, f"cylinder W with 1/dt = 5, step {it}")
+
+
 def test_cylinder_wall_loads_match_oracle():
     """a10 on a curved body: force and drag coefficient on the cylinder from the wall fluxes."""
     p = wl.cylinder(n_r=6, n_theta=16, nv=12, R=0.5, R_out=3.0, Ma=0.5, Kn=0.3)

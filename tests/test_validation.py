@@ -104,3 +104,10 @@ def test_kinetic_ring_placement():
     for p, prec in ((wl.box3d(ni=20, nj=20, nk=20, nv=8), "f32"), (wl.box3d(ni=16, nj=16, nk=16, nv=8), "f64")):
         assert gsis.footprint_bytes(p, prec) == gsis.footprint_bytes(p, prec, kinetic_ring=1), p.name
     assert code(small, kinetic_ring=2) == GSIS_E_INVALID
+
+
+def test_pseudo_time_step_only_in_the_kinetic_iteration():
+    p = wl.cavity(n=6, nv=8)
+    assert code(p, mode=gsis.MODE_DVM, kin_inv_dt=10.0) == gsis.GSIS_OK
+    assert code(p, kin_inv_dt=10.0) == gsis.GSIS_E_UNSUPPORTED
+    assert code(p, mode=gsis.MODE_DVM, kin_inv_dt=-1.0) == GSIS_E_INVALID
