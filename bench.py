@@ -259,6 +259,127 @@ def run_couette(args):
     return 0
 
 
+# Bodies on general (curvilinear) O-grids: the kinetic iteration (DVM mode) with two colour
+# passes per step and a pseudo-time step (1/dt = 1000: an impulsive Ma-4 start on the sphere
+# keeps a positive density in the wake for the steps timed here), FP32 / BF16 storage.
+BODIES = {
+    # sphere of diameter 1: 32 radial (first 0.0224, ratio 1.1, R_out 5) x 24 polar x 48 azimuthal
+    # cells, Ma 4, Kn 0.05, 48^3 velocities on [-12, 12]^3
+    "sphere": dict(kind="sphere", n=(32, 24, 48), nv=48, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0),
+    # cylinder of diameter 1 in cross flow: 64 radial (first 0.01, R_out 10) x 128 azimuthal cells,
+    # Ma 2, Kn 0.05, 40^3 velocities on [-9, 9]^3
+    "cylinder": dict(kind="cylinder", n=(64, 1, 128), nv=40, vmax=9.0, Ma=2.0, Kn=0.05, first=0.01, R_out=10.0),
+}
+BODY_SWEEPS, BODY_INV_DT = 2, 1000.0
+
+
+def body_problem(name):
+    from paper_2310_18916_gb300 import workloads as wl
+
+    b = BODIES[name]
+    if b["kind"] == "sphere":
+        return wl.sphere(n_r=b["n"][0], n_pol=b["n"][1], n_az=b["n"][2], nv=b["nv"], R=0.5, R_out=b["R_out"],
+                         first=b["first"], Ma=b["Ma"], Kn=b["Kn"], vmax=b["vmax"])
+    return wl.cylinder(n_r=b["n"][0], n_theta=b["n"][2], nv=b["nv"], R=0.5, R_out=b["R_out"], first=b["first"],
+                       Ma=b["Ma"], Kn=b["Kn"], vmax=b["vmax"])
+
+
+def run_body(args):
+    """Kinetic iteration on a body-fitted O-grid (the general-mesh path): phase-space updates/s,
+    the general kinetic kernel's HBM roofline, the end-to-end figure through the public API and
+    the oracle's CPU baseline on a bounded sample (fewer velocities)."""
+    import numpy as np
+    import torch
+
+    from paper_2310_18916_gb300 import gsis
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    p = body_problem(args.body)
+    pts = p.ncells * p.nvel
+    kw = dict(precision=args.precision, mode="dvm", n_sweeps=BODY_SWEEPS, kin_inv_dt=BODY_INV_DT)
+    s = gsis.Solver(p, kinetic_presteps=0, **kw)
+    for _ in range(args.warmup):
+        s.step()
+    s.profile(True, reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    phase, nsteps, launches = s.profile(False)
+    eps = float(s.residual()[3])
+    W = s.W()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    s2 = gsis.Solver(p, kinetic_presteps=0, **kw)
+    for _ in range(args.steps):
+        s2.step()
+        W2 = s2.W()
+    s2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    del s2
+    peak, peak_kind, _ = measured_peaks()
+    sbytes = {"f32": 4, "f64": 8, "bf16": 2}[args.precision]
+    kin_ms = phase[1] / max(nsteps, 1)
+    ms = ms_total / args.steps
+    line = {
+        "metric": f"phase-space updates/s (kinetic iteration, {args.body} O-grid)", "value": pts * args.steps / (ms_total / 1e3),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
+        "config": {"workload": f"{p.name}: {BODIES[args.body]}", "precision": f"{args.precision} VDF",
+                   "cells": p.ncells, "velocities": p.nvel, "points": pts, "n_sweeps": BODY_SWEEPS,
+                   "kin_inv_dt": BODY_INV_DT, "parallelism": "1 GPU",
+                   "l2": f"inputs larger than L2 (VDF {pts * sbytes / 1e9:.2f} GB)", "eps_last": eps,
+                   "rho_range": [float(W[:, 0].min()), float(W[:, 0].max())]},
+        "phase_ms_per_step": {k: v / max(nsteps, 1) for k, v in zip(
+            ("wall_prepass", "kinetic", "reduce_moments", "synthetic_fp64", "residual_state"), phase)},
+        "roofline": {"kernel": "kinetic_general_kernel", "bound": "hbm",
+                     "achieved": 2 * sbytes * pts / (kin_ms / 1e3) / 1e9, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": 2 * sbytes * pts / (kin_ms / 1e3) / 1e9 / peak,
+                     "traffic": None, "algorithmic_bytes_per_launch": 2 * sbytes * pts, "launch_ms": kin_ms,
+                     "share_of_step": kin_ms / ms},
+        "e2e": {"value": pts * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": (p.nodes.nbytes + 6 * p.vx.nbytes + p.W0.nbytes) / args.steps,
+                "d2h_bytes_per_step": W2.nbytes, "seconds": e2e_s,
+                "includes": "create from host inputs, steps, per-step state read, destroy"},
+        "gpu_launches": launches / max(nsteps, 1) * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = body_oracle_sample(args.body)
+    print(json.dumps(line))
+    return 0
+
+
+def body_oracle_sample(name):
+    """The oracle's kinetic iteration on the same mesh with 12^3 velocities (one step, all host
+    cores), scaled to updates/s."""
+    from oracle.oracle import Oracle
+
+    p = body_problem(name)
+    b = BODIES[name]
+    from paper_2310_18916_gb300 import workloads as wl
+    v, w = wl.midpoint_grid(12, -b["vmax"], b["vmax"])
+    p.vx, p.vy, p.vz, p.wx, p.wy, p.wz = v, v.copy(), v.copy(), w, w.copy(), w.copy()
+    cores = os.cpu_count() or 1
+    o = Oracle(p, mode=1, n_sweeps=BODY_SWEEPS, kin_inv_dt=BODY_INV_DT, nthreads=cores)
+    t0 = time.perf_counter()
+    o.step()
+    dt = time.perf_counter() - t0
+    return {"value": p.ncells * p.nvel / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one kinetic-iteration step of the same mesh with 12^3 velocities ({dt:.1f} s)"}
+
+
 def run_serve(args):
     """Configuration 5 scaled to minutes: a seeded Poisson stream of steady cavity solves (sizes,
     velocity counts and arrival gaps scaled down, Kn log-uniform in [1e-3, 1], lid Mach number in
@@ -345,6 +466,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="instead of the throughput line: the serving stream")
     ap.add_argument("--couette", action="store_true",
                     help="instead of the throughput line: Couette flow to eps < 1e-8 in FP64, GPU vs oracle")
+    ap.add_argument("--body", choices=sorted(BODIES),
+                    help="instead of the cavity line: the kinetic iteration on a body-fitted O-grid")
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: one solve sharded over the ranks' velocities (strong scaling) "
                          "instead of a replica per rank")
@@ -361,6 +484,8 @@ def main():
         return run_serve(args)
     if args.couette:
         return run_couette(args)
+    if args.body:
+        return run_body(args)
 
     import numpy as np
     import torch

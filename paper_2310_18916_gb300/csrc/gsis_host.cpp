@@ -958,8 +958,9 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
 template <typename T, typename S>
 static int plan_kinetic(gsis_solver *s) {
   if (s->general) {
-    // persistent grid of 8-warp CTAs over the velocity blocks, at most 2 per SM: each holds
-    // whole-mesh work arrays for its block of 32 velocities
+    // persistent grid of 8-warp CTAs over the velocity blocks, as many as the SMs hold (the
+    // kernel is latency-bound) while their whole-mesh work arrays, one set per CTA for its
+    // block of 32 velocities, stay within 32 GB
     s->kin_smem = 0;
     s->kin_warps = 8;
     s->kin_gstride = kinetic_general_stride<T, S>(s->nc, s->nvdf);
@@ -970,7 +971,9 @@ static int plan_kinetic(gsis_solver *s) {
     } else {
       cudaGetLastError();
     }
-    s->kin_grid = std::max(1, std::min(s->nblocks, std::max(1, std::min(occ, 2)) * sms));
+    const size_t budget = (size_t)32 << 30;
+    const int by_mem = (int)std::max<size_t>(1, budget / ((size_t)sms * s->kin_gstride));
+    s->kin_grid = std::max(1, std::min(s->nblocks, std::max(1, std::min(occ, by_mem)) * sms));
     s->kin_scratch_bytes = (size_t)s->kin_grid * s->kin_gstride;
     return GSIS_OK;
   }
