@@ -891,9 +891,13 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
         num[k] += m.dW[6 * i + k] * m.dW[6 * i + k] * s->vol[i];
         den[k] += W[6 * i + k] * W[6 * i + k] * s->vol[i];
       }
-    double delta = 0.0;
+    /* the relative increment of every field that is not identically zero: as for eps, a field
+       whose volume-weighted RMS is below 1e-12 (the z momentum of a 2D flow, rounding noise)
+       has no relative increment to test */
+    double vsum = 0.0, delta = 0.0;
+    for (int i = 0; i < nc; ++i) vsum += s->vol[i];
     for (int k = 0; k < nW; ++k)
-      if (den[k] > 0) {
+      if (den[k] > 1e-24 * vsum) {
         double e = sqrt(num[k] / den[k]);
         if (e > delta) delta = e;
       }

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsis.so")
-SOURCES = ["kinetic.cu", "reduce.cu", "macro.cu", "noalloc.cu", "gsis_host.cpp"]
+SOURCES = ["kinetic.cu", "reduce.cu", "macro.cu", "macro_general.cu", "noalloc.cu", "gsis_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -78,6 +78,13 @@ struct gsis_solver {
   int *d_gnb = nullptr, *d_gwid = nullptr;
   unsigned char *d_gin = nullptr;
   double *d_wall_area = nullptr;
+  std::vector<double> xc64;
+  // general meshes, GSIS mode: FP64 geometry and the synthetic solve's work arrays
+  GenCell<double> *d_gen64 = nullptr;
+  double *d_xc = nullptr, *d_kpart = nullptr;
+  double *g_W = nullptr, *g_pr = nullptr, *g_mu = nullptr, *g_gW = nullptr, *g_phW = nullptr, *g_gP = nullptr;
+  double *g_R = nullptr, *g_D = nullptr, *g_dW = nullptr, *g_F0 = nullptr, *g_part = nullptr;
+  int *g_flag = nullptr;
   int kin_grid = 0;
   size_t kin_scratch_bytes = 0;
   // device
@@ -339,15 +346,61 @@ struct gsis_solver {
     if (rc) return rc;
     launches += nwall > 0;
     mark(1);
-    rc = general ? cuda(launch_kinetic_general<T, S>(kin_args<T, S>(), kin_grid, stream), "kinetic")
-                 : cuda(launch_kinetic<T, S>(kin_args<T, S>(), nblocks, kin_warps, kin_smem, stream), "kinetic");
+    if (general) {
+      KinArgs<T, S> ka = kin_args<T, S>();
+      if (mode == GSIS_MODE_GSIS) {
+        ka.kpart = d_kpart;
+        rc = cuda(cudaMemsetAsync(d_kpart, 0, (size_t)kin_grid * nc * 6 * sizeof(double), stream), "memset");
+        if (rc) return rc;
+      }
+      rc = cuda(launch_kinetic_general<T, S>(ka, kin_grid, stream), "kinetic");
+    } else {
+      rc = cuda(launch_kinetic<T, S>(kin_args<T, S>(), nblocks, kin_warps, kin_smem, stream), "kinetic");
+    }
     if (rc) return rc;
     mark(2);
     rc = reduce_and_finalize<T, S>(true);
     if (rc) return rc;
     launches += 1 + 1 + (nwall > 0) + 2;
     mark(3);
-    if (mode == GSIS_MODE_GSIS) {
+    if (mode == GSIS_MODE_GSIS && general) {
+      // the kinetic face fluxes summed per cell, then the general synthetic solve
+      rc = cuda(launch_sum_kpart(d_kpart, kin_grid, (int)nc, d_K, stream), "kinetic flux sums");
+      if (rc) return rc;
+      MacroGenArgs m{};
+      m.nc = (int)nc;
+      m.nW = gas.model == GSIS_RYKOV ? 6 : 5;
+      m.model = gas.model;
+      m.steps = opt.macro_steps;
+      m.sweeps = opt.macro_sweeps;
+      m.closed = closed;
+      m.ncol0 = ncol0;
+      m.mu0 = Kn / std::sqrt(3.14159265358979323846);
+      m.omega = omega;
+      m.cfl = opt.macro_cfl;
+      m.tol = opt.macro_tol;
+      m.d_r = gas.d_r;
+      m.Z_r = gas.Z_r;
+      for (int k = 0; k < 4; ++k) m.A[k] = gas.A[k];
+      m.mass_ref = mass_ref;
+      m.vsum = vsum;
+      m.gen = d_gen64;
+      m.gnb = d_gnb;
+      m.xc = d_xc;
+      m.vol = d_vol;
+      m.wall_uT = d_wall_uT;
+      m.Mh = d_Mh;
+      m.K = d_K;
+      m.colcells = d_colcells;
+      m.W = g_W; m.pr = g_pr; m.mu = g_mu; m.gW = g_gW; m.phW = g_phW; m.gP = g_gP;
+      m.R = g_R; m.D = g_D; m.dW = g_dW; m.F0 = g_F0; m.part = g_part; m.flag = g_flag;
+      m.Wout = d_Wnew;
+      m.err = d_err;
+      m.iters = d_iters;
+      rc = cuda(run_macro_general(m, stream), "synthetic solve");
+      if (rc) return rc;
+      launches += 2 + opt.macro_steps * (6 + 2 * opt.macro_sweeps);
+    } else if (mode == GSIS_MODE_GSIS) {
       MacroArgs m{};
       m.g = kg;
       for (int d = 0; d < 3; ++d) m.ax[d] = d_ax64[d];
@@ -364,6 +417,7 @@ struct gsis_solver {
       m.Z_r = gas.Z_r;
       for (int k = 0; k < 4; ++k) m.A[k] = gas.A[k];
       m.mass_ref = mass_ref;
+      m.den_floor = 1e-24 * vsum;
       m.closed = closed;
       m.Mh = d_Mh;
       m.K = d_K;
@@ -570,10 +624,6 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
       return GSIS_E_INVALID;
     }
   if (general) {
-    if (o->mode == GSIS_MODE_GSIS) {
-      why = "the synthetic solve is built for rectilinear meshes only: use GSIS_MODE_DVM on general meshes";
-      return GSIS_E_UNSUPPORTED;
-    }
     if (o->shard_count > 1) { why = "velocity sharding is built for rectilinear meshes only"; return GSIS_E_UNSUPPORTED; }
     return GSIS_OK;  // volumes are checked when the geometry is built
   }
@@ -667,7 +717,8 @@ static int build_general(gsis_solver *s, const gsis_mesh *m) {
   s->gwid.assign((size_t)6 * nc, -1);
   s->gin.assign((size_t)6 * nc, 0);
   s->vol.assign(nc, 0.0);
-  std::vector<double> xc((size_t)3 * nc);
+  s->xc64.assign((size_t)3 * nc, 0.0);
+  std::vector<double> &xc = s->xc64;
   s->vsum = 0.0;
   s->nwall = 0;
   s->wall_cell.clear();
@@ -1013,6 +1064,9 @@ static size_t footprint(const gsis_solver *s) {
   b += (size_t)s->nblocks * (s->nwall + 1) * NWF * T;  // wall partials
   b += s->kin_scratch_bytes;                          // kinetic ring or work arrays in global memory
   if (s->general) b += nc * (sizeof(GenCell<double>) + 6 * (2 * sizeof(int) + 1)) + (size_t)s->nwall * 8;
+  if (s->general && s->opt.mode == GSIS_MODE_GSIS)
+    b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36) * 8) +
+         12 * 8 * (size_t)macro_general_parts((int)nc);
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
@@ -1043,6 +1097,23 @@ static int allocate_and_upload(gsis_solver *s) {
     A(s->d_gwid, 6 * nc * sizeof(int));
     A(s->d_gin, 6 * nc);
     A(s->d_wall_area, (size_t)(s->nwall + 1) * sizeof(double));
+    if (s->opt.mode == GSIS_MODE_GSIS) {
+      A(s->d_gen64, nc * sizeof(GenCell<double>));
+      A(s->d_xc, 3 * nc * sizeof(double));
+      A(s->d_kpart, (size_t)s->kin_grid * nc * 6 * sizeof(double));
+      A(s->g_W, 6 * nc * sizeof(double));
+      A(s->g_pr, 6 * nc * sizeof(double));
+      A(s->g_mu, nc * sizeof(double));
+      A(s->g_gW, 18 * nc * sizeof(double));
+      A(s->g_phW, 6 * nc * sizeof(double));
+      A(s->g_gP, 15 * nc * sizeof(double));
+      A(s->g_R, 6 * nc * sizeof(double));
+      A(s->g_D, 6 * nc * sizeof(double));
+      A(s->g_dW, 6 * nc * sizeof(double));
+      A(s->g_F0, 36 * nc * sizeof(double));
+      A(s->g_part, 12 * (size_t)macro_general_parts((int)nc) * sizeof(double));
+      A(s->g_flag, 2 * sizeof(int));
+    }
   }
   A(s->d_K, nc * 6 * sizeof(double));
   A(s->d_stT, nc * NST * sizeof(T));
@@ -1128,6 +1199,8 @@ static int allocate_and_upload(gsis_solver *s) {
     if (!rc) rc = s->upload(s->d_gwid, s->gwid.data(), 6 * nc * sizeof(int));
     if (!rc) rc = s->upload(s->d_gin, s->gin.data(), 6 * nc);
     if (!rc && s->nwall) rc = s->upload(s->d_wall_area, s->wall_area.data(), s->nwall * sizeof(double));
+    if (!rc && s->d_gen64) rc = s->upload(s->d_gen64, s->gen64.data(), nc * sizeof(GenCell<double>));
+    if (!rc && s->d_xc) rc = s->upload(s->d_xc, s->xc64.data(), 3 * nc * sizeof(double));
   }
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_ticket, 0, 4 * sizeof(unsigned), s->stream), "memset");
   if (!rc) rc = s->cuda(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream), "memset");

@@ -119,6 +119,8 @@ struct KinArgs {
   const int *gwid;          // [cell][6] wall-face id, -1 if the side is not a wall
   const unsigned char *gin; // [cell][6] far-field sides: 1 where the free stream enters
   int n_sweeps;             // point-implicit passes over the colours
+  double *kpart;            // [CTA][cell][6] per-CTA sums of the outward kinetic face fluxes
+                            // (area-integrated, over the cell's faces); nullptr: not wanted
 };
 
 // ---- launchers (defined in the .cu files) ----
@@ -150,6 +152,8 @@ template <typename T, typename S>
 cudaError_t kinetic_general_shape(int nvdf, int *ctas_per_sm);
 template <typename T, typename S>
 size_t kinetic_general_stride(int nc, int nvdf);
+// K [cell][6] = sum over the CTAs of kpart (fixed order)
+cudaError_t launch_sum_kpart(const double *kpart, int nparts, int nc, double *K, cudaStream_t s);
 template <typename T, typename S>
 cudaError_t launch_wall_prepass_general(const KinArgs<T, S> &a, const int *wall_cell, const int *wall_side, int nwall,
                                         double *rho_w, cudaStream_t s);
@@ -246,6 +250,7 @@ struct MacroArgs {
   int model, nW, steps, sweeps;
   double d_r, Z_r, A[4];
   double mass_ref;
+  double den_floor;        // 1e-24 x total volume: fields with sum W_k^2 V below it count as zero
   int closed;
   const double *Mh;        // [cell][18] initial state W^{n+1/2}
   const double *K;         // [cell][6] sum over the cell's faces of the outward kinetic flux (area-integrated)
@@ -263,6 +268,27 @@ struct MacroArgs {
   int *err;
   int *iters;              // out
 };
+// The synthetic solve on general meshes (one thread per cell, one launch per phase)
+struct MacroGenArgs {
+  int nc, nW, model, steps, sweeps, closed, ncol0;
+  double mu0, omega, cfl, tol, d_r, Z_r, A[4], mass_ref;
+  double vsum;                 // total volume (fields with sum W_k^2 V <= 1e-24 vsum count as zero)
+  const GenCell<double> *gen;  // [cell] FP64 geometry
+  const int *gnb;              // [cell][6]
+  const double *xc, *vol;      // [cell][3], [cell]
+  const double *wall_uT;       // [6][4]: wall u, T; far field: free-stream u, T
+  const double *Mh;            // [cell][18] W^{n+1/2}
+  const double *K;             // [cell][6] area-integrated outward kinetic flux summed over the faces
+  const int *colcells;         // red cells then black cells
+  // work
+  double *W, *pr, *mu, *gW, *phW, *gP, *R, *D, *dW, *F0, *part;
+  int *flag;                   // [0] early exit fired, [1] inner steps used
+  double *Wout;                // [cell][6] prim W^{n+1}
+  int *err, *iters;
+};
+int macro_general_parts(int nc);  // blocks of the per-cell launches (rows of `part`)
+cudaError_t run_macro_general(const MacroGenArgs &a, cudaStream_t s);
+
 constexpr int MACRO_MAX_GRID = 512;  // blocks of the synthetic-solve kernel at most
 constexpr int MACRO_BAR_WORDS = 512;  // barrier words, cleared before each launch
 cudaError_t launch_macro(const MacroArgs &a, int grid, int block, cudaStream_t s);

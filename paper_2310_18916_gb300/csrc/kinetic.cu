@@ -1197,6 +1197,60 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
 #pragma unroll
         for (int q = 0; q < NV; ++q) Fio<T, S>::st(F[q] + (size_t)c * VB + lane, fi[q] + df[q]);
       }
+      if (A.kpart) {
+        // outward flux through every face at the new level (upwind face value of f^n plus the
+        // upwind cell's increment; boundary values carry none), summed over the faces; then
+        // its moments over this block's velocities
+        T psi[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) psi[q] = (T)0;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+          const int nb = __ldg(A.gnb + 6 * c + s);
+          if (nb == NB_ABSENT || nb == NB_AXIS) continue;
+          const GenFace<T> &fa = g.f[s];
+          const T sn = dot_xi(fa.S, x, y, z);
+          T e[NV];
+          if (sn > (T)0) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+              e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2] + df[q];
+          } else if (sn < (T)0) {
+            if (nb >= 0) {
+              const GenFace<T> &fb = A.gen[nb].f[s ^ 1];
+#pragma unroll
+              for (int q = 0; q < NV; ++q)
+                e[q] = FC(nb, q) + GS(nb, q, 0) * fb.r[0] + GS(nb, q, 1) * fb.r[1] + GS(nb, q, 2) * fb.r[2] +
+                       dfs[((size_t)nb * NV + q) * VB + lane];
+            } else if (nb == NB_WALL || A.gin[6 * c + s]) {
+              const double *uT = A.wall_uT + 4 * s;
+              const T M = wall_maxwellian<T>(uT, x, y, z) * (nb == NB_WALL ? (T)A.rho_w[__ldg(A.gwid + 6 * c + s)] : (T)1);
+              e[0] = M;
+              if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
+            } else {
+#pragma unroll
+              for (int q = 0; q < NV; ++q)
+                e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2];
+            }
+          } else {
+            continue;
+          }
+#pragma unroll
+          for (int q = 0; q < NV; ++q) psi[q] += sn * e[q];
+        }
+        const T p0 = wv * psi[0], p1 = NV == 2 ? wv * psi[NV - 1] : (T)0;
+        const T m0 = warp_sum(p0), m1 = warp_sum(p0 * x), m2 = warp_sum(p0 * y), m3 = warp_sum(p0 * z);
+        const T m4 = warp_sum(p0 * e2 + p1), m5 = NV == 2 ? warp_sum(p1) : (T)0;
+        if (lane == 0) {
+          double *Kp = A.kpart + ((size_t)blockIdx.x * nc + c) * 6;
+          Kp[0] += (double)m0;
+          Kp[1] += (double)m1;
+          Kp[2] += (double)m2;
+          Kp[3] += (double)m3;
+          Kp[4] += (double)m4;
+          Kp[5] += (double)m5;
+        }
+      }
       for (int s = 0; s < 6; ++s) {
         const int wid = __ldg(A.gwid + 6 * c + s);
         if (wid < 0) continue;
@@ -1299,6 +1353,22 @@ __global__ void __launch_bounds__(256) wall_prepass_general_kernel(const KinArgs
     }
     rho_w[w] = n / d;
   }
+}
+
+__global__ void sum_kpart_kernel(const double *kpart, int nparts, int nc, double *K) {
+  const size_t n = (size_t)nc * 6;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int p = 0; p < nparts; ++p) acc += kpart[(size_t)p * n + i];
+    K[i] = acc;
+  }
+}
+
+cudaError_t launch_sum_kpart(const double *kpart, int nparts, int nc, double *K, cudaStream_t s) {
+  int grid = (int)(((size_t)nc * 6 + 255) / 256);
+  if (grid > 152 * 8) grid = 152 * 8;
+  sum_kpart_kernel<<<grid, 256, 0, s>>>(kpart, nparts, nc, K);
+  return cudaGetLastError();
 }
 
 template <typename T, typename S>

@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(kBlock) macro_kernel(MacroArgs m) {
     if (check && threadIdx.x < 32) {
       const int k = threadIdx.x;
       const double den = __shfl_sync(0xffffffffu, rsum, (k + 6) & 31);
-      bool done = !(k < NW && den > 0.0 && !(rsum < m.tol * m.tol * den));
+      bool done = !(k < NW && den > m.den_floor && !(rsum < m.tol * m.tol * den));
       done = __all_sync(0xffffffffu, done);
       if (k == 0) sdone = done;
     }

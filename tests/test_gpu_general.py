@@ -1,8 +1,8 @@
 """General (curvilinear) structured meshes on the GPU against the FP64 oracle: the kinetic
-iteration on a cylinder O-grid (wall inside, far field outside, wrapped azimuth) and a sphere
-O-grid (pole sides of zero area), with several colour passes per step; FP64 element by element,
-FP32 within its rounding; the Rykov model; wall fluxes and loads; the collisionless reservoir
-slab against its exact discrete solution."""
+iteration and GSIS on a cylinder O-grid (wall inside, far field outside, wrapped azimuth) and a
+sphere O-grid (pole sides of zero area), with several colour passes per step; FP64 element by
+element, FP32 within its rounding; the Rykov model; wall fluxes and loads; the collisionless
+reservoir slab against its exact discrete solution."""
 import numpy as np
 import pytest
 
@@ -124,8 +124,54 @@ def test_reservoir_wall_exact_on_gpu():
     assert np.abs(f - exact[None, :]).max() < 1e-6 * np.abs(exact).max()
 
 
-def test_general_mesh_gsis_mode_is_unsupported():
-    p = wl.cylinder(n_r=4, n_theta=8, nv=8)
-    with pytest.raises(gsis.GsisError) as e:
-        gsis.Solver(p, precision="f32", mode="gsis")
-    assert e.value.code == gsis.GSIS_E_UNSUPPORTED
+def gsis_pair(p, precision, n_sweeps, W0=None, macro_steps=40):
+    g = gsis.Solver(p, precision=precision, mode="gsis", init_W=W0, kinetic_presteps=0, n_sweeps=n_sweeps,
+                    macro_steps=macro_steps, macro_tol=0.0)
+    o = Oracle(p, W0=W0, mode=0, n_sweeps=n_sweeps, macro_steps=macro_steps, macro_tol=0.0)
+    return g, o
+
+
+@pytest.mark.parametrize("body", ["cylinder", "sphere"])
+def test_gsis_steps_on_ogrids_fp64(body):
+    """The synthetic solve on general meshes (Rusanov + NSF faces, far-field faces against the
+    free stream, wall faces by the equilibrium wall flux, red/black LU-SGS) after the kinetic
+    step, GSIS outer steps against the oracle."""
+    if body == "cylinder":
+        p = wl.cylinder(n_r=6, n_theta=12, nv=12, R=0.5, R_out=3.0, first=0.15, Ma=0.5, Kn=0.2, T_w=1.5)
+    else:
+        p = wl.sphere(n_r=4, n_pol=5, n_az=8, nv=10, R=0.5, R_out=3.0, Ma=0.6, Kn=0.3)
+    W = wl.perturbed_state(p, seed=45, amp=0.03)
+    g, o = gsis_pair(p, "f64", 2, W0=W)
+    for it in range(3):
+        g.step()
+        o.step()
+        scaled_close(g.W(), o.W(), 1e-10, f"{body} GSIS W, step {it}")
+    assert g.stats()[1] == o.macro_iters
+    fg, fo = g.get_f(), o.get_f()[0]
+    assert np.abs(fg - fo).max() <= 1e-10 * np.abs(fo).max()
+
+
+def test_gsis_rykov_cylinder_fp64():
+    p = wl.as_rykov(wl.cylinder(n_r=5, n_theta=10, nv=10, R=0.5, R_out=3.0, Ma=0.5, Kn=0.2, T_w=1.3))
+    g, o = gsis_pair(p, "f64", 2)
+    for it in range(2):
+        g.step()
+        o.step()
+        scaled_close(g.W(), o.W(), 1e-10, f"Rykov cylinder GSIS W, step {it}")
+
+
+def test_gsis_cylinder_fp32_and_early_exit():
+    p = wl.cylinder(n_r=6, n_theta=12, nv=16, R=0.5, R_out=3.0, Ma=0.5, Kn=0.2)
+    g, o = gsis_pair(p, "f32", 2, macro_steps=60)
+    for it in range(2):
+        g.step()
+        o.step()
+        scaled_close(g.W(), o.W(), 5e-5, f"FP32 cylinder GSIS W, step {it}")
+    # with the inner tolerance the solve stops early, at the oracle's inner step
+    g2 = gsis.Solver(p, precision="f64", mode="gsis", kinetic_presteps=0, n_sweeps=2, macro_steps=300,
+                     macro_tol=1e-6)
+    o2 = Oracle(p, mode=0, n_sweeps=2, macro_steps=300, macro_tol=1e-6)
+    g2.step()
+    o2.step()
+    assert g2.stats()[1] == o2.macro_iters < 300
+    scaled_close(g2.W(), o2.W(), 1e-10, "cylinder GSIS W with the inner tolerance")

@@ -26,12 +26,13 @@ def test_valid_problems_pass():
         assert code(p) == gsis.GSIS_OK, p.name
 
 
-def test_curved_mesh_runs_the_kinetic_iteration_only():
+def test_curved_mesh_takes_the_general_path():
     p = wl.cavity(n=8, nv=8)
     nodes = p.nodes.copy()
     nodes[..., 0] += 0.01 * nodes[..., 1]  # x depends on J: not rectilinear
-    assert code(dataclasses.replace(p, nodes=nodes)) == gsis.GSIS_E_UNSUPPORTED
-    assert code(dataclasses.replace(p, nodes=nodes), mode=gsis.MODE_DVM) == gsis.GSIS_OK
+    q = dataclasses.replace(p, nodes=nodes)
+    assert code(q) == gsis.GSIS_OK and code(q, mode=gsis.MODE_DVM) == gsis.GSIS_OK
+    assert code(q, shard=(0, 2)) == gsis.GSIS_E_UNSUPPORTED
 
 
 def test_non_increasing_nodes_are_rejected():
@@ -46,9 +47,9 @@ def test_boundary_conditions_must_match_the_axis():
     bc = list(p.bc)
     bc[0] = wl.PERIODIC  # a periodic axis is periodic on both sides
     assert code(dataclasses.replace(p, bc=bc)) == GSIS_E_INVALID
-    bc[1] = wl.PERIODIC  # a wrapped axis takes the general path: kinetic iteration only
-    assert code(dataclasses.replace(p, bc=bc)) == gsis.GSIS_E_UNSUPPORTED
-    assert code(dataclasses.replace(p, bc=bc), mode=gsis.MODE_DVM) == gsis.GSIS_OK
+    bc[1] = wl.PERIODIC  # a wrapped axis takes the general path
+    assert code(dataclasses.replace(p, bc=bc)) == gsis.GSIS_OK
+    assert code(dataclasses.replace(p, bc=bc), shard=(0, 2)) == gsis.GSIS_E_UNSUPPORTED
     bc = list(p.bc)
     bc[4] = wl.WALL  # an axis with one cell must be PERIODIC on both sides
     assert code(dataclasses.replace(p, bc=bc)) == GSIS_E_INVALID
@@ -57,13 +58,16 @@ def test_boundary_conditions_must_match_the_axis():
     assert code(dataclasses.replace(p, bc=bc), mode=gsis.MODE_DVM) == GSIS_E_INVALID
 
 
-def test_general_meshes_run_the_kinetic_iteration():
-    """O-grids (far field, pole and wrapped sides) are accepted in DVM mode on one device, with
-    several colour passes; the synthetic solve and sharding on them are not built."""
+def test_general_meshes_are_accepted():
+    """O-grids (far field, pole and wrapped sides) are accepted in both modes on one device, with
+    several colour passes; velocity sharding on them is not built."""
     for p in (wl.cylinder(n_r=6, n_theta=12, nv=8), wl.sphere(n_r=4, n_pol=4, n_az=6, nv=8),
               wl.reservoir_wall(n_cells=6, nv=8)):
         assert code(p, mode=gsis.MODE_DVM, n_sweeps=3) == gsis.GSIS_OK, p.name
-        assert code(p) == gsis.GSIS_E_UNSUPPORTED, p.name
+        assert code(p) == gsis.GSIS_OK, p.name
+        assert code(p, shard=(0, 2)) == gsis.GSIS_E_UNSUPPORTED, p.name
+        # the synthetic solve's work arrays count in GSIS mode only
+        assert gsis.footprint_bytes(p) > gsis.footprint_bytes(p, mode=gsis.MODE_DVM), p.name
         assert code(p, mode=gsis.MODE_DVM, n_sweeps=0) == GSIS_E_INVALID, p.name
     p = wl.cylinder(n_r=6, n_theta=12, nv=8)
     nodes = p.nodes.copy()
