@@ -269,6 +269,8 @@ BODIES = {
     # cylinder of diameter 1 in cross flow: 64 radial (first 0.01, R_out 10) x 128 azimuthal cells,
     # Ma 2, Kn 0.05, 40^3 velocities on [-9, 9]^3
     "cylinder": dict(kind="cylinder", n=(64, 1, 128), nv=40, vmax=9.0, Ma=2.0, Kn=0.05, first=0.01, R_out=10.0),
+    # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
+    "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }
 BODY_SWEEPS, BODY_INV_DT = 2, 1000.0
 

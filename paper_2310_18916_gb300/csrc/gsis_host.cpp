@@ -1011,18 +1011,18 @@ static int plan_kinetic(gsis_solver *s) {
   if (s->general) {
     // persistent grid of 8-warp CTAs over the velocity blocks, as many as the SMs hold (the
     // kernel is latency-bound) while their whole-mesh work arrays, one set per CTA for its
-    // block of 32 velocities, stay within 32 GB
+    // block of 32 velocities, stay within 48 GB
     s->kin_smem = 0;
     s->kin_warps = 8;
-    s->kin_gstride = kinetic_general_stride<T, S>(s->nc, s->nvdf);
+    s->kin_gstride = kinetic_general_stride<T, S>(s->nc, s->nvdf, s->kg.nact);
     int dev = 0, sms = 152, occ = 2;
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
-      const int rc = s->cuda(kinetic_general_shape<T, S>(s->nvdf, &occ), "kinetic shape");
+      const int rc = s->cuda(kinetic_general_shape<T, S>(s->nvdf, s->kg.nact, &occ), "kinetic shape");
       if (rc) return rc;
     } else {
       cudaGetLastError();
     }
-    const size_t budget = (size_t)32 << 30;
+    const size_t budget = (size_t)48 << 30;
     const int by_mem = (int)std::max<size_t>(1, budget / ((size_t)sms * s->kin_gstride));
     s->kin_grid = std::max(1, std::min(s->nblocks, std::max(1, std::min(occ, by_mem)) * sms));
     s->kin_scratch_bytes = (size_t)s->kin_grid * s->kin_gstride;

@@ -149,9 +149,9 @@ cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon
 template <typename T, typename S>
 cudaError_t launch_kinetic_general(const KinArgs<T, S> &a, int grid, cudaStream_t s);
 template <typename T, typename S>
-cudaError_t kinetic_general_shape(int nvdf, int *ctas_per_sm);
+cudaError_t kinetic_general_shape(int nvdf, int nact, int *ctas_per_sm);
 template <typename T, typename S>
-size_t kinetic_general_stride(int nc, int nvdf);
+size_t kinetic_general_stride(int nc, int nvdf, int nact);
 // K [cell][6] = sum over the CTAs of kpart (fixed order)
 cudaError_t launch_sum_kpart(const double *kpart, int nparts, int nc, double *K, cudaStream_t s);
 template <typename T, typename S>

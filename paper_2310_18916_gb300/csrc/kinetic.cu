@@ -1032,22 +1032,23 @@ __device__ __forceinline__ T venkat_general(const GenCell<T> &g, const int *nb, 
   return ddiv(bn, bd);
 }
 
-template <typename T, typename S, int NV>
+template <typename T, typename S, int NV, int NACT>
 __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S> A) {
+  constexpr int NF = 2 * NACT;  // sides of the active axes (the others carry no transport)
   const KinGeom &G = A.g;
   const int nc = G.nc, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   constexpr int SL = stage_state_len<S, NV>();
   constexpr int CL = NV == 2 ? NST_RYKOV : 16;
-  // work arrays of this CTA: f^n, limited gradient, residual, increment [cell][q][VB];
-  // diagonal and M_t of W^n [cell][VB]
+  // work arrays of this CTA: f^n, the limited face values of every active side, residual and
+  // increment [cell][q][...][VB]; the implicit diagonal [cell][VB]
   T *fc = reinterpret_cast<T *>(A.gscratch + (size_t)blockIdx.x * A.gstride);
-  T *gs = fc + (size_t)nc * NV * VB;
-  T *rs = gs + (size_t)nc * NV * 3 * VB;
+  T *ffs = fc + (size_t)nc * NV * VB;
+  T *rs = ffs + (size_t)nc * NV * NF * VB;
   T *dfs = rs + (size_t)nc * NV * VB;
   T *ds = dfs + (size_t)nc * NV * VB;
-  T *ms = ds + (size_t)nc * VB;
   auto FC = [&](int c, int q) -> T & { return fc[((size_t)c * NV + q) * VB + lane]; };
-  auto GS = [&](int c, int q, int k) -> T & { return gs[(((size_t)c * NV + q) * 3 + k) * VB + lane]; };
+  auto FF = [&](int c, int q, int s) -> T & { return ffs[(((size_t)c * NV + q) * NF + s) * VB + lane]; };
+  auto DF = [&](int c, int q) -> T & { return dfs[((size_t)c * NV + q) * VB + lane]; };
   for (int b = blockIdx.x; b < A.nblocks; b += gridDim.x) {
     const int oct = A.boct[b];
     const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
@@ -1056,7 +1057,7 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
     S *F[NV];
     F[0] = A.f + (size_t)b * nc * VB;
     if constexpr (NV == 2) F[NV - 1] = A.f1 + (size_t)b * nc * VB;
-    // f^n of every cell (Eq. updatef applied on load)
+    // f^n of every cell (Eq. updatef applied on load); the increments start at zero
     for (int c = warp; c < nc; c += nw) {
       T st[SL], stored[NV], f[NV];
       load_state<SL>(state_of(A.st, c), st);
@@ -1064,32 +1065,39 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
       for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(F[q] + (size_t)c * VB + lane);
       corrected_all<T, S, NV>(stored, st, x, y, z, f);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) FC(c, q) = f[q];
+      for (int q = 0; q < NV; ++q) {
+        FC(c, q) = f[q];
+        DF(c, q) = (T)0;
+      }
     }
     __syncthreads();
-    // limited least-squares gradient
+    // limited least-squares reconstruction: the face value of every active side
     for (int c = warp; c < nc; c += nw) {
       const GenCell<T> &g = A.gen[c];
       int nb[6];
 #pragma unroll
-      for (int s = 0; s < 6; ++s) nb[s] = __ldg(A.gnb + 6 * c + s);
+      for (int s = 0; s < 6; ++s) nb[s] = s < NF ? __ldg(A.gnb + 6 * c + s) : NB_ABSENT;
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         const T fi = FC(c, q);
+        T fj[NF];
+#pragma unroll
+        for (int s = 0; s < NF; ++s) fj[s] = nb[s] >= 0 ? FC(nb[s], q) : fi;
         T gr[3] = {(T)0, (T)0, (T)0}, fmax = fi, fmin = fi;
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
+        for (int s = 0; s < NF; ++s) {
           if (nb[s] < 0) continue;
-          const T fj = FC(nb[s], q), d = fj - fi;
+          const T d = fj[s] - fi;
           gr[0] += g.f[s].w[0] * d;
           gr[1] += g.f[s].w[1] * d;
           gr[2] += g.f[s].w[2] * d;
-          fmax = fmax > fj ? fmax : fj;
-          fmin = fmin < fj ? fmin : fj;
+          fmax = fmax > fj[s] ? fmax : fj[s];
+          fmin = fmin < fj[s] ? fmin : fj[s];
         }
         const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) GS(c, q, k) = phi * gr[k];
+        for (int s = 0; s < NF; ++s)
+          FF(c, q, s) = fi + phi * (gr[0] * g.f[s].r[0] + gr[1] * g.f[s].r[1] + gr[2] * g.f[s].r[2]);
       }
     }
     __syncthreads();
@@ -1099,32 +1107,25 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
       T st[CL];
       load_state<CL>(state_of(A.st, c), st);
       const T cx = x - st[0], cy = y - st[1], cz = z - st[2];
-      T mw, gq[NV], fi[NV], acc[NV];
+      T mw, gq[NV], acc[NV];
       reference<T, NV>(st, cx, cy, cz, cx * cx + cy * cy + cz * cz, mw, gq);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        fi[q] = FC(c, q);
-        acc[q] = (gq[q] - fi[q]) * st[11];
-      }
+      for (int q = 0; q < NV; ++q) acc[q] = (gq[q] - FC(c, q)) * st[11];
       T D = st[15];
 #pragma unroll
-      for (int s = 0; s < 6; ++s) {
+      for (int s = 0; s < NF; ++s) {
         const int nb = __ldg(A.gnb + 6 * c + s);
         if (nb == NB_ABSENT || nb == NB_AXIS) continue;
-        const GenFace<T> &fa = g.f[s];
-        const T sn = dot_xi(fa.S, x, y, z), k = sn * g.invV;
+        const T sn = dot_xi(g.f[s].S, x, y, z), k = sn * g.invV;
         T e[NV];
         if (sn > (T)0) {
           D += k;
 #pragma unroll
-          for (int q = 0; q < NV; ++q)
-            e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2];
+          for (int q = 0; q < NV; ++q) e[q] = FF(c, q, s);
         } else if (sn < (T)0) {
           if (nb >= 0) {
-            const GenFace<T> &fb = A.gen[nb].f[s ^ 1];
 #pragma unroll
-            for (int q = 0; q < NV; ++q)
-              e[q] = FC(nb, q) + GS(nb, q, 0) * fb.r[0] + GS(nb, q, 1) * fb.r[1] + GS(nb, q, 2) * fb.r[2];
+            for (int q = 0; q < NV; ++q) e[q] = FF(nb, q, s ^ 1);
           } else if (nb == NB_WALL || A.gin[6 * c + s]) {
             // the wall's re-emission rho_w M_w, or the free stream entering (f1: (d_r T / 4) M)
             const double *uT = A.wall_uT + 4 * s;
@@ -1134,8 +1135,7 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
           } else {
             // far field where the free stream leaves: the cell's own face value
 #pragma unroll
-            for (int q = 0; q < NV; ++q)
-              e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2];
+            for (int q = 0; q < NV; ++q) e[q] = FF(c, q, s);
           }
         } else {
           continue;
@@ -1146,11 +1146,9 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
 #pragma unroll
       for (int q = 0; q < NV; ++q) rs[((size_t)c * NV + q) * VB + lane] = acc[q];
       ds[(size_t)c * VB + lane] = D;
-      ms[(size_t)c * VB + lane] = mw;
     }
-    // point-implicit passes over the colours of this octant
-    for (int c = threadIdx.x; c < nc * NV * VB; c += blockDim.x) dfs[c] = (T)0;
     __syncthreads();
+    // point-implicit passes over the colours of this octant
     const int4 *natcell = A.natcell + (size_t)oct * nc;
     for (int pass = 0; pass < A.n_sweeps; ++pass) {
       for (int col = 0; col < G.ncol; ++col) {
@@ -1162,35 +1160,37 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
 #pragma unroll
           for (int q = 0; q < NV; ++q) acc[q] = rs[((size_t)c * NV + q) * VB + lane];
 #pragma unroll
-          for (int s = 0; s < 6; ++s) {
+          for (int s = 0; s < NF; ++s) {
             const int nb = __ldg(A.gnb + 6 * c + s);
             if (nb < 0) continue;  // boundary increments are lagged (zero)
             const T sn = dot_xi(g.f[s].S, x, y, z);
             if (sn < (T)0) {
 #pragma unroll
-              for (int q = 0; q < NV; ++q) acc[q] += -sn * g.invV * dfs[((size_t)nb * NV + q) * VB + lane];
+              for (int q = 0; q < NV; ++q) acc[q] += -sn * g.invV * DF(nb, q);
             }
           }
           const T D = ds[(size_t)c * VB + lane];
 #pragma unroll
-          for (int q = 0; q < NV; ++q) dfs[((size_t)c * NV + q) * VB + lane] = ddiv(acc[q], D);
+          for (int q = 0; q < NV; ++q) DF(c, q) = ddiv(acc[q], D);
         }
         __syncthreads();
       }
     }
-    // f^{n+1/2} = f^n + df (stored relative to M_t of W^n for FP32 / BF16) and the outward flux
-    // moments of the wall faces, per unit area
+    // f^{n+1/2} = f^n + df (stored relative to M_t of W^n for FP32 / BF16), the outward flux
+    // moments of the wall faces per unit area and, in GSIS mode, the kinetic face-flux sums
     for (int c = warp; c < nc; c += nw) {
       const GenCell<T> &g = A.gen[c];
       T fi[NV], df[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         fi[q] = FC(c, q);
-        df[q] = dfs[((size_t)c * NV + q) * VB + lane];
+        df[q] = DF(c, q);
       }
       if constexpr (StoredRelative<S>::value) {
-        const T mw = ms[(size_t)c * VB + lane];
-        const T r1 = NV == 2 ? state_of(A.st, c)[29] : (T)0;
+        const T *st = state_of(A.st, c);
+        const T cx = x - st[0], cy = y - st[1], cz = z - st[2];
+        const T mw = st[4] * dexp(-(cx * cx + cy * cy + cz * cz) * st[3]);
+        const T r1 = NV == 2 ? st[29] : (T)0;
 #pragma unroll
         for (int q = 0; q < NV; ++q) Fio<T, S>::st(F[q] + (size_t)c * VB + lane, fi[q] + df[q] - (q == 0 ? mw : r1 * mw));
       } else {
@@ -1205,23 +1205,18 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
 #pragma unroll
         for (int q = 0; q < NV; ++q) psi[q] = (T)0;
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
+        for (int s = 0; s < NF; ++s) {
           const int nb = __ldg(A.gnb + 6 * c + s);
           if (nb == NB_ABSENT || nb == NB_AXIS) continue;
-          const GenFace<T> &fa = g.f[s];
-          const T sn = dot_xi(fa.S, x, y, z);
+          const T sn = dot_xi(g.f[s].S, x, y, z);
           T e[NV];
           if (sn > (T)0) {
 #pragma unroll
-            for (int q = 0; q < NV; ++q)
-              e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2] + df[q];
+            for (int q = 0; q < NV; ++q) e[q] = FF(c, q, s) + df[q];
           } else if (sn < (T)0) {
             if (nb >= 0) {
-              const GenFace<T> &fb = A.gen[nb].f[s ^ 1];
 #pragma unroll
-              for (int q = 0; q < NV; ++q)
-                e[q] = FC(nb, q) + GS(nb, q, 0) * fb.r[0] + GS(nb, q, 1) * fb.r[1] + GS(nb, q, 2) * fb.r[2] +
-                       dfs[((size_t)nb * NV + q) * VB + lane];
+              for (int q = 0; q < NV; ++q) e[q] = FF(nb, q, s ^ 1) + DF(nb, q);
             } else if (nb == NB_WALL || A.gin[6 * c + s]) {
               const double *uT = A.wall_uT + 4 * s;
               const T M = wall_maxwellian<T>(uT, x, y, z) * (nb == NB_WALL ? (T)A.rho_w[__ldg(A.gwid + 6 * c + s)] : (T)1);
@@ -1229,8 +1224,7 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
               if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
             } else {
 #pragma unroll
-              for (int q = 0; q < NV; ++q)
-                e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2];
+              for (int q = 0; q < NV; ++q) e[q] = FF(c, q, s);
             }
           } else {
             continue;
@@ -1251,7 +1245,7 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
           Kp[5] += (double)m5;
         }
       }
-      for (int s = 0; s < 6; ++s) {
+      for (int s = 0; s < NF; ++s) {
         const int wid = __ldg(A.gwid + 6 * c + s);
         if (wid < 0) continue;
         const GenFace<T> &fa = g.f[s];
@@ -1259,8 +1253,7 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
         T e[NV];
         if (sn > (T)0) {
 #pragma unroll
-          for (int q = 0; q < NV; ++q)
-            e[q] = fi[q] + GS(c, q, 0) * fa.r[0] + GS(c, q, 1) * fa.r[1] + GS(c, q, 2) * fa.r[2] + df[q];
+          for (int q = 0; q < NV; ++q) e[q] = FF(c, q, s) + df[q];
         } else {
           const double *uT = A.wall_uT + 4 * s;
           const T M = sn < (T)0 ? wall_maxwellian<T>(uT, x, y, z) * (T)A.rho_w[wid] : (T)0;
@@ -1372,22 +1365,27 @@ cudaError_t launch_sum_kpart(const double *kpart, int nparts, int nc, double *K,
 }
 
 template <typename T, typename S>
-size_t kinetic_general_stride(int nc, int nvdf) {
-  return (((size_t)nc * VB * (6 * nvdf + 2)) * sizeof(T) + 255) & ~(size_t)255;
+size_t kinetic_general_stride(int nc, int nvdf, int nact) {
+  return (((size_t)nc * VB * (nvdf * (3 + 2 * nact) + 1)) * sizeof(T) + 255) & ~(size_t)255;
 }
 
 template <typename T, typename S>
-cudaError_t kinetic_general_shape(int nvdf, int *ctas_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      ctas_per_sm, nvdf == 2 ? kinetic_general_kernel<T, S, 2> : kinetic_general_kernel<T, S, 1>, 256, 0);
+static void (*kinetic_general_fn(int nvdf, int nact))(const KinArgs<T, S>) {
+  if (nvdf == 2)
+    return nact == 1 ? kinetic_general_kernel<T, S, 2, 1>
+                     : (nact == 2 ? kinetic_general_kernel<T, S, 2, 2> : kinetic_general_kernel<T, S, 2, 3>);
+  return nact == 1 ? kinetic_general_kernel<T, S, 1, 1>
+                   : (nact == 2 ? kinetic_general_kernel<T, S, 1, 2> : kinetic_general_kernel<T, S, 1, 3>);
+}
+
+template <typename T, typename S>
+cudaError_t kinetic_general_shape(int nvdf, int nact, int *ctas_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kinetic_general_fn<T, S>(nvdf, nact), 256, 0);
 }
 
 template <typename T, typename S>
 cudaError_t launch_kinetic_general(const KinArgs<T, S> &a, int grid, cudaStream_t s) {
-  if (a.nvdf == 2)
-    kinetic_general_kernel<T, S, 2><<<grid, 256, 0, s>>>(a);
-  else
-    kinetic_general_kernel<T, S, 1><<<grid, 256, 0, s>>>(a);
+  kinetic_general_fn<T, S>(a.nvdf, a.g.nact)<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1414,8 +1412,8 @@ cudaError_t launch_wall_prepass_general(const KinArgs<T, S> &a, const int *wall_
   template cudaError_t launch_import_f<T, S>(const KinArgs<T, S> &, int, const int *, int, int, const double *, \
                                              cudaStream_t);                                                      \
   template cudaError_t launch_kinetic_general<T, S>(const KinArgs<T, S> &, int, cudaStream_t);                   \
-  template cudaError_t kinetic_general_shape<T, S>(int, int *);                                                  \
-  template size_t kinetic_general_stride<T, S>(int, int);                                                        \
+  template cudaError_t kinetic_general_shape<T, S>(int, int, int *);                                             \
+  template size_t kinetic_general_stride<T, S>(int, int, int);                                                   \
   template cudaError_t launch_wall_prepass_general<T, S>(const KinArgs<T, S> &, const int *, const int *, int,   \
                                                          double *, cudaStream_t);
 GSIS_INST(float, float)
