@@ -152,6 +152,11 @@ typedef struct {
                            twice as many blocks resident per SM; else in a device scratch of the
                            solver's own, counted by gsis_footprint_bytes.  1: always in the
                            device scratch.  Results are bit-identical either way. */
+  int euler_presteps;   /* inner steps of the inviscid synthetic solve (Euler fluxes, slip walls,
+                           far field against the free stream) run once at creation, before the
+                           kinetic presteps; f then starts as the Maxwellian of their result
+                           (the Euler preconditioning of Algorithm 1 for strong shocks).  Default
+                           0; general blocks only (GSIS_E_UNSUPPORTED on rectilinear ones). */
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;

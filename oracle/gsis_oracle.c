@@ -1098,6 +1098,21 @@ void orc_destroy(orc_solver *s) {
   free(s);
 }
 
+/* f = Maxwellian of W (rho, u, T_t, T_r per cell); f1 = (d_r T_r / 4) M */
+static void set_maxwellian(orc_solver *s, const double *W) {
+  int nc = s->nc;
+  for (int i = 0; i < nc; ++i) {
+    const double *w0 = W + 6 * i;
+    double xi[3], w;
+    for (int v = 0; v < s->nv; ++v) {
+      vel_of(s, v, xi, &w);
+      double M = maxwellian(w0[0], w0 + 1, w0[4], xi);
+      s->f0[(size_t)v * nc + i] = M;
+      if (s->nvdf == 2) s->f1[(size_t)v * nc + i] = s->g.d_r * w0[5] / 4.0 * M;
+    }
+  }
+}
+
 static int init_state_from_f(orc_solver *s) {
   int rc = all_moments(s);
   if (rc) return rc;
@@ -1158,20 +1173,38 @@ int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const o
           if (colour_of(s, i, sgn) == col) s->corder[(size_t)oct * nc + t++] = i;
     }
   }
-  for (int i = 0; i < nc; ++i) {
-    const double *w0 = W0 + 6 * i;
-    double xi[3], w;
-    for (int v = 0; v < s->nv; ++v) {
-      vel_of(s, v, xi, &w);
-      double M = maxwellian(w0[0], w0 + 1, w0[4], xi);
-      s->f0[(size_t)v * nc + i] = M;
-      if (s->nvdf == 2) s->f1[(size_t)v * nc + i] = g->d_r * w0[5] / 4.0 * M;
-    }
-  }
+  set_maxwellian(s, W0);
   rc = init_state_from_f(s);
   if (rc) { orc_destroy(s); return rc; }
   *out = s;
   return ORC_OK;
+}
+
+/* Euler preconditioning (the presteps of Algorithm 1 for configurations with strong shocks):
+   n inner steps of the synthetic solve in its inviscid form (Euler fluxes, slip walls, no
+   high-order correction) from the current state, then f restarts as the Maxwellian of the
+   result. */
+int orc_euler_presteps(orc_solver *s, int n) {
+  int nc = s->nc, used = 0;
+  double *Wc = (double *)calloc(6 * (size_t)nc, sizeof(double)), *Wp = (double *)malloc(sizeof(double) * 6 * nc);
+  if (!Wc || !Wp) { free(Wc); free(Wp); return ORC_E_OOM; }
+  for (int i = 0; i < nc; ++i) cons_of(s, s->st + 12 * i, Wc + 6 * i);
+  int rc = macro_solve(s, Wc, s->fkin, 1, n, s->o.macro_tol, &used);
+  if (!rc) {
+    double mm = 0.0;
+    for (int i = 0; i < nc; ++i) {
+      prim_of(s, Wc + 6 * i, Wp + 6 * i);
+      mm += Wp[6 * i] * s->vol[i];
+    }
+    if (!s->open)
+      for (int i = 0; i < nc; ++i) Wp[6 * i] *= s->mass_ref / mm;
+    set_maxwellian(s, Wp);
+    rc = init_state_from_f(s);
+    s->macro_iters = used;
+  }
+  free(Wc);
+  free(Wp);
+  return rc;
 }
 
 int orc_set_f(orc_solver *s, const double *f0, const double *f1) {

@@ -75,6 +75,9 @@ int orc_get_f(const orc_solver *s, double *f0, double *f1);
 int orc_step(orc_solver *s);
 /* n plain kinetic steps whatever the mode (the preconditioning of Algorithm 1). */
 int orc_presteps(orc_solver *s, int n);
+/* Euler preconditioning: n inner steps of the inviscid synthetic solve (slip walls, far field
+   against the free stream) from the current state; f restarts as the Maxwellian of the result. */
+int orc_euler_presteps(orc_solver *s, int n);
 
 /* Parts of one outer step, for timing and unit tests. */
 int orc_wall_prepass(orc_solver *s);                       /* rho_w from the current f */

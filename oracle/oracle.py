@@ -48,6 +48,7 @@ def lib():
                      "orc_nwall", "orc_macro_iters"):
             getattr(L, name).argtypes = [C.c_void_p]
         L.orc_presteps.argtypes = [C.c_void_p, C.c_int]
+        L.orc_euler_presteps.argtypes = [C.c_void_p, C.c_int]
         L.orc_kinetic_velocities.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_eps.argtypes = [C.c_void_p]
         L.orc_eps.restype = C.c_double
@@ -147,6 +148,9 @@ class Oracle:
 
     def presteps(self, n):
         self._rc(lib().orc_presteps(self.h, n), "orc_presteps")
+
+    def euler_presteps(self, n):
+        self._rc(lib().orc_euler_presteps(self.h, n), "orc_euler_presteps")
 
     def run(self, max_outer, tol):
         hist = []

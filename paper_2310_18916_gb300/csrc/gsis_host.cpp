@@ -222,6 +222,43 @@ struct gsis_solver {
     return a;
   }
 
+  // the synthetic solve on general meshes: GSIS inner steps from the moments Mh (K set by the
+  // caller); Euler mode sets euler, steps, Mh / mh_stride itself
+  MacroGenArgs macro_general_args() const {
+    MacroGenArgs m{};
+    m.nc = (int)nc;
+    m.nW = gas.model == GSIS_RYKOV ? 6 : 5;
+    m.model = gas.model;
+    m.steps = opt.macro_steps;
+    m.sweeps = opt.macro_sweeps;
+    m.closed = closed;
+    m.ncol0 = ncol0;
+    m.euler = 0;
+    m.mh_stride = 18;
+    m.mu0 = Kn / std::sqrt(3.14159265358979323846);
+    m.omega = omega;
+    m.cfl = opt.macro_cfl;
+    m.tol = opt.macro_tol;
+    m.d_r = gas.d_r;
+    m.Z_r = gas.Z_r;
+    for (int k = 0; k < 4; ++k) m.A[k] = gas.A[k];
+    m.mass_ref = mass_ref;
+    m.vsum = vsum;
+    m.gen = d_gen64;
+    m.gnb = d_gnb;
+    m.xc = d_xc;
+    m.vol = d_vol;
+    m.wall_uT = d_wall_uT;
+    m.Mh = d_Mh;
+    m.colcells = d_colcells;
+    m.W = g_W; m.pr = g_pr; m.mu = g_mu; m.gW = g_gW; m.phW = g_phW; m.gP = g_gP;
+    m.R = g_R; m.D = g_D; m.dW = g_dW; m.F0 = g_F0; m.part = g_part; m.flag = g_flag;
+    m.Wout = d_Wnew;
+    m.err = d_err;
+    m.iters = d_iters;
+    return m;
+  }
+
   // sum over the velocity shards (no-op unsharded)
   int exchange(double *dev, size_t count, const char *what) {
     if (opt.shard_count <= 1 || count == 0) return GSIS_OK;
@@ -367,36 +404,8 @@ struct gsis_solver {
       // the kinetic face fluxes summed per cell, then the general synthetic solve
       rc = cuda(launch_sum_kpart(d_kpart, kin_grid, (int)nc, d_K, stream), "kinetic flux sums");
       if (rc) return rc;
-      MacroGenArgs m{};
-      m.nc = (int)nc;
-      m.nW = gas.model == GSIS_RYKOV ? 6 : 5;
-      m.model = gas.model;
-      m.steps = opt.macro_steps;
-      m.sweeps = opt.macro_sweeps;
-      m.closed = closed;
-      m.ncol0 = ncol0;
-      m.mu0 = Kn / std::sqrt(3.14159265358979323846);
-      m.omega = omega;
-      m.cfl = opt.macro_cfl;
-      m.tol = opt.macro_tol;
-      m.d_r = gas.d_r;
-      m.Z_r = gas.Z_r;
-      for (int k = 0; k < 4; ++k) m.A[k] = gas.A[k];
-      m.mass_ref = mass_ref;
-      m.vsum = vsum;
-      m.gen = d_gen64;
-      m.gnb = d_gnb;
-      m.xc = d_xc;
-      m.vol = d_vol;
-      m.wall_uT = d_wall_uT;
-      m.Mh = d_Mh;
+      MacroGenArgs m = macro_general_args();
       m.K = d_K;
-      m.colcells = d_colcells;
-      m.W = g_W; m.pr = g_pr; m.mu = g_mu; m.gW = g_gW; m.phW = g_phW; m.gP = g_gP;
-      m.R = g_R; m.D = g_D; m.dW = g_dW; m.F0 = g_F0; m.part = g_part; m.flag = g_flag;
-      m.Wout = d_Wnew;
-      m.err = d_err;
-      m.iters = d_iters;
       rc = cuda(run_macro_general(m, stream), "synthetic solve");
       if (rc) return rc;
       launches += 2 + opt.macro_steps * (6 + 2 * opt.macro_sweeps);
@@ -576,6 +585,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   }
   if (o->mode != GSIS_MODE_GSIS && o->mode != GSIS_MODE_DVM) { why = "bad mode"; return GSIS_E_INVALID; }
   if (o->kinetic_ring != 0 && o->kinetic_ring != 1) { why = "kinetic_ring must be 0 or 1"; return GSIS_E_INVALID; }
+  if (o->euler_presteps < 0) { why = "euler_presteps must be >= 0"; return GSIS_E_INVALID; }
   if (o->shard_count > 1 && (o->shard_index < 0 || o->shard_index >= o->shard_count || !o->allreduce)) {
     why = "velocity sharding needs 0 <= shard_index < shard_count and an allreduce callback";
     return GSIS_E_INVALID;
@@ -623,6 +633,10 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
       why = "wall and free-stream temperatures must be positive";
       return GSIS_E_INVALID;
     }
+  if (!general && o->euler_presteps > 0) {
+    why = "Euler presteps are built on general meshes only";
+    return GSIS_E_UNSUPPORTED;
+  }
   if (general) {
     if (o->shard_count > 1) { why = "velocity sharding is built for rectilinear meshes only"; return GSIS_E_UNSUPPORTED; }
     return GSIS_OK;  // volumes are checked when the geometry is built
@@ -1064,7 +1078,7 @@ static size_t footprint(const gsis_solver *s) {
   b += (size_t)s->nblocks * (s->nwall + 1) * NWF * T;  // wall partials
   b += s->kin_scratch_bytes;                          // kinetic ring or work arrays in global memory
   if (s->general) b += nc * (sizeof(GenCell<double>) + 6 * (2 * sizeof(int) + 1)) + (size_t)s->nwall * 8;
-  if (s->general && s->opt.mode == GSIS_MODE_GSIS)
+  if (s->general && (s->opt.mode == GSIS_MODE_GSIS || s->opt.euler_presteps > 0))
     b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36) * 8) +
          12 * 8 * (size_t)macro_general_parts((int)nc);
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
@@ -1097,7 +1111,7 @@ static int allocate_and_upload(gsis_solver *s) {
     A(s->d_gwid, 6 * nc * sizeof(int));
     A(s->d_gin, 6 * nc);
     A(s->d_wall_area, (size_t)(s->nwall + 1) * sizeof(double));
-    if (s->opt.mode == GSIS_MODE_GSIS) {
+    if (s->opt.mode == GSIS_MODE_GSIS || s->opt.euler_presteps > 0) {
       A(s->d_gen64, nc * sizeof(GenCell<double>));
       A(s->d_xc, 3 * nc * sizeof(double));
       A(s->d_kpart, (size_t)s->kin_grid * nc * 6 * sizeof(double));
@@ -1238,6 +1252,8 @@ extern "C" int gsis_footprint_bytes(const gsis_mesh *mesh, const gsis_vgrid *vgr
   return GSIS_OK;
 }
 
+static int init_state_from(gsis_solver *s, std::vector<double> &W0);
+
 static int init_state(gsis_solver *s) {
   const size_t nc = s->nc;
   std::vector<double> W0(nc * 6);
@@ -1251,6 +1267,29 @@ static int init_state(gsis_solver *s) {
     }
     if (!(W0[c * 6] > 0) || !(W0[c * 6 + 4] > 0)) return s->fail(GSIS_E_INVALID, "initial state must have rho, T > 0");
   }
+  return init_state_from(s, W0);
+}
+
+// Euler preconditioning on general meshes: the inviscid synthetic solve from the current state
+// W^n for euler_presteps inner steps, then f restarts as the Maxwellian of its result
+static int euler_presteps(gsis_solver *s) {
+  MacroGenArgs m = s->macro_general_args();
+  m.euler = 1;
+  m.steps = s->opt.euler_presteps;
+  m.Mh = s->d_Wstate;
+  m.mh_stride = 6;
+  m.K = nullptr;
+  int rc = s->cuda(run_macro_general(m, s->stream), "Euler presteps");
+  std::vector<double> W((size_t)s->nc * 6);
+  if (!rc) rc = s->cuda(cudaMemcpyAsync(W.data(), s->d_Wnew, W.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream), "W");
+  if (!rc) rc = s->cuda(cudaStreamSynchronize(s->stream), "sync");
+  if (!rc) rc = s->check_err();
+  if (rc) return rc;
+  return init_state_from(s, W);
+}
+
+static int init_state_from(gsis_solver *s, std::vector<double> &W0) {
+  const size_t nc = s->nc;
   double *dW0 = nullptr;
   int rc = s->cuda(cudaMalloc(&dW0, nc * 6 * sizeof(double)), "temporary");
   if (rc) return rc;
@@ -1288,6 +1327,7 @@ extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const
   if (!rc) rc = GSIS_DISPATCH(s->prec, (plan_kinetic<T, S>(s)));
   if (!rc) rc = GSIS_DISPATCH(s->prec, (allocate_and_upload<T, S>(s)));
   if (!rc) rc = init_state(s);
+  if (!rc && o.euler_presteps > 0) rc = euler_presteps(s);
   for (int t = 0; !rc && t < o.kinetic_presteps; ++t) rc = s->step(GSIS_MODE_DVM);
   if (rc) {
     g_create_error = s->last_error;

@@ -271,13 +271,15 @@ struct MacroArgs {
 // The synthetic solve on general meshes (one thread per cell, one launch per phase)
 struct MacroGenArgs {
   int nc, nW, model, steps, sweeps, closed, ncol0;
+  int euler;                   // 1: the inviscid presteps (slip walls, no correction, K unused)
+  int mh_stride;               // doubles per cell of Mh (18: the moments; 6: a primitive state)
   double mu0, omega, cfl, tol, d_r, Z_r, A[4], mass_ref;
   double vsum;                 // total volume (fields with sum W_k^2 V <= 1e-24 vsum count as zero)
   const GenCell<double> *gen;  // [cell] FP64 geometry
   const int *gnb;              // [cell][6]
   const double *xc, *vol;      // [cell][3], [cell]
   const double *wall_uT;       // [6][4]: wall u, T; far field: free-stream u, T
-  const double *Mh;            // [cell][18] W^{n+1/2}
+  const double *Mh;            // [cell][mh_stride] initial primitives rho, u, T_t, T_r
   const double *K;             // [cell][6] area-integrated outward kinetic flux summed over the faces
   const int *colcells;         // red cells then black cells
   // work

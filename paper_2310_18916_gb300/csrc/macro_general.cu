@@ -16,6 +16,8 @@
 //            (F(W_j + dW_j) - F(W_j)) . n - gamma dW_j (Eq. res_macro);
 //   update   W += dW, the relative increment per field, and the early exit below macro_tol.
 // Work is skipped once the early exit has fired, so the whole solve is enqueued at once.
+// Euler mode (the presteps of Algorithm 1): Euler fluxes only, slip walls (pressure), no
+// high-order correction and no kinetic flux sums.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -173,6 +175,7 @@ __device__ void face_flux(const MacroGenArgs &m, int i, int side, int j, const d
   const double lR = fabs(pR[1] * n[0] + pR[2] * n[1] + pR[3] * n[2]) + sound(pR[4]);
   const double lam = lL > lR ? lL : lR;
   for (int k = 0; k < 6; ++k) F[k] = k < m.nW ? 0.5 * (FL[k] + FR[k]) - 0.5 * lam * (WR[k] - WL[k]) : 0.0;
+  if (m.euler) return;
   double nsf[12], sn[3], uf[3];
   face_nsf(m, i, jv, nsf);
   for (int a = 0; a < 3; ++a) uf[a] = 0.5 * (m.pr[6 * (size_t)i + 1 + a] + m.pr[6 * (size_t)jv + 1 + a]);
@@ -188,7 +191,7 @@ __device__ __forceinline__ bool done(const MacroGenArgs &m) { return *(volatile 
 __global__ void init_kernel(MacroGenArgs m) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
     double p[6];
-    for (int k = 0; k < 6; ++k) p[k] = m.Mh[18 * (size_t)c + k];
+    for (int k = 0; k < 6; ++k) p[k] = m.Mh[(size_t)m.mh_stride * c + k];
     cons_of(m, p, m.W + 6 * (size_t)c);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -257,17 +260,28 @@ __global__ void resid_kernel(MacroGenArgs m, int step) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
     const GenCell<double> &g = m.gen[c];
     double acc[6];
-    for (int k = 0; k < 6; ++k) acc[k] = m.K[6 * (size_t)c + k];
+    for (int k = 0; k < 6; ++k) acc[k] = m.euler ? 0.0 : m.K[6 * (size_t)c + k];
     for (int s = 0; s < 6; ++s) {
       const int nb = m.gnb[6 * (size_t)c + s];
       if (nb == NB_ABSENT || nb == NB_AXIS) continue;
       const double *S = g.f[s].S;
       const double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
       double F[6];
-      if (nb == NB_WALL)
+      if (nb == NB_WALL && m.euler) {
+        // slip wall: the pressure of the cell
+        const double *pc = m.pr + 6 * (size_t)c;
+        const double pt = 0.5 * pc[0] * pc[4];
+        for (int k = 0; k < 6; ++k) F[k] = 0.0;
+        for (int a = 0; a < 3; ++a) F[1 + a] = pt * n[a];
+      } else if (nb == NB_WALL) {
         wall_eq_flux(m, s, m.pr + 6 * (size_t)c, n, F);
-      else
+      } else {
         face_flux(m, c, s, nb, n, F);
+      }
+      if (m.euler) {
+        for (int k = 0; k < m.nW; ++k) acc[k] += F[k] * A;
+        continue;
+      }
       double *F0 = m.F0 + 36 * (size_t)c + 6 * s;
       if (step == 0)
         for (int k = 0; k < 6; ++k) F0[k] = F[k];
@@ -297,10 +311,11 @@ __device__ double face_gamma(const MacroGenArgs &m, int c, int s, int nb, const 
     const double d[3] = {m.xc[3 * (size_t)nb] - m.xc[3 * (size_t)c], m.xc[3 * (size_t)nb + 1] - m.xc[3 * (size_t)c + 1],
                          m.xc[3 * (size_t)nb + 2] - m.xc[3 * (size_t)c + 2]};
     const double ni = m.mu[c] / pc[0], nj = m.mu[nb] / pj[0];
-    return (li > lj ? li : lj) + 2.0 * (ni > nj ? ni : nj) / fabs(dot3(n, d));
+    const double lam = li > lj ? li : lj;
+    return m.euler ? lam : lam + 2.0 * (ni > nj ? ni : nj) / fabs(dot3(n, d));
   }
   const double *r = m.gen[c].f[s].r;
-  return li + 2.0 * (m.mu[c] / pc[0]) / fabs(dot3(n, r));
+  return m.euler ? li : li + 2.0 * (m.mu[c] / pc[0]) / fabs(dot3(n, r));
 }
 
 __global__ void diag_kernel(MacroGenArgs m) {

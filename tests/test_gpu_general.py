@@ -175,3 +175,18 @@ def test_gsis_cylinder_fp32_and_early_exit():
     o2.step()
     assert g2.stats()[1] == o2.macro_iters < 300
     scaled_close(g2.W(), o2.W(), 1e-10, "cylinder GSIS W with the inner tolerance")
+
+
+def test_euler_presteps_then_gsis_on_a_cylinder_fp64():
+    """The inviscid presteps at creation (slip wall, far field against the free stream), then
+    GSIS steps from the Maxwellian of their result, against the oracle."""
+    p = wl.cylinder(n_r=6, n_theta=12, nv=12, R=0.5, R_out=3.0, Ma=0.8, Kn=0.1)
+    g = gsis.Solver(p, precision="f64", mode="gsis", kinetic_presteps=0, n_sweeps=2, macro_steps=40, macro_tol=0.0,
+                    euler_presteps=60)
+    o = Oracle(p, mode=0, n_sweeps=2, macro_steps=40, macro_tol=0.0)
+    o.euler_presteps(60)
+    scaled_close(g.W(), o.W(), 1e-10, "W after the Euler presteps")
+    for it in range(2):
+        g.step()
+        o.step()
+        scaled_close(g.W(), o.W(), 1e-10, f"GSIS W after Euler presteps, step {it}")

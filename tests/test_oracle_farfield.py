@@ -109,3 +109,23 @@ def test_collisionless_reservoir_and_hot_wall(U):
     _, _, rw, fl = o.wall()
     assert rw[0] == pytest.approx(rho_w, rel=1e-7)
     assert abs(fl[0, 0]) < 1e-7  # no net mass flux into the wall
+
+
+def test_euler_presteps_converge_to_a_mirror_symmetric_cylinder_flow():
+    """The inviscid presteps on a cylinder O-grid in a stream along +x, run to their inner
+    tolerance: the grid and the flow are symmetric about the x axis (cell j mirrors cell
+    n - 1 - j), so the converged density and u_x are even and u_y odd (the red/black order is
+    not, so only the converged state is); the front stagnation point is compressed."""
+    n_t = 16
+    p = wl.cylinder(n_r=8, n_theta=n_t, nv=8, R=0.5, R_out=4.0, Ma=0.5, Kn=0.1)
+    o = Oracle(p, mode=0, macro_tol=1e-13)
+    W0 = o.W()
+    o.euler_presteps(600)
+    W = o.W().reshape(n_t, 8, 6)
+    M = W[::-1]  # azimuthal mirror image
+    assert o.macro_iters < 600  # converged below the inner tolerance
+    np.testing.assert_allclose(W[..., 0], M[..., 0], rtol=1e-12)
+    np.testing.assert_allclose(W[..., 1], M[..., 1], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(W[..., 2], -M[..., 2], rtol=1e-12, atol=1e-14)
+    front = W[n_t // 2 - 1: n_t // 2 + 1, 0, 0]  # the wall cells facing the stream (theta near pi)
+    assert (front > 1.05).all() and np.abs(W - W0.reshape(n_t, 8, 6)).max() > 1e-2

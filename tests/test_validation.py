@@ -115,3 +115,9 @@ def test_pseudo_time_step_only_in_the_kinetic_iteration():
     assert code(p, mode=gsis.MODE_DVM, kin_inv_dt=10.0) == gsis.GSIS_OK
     assert code(p, kin_inv_dt=10.0) == gsis.GSIS_E_UNSUPPORTED
     assert code(p, mode=gsis.MODE_DVM, kin_inv_dt=-1.0) == GSIS_E_INVALID
+
+
+def test_euler_presteps_on_general_meshes_only():
+    assert code(wl.cylinder(n_r=6, n_theta=12, nv=8), euler_presteps=100) == gsis.GSIS_OK
+    assert code(wl.cavity(n=6, nv=8), euler_presteps=100) == gsis.GSIS_E_UNSUPPORTED
+    assert code(wl.cylinder(n_r=6, n_theta=12, nv=8), euler_presteps=-1) == GSIS_E_INVALID
