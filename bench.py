@@ -269,6 +269,10 @@ BODIES = {
     # cylinder of diameter 1 in cross flow: 64 radial (first 0.01, R_out 10) x 128 azimuthal cells,
     # Ma 2, Kn 0.05, 40^3 velocities on [-9, 9]^3
     "cylinder": dict(kind="cylinder", n=(64, 1, 128), nv=40, vmax=9.0, Ma=2.0, Kn=0.05, first=0.01, R_out=10.0),
+    # subsonic cylinder for the GSIS outer step on a body (Euler presteps, then GSIS): 64 x 128
+    # cells, Ma 0.5, Kn 0.05, 40^3 velocities on [-6, 6]^3
+    "cylinder_gsis": dict(kind="cylinder", n=(64, 1, 128), nv=40, vmax=6.0, Ma=0.5, Kn=0.05, first=0.01, R_out=10.0,
+                          mode="gsis", euler_presteps=300),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }
@@ -299,7 +303,12 @@ def run_body(args):
     torch.cuda.set_device(local)
     p = body_problem(args.body)
     pts = p.ncells * p.nvel
-    kw = dict(precision=args.precision, mode="dvm", n_sweeps=BODY_SWEEPS, kin_inv_dt=BODY_INV_DT)
+    b = BODIES[args.body]
+    mode = b.get("mode", "dvm")
+    if mode == "gsis":
+        kw = dict(precision=args.precision, mode="gsis", n_sweeps=BODY_SWEEPS, euler_presteps=b["euler_presteps"])
+    else:
+        kw = dict(precision=args.precision, mode="dvm", n_sweeps=BODY_SWEEPS, kin_inv_dt=BODY_INV_DT)
     s = gsis.Solver(p, kinetic_presteps=0, **kw)
     for _ in range(args.warmup):
         s.step()
@@ -334,13 +343,15 @@ def run_body(args):
     kin_ms = phase[1] / max(nsteps, 1)
     ms = ms_total / args.steps
     line = {
-        "metric": f"phase-space updates/s (kinetic iteration, {args.body} O-grid)", "value": pts * args.steps / (ms_total / 1e3),
+        "metric": f"phase-space updates/s ({'GSIS outer step' if mode == 'gsis' else 'kinetic iteration'}, "
+                  f"{b['kind']} O-grid)", "value": pts * args.steps / (ms_total / 1e3),
         "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
         "config": {"workload": f"{p.name}: {BODIES[args.body]}", "precision": f"{args.precision} VDF",
                    "cells": p.ncells, "velocities": p.nvel, "points": pts, "n_sweeps": BODY_SWEEPS,
-                   "kin_inv_dt": BODY_INV_DT, "parallelism": "1 GPU",
+                   "mode": mode, "kin_inv_dt": kw.get("kin_inv_dt", 0.0),
+                   "euler_presteps": kw.get("euler_presteps", 0), "parallelism": "1 GPU",
                    "l2": f"inputs larger than L2 (VDF {pts * sbytes / 1e9:.2f} GB)", "eps_last": eps,
                    "rho_range": [float(W[:, 0].min()), float(W[:, 0].max())]},
         "phase_ms_per_step": {k: v / max(nsteps, 1) for k, v in zip(
@@ -364,22 +375,28 @@ def run_body(args):
 
 
 def body_oracle_sample(name):
-    """The oracle's kinetic iteration on the same mesh with 12^3 velocities (one step, all host
-    cores), scaled to updates/s."""
+    """The oracle on the same mesh with 12^3 velocities (one step of the same mode, all host
+    cores; the Euler presteps of a GSIS body untimed), scaled to updates/s."""
     from oracle.oracle import Oracle
+    from paper_2310_18916_gb300 import workloads as wl
 
     p = body_problem(name)
     b = BODIES[name]
-    from paper_2310_18916_gb300 import workloads as wl
     v, w = wl.midpoint_grid(12, -b["vmax"], b["vmax"])
     p.vx, p.vy, p.vz, p.wx, p.wy, p.wz = v, v.copy(), v.copy(), w, w.copy(), w.copy()
     cores = os.cpu_count() or 1
-    o = Oracle(p, mode=1, n_sweeps=BODY_SWEEPS, kin_inv_dt=BODY_INV_DT, nthreads=cores)
+    if b.get("mode", "dvm") == "gsis":
+        o = Oracle(p, mode=0, n_sweeps=BODY_SWEEPS, nthreads=cores)
+        o.euler_presteps(b["euler_presteps"])
+        what = "GSIS outer step (300 inner synthetic steps at most)"
+    else:
+        o = Oracle(p, mode=1, n_sweeps=BODY_SWEEPS, kin_inv_dt=BODY_INV_DT, nthreads=cores)
+        what = "kinetic-iteration step"
     t0 = time.perf_counter()
     o.step()
     dt = time.perf_counter() - t0
     return {"value": p.ncells * p.nvel / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one kinetic-iteration step of the same mesh with 12^3 velocities ({dt:.1f} s)"}
+            "sample": f"one {what} of the same mesh with 12^3 velocities ({dt:.1f} s)"}
 
 
 def run_serve(args):

@@ -442,7 +442,7 @@ __global__ void final_kernel(MacroGenArgs m) {
 
 int macro_general_parts(int nc) {
   int grid = (nc + kBlock - 1) / kBlock;
-  return grid > 1024 ? 1024 : grid;
+  return grid > 4096 ? 4096 : grid;
 }
 
 cudaError_t run_macro_general(const MacroGenArgs &m, cudaStream_t s) {
