@@ -84,6 +84,7 @@ struct gsis_solver {
   double *d_xc = nullptr, *d_kpart = nullptr;
   double *g_W = nullptr, *g_pr = nullptr, *g_mu = nullptr, *g_gW = nullptr, *g_phW = nullptr, *g_gP = nullptr;
   double *g_R = nullptr, *g_D = nullptr, *g_dW = nullptr, *g_F0 = nullptr, *g_part = nullptr;
+  double *g_Ff = nullptr, *g_gam = nullptr;
   int *g_flag = nullptr;
   int kin_grid = 0;
   size_t kin_scratch_bytes = 0;
@@ -253,6 +254,8 @@ struct gsis_solver {
     m.colcells = d_colcells;
     m.W = g_W; m.pr = g_pr; m.mu = g_mu; m.gW = g_gW; m.phW = g_phW; m.gP = g_gP;
     m.R = g_R; m.D = g_D; m.dW = g_dW; m.F0 = g_F0; m.part = g_part; m.flag = g_flag;
+    m.Ff = g_Ff;
+    m.gam = g_gam;
     m.Wout = d_Wnew;
     m.err = d_err;
     m.iters = d_iters;
@@ -408,7 +411,7 @@ struct gsis_solver {
       m.K = d_K;
       rc = cuda(run_macro_general(m, stream), "synthetic solve");
       if (rc) return rc;
-      launches += 2 + opt.macro_steps * (6 + 2 * opt.macro_sweeps);
+      launches += 2 + opt.macro_steps * (7 + 2 * opt.macro_sweeps);
     } else if (mode == GSIS_MODE_GSIS) {
       MacroArgs m{};
       m.g = kg;
@@ -1079,7 +1082,7 @@ static size_t footprint(const gsis_solver *s) {
   b += s->kin_scratch_bytes;                          // kinetic ring or work arrays in global memory
   if (s->general) b += nc * (sizeof(GenCell<double>) + 6 * (2 * sizeof(int) + 1)) + (size_t)s->nwall * 8;
   if (s->general && (s->opt.mode == GSIS_MODE_GSIS || s->opt.euler_presteps > 0))
-    b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36) * 8) +
+    b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36 + 36 + 6) * 8) +
          12 * 8 * (size_t)macro_general_parts((int)nc);
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
@@ -1125,6 +1128,8 @@ static int allocate_and_upload(gsis_solver *s) {
       A(s->g_D, 6 * nc * sizeof(double));
       A(s->g_dW, 6 * nc * sizeof(double));
       A(s->g_F0, 36 * nc * sizeof(double));
+      A(s->g_Ff, 36 * nc * sizeof(double));
+      A(s->g_gam, 6 * nc * sizeof(double));
       A(s->g_part, 12 * (size_t)macro_general_parts((int)nc) * sizeof(double));
       A(s->g_flag, 2 * sizeof(int));
     }

@@ -284,6 +284,8 @@ struct MacroGenArgs {
   const int *colcells;         // red cells then black cells
   // work
   double *W, *pr, *mu, *gW, *phW, *gP, *R, *D, *dW, *F0, *part;
+  double *Ff;                  // [cell][6][6]: interior face fluxes, then F(W_j) . n for the sweeps
+  double *gam;                 // [cell][6] gamma of each interior face for the sweeps
   int *flag;                   // [0] early exit fired, [1] inner steps used
   double *Wout;                // [cell][6] prim W^{n+1}
   int *err, *iters;

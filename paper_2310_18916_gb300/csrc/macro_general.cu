@@ -5,6 +5,7 @@
 //   prim     primitives and viscosity of W;
 //   grad     least-squares gradients of the conservative fields with their Venkatakrishnan
 //            limiters, and of the primitives u, T_t, T_r;
+//   face     each interior face flux once (the other cell takes its negative);
 //   resid    R_i = -(1/V_i) [K_i + sum_faces (F_f - F_f^0) A_f] + Q_i: K_i the area-integrated
 //            outward kinetic flux of the last kinetic step summed over the cell's faces, F_f the
 //            face flux of this scheme (Rusanov + NSF between the two reconstructed states; a
@@ -255,6 +256,21 @@ __global__ void grad_kernel(MacroGenArgs m) {
   }
 }
 
+// Interior faces once each, from the cell on their lower side (the upper sides 1, 3, 5 of every
+// cell): the flux seen from the other cell is its exact negative (opposite normal, swapped
+// states), so each cell's residual reads it instead of computing it again.
+__global__ void face_kernel(MacroGenArgs m) {
+  if (done(m)) return;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * m.nc; t += gridDim.x * blockDim.x) {
+    const int c = t / 3, s = 2 * (t - 3 * c) + 1;
+    const int nb = m.gnb[6 * (size_t)c + s];
+    if (nb < 0) continue;
+    const double *S = m.gen[c].f[s].S;
+    const double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
+    face_flux(m, c, s, nb, n, m.Ff + 36 * (size_t)c + 6 * s);
+  }
+}
+
 __global__ void resid_kernel(MacroGenArgs m, int step) {
   if (done(m)) return;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
@@ -275,6 +291,9 @@ __global__ void resid_kernel(MacroGenArgs m, int step) {
         for (int a = 0; a < 3; ++a) F[1 + a] = pt * n[a];
       } else if (nb == NB_WALL) {
         wall_eq_flux(m, s, m.pr + 6 * (size_t)c, n, F);
+      } else if (nb >= 0) {
+        const double *Fs = (s & 1) ? m.Ff + 36 * (size_t)c + 6 * s : m.Ff + 36 * (size_t)nb + 6 * (s ^ 1);
+        for (int k = 0; k < 6; ++k) F[k] = (s & 1) ? Fs[k] : -Fs[k];
       } else {
         face_flux(m, c, s, nb, n, F);
       }
@@ -330,7 +349,13 @@ __global__ void diag_kernel(MacroGenArgs m) {
       const double *S = g.f[s].S;
       const double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
       lsum += (fabs(p[1] * n[0] + p[2] * n[1] + p[3] * n[2]) + sound(p[4])) * A;
-      gsum += face_gamma(m, c, s, nb, n) * A;
+      const double gam = face_gamma(m, c, s, nb, n);
+      gsum += gam * A;
+      if (nb >= 0) {
+        // what the sweeps need of this neighbour, fixed during them: gamma and F(W_j) . n
+        m.gam[6 * (size_t)c + s] = gam;
+        euler_flux(m, m.W + 6 * (size_t)nb, n, m.Ff + 36 * (size_t)c + 6 * s);
+      }
     }
     const double V = m.vol[c];
     const double dt = m.cfl * V / lsum;
@@ -354,11 +379,11 @@ __global__ void sweep_kernel(MacroGenArgs m, int first, int count) {
       if (nb < 0) continue;
       const double *S = g.f[s].S;
       const double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
-      const double gam = face_gamma(m, c, s, nb, n);
-      double Wn[6], F1[6], F0[6];
+      const double gam = m.gam[6 * (size_t)c + s];
+      const double *F0 = m.Ff + 36 * (size_t)c + 6 * s;
+      double Wn[6], F1[6];
       for (int k = 0; k < 6; ++k) Wn[k] = m.W[6 * (size_t)nb + k] + m.dW[6 * (size_t)nb + k];
       euler_flux(m, Wn, n, F1);
-      euler_flux(m, m.W + 6 * (size_t)nb, n, F0);
       for (int k = 0; k < m.nW; ++k) acc[k] -= ((F1[k] - F0[k]) - gam * m.dW[6 * (size_t)nb + k]) * A / (2.0 * V);
     }
     for (int k = 0; k < m.nW; ++k) m.dW[6 * (size_t)c + k] = acc[k] / m.D[6 * (size_t)c + k];
@@ -451,6 +476,7 @@ cudaError_t run_macro_general(const MacroGenArgs &m, cudaStream_t s) {
   for (int step = 0; step < m.steps; ++step) {
     prim_kernel<<<grid, kBlock, 0, s>>>(m);
     grad_kernel<<<grid, kBlock, 0, s>>>(m);
+    face_kernel<<<grid, kBlock, 0, s>>>(m);
     resid_kernel<<<grid, kBlock, 0, s>>>(m, step);
     diag_kernel<<<grid, kBlock, 0, s>>>(m);
     for (int sw = 0; sw < m.sweeps; ++sw) {
