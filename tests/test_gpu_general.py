@@ -190,3 +190,23 @@ def test_euler_presteps_then_gsis_on_a_cylinder_fp64():
         g.step()
         o.step()
         scaled_close(g.W(), o.W(), 1e-10, f"GSIS W after Euler presteps, step {it}")
+
+
+def test_free_molecular_cylinder_drag_on_gpu():
+    """The GPU's wall loads on the cylinder at Kn = 1e6 against the discrete free-molecular force
+    (the closed form of tests/test_oracle_farfield.py), FP64 and FP32."""
+    from test_oracle_farfield import cylinder_free_molecular, free_molecular_force
+
+    p = cylinder_free_molecular()
+    S = Oracle(p, mode=1).geometry()[2].reshape(32, 10, 6, 3)[:, 0, 0, :]
+    exact = free_molecular_force(p, S, p.wall_u[1], p.wall_T[0])
+    U = p.wall_u[1][0]
+    for precision, rel in (("f64", 1e-4), ("f32", 2e-4)):
+        g = gsis.Solver(p, precision=precision, mode="dvm", kinetic_presteps=0, n_sweeps=2, kin_inv_dt=2.0)
+        for _ in range(15):
+            g.step()
+        out = g.wall_loads([0], (1.0, 0.0, 0.0), 1.0, U, 1.0)
+        g.close()
+        assert abs(out[0] - exact[0]) < rel * exact[0], precision
+        assert abs(out[1]) < 1e-6 * exact[0], precision
+        assert out[4] == pytest.approx(out[0] / (0.5 * U * U), rel=1e-12)
