@@ -283,7 +283,7 @@ struct MacroGenArgs {
   const double *K;             // [cell][6] area-integrated outward kinetic flux summed over the faces
   const int *colcells;         // red cells then black cells
   // work
-  double *W, *pr, *mu, *gW, *phW, *gP, *R, *D, *dW, *F0, *part;
+  double *W, *pr, *mu, *gW, *phW, *gP, *R, *D, *dW, *F0, *part;  // D: the inverse LU-SGS diagonal
   double *Ff;                  // [cell][6][6]: interior face fluxes, then F(W_j) . n for the sweeps
   double *gam;                 // [cell][6] gamma of each interior face for the sweeps
   int *flag;                   // [0] early exit fired, [1] inner steps used

@@ -37,15 +37,16 @@ __device__ __forceinline__ double dot3(const double *a, const double *b) { retur
 
 // primitives rho, u, T_t, T_r of conservative W (rho, rho u, rho E, rho E_r), E = |u|^2/2 +
 // 3 T_t / 4 (+ d_r T_r / 4 in rho E_r)
+// (one reciprocal of rho: FP64 divisions cost several FP64 instructions each on this GPU)
 __device__ void prim_of(const MacroGenArgs &m, const double *W, double *p) {
-  const double rho = W[0], u0 = W[1] / rho, u1 = W[2] / rho, u2 = W[3] / rho;
+  const double rho = W[0], ir = 1.0 / rho, u0 = W[1] * ir, u1 = W[2] * ir, u2 = W[3] * ir;
   const double Er = m.nW == 6 ? W[5] : 0.0;
   p[0] = rho;
   p[1] = u0;
   p[2] = u1;
   p[3] = u2;
-  p[4] = (W[4] - 0.5 * rho * (u0 * u0 + u1 * u1 + u2 * u2) - Er) / (0.75 * rho);
-  p[5] = m.nW == 6 ? Er / (m.d_r * rho / 4.0) : p[4];
+  p[4] = (W[4] - 0.5 * rho * (u0 * u0 + u1 * u1 + u2 * u2) - Er) * (ir * (4.0 / 3.0));
+  p[5] = m.nW == 6 ? Er * (ir * (4.0 / m.d_r)) : p[4];
 }
 
 __device__ void cons_of(const MacroGenArgs &m, const double *p, double *W) {
@@ -266,7 +267,7 @@ __global__ void face_kernel(MacroGenArgs m) {
     const int nb = m.gnb[6 * (size_t)c + s];
     if (nb < 0) continue;
     const double *S = m.gen[c].f[s].S;
-    const double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
+    const double A = sqrt(dot3(S, S)), iA = 1.0 / A, n[3] = {S[0] * iA, S[1] * iA, S[2] * iA};
     face_flux(m, c, s, nb, n, m.Ff + 36 * (size_t)c + 6 * s);
   }
 }
@@ -281,7 +282,7 @@ __global__ void resid_kernel(MacroGenArgs m, int step) {
       const int nb = m.gnb[6 * (size_t)c + s];
       if (nb == NB_ABSENT || nb == NB_AXIS) continue;
       const double *S = g.f[s].S;
-      const double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
+      const double A = sqrt(dot3(S, S)), iA = 1.0 / A, n[3] = {S[0] * iA, S[1] * iA, S[2] * iA};
       double F[6];
       if (nb == NB_WALL && m.euler) {
         // slip wall: the pressure of the cell
@@ -347,7 +348,7 @@ __global__ void diag_kernel(MacroGenArgs m) {
       const int nb = m.gnb[6 * (size_t)c + s];
       if (nb == NB_ABSENT || nb == NB_AXIS) continue;
       const double *S = g.f[s].S;
-      const double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
+      const double A = sqrt(dot3(S, S)), iA = 1.0 / A, n[3] = {S[0] * iA, S[1] * iA, S[2] * iA};
       lsum += (fabs(p[1] * n[0] + p[2] * n[1] + p[3] * n[2]) + sound(p[4])) * A;
       const double gam = face_gamma(m, c, s, nb, n);
       gsum += gam * A;
@@ -361,7 +362,8 @@ __global__ void diag_kernel(MacroGenArgs m) {
     const double dt = m.cfl * V / lsum;
     double srcdiag = 0.0;
     if (m.nW == 6) srcdiag = 1.0 / (m.Z_r * (2.0 * m.mu0 * pow(p[4], m.omega - 1.0) / p[0]));
-    for (int k = 0; k < 6; ++k) m.D[6 * (size_t)c + k] = 1.0 / dt + gsum / (2.0 * V) + (k == 5 ? srcdiag : 0.0);
+    // the sweeps multiply by the inverse diagonal
+    for (int k = 0; k < 6; ++k) m.D[6 * (size_t)c + k] = 1.0 / (1.0 / dt + gsum / (2.0 * V) + (k == 5 ? srcdiag : 0.0));
     for (int k = 0; k < 6; ++k) m.dW[6 * (size_t)c + k] = 0.0;
   }
 }
@@ -371,22 +373,22 @@ __global__ void sweep_kernel(MacroGenArgs m, int first, int count) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
     const int c = m.colcells[first + t];
     const GenCell<double> &g = m.gen[c];
-    const double V = m.vol[c];
     double acc[6];
     for (int k = 0; k < 6; ++k) acc[k] = m.R[6 * (size_t)c + k];
     for (int s = 0; s < 6; ++s) {
       const int nb = m.gnb[6 * (size_t)c + s];
       if (nb < 0) continue;
       const double *S = g.f[s].S;
-      const double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A};
+      const double A = sqrt(dot3(S, S)), iA = 1.0 / A, n[3] = {S[0] * iA, S[1] * iA, S[2] * iA};
       const double gam = m.gam[6 * (size_t)c + s];
       const double *F0 = m.Ff + 36 * (size_t)c + 6 * s;
       double Wn[6], F1[6];
       for (int k = 0; k < 6; ++k) Wn[k] = m.W[6 * (size_t)nb + k] + m.dW[6 * (size_t)nb + k];
       euler_flux(m, Wn, n, F1);
-      for (int k = 0; k < m.nW; ++k) acc[k] -= ((F1[k] - F0[k]) - gam * m.dW[6 * (size_t)nb + k]) * A / (2.0 * V);
+      const double kA = 0.5 * A * g.invV;
+      for (int k = 0; k < m.nW; ++k) acc[k] -= ((F1[k] - F0[k]) - gam * m.dW[6 * (size_t)nb + k]) * kA;
     }
-    for (int k = 0; k < m.nW; ++k) m.dW[6 * (size_t)c + k] = acc[k] / m.D[6 * (size_t)c + k];
+    for (int k = 0; k < m.nW; ++k) m.dW[6 * (size_t)c + k] = acc[k] * m.D[6 * (size_t)c + k];
   }
 }
 
