@@ -231,7 +231,10 @@ int gsis_wall_loads(gsis_handle h, unsigned side_mask, const double *dir, double
 /* Per cell the sum over its faces of the outward kinetic face flux of the last kinetic step
  * (mass, momentum(3), energy, internal energy; area-integrated): the kinetic information the
  * synthetic solve uses (Eq. full_constitutive evaluated with the kinetic scheme's own fluxes).
- * host_out holds ncells x 6 doubles. */
+ * host_out holds ncells x 6 doubles.  Rectilinear blocks obtain it from the collision moments
+ * (exact there: one colour pass solves the implicit system); general blocks sum the face fluxes
+ * in GSIS mode, and in DVM mode report the collision-moment form, which a finite number of
+ * colour passes satisfies only approximately. */
 int gsis_kinetic_flux_sum(gsis_handle h, double *host_out, size_t out_len);
 
 /* VDF transfer, FP64 host arrays [cell][v] (f1 for the Rykov model only, else NULL).
