@@ -369,7 +369,8 @@ static int far_inflow(const orc_solver *s, int i, int side) {
 /* Face values (f, and f1 for Rykov) entering the domain through the boundary face (i, side)
    for velocity xi: at a wall the re-emitted rho_w M_w (f1 = (d_r T_w / 4) f); at a far field
    the free-stream Maxwellian where the free stream does not leave through the face
-   (U_inf . S <= 0), else the cell's own face values own[] (zero gradient). */
+   (U_inf . S <= 0), else the cell's own values own[] (zero gradient: the first-order value,
+   which keeps the interior gradient out of the boundary condition). */
 static void boundary_in(const orc_solver *s, int i, int side, const double *xi, const double own[2], double e[2]) {
   if (s->nb[6 * i + side] == -1) {
     double M = s->rho_w[s->wid[6 * i + side]] * wall_maxwellian(s, side, xi);
@@ -434,7 +435,7 @@ static void kinetic_velocity(orc_solver *s, int v, kin_work *wk) {
           for (int q = 0; q < s->nvdf; ++q) flux[q] += sn * wk->ff[((size_t)q * nc + j) * 6 + opp];
         } else {
           double own[2] = {0.0, 0.0}, e[2];
-          for (int q = 0; q < s->nvdf; ++q) own[q] = wk->ff[((size_t)q * nc + i) * 6 + side];
+          for (int q = 0; q < s->nvdf; ++q) own[q] = fq[q][i];
           boundary_in(s, i, side, xi, own, e);
           for (int q = 0; q < s->nvdf; ++q) flux[q] += sn * e[q];
         }
@@ -480,7 +481,7 @@ static void kinetic_velocity(orc_solver *s, int v, kin_work *wk) {
               e[q] = wk->ff[((size_t)q * nc + j) * 6 + (side ^ 1)] + wk->df[(size_t)q * nc + j];
           } else {
             double own[2] = {0.0, 0.0};
-            for (int q = 0; q < s->nvdf; ++q) own[q] = wk->ff[((size_t)q * nc + i) * 6 + side];
+            for (int q = 0; q < s->nvdf; ++q) own[q] = fq[q][i];
             boundary_in(s, i, side, xi, own, e);
             if (s->nvdf == 1) e[1] = 0.0;
           }

@@ -1133,9 +1133,9 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
             e[0] = M;
             if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
           } else {
-            // far field where the free stream leaves: the cell's own face value
+            // far field where the free stream leaves: the cell's own value (zero gradient)
 #pragma unroll
-            for (int q = 0; q < NV; ++q) e[q] = FF(c, q, s);
+            for (int q = 0; q < NV; ++q) e[q] = FC(c, q);
           }
         } else {
           continue;
@@ -1224,7 +1224,7 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
               if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
             } else {
 #pragma unroll
-              for (int q = 0; q < NV; ++q) e[q] = FF(c, q, s);
+              for (int q = 0; q < NV; ++q) e[q] = fi[q];
             }
           } else {
             continue;
