@@ -62,9 +62,8 @@ enum gsis_mode { GSIS_MODE_GSIS = 0, GSIS_MODE_DVM = 1 };
  * Axes with one cell come after the others.  A rectilinear block (node x depends on I only,
  * y on J, z on K, increasing) with WALL sides and one-cell periodic axes takes the rectilinear
  * kernels; any other block (curvilinear, far field, pole or wrapped sides) takes the general
- * ones, with n_sweeps colour passes per kinetic step, in both modes on one device (velocity
- * sharding on such blocks returns GSIS_E_UNSUPPORTED).  Cells must have positive volume, else
- * GSIS_E_INVALID. */
+ * ones, with n_sweeps colour passes per kinetic step, in both modes and velocity-sharded alike.
+ * Cells must have positive volume, else GSIS_E_INVALID. */
 typedef struct {
   int ni, nj, nk;
   const double *nodes;

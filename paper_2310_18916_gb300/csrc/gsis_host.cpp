@@ -81,7 +81,7 @@ struct gsis_solver {
   std::vector<double> xc64;
   // general meshes, GSIS mode: FP64 geometry and the synthetic solve's work arrays
   GenCell<double> *d_gen64 = nullptr;
-  double *d_xc = nullptr, *d_kpart = nullptr;
+  double *d_xc = nullptr, *d_kpart = nullptr, *d_wden = nullptr;
   double *g_W = nullptr, *g_pr = nullptr, *g_mu = nullptr, *g_gW = nullptr, *g_phW = nullptr, *g_gP = nullptr;
   double *g_R = nullptr, *g_D = nullptr, *g_dW = nullptr, *g_F0 = nullptr, *g_part = nullptr;
   double *g_Ff = nullptr, *g_gam = nullptr;
@@ -220,6 +220,7 @@ struct gsis_solver {
     a.gwid = d_gwid;
     a.gin = d_gin;
     a.n_sweeps = opt.n_sweeps;
+    a.wden = d_wden;
     return a;
   }
 
@@ -406,6 +407,7 @@ struct gsis_solver {
     if (mode == GSIS_MODE_GSIS && general) {
       // the kinetic face fluxes summed per cell, then the general synthetic solve
       rc = cuda(launch_sum_kpart(d_kpart, kin_grid, (int)nc, d_K, stream), "kinetic flux sums");
+      if (!rc) rc = exchange(d_K, (size_t)nc * 6, "kinetic flux sums");
       if (rc) return rc;
       MacroGenArgs m = macro_general_args();
       m.K = d_K;
@@ -640,10 +642,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     why = "Euler presteps are built on general meshes only";
     return GSIS_E_UNSUPPORTED;
   }
-  if (general) {
-    if (o->shard_count > 1) { why = "velocity sharding is built for rectilinear meshes only"; return GSIS_E_UNSUPPORTED; }
-    return GSIS_OK;  // volumes are checked when the geometry is built
-  }
+  if (general) return GSIS_OK;  // volumes are checked when the geometry is built
   const int N0 = m->ni + 1, N1 = m->nj + 1, N2 = m->nk + 1;
   auto node = [&](int I, int J, int K, int d) { return m->nodes[3 * ((size_t)I + (size_t)N0 * ((size_t)J + (size_t)N1 * K)) + d]; };
   (void)N2;
@@ -1114,6 +1113,7 @@ static int allocate_and_upload(gsis_solver *s) {
     A(s->d_gwid, 6 * nc * sizeof(int));
     A(s->d_gin, 6 * nc);
     A(s->d_wall_area, (size_t)(s->nwall + 1) * sizeof(double));
+    A(s->d_wden, (size_t)(s->nwall + 1) * sizeof(double));
     if (s->opt.mode == GSIS_MODE_GSIS || s->opt.euler_presteps > 0) {
       A(s->d_gen64, nc * sizeof(GenCell<double>));
       A(s->d_xc, 3 * nc * sizeof(double));
@@ -1218,6 +1218,10 @@ static int allocate_and_upload(gsis_solver *s) {
     if (!rc) rc = s->upload(s->d_gwid, s->gwid.data(), 6 * nc * sizeof(int));
     if (!rc) rc = s->upload(s->d_gin, s->gin.data(), 6 * nc);
     if (!rc && s->nwall) rc = s->upload(s->d_wall_area, s->wall_area.data(), s->nwall * sizeof(double));
+    if (!rc && s->nwall)
+      rc = s->cuda(launch_wall_den_general<T, S>(s->kin_args<T, S>(), s->d_vel64, s->nslots_all, s->d_wall_cell,
+                                                 s->d_wall_side, s->nwall, s->d_wden, s->stream),
+                   "wall denominators");
     if (!rc && s->d_gen64) rc = s->upload(s->d_gen64, s->gen64.data(), nc * sizeof(GenCell<double>));
     if (!rc && s->d_xc) rc = s->upload(s->d_xc, s->xc64.data(), 3 * nc * sizeof(double));
   }

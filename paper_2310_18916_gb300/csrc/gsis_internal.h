@@ -121,6 +121,8 @@ struct KinArgs {
   int n_sweeps;             // point-implicit passes over the colours
   double *kpart;            // [CTA][cell][6] per-CTA sums of the outward kinetic face fluxes
                             // (area-integrated, over the cell's faces); nullptr: not wanted
+  const double *wden;       // [wall face] re-emission flux of M(u_w, T_w) over every velocity
+                            // (all shards), the denominator of rho_w
 };
 
 // ---- launchers (defined in the .cu files) ----
@@ -152,6 +154,11 @@ template <typename T, typename S>
 cudaError_t kinetic_general_shape(int nvdf, int nact, int *ctas_per_sm);
 template <typename T, typename S>
 size_t kinetic_general_stride(int nc, int nvdf, int nact);
+// general meshes: per wall face, the flux of the wall Maxwellian leaving the wall summed over
+// every velocity slot (nslots_all of vel64, all shards), the denominator of rho_w
+template <typename T, typename S>
+cudaError_t launch_wall_den_general(const KinArgs<T, S> &a, const double *vel64, int nslots_all, const int *wall_cell,
+                                    const int *wall_side, int nwall, double *wden, cudaStream_t s);
 // K [cell][6] = sum over the CTAs of kpart (fixed order)
 cudaError_t launch_sum_kpart(const double *kpart, int nparts, int nc, double *K, cudaStream_t s);
 template <typename T, typename S>

@@ -1344,8 +1344,42 @@ __global__ void __launch_bounds__(256) wall_prepass_general_kernel(const KinArgs
       n += red[0][k];
       d += red[1][k];
     }
-    rho_w[w] = n / d;
+    // a velocity shard holds part of the numerator; the denominator covers every velocity
+    rho_w[w] = n / (A.wden ? A.wden[w] : d);
   }
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) wall_den_general_kernel(const KinArgs<T, S> A, const double *vel64, int nslots,
+                                                               const int *wall_cell, const int *wall_side,
+                                                               double *wden) {
+  __shared__ double red[8];
+  const int w = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = wall_cell[w], side = wall_side[w];
+  const GenFace<T> &fa = A.gen[c].f[side];
+  const double *uT = A.wall_uT + 4 * side;
+  double den = 0.0;
+  for (int v = threadIdx.x; v < nslots; v += blockDim.x) {
+    const T x = (T)vel64[4 * v], y = (T)vel64[4 * v + 1], z = (T)vel64[4 * v + 2], wv = (T)vel64[4 * v + 3];
+    const T sn = dot_xi(fa.S, x, y, z);
+    if (sn < (T)0) den += (double)(wv * -sn * wall_maxwellian<T>(uT, x, y, z));
+  }
+  for (int o = 16; o > 0; o >>= 1) den += __shfl_xor_sync(0xffffffffu, den, o);
+  if (lane == 0) red[warp] = den;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double d = 0.0;
+    for (int k = 0; k < 8; ++k) d += red[k];
+    wden[w] = d;
+  }
+}
+
+template <typename T, typename S>
+cudaError_t launch_wall_den_general(const KinArgs<T, S> &a, const double *vel64, int nslots_all, const int *wall_cell,
+                                    const int *wall_side, int nwall, double *wden, cudaStream_t s) {
+  if (nwall == 0) return cudaSuccess;
+  wall_den_general_kernel<T, S><<<nwall, 256, 0, s>>>(a, vel64, nslots_all, wall_cell, wall_side, wden);
+  return cudaGetLastError();
 }
 
 __global__ void sum_kpart_kernel(const double *kpart, int nparts, int nc, double *K) {
@@ -1415,7 +1449,9 @@ cudaError_t launch_wall_prepass_general(const KinArgs<T, S> &a, const int *wall_
   template cudaError_t kinetic_general_shape<T, S>(int, int, int *);                                             \
   template size_t kinetic_general_stride<T, S>(int, int, int);                                                   \
   template cudaError_t launch_wall_prepass_general<T, S>(const KinArgs<T, S> &, const int *, const int *, int,   \
-                                                         double *, cudaStream_t);
+                                                         double *, cudaStream_t);                                \
+  template cudaError_t launch_wall_den_general<T, S>(const KinArgs<T, S> &, const double *, int, const int *,    \
+                                                     const int *, int, double *, cudaStream_t);
 GSIS_INST(float, float)
 GSIS_INST(double, double)
 GSIS_INST(float, __nv_bfloat16)

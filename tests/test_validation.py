@@ -32,7 +32,6 @@ def test_curved_mesh_takes_the_general_path():
     nodes[..., 0] += 0.01 * nodes[..., 1]  # x depends on J: not rectilinear
     q = dataclasses.replace(p, nodes=nodes)
     assert code(q) == gsis.GSIS_OK and code(q, mode=gsis.MODE_DVM) == gsis.GSIS_OK
-    assert code(q, shard=(0, 2)) == gsis.GSIS_E_UNSUPPORTED
 
 
 def test_non_increasing_nodes_are_rejected():
@@ -49,7 +48,7 @@ def test_boundary_conditions_must_match_the_axis():
     assert code(dataclasses.replace(p, bc=bc)) == GSIS_E_INVALID
     bc[1] = wl.PERIODIC  # a wrapped axis takes the general path
     assert code(dataclasses.replace(p, bc=bc)) == gsis.GSIS_OK
-    assert code(dataclasses.replace(p, bc=bc), shard=(0, 2)) == gsis.GSIS_E_UNSUPPORTED
+    assert code(dataclasses.replace(p, bc=bc), shard=(0, 2)) == gsis.GSIS_OK
     bc = list(p.bc)
     bc[4] = wl.WALL  # an axis with one cell must be PERIODIC on both sides
     assert code(dataclasses.replace(p, bc=bc)) == GSIS_E_INVALID
@@ -59,13 +58,13 @@ def test_boundary_conditions_must_match_the_axis():
 
 
 def test_general_meshes_are_accepted():
-    """O-grids (far field, pole and wrapped sides) are accepted in both modes on one device, with
-    several colour passes; velocity sharding on them is not built."""
+    """O-grids (far field, pole and wrapped sides) are accepted in both modes, with several colour
+    passes, and velocity-sharded."""
     for p in (wl.cylinder(n_r=6, n_theta=12, nv=8), wl.sphere(n_r=4, n_pol=4, n_az=6, nv=8),
               wl.reservoir_wall(n_cells=6, nv=8)):
         assert code(p, mode=gsis.MODE_DVM, n_sweeps=3) == gsis.GSIS_OK, p.name
         assert code(p) == gsis.GSIS_OK, p.name
-        assert code(p, shard=(0, 2)) == gsis.GSIS_E_UNSUPPORTED, p.name
+        assert code(p, shard=(0, 2)) == gsis.GSIS_OK, p.name
         # the synthetic solve's work arrays count in GSIS mode only
         assert gsis.footprint_bytes(p) > gsis.footprint_bytes(p, mode=gsis.MODE_DVM), p.name
         assert code(p, mode=gsis.MODE_DVM, n_sweeps=0) == GSIS_E_INVALID, p.name
