@@ -54,7 +54,8 @@ enum gsis_mode { GSIS_MODE_GSIS = 0, GSIS_MODE_DVM = 1 };
  *             temperature wall_T[side];
  *   PERIODIC  on both sides of an axis.  An axis with one cell must be PERIODIC (it then carries
  *             no transport); with at least 3 cells the axis closes on itself, the two ends being
- *             neighbours (the azimuth of an O-grid: the mesh geometry already joins them);
+ *             neighbours (the azimuth of an O-grid: the mesh geometry already joins them), and
+ *             GSIS mode and Euler presteps need an even cell count on it;
  *   FARFIELD  free stream of density 1, velocity wall_u[side] and temperature wall_T[side]:
  *             molecules entering through a face carry its Maxwellian where the free stream does
  *             not leave through the face, else the cell's own face value;

@@ -84,7 +84,7 @@ struct gsis_solver {
   double *d_xc = nullptr, *d_kpart = nullptr, *d_wden = nullptr;
   double *g_W = nullptr, *g_pr = nullptr, *g_mu = nullptr, *g_gW = nullptr, *g_phW = nullptr, *g_gP = nullptr;
   double *g_R = nullptr, *g_D = nullptr, *g_dW = nullptr, *g_F0 = nullptr, *g_part = nullptr;
-  double *g_Ff = nullptr, *g_gam = nullptr;
+  double *g_Ff = nullptr, *g_gam = nullptr, *g_FW0 = nullptr, *g_FW = nullptr;
   int *g_flag = nullptr;
   int kin_grid = 0;
   size_t kin_scratch_bytes = 0;
@@ -257,6 +257,8 @@ struct gsis_solver {
     m.R = g_R; m.D = g_D; m.dW = g_dW; m.F0 = g_F0; m.part = g_part; m.flag = g_flag;
     m.Ff = g_Ff;
     m.gam = g_gam;
+    m.FW0 = g_FW0;
+    m.FW = g_FW;
     m.Wout = d_Wnew;
     m.err = d_err;
     m.iters = d_iters;
@@ -631,6 +633,12 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
         return GSIS_E_INVALID;
       }
       if (lo == GSIS_BC_PERIODIC && n[a] < 3) { why = "a wrapped axis needs at least 3 cells"; return GSIS_E_INVALID; }
+      // the synthetic solve updates red and black cells (i+j+k even / odd) in parallel: across
+      // the wrap of an odd axis two neighbours share a colour
+      if (lo == GSIS_BC_PERIODIC && (n[a] & 1) && (o->mode == GSIS_MODE_GSIS || o->euler_presteps > 0)) {
+        why = "the synthetic solve needs an even number of cells on a wrapped axis";
+        return GSIS_E_UNSUPPORTED;
+      }
     }
   }
   for (int s = 0; s < 6; ++s)
@@ -1081,7 +1089,7 @@ static size_t footprint(const gsis_solver *s) {
   b += s->kin_scratch_bytes;                          // kinetic ring or work arrays in global memory
   if (s->general) b += nc * (sizeof(GenCell<double>) + 6 * (2 * sizeof(int) + 1)) + (size_t)s->nwall * 8;
   if (s->general && (s->opt.mode == GSIS_MODE_GSIS || s->opt.euler_presteps > 0))
-    b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36 + 36 + 6) * 8) +
+    b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36 + 36 + 6 + 36) * 8) +
          12 * 8 * (size_t)macro_general_parts((int)nc);
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
   b += nc * NST * (T + 8);                    // states
@@ -1130,6 +1138,8 @@ static int allocate_and_upload(gsis_solver *s) {
       A(s->g_F0, 36 * nc * sizeof(double));
       A(s->g_Ff, 36 * nc * sizeof(double));
       A(s->g_gam, 6 * nc * sizeof(double));
+      A(s->g_FW0, 18 * nc * sizeof(double));
+      A(s->g_FW, 18 * nc * sizeof(double));
       A(s->g_part, 12 * (size_t)macro_general_parts((int)nc) * sizeof(double));
       A(s->g_flag, 2 * sizeof(int));
     }

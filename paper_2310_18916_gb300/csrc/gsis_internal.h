@@ -291,8 +291,9 @@ struct MacroGenArgs {
   const int *colcells;         // red cells then black cells
   // work
   double *W, *pr, *mu, *gW, *phW, *gP, *R, *D, *dW, *F0, *part;  // D: the inverse LU-SGS diagonal
-  double *Ff;                  // [cell][6][6]: interior face fluxes, then F(W_j) . n for the sweeps
+  double *Ff;                  // [cell][6][6]: interior face fluxes
   double *gam;                 // [cell][6] gamma of each interior face for the sweeps
+  double *FW0, *FW;            // [cell][3][6] axis fluxes at W and at W + dW for the sweeps
   int *flag;                   // [0] early exit fired, [1] inner steps used
   double *Wout;                // [cell][6] prim W^{n+1}
   int *err, *iters;

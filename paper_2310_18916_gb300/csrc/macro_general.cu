@@ -73,6 +73,21 @@ __device__ void euler_flux(const MacroGenArgs &m, const double *W, const double 
   F[5] = m.nW == 6 ? W[5] * un : 0.0;
 }
 
+// the convective flux along each axis, F_a (a = x, y, z): F . n = sum_a F_a n_a
+__device__ void axis_fluxes(const MacroGenArgs &m, const double *W, double *Fa) {
+  double p[6];
+  prim_of(m, W, p);
+  const double pt = 0.5 * p[0] * p[4];
+  for (int a = 0; a < 3; ++a) {
+    const double ua = p[1 + a];
+    double *F = Fa + 6 * a;
+    F[0] = W[0] * ua;
+    for (int b = 0; b < 3; ++b) F[1 + b] = W[1 + b] * ua + (a == b ? pt : 0.0);
+    F[4] = (W[4] + pt) * ua;
+    F[5] = m.nW == 6 ? W[5] * ua : 0.0;
+  }
+}
+
 __device__ __forceinline__ double sound(double Tt) { return sqrt(Tt * (5.0 / 6.0)); }
 
 // Eq. mu_kappa with R = 1/2: (kt, kr) = (mu / 4) A^{-1} (5, d_r); Shakhov: A_tt = 2/3, no kr
@@ -352,12 +367,11 @@ __global__ void diag_kernel(MacroGenArgs m) {
       lsum += (fabs(p[1] * n[0] + p[2] * n[1] + p[3] * n[2]) + sound(p[4])) * A;
       const double gam = face_gamma(m, c, s, nb, n);
       gsum += gam * A;
-      if (nb >= 0) {
-        // what the sweeps need of this neighbour, fixed during them: gamma and F(W_j) . n
-        m.gam[6 * (size_t)c + s] = gam;
-        euler_flux(m, m.W + 6 * (size_t)nb, n, m.Ff + 36 * (size_t)c + 6 * s);
-      }
+      if (nb >= 0) m.gam[6 * (size_t)c + s] = gam;  // fixed during the sweeps
     }
+    // this cell's axis fluxes at W (the sweeps' base) and at W + dW (dW = 0 until it is updated)
+    axis_fluxes(m, m.W + 6 * (size_t)c, m.FW0 + 18 * (size_t)c);
+    for (int k = 0; k < 18; ++k) m.FW[18 * (size_t)c + k] = m.FW0[18 * (size_t)c + k];
     const double V = m.vol[c];
     const double dt = m.cfl * V / lsum;
     double srcdiag = 0.0;
@@ -381,14 +395,21 @@ __global__ void sweep_kernel(MacroGenArgs m, int first, int count) {
       const double *S = g.f[s].S;
       const double A = sqrt(dot3(S, S)), iA = 1.0 / A, n[3] = {S[0] * iA, S[1] * iA, S[2] * iA};
       const double gam = m.gam[6 * (size_t)c + s];
-      const double *F0 = m.Ff + 36 * (size_t)c + 6 * s;
-      double Wn[6], F1[6];
-      for (int k = 0; k < 6; ++k) Wn[k] = m.W[6 * (size_t)nb + k] + m.dW[6 * (size_t)nb + k];
-      euler_flux(m, Wn, n, F1);
+      // (F(W_j + dW_j) - F(W_j)) . n from the neighbour's axis fluxes
+      const double *F1 = m.FW + 18 * (size_t)nb, *F0 = m.FW0 + 18 * (size_t)nb;
       const double kA = 0.5 * A * g.invV;
-      for (int k = 0; k < m.nW; ++k) acc[k] -= ((F1[k] - F0[k]) - gam * m.dW[6 * (size_t)nb + k]) * kA;
+      for (int k = 0; k < m.nW; ++k) {
+        const double dF = (F1[k] - F0[k]) * n[0] + (F1[6 + k] - F0[6 + k]) * n[1] + (F1[12 + k] - F0[12 + k]) * n[2];
+        acc[k] -= (dF - gam * m.dW[6 * (size_t)nb + k]) * kA;
+      }
     }
-    for (int k = 0; k < m.nW; ++k) m.dW[6 * (size_t)c + k] = acc[k] * m.D[6 * (size_t)c + k];
+    double Wn[6];
+    for (int k = 0; k < 6; ++k) {
+      const double d = k < m.nW ? acc[k] * m.D[6 * (size_t)c + k] : 0.0;
+      if (k < m.nW) m.dW[6 * (size_t)c + k] = d;
+      Wn[k] = m.W[6 * (size_t)c + k] + d;
+    }
+    axis_fluxes(m, Wn, m.FW + 18 * (size_t)c);
   }
 }
 

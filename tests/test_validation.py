@@ -120,3 +120,13 @@ def test_euler_presteps_on_general_meshes_only():
     assert code(wl.cylinder(n_r=6, n_theta=12, nv=8), euler_presteps=100) == gsis.GSIS_OK
     assert code(wl.cavity(n=6, nv=8), euler_presteps=100) == gsis.GSIS_E_UNSUPPORTED
     assert code(wl.cylinder(n_r=6, n_theta=12, nv=8), euler_presteps=-1) == GSIS_E_INVALID
+
+
+def test_odd_wrapped_axis_only_in_the_kinetic_iteration():
+    """The synthetic solve's red/black colouring needs an even cell count on a wrapped axis
+    (across the wrap of an odd one two neighbours would share a colour); the kinetic colours do
+    not."""
+    p = wl.cylinder(n_r=6, n_theta=11, nv=8)
+    assert code(p) == gsis.GSIS_E_UNSUPPORTED
+    assert code(p, mode=gsis.MODE_DVM) == gsis.GSIS_OK
+    assert code(p, mode=gsis.MODE_DVM, euler_presteps=10) == gsis.GSIS_E_UNSUPPORTED
