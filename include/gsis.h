@@ -3,10 +3,10 @@
  *
  * Method: general synthetic iterative scheme (GSIS-II) of arXiv 2310.18916,
  * "Efficient parallel solver for rarefied gas flow using GSIS":
- *   - kinetic step over phase space (Section 3.1, Eq. delta_equations and the
+ *   - kinetic step over phase space (Section 3.2, Eq. delta_equations and the
  *     point-implicit form that follows it; Algorithm 3 body),
  *   - velocity moments (Eq. getmoment), high-order terms (Eq. full_constitutive),
- *   - FP64 synthetic NSF solve (Section 3.2, Eq. macro, delta_Macroscopic_equations,
+ *   - FP64 synthetic NSF solve (Section 3.3, Eq. macro, delta_Macroscopic_equations,
  *     res_macro; Algorithm 2 body),
  *   - VDF correction (Eq. updatef) and residual (Eq. convergence_critertion),
  *   - driven by the outer loop of Algorithm 1.
@@ -47,7 +47,7 @@ enum gsis_model { GSIS_SHAKHOV = 0, GSIS_RYKOV = 1 };
 enum gsis_precision { GSIS_F64 = 0, GSIS_F32 = 1, GSIS_BF16 = 2 };
 enum gsis_mode { GSIS_MODE_GSIS = 0, GSIS_MODE_DVM = 1 };
 
-/* Structured hexahedral block (spatial finite-volume cells of Section 3.1).
+/* Structured hexahedral block (spatial finite-volume cells of Section 3.2).
  * nodes: (ni+1)(nj+1)(nk+1) x 3 doubles (host), node (I,J,K) at index I + (ni+1)(J + (nj+1)K).
  * bc[side], side = i-, i+, j-, j+, k-, k+ (x-, x+, ... on a rectilinear block):
  *   WALL      isothermal, fully diffuse wall with velocity wall_u[side] (tangential) and
@@ -73,7 +73,7 @@ typedef struct {
   double wall_T[6];
 } gsis_mesh;
 
-/* Tensor-product discrete velocity grid (Section 3, velocity-space discretisation):
+/* Tensor-product discrete velocity grid (Section 3.1, velocity-space discretisation):
  * n[d] nodes x[d][.] with quadrature weights w[d][.] per axis d (host arrays, copied).
  * The discrete velocity index used by gsis_get_f / gsis_set_f is v = ix + n0 (iy + n1 iz). */
 typedef struct {
@@ -171,8 +171,9 @@ int gsis_footprint_bytes(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const g
 
 /* Build a solver: copy the inputs, build geometry and velocity blocks, allocate device state,
  * set f0 = Maxwellian(init_W) and run opt->kinetic_presteps plain kinetic steps
- * (Algorithm 1, first line).  Kn: Knudsen number, mu(T0)/(p0 L) sqrt(pi R T0/2) (Section 2.1).
- * Ma: reserved for free-stream boundaries (unused by walls; pass 0).
+ * (the preconditioning of Algorithm 1).  Kn: Knudsen number, mu(T0)/(p0 L) sqrt(pi R T0/2) (Section 2.1).
+ * Ma: unused (the free stream of FARFIELD sides is given in the mesh); pass 0.  With
+ * opt->euler_presteps > 0 the inviscid presteps run first and f starts from their result.
  * On success *out is a new handle; on failure *out is NULL. */
 int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const gsis_gas *gas, double Kn,
                 double Ma, const gsis_options *opt, gsis_handle *out);

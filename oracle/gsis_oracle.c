@@ -109,7 +109,7 @@ void orc_conductivity(const orc_gas *g, double mu, double *kt, double *kr) {
 }
 
 /* Reference distributions g_0t, g_0r, g_1t, g_1r of Section 2.2 combined as
-   g = (1 - 1/Z_r) g_t + g_r / Z_r (Section 3.1); heat fluxes q0, q1 from the
+   g = (1 - 1/Z_r) g_t + g_r / Z_r (Section 3.2); heat fluxes q0, q1 from the
    2x2 relaxation map of Section 2.2.  Shakhov: g0 = g_0t, no g1. */
 void orc_reference(const orc_gas *g, const double *st, const double *xi, double *g0, double *g1) {
   double rho = st[0], Tt = st[4], Tr = st[5];
@@ -243,7 +243,7 @@ static int build_geometry(orc_solver *s, const orc_mesh *m) {
   return ORC_OK;
 }
 
-/* ---------------- reconstruction (Section 3.1) ---------------- */
+/* ---------------- reconstruction (Section 3.2) ---------------- */
 
 /* Least-squares gradient over the face neighbours inside the domain:
    minimise sum_j (q_j - q_i - grad . (x_j - x_i))^2 via its 3x3 normal equations. */
@@ -352,7 +352,7 @@ int orc_wall_prepass(orc_solver *s) {
   return ORC_OK;
 }
 
-/* ---------------- kinetic step (Section 3.1, Algorithm 3 body) ---------------- */
+/* ---------------- kinetic step (Section 3.2, Algorithm 3 body) ---------------- */
 
 typedef struct {
   double *ff, *r, *df, *D;
@@ -590,7 +590,7 @@ static int all_moments(orc_solver *s) {
   return bad ? ORC_E_DIVERGED : ORC_OK;
 }
 
-/* ---------------- macroscopic synthetic solve (Section 3.2) ---------------- */
+/* ---------------- macroscopic synthetic solve (Section 3.3) ---------------- */
 
 /* conservative W: rho, rho u, rho E, rho E_r;  E = |u|^2/2 + 3Tt/4 + d_r Tr/4 */
 static void prim_of(const orc_solver *s, const double *W, double *pr) {
@@ -629,7 +629,7 @@ static double sound(double Tt) { return sqrt(5.0 * Tt / 6.0); }  /* sqrt(5 p_t /
    moving towards the wall leaves, the wall re-emits rho_w M(u_w, T_w) with zero net mass
    flux.  Half-range normal moments J_k of N(u_n, T/2) satisfy
    J_k = u_n J_{k-1} + (k-1) (T/2) J_{k-2} + (T/2) M_n(0) [k = 1].
-   Used for the increment-based "boundary flux modification" of Section 3.2. */
+   Used for the increment-based "boundary flux modification" of Section 3.3. */
 static void wall_eq_flux(const orc_solver *s, int side, const double *pr, const double *n, double *F) {
   double rho = pr[0], T = pr[4], un = dot3(pr + 1, n), Tw = s->wall_T[side];
   const double *uw = s->wall_u[side];

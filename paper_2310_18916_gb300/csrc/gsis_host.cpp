@@ -721,7 +721,7 @@ std::vector<AxisCell<T>> cast_axis(const std::vector<AxisCell<double>> &in) {
 
 }  // namespace
 
-// Finite-volume geometry of a general structured block (Section 3.1): a face's area vector is
+// Finite-volume geometry of a general structured block (Section 3.2): a face's area vector is
 // half the cross product of its diagonals, oriented out of the cell; its centre the mean of its
 // corners; a cell's centre the mean of its 8 corners and its volume (1/3) sum x_f . S_f
 // (divergence theorem with F = x / 3).  Least squares: the unweighted normal equations over

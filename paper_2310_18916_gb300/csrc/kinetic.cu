@@ -1,4 +1,4 @@
-// kinetic.cu -- the mesoscopic kinetic step of GSIS on sm_103a (Section 3.1 of arXiv 2310.18916).
+// kinetic.cu -- the mesoscopic kinetic step of GSIS on sm_103a (Section 3.2 of arXiv 2310.18916).
 //
 // One CTA owns one block of VB = 32 discrete velocities of a single octant (one per lane) and
 // marches through the spatial cells colour by colour, the colours being the hyperplanes
@@ -7,7 +7,7 @@
 //     while staging f^n into a three-colour shared-memory ring,
 //   - builds the reference distribution g (Shakhov g_0t, Section 2.2),
 //   - takes the LSQ gradient and the Venkatakrishnan limiter, reconstructs the outflow face
-//     value (second-order upwind, Section 3.1),
+//     value (second-order upwind, Section 3.2),
 //   - solves the point-implicit delta form with the first-order upwind implicit operator,
 //     taking the inflow value "face value + upwind increment" from the previous colour
 //     (exact in one pass on a rectilinear grid: every inflow neighbour has a lower colour),
@@ -996,7 +996,7 @@ cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon
 //
 // On a curved mesh the upwind side of a face changes with the velocity, so the colour sweeps are
 // no longer exact in one pass; the kernel therefore keeps whole-mesh work arrays for its block
-// of 32 velocities (in its own slice of a device scratch) and runs the steps of Section 3.1 one
+// of 32 velocities (in its own slice of a device scratch) and runs the steps of Section 3.2 one
 // after another: f^n with the pending correction, the limited LSQ gradient, the second-order
 // upwind residual with the implicit diagonal, n_sweeps point-implicit passes over the colours
 // of the octant (a cell's inflow increments are the neighbours' latest), the update.  A

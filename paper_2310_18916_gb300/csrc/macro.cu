@@ -1,4 +1,4 @@
-// macro.cu -- FP64 synthetic NSF solve of GSIS-II on sm_103a (Section 3.2 of arXiv 2310.18916).
+// macro.cu -- FP64 synthetic NSF solve of GSIS-II on sm_103a (Section 3.3 of arXiv 2310.18916).
 //
 // One persistent cooperative kernel runs all inner steps (Algorithm 2 body).  FP64 on GB300 is
 // 1/58 of the FP32 rate and the problem has O(10^4) cells, so the solve is bound by FP64
@@ -19,7 +19,7 @@
 // corr = K - S(W^{n+1/2}), K the kinetic step's sum of outward face fluxes and S this scheme's,
 // so the residual at W^{n+1/2} is the kinetic step's moment residual.  Wall faces use the
 // equilibrium wall flux of the boundary cell (its increment over the inner steps is the
-// boundary-flux modification of Section 3.2; its value at W^{n+1/2} cancels in corr).
+// boundary-flux modification of Section 3.3; its value at W^{n+1/2} cancels in corr).
 // Phases are separated by a grid barrier whose spin is bounded: on time-out it raises an error
 // flag and every block returns.
 // Per-cell arrays are indexed only by compile-time constants (the field count NW is a template

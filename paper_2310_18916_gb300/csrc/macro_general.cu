@@ -1,4 +1,4 @@
-// macro_general.cu -- the FP64 synthetic NSF solve of GSIS (Section 3.2, Algorithm 2) on general
+// macro_general.cu -- the FP64 synthetic NSF solve of GSIS (Section 3.3, Algorithm 2) on general
 // (curvilinear) structured meshes: O-grids with far-field, pole and wrapped sides.
 //
 // Per inner step, one thread per cell, one launch per phase:
