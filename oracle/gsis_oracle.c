@@ -17,7 +17,9 @@
  *   distributions, tau, conductivities, collision conservation, uniform
  *   equilibrium, free-molecular Couette, wall mass balance, NSF limit,
  *   refinement, GSIS-vs-DVM fixed point, O-grid geometry (wrapped azimuth, pole faces),
- *   far field (uniform free stream, collisionless reservoir against a wall): pinned.
+ *   far field (uniform free stream, collisionless reservoir against a wall), the
+ *   free-molecular force on a cylinder, the Euler presteps (mirror symmetry of the converged
+ *   inviscid cylinder flow): pinned.
  *   Macro-solver details the paper leaves to its references (face gradient,
  *   Gamma, time step): pinned only through the fixed point (kinetic/GSIS agree).
  */
