@@ -361,18 +361,18 @@ typedef struct {
   double *fl;            /* this velocity's outward face fluxes [cell][side][6] */
 } kin_work;
 
-/* A far-field face lets the free stream in unless the stream leaves through it: U_inf . S <= 0,
-   with faces tangential to the stream (|U_inf . S| at rounding level) counted as inflow. */
+/* A far-field face lets the free stream in unless the stream leaves through it faster than
+   sound (U_inf . n > c_inf = sqrt(5 T_inf / 6)): a reservoir boundary, except where nothing
+   travels upstream into the domain. */
 static int far_inflow(const orc_solver *s, int i, int side) {
   const double *U = s->wall_u[side], *S = s->S + 18 * i + 3 * side;
-  return dot3(U, S) <= 1e-12 * sqrt(dot3(U, U) * dot3(S, S));
+  return dot3(U, S) <= sqrt(5.0 * s->wall_T[side] / 6.0) * sqrt(dot3(S, S));
 }
 
 /* Face values (f, and f1 for Rykov) entering the domain through the boundary face (i, side)
    for velocity xi: at a wall the re-emitted rho_w M_w (f1 = (d_r T_w / 4) f); at a far field
-   the free-stream Maxwellian where the free stream does not leave through the face
-   (U_inf . S <= 0), else the cell's own values own[] (zero gradient: the first-order value,
-   which keeps the interior gradient out of the boundary condition). */
+   the free-stream Maxwellian, except where the free stream leaves through the face faster than
+   sound, where they carry the cell's own values own[] (zero gradient, first order). */
 static void boundary_in(const orc_solver *s, int i, int side, const double *xi, const double own[2], double e[2]) {
   if (s->nb[6 * i + side] == -1) {
     double M = s->rho_w[s->wid[6 * i + side]] * wall_maxwellian(s, side, xi);

@@ -807,11 +807,11 @@ static int build_general(gsis_solver *s, const gsis_mesh *m) {
           } else if (b == GSIS_BC_AXIS) nb = NB_AXIS;
           else if (b == GSIS_BC_FARFIELD) {
             nb = NB_FAR;
-            // the free stream enters unless it leaves through the face (tangential faces enter)
+            // a reservoir boundary: the free stream enters unless it leaves through the face
+            // faster than sound, c = sqrt(5 T / 6)
             const double *U = m->wall_u[side];
             const double un = U[0] * S[0] + U[1] * S[1] + U[2] * S[2];
-            const double Un = std::sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-            s->gin[6 * (size_t)c + side] = un <= 1e-12 * Un * A;
+            s->gin[6 * (size_t)c + side] = un <= std::sqrt(5.0 * m->wall_T[side] / 6.0) * A;
           } else {
             nb = NB_WALL;
             s->gwid[6 * (size_t)c + side] = s->nwall++;
