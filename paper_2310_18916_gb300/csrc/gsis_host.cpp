@@ -1,9 +1,11 @@
 // gsis_host.cpp -- host solver object behind the C ABI of include/gsis.h.
 //
-// Builds the rectilinear geometry, the octant-blocked velocity layout, the colour tables and the
-// wall tables, owns every device buffer, and sequences one outer iteration of Algorithm 1:
-//   wall pre-pass -> fused kinetic step -> block reduction -> moments (+ closed-domain mass
-//   scale) -> [GSIS: FP64 synthetic solve] -> eps -> state of the next step.
+// Builds the geometry (rectilinear axes, or the per-cell finite-volume geometry of a general
+// structured block), the octant-blocked velocity layout, the colour tables and the wall tables,
+// owns every device buffer, and sequences one outer iteration of Algorithm 1:
+//   wall pre-pass -> kinetic step -> block reduction -> moments (+ closed-domain mass scale)
+//   -> [GSIS: FP64 synthetic solve] -> eps -> state of the next step,
+// with the rectilinear kernels or the general-mesh ones; plus the Euler presteps at creation.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

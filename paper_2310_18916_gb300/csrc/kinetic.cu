@@ -999,8 +999,11 @@ cudaError_t launch_import_f(const KinArgs<T, S> &a, int q, const int *slot_canon
 // of 32 velocities (in its own slice of a device scratch) and runs the steps of Section 3.2 one
 // after another: f^n with the pending correction, the limited LSQ gradient, the second-order
 // upwind residual with the implicit diagonal, n_sweeps point-implicit passes over the colours
-// of the octant (a cell's inflow increments are the neighbours' latest), the update.  A
-// persistent grid walks the velocity blocks, one block per CTA at a time.
+// of the octant (a cell's inflow increments are the neighbours' latest), the update with the
+// wall-face fluxes and, for GSIS, the per-cell kinetic face-flux sums.  A persistent grid walks
+// the velocity blocks, one block per CTA at a time.  Far-field faces: the free-stream
+// Maxwellian enters unless the stream leaves faster than sound (host flag gin), else the
+// cell's own value; pole (AXIS) and absent sides carry no flux.
 
 template <typename T>
 __device__ __forceinline__ T dot_xi(const T *S, T x, T y, T z) {
