@@ -69,3 +69,21 @@ def test_limiter_is_one_for_linear_data_and_small_at_extrema():
     # east face: D2 = g dx/2 = 1/8, Dm = 0; eps^2 = (K h)^3 with h = V^(1/3) = 1/8 (K = 1):
     # phi = eps^2 / (2 D2^2 + eps^2) = (1/512) / (1/32 + 1/512) = 1/17
     assert o.cell_limiter(27, q) == pytest.approx(1.0 / 17.0, rel=1e-12)
+
+
+def test_body_grid_generators():
+    """The O-grid inputs: geometric radial spacing with the requested first width and the
+    configuration-3 ratio, a closed azimuth (the last node row is the first), exact poles."""
+    r = wl.radial_nodes(32, 0.5, 5.0, first=0.0224)
+    d = np.diff(r)
+    assert r[0] == 0.5 and r[-1] == 5.0 and abs(d[0] - 0.0224) < 1e-12
+    np.testing.assert_allclose(d[1:-1] / d[:-2], d[1] / d[0], rtol=1e-9)
+    assert abs(d[1] / d[0] - 1.1) < 1e-3
+    c = wl.cylinder(n_r=4, n_theta=6, nv=4)
+    assert np.array_equal(c.nodes[:, -1], c.nodes[:, 0])
+    s = wl.sphere(n_r=3, n_pol=4, n_az=6, nv=4)
+    assert np.array_equal(s.nodes[-1], s.nodes[0])                                # closed azimuth
+    for pole in (0, -1):  # every azimuth meets at one point on the axis
+        pts = s.nodes[:, pole, :, :]
+        assert np.abs(pts[..., 1:]).max() == 0.0
+        assert np.abs(pts - pts[:1]).max() == 0.0
