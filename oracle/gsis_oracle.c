@@ -362,11 +362,14 @@ typedef struct {
 } kin_work;
 
 /* A far-field face lets the free stream in unless the stream leaves through it faster than
-   sound (U_inf . n > c_inf = sqrt(5 T_inf / 6)): a reservoir boundary, except where nothing
-   travels upstream into the domain. */
+   sound (U_inf . n > c_inf): a reservoir boundary, except where nothing travels upstream into
+   the domain.  c_inf^2 = gamma R T_inf with R T = T/2 and the equilibrium ratio of specific
+   heats of the free stream, gamma = (5 + d_r)/(3 + d_r) (5/3 monatomic, 7/5 for d_r = 2). */
 static int far_inflow(const orc_solver *s, int i, int side) {
   const double *U = s->wall_u[side], *S = s->S + 18 * i + 3 * side;
-  return dot3(U, S) <= sqrt(5.0 * s->wall_T[side] / 6.0) * sqrt(dot3(S, S));
+  double dr = s->nvdf == 2 ? s->g.d_r : 0.0;
+  double gam = (5.0 + dr) / (3.0 + dr);
+  return dot3(U, S) <= sqrt(0.5 * gam * s->wall_T[side]) * sqrt(dot3(S, S));
 }
 
 /* Face values (f, and f1 for Rykov) entering the domain through the boundary face (i, side)

@@ -810,10 +810,13 @@ static int build_general(gsis_solver *s, const gsis_mesh *m) {
           else if (b == GSIS_BC_FARFIELD) {
             nb = NB_FAR;
             // a reservoir boundary: the free stream enters unless it leaves through the face
-            // faster than sound, c = sqrt(5 T / 6)
+            // faster than sound, c^2 = gamma R T with gamma = (5 + d_r) / (3 + d_r) of the
+            // free stream in equilibrium (5/3 monatomic, 7/5 for d_r = 2) and R T = T / 2
             const double *U = m->wall_u[side];
             const double un = U[0] * S[0] + U[1] * S[1] + U[2] * S[2];
-            s->gin[6 * (size_t)c + side] = un <= std::sqrt(5.0 * m->wall_T[side] / 6.0) * A;
+            const double dr = s->gas.model == GSIS_RYKOV ? s->gas.d_r : 0.0;
+            const double gam = (5.0 + dr) / (3.0 + dr);
+            s->gin[6 * (size_t)c + side] = un <= std::sqrt(0.5 * gam * m->wall_T[side]) * A;
           } else {
             nb = NB_WALL;
             s->gwid[6 * (size_t)c + side] = s->nwall++;
@@ -1578,6 +1581,8 @@ extern "C" int gsis_destroy(gsis_handle h) {
   delete h;
   return GSIS_OK;
 }
+
+void gsis::set_handle_free_error(const char *msg) { g_create_error = msg; }
 
 extern "C" const char *gsis_last_error(gsis_handle h) {
   if (!h) return g_create_error.c_str();

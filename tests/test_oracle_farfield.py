@@ -87,18 +87,28 @@ def test_uniform_free_stream_is_steady_on_a_curved_mesh(mode):
     assert np.abs(f - M[None, :]).max() < drift0 + 1e-8
 
 
-@pytest.mark.parametrize("U", [(0.0, 0.3, 0.0), (0.0, 0.0, -0.4), (-0.3, 0.0, 0.0), (-1.2, 0.0, 0.0)])
-def test_collisionless_reservoir_and_hot_wall(U):
+@pytest.mark.parametrize("U,model", [((0.0, 0.3, 0.0), wl.SHAKHOV), ((0.0, 0.0, -0.4), wl.SHAKHOV),
+                                     ((-0.3, 0.0, 0.0), wl.SHAKHOV), ((-1.2, 0.0, 0.0), wl.SHAKHOV),
+                                     ((-0.88, 0.0, 0.0), wl.SHAKHOV), ((-0.88, 0.0, 0.0), wl.RYKOV),
+                                     ((-0.8, 0.0, 0.0), wl.RYKOV)])
+def test_collisionless_reservoir_and_hot_wall(U, model):
     """The slab starts from a gas unlike the reservoir (rho 0.5, T 1.5, at rest). The far field
     is a reservoir and injects the free stream, also where the stream leaves subsonically
-    (U_x = -0.3); where it leaves faster than sound (U_x = -1.2 < -sqrt(5/6)) the incoming
-    molecules keep the cell's own values, so the initial gas stays."""
+    (U_x = -0.3); where it leaves faster than sound (U_x = -1.2) the incoming molecules keep the
+    cell's own values, so the initial gas stays.  The speed of sound is the free stream's,
+    c^2 = gamma T/2 with gamma = 5/3 for the monatomic gas and 7/5 for the diatomic Rykov gas
+    (d_r = 2, internal modes in equilibrium in the free stream): U_x = -0.88 leaves
+    subsonically in the first and supersonically in the second."""
     p = wl.reservoir_wall(n_cells=8, nv=16, U=U, T_inf=1.0, T_w=2.0, Kn=1e9)
+    gamma = 5.0 / 3.0
+    if model == wl.RYKOV:
+        p = wl.as_rykov(p)
+        gamma = 7.0 / 5.0
     W0 = np.tile([0.5, 0.0, 0.0, 0.0, 1.5, 1.5], (p.ncells, 1))
     o = Oracle(p, W0=W0, mode=1)
     o.step(4)
     f, _ = o.get_f()
-    inflow = -U[0] <= np.sqrt(5.0 / 6.0)
+    inflow = -U[0] <= np.sqrt(gamma / 2.0)
     Minf, vx = _maxwellian(1.0, U, 1.0, p.vx, p.vy, p.vz) if inflow else _maxwellian(0.5, (0, 0, 0), 1.5, p.vx, p.vy, p.vz)
     Mw, _ = _maxwellian(1.0, (0.0, 0.0, 0.0), 2.0, p.vx, p.vy, p.vz)
     w = _weights(p)
