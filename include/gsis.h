@@ -172,7 +172,12 @@ int gsis_footprint_bytes(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const g
 /* Build a solver: copy the inputs, build geometry and velocity blocks, allocate device state,
  * set f0 = Maxwellian(init_W) and run opt->kinetic_presteps plain kinetic steps
  * (the preconditioning of Algorithm 1).  Kn: Knudsen number, mu(T0)/(p0 L) sqrt(pi R T0/2) (Section 2.1).
- * Ma: unused (the free stream of FARFIELD sides is given in the mesh); pass 0.  With
+ * Ma: Mach number of the problem (Section 5 states each case by its free-stream Mach number):
+ * the free stream's speed |wall_u| over its speed of sound for a mesh with FARFIELD sides, else
+ * the fastest WALL's speed over the speed of sound at that wall's temperature, with
+ * c^2 = gamma T / 2 (speeds in sqrt(2 R T0)) and gamma = (5 + d_r)/(3 + d_r) (5/3 for Shakhov).
+ * The speeds themselves come from the mesh; a Ma that disagrees with them by more than
+ * 1e-9 max(1, Ma) is refused with GSIS_E_INVALID before anything is allocated.  With
  * opt->euler_presteps > 0 the inviscid presteps run first and f starts from their result.
  * On success *out is a new handle; on failure *out is NULL. */
 int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const gsis_gas *gas, double Kn,
@@ -261,11 +266,16 @@ int gsis_stats(gsis_handle h, int *outer_total, int *macro_iters_last);
  * allowed.  It allocates nothing: its only scratch is a fixed 8 MiB array of static device
  * memory (every GPU that loads this library holds it until the process exits).
  *   f_dev:   device, FP32, [cell][v], v = ix + nx (iy + ny iz) (the layout of gsis_get_f)
- *   vel_dev: device, FP32, [v][4] = xi_x, xi_y, xi_z, quadrature weight
+ *   vel_dev: device, FP32, 16-byte aligned, [v][4] = xi_x, xi_y, xi_z, quadrature weight
  *   out_dev: device, FP64, [cell][18] = the GSIS_F_HALF fields of gsis_moments: rho, u(3),
- *            Tt, Tr (= Tt), sigma(xx,yy,zz,xy,xz,yz), qt(3), qr(3) (= 0)  (Eq. getmoment)
+ *            Tt, Tr (= Tt), sigma(xx,yy,zz,xy,xz,yz), qt(3), qr(3) (= 0)
  *   stream:  cudaStream_t (NULL = default stream); the call only enqueues work on it.
- * Limits: ncells <= 8 MiB / (13 x 8 B) = 80659, else GSIS_E_INVALID (nothing is launched).
+ * Accuracy: two passes, both summed in FP32 with compensated (Kahan) accumulators and the
+ * per-chunk partials combined in FP64 in a fixed order: the mean velocity first, then the
+ * moments about it, so fast streams (|u| several times the thermal speed) keep the relative
+ * accuracy of slow ones.  out_dev doubles as the store of the mean velocity between passes.
+ * Limits: ncells <= 8 MiB / (12 x 8 B) = 87381, else GSIS_E_INVALID (nothing is launched;
+ * gsis_last_error(NULL) says why).
  * The first call on a device, with that device current, looks up the scratch's device address
  * (cudaGetSymbolAddress); make that first call before capturing a stream into a graph.
  * Calls share the scratch: two calls whose work overlaps on the GPU (different streams,
@@ -278,7 +288,8 @@ int gsis_vdf_moments_noalloc(const float *f_dev, const float *vel_dev, int ncell
 /* Release everything held by h.  NULL-safe. */
 int gsis_destroy(gsis_handle h);
 
-/* Message of the last error on h (or of the last failed gsis_create when h is NULL). */
+/* Message of the last error on h (or, when h is NULL, of the last failed gsis_create or
+ * gsis_vdf_moments_noalloc on this host thread). */
 const char *gsis_last_error(gsis_handle h);
 
 /* Self-test of the bounded device waits, on the current device: which = 0 runs the synthetic

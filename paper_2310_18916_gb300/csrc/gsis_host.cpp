@@ -1327,9 +1327,26 @@ static int init_state_from(gsis_solver *s, std::vector<double> &W0) {
   return GSIS_DISPATCH(s->prec, (s->state_from_f<T, S>(W0.data())));
 }
 
+// Mach number the mesh's boundary data describe: the free stream's (far-field sides) or, without
+// a far field, the fastest wall's, each over the speed of sound at its own temperature,
+// c^2 = gamma R T with R T = T / 2 and gamma = (5 + d_r) / (3 + d_r) (Section 2.1: internal
+// energy d_r R T_r / 2 beside the translational 3 R T_t / 2).
+static double mesh_mach(const gsis_mesh *m, const gsis_gas *g) {
+  const double dr = g->model == GSIS_RYKOV ? g->d_r : 0.0;
+  const double gam = (5.0 + dr) / (3.0 + dr);
+  bool far = false;
+  for (int s = 0; s < 6; ++s) far = far || m->bc[s] == GSIS_BC_FARFIELD;
+  double ma = 0.0;
+  for (int s = 0; s < 6; ++s) {
+    if (m->bc[s] != (far ? GSIS_BC_FARFIELD : GSIS_BC_WALL)) continue;
+    const double *u = m->wall_u[s];
+    ma = std::max(ma, std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / std::sqrt(0.5 * gam * m->wall_T[s]));
+  }
+  return ma;
+}
+
 extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const gsis_gas *gas, double Kn, double Ma,
                            const gsis_options *opt, gsis_handle *out) {
-  (void)Ma;
   if (out) *out = nullptr;
   if (!out) { g_create_error = "out is NULL"; return GSIS_E_INVALID; }
   gsis_options o;
@@ -1338,6 +1355,16 @@ extern "C" int gsis_create(const gsis_mesh *mesh, const gsis_vgrid *vgrid, const
   std::string why;
   int rc = validate(mesh, vgrid, gas, Kn, &o, why);
   if (rc) { g_create_error = why; return rc; }
+  {
+    const double ma_mesh = mesh_mach(mesh, gas);
+    if (!std::isfinite(Ma) || !(Ma >= 0.0) || std::fabs(Ma - ma_mesh) > 1e-9 * std::max(1.0, ma_mesh)) {
+      char buf[200];
+      std::snprintf(buf, sizeof buf, "Ma = %.9g disagrees with the %s speed of the mesh (Ma = %.9g)", Ma,
+                    ma_mesh > 0 || Ma > 0 ? "free-stream or wall" : "zero", ma_mesh);
+      g_create_error = buf;
+      return GSIS_E_INVALID;
+    }
+  }
   gsis_solver *s = new (std::nothrow) gsis_solver();
   if (!s) { g_create_error = "out of host memory"; return GSIS_E_OOM; }
   s->opt = o;

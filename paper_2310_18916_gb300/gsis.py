@@ -199,7 +199,8 @@ class Solver:
             o.free = self._free_cb
         self.options = o
         h = C.c_void_p()
-        rc = L.gsis_create(C.byref(m), C.byref(vg), C.byref(g), float(problem.Kn), 0.0, C.byref(o), C.byref(h))
+        rc = L.gsis_create(C.byref(m), C.byref(vg), C.byref(g), float(problem.Kn), float(problem.Ma), C.byref(o),
+                           C.byref(h))
         if rc != 0:
             raise GsisError(rc, L.gsis_last_error(None).decode())
         self.h = h

@@ -55,6 +55,19 @@ class Problem:
     def nvel(self) -> int:
         return len(self.vx) * len(self.vy) * len(self.vz)
 
+    @property
+    def Ma(self) -> float:
+        """The Mach number that describes this problem at the library's boundary: the free
+        stream's speed over its speed of sound where the mesh has far-field sides, else the
+        fastest wall's speed over the speed of sound at that wall's temperature, with
+        c^2 = gamma T / 2 (T in T0, speeds in sqrt(2 R T0)) and gamma = (5 + d_r) / (3 + d_r)."""
+        d_r = self.d_r if self.model == RYKOV else 0.0
+        gamma = (5.0 + d_r) / (3.0 + d_r)
+        far = [s for s in range(6) if self.bc[s] == FARFIELD]
+        sides = far if far else [s for s in range(6) if self.bc[s] == WALL]
+        return max([float(np.linalg.norm(self.wall_u[s])) / np.sqrt(0.5 * gamma * self.wall_T[s]) for s in sides],
+                   default=0.0)
+
 
 def midpoint_grid(n: int, lo: float, hi: float):
     """Uniform midpoint nodes and equal weights on [lo, hi]."""

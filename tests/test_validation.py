@@ -130,3 +130,37 @@ def test_odd_wrapped_axis_only_in_the_kinetic_iteration():
     assert code(p) == gsis.GSIS_E_UNSUPPORTED
     assert code(p, mode=gsis.MODE_DVM) == gsis.GSIS_OK
     assert code(p, mode=gsis.MODE_DVM, euler_presteps=10) == gsis.GSIS_E_UNSUPPORTED
+
+
+def _create_rc(p, Ma):
+    """gsis_create through the C ABI with a given Ma; only for inputs refused before any CUDA call."""
+    import ctypes as C
+
+    L = gsis.load()
+    keep = []
+    m, vg, g = gsis.build_structs(p, keep)
+    o = gsis.Options()
+    L.gsis_default_options(C.byref(o))
+    h = C.c_void_p(0)
+    rc = L.gsis_create(C.byref(m), C.byref(vg), C.byref(g), float(p.Kn), float(Ma), C.byref(o), C.byref(h))
+    assert not h.value
+    return rc, L.gsis_last_error(None).decode()
+
+
+def test_mach_number_must_match_the_free_stream_or_wall_speed():
+    """gsis_create takes Ma of the free stream or of the lid (Section 5 states cases by Ma) and
+    refuses a value the mesh's speeds contradict, before allocating anything."""
+    cav = wl.cavity(n=8, nv=8, lid=0.16)
+    assert cav.Ma == pytest.approx(0.16 / np.sqrt(5.0 / 6.0), rel=1e-14)
+    for wrong in (0.0, 0.2, -0.16, float("nan")):
+        rc, msg = _create_rc(cav, wrong)
+        assert rc == GSIS_E_INVALID and "Ma" in msg, (wrong, rc, msg)
+    cyl = wl.cylinder(n_r=4, n_theta=8, nv=8, Ma=2.0)
+    assert cyl.Ma == pytest.approx(2.0, rel=1e-14)
+    assert _create_rc(cyl, 2.1)[0] == GSIS_E_INVALID
+    assert _create_rc(cyl, 1.0)[0] == GSIS_E_INVALID
+    # the same speeds in the diatomic gas: gamma = 7/5 gives a higher Mach number
+    ry = wl.as_rykov(wl.cylinder(n_r=4, n_theta=8, nv=8, Ma=2.0))
+    assert ry.Ma == pytest.approx(2.0 * np.sqrt((5.0 / 3.0) / (7.0 / 5.0)), rel=1e-14)
+    rc, msg = _create_rc(ry, 2.0)
+    assert rc == GSIS_E_INVALID and "disagrees" in msg
