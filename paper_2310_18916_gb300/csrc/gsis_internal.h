@@ -309,4 +309,7 @@ cudaError_t probe_barrier_timeout(unsigned *bar, int *err, long long limit, cuda
 cudaError_t probe_mbarrier_timeout(int *err, long long limit, cudaStream_t s);
 cudaError_t macro_launch_shape(int nc, int max_sms, int *grid, int *block);
 
+// message returned by gsis_last_error(NULL) for a failed call that has no handle
+void set_handle_free_error(const char *msg);
+
 }  // namespace gsis
