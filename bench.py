@@ -1,10 +1,15 @@
 """Benchmark: phase-space updates per second of the GSIS solver on the 2D lid-driven cavity
-(128 x 128 cells, 32^3 velocities on [-5, 5]^3 = 537M phase-space points, Kn = 0.1, lid 0.16,
-FP32 VDF storage with the FP64 synthetic NSF solve).
+(128 x 128 cells, 32^3 velocities on [-5, 5]^3 = 537M phase-space points, Kn = 0.1, lid 0.16).
+
+The headline is the plain FP64 path (FP64 VDF, FP64 kinetic arithmetic, FP64 synthetic solve).
+The same line carries the FP32- and BF16-storage forms beside it (FP32 kinetic arithmetic with
+compensated FP32 moments, FP64 synthetic solve): their updates/s, their time to eps < 1e-6 (or
+to their storage round-off floor) and the relative L2 distance of their converged density and
+temperature from the FP64 solution.
 
 One step = one outer GSIS iteration (Algorithm 1): wall pre-pass, fused kinetic step,
-moments, FP64 synthetic solve (300 inner steps), residual and the next state.  The VDF (2.1 GB)
-is far larger than L2 (129 MB), so no L2 flush is needed between steps.
+moments, FP64 synthetic solve (300 inner steps), residual and the next state.  The VDF (4.3 GB
+in FP64) is far larger than L2 (129 MB), so no L2 flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU ("replicas only").
@@ -12,6 +17,7 @@ Under torchrun (N > 1) every rank runs an independent replica on its own GPU ("r
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -33,13 +39,33 @@ UNIT = "updates/s"
 # log as one flop each): gradients and limiters 490, face fluxes 350, four red/black sweeps with
 # the residual, update and axis-flux increments 716.
 MACRO_FLOPS_PER_CELL_STEP_2D = 1556
-# FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA lanes per clock
-# x 2 flops x the maximum SM clock
-FP64_LANES_PER_SM = 2
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the 128^2 cavity with
-# 32^3 velocities in FP32, from one ncu pass over the benchmark itself; None once the kernel has
-# changed since the capture
-DRAM_BYTES_PER_LAUNCH = {"kinetic_kernel": 2186.25e6 + 2092.57e6, "macro_kernel": 14.54e6 + 3.19e6}
+# Arithmetic of the kinetic step per phase-space point, 2D Shakhov, counted from the formulas
+# in the same way (comparisons, min / max and selections not counted): the correction of
+# Eq. updatef on load (two Maxwellians and the combination) 25, the LSQ gradient of two axes 10,
+# the Venkatakrishnan limiter 34, the Shakhov reference distribution 11 beyond the Maxwellian it
+# shares with the correction, the collision and flux terms of the delta form 19, the division by
+# the implicit diagonal, the update and the published face increments 4.
+KINETIC_FLOPS_PER_POINT_2D = 103
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu pass over the
+# 128^2 cavity with 32^3 velocities, keyed by kernel, precision and the SHA-256 prefix of the
+# kernel's source file at capture time: a figure whose source has changed since is reported as
+# null (stale).
+DRAM_BYTES_PER_LAUNCH = {}
+KERNEL_SOURCES = {"kinetic_kernel": "kinetic.cu", "moments_kernel": "kinetic.cu", "macro_kernel": "macro.cu"}
+
+
+def source_sha(kernel):
+    path = os.path.join(ROOT, "paper_2310_18916_gb300", "csrc", KERNEL_SOURCES[kernel])
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:12]
+
+
+def traffic(kernel, precision):
+    """Measured DRAM bytes per launch, or None when not captured for this source."""
+    rec = DRAM_BYTES_PER_LAUNCH.get((kernel, precision))
+    if rec is None or rec[1] != source_sha(kernel):
+        return None
+    return rec[0]
 
 
 def workload_name(c=CFG):
@@ -119,76 +145,129 @@ def measured_peaks():
     return 6800.0, "fallback", 2070.0
 
 
-def oracle_sample(c=CFG, nv_sample=16, macro_sample=100):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: the same 128^2 mesh
-    with an nv_sample^3 velocity grid (kinetic cost per phase-space point does not depend on the
-    velocity count) and macro_sample of the 300 inner synthetic steps.  Returns the estimated
-    seconds of one full outer step and a description."""
+def fp64_peak_tflops():
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul on float64), 6144^3, best of
+    three after a warm-up, CUDA events (2 n^3 flops per product)."""
+    import torch
+
+    n = 6144
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        c = a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b, c
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def oracle_outer_steps(p, steps, threads):
+    """Complete FP64 oracle outer steps (kinetic step over every point, moments, the 300 inner
+    synthetic steps, residual and correction) of problem p, each timed; creation untimed."""
     from oracle.oracle import Oracle
-    from paper_2310_18916_gb300 import workloads as wl
 
-    p = wl.cavity(n=c["n"], nv=nv_sample, vmax=c["vmax"], Kn=c["Kn"], lid=c["lid"])
-    if c["model"] == "rykov":
-        p = wl.as_rykov(p)
-    o = Oracle(p, mode=0, macro_steps=macro_sample, macro_tol=0.0)
-    t0 = time.perf_counter()
-    o.wall_prepass()
-    o.kinetic_velocities(0, o.nv)
-    t1 = time.perf_counter()
-    o.macro_from_current()
-    t2 = time.perf_counter()
-    full_pts = c["n"] ** 2 * c["nv"] ** 3 * (2 if c["model"] == "rykov" else 1)
-    kin_scale = c["nv"] ** 3 / o.nv
-    est = (t1 - t0) * kin_scale + (t2 - t1) * (300.0 / macro_sample)
-    desc = (f"oracle kinetic step on the {c['n']}^2 mesh with {nv_sample}^3 velocities ({t1 - t0:.2f} s, scaled x"
-            f"{kin_scale:.0f} to {c['nv']}^3) + moments and {macro_sample} of 300 synthetic inner steps ({t2 - t1:.2f} s, "
-            f"scaled x{300.0 / macro_sample:.0f}); {full_pts} points per full step")
-    return est, desc, (t2 - t0)
+    o = Oracle(p, mode=0, nthreads=threads)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        o.step()
+        times.append(time.perf_counter() - t0)
+    return times
 
 
-def run_time_to_steady(args):
-    """Wall time from solver creation (host inputs) to eps < tol, per VDF precision, on one GPU,
-    with the accuracy of the FP32 / BF16 solutions against the plain FP64 one.  Each precision
-    stops at the first of eps < tol, a stall of eps (its storage round-off floor: 20 steps
-    without a new minimum) or max_steps."""
-    import numpy as np
+SAMPLE_CELLS = 16  # the bounded CPU sample: a 16 x 16 cavity with the workload's velocity grid
+
+
+def sample_problem(c=CFG):
+    """The workload's cavity at 16 x 16 cells with the same velocity grid, lid, Kn and gas: the
+    same 32768 velocities per cell, so the kinetic work per point and the synthetic solve's work
+    per point (cells / points) are those of the full workload."""
+    return problem(dict(c, n=SAMPLE_CELLS))
+
+
+def cpu_baseline(c=CFG):
+    """The oracle as it stands on the host cores: one complete outer step of the full workload
+    on every core, and two complete outer steps of the 16 x 16 sample on one thread."""
+    cores = os.cpu_count() or 1
+    p = problem(c)
+    nvdf = 2 if c["model"] == "rykov" else 1
+    full = oracle_outer_steps(p, 1, cores)[0]
+    q = sample_problem(c)
+    one = oracle_outer_steps(q, 2, 1)
+    qpts = q.ncells * q.nvel * nvdf
+    return {"value": p.ncells * p.nvel * nvdf / full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one complete FP64 outer step (300 inner synthetic steps) of the full {c['n']}^2 x {c['nv']}^3 "
+                      f"workload on {cores} threads, timed: {full:.1f} s (creation untimed)",
+            "single_thread": {"value": qpts * len(one) / sum(one), "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": f"two complete FP64 outer steps of the {SAMPLE_CELLS}x{SAMPLE_CELLS}-cell cavity "
+                                        f"with the same {c['nv']}^3 velocities ({qpts} points), timed: "
+                                        f"{sum(one):.1f} s"}}
+
+
+def time_to_steady(p, prec, tol, max_steps, stall=20):
+    """Wall time from solver creation (host inputs) to eps < tol for one VDF precision, on one GPU.
+    Stops at the first of eps < tol, a stall of eps (its storage round-off floor: `stall` steps
+    without a new minimum) or max_steps.  Returns the record and the final state W."""
     import torch
 
     from paper_2310_18916_gb300 import gsis
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = gsis.Solver(p, precision=prec, mode="gsis")
+    best, since, hist = float("inf"), 0, []
+    for _ in range(max_steps):
+        e = s.step()
+        hist.append(e)
+        if e < best:
+            best, since = e, 0
+        else:
+            since += 1
+        if e < tol or since >= stall:
+            break
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    W = s.W()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"precision": prec, "tol": tol, "reached": hist[-1] < tol, "steps": len(hist), "seconds": sec,
+            "eps_last": hist[-1], "eps_min": min(hist)}, W
+
+
+def against_fp64(W, ref, vol):
+    """Relative L2 (volume-weighted) of density and temperature and the largest velocity
+    difference over the largest speed, against the FP64 solution."""
+    import numpy as np
+
+    rl2 = lambda a, b: float(np.sqrt(((a - b) ** 2 * vol).sum() / (b ** 2 * vol).sum()))
+    return {"rho": rl2(W[:, 0], ref[:, 0]), "T": rl2(W[:, 4], ref[:, 4]),
+            "u_max_abs_over_max": float(np.abs(W[:, 1:3] - ref[:, 1:3]).max() / np.abs(ref[:, 1:3]).max())}
+
+
+def run_time_to_steady(args):
+    """Time to eps < tol per VDF precision (FP64, FP32, BF16) with the accuracy of the FP32 / BF16
+    solutions against the plain FP64 one."""
+    import numpy as np
+    import torch
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     p = problem()
     vol = np.full(p.ncells, 1.0 / p.ncells)
     out, ref = [], None
     for prec in ("f64", "f32", "bf16"):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s = gsis.Solver(p, precision=prec, mode="gsis")
-        best, since, hist = float("inf"), 0, []
-        for k in range(args.tts_max_steps):
-            e = s.step()
-            hist.append(e)
-            if e < best:
-                best, since = e, 0
-            else:
-                since += 1
-            if e < args.tts_tol or since >= 20:
-                break
-        torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
-        W = s.W()
-        s.close()
-        del s
-        torch.cuda.empty_cache()
-        rec = {"precision": prec, "tol": args.tts_tol, "reached": hist[-1] < args.tts_tol, "steps": len(hist),
-               "seconds": sec, "eps_last": hist[-1], "eps_min": min(hist)}
+        rec, W = time_to_steady(p, prec, args.tts_tol, args.tts_max_steps)
         if prec == "f64":
             ref = W
         else:
-            rl2 = lambda a, b: float(np.sqrt(((a - b) ** 2 * vol).sum() / (b ** 2 * vol).sum()))
-            rec["rel_l2_vs_f64"] = {"rho": rl2(W[:, 0], ref[:, 0]), "T": rl2(W[:, 4], ref[:, 4]),
-                                    "u_max_abs_over_max": float(np.abs(W[:, 1:3] - ref[:, 1:3]).max()
-                                                                / np.abs(ref[:, 1:3]).max())}
+            rec["rel_l2_vs_f64"] = against_fp64(W, ref, vol)
         out.append(rec)
     print(json.dumps({"metric": "time to steady state (GSIS, 2D cavity, from host inputs)", "unit": "s",
                       "higher_is_better": False, "config": {"workload": workload_name()}, "results": out}))
@@ -442,26 +521,68 @@ def run_serve(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on every host core.  Each step is one
+    complete outer step (kinetic step, moments, 300 inner synthetic steps, residual) of the
+    bounded sample of the workload: the cavity at 16 x 16 cells with the workload's 32^3 velocity
+    grid, lid, Kn and gas, so that each update carries the same kinetic and synthetic work as at
+    128^2.  W untimed steps, then K timed ones; value = points updated / time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     cores = os.cpu_count() or 1
-    times, desc = [], ""
-    for i in range(args.warmup + args.steps):
-        est, desc, _ = oracle_sample(nv_sample=6, macro_sample=15)
-        if i >= args.warmup:
-            times.append(est)
-    pts = CFG["n"] ** 2 * CFG["nv"] ** 3
-    ms = 1e3 * statistics.mean(times)
-    value = pts / (ms / 1e3)
+    q = sample_problem()
+    nvdf = 2 if CFG["model"] == "rykov" else 1
+    qpts = q.ncells * q.nvel * nvdf
+    times = oracle_outer_steps(q, args.warmup + args.steps, cores)[args.warmup:]
+    total = sum(times)
+    ms = 1e3 * total / args.steps
+    value = qpts * args.steps / total
+    desc = (f"each step one complete FP64 oracle outer step of the {SAMPLE_CELLS}x{SAMPLE_CELLS}-cell cavity with the "
+            f"workload's {CFG['nv']}^3 velocities ({qpts} points), {cores} threads, timed; {args.warmup} untimed steps first")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(), "precision": "f64 (CPU oracle)", "parallelism": f"{cores} host threads"},
+            "config": {"workload": workload_name(), "precision": "f64 (CPU oracle)", "parallelism": f"{cores} host threads",
+                       "sample": desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def timed_steps(p, prec, steps, warmup, barrier, local, shard_kw=None):
+    """W untimed then K timed GSIS outer steps of a fresh solver on the device (CUDA events on
+    the solver's stream, clocks sampled meanwhile), with the per-phase profile of the timed
+    steps.  The solver is destroyed afterwards."""
+    import torch
+
+    from paper_2310_18916_gb300 import gsis
+
+    s = gsis.Solver(p, precision=prec, mode="gsis", **(shard_kw or {}))
+    for _ in range(warmup):
+        s.step()
+    s.profile(True, reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            s.step()
+        e1.record(stream)
+        barrier()
+    out = {"ms_total": e0.elapsed_time(e1)}
+    out["phase"], out["nsteps"], out["launches"] = s.profile(False)
+    out["eps"] = float(s.residual()[3])
+    out["macro_iters"] = s.stats()[1]
+    out["clocks"] = clk.summary()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return out
+
+
+PHASES = ("wall_prepass", "kinetic", "reduce_moments", "synthetic_fp64", "residual_state")
 
 
 def main():
@@ -470,9 +591,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16"],
-                    help="VDF storage (kinetic arithmetic is FP32 for f32 and bf16)")
+    ap.add_argument("--precision", default="f64", choices=["f32", "f64", "bf16"],
+                    help="VDF storage of the headline (kinetic arithmetic is FP64 for f64, FP32 for f32 and bf16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32 / BF16 sub-records and the time-to-steady comparison")
     ap.add_argument("--n", type=int, default=CFG["n"], help="cells per side (profiling cases use 64)")
     ap.add_argument("--nv", type=int, default=CFG["nv"], help="velocities per axis")
     ap.add_argument("--kn", type=float, default=CFG["Kn"])
@@ -533,33 +656,15 @@ def main():
     if sharded:
         from paper_2310_18916_gb300 import sharding
         shard_kw = dict(shard=(rank, world), allreduce=sharding.dist_allreduce())
-    s = gsis.Solver(p, precision=args.precision, mode="gsis", **shard_kw)
-    for _ in range(args.warmup):
-        s.step()
-    s.profile(True, reset=True)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        e0.record(stream)
-        for _ in range(args.steps):
-            s.step()
-        e1.record(stream)
-        barrier()
-    ms_total = e0.elapsed_time(e1)
-    phase, nsteps, launches = s.profile(False)
-    eps = float(s.residual()[3])
-    _, macro_iters = s.stats()
+    head = timed_steps(p, args.precision, args.steps, args.warmup, barrier, local, shard_kw)
+    ms_total = head["ms_total"]
     if dist is not None:
         t = torch.tensor([ms_total], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
     ms = ms_total / args.steps
     value = (1 if sharded else world) * pts * args.steps / (ms_total / 1e3)
-    kin_ms = phase[1] / max(nsteps, 1)
-    s.close()
-    del s
-    torch.cuda.empty_cache()
+    per = lambda rec, k: rec["phase"][PHASES.index(k)] / max(rec["nsteps"], 1)
 
     # end to end through the public API: create from host inputs, K steps each followed by a
     # device->host read of the state, destroy
@@ -573,8 +678,39 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     del s2
+    torch.cuda.empty_cache()
     h2d = p.nodes.nbytes + 6 * p.vx.nbytes + p.W0.nbytes
     d2h = W.nbytes + 4 * 8
+
+    # the FP32 / BF16 storage forms beside the FP64 headline: throughput, and time to steady
+    # state with the accuracy of the result against the FP64 solution
+    forms = None
+    if world == 1 and args.precision == "f64" and not args.no_forms:
+        vol = np.full(p.ncells, 1.0 / p.ncells)
+        tts = {}
+        for prec in ("f64", "f32", "bf16"):
+            tts[prec] = time_to_steady(p, prec, args.tts_tol, args.tts_max_steps)
+        forms = {"time_to_steady_f64": tts["f64"][0]}
+        for prec in ("f32", "bf16"):
+            r = timed_steps(p, prec, args.steps, args.warmup, barrier, local)
+            sb = {"f32": 4, "bf16": 2}[prec]
+            kin = per(r, "kinetic")
+            peak, peak_kind, _ = measured_peaks()
+            rec = {"value": pts * args.steps / (r["ms_total"] / 1e3), "unit": UNIT,
+                   "ms_per_step": r["ms_total"] / args.steps, "steps": args.steps, "warmup": args.warmup,
+                   "dtype": "f32", "storage": prec,
+                   "phase_ms_per_step": {k: per(r, k) for k in PHASES},
+                   "roofline_kinetic": {"kernel": "kinetic_kernel", "bound": "hbm",
+                                        "achieved": 2 * sb * pts / (kin / 1e3) / 1e9, "peak": peak,
+                                        "peak_kind": peak_kind, "unit": "GB/s",
+                                        "frac": 2 * sb * pts / (kin / 1e3) / 1e9 / peak,
+                                        "traffic": traffic("kinetic_kernel", prec),
+                                        "algorithmic_bytes_per_launch": 2 * sb * pts, "launch_ms": kin},
+                   "gpu_launches": r["launches"], "clocks": r["clocks"],
+                   "time_to_steady": tts[prec][0],
+                   "rel_l2_vs_f64": against_fp64(tts[prec][1], tts["f64"][1], vol),
+                   "speedup_time_to_steady_vs_f64": tts["f64"][0]["seconds"] / tts[prec][0]["seconds"]}
+            forms[prec] = rec
 
     if rank != 0:
         if dist is not None:
@@ -582,50 +718,70 @@ def main():
         return 0
     peak, peak_kind, sm_mhz = measured_peaks()
     sbytes = {"f32": 4, "f64": 8, "bf16": 2}[args.precision]
-    alg_bytes = 2 * sbytes * pts
-    achieved = alg_bytes / (kin_ms / 1e3) / 1e9
-    macro_ms = phase[3] / max(nsteps, 1)
+    kin_ms, macro_ms = per(head, "kinetic"), per(head, "synthetic_fp64")
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    fp64_peak = nsm * FP64_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    # (the flop tally is the five-field Shakhov solve's; the Rykov solve has no tally: no frac)
-    macro_flops = MACRO_FLOPS_PER_CELL_STEP_2D * p.ncells * macro_iters if nvdf == 1 else None
-    macro_tflops = macro_flops / (macro_ms / 1e3) / 1e12 if macro_flops else None
+    fp64_derived = nsm * 2 * 2 * sm_mhz * 1e6 / 1e12
+    try:
+        fp64_meas = fp64_peak_tflops() if world == 1 else None
+    except RuntimeError:
+        fp64_meas = None
+    fp64_peak = fp64_meas if fp64_meas else fp64_derived
+    fp64_kind = ("measured: cuBLAS DGEMM 6144^3 (torch.matmul, float64), best of 3, in this run" if fp64_meas else
+                 "derived: SMs x 2 FP64 FMA lanes x 2 flops x max SM clock")
+    macro_flops = MACRO_FLOPS_PER_CELL_STEP_2D * p.ncells * head["macro_iters"] if nvdf == 1 else None
     vdf_gb = p.ncells * p.nvel * sbytes / 1e9
+    if args.precision == "f64":
+        # the dominant kernel of the FP64 step: the kinetic kernel, bound by the FP64 pipe
+        kflops = KINETIC_FLOPS_PER_POINT_2D * pts if nvdf == 1 and p.nk == 1 else None
+        roof = {"kernel": "kinetic_kernel", "bound": "alu",
+                "achieved": kflops / (kin_ms / 1e3) / 1e12 if kflops else None, "peak": fp64_peak,
+                "peak_kind": fp64_kind, "unit": "TFLOP/s",
+                "frac": kflops / (kin_ms / 1e3) / 1e12 / fp64_peak if kflops else None,
+                "traffic": traffic("kinetic_kernel", "f64"), "algorithmic_flops_per_launch": kflops,
+                "flops_per_point": KINETIC_FLOPS_PER_POINT_2D, "launch_ms": kin_ms, "share_of_step": kin_ms / ms,
+                "algorithmic_bytes_per_launch": 2 * sbytes * pts,
+                "hbm_frac": 2 * sbytes * pts / (kin_ms / 1e3) / 1e9 / peak}
+    else:
+        roof = {"kernel": "kinetic_kernel", "bound": "hbm", "achieved": 2 * sbytes * pts / (kin_ms / 1e3) / 1e9,
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": 2 * sbytes * pts / (kin_ms / 1e3) / 1e9 / peak,
+                "traffic": traffic("kinetic_kernel", args.precision), "algorithmic_bytes_per_launch": 2 * sbytes * pts,
+                "launch_ms": kin_ms, "share_of_step": kin_ms / ms}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
-        "config": {"workload": workload_name(), "precision": f"{args.precision} VDF, f64 synthetic solve",
+        "config": {"workload": workload_name(),
+                   "precision": f"{args.precision} VDF, {'f64' if args.precision == 'f64' else 'f32'} kinetic "
+                                f"arithmetic, f64 synthetic solve",
                    "cells": p.ncells, "velocities": p.nvel, "points": pts,
                    "parallelism": f"velocity shards x{world}" if sharded else ("replicas" if world > 1 else "1 GPU"),
                    "l2": f"inputs larger than L2 (VDF {vdf_gb:.2f} GB)" if vdf_gb > 0.129 else
-                         f"VDF {vdf_gb:.3f} GB fits in L2 (profiling size)", "macro_inner_steps": macro_iters, "eps_last": eps},
-        "phase_ms_per_step": {k: v / max(nsteps, 1) for k, v in zip(
-            ("wall_prepass", "kinetic", "reduce_moments", "synthetic_fp64", "residual_state"), phase)},
+                         f"VDF {vdf_gb:.3f} GB fits in L2 (profiling size)", "macro_inner_steps": head["macro_iters"],
+                   "eps_last": head["eps"]},
+        "phase_ms_per_step": {k: per(head, k) for k in PHASES},
         "kinetic_updates_per_s": pts / (kin_ms / 1e3),
-        # the dominant kernel: the FP64 synthetic solve (one persistent launch per step)
-        "roofline": {"kernel": "macro_kernel", "bound": "alu", "achieved": macro_tflops, "peak": fp64_peak,
-                     "peak_kind": "derived FP64 peak: SMs x 2 FP64 FMA lanes x 2 flops x max SM clock",
-                     "unit": "TFLOP/s", "frac": macro_tflops / fp64_peak if macro_tflops else None,
-                     "traffic": DRAM_BYTES_PER_LAUNCH["macro_kernel"] if args.n == 128 and nvdf == 1 else None,
-                     "algorithmic_flops_per_launch": macro_flops, "flops_per_cell_inner_step": MACRO_FLOPS_PER_CELL_STEP_2D,
-                     "launch_ms": macro_ms, "share_of_step": macro_ms / ms},
-        "roofline_kinetic": {"kernel": "kinetic_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
-                             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                             "traffic": DRAM_BYTES_PER_LAUNCH["kinetic_kernel"]
-                             if args.n == 128 and args.precision == "f32" and nvdf == 1 else None,
-                             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": kin_ms, "share_of_step": kin_ms / ms},
+        "roofline": roof,
+        "roofline_synthetic": {"kernel": "macro_kernel", "bound": "alu",
+                               "achieved": macro_flops / (macro_ms / 1e3) / 1e12 if macro_flops else None,
+                               "peak": fp64_peak, "peak_kind": fp64_kind, "unit": "TFLOP/s",
+                               "frac": macro_flops / (macro_ms / 1e3) / 1e12 / fp64_peak if macro_flops else None,
+                               "traffic": traffic("macro_kernel", "f64") if args.n == 128 and nvdf == 1 else None,
+                               "algorithmic_flops_per_launch": macro_flops,
+                               "flops_per_cell_inner_step": MACRO_FLOPS_PER_CELL_STEP_2D, "launch_ms": macro_ms,
+                               "share_of_step": macro_ms / ms},
+        "fp64_peak_tflops": {"measured": fp64_meas, "derived": fp64_derived},
         "e2e": {"value": (1 if sharded else world) * args.steps * pts / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h, "seconds": e2e_s, "includes": "create from host inputs, steps, per-step state read, destroy"},
-        "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
     }
+    if forms is not None:
+        line["forms"] = forms
     if world == 1 and not args.no_cpu_baseline:
-        est, desc, wall = oracle_sample()
-        line["cpu_baseline"] = {"value": pts / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": desc, "sample_seconds": wall}
+        line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
