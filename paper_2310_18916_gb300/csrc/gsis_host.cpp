@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/gsis.h"
@@ -64,6 +65,11 @@ struct gsis_solver {
   std::vector<double> vel64;      // this shard's slots [slot][4]
   std::vector<double> vel64_all;  // every slot (wall constants integrate over all velocities)
   int nslots_all = 0;
+  std::vector<double> vaxis;      // the 1-D grids: nodes of x, y, z, then their weights
+  // FP64 storage with the Shakhov model: moments about the origin from a per-slot table and the
+  // reference distribution's sums in closed form (launch_moments_origin)
+  bool origin_mom = false;
+  double *d_mtab = nullptr, *d_vaxis = nullptr;
   // walls
   int nwall = 0;
   std::vector<int> wall_cell, wall_side, wall_sides_list;
@@ -291,11 +297,22 @@ struct gsis_solver {
   // and the wall fluxes
   template <typename T, typename S>
   int reduce_and_finalize(bool closed_scale) {
-    int rc = cuda(launch_moments<T, S>(kin_args<T, S>(), mom_bpc, mom_nchunks, d_mp, stream), "moments");
+    const bool first_shard = opt.shard_count <= 1 || opt.shard_index == 0;
+    int rc;
+    if constexpr (std::is_same<T, double>::value && std::is_same<S, double>::value) {
+      if (origin_mom)
+        rc = cuda(launch_moments_origin(kin_args<T, S>(), d_mtab, mom_bpc, mom_nchunks, d_st64, d_vaxis, nv_axis,
+                                        first_shard ? 1 : 0, d_mp, stream),
+                  "moments");
+      else
+        rc = cuda(launch_moments<T, S>(kin_args<T, S>(), mom_bpc, mom_nchunks, d_mp, stream), "moments");
+    } else {
+      rc = cuda(launch_moments<T, S>(kin_args<T, S>(), mom_bpc, mom_nchunks, d_mp, stream), "moments");
+    }
     if (rc) return rc;
     rc = cuda(launch_reduce<T>(d_mp, mom_nchunks, nvdf, static_cast<const T *>(d_wpart), d_boct, nblocks, kg, d_wall_cell,
-                               d_wall_side, nwall, d_rho_w, d_Zw, opt.shard_count <= 1 || opt.shard_index == 0,
-                               general, d_vol, d_st64, d_mom, d_K, d_wf, stream),
+                               d_wall_side, nwall, d_rho_w, d_Zw, first_shard, general, d_vol, d_st64, d_mom, d_K, d_wf,
+                               stream, origin_mom),
               "reduce");
     if (!rc) rc = exchange(d_mom, (size_t)nc * MOM_STRIDE, "moments");
     if (!rc) rc = exchange(d_K, (size_t)nc * 6, "kinetic flux sums");
@@ -662,23 +679,62 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   return GSIS_OK;
 }
 
-// Velocity slots: velocities grouped by octant (sign of each component, 0 counted +), each
-// octant padded to a multiple of VB with weight-0 copies of its first velocity.
-void build_slots(const gsis_vgrid *vg, std::vector<int> &slot_canon, std::vector<int8_t> &boct,
+// Tile shape (TX, TY, TZ), TX TY TZ = VB, that splits every octant of a tensor-product grid
+// exactly: each axis's count of negative and of non-negative nodes is a multiple of its tile
+// extent.  Only shapes with TX + TY + TZ <= KFAC_MAX per-axis factors qualify; {0, 0, 0} if none.
+static void choose_tile(const gsis_vgrid *vg, int tile[3]) {
+  static const int shapes[3][3] = {{4, 4, 2}, {4, 2, 4}, {2, 4, 4}};
+  tile[0] = tile[1] = tile[2] = 0;
+  int neg[3], pos[3];
+  for (int a = 0; a < 3; ++a) {
+    neg[a] = pos[a] = 0;
+    for (int i = 0; i < vg->n[a]; ++i) (vg->x[a][i] < 0 ? neg[a] : pos[a])++;
+  }
+  for (const auto &t : shapes) {
+    bool ok = t[0] + t[1] + t[2] <= KFAC_MAX;
+    for (int a = 0; a < 3 && ok; ++a) ok = neg[a] % t[a] == 0 && pos[a] % t[a] == 0;
+    if (ok) {
+      for (int a = 0; a < 3; ++a) tile[a] = t[a];
+      return;
+    }
+  }
+}
+
+// Velocity slots: velocities grouped by octant (sign of each component, 0 counted +).  With a
+// tile shape each block of VB slots is one TX x TY x TZ tile of its octant, lane
+// lx + TX (ly + TY lz) at the tile's node (lx, ly, lz), so that a Maxwellian over the block is a
+// product of TX + TY + TZ one-dimensional factors; otherwise each octant is listed x-fastest and
+// padded to a multiple of VB with weight-0 copies of its first velocity.
+void build_slots(const gsis_vgrid *vg, const int tile[3], std::vector<int> &slot_canon, std::vector<int8_t> &boct,
                  std::vector<double> &vel64) {
-  const int nx = vg->n[0], ny = vg->n[1], nz = vg->n[2];
   slot_canon.clear();
   boct.clear();
   vel64.clear();
+  const int nx = vg->n[0], ny = vg->n[1], nz = vg->n[2];
   for (int oct = 0; oct < 8; ++oct) {
+    std::vector<int> ax[3];
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < vg->n[a]; ++i)
+        if ((vg->x[a][i] < 0) == (((oct >> a) & 1) != 0)) ax[a].push_back(i);
     std::vector<int> list;
-    for (int iz = 0; iz < nz; ++iz)
-      for (int iy = 0; iy < ny; ++iy)
-        for (int ix = 0; ix < nx; ++ix) {
-          const double x = vg->x[0][ix], y = vg->x[1][iy], z = vg->x[2][iz];
-          const int o = (x < 0 ? 1 : 0) | (y < 0 ? 2 : 0) | (z < 0 ? 4 : 0);
-          if (o == oct) list.push_back(ix + nx * (iy + ny * iz));
-        }
+    if (tile[0] > 0) {
+      // nodes by increasing |xi| on each axis, so that mirror-image octants list mirror-image
+      // velocities in the same lane order
+      for (int a = 0; a < 3; ++a)
+        if ((oct >> a) & 1) std::reverse(ax[a].begin(), ax[a].end());
+      const int T0 = tile[0], T1 = tile[1], T2 = tile[2];
+      for (size_t bz = 0; bz < ax[2].size(); bz += T2)
+        for (size_t by = 0; by < ax[1].size(); by += T1)
+          for (size_t bx = 0; bx < ax[0].size(); bx += T0)
+            for (int lz = 0; lz < T2; ++lz)
+              for (int ly = 0; ly < T1; ++ly)
+                for (int lx = 0; lx < T0; ++lx)
+                  list.push_back(ax[0][bx + lx] + nx * (ax[1][by + ly] + ny * ax[2][bz + lz]));
+    } else {
+      for (int iz : ax[2])
+        for (int iy : ax[1])
+          for (int ix : ax[0]) list.push_back(ix + nx * (iy + ny * iz));
+    }
     if (list.empty()) continue;
     const size_t padded = (list.size() + VB - 1) / VB * VB;
     for (size_t t = 0; t < padded; ++t) {
@@ -1011,7 +1067,14 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
   s->nv_axis[1] = vg->n[1];
   s->nv_axis[2] = vg->n[2];
   s->nvc = vg->n[0] * vg->n[1] * vg->n[2];
-  build_slots(vg, s->slot_canon, s->boct, s->vel64);
+  // only the FP64 Shakhov kinetic kernel uses tiles (factored Maxwellians); FP32 and BF16 keep
+  // the x-fastest octant order
+  if (s->prec == GSIS_F64 && s->nvdf == 1) choose_tile(vg, s->kg.tile);
+  else s->kg.tile[0] = s->kg.tile[1] = s->kg.tile[2] = 0;
+  build_slots(vg, s->kg.tile, s->slot_canon, s->boct, s->vel64);
+  s->vaxis.clear();
+  for (int a = 0; a < 3; ++a) s->vaxis.insert(s->vaxis.end(), vg->x[a], vg->x[a] + vg->n[a]);
+  for (int a = 0; a < 3; ++a) s->vaxis.insert(s->vaxis.end(), vg->w[a], vg->w[a] + vg->n[a]);
   s->vel64_all = s->vel64;
   s->nslots_all = (int)s->slot_canon.size();
   const int K = s->opt.shard_count > 1 ? s->opt.shard_count : 1;
@@ -1097,6 +1160,8 @@ static size_t footprint(const gsis_solver *s) {
     b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36 + 36 + 6 + 36) * 8) +
          12 * 8 * (size_t)macro_general_parts((int)nc);
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
+  if (Sb == 8 && s->nvdf == 1)                      // FP64 origin moments: the extra chunk, the table
+    b += (size_t)nc * moment_len(1) * 8 + (size_t)s->nslots * 16 * 8 + s->vaxis.size() * 8;
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
   b += nc * (6 + 6 + 18 + 6 + 15 + 1 + 6 + 6 + 6 + 36 + 6 + 3 + 18 + 8 + 36) * 8;  // synthetic-solve work
@@ -1117,7 +1182,12 @@ static int allocate_and_upload(gsis_solver *s) {
     s->mom_bpc = std::max(1, std::min(64, (s->nblocks + want - 1) / want));
     s->mom_nchunks = (s->nblocks + s->mom_bpc - 1) / s->mom_bpc;
   }
-  A(s->d_mp, (size_t)s->mom_nchunks * nc * moment_len(s->nvdf) * sizeof(double));
+  s->origin_mom = std::is_same<T, double>::value && s->nvdf == 1;
+  A(s->d_mp, (size_t)(s->mom_nchunks + (s->origin_mom ? 1 : 0)) * nc * moment_len(s->nvdf) * sizeof(double));
+  if (s->origin_mom) {
+    A(s->d_mtab, (size_t)s->nslots * 16 * sizeof(double));
+    A(s->d_vaxis, s->vaxis.size() * sizeof(double));
+  }
   A(s->d_wpart, (size_t)s->nblocks * (s->nwall + 1) * NWF * sizeof(T));
   if (s->kin_scratch_bytes) A(s->d_kscratch, s->kin_scratch_bytes);
   if (s->general) {
@@ -1209,6 +1279,21 @@ static int allocate_and_upload(gsis_solver *s) {
   if (rc) return rc;
   std::vector<T> velT(s->vel64.begin(), s->vel64.end());
   rc = s->upload(s->d_vel, velT.data(), velT.size() * sizeof(T));
+  std::vector<double> mtab;
+  if (s->origin_mom) {
+    // per slot: w (1, x, y, z, xx, yy, zz, xy, xz, yz, |xi|^2 x, |xi|^2 y, |xi|^2 z), padded to 16
+    mtab.assign((size_t)s->nslots * 16, 0.0);
+    for (int v = 0; v < s->nslots; ++v) {
+      const double x = s->vel64[4 * v], y = s->vel64[4 * v + 1], z = s->vel64[4 * v + 2], w = s->vel64[4 * v + 3];
+      const double q2 = x * x + y * y + z * z;
+      const double t[NMOM] = {w, w * x, w * y, w * z, w * x * x, w * y * y, w * z * z, w * x * y, w * x * z, w * y * z,
+                              w * q2 * x, w * q2 * y, w * q2 * z};
+      for (int k = 0; k < NMOM; ++k) mtab[(size_t)v * 16 + k] = t[k];
+    }
+    if (!rc) rc = s->upload(s->d_mtab, mtab.data(), mtab.size() * sizeof(double));
+    if (!rc) rc = s->upload(s->d_vaxis, s->vaxis.data(), s->vaxis.size() * sizeof(double));
+    if (!rc) rc = s->cuda(cudaStreamSynchronize(s->stream), "sync");  // mtab leaves scope
+  }
   if (!rc) rc = s->upload(s->d_vel64, s->vel64_all.data(), s->vel64_all.size() * sizeof(double));
   for (int a = 0; a < 3 && !rc; ++a) {
     auto cv = cast_axis<T>(s->axc[a]);

@@ -72,7 +72,9 @@ struct KinGeom {
   int ntrans[3];        // transverse face count per axis (0 if inactive)
   int wall_base[6];     // first wall-face id of each side, -1 if not a wall
   double K3;            // venkat K^3: eps^2 = K^3 V
+  int tile[3];          // velocity blocks as TX x TY x TZ tiles of their octant ({0,0,0}: not tiled)
 };
+constexpr int KFAC_MAX = 10;    // one-dimensional Maxwellian factors per tiled block at most
 
 // General (curvilinear) structured meshes.  Per cell and side: the outward area vector S, the
 // vector r from the cell centre to the face centre, the least-squares weight w (gradient =
@@ -138,6 +140,12 @@ cudaError_t launch_wall_prepass(const KinArgs<T, S> &a, const int *wall_cell, co
                                 const double *Z0, double *rho_w, int nslots, cudaStream_t s);
 template <typename T, typename S>
 cudaError_t launch_moments(const KinArgs<T, S> &a, int blocks_per_chunk, int nchunks, double *mp, cudaStream_t s);
+// FP64 storage, Shakhov: moments about the origin from the per-slot table mtab [slot][16] into
+// chunks 0..nchunks-1 of mp, and the closed-form sums of w phi g^n (from the 1-D grids in vaxis:
+// nodes of x, y, z, then their weights) into chunk nchunks (zeros unless emit)
+cudaError_t launch_moments_origin(const KinArgs<double, double> &a, const double *mtab, int blocks_per_chunk,
+                                  int nchunks, const double *st64, const double *vaxis, const int *nv_axis, int emit,
+                                  double *mp, cudaStream_t s);
 template <typename T, typename S>
 cudaError_t launch_init_maxwellian(const KinArgs<T, S> &a, const double *W0, int nblocks, cudaStream_t s);
 template <typename T, typename S>
@@ -177,11 +185,15 @@ cudaError_t launch_wall_constants(const double *vel64, int nslots, const double 
 // per-chunk moment partials [chunk][cell][18] -> mom [cell][13] and kinetic flux sum
 // K [cell][6] (outward, area-integrated, via the delta-form identity); per-block wall partials
 // -> wf [wall][6] outward kinetic wall flux per unit area.
+// origin: the chunks hold FP64 moments about the origin and, in the last chunk, the sums of
+// w phi g^n (launch_moments_origin); the reduction forms the collision sums and shifts the
+// moments to the state velocity.
 template <typename T>
 cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpart, const int8_t *boct, int nblocks,
                           const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
                           const double *rho_w, const double *Zw, bool emit, bool general, const double *vol,
-                          const double *st64, double *mom, double *K, double *wf, cudaStream_t s);
+                          const double *st64, double *mom, double *K, double *wf, cudaStream_t s,
+                          bool origin = false);
 constexpr int MOM_STRIDE = NMOM + NMOM1;  // per-cell raw moments: f0 then f1
 
 struct FinalizeArgs {

@@ -75,9 +75,10 @@ struct StoredRelative<__nv_bfloat16> : std::true_type {};
 template <>
 struct StoredRelative<float> : std::true_type {};
 
-// state values a loader of stored f needs: 16, or 24 with the storage reference
+// state values a loader of stored f needs: 24 with the storage reference (FP32, BF16), 12 for
+// FP64 storage (slots 0..10, rounded up to whole 16-byte rows)
 template <typename S>
-__host__ __device__ constexpr int state_len() { return StoredRelative<S>::value ? 24 : 16; }
+__host__ __device__ constexpr int state_len() { return StoredRelative<S>::value ? 24 : 12; }
 
 // f^n from a stored value: f_raw = stored (+ M_r for relative storage), then Eq. updatef
 template <typename T, typename S>
@@ -138,6 +139,30 @@ __device__ __forceinline__ void reference(const T *st, T cx, T cy, T cz, T c2, T
 template <typename S, int NV>
 __host__ __device__ constexpr int stage_state_len() { return NV == 2 ? NST_RYKOV : state_len<S>(); }
 
+// Comparisons on the integer pipe for FP64.  On this GPU an FP64 comparison, min or max holds a
+// sub-partition's FP64 pipe as long as an FMA; the bit patterns of IEEE doubles order like their
+// values once the magnitude bits of negative values are inverted (sign-magnitude to two's
+// complement order), so the comparisons below give the same results on the integer pipe.  FP32
+// keeps its native comparisons.
+__device__ __forceinline__ long long ordered_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool is_greater(double a, double b) { return ordered_key(a) > ordered_key(b); }
+__device__ __forceinline__ bool is_greater(float a, float b) { return a > b; }
+__device__ __forceinline__ double larger(double a, double b) { return is_greater(a, b) ? a : b; }
+__device__ __forceinline__ float larger(float a, float b) { return a > b ? a : b; }
+__device__ __forceinline__ double smaller(double a, double b) { return is_greater(a, b) ? b : a; }
+__device__ __forceinline__ float smaller(float a, float b) { return a < b ? a : b; }
+// a > 0
+__device__ __forceinline__ bool is_positive(double a) { return __double_as_longlong(a) > 0; }
+__device__ __forceinline__ bool is_positive(float a) { return a > 0.f; }
+// a <= b and a < b for a, b >= 0 (non-negative doubles order like their bit patterns)
+__device__ __forceinline__ bool nonneg_le(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+__device__ __forceinline__ bool nonneg_le(float a, float b) { return a <= b; }
+__device__ __forceinline__ bool nonneg_lt(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool nonneg_lt(float a, float b) { return a < b; }
+
 // Venkatakrishnan limiter of one cell: min over its faces (and 1) of
 //   (Dm^2 + 2 D2 Dm + e^2) / (Dm^2 + D2 Dm + 2 D2^2 + e^2),
 // the face function with numerator and denominator divided by D2; both are positive, so
@@ -152,15 +177,15 @@ __device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const
 #pragma unroll
   for (int a = 0; a < NACT; ++a) {
     const T dh = gr[a] * rhi[a], dl = gr[a] * rlo[a];
-    const bool pos = gr[a] > (T)0;
+    const bool pos = is_positive(gr[a]);
     const T mh = pos ? dp : dn, ml = pos ? dn : dp;
-    const bool hi = fabs(mh) * fabs(dl) <= fabs(ml) * fabs(dh);
+    const bool hi = nonneg_le(fabs(mh) * fabs(dl), fabs(ml) * fabs(dh));
     // (gr = 0: D2 = 0 and the face value is 1, which never lowers the minimum)
     const T d2 = hi ? dh : dl, dm = hi ? mh : ml;
     const T dm2 = dm * dm + eps2;
     const T n = (T)2 * d2 * dm + dm2;
     const T d = d2 * ((T)2 * d2 + dm) + dm2;
-    if (n * bd < bn * d) { bn = n; bd = d; }
+    if (nonneg_lt(n * bd, bn * d)) { bn = n; bd = d; }
   }
   return ddiv(bn, bd);
 }
@@ -287,16 +312,17 @@ __device__ __forceinline__ void load_state_shared(const T *src, T *st, int n) {
 }
 
 // shared-memory layout of the kinetic kernel: the three-colour ring and the face buffers (T),
-// the bulk-copy staging area for one colour (stored f in S, then the state rows in T), the
-// mbarrier
+// with factored Maxwellians the factor cache of two colours (KFAC_MAX values per cell), the
+// bulk-copy staging area for one colour (stored f in S, then the state rows in T), the mbarrier
 template <typename T, typename S>
 struct KinSmem {
-  size_t ring, ebuf, rawf, rawst, bar, total;
-  __host__ __device__ KinSmem(const KinGeom &g, int nv, int sl) {
+  size_t ring, ebuf, fcache, rawf, rawst, bar, total;
+  __host__ __device__ KinSmem(const KinGeom &g, int nv, int sl, bool fx) {
     ring = 0;
     ebuf = ring + (size_t)3 * g.maxcol * nv * VB * sizeof(T);
-    rawf = ebuf;
-    for (int a = 0; a < 3; ++a) rawf += (size_t)g.ntrans[a] * nv * VB * sizeof(T);
+    fcache = ebuf;
+    for (int a = 0; a < 3; ++a) fcache += (size_t)g.ntrans[a] * nv * VB * sizeof(T);
+    rawf = fcache + (fx ? (size_t)2 * g.maxcol * KFAC_MAX * sizeof(T) : 0);
     rawf = (rawf + 15) & ~(size_t)15;
     rawst = (rawf + (size_t)g.maxcol * nv * VB * sizeof(S) + 15) & ~(size_t)15;
     bar = (rawst + (size_t)g.maxcol * sl * sizeof(T) + 15) & ~(size_t)15;
@@ -304,16 +330,29 @@ struct KinSmem {
   }
 };
 
+// FX: factored Maxwellians (FP64 Shakhov on a tiled velocity grid).  The block's 32 velocities
+// are a TX x TY x TZ tile, so exp(-|xi - u|^2 / T) over the block is the product of
+// F = TX + TY + TZ one-dimensional factors exp(-(xi_a - u_a)^2 / T).  When a cell is staged, lane
+// t < 2F evaluates factor t of the two Maxwellians of Eq. updatef (M(W^n) for t < F, M(W^{n-1/2})
+// above), one exponential per lane for the whole warp, and every lane gathers its three
+// factors of each by shuffles.  The factors of M(W^n) stay in the factor cache until the cell
+// is computed, where M(W^n) is also the Maxwellian of the reference distribution g.  Three
+// exponentials per point become one evaluation per 32 points per Maxwellian.
+template <typename T, typename S>
+__host__ __device__ inline bool factored(const KinGeom &g, int nvdf) {
+  return sizeof(T) == 8 && sizeof(S) == 8 && nvdf == 1 && g.tile[0] > 0;
+}
+
 // GM: the colour ring and face buffers of a velocity block too large for shared memory (3D
 // meshes: a colour of n^3 cells has O(n^2) cells) live in the block's own slice of a global
 // scratch (L2-resident where it fits), and each colour is staged with plain loads.  The
 // arithmetic and the order of every cell's inputs are those of the shared-memory kernel.
-template <typename T, typename S, int NACT, int NV, bool GM>
+template <typename T, typename S, int NACT, int NV, bool GM, bool FX>
 __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   const KinGeom &G = A.g;
   constexpr int SL = stage_state_len<S, NV>();
-  const KinSmem<T, S> L(G, NV, SL);
+  const KinSmem<T, S> L(G, NV, SL, FX);
   unsigned char *smem_raw = GM ? A.gscratch + (size_t)blockIdx.x * A.gstride : smem_dyn;
   T *ring = reinterpret_cast<T *>(smem_raw + L.ring);
   T *ebuf[3];
@@ -327,6 +366,7 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   }
   S *rawf = reinterpret_cast<S *>(smem_raw + L.rawf);
   T *rawst = reinterpret_cast<T *>(smem_raw + L.rawst);
+  T *fcache = reinterpret_cast<T *>(smem_raw + L.fcache);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L.bar);
   const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int oct = A.boct[b];
@@ -334,6 +374,26 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
   const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
   const T xi[3] = {vp[0], vp[1], vp[2]};
   const T wv = vp[3];
+  // factored Maxwellians: this lane's tile position (lx, ly, lz), the source lanes of its three
+  // factors, and the factor it evaluates: Maxwellian fj (0: W^n, 1: W^{n-1/2}), axis fa, node fx
+  int src[3] = {0, 0, 0}, fj = 0, fa = 0, NF = 0;
+  bool fon = false;
+  T fnode = (T)0;
+  if constexpr (FX) {
+    const int TX = G.tile[0], TY = G.tile[1];
+    NF = G.tile[0] + G.tile[1] + G.tile[2];
+    src[0] = lane % TX;
+    src[1] = TX + (lane / TX) % TY;
+    src[2] = TX + TY + lane / (TX * TY);
+    fon = lane < 2 * NF;
+    fj = lane >= NF ? 1 : 0;
+    const int r = lane - fj * NF;
+    fa = r < TX ? 0 : (r < TX + TY ? 1 : 2);
+    const int nl = fa == 0 ? r : (fa == 1 ? TX * (r - TX) : TX * TY * (r - TX - TY));
+    const T vx = __shfl_sync(0xffffffffu, xi[0], nl & 31), vy = __shfl_sync(0xffffffffu, xi[1], nl & 31),
+            vz = __shfl_sync(0xffffffffu, xi[2], nl & 31);
+    fnode = fa == 0 ? vx : (fa == 1 ? vy : vz);
+  }
   const T e2 = (T)0.5 * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
   T axi[3], Mw[3], Mw1[3];
   int upside[3];
@@ -407,7 +467,20 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) stored[q] = Fio<T, S>::ld(rawf + (size_t)(p * NV + q) * VB + lane);
       }
-      corrected_all<T, S, NV>(stored, st, xi[0], xi[1], xi[2], f);
+      if constexpr (FX) {
+        // this lane's factor of Maxwellian fj (state slots 0..4: W^n, 5..9: W^{n-1/2})
+        const T ua = fa == 0 ? (fj ? st[5] : st[0]) : (fa == 1 ? (fj ? st[6] : st[1]) : (fj ? st[7] : st[2]));
+        const T dv = fon ? fnode - ua : (T)0;
+        const T e = dexp(-dv * dv * (fj ? st[8] : st[3]));
+        if (fon && !fj) fcache[(size_t)((c & 1) * G.maxcol + p) * KFAC_MAX + lane] = e;
+        const T mn = st[4] * __shfl_sync(0xffffffffu, e, src[0]) * __shfl_sync(0xffffffffu, e, src[1]) *
+                     __shfl_sync(0xffffffffu, e, src[2]);
+        const T mo = st[9] * __shfl_sync(0xffffffffu, e, NF + src[0]) * __shfl_sync(0xffffffffu, e, NF + src[1]) *
+                     __shfl_sync(0xffffffffu, e, NF + src[2]);
+        f[0] = st[10] * stored[0] + mn - mo;
+      } else {
+        corrected_all<T, S, NV>(stored, st, xi[0], xi[1], xi[2], f);
+      }
 #pragma unroll
       for (int q = 0; q < NV; ++q) slot[(p * NV + q) * VB + lane] = f[q];
     }
@@ -480,13 +553,13 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
             T fup = fi[q], fdn = fi[q];
             if (nb[2 * a] >= 0) {
               fup = slotm[(nb[2 * a] * NV + q) * VB + lane];
-              fmax[q] = fmax[q] > fup ? fmax[q] : fup;
-              fmin[q] = fmin[q] < fup ? fmin[q] : fup;
+              fmax[q] = larger(fmax[q], fup);
+              fmin[q] = smaller(fmin[q], fup);
             }
             if (nb[2 * a + 1] >= 0) {
               fdn = slotp[(nb[2 * a + 1] * NV + q) * VB + lane];
-              fmax[q] = fmax[q] > fdn ? fmax[q] : fdn;
-              fmin[q] = fmin[q] < fdn ? fmin[q] : fdn;
+              fmax[q] = larger(fmax[q], fdn);
+              fmin[q] = smaller(fmin[q], fdn);
             }
             const T flo = sg[a] > 0 ? fup : fdn, fhi = sg[a] > 0 ? fdn : fup;
             gr[q][a] = gc.clo * (flo - fi[q]) + gc.chi * (fhi - fi[q]);
@@ -503,7 +576,15 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
       const T cx = xi[0] - st[0], cy = xi[1] - st[1], cz = xi[2] - st[2];
       const T c2 = cx * cx + cy * cy + cz * cz;
       T mw, g[NV];  // mw: Maxwellian of W^n
-      reference<T, NV>(st, cx, cy, cz, c2, mw, g);
+      if constexpr (FX) {
+        // M(W^n) from the cached factors (the product the staging formed for Eq. updatef), then
+        // the Shakhov g_0t of Section 2.2
+        const T *fc = fcache + (size_t)((c & 1) * G.maxcol + p) * KFAC_MAX;
+        mw = st[4] * fc[src[0]] * fc[src[1]] * fc[src[2]];
+        g[0] = mw * ((T)1 + (st[12] * cx + st[13] * cy + st[14] * cz) * (c2 * st[3] - (T)2.5));
+      } else {
+        reference<T, NV>(st, cx, cy, cz, c2, mw, g);
+      }
       T acc[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) acc[q] = (g[q] - fi[q]) * st[11];
@@ -570,7 +651,7 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
 template <typename T, typename S>
 size_t kinetic_smem_bytes(const KinGeom &g, int nvdf) {
   const int sl = nvdf == 2 ? stage_state_len<S, 2>() : stage_state_len<S, 1>();
-  return KinSmem<T, S>(g, nvdf, sl).total;
+  return KinSmem<T, S>(g, nvdf, sl, factored<T, S>(g, nvdf)).total;
 }
 
 // the ring and face buffers only (the bulk-copy staging area is not used from global memory),
@@ -578,27 +659,33 @@ size_t kinetic_smem_bytes(const KinGeom &g, int nvdf) {
 template <typename T, typename S>
 size_t kinetic_gscratch_stride(const KinGeom &g, int nvdf) {
   const int sl = nvdf == 2 ? stage_state_len<S, 2>() : stage_state_len<S, 1>();
-  return (KinSmem<T, S>(g, nvdf, sl).rawf + 255) & ~(size_t)255;
+  return (KinSmem<T, S>(g, nvdf, sl, factored<T, S>(g, nvdf)).rawf + 255) & ~(size_t)255;
 }
 
 template <typename T, typename S, bool GM>
-static void (*kinetic_fn_gm(int nact, int nvdf))(const KinArgs<T, S>) {
+static void (*kinetic_fn_gm(int nact, int nvdf, bool fx))(const KinArgs<T, S>) {
   if (nvdf == 2)
-    return nact == 1 ? kinetic_kernel<T, S, 1, 2, GM>
-                     : (nact == 2 ? kinetic_kernel<T, S, 2, 2, GM> : kinetic_kernel<T, S, 3, 2, GM>);
-  return nact == 1 ? kinetic_kernel<T, S, 1, 1, GM>
-                   : (nact == 2 ? kinetic_kernel<T, S, 2, 1, GM> : kinetic_kernel<T, S, 3, 1, GM>);
+    return nact == 1 ? kinetic_kernel<T, S, 1, 2, GM, false>
+                     : (nact == 2 ? kinetic_kernel<T, S, 2, 2, GM, false> : kinetic_kernel<T, S, 3, 2, GM, false>);
+  if constexpr (std::is_same<T, double>::value && std::is_same<S, double>::value) {
+    if (fx)
+      return nact == 1 ? kinetic_kernel<T, S, 1, 1, GM, true>
+                       : (nact == 2 ? kinetic_kernel<T, S, 2, 1, GM, true> : kinetic_kernel<T, S, 3, 1, GM, true>);
+  }
+  return nact == 1 ? kinetic_kernel<T, S, 1, 1, GM, false>
+                   : (nact == 2 ? kinetic_kernel<T, S, 2, 1, GM, false> : kinetic_kernel<T, S, 3, 1, GM, false>);
 }
 
 template <typename T, typename S>
-static void (*kinetic_fn(int nact, int nvdf, bool gm))(const KinArgs<T, S>) {
-  return gm ? kinetic_fn_gm<T, S, true>(nact, nvdf) : kinetic_fn_gm<T, S, false>(nact, nvdf);
+static void (*kinetic_fn(const KinGeom &g, int nvdf, bool gm))(const KinArgs<T, S>) {
+  const bool fx = factored<T, S>(g, nvdf);
+  return gm ? kinetic_fn_gm<T, S, true>(g.nact, nvdf, fx) : kinetic_fn_gm<T, S, false>(g.nact, nvdf, fx);
 }
 
 template <typename T, typename S>
 cudaError_t kinetic_shape(const KinGeom &g, int nvdf, bool gm, int want_warps, size_t smem, int *warps,
                           int *ctas_per_sm) {
-  void (*k)(const KinArgs<T, S>) = kinetic_fn<T, S>(g.nact, nvdf, gm);
+  void (*k)(const KinArgs<T, S>) = kinetic_fn<T, S>(g, nvdf, gm);
   cudaFuncAttributes attr;
   cudaError_t e = cudaFuncGetAttributes(&attr, k);
   if (e != cudaSuccess) return e;
@@ -610,7 +697,7 @@ cudaError_t kinetic_shape(const KinGeom &g, int nvdf, bool gm, int want_warps, s
 
 template <typename T, typename S>
 cudaError_t launch_kinetic(const KinArgs<T, S> &a, int nblocks, int nwarps, size_t smem, cudaStream_t s) {
-  void (*k)(const KinArgs<T, S>) = kinetic_fn<T, S>(a.g.nact, a.nvdf, a.gscratch != nullptr);
+  void (*k)(const KinArgs<T, S>) = kinetic_fn<T, S>(a.g, a.nvdf, a.gscratch != nullptr);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<nblocks, nwarps * 32, smem, s>>>(a);
@@ -666,8 +753,8 @@ __global__ void wall_prepass_kernel(const KinArgs<T, S> A, const int *wall_cell,
       T flo = fi, fhi = fi;
       if (has[a][0]) flo = corrected_stored<T, S>(Fio<T, S>::ld(Fb + (size_t)(cell - stride[a]) * VB + ln), stn[a][0], x, y, z);
       if (has[a][1]) fhi = corrected_stored<T, S>(Fio<T, S>::ld(Fb + (size_t)(cell + stride[a]) * VB + ln), stn[a][1], x, y, z);
-      if (has[a][0]) { fmax = fmax > flo ? fmax : flo; fmin = fmin < flo ? fmin : flo; }
-      if (has[a][1]) { fmax = fmax > fhi ? fmax : fhi; fmin = fmin < fhi ? fmin : fhi; }
+      if (has[a][0]) { fmax = larger(fmax, flo); fmin = smaller(fmin, flo); }
+      if (has[a][1]) { fmax = larger(fmax, fhi); fmin = smaller(fmin, fhi); }
       gr[a] = gc[a].clo * (flo - fi) + gc[a].chi * (fhi - fi);
       rlo[a] = gc[a].rlo;
       rhi[a] = gc[a].rhi;
@@ -903,6 +990,113 @@ cudaError_t launch_moments(const KinArgs<T, S> &a, int blocks_per_chunk, int nch
   return cudaGetLastError();
 }
 
+// FP64 storage with the Shakhov model: the 13 moments of the stored f^{n+1/2} about the origin,
+// sum_v f_v t_k(v) with the per-slot table t_k = w (1, xi(3), xi_a xi_b (6), |xi|^2 xi(3)) (16
+// doubles per slot, the last three 0): one FMA per moment and point and no exponential.  The
+// collision sums sum_v w phi (g^n - f) are assembled per cell by the reduction from the closed
+// form of sum_v w phi g^n (ref_sums_kernel) and these moments.  Per-block plain sums, compensated
+// (Kahan) across the chunk's blocks, as in moments_kernel.
+__global__ void __launch_bounds__(128) moments_origin_kernel(const KinArgs<double, double> A, const double *mtab,
+                                                             int blocks_per_chunk, double *mp) {
+  const int chunk = blockIdx.y;
+  const int b0 = chunk * blocks_per_chunk;
+  const int nb = min(blocks_per_chunk, A.nblocks - b0);
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= A.g.nc) return;
+  MomAcc<double, NMOM> acc;
+  acc.zero();
+  for (int bb = 0; bb < nb; ++bb) {
+    double f[VB];
+    load_block_f<double, double>(A.f + ((size_t)(b0 + bb) * A.g.nc + cell) * VB, f);
+    const double2 *tb = reinterpret_cast<const double2 *>(mtab + (size_t)(b0 + bb) * VB * 16);
+    double sum[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) sum[k] = 0.0;
+#pragma unroll
+    for (int l = 0; l < VB; ++l) {
+      double t[14];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const double2 v = __ldg(tb + l * 8 + q);
+        t[2 * q] = v.x;
+        t[2 * q + 1] = v.y;
+      }
+#pragma unroll
+      for (int k = 0; k < NMOM; ++k) sum[k] = fma(f[l], t[k], sum[k]);
+    }
+    acc.add(sum);
+  }
+  double *out = mp + ((size_t)chunk * A.g.nc + cell) * (NMOM + NFF);
+#pragma unroll
+  for (int k = 0; k < NMOM; ++k) out[k] = acc.s[k] - acc.c[k];
+#pragma unroll
+  for (int k = NMOM; k < NMOM + NFF; ++k) out[k] = 0.0;
+}
+
+// Closed form of sum_v w phi(xi) g^n(xi), phi = 1, xi(3), |xi|^2/2, for the Shakhov g_0t of
+// Section 2.2 on a tensor-product velocity grid: with c = xi - u and
+// g = C e^{-|c|^2/T} [1 + a.c (|c|^2/T - 5/2)], every term is a polynomial in c times a product
+// of one-dimensional Gaussians, so the sum over the grid factorises into the one-dimensional
+// sums m_a[k] = sum_i w_a(i) e^{-c_a(i)^2/T} c_a(i)^k (k <= 5).  One thread per cell writes its
+// row of the extra moment chunk (moments 0, collision sums in slots 13..17); emit = 0 (the
+// velocity shards other than the first) writes zeros, so the sum over shards counts it once.
+__global__ void ref_sums_kernel(int nc, const double *st64, const double *vaxis, int nx, int ny, int nz, int emit,
+                                double *row) {
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= nc) return;
+  double *o = row + (size_t)cell * (NMOM + NFF);
+#pragma unroll
+  for (int k = 0; k < NMOM + NFF; ++k) o[k] = 0.0;
+  if (!emit) return;
+  const double *st = st64 + (size_t)cell * NST;
+  const double u[3] = {st[0], st[1], st[2]}, invT = st[3], C = st[4], aq[3] = {st[12], st[13], st[14]};
+  const int n[3] = {nx, ny, nz};
+  const double *xs[3] = {vaxis, vaxis + nx, vaxis + nx + ny};
+  const double *ws[3] = {vaxis + nx + ny + nz, vaxis + 2 * nx + ny + nz, vaxis + 2 * nx + 2 * ny + nz};
+  double m[3][6];
+  for (int a = 0; a < 3; ++a) {
+    for (int k = 0; k < 6; ++k) m[a][k] = 0.0;
+    for (int i = 0; i < n[a]; ++i) {
+      const double c = xs[a][i] - u[a];
+      double p = ws[a][i] * exp(-c * c * invT);
+      for (int k = 0; k < 6; ++k) {
+        m[a][k] += p;
+        p *= c;
+      }
+    }
+  }
+  auto mono = [&](int px, int py, int pz) { return m[0][px] * m[1][py] * m[2][pz]; };
+  // sum_v w g c^e for the exponent triple e
+  auto G = [&](int px, int py, int pz) {
+    double t1 = 0.0;
+    for (int b = 0; b < 3; ++b) {
+      const int e[3] = {px + (b == 0), py + (b == 1), pz + (b == 2)};
+      const double s3 = mono(e[0] + 2, e[1], e[2]) + mono(e[0], e[1] + 2, e[2]) + mono(e[0], e[1], e[2] + 2);
+      t1 += aq[b] * (invT * s3 - 2.5 * mono(e[0], e[1], e[2]));
+    }
+    return C * (mono(px, py, pz) + t1);
+  };
+  const double g1 = G(0, 0, 0);
+  const double gc[3] = {G(1, 0, 0), G(0, 1, 0), G(0, 0, 1)};
+  const double gc2 = G(2, 0, 0) + G(0, 2, 0) + G(0, 0, 2);
+  o[NMOM] = g1;
+  for (int a = 0; a < 3; ++a) o[NMOM + 1 + a] = gc[a] + u[a] * g1;
+  o[NMOM + 4] = 0.5 * gc2 + (u[0] * gc[0] + u[1] * gc[1] + u[2] * gc[2]) +
+                0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * g1;
+}
+
+cudaError_t launch_moments_origin(const KinArgs<double, double> &a, const double *mtab, int blocks_per_chunk,
+                                  int nchunks, const double *st64, const double *vaxis, const int *nv_axis, int emit,
+                                  double *mp, cudaStream_t s) {
+  dim3 grid((a.g.nc + 127) / 128, nchunks);
+  moments_origin_kernel<<<grid, 128, 0, s>>>(a, mtab, blocks_per_chunk, mp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ref_sums_kernel<<<(a.g.nc + 127) / 128, 128, 0, s>>>(a.g.nc, st64, vaxis, nv_axis[0], nv_axis[1], nv_axis[2], emit,
+                                                       mp + (size_t)nchunks * a.g.nc * (NMOM + NFF));
+  return cudaGetLastError();
+}
+
 // f_raw = Maxwellian(W0) of each cell at each slot velocity, in the storage precision (the
 // per-cell factor rho (pi T)^(-3/2) and 1/T in FP64, the exponential in T).  Relative (BF16,
 // FP32) storage writes zero deviations from M(W0), which the initial state names as the
@@ -1094,8 +1288,8 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
           gr[0] += g.f[s].w[0] * d;
           gr[1] += g.f[s].w[1] * d;
           gr[2] += g.f[s].w[2] * d;
-          fmax = fmax > fj[s] ? fmax : fj[s];
-          fmin = fmin < fj[s] ? fmin : fj[s];
+          fmax = larger(fmax, fj[s]);
+          fmin = smaller(fmin, fj[s]);
         }
         const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
 #pragma unroll
@@ -1322,8 +1516,8 @@ __global__ void __launch_bounds__(256) wall_prepass_general_kernel(const KinArgs
         gr[0] += g.f[s].w[0] * d;
         gr[1] += g.f[s].w[1] * d;
         gr[2] += g.f[s].w[2] * d;
-        fmax = fmax > fj ? fmax : fj;
-        fmin = fmin < fj ? fmin : fj;
+        fmax = larger(fmax, fj);
+        fmin = smaller(fmin, fj);
       }
       const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
       const T ff = fi + (phi * gr[0]) * fa.r[0] + (phi * gr[1]) * fa.r[1] + (phi * gr[2]) * fa.r[2];

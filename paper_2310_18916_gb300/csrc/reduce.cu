@@ -40,6 +40,53 @@ __global__ void reduce_moments_kernel(const double *mp, int nchunks, int nc, int
   }
 }
 
+// FP64 storage, Shakhov: chunks 0..nchunks-1 hold sum w f (1, xi, xi xi, |xi|^2 xi) about the
+// origin, the last chunk sum w phi g^n.  Per cell: K = V/tau (G - F) with F = sum w phi f
+// (phi = 1, xi, |xi|^2/2), and the moments about the state velocity u by the binomial shift
+//   M1 = S1 - u S0,  M2_ab = S2_ab - u_a S1_b - u_b S1_a + u_a u_b S0,
+//   M3_a = S3_a - u_a tr S2 - 2 (S2 u)_a + 2 u_a (u.S1) + |u|^2 S1_a - |u|^2 u_a S0.
+__global__ void reduce_origin_kernel(const double *mp, int nrows, int nc, const double *vol, const double *st64,
+                                     double *mom, double *K) {
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= nc) return;
+  constexpr int NP = NMOM + NFF;
+  double S[NP];
+  for (int k = 0; k < NP; ++k) S[k] = 0.0;
+  for (int ch = 0; ch < nrows; ++ch) {
+    const double *r = mp + ((size_t)ch * nc + cell) * NP;
+    for (int k = 0; k < NP; ++k) S[k] += r[k];
+  }
+  const double *st = st64 + (size_t)cell * NST;
+  const double u[3] = {st[0], st[1], st[2]};
+  const double kf = vol[cell] * st[11];
+  const double S0 = S[0], S1[3] = {S[1], S[2], S[3]};
+  const double S2[3][3] = {{S[4], S[7], S[8]}, {S[7], S[5], S[9]}, {S[8], S[9], S[6]}};
+  const double trS2 = S[4] + S[5] + S[6];
+  double *k6 = K + (size_t)cell * 6;
+  k6[0] = kf * (S[NMOM] - S0);
+  for (int a = 0; a < 3; ++a) k6[1 + a] = kf * (S[NMOM + 1 + a] - S1[a]);
+  k6[4] = kf * (S[NMOM + 4] - 0.5 * trS2);
+  k6[5] = 0.0;
+  const double uS1 = u[0] * S1[0] + u[1] * S1[1] + u[2] * S1[2];
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  double M2[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) M2[a][b] = S2[a][b] - u[a] * S1[b] - u[b] * S1[a] + u[a] * u[b] * S0;
+  double *M = mom + (size_t)cell * MOM_STRIDE;
+  M[0] = S0;
+  for (int a = 0; a < 3; ++a) M[1 + a] = S1[a] - u[a] * S0;
+  M[4] = M2[0][0];
+  M[5] = M2[1][1];
+  M[6] = M2[2][2];
+  M[7] = M2[0][1];
+  M[8] = M2[0][2];
+  M[9] = M2[1][2];
+  for (int a = 0; a < 3; ++a) {
+    const double S2u = S2[a][0] * u[0] + S2[a][1] * u[1] + S2[a][2] * u[2];
+    M[10 + a] = S[10 + a] - u[a] * trS2 - 2.0 * S2u + 2.0 * u[a] * uS1 + uu * S1[a] - uu * u[a] * S0;
+  }
+}
+
 // Outward kinetic wall flux per unit area: the half moving towards the wall from the wall cells'
 // block partials (blocks whose octant moves towards this wall), the re-emitted half rho_w Zw.
 // General meshes (general = 1): every block's partial already holds both halves along the
@@ -75,13 +122,16 @@ template <typename T>
 cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpart, const int8_t *boct, int nblocks,
                           const KinGeom &g, const int *wall_cell, const int *wall_side, int nwall,
                           const double *rho_w, const double *Zw, bool emit, bool general, const double *vol,
-                          const double *st64, double *mom, double *K, double *wf, cudaStream_t s) {
+                          const double *st64, double *mom, double *K, double *wf, cudaStream_t s, bool origin) {
   (void)wall_cell;
   const int np = moment_len(nvdf);
   const size_t n = (size_t)g.nc * np;
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 16) grid = 152 * 16;
-  reduce_moments_kernel<<<grid, 256, 0, s>>>(mp, nchunks, g.nc, np, vol, st64, mom, K);
+  if (origin)
+    reduce_origin_kernel<<<(g.nc + 127) / 128, 128, 0, s>>>(mp, nchunks + 1, g.nc, vol, st64, mom, K);
+  else
+    reduce_moments_kernel<<<grid, 256, 0, s>>>(mp, nchunks, g.nc, np, vol, st64, mom, K);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nwall == 0 || wpart == nullptr) return e;
   reduce_wall_kernel<T><<<nwall, 32 * NWF, 0, s>>>(wpart, boct, nblocks, nwall, wall_side, rho_w, Zw, emit ? 1 : 0,
@@ -90,11 +140,12 @@ cudaError_t launch_reduce(const double *mp, int nchunks, int nvdf, const T *wpar
 }
 template cudaError_t launch_reduce<float>(const double *, int, int, const float *, const int8_t *, int, const KinGeom &,
                                           const int *, const int *, int, const double *, const double *, bool, bool,
-                                          const double *, const double *, double *, double *, double *, cudaStream_t);
+                                          const double *, const double *, double *, double *, double *, cudaStream_t,
+                                          bool);
 template cudaError_t launch_reduce<double>(const double *, int, int, const double *, const int8_t *, int,
                                            const KinGeom &, const int *, const int *, int, const double *,
                                            const double *, bool, bool, const double *, const double *, double *,
-                                           double *, double *, cudaStream_t);
+                                           double *, double *, cudaStream_t, bool);
 
 // ---------------------------------------------------------------------------------------------
 // Raw moments about the state velocity un -> rho, u, Tt, sigma, q about the mean velocity.
