@@ -343,8 +343,13 @@ def run_couette(args):
 # keeps a positive density in the wake for the steps timed here), FP32 / BF16 storage.
 BODIES = {
     # sphere of diameter 1: 32 radial (first 0.0224, ratio 1.1, R_out 5) x 24 polar x 48 azimuthal
-    # cells, Ma 4, Kn 0.05, 48^3 velocities on [-12, 12]^3
-    "sphere": dict(kind="sphere", n=(32, 24, 48), nv=48, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0),
+    # cells, Ma 4, Kn 0.05, 48^3 velocities on [-12, 12]^3 clustered about the free stream
+    "sphere": dict(kind="sphere", n=(32, 24, 48), nv=48, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0,
+                   clustered=True),
+    # the same sphere on a locally refined unstructured velocity set (truncation sphere about the
+    # post-shock velocity, refined about the free stream and the wall velocity)
+    "sphere_vset": dict(kind="sphere", n=(32, 24, 48), nv=4, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0,
+                        vset=dict(n_base=16, refine=3)),
     # cylinder of diameter 1 in cross flow: 64 radial (first 0.01, R_out 10) x 128 azimuthal cells,
     # Ma 2, Kn 0.05, 40^3 velocities on [-9, 9]^3
     "cylinder": dict(kind="cylinder", n=(64, 1, 128), nv=40, vmax=9.0, Ma=2.0, Kn=0.05, first=0.01, R_out=10.0),
@@ -363,8 +368,13 @@ def body_problem(name):
 
     b = BODIES[name]
     if b["kind"] == "sphere":
-        return wl.sphere(n_r=b["n"][0], n_pol=b["n"][1], n_az=b["n"][2], nv=b["nv"], R=0.5, R_out=b["R_out"],
-                         first=b["first"], Ma=b["Ma"], Kn=b["Kn"], vmax=b["vmax"])
+        p = wl.sphere(n_r=b["n"][0], n_pol=b["n"][1], n_az=b["n"][2], nv=b["nv"], R=0.5, R_out=b["R_out"],
+                      first=b["first"], Ma=b["Ma"], Kn=b["Kn"], vmax=b["vmax"])
+        if b.get("clustered"):
+            p = wl.with_clustered_velocities(p, b["nv"], b["vmax"])
+        if b.get("vset"):
+            p = wl.with_velocity_set(p, wl.hybrid_velocity_set(p.wall_u[1], T_inf=1.0, T_w=p.wall_T[0], **b["vset"]))
+        return p
     return wl.cylinder(n_r=b["n"][0], n_theta=b["n"][2], nv=b["nv"], R=0.5, R_out=b["R_out"], first=b["first"],
                        Ma=b["Ma"], Kn=b["Kn"], vmax=b["vmax"])
 
@@ -463,6 +473,7 @@ def body_oracle_sample(name):
     b = BODIES[name]
     v, w = wl.midpoint_grid(12, -b["vmax"], b["vmax"])
     p.vx, p.vy, p.vz, p.wx, p.wy, p.wz = v, v.copy(), v.copy(), w, w.copy(), w.copy()
+    p.vpoints = None
     cores = os.cpu_count() or 1
     if b.get("mode", "dvm") == "gsis":
         o = Oracle(p, mode=0, n_sweeps=BODY_SWEEPS, nthreads=cores)

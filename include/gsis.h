@@ -73,13 +73,20 @@ typedef struct {
   double wall_T[6];
 } gsis_mesh;
 
-/* Tensor-product discrete velocity grid (Section 3.1, velocity-space discretisation):
- * n[d] nodes x[d][.] with quadrature weights w[d][.] per axis d (host arrays, copied).
- * The discrete velocity index used by gsis_get_f / gsis_set_f is v = ix + n0 (iy + n1 iz). */
+/* Discrete velocity set (Section 3.1, velocity-space discretisation), host arrays, copied.
+ * Tensor product (npoints = 0): n[d] nodes x[d][.] with quadrature weights w[d][.] per axis d;
+ *   the discrete velocity index used by gsis_get_f / gsis_set_f is v = ix + n0 (iy + n1 iz).
+ * Unstructured (npoints > 0; the locally refined velocity meshes of the paper's unstructured
+ *   velocity-space discretisation): points[v][4] = xi_x, xi_y, xi_z and the quadrature weight
+ *   (the volume of the velocity cell of discrete velocity v), v = 0 .. npoints-1 the index of
+ *   gsis_get_f / gsis_set_f; n, x and w are not read.  Weights must be positive and finite,
+ *   else GSIS_E_INVALID. */
 typedef struct {
   int n[3];
   const double *x[3];
   const double *w[3];
+  int npoints;
+  const double *points;
 } gsis_vgrid;
 
 /* Gas model (Section 2): Shakhov (monatomic, Pr = 2/3; the g_0t reference distribution) or

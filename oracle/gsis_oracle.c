@@ -45,6 +45,7 @@ struct orc_solver {
   int nvdf;              /* 1 (Shakhov) or 2 (Rykov) */
   int nW;                /* 5 (Shakhov) or 6 (Rykov) conservative components */
   double *vx, *vy, *vz, *wx, *wy, *wz;
+  double *pts;           /* unstructured velocity set [v][4] (NULL: the tensor product above) */
   /* geometry */
   double *vol, *xc, *S, *xf, *eps2;
   int *nb;               /* per cell and side: >=0 neighbour, -1 wall, -2 absent (inactive axis),
@@ -71,7 +72,15 @@ struct orc_solver {
 
 static int cid(const orc_solver *s, int i, int j, int k) { return i + s->ni * (j + s->nj * k); }
 
+/* discrete velocity v and its quadrature weight (Section 3.1): a node of the tensor product of
+   the three axis grids, or point v of an unstructured set with its velocity cell's volume */
 static void vel_of(const orc_solver *s, int v, double xi[3], double *w) {
+  if (s->pts) {
+    const double *q = s->pts + 4 * (size_t)v;
+    xi[0] = q[0]; xi[1] = q[1]; xi[2] = q[2];
+    *w = q[3];
+    return;
+  }
   int ix = v % s->nvx, iy = (v / s->nvx) % s->nvy, iz = v / (s->nvx * s->nvy);
   xi[0] = s->vx[ix]; xi[1] = s->vy[iy]; xi[2] = s->vz[iz];
   *w = s->wx[ix] * s->wy[iy] * s->wz[iz];
@@ -1067,6 +1076,12 @@ static int run_step(orc_solver *s, int mode) {
 
 int orc_step(orc_solver *s) { return run_step(s, s->o.mode); }
 
+/* 1/dt of the kinetic delta form for the following steps (a pseudo-time schedule) */
+void orc_set_kin_inv_dt(orc_solver *s, double inv_dt) { s->o.kin_inv_dt = inv_dt; }
+
+/* run the next steps in another mode (ORC_GSIS or ORC_DVM) */
+void orc_set_mode(orc_solver *s, int mode) { s->o.mode = mode; }
+
 int orc_presteps(orc_solver *s, int n) {
   for (int t = 0; t < n; ++t) {
     int rc = run_step(s, ORC_DVM);
@@ -1097,7 +1112,7 @@ static double *dup(const double *a, int n) {
 
 void orc_destroy(orc_solver *s) {
   if (!s) return;
-  free(s->vx); free(s->vy); free(s->vz); free(s->wx); free(s->wy); free(s->wz);
+  free(s->vx); free(s->vy); free(s->vz); free(s->wx); free(s->wy); free(s->wz); free(s->pts);
   free(s->vol); free(s->xc); free(s->S); free(s->xf); free(s->eps2); free(s->nb); free(s->wid);
   free(s->wcell); free(s->wside); free(s->rho_w);
   free(s->f0); free(s->f1); free(s->st); free(s->Mh); free(s->hot); free(s->kin); free(s->fkin); free(s->corder);
@@ -1131,12 +1146,23 @@ static int init_state_from_f(orc_solver *s) {
 int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const orc_opts *o, const double *W0,
                orc_solver **out) {
   *out = NULL;
-  if (m->ni < 1 || m->nj < 1 || m->nk < 1 || vg->n[0] < 1 || vg->n[1] < 1 || vg->n[2] < 1) return ORC_E_INVALID;
+  if (m->ni < 1 || m->nj < 1 || m->nk < 1) return ORC_E_INVALID;
+  if (vg->npoints > 0 ? !vg->points : (vg->n[0] < 1 || vg->n[1] < 1 || vg->n[2] < 1)) return ORC_E_INVALID;
   if (g->model == ORC_RYKOV && !(g->d_r > 0)) return ORC_E_INVALID;
   orc_solver *s = (orc_solver *)calloc(1, sizeof(orc_solver));
   if (!s) return ORC_E_OOM;
   s->ni = m->ni; s->nj = m->nj; s->nk = m->nk; s->nc = m->ni * m->nj * m->nk;
-  s->nvx = vg->n[0]; s->nvy = vg->n[1]; s->nvz = vg->n[2]; s->nv = s->nvx * s->nvy * s->nvz;
+  if (vg->npoints > 0) {
+    /* one-node placeholders for the unused axis arrays */
+    static const double one = 1.0;
+    s->nvx = s->nvy = s->nvz = 1;
+    s->nv = vg->npoints;
+    s->pts = dup(vg->points, 4 * vg->npoints);
+    s->vx = dup(&one, 1); s->vy = dup(&one, 1); s->vz = dup(&one, 1);
+    s->wx = dup(&one, 1); s->wy = dup(&one, 1); s->wz = dup(&one, 1);
+  } else {
+    s->nvx = vg->n[0]; s->nvy = vg->n[1]; s->nvz = vg->n[2]; s->nv = s->nvx * s->nvy * s->nvz;
+  }
   memcpy(s->bc, m->bc, sizeof s->bc);
   memcpy(s->wall_u, m->wall_u, sizeof s->wall_u);
   memcpy(s->wall_T, m->wall_T, sizeof s->wall_T);
@@ -1144,8 +1170,10 @@ int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const o
   if (s->o.n_sweeps < 1) s->o.n_sweeps = 1;
   s->nvdf = g->model == ORC_RYKOV ? 2 : 1;
   s->nW = g->model == ORC_RYKOV ? 6 : 5;
-  s->vx = dup(vg->x[0], s->nvx); s->vy = dup(vg->x[1], s->nvy); s->vz = dup(vg->x[2], s->nvz);
-  s->wx = dup(vg->w[0], s->nvx); s->wy = dup(vg->w[1], s->nvy); s->wz = dup(vg->w[2], s->nvz);
+  if (!s->pts) {
+    s->vx = dup(vg->x[0], s->nvx); s->vy = dup(vg->x[1], s->nvy); s->vz = dup(vg->x[2], s->nvz);
+    s->wx = dup(vg->w[0], s->nvx); s->wy = dup(vg->w[1], s->nvy); s->wz = dup(vg->w[2], s->nvz);
+  }
   int nc = s->nc;
   s->vol = (double *)malloc(sizeof(double) * nc);
   s->xc = (double *)malloc(sizeof(double) * 3 * nc);
@@ -1161,7 +1189,7 @@ int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const o
   s->fkin = (double *)calloc(36 * (size_t)nc, sizeof(double));
   s->f0 = (double *)malloc(sizeof(double) * (size_t)nc * s->nv);
   s->f1 = s->nvdf == 2 ? (double *)malloc(sizeof(double) * (size_t)nc * s->nv) : NULL;
-  if (!s->vx || !s->vy || !s->vz || !s->wx || !s->wy || !s->wz || !s->vol || !s->xc || !s->S || !s->xf ||
+  if (!s->vx || !s->vy || !s->vz || !s->wx || !s->wy || !s->wz || (vg->npoints > 0 && !s->pts) || !s->vol || !s->xc || !s->S || !s->xf ||
       !s->eps2 || !s->nb || !s->wid || !s->st || !s->Mh || !s->hot || !s->kin || !s->fkin || !s->f0 || (s->nvdf == 2 && !s->f1)) {
     orc_destroy(s);
     return ORC_E_OOM;

@@ -39,6 +39,8 @@ typedef struct {
   int n[3];
   const double *x[3];   /* nodes per axis */
   const double *w[3];   /* quadrature weights per axis */
+  int npoints;          /* > 0: an unstructured set of npoints velocities (n, x, w unused) */
+  const double *points; /* [npoints][4]: xi_x, xi_y, xi_z, weight (the velocity cell's volume) */
 } orc_vgrid;
 
 typedef struct {
@@ -73,6 +75,9 @@ int orc_get_f(const orc_solver *s, double *f0, double *f1);
 
 /* One outer iteration of Algorithm 1 (mode GSIS) or one plain DVM step (mode DVM). */
 int orc_step(orc_solver *s);
+/* 1/dt of the kinetic delta form and the mode for the following steps. */
+void orc_set_kin_inv_dt(orc_solver *s, double inv_dt);
+void orc_set_mode(orc_solver *s, int mode);
 /* n plain kinetic steps whatever the mode (the preconditioning of Algorithm 1). */
 int orc_presteps(orc_solver *s, int n);
 /* Euler preconditioning: n inner steps of the inviscid synthetic solve (slip walls, far field

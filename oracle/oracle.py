@@ -21,7 +21,7 @@ class OrcMesh(C.Structure):
 
 
 class OrcVgrid(C.Structure):
-    _fields_ = [("n", C.c_int * 3), ("x", D * 3), ("w", D * 3)]
+    _fields_ = [("n", C.c_int * 3), ("x", D * 3), ("w", D * 3), ("npoints", C.c_int), ("points", D)]
 
 
 class OrcGas(C.Structure):
@@ -48,6 +48,8 @@ def lib():
                      "orc_nwall", "orc_macro_iters"):
             getattr(L, name).argtypes = [C.c_void_p]
         L.orc_presteps.argtypes = [C.c_void_p, C.c_int]
+        L.orc_set_kin_inv_dt.argtypes = [C.c_void_p, C.c_double]
+        L.orc_set_mode.argtypes = [C.c_void_p, C.c_int]
         L.orc_euler_presteps.argtypes = [C.c_void_p, C.c_int]
         L.orc_kinetic_velocities.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_eps.argtypes = [C.c_void_p]
@@ -119,6 +121,11 @@ class Oracle:
             vg.n[a] = len(x)
             vg.x[a] = _p(x)
             vg.w[a] = _p(w)
+        if getattr(p, "vpoints", None) is not None:
+            pts = np.ascontiguousarray(p.vpoints, dtype=np.float64)
+            self._keep.append(pts)
+            vg.npoints = len(pts)
+            vg.points = _p(pts)
         g = gas_struct(p)
         oo = OrcOpts(**o)
         W = np.ascontiguousarray(p.W0 if W0 is None else W0, dtype=np.float64)
@@ -145,6 +152,12 @@ class Oracle:
         for _ in range(n):
             self._rc(lib().orc_step(self.h), "orc_step")
         return self.eps
+
+    def set_kin_inv_dt(self, inv_dt):
+        lib().orc_set_kin_inv_dt(self.h, float(inv_dt))
+
+    def set_mode(self, mode):
+        lib().orc_set_mode(self.h, int(mode))
 
     def presteps(self, n):
         self._rc(lib().orc_presteps(self.h, n), "orc_presteps")

@@ -66,6 +66,7 @@ struct gsis_solver {
   std::vector<double> vel64_all;  // every slot (wall constants integrate over all velocities)
   int nslots_all = 0;
   std::vector<double> vaxis;      // the 1-D grids: nodes of x, y, z, then their weights
+  bool point_set = false;         // an unstructured velocity set (no tensor product)
   // FP64 storage with the Shakhov model: moments about the origin from a per-slot table and the
   // reference distribution's sums in closed form (launch_moments_origin)
   bool origin_mom = false;
@@ -601,8 +602,20 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     why = "too many cells";
     return GSIS_E_UNSUPPORTED;
   }
-  for (int d = 0; d < 3; ++d)
-    if (vg->n[d] < 1 || !vg->x[d] || !vg->w[d]) { why = "bad velocity grid"; return GSIS_E_INVALID; }
+  if (vg->npoints > 0) {
+    if (!vg->points) { why = "npoints > 0 needs points"; return GSIS_E_INVALID; }
+    for (int v = 0; v < vg->npoints; ++v) {
+      const double *q = vg->points + 4 * (size_t)v;
+      if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) || !(q[3] > 0) || !std::isfinite(q[3])) {
+        why = "velocity points must be finite with positive weights";
+        return GSIS_E_INVALID;
+      }
+    }
+  } else {
+    if (vg->npoints < 0) { why = "npoints must be >= 0"; return GSIS_E_INVALID; }
+    for (int d = 0; d < 3; ++d)
+      if (vg->n[d] < 1 || !vg->x[d] || !vg->w[d]) { why = "bad velocity grid"; return GSIS_E_INVALID; }
+  }
   if (!(Kn > 0)) { why = "Kn must be positive"; return GSIS_E_INVALID; }
   if (!(o->venkat_K > 0)) { why = "venkat_K must be positive"; return GSIS_E_INVALID; }
   if (o->precision != GSIS_F32 && o->precision != GSIS_F64 && o->precision != GSIS_BF16) {
@@ -710,6 +723,27 @@ void build_slots(const gsis_vgrid *vg, const int tile[3], std::vector<int> &slot
   slot_canon.clear();
   boct.clear();
   vel64.clear();
+  if (vg->npoints > 0) {
+    // an unstructured set: each octant's points in input order, padded with weight-0 copies
+    for (int oct = 0; oct < 8; ++oct) {
+      std::vector<int> list;
+      for (int v = 0; v < vg->npoints; ++v) {
+        const double *q = vg->points + 4 * (size_t)v;
+        const int o = (q[0] < 0 ? 1 : 0) | (q[1] < 0 ? 2 : 0) | (q[2] < 0 ? 4 : 0);
+        if (o == oct) list.push_back(v);
+      }
+      if (list.empty()) continue;
+      const size_t padded = (list.size() + VB - 1) / VB * VB;
+      for (size_t t = 0; t < padded; ++t) {
+        const bool real = t < list.size();
+        const double *q = vg->points + 4 * (size_t)(real ? list[t] : list[0]);
+        slot_canon.push_back(real ? list[t] : list[0]);
+        vel64.insert(vel64.end(), {q[0], q[1], q[2], real ? q[3] : 0.0});
+      }
+      for (size_t b = 0; b < padded / VB; ++b) boct.push_back((int8_t)oct);
+    }
+    return;
+  }
   const int nx = vg->n[0], ny = vg->n[1], nz = vg->n[2];
   for (int oct = 0; oct < 8; ++oct) {
     std::vector<int> ax[3];
@@ -1063,18 +1097,19 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
     if (col == 0) s->ncol0 = (int)s->colcells.size();
   }
   // velocities
-  s->nv_axis[0] = vg->n[0];
-  s->nv_axis[1] = vg->n[1];
-  s->nv_axis[2] = vg->n[2];
-  s->nvc = vg->n[0] * vg->n[1] * vg->n[2];
+  s->point_set = vg->npoints > 0;
+  for (int a = 0; a < 3; ++a) s->nv_axis[a] = s->point_set ? 0 : vg->n[a];
+  s->nvc = s->point_set ? vg->npoints : vg->n[0] * vg->n[1] * vg->n[2];
   // only the FP64 Shakhov kinetic kernel uses tiles (factored Maxwellians); FP32 and BF16 keep
   // the x-fastest octant order
-  if (s->prec == GSIS_F64 && s->nvdf == 1) choose_tile(vg, s->kg.tile);
+  if (s->prec == GSIS_F64 && s->nvdf == 1 && !s->point_set) choose_tile(vg, s->kg.tile);
   else s->kg.tile[0] = s->kg.tile[1] = s->kg.tile[2] = 0;
   build_slots(vg, s->kg.tile, s->slot_canon, s->boct, s->vel64);
   s->vaxis.clear();
-  for (int a = 0; a < 3; ++a) s->vaxis.insert(s->vaxis.end(), vg->x[a], vg->x[a] + vg->n[a]);
-  for (int a = 0; a < 3; ++a) s->vaxis.insert(s->vaxis.end(), vg->w[a], vg->w[a] + vg->n[a]);
+  if (!s->point_set) {
+    for (int a = 0; a < 3; ++a) s->vaxis.insert(s->vaxis.end(), vg->x[a], vg->x[a] + vg->n[a]);
+    for (int a = 0; a < 3; ++a) s->vaxis.insert(s->vaxis.end(), vg->w[a], vg->w[a] + vg->n[a]);
+  }
   s->vel64_all = s->vel64;
   s->nslots_all = (int)s->slot_canon.size();
   const int K = s->opt.shard_count > 1 ? s->opt.shard_count : 1;
@@ -1160,7 +1195,7 @@ static size_t footprint(const gsis_solver *s) {
     b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36 + 36 + 6 + 36) * 8) +
          12 * 8 * (size_t)macro_general_parts((int)nc);
   b += (size_t)nc * moment_len(s->nvdf) * 8 * 16;  // moment chunks (bounded)
-  if (Sb == 8 && s->nvdf == 1)                      // FP64 origin moments: the extra chunk, the table
+  if (Sb == 8 && s->nvdf == 1 && !s->point_set)     // FP64 origin moments: the extra chunk, the table
     b += (size_t)nc * moment_len(1) * 8 + (size_t)s->nslots * 16 * 8 + s->vaxis.size() * 8;
   b += nc * NST * (T + 8);                    // states
   b += nc * (13 + 18 + 18 + 12 + 6 + 6 + 1) * 8;
@@ -1182,7 +1217,7 @@ static int allocate_and_upload(gsis_solver *s) {
     s->mom_bpc = std::max(1, std::min(64, (s->nblocks + want - 1) / want));
     s->mom_nchunks = (s->nblocks + s->mom_bpc - 1) / s->mom_bpc;
   }
-  s->origin_mom = std::is_same<T, double>::value && s->nvdf == 1;
+  s->origin_mom = std::is_same<T, double>::value && s->nvdf == 1 && !s->point_set;
   A(s->d_mp, (size_t)(s->mom_nchunks + (s->origin_mom ? 1 : 0)) * nc * moment_len(s->nvdf) * sizeof(double));
   if (s->origin_mom) {
     A(s->d_mtab, (size_t)s->nslots * 16 * sizeof(double));

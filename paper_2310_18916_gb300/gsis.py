@@ -34,7 +34,7 @@ class Mesh(C.Structure):
 
 
 class Vgrid(C.Structure):
-    _fields_ = [("n", C.c_int * 3), ("x", D * 3), ("w", D * 3)]
+    _fields_ = [("n", C.c_int * 3), ("x", D * 3), ("w", D * 3), ("npoints", C.c_int), ("points", D)]
 
 
 class Gas(C.Structure):
@@ -125,6 +125,11 @@ def build_structs(problem, keep):
         vg.n[a] = len(x)
         vg.x[a] = _p(x)
         vg.w[a] = _p(w)
+    if getattr(problem, "vpoints", None) is not None:
+        pts = np.ascontiguousarray(problem.vpoints, dtype=np.float64)
+        keep.append(pts)
+        vg.npoints = len(pts)
+        vg.points = _p(pts)
     g = Gas()
     g.model, g.omega, g.d_r, g.Z_r = problem.model, problem.omega, problem.d_r, problem.Z_r
     for k in range(4):

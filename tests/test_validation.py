@@ -164,3 +164,18 @@ def test_mach_number_must_match_the_free_stream_or_wall_speed():
     assert ry.Ma == pytest.approx(2.0 * np.sqrt((5.0 / 3.0) / (7.0 / 5.0)), rel=1e-14)
     rc, msg = _create_rc(ry, 2.0)
     assert rc == GSIS_E_INVALID and "disagrees" in msg
+
+
+def test_unstructured_velocity_sets_are_validated():
+    p = wl.with_velocity_set(wl.cavity(n=8, nv=4), wl.hybrid_velocity_set((0.2, 0.0, 0.0), n_base=8, refine=2))
+    assert code(p) == gsis.GSIS_OK
+    for bad in (np.nan, -1.0, 0.0):
+        q = wl.with_velocity_set(wl.cavity(n=8, nv=4), p.vpoints.copy())
+        q.vpoints[3, 3] = bad
+        assert code(q) == GSIS_E_INVALID, bad
+    q = wl.with_velocity_set(wl.cavity(n=8, nv=4), p.vpoints.copy())
+    q.vpoints[5, 1] = np.inf
+    assert code(q) == GSIS_E_INVALID
+    # footprints grow with the padded point count, not with the ignored tensor axes
+    big = wl.with_velocity_set(wl.cavity(n=8, nv=4), np.concatenate([p.vpoints, p.vpoints + [0.01, 0, 0, 0]]))
+    assert gsis.footprint_bytes(big) > gsis.footprint_bytes(p)
