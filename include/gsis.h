@@ -71,6 +71,33 @@ typedef struct {
   int bc[6];
   double wall_u[6][3];
   double wall_T[6];
+  /* Unstructured mesh (ncells > 0; the hexahedral, prismatic, pyramidal and tetrahedral cells
+   * of the paper's spatial meshes, Section 5): ni, nj, nk and nodes are then not read.
+   *   unodes:     [nnodes][3] node coordinates (host).
+   *   cells:      [ncells][8] node ids of each cell as a hexahedron with corner t at the
+   *               offsets (t & 1, (t >> 1) & 1, t >> 2) of the block convention above; other
+   *               shapes repeat ids (prism a b c c d e f f, pyramid a b c d e e e e, tetrahedron
+   *               a b c c d d d d), and a side whose corners span no area carries no flux.
+   *   face_patch: [ncells][6] per side (0: corners 0 2 6 4, 1: 1 3 7 5, 2: 0 1 5 4, 3: 2 3 7 6,
+   *               4: 0 1 3 2, 5: 4 5 7 6): -1 where the side is shared with another cell (the
+   *               two cells list the same node ids on it), else the boundary patch 0..5 whose
+   *               bc, wall_u and wall_T above apply.  A PERIODIC patch marks the two faces of a
+   *               mesh one cell layer thick in z (faces normal to z): no transport across them
+   *               and no z gradient, the unstructured form of a one-cell periodic axis; AXIS
+   *               faces carry no flux.
+   * Cells are swept in the colours of a greedy colouring of the face graph (cells in index
+   * order, each taking the smallest colour none of its neighbours holds): n_sweeps passes in
+   * the kinetic step, the synthetic solve's LU-SGS over the same colours.  Least-squares
+   * gradients: over the face neighbours on a mesh of hexahedra, over every node-sharing cell on
+   * a mesh with prisms, pyramids or tetrahedra.  GSIS_MODE_GSIS and Euler presteps need a mesh
+   * of hexahedra (GSIS_E_UNSUPPORTED otherwise); the kinetic iteration runs on every shape.  Faces must be planar
+   * to round-off, cells of positive volume; an unmatched side with patch -1, a patch out of
+   * range or a shared side with a patch gives GSIS_E_INVALID. */
+  int ncells;
+  int nnodes;
+  const double *unodes;
+  const int *cells;
+  const int *face_patch;
 } gsis_mesh;
 
 /* Discrete velocity set (Section 3.1, velocity-space discretisation), host arrays, copied.

@@ -32,6 +32,7 @@
 #endif
 
 #define PI 3.14159265358979323846
+#define STENCIL_MAX 80
 #define SQRT_PI 1.77245385090551602730
 
 struct orc_solver {
@@ -66,11 +67,24 @@ struct orc_solver {
   double eps;
   int macro_iters;
   int *corder;           /* per octant (8) the cells sorted by colour, then by index */
+  /* unstructured meshes: per cell and side the neighbour's side of the shared face and the
+     boundary patch; per cell its colour (NULL on structured blocks: side ^ 1, the side itself,
+     hyperplanes / red-black) */
+  int *nbf, *pat, *colour;
+  int ncolour;
+  /* unstructured meshes: the least-squares stencil of each cell (-1 padded): on a mesh of
+     hexahedra the face neighbours in side order; on a mesh with prisms, pyramids or tetrahedra
+     every other cell sharing a node with it, ascending (face neighbours alone leave the
+     second-order upwind scheme unstable on simplices) */
+  int *sten;
   double mass_ref;       /* total mass of the closed domain (set with f) */
   double mass_scale;     /* rescaling applied after the last kinetic step */
 };
 
 static int cid(const orc_solver *s, int i, int j, int k) { return i + s->ni * (j + s->nj * k); }
+/* the neighbour's side of the face cell i shares through `side`, and the boundary patch of a side */
+static int opp_side(const orc_solver *s, int i, int side) { return s->nbf ? s->nbf[6 * i + side] : side ^ 1; }
+static int patch_of(const orc_solver *s, int i, int side) { return s->pat ? s->pat[6 * i + side] : side; }
 
 /* discrete velocity v and its quadrature weight (Section 3.1): a node of the tensor product of
    the three axis grids, or point v of an unstructured set with its velocity cell's volume */
@@ -261,8 +275,8 @@ static int build_geometry(orc_solver *s, const orc_mesh *m) {
 static void lsq_grad(const orc_solver *s, int i, const double *q, int stride, double g[3]) {
   double A[3][3] = {{0}}, b[3] = {0};
   const double *xi = s->xc + 3 * i;
-  for (int side = 0; side < 6; ++side) {
-    int j = s->nb[6 * i + side];
+  for (int t = 0; t < (s->sten ? STENCIL_MAX : 6); ++t) {
+    int j = s->sten ? s->sten[(size_t)STENCIL_MAX * i + t] : s->nb[6 * i + t];
     if (j < 0) continue;
     double d[3] = {s->xc[3 * j] - xi[0], s->xc[3 * j + 1] - xi[1], s->xc[3 * j + 2] - xi[2]};
     double dq = q[(size_t)j * stride] - q[(size_t)i * stride];
@@ -276,9 +290,30 @@ static void lsq_grad(const orc_solver *s, int i, const double *q, int stride, do
       for (int t = 0; t < 3; ++t) A[a][t] = A[t][a] = 0.0;
       A[a][a] = 1.0; b[a] = 0.0;
     }
-  /* Cramer's rule */
   double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
                A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  if (s->colour) {
+    /* unstructured: a cell whose neighbours leave the fit undetermined (a corner tetrahedron)
+       adds its boundary faces' centres with its own value (rows that change A, not b) */
+    double tr = 0.0;
+    int nact = 0;
+    for (int a = 0; a < 3; ++a)
+      if (s->active[a]) { tr += A[a][a]; ++nact; }
+    if (!(det > 1e-9 * pow(tr, nact))) {
+      for (int side = 0; side < 6; ++side) {
+        int j = s->nb[6 * i + side];
+        const double *S = s->S + 18 * i + 3 * side, *xf = s->xf + 18 * i + 3 * side;
+        if (j >= 0 || j == -2 || !(dot3(S, S) > 0)) continue;
+        double r[3] = {xf[0] - xi[0], xf[1] - xi[1], xf[2] - xi[2]};
+        for (int a = 0; a < 3; ++a)
+          for (int cc = 0; cc < 3; ++cc)
+            if (s->active[a] && s->active[cc]) A[a][cc] += r[a] * r[cc];
+      }
+      det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+            A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    }
+  }
+  /* Cramer's rule */
   for (int col = 0; col < 3; ++col) {
     double M[3][3];
     memcpy(M, A, sizeof M);
@@ -355,7 +390,7 @@ int orc_wall_prepass(orc_solver *s) {
         reconstruct(s, c, s->f0 + (size_t)v * s->nc, 1, ff);
         num += w * sn * ff[side];
       } else if (sn < 0) {
-        den += w * (-sn) * wall_maxwellian(s, side, xi);
+        den += w * (-sn) * wall_maxwellian(s, patch_of(s, c, side), xi);
       }
     }
     s->rho_w[wf] = num / den;
@@ -375,10 +410,11 @@ typedef struct {
    the domain.  c_inf^2 = gamma R T_inf with R T = T/2 and the equilibrium ratio of specific
    heats of the free stream, gamma = (5 + d_r)/(3 + d_r) (5/3 monatomic, 7/5 for d_r = 2). */
 static int far_inflow(const orc_solver *s, int i, int side) {
-  const double *U = s->wall_u[side], *S = s->S + 18 * i + 3 * side;
+  const int p = patch_of(s, i, side);
+  const double *U = s->wall_u[p], *S = s->S + 18 * i + 3 * side;
   double dr = s->nvdf == 2 ? s->g.d_r : 0.0;
   double gam = (5.0 + dr) / (3.0 + dr);
-  return dot3(U, S) <= sqrt(0.5 * gam * s->wall_T[side]) * sqrt(dot3(S, S));
+  return dot3(U, S) <= sqrt(0.5 * gam * s->wall_T[p]) * sqrt(dot3(S, S));
 }
 
 /* Face values (f, and f1 for Rykov) entering the domain through the boundary face (i, side)
@@ -387,13 +423,15 @@ static int far_inflow(const orc_solver *s, int i, int side) {
    sound, where they carry the cell's own values own[] (zero gradient, first order). */
 static void boundary_in(const orc_solver *s, int i, int side, const double *xi, const double own[2], double e[2]) {
   if (s->nb[6 * i + side] == -1) {
-    double M = s->rho_w[s->wid[6 * i + side]] * wall_maxwellian(s, side, xi);
+    const int p = patch_of(s, i, side);
+    double M = s->rho_w[s->wid[6 * i + side]] * wall_maxwellian(s, p, xi);
     e[0] = M;
-    e[1] = s->g.d_r * s->wall_T[side] / 4.0 * M;
+    e[1] = s->g.d_r * s->wall_T[p] / 4.0 * M;
   } else if (far_inflow(s, i, side)) {
-    double M = maxwellian(1.0, s->wall_u[side], s->wall_T[side], xi);
+    const int p = patch_of(s, i, side);
+    double M = maxwellian(1.0, s->wall_u[p], s->wall_T[p], xi);
     e[0] = M;
-    e[1] = s->g.d_r * s->wall_T[side] / 4.0 * M;
+    e[1] = s->g.d_r * s->wall_T[p] / 4.0 * M;
   } else {
     e[0] = own[0];
     e[1] = own[1];
@@ -445,7 +483,7 @@ static void kinetic_velocity(orc_solver *s, int v, kin_work *wk) {
         for (int q = 0; q < s->nvdf; ++q) flux[q] += sn * wk->ff[((size_t)q * nc + i) * 6 + side];
       } else if (sn < 0) {
         if (j >= 0) {
-          int opp = side ^ 1;
+          int opp = opp_side(s, i, side);
           for (int q = 0; q < s->nvdf; ++q) flux[q] += sn * wk->ff[((size_t)q * nc + j) * 6 + opp];
         } else {
           double own[2] = {0.0, 0.0}, e[2];
@@ -492,7 +530,7 @@ static void kinetic_velocity(orc_solver *s, int v, kin_work *wk) {
         } else if (sn < 0) {
           if (j >= 0) {
             for (int q = 0; q < s->nvdf; ++q)
-              e[q] = wk->ff[((size_t)q * nc + j) * 6 + (side ^ 1)] + wk->df[(size_t)q * nc + j];
+              e[q] = wk->ff[((size_t)q * nc + j) * 6 + opp_side(s, i, side)] + wk->df[(size_t)q * nc + j];
           } else {
             double own[2] = {0.0, 0.0};
             for (int q = 0; q < s->nvdf; ++q) own[q] = fq[q][i];
@@ -550,6 +588,218 @@ int orc_kinetic_velocities(orc_solver *s, int v0, int v1) {
   }
   free(fl);
   return bad ? ORC_E_OOM : ORC_OK;
+}
+
+/* ---------------- unstructured meshes (Section 5's cell shapes) ---------------- */
+
+/* the six sides of a hexahedron of corners t = (t & 1, (t >> 1) & 1, t >> 2), in cyclic order */
+static const int HEX_SIDE[6][4] = {{0, 2, 6, 4}, {1, 3, 7, 5}, {0, 1, 5, 4}, {2, 3, 7, 6}, {0, 1, 3, 2}, {4, 5, 7, 6}};
+
+typedef struct { int id[4]; int face; } face_key;
+
+static int key_cmp(const void *a, const void *b) {
+  const face_key *x = (const face_key *)a, *y = (const face_key *)b;
+  for (int t = 0; t < 4; ++t)
+    if (x->id[t] != y->id[t]) return x->id[t] < y->id[t] ? -1 : 1;
+  return x->face < y->face ? -1 : (x->face > y->face);
+}
+
+static void unode(const orc_mesh *m, int id, double p[3]) {
+  for (int d = 0; d < 3; ++d) p[d] = m->unodes[3 * (size_t)id + d];
+}
+
+/* Cells given as hexahedra of node ids (other shapes repeat ids).  Geometry per side: four
+   distinct corners, the quadrilateral of the structured blocks (half the cross product of the
+   diagonals, centre the corner mean); three, a triangle (half the cross product of two edges,
+   centre their mean); fewer, no area and no flux.  Cell centre: mean of the distinct corners.
+   Shared sides: the same set of node ids on two cells.  Other sides take their patch's
+   condition; a PERIODIC patch (faces normal to z) makes a one-layer mesh: no transport across
+   it and no z gradient.  Colours: greedy, cells in index order, each the smallest colour none of
+   its face neighbours already has. */
+static int build_geometry_unstructured(orc_solver *s, const orc_mesh *m) {
+  int nc = s->nc;
+  s->open = 0;
+  s->nwall = 0;
+  s->active[0] = s->active[1] = s->active[2] = 1;
+  s->nbf = (int *)malloc(sizeof(int) * 6 * nc);
+  s->pat = (int *)malloc(sizeof(int) * 6 * nc);
+  s->colour = (int *)malloc(sizeof(int) * nc);
+  face_key *keys = (face_key *)malloc(sizeof(face_key) * 6 * (size_t)nc);
+  double *area = (double *)malloc(sizeof(double) * 6 * (size_t)nc);
+  if (!s->nbf || !s->pat || !s->colour || !keys || !area) { free(keys); free(area); return ORC_E_OOM; }
+  int nk = 0;
+  for (int c = 0; c < nc; ++c) {
+    const int *ids = m->cells + 8 * (size_t)c;
+    int dist[8], nd = 0;
+    for (int t = 0; t < 8; ++t) {
+      int seen = 0;
+      for (int u = 0; u < nd; ++u) seen |= dist[u] == ids[t];
+      if (!seen) dist[nd++] = ids[t];
+    }
+    double *xc = s->xc + 3 * c, p[3];
+    xc[0] = xc[1] = xc[2] = 0.0;
+    for (int u = 0; u < nd; ++u) {
+      unode(m, dist[u], p);
+      for (int d = 0; d < 3; ++d) xc[d] += p[d] / nd;
+    }
+    double V = 0.0;
+    for (int side = 0; side < 6; ++side) {
+      int q[4], fd[4], nf = 0;
+      for (int t = 0; t < 4; ++t) q[t] = ids[HEX_SIDE[side][t]];
+      for (int t = 0; t < 4; ++t) {
+        int seen = 0;
+        for (int u = 0; u < nf; ++u) seen |= fd[u] == q[t];
+        if (!seen) fd[nf++] = q[t];
+      }
+      double *S = s->S + 18 * c + 3 * side, *xf = s->xf + 18 * c + 3 * side;
+      S[0] = S[1] = S[2] = xf[0] = xf[1] = xf[2] = 0.0;
+      if (nf == 4) {
+        double pq[4][3];
+        for (int t = 0; t < 4; ++t) unode(m, q[t], pq[t]);
+        quad((const double(*)[3])pq, S, xf);
+      } else if (nf == 3) {
+        double a[3], b[3], c3[3], e1[3], e2[3];
+        unode(m, fd[0], a); unode(m, fd[1], b); unode(m, fd[2], c3);
+        for (int d = 0; d < 3; ++d) { e1[d] = b[d] - a[d]; e2[d] = c3[d] - a[d]; xf[d] = (a[d] + b[d] + c3[d]) / 3.0; }
+        S[0] = 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+        S[1] = 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+        S[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+      } else {
+        for (int t = 0; t < 4; ++t) { unode(m, q[t], p); for (int d = 0; d < 3; ++d) xf[d] += p[d] / 4.0; }
+      }
+      double r[3] = {xf[0] - xc[0], xf[1] - xc[1], xf[2] - xc[2]};
+      if (dot3(S, r) < 0) { S[0] = -S[0]; S[1] = -S[1]; S[2] = -S[2]; }
+      V += dot3(xf, S) / 3.0;
+      area[6 * c + side] = nf >= 3 ? sqrt(dot3(S, S)) : 0.0;
+      s->nb[6 * c + side] = -2;
+      s->nbf[6 * c + side] = -1;
+      s->pat[6 * c + side] = -1;
+      s->wid[6 * c + side] = -1;
+      if (area[6 * c + side] > 0) {
+        /* sorted distinct ids, padded with -1 */
+        for (int t = 0; t < 4; ++t) keys[nk].id[t] = t < nf ? fd[t] : -1;
+        for (int t = 1; t < nf; ++t)
+          for (int u = t; u > 0 && keys[nk].id[u - 1] > keys[nk].id[u]; --u) {
+            int x = keys[nk].id[u]; keys[nk].id[u] = keys[nk].id[u - 1]; keys[nk].id[u - 1] = x;
+          }
+        keys[nk].face = 6 * c + side;
+        ++nk;
+      }
+    }
+    if (!(V > 0)) { free(keys); free(area); return ORC_E_INVALID; }
+    s->vol[c] = V;
+    s->eps2[c] = pow(s->o.venkat_K * cbrt(V), 3.0);
+  }
+  qsort(keys, nk, sizeof(face_key), key_cmp);
+  for (int t = 0; t + 1 < nk; ++t)
+    if (memcmp(keys[t].id, keys[t + 1].id, sizeof keys[t].id) == 0) {
+      int f = keys[t].face, g = keys[t + 1].face;
+      if (m->face_patch[f] >= 0 || m->face_patch[g] >= 0) { free(keys); free(area); return ORC_E_INVALID; }
+      s->nb[f] = g / 6; s->nbf[f] = g % 6;
+      s->nb[g] = f / 6; s->nbf[g] = f % 6;
+      ++t;
+    }
+  free(keys);
+  int one_layer = 0;
+  for (int c = 0; c < nc; ++c)
+    for (int side = 0; side < 6; ++side) {
+      int f = 6 * c + side;
+      if (!(area[f] > 0) || s->nb[f] >= 0) continue;
+      int p = m->face_patch[f];
+      if (p < 0 || p > 5) { free(area); return ORC_E_INVALID; }
+      s->pat[f] = p;
+      int b = m->bc[p];
+      if (b == ORC_BC_WALL) { s->nb[f] = -1; s->wid[f] = s->nwall++; }
+      else if (b == ORC_BC_FARFIELD) { s->nb[f] = -4; s->open = 1; }
+      else if (b == ORC_BC_AXIS) s->nb[f] = -3;
+      else if (b == ORC_BC_PERIODIC) {
+        const double *S = s->S + 18 * c + 3 * side;
+        if (fabs(S[2]) < (1.0 - 1e-9) * area[f]) { free(area); return ORC_E_INVALID; }
+        s->nb[f] = -2;
+        one_layer = 1;
+      } else { free(area); return ORC_E_INVALID; }
+    }
+  free(area);
+  s->active[2] = !one_layer;
+  /* node-sharing neighbours: cells listed per node, then merged per cell */
+  {
+    int nn = m->nnodes;
+    int *cnt = (int *)calloc(nn + 1, sizeof(int));
+    s->sten = (int *)malloc(sizeof(int) * STENCIL_MAX * (size_t)nc);
+    if (!cnt || !s->sten) { free(cnt); return ORC_E_OOM; }
+    for (int c = 0; c < nc; ++c)
+      for (int t = 0; t < 8; ++t) {
+        int dup = 0;
+        for (int u = 0; u < t; ++u) dup |= m->cells[8 * (size_t)c + u] == m->cells[8 * (size_t)c + t];
+        if (!dup) cnt[m->cells[8 * (size_t)c + t] + 1]++;
+      }
+    for (int v = 0; v < nn; ++v) cnt[v + 1] += cnt[v];
+    int *lst = (int *)malloc(sizeof(int) * (cnt[nn] + 1)), *pos = (int *)malloc(sizeof(int) * (nn + 1));
+    if (!lst || !pos) { free(cnt); free(lst); free(pos); return ORC_E_OOM; }
+    memcpy(pos, cnt, sizeof(int) * (nn + 1));
+    for (int c = 0; c < nc; ++c)
+      for (int t = 0; t < 8; ++t) {
+        int dup = 0;
+        for (int u = 0; u < t; ++u) dup |= m->cells[8 * (size_t)c + u] == m->cells[8 * (size_t)c + t];
+        if (!dup) lst[pos[m->cells[8 * (size_t)c + t]]++] = c;
+      }
+    int all_hex = 1;
+    for (int c = 0; c < nc; ++c) {
+      int ndist = 0;
+      for (int t = 0; t < 8; ++t) {
+        int dup = 0;
+        for (int u = 0; u < t; ++u) dup |= m->cells[8 * (size_t)c + u] == m->cells[8 * (size_t)c + t];
+        ndist += !dup;
+      }
+      if (ndist < 8) all_hex = 0;
+    }
+    for (int c = 0; c < nc; ++c) {
+      int *st = s->sten + (size_t)STENCIL_MAX * c, k = 0;
+      for (int t = 0; t < STENCIL_MAX; ++t) st[t] = -1;
+      if (all_hex) {
+        for (int side = 0; side < 6; ++side)
+          if (s->nb[6 * c + side] >= 0) st[k++] = s->nb[6 * c + side];
+        continue;
+      }
+      for (int t = 0; t < 8; ++t) {
+        int v = m->cells[8 * (size_t)c + t];
+        for (int e = cnt[v]; e < cnt[v + 1]; ++e) {
+          int o = lst[e], seen = o == c;
+          for (int u = 0; u < k && !seen; ++u) seen = st[u] == o;
+          if (!seen) {
+            if (k == STENCIL_MAX) { free(cnt); free(lst); free(pos); return ORC_E_INVALID; }
+            st[k++] = o;
+          }
+        }
+      }
+      /* ascending order, so the sums do not depend on the node order */
+      for (int a = 1; a < k; ++a)
+        for (int b = a; b > 0 && st[b - 1] > st[b]; --b) { int x = st[b]; st[b] = st[b - 1]; st[b - 1] = x; }
+    }
+    free(cnt); free(lst); free(pos);
+  }
+  s->ncolour = 0;
+  for (int c = 0; c < nc; ++c) {
+    int k = 0, clash = 1;
+    while (clash) {
+      clash = 0;
+      for (int side = 0; side < 6; ++side) {
+        int j = s->nb[6 * c + side];
+        if (j >= 0 && j < c && s->colour[j] == k) clash = 1;
+      }
+      if (clash) ++k;
+    }
+    s->colour[c] = k;
+    if (k + 1 > s->ncolour) s->ncolour = k + 1;
+  }
+  s->wcell = (int *)malloc(sizeof(int) * (s->nwall + 1));
+  s->wside = (int *)malloc(sizeof(int) * (s->nwall + 1));
+  s->rho_w = (double *)calloc(s->nwall + 1, sizeof(double));
+  if (!s->wcell || !s->wside || !s->rho_w) return ORC_E_OOM;
+  for (int c = 0; c < nc; ++c)
+    for (int side = 0; side < 6; ++side)
+      if (s->wid[6 * c + side] >= 0) { s->wcell[s->wid[6 * c + side]] = c; s->wside[s->wid[6 * c + side]] = side; }
+  return ORC_OK;
 }
 
 /* ---------------- moments (Eq. getmoment) ---------------- */
@@ -715,7 +965,7 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
     const double *S = s->S + 18 * i + 3 * side;
     double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A}, pr[6];
     prim_of(s, W + 6 * i, pr);
-    wall_eq_flux(s, side, pr, n, feq0 + 6 * wf);
+    wall_eq_flux(s, patch_of(s, i, side), pr, n, feq0 + 6 * wf);
   }
   for (int step = 0; step < max_steps; ++step) {
     for (int i = 0; i < nc; ++i) {
@@ -746,7 +996,7 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
           } else {
             /* frozen kinetic wall flux plus the increment of the equilibrium wall flux */
             double feq[6];
-            wall_eq_flux(s, side, m.pr + 6 * i, n, feq);
+            wall_eq_flux(s, patch_of(s, i, side), m.pr + 6 * i, n, feq);
             for (int k = 0; k < nW; ++k) m.R[6 * i + k] -= fkin[36 * i + 6 * side + k] + (feq[k] - feq0[6 * wf + k]) * A;
           }
           continue;
@@ -763,8 +1013,8 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
           for (int k = 0; k < nW; ++k) WL[k] = W[6 * i + k] + m.phW[6 * i + k] * dot3(m.gW + 18 * i + 3 * k, ri);
           prim_of(s, WL, pL);
           if (!(pL[0] > 0) || !(pL[4] > 0) || !(pL[5] > 0)) { memcpy(WL, W + 6 * i, sizeof WL); prim_of(s, WL, pL); }
-          double pinf[6] = {1.0, s->wall_u[side][0], s->wall_u[side][1], s->wall_u[side][2], s->wall_T[side],
-                            s->wall_T[side]};
+          const int pp = patch_of(s, i, side);
+          double pinf[6] = {1.0, s->wall_u[pp][0], s->wall_u[pp][1], s->wall_u[pp][2], s->wall_T[pp], s->wall_T[pp]};
           cons_of(s, pinf, WR);
           prim_of(s, WR, pR);
           euler_flux(s, WL, n, FL);
@@ -871,10 +1121,10 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
     /* matrix-free LU-SGS, colour ordered: red-black cells, macro_sweeps passes (Eq. res_macro) */
     for (int i = 0; i < 6 * nc; ++i) m.dW[i] = 0.0;
     for (int sw = 0; sw < s->o.macro_sweeps; ++sw)
-      for (int col = 0; col < 2; ++col)
+      for (int col = 0; col < (s->colour ? s->ncolour : 2); ++col)
         for (int i = 0; i < nc; ++i) {
           int ii = i % s->ni, jj = (i / s->ni) % s->nj, kk = i / (s->ni * s->nj);
-          if (((ii + jj + kk) & 1) != col) continue;
+          if ((s->colour ? s->colour[i] : (ii + jj + kk) & 1) != col) continue;
           double acc[6];
           for (int k = 0; k < nW; ++k) acc[k] = m.R[6 * i + k];
           double V = s->vol[i];
@@ -1116,6 +1366,7 @@ void orc_destroy(orc_solver *s) {
   free(s->vol); free(s->xc); free(s->S); free(s->xf); free(s->eps2); free(s->nb); free(s->wid);
   free(s->wcell); free(s->wside); free(s->rho_w);
   free(s->f0); free(s->f1); free(s->st); free(s->Mh); free(s->hot); free(s->kin); free(s->fkin); free(s->corder);
+  free(s->nbf); free(s->pat); free(s->colour); free(s->sten);
   free(s);
 }
 
@@ -1146,12 +1397,14 @@ static int init_state_from_f(orc_solver *s) {
 int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const orc_opts *o, const double *W0,
                orc_solver **out) {
   *out = NULL;
-  if (m->ni < 1 || m->nj < 1 || m->nk < 1) return ORC_E_INVALID;
+  if (m->ncells <= 0 && (m->ni < 1 || m->nj < 1 || m->nk < 1)) return ORC_E_INVALID;
+  if (m->ncells > 0 && (!m->unodes || !m->cells || !m->face_patch)) return ORC_E_INVALID;
   if (vg->npoints > 0 ? !vg->points : (vg->n[0] < 1 || vg->n[1] < 1 || vg->n[2] < 1)) return ORC_E_INVALID;
   if (g->model == ORC_RYKOV && !(g->d_r > 0)) return ORC_E_INVALID;
   orc_solver *s = (orc_solver *)calloc(1, sizeof(orc_solver));
   if (!s) return ORC_E_OOM;
-  s->ni = m->ni; s->nj = m->nj; s->nk = m->nk; s->nc = m->ni * m->nj * m->nk;
+  if (m->ncells > 0) { s->ni = m->ncells; s->nj = s->nk = 1; s->nc = m->ncells; }
+  else { s->ni = m->ni; s->nj = m->nj; s->nk = m->nk; s->nc = m->ni * m->nj * m->nk; }
   if (vg->npoints > 0) {
     /* one-node placeholders for the unused axis arrays */
     static const double one = 1.0;
@@ -1194,11 +1447,19 @@ int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const o
     orc_destroy(s);
     return ORC_E_OOM;
   }
-  int rc = build_geometry(s, m);
+  int rc = m->ncells > 0 ? build_geometry_unstructured(s, m) : build_geometry(s, m);
   if (rc) { orc_destroy(s); return rc; }
   s->corder = (int *)malloc(sizeof(int) * 8 * (size_t)nc);
   if (!s->corder) { orc_destroy(s); return ORC_E_OOM; }
-  {
+  if (s->colour) {
+    /* every octant sweeps the cells colour by colour, in index order within a colour */
+    for (int oct = 0; oct < 8; ++oct) {
+      int t = 0;
+      for (int col = 0; col < s->ncolour; ++col)
+        for (int i = 0; i < nc; ++i)
+          if (s->colour[i] == col) s->corder[(size_t)oct * nc + t++] = i;
+    }
+  } else {
     int ncol = s->ni + s->nj + s->nk - 2;
     for (int oct = 0; oct < 8; ++oct) {
       int sgn[3] = {oct & 1 ? -1 : 1, oct & 2 ? -1 : 1, oct & 4 ? -1 : 1}, t = 0;

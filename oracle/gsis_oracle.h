@@ -33,6 +33,14 @@ typedef struct {
   int bc[6];            /* sides x-, x+, y-, y+, z-, z+ (index space: i-, i+, j-, j+, k-, k+) */
   double wall_u[6][3];
   double wall_T[6];
+  /* unstructured mesh (ncells > 0; ni, nj, nk, nodes unused): cells as hexahedra of node ids,
+     corner t at offsets (t & 1, (t >> 1) & 1, t >> 2), other shapes repeating ids; per side
+     (corners 0 2 6 4 | 1 3 7 5 | 0 1 5 4 | 2 3 7 6 | 0 1 3 2 | 4 5 7 6) -1 when shared with
+     another cell, else the boundary patch 0..5 indexing bc, wall_u, wall_T */
+  int ncells, nnodes;
+  const double *unodes; /* [nnodes][3] */
+  const int *cells;     /* [ncells][8] */
+  const int *face_patch;/* [ncells][6] */
 } orc_mesh;
 
 typedef struct {

@@ -17,7 +17,8 @@ D = C.POINTER(C.c_double)
 
 class OrcMesh(C.Structure):
     _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nk", C.c_int), ("nodes", D), ("bc", C.c_int * 6),
-                ("wall_u", (C.c_double * 3) * 6), ("wall_T", C.c_double * 6)]
+                ("wall_u", (C.c_double * 3) * 6), ("wall_T", C.c_double * 6), ("ncells", C.c_int), ("nnodes", C.c_int),
+                ("unodes", D), ("cells", C.POINTER(C.c_int)), ("face_patch", C.POINTER(C.c_int))]
 
 
 class OrcVgrid(C.Structure):
@@ -108,6 +109,15 @@ class Oracle:
         m = OrcMesh()
         m.ni, m.nj, m.nk = p.ni, p.nj, p.nk
         m.nodes = _p(nodes)
+        if getattr(p, "ucells", None) is not None:
+            un = np.ascontiguousarray(p.unodes, dtype=np.float64)
+            uc = np.ascontiguousarray(p.ucells, dtype=np.int32)
+            up = np.ascontiguousarray(p.upatch, dtype=np.int32)
+            self._keep += [un, uc, up]
+            m.ncells, m.nnodes = len(uc), len(un)
+            m.unodes = _p(un)
+            m.cells = uc.ctypes.data_as(C.POINTER(C.c_int))
+            m.face_patch = up.ctypes.data_as(C.POINTER(C.c_int))
         for s in range(6):
             m.bc[s] = p.bc[s]
             m.wall_T[s] = p.wall_T[s]

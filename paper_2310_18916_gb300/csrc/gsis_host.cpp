@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -79,6 +81,20 @@ struct gsis_solver {
   // general (curvilinear) meshes: per-cell geometry, neighbour codes, wall-face ids, far-field
   // inflow sides, wall-face areas; the kinetic kernel's persistent grid
   bool general = false;
+  // unstructured meshes: the neighbour's side of each shared face and the boundary patch of each
+  // boundary face (both absent on structured blocks, whose opposite side is s ^ 1 and whose
+  // patches are the block sides); the synthetic solve's colour offsets into colcells
+  bool unstructured = false;
+  std::vector<unsigned char> gnf, gpat;
+  unsigned char *d_gnf = nullptr, *d_gpat = nullptr;
+  std::vector<int> wall_patch;
+  int *d_wall_patch = nullptr;
+  std::vector<int> gs_off, gs_idx;      // least-squares stencil (CSR) of an unstructured mesh
+  std::vector<double> gs_w;             // [entry][3]
+  int *d_gso = nullptr, *d_gsi = nullptr;
+  void *d_gsw = nullptr;                // in the kinetic precision
+  double *d_gsw64 = nullptr;
+  std::vector<int> mcol_off;
   std::vector<GenCell<double>> gen64;
   std::vector<int> gnb, gwid;
   std::vector<unsigned char> gin;
@@ -230,6 +246,11 @@ struct gsis_solver {
     a.gin = d_gin;
     a.n_sweeps = opt.n_sweeps;
     a.wden = d_wden;
+    a.gnf = d_gnf;
+    a.gpat = d_gpat;
+    a.gso = d_gso;
+    a.gsi = d_gsi;
+    a.gsw = static_cast<const T *>(d_gsw);
     return a;
   }
 
@@ -244,6 +265,13 @@ struct gsis_solver {
     m.sweeps = opt.macro_sweeps;
     m.closed = closed;
     m.ncol0 = ncol0;
+    m.ncolm = (int)mcol_off.size() - 1;
+    for (int c = 0; c <= m.ncolm && c <= MACRO_MAX_COLOURS; ++c) m.colm_off[c] = mcol_off[c];
+    m.gnf = d_gnf;
+    m.gpat = d_gpat;
+    m.gso = d_gso;
+    m.gsi = d_gsi;
+    m.gsw = d_gsw64;
     m.euler = 0;
     m.mh_stride = 18;
     m.mu0 = Kn / std::sqrt(3.14159265358979323846);
@@ -583,6 +611,7 @@ bool rectilinear_nodes(const gsis_mesh *m) {
 }
 
 bool needs_general(const gsis_mesh *m) {
+  if (m->ncells > 0) return true;
   const int n[3] = {m->ni, m->nj, m->nk};
   for (int side = 0; side < 6; ++side) {
     const int b = m->bc[side];
@@ -593,12 +622,35 @@ bool needs_general(const gsis_mesh *m) {
 
 int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double Kn, const gsis_options *o,
              std::string &why) {
-  if (!m || !vg || !g || !o || !m->nodes) { why = "NULL argument"; return GSIS_E_INVALID; }
-  if (m->ni < 1 || m->nj < 1 || m->nk < 1 || m->ni > 1023 || m->nj > 1023 || m->nk > 1023) {
-    why = "cell counts must be in [1, 1023]";
-    return GSIS_E_INVALID;
+  if (!m || !vg || !g || !o) { why = "NULL argument"; return GSIS_E_INVALID; }
+  if (m->ncells < 0) { why = "ncells must be >= 0"; return GSIS_E_INVALID; }
+  if (m->ncells > 0) {
+    if (!m->unodes || !m->cells || !m->face_patch || m->nnodes < 4) {
+      why = "an unstructured mesh needs unodes, cells, face_patch and at least 4 nodes";
+      return GSIS_E_INVALID;
+    }
+    if ((double)m->ncells * NST >= 4294967296.0) { why = "too many cells"; return GSIS_E_UNSUPPORTED; }
+    for (size_t t = 0; t < (size_t)8 * m->ncells; ++t)
+      if (m->cells[t] < 0 || m->cells[t] >= m->nnodes) { why = "cell node id out of range"; return GSIS_E_INVALID; }
+    for (size_t t = 0; t < (size_t)6 * m->ncells; ++t) {
+      const int p = m->face_patch[t];
+      if (p < -1 || p > 5) { why = "face patch out of range"; return GSIS_E_INVALID; }
+      if (p >= 0 && (m->bc[p] < GSIS_BC_WALL || m->bc[p] > GSIS_BC_AXIS)) { why = "bad boundary condition"; return GSIS_E_INVALID; }
+      if (p >= 0 && (m->bc[p] == GSIS_BC_WALL || m->bc[p] == GSIS_BC_FARFIELD) && !(m->wall_T[p] > 0)) {
+        why = "wall and free-stream temperatures must be positive";
+        return GSIS_E_INVALID;
+      }
+    }
+    for (size_t t = 0; t < (size_t)3 * m->nnodes; ++t)
+      if (!std::isfinite(m->unodes[t])) { why = "node coordinates must be finite"; return GSIS_E_INVALID; }
+  } else {
+    if (!m->nodes) { why = "NULL argument"; return GSIS_E_INVALID; }
+    if (m->ni < 1 || m->nj < 1 || m->nk < 1 || m->ni > 1023 || m->nj > 1023 || m->nk > 1023) {
+      why = "cell counts must be in [1, 1023]";
+      return GSIS_E_INVALID;
+    }
   }
-  if ((double)m->ni * m->nj * m->nk * NST >= 4294967296.0) {  // 32-bit state offsets in the kernels
+  if (m->ncells == 0 && (double)m->ni * m->nj * m->nk * NST >= 4294967296.0) {  // 32-bit state offsets in the kernels
     why = "too many cells";
     return GSIS_E_UNSUPPORTED;
   }
@@ -645,6 +697,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     return GSIS_E_UNSUPPORTED;
   }
   if (general && (o->n_sweeps < 1 || o->n_sweeps > 64)) { why = "n_sweeps must be in [1, 64]"; return GSIS_E_INVALID; }
+  if (m->ncells > 0) return GSIS_OK;  // faces, volumes and colours are checked when the mesh is built
   const int n[3] = {m->ni, m->nj, m->nk};
   bool seen_inactive = false;
   for (int a = 0; a < 3; ++a) {
@@ -953,7 +1006,316 @@ static int build_general(gsis_solver *s, const gsis_mesh *m) {
   return GSIS_OK;
 }
 
+// Unstructured meshes: every cell a hexahedron of node ids (other shapes repeat ids), its six
+// sides with corners in cyclic order; a side's geometry as on structured blocks (a quadrilateral:
+// half the cross product of its diagonals, centre the corner mean), a side with three distinct
+// corners a triangle (half the cross product of two edges, centre their mean), fewer: no area.
+static const int kHexSide[6][4] = {{0, 2, 6, 4}, {1, 3, 7, 5}, {0, 1, 5, 4}, {2, 3, 7, 6}, {0, 1, 3, 2}, {4, 5, 7, 6}};
+
+static int setup_unstructured_mesh(gsis_solver *s, const gsis_mesh *m) {
+  const int nc = m->ncells;
+  s->unstructured = true;
+  s->general = true;
+  s->nc = nc;
+  s->n[0] = nc;
+  s->n[1] = s->n[2] = 1;
+  for (int a = 0; a < 3; ++a) {
+    // placeholders: the axis arrays serve rectilinear blocks only
+    s->X[a] = {0.0, 1.0};
+    AxisCell<double> c{};
+    c.h = 1.0;
+    c.invh = 1.0;
+    s->axc[a].assign(1, c);
+  }
+  KinGeom &g = s->kg;
+  g = KinGeom{};
+  g.nc = nc;
+  g.n[0] = nc;
+  g.n[1] = g.n[2] = 1;
+  for (int a = 0; a < 3; ++a) g.act[a] = 1;
+  g.nact = 3;
+  g.K3 = s->opt.venkat_K * s->opt.venkat_K * s->opt.venkat_K;
+  for (int side = 0; side < 6; ++side) g.wall_base[side] = -1;
+  for (int p = 0; p < 6; ++p) {
+    for (int d = 0; d < 3; ++d) s->wall_uT[p][d] = m->wall_u[p][d];
+    s->wall_uT[p][3] = m->wall_T[p];
+  }
+  s->nwall = 0;
+  s->wall_cell.clear();
+  s->wall_side.clear();
+  s->wall_area.clear();
+  s->wall_patch.clear();
+  s->wall_sides_list.clear();
+  s->closed = 1;
+  s->gen64.assign(nc, GenCell<double>{});
+  s->gnb.assign((size_t)6 * nc, NB_ABSENT);
+  s->gwid.assign((size_t)6 * nc, -1);
+  s->gin.assign((size_t)6 * nc, 0);
+  s->gnf.assign((size_t)6 * nc, 255);
+  s->gpat.assign((size_t)6 * nc, 255);
+  s->vol.assign(nc, 0.0);
+  s->xc64.assign((size_t)3 * nc, 0.0);
+  s->vsum = 0.0;
+  const double K3 = g.K3;
+  auto X = [&](int id, int d) { return m->unodes[3 * (size_t)id + d]; };
+  std::vector<double> area((size_t)6 * nc, 0.0);
+  std::vector<std::array<int, 4>> key((size_t)6 * nc);
+  for (int c = 0; c < nc; ++c) {
+    const int *ids = m->cells + 8 * (size_t)c;
+    std::vector<int> dist;
+    for (int t = 0; t < 8; ++t)
+      if (std::find(dist.begin(), dist.end(), ids[t]) == dist.end()) dist.push_back(ids[t]);
+    double cen[3] = {0, 0, 0};
+    for (int id : dist)
+      for (int d = 0; d < 3; ++d) cen[d] += X(id, d) / dist.size();
+    for (int d = 0; d < 3; ++d) s->xc64[3 * (size_t)c + d] = cen[d];
+    GenCell<double> &gc = s->gen64[c];
+    double V = 0.0;
+    for (int side = 0; side < 6; ++side) {
+      int q[4];
+      for (int t = 0; t < 4; ++t) q[t] = ids[kHexSide[side][t]];
+      std::vector<int> fd;
+      for (int t = 0; t < 4; ++t)
+        if (std::find(fd.begin(), fd.end(), q[t]) == fd.end()) fd.push_back(q[t]);
+      double S[3] = {0, 0, 0}, xf[3] = {0, 0, 0};
+      if (fd.size() == 4) {
+        double d1[3], d2[3];
+        for (int d = 0; d < 3; ++d) {
+          d1[d] = X(q[2], d) - X(q[0], d);
+          d2[d] = X(q[3], d) - X(q[1], d);
+          xf[d] = 0.25 * (X(q[0], d) + X(q[1], d) + X(q[2], d) + X(q[3], d));
+        }
+        S[0] = 0.5 * (d1[1] * d2[2] - d1[2] * d2[1]);
+        S[1] = 0.5 * (d1[2] * d2[0] - d1[0] * d2[2]);
+        S[2] = 0.5 * (d1[0] * d2[1] - d1[1] * d2[0]);
+      } else if (fd.size() == 3) {
+        double e1[3], e2[3];
+        for (int d = 0; d < 3; ++d) {
+          e1[d] = X(fd[1], d) - X(fd[0], d);
+          e2[d] = X(fd[2], d) - X(fd[0], d);
+          xf[d] = (X(fd[0], d) + X(fd[1], d) + X(fd[2], d)) / 3.0;
+        }
+        S[0] = 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+        S[1] = 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+        S[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+      } else {
+        for (int t = 0; t < 4; ++t)
+          for (int d = 0; d < 3; ++d) xf[d] += 0.25 * X(q[t], d);
+      }
+      double r[3] = {xf[0] - cen[0], xf[1] - cen[1], xf[2] - cen[2]};
+      if (S[0] * r[0] + S[1] * r[1] + S[2] * r[2] < 0)
+        for (int d = 0; d < 3; ++d) S[d] = -S[d];
+      V += (xf[0] * S[0] + xf[1] * S[1] + xf[2] * S[2]) / 3.0;
+      const double A = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+      for (int d = 0; d < 3; ++d) {
+        gc.f[side].S[d] = S[d];
+        gc.f[side].r[d] = r[d];
+      }
+      gc.f[side].invA = A > 0 ? 1.0 / A : 0.0;
+      area[6 * (size_t)c + side] = fd.size() >= 3 ? A : 0.0;
+      std::sort(fd.begin(), fd.end());
+      std::array<int, 4> k{-1, -1, -1, -1};
+      for (size_t t = 0; t < fd.size(); ++t) k[t] = fd[t];
+      key[6 * (size_t)c + side] = k;
+    }
+    if (!(V > 0)) return s->fail(GSIS_E_INVALID, "cell %d has volume %g", c, V);
+    s->vol[c] = V;
+    s->vsum += V;
+    gc.invV = 1.0 / V;
+    gc.eps2 = K3 * V;
+  }
+  // shared sides: the same node set on two cells
+  std::map<std::array<int, 4>, int> open;
+  for (int c = 0; c < nc; ++c)
+    for (int side = 0; side < 6; ++side) {
+      const size_t f = 6 * (size_t)c + side;
+      if (!(area[f] > 0)) continue;
+      auto it = open.find(key[f]);
+      if (it == open.end()) {
+        open.emplace(key[f], (int)f);
+        continue;
+      }
+      const int o = it->second, oc = o / 6, os = o % 6;
+      open.erase(it);
+      if (m->face_patch[f] >= 0 || m->face_patch[o] >= 0)
+        return s->fail(GSIS_E_INVALID, "cell %d side %d is shared with cell %d but has a boundary patch", c, side, oc);
+      s->gnb[f] = oc;
+      s->gnf[f] = (unsigned char)os;
+      s->gnb[o] = c;
+      s->gnf[o] = (unsigned char)side;
+    }
+  // boundary sides, walls numbered cell by cell, side by side
+  bool one_layer = false;
+  const double dr = s->gas.model == GSIS_RYKOV ? s->gas.d_r : 0.0;
+  const double gam = (5.0 + dr) / (3.0 + dr);
+  for (int c = 0; c < nc; ++c)
+    for (int side = 0; side < 6; ++side) {
+      const size_t f = 6 * (size_t)c + side;
+      if (!(area[f] > 0) || s->gnb[f] >= 0) continue;
+      const int p = m->face_patch[f];
+      if (p < 0) return s->fail(GSIS_E_INVALID, "cell %d side %d is neither shared nor on a boundary patch", c, side);
+      s->gpat[f] = (unsigned char)p;
+      const double *S = s->gen64[c].f[side].S;
+      const double A = area[f];
+      switch (m->bc[p]) {
+        case GSIS_BC_WALL:
+          s->gnb[f] = NB_WALL;
+          s->gwid[f] = s->nwall++;
+          s->wall_cell.push_back(c);
+          s->wall_side.push_back(side);
+          s->wall_area.push_back(A);
+          s->wall_patch.push_back(p);
+          break;
+        case GSIS_BC_FARFIELD: {
+          s->gnb[f] = NB_FAR;
+          s->closed = 0;
+          const double *U = m->wall_u[p];
+          s->gin[f] = U[0] * S[0] + U[1] * S[1] + U[2] * S[2] <= std::sqrt(0.5 * gam * m->wall_T[p]) * A;
+          break;
+        }
+        case GSIS_BC_PERIODIC:
+          if (std::fabs(S[2]) < (1.0 - 1e-9) * A)
+            return s->fail(GSIS_E_UNSUPPORTED, "PERIODIC patches of an unstructured mesh must be normal to z (cell %d)", c);
+          s->gnb[f] = NB_ABSENT;
+          one_layer = true;
+          break;
+        default:
+          s->gnb[f] = NB_AXIS;
+      }
+    }
+  // Least-squares stencils (no z component on a one-layer mesh): on a mesh of hexahedra a cell
+  // fits its face neighbours; on a mesh with prisms, pyramids or tetrahedra every other cell
+  // sharing a node with it (the second-order upwind scheme with face neighbours only is unstable
+  // on simplices).  A cell
+  // whose stencil does not determine a gradient (a corner tetrahedron) also fits the centres of
+  // its boundary faces, each carrying the cell's own value: rows of the normal matrix that add
+  // nothing to the gradient sum.
+  const bool active[3] = {true, true, !one_layer};
+  const int nact = one_layer ? 2 : 3;
+  auto det3 = [](const double A[3][3]) {
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  };
+  std::vector<std::vector<int>> node_cells(m->nnodes);
+  std::vector<int> ndist(nc, 0);
+  for (int c = 0; c < nc; ++c) {
+    const int *ids = m->cells + 8 * (size_t)c;
+    for (int t = 0; t < 8; ++t) {
+      bool dup = false;
+      for (int u = 0; u < t; ++u) dup = dup || ids[u] == ids[t];
+      if (!dup) {
+        node_cells[ids[t]].push_back(c);
+        ++ndist[c];
+      }
+    }
+  }
+  // (a mesh with any simplex cell takes node-sharing stencils everywhere: face stencils on its
+  // hexahedra next to simplices' node stencils left the mixed scheme unstable too)
+  const bool all_hex = std::all_of(ndist.begin(), ndist.end(), [](int k) { return k == 8; });
+  if (!all_hex && (s->opt.mode == GSIS_MODE_GSIS || s->opt.euler_presteps > 0))
+    return s->fail(GSIS_E_UNSUPPORTED,
+                   "the synthetic solve is built on hexahedral meshes only; prisms, pyramids and tetrahedra take "
+                   "GSIS_MODE_DVM");
+  s->gs_off.assign(nc + 1, 0);
+  s->gs_idx.clear();
+  s->gs_w.clear();
+  for (int c = 0; c < nc; ++c) {
+    std::vector<int> st;
+    if (all_hex) {
+      for (int side = 0; side < 6; ++side)
+        if (s->gnb[6 * (size_t)c + side] >= 0) st.push_back(s->gnb[6 * (size_t)c + side]);
+    } else {
+      for (int t = 0; t < 8; ++t)
+        for (int o : node_cells[m->cells[8 * (size_t)c + t]])
+          if (o != c && std::find(st.begin(), st.end(), o) == st.end()) st.push_back(o);
+      std::sort(st.begin(), st.end());
+      if (st.size() > 80) return s->fail(GSIS_E_UNSUPPORTED, "cell %d: %d stencil cells (at most 80)", c, (int)st.size());
+    }
+    double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    std::vector<std::array<double, 3>> dv(st.size());
+    for (size_t e = 0; e < st.size(); ++e) {
+      for (int d = 0; d < 3; ++d)
+        dv[e][d] = active[d] ? s->xc64[3 * (size_t)st[e] + d] - s->xc64[3 * (size_t)c + d] : 0.0;
+      for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) A[r][q] += dv[e][r] * dv[e][q];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (!active[a]) A[a][a] = 1.0;
+    double tr = 0.0;
+    for (int a = 0; a < 3; ++a)
+      if (active[a]) tr += A[a][a];
+    if (!(det3(A) > 1e-9 * std::pow(tr, nact)))
+      for (int side = 0; side < 6; ++side) {
+        const size_t f = 6 * (size_t)c + side;
+        if (!(area[f] > 0) || s->gnb[f] >= 0 || s->gnb[f] == NB_ABSENT) continue;
+        const double *r = s->gen64[c].f[side].r;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            if (active[a] && active[b]) A[a][b] += r[a] * r[b];
+      }
+    const double det = det3(A);
+    if (!(std::fabs(det) > 0)) return s->fail(GSIS_E_INVALID, "cell %d: singular least-squares system", c);
+    double inv[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) {
+        const int r1 = (q + 1) % 3, r2 = (q + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+        inv[r][q] = (A[r1][c1] * A[r2][c2] - A[r1][c2] * A[r2][c1]) / det;
+      }
+    for (size_t e = 0; e < st.size(); ++e) {
+      s->gs_idx.push_back(st[e]);
+      for (int r = 0; r < 3; ++r) s->gs_w.push_back(inv[r][0] * dv[e][0] + inv[r][1] * dv[e][1] + inv[r][2] * dv[e][2]);
+    }
+    s->gs_off[c + 1] = (int)s->gs_idx.size();
+  }
+  // greedy colouring of the face graph, cells in index order
+  std::vector<int> colour(nc, -1);
+  int ncol = 0;
+  for (int c = 0; c < nc; ++c) {
+    unsigned long long used = 0;
+    for (int side = 0; side < 6; ++side) {
+      const int nb = s->gnb[6 * (size_t)c + side];
+      if (nb >= 0 && colour[nb] >= 0) used |= 1ull << colour[nb];
+    }
+    int k = 0;
+    while (used >> k & 1ull) ++k;
+    colour[c] = k;
+    ncol = std::max(ncol, k + 1);
+  }
+  if (ncol > MACRO_MAX_COLOURS) return s->fail(GSIS_E_UNSUPPORTED, "%d colours (at most %d)", ncol, MACRO_MAX_COLOURS);
+  std::vector<int> order;
+  s->col_off.assign(ncol + 1, 0);
+  g.ncol = ncol;
+  g.maxcol = 0;
+  for (int k = 0; k < ncol; ++k) {
+    for (int c = 0; c < nc; ++c)
+      if (colour[c] == k) order.push_back(c);
+    s->col_off[k + 1] = (int)order.size();
+    g.maxcol = std::max(g.maxcol, s->col_off[k + 1] - s->col_off[k]);
+  }
+  s->col_cell = order;
+  s->pos_of.assign(nc, 0);
+  s->entries.assign(nc, EntryInfo{});
+  s->natcell.assign((size_t)8 * nc, int4{0, 0, 0, 0});
+  for (int oct = 0; oct < 8; ++oct)
+    for (int e = 0; e < nc; ++e) s->natcell[(size_t)oct * nc + e] = int4{order[e], 0, 0, 0};
+  // the synthetic solve's LU-SGS passes over the same colours
+  s->colcells = order;
+  s->mcol_off = s->col_off;
+  s->ncol0 = s->col_off[1];
+  return GSIS_OK;
+}
+
+static int setup_mesh(gsis_solver *s, const gsis_mesh *m);
+static int setup_velocities(gsis_solver *s, const gsis_vgrid *vg);
+
 static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
+  int rc0 = m->ncells > 0 ? setup_unstructured_mesh(s, m) : setup_mesh(s, m);
+  if (rc0) return rc0;
+  return setup_velocities(s, vg);
+}
+
+// structured blocks
+static int setup_mesh(gsis_solver *s, const gsis_mesh *m) {
   s->n[0] = m->ni;
   s->n[1] = m->nj;
   s->n[2] = m->nk;
@@ -1096,7 +1458,12 @@ static int setup(gsis_solver *s, const gsis_mesh *m, const gsis_vgrid *vg) {
     }
     if (col == 0) s->ncol0 = (int)s->colcells.size();
   }
-  // velocities
+  s->mcol_off = {0, s->ncol0, (int)s->nc};
+  s->wall_patch = s->wall_side;
+  return GSIS_OK;
+}
+
+static int setup_velocities(gsis_solver *s, const gsis_vgrid *vg) {
   s->point_set = vg->npoints > 0;
   for (int a = 0; a < 3; ++a) s->nv_axis[a] = s->point_set ? 0 : vg->n[a];
   s->nvc = s->point_set ? vg->npoints : vg->n[0] * vg->n[1] * vg->n[2];
@@ -1191,6 +1558,7 @@ static size_t footprint(const gsis_solver *s) {
   b += (size_t)s->nblocks * (s->nwall + 1) * NWF * T;  // wall partials
   b += s->kin_scratch_bytes;                          // kinetic ring or work arrays in global memory
   if (s->general) b += nc * (sizeof(GenCell<double>) + 6 * (2 * sizeof(int) + 1)) + (size_t)s->nwall * 8;
+  if (s->unstructured) b += 14 * nc + (nc + 1) * 4 + s->gs_idx.size() * (4 + 3 * (T + 8));
   if (s->general && (s->opt.mode == GSIS_MODE_GSIS || s->opt.euler_presteps > 0))
     b += nc * (sizeof(GenCell<double>) + (3 + 6 * (size_t)s->kin_grid + 6 + 6 + 1 + 18 + 6 + 15 + 6 + 6 + 6 + 36 + 36 + 6 + 36) * 8) +
          12 * 8 * (size_t)macro_general_parts((int)nc);
@@ -1273,6 +1641,15 @@ static int allocate_and_upload(gsis_solver *s) {
   A(s->d_wall_uT, 24 * sizeof(double));
   A(s->d_wall_cell, (size_t)(s->nwall + 1) * sizeof(int));
   A(s->d_wall_side, (size_t)(s->nwall + 1) * sizeof(int));
+  A(s->d_wall_patch, (size_t)(s->nwall + 1) * sizeof(int));
+  if (s->unstructured) {
+    A(s->d_gnf, 6 * nc);
+    A(s->d_gpat, 6 * nc);
+    A(s->d_gso, (nc + 1) * sizeof(int));
+    A(s->d_gsi, (s->gs_idx.size() + 1) * sizeof(int));
+    A(s->d_gsw, (s->gs_idx.size() + 1) * 3 * sizeof(T));
+    A(s->d_gsw64, (s->gs_idx.size() + 1) * 3 * sizeof(double));
+  }
   A(s->d_wall_sides, 6 * sizeof(int));
   A(s->d_mom, nc * MOM_STRIDE * sizeof(double));
   A(s->d_wf, (size_t)(s->nwall + 1) * 6 * sizeof(double));
@@ -1341,6 +1718,17 @@ static int allocate_and_upload(gsis_solver *s) {
   if (!rc) rc = s->upload(s->d_natcell, s->natcell.data(), 8 * nc * sizeof(int4));
   if (!rc && s->nwall) rc = s->upload(s->d_wall_cell, s->wall_cell.data(), s->nwall * sizeof(int));
   if (!rc && s->nwall) rc = s->upload(s->d_wall_side, s->wall_side.data(), s->nwall * sizeof(int));
+  if (!rc && s->nwall) rc = s->upload(s->d_wall_patch, s->wall_patch.data(), s->nwall * sizeof(int));
+  if (!rc && s->unstructured) rc = s->upload(s->d_gnf, s->gnf.data(), 6 * nc);
+  if (!rc && s->unstructured) rc = s->upload(s->d_gpat, s->gpat.data(), 6 * nc);
+  std::vector<T> gswT(s->gs_w.begin(), s->gs_w.end());
+  if (!rc && s->unstructured) rc = s->upload(s->d_gso, s->gs_off.data(), (nc + 1) * sizeof(int));
+  if (!rc && s->unstructured && !s->gs_idx.empty()) {
+    rc = s->upload(s->d_gsi, s->gs_idx.data(), s->gs_idx.size() * sizeof(int));
+    if (!rc) rc = s->upload(s->d_gsw, gswT.data(), gswT.size() * sizeof(T));
+    if (!rc) rc = s->upload(s->d_gsw64, s->gs_w.data(), s->gs_w.size() * sizeof(double));
+    if (!rc) rc = s->cuda(cudaStreamSynchronize(s->stream), "sync");  // gswT leaves scope
+  }
   if (!rc && !s->wall_sides_list.empty())
     rc = s->upload(s->d_wall_sides, s->wall_sides_list.data(), s->wall_sides_list.size() * sizeof(int));
   if (!rc) rc = s->upload(s->d_wall_uT, &s->wall_uT[0][0], 24 * sizeof(double));
@@ -1454,11 +1842,18 @@ static int init_state_from(gsis_solver *s, std::vector<double> &W0) {
 static double mesh_mach(const gsis_mesh *m, const gsis_gas *g) {
   const double dr = g->model == GSIS_RYKOV ? g->d_r : 0.0;
   const double gam = (5.0 + dr) / (3.0 + dr);
+  // the sides of a block, or the patches an unstructured mesh uses
+  bool used[6] = {true, true, true, true, true, true};
+  if (m->ncells > 0) {
+    for (int s = 0; s < 6; ++s) used[s] = false;
+    for (size_t t = 0; t < (size_t)6 * m->ncells; ++t)
+      if (m->face_patch[t] >= 0) used[m->face_patch[t]] = true;
+  }
   bool far = false;
-  for (int s = 0; s < 6; ++s) far = far || m->bc[s] == GSIS_BC_FARFIELD;
+  for (int s = 0; s < 6; ++s) far = far || (used[s] && m->bc[s] == GSIS_BC_FARFIELD);
   double ma = 0.0;
   for (int s = 0; s < 6; ++s) {
-    if (m->bc[s] != (far ? GSIS_BC_FARFIELD : GSIS_BC_WALL)) continue;
+    if (!used[s] || m->bc[s] != (far ? GSIS_BC_FARFIELD : GSIS_BC_WALL)) continue;
     const double *u = m->wall_u[s];
     ma = std::max(ma, std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / std::sqrt(0.5 * gam * m->wall_T[s]));
   }
@@ -1621,7 +2016,7 @@ extern "C" int gsis_wall_loads(gsis_handle h, unsigned side_mask, const double *
   WallLoadArgs a{};
   a.wf = h->d_wf;
   a.wall_cell = h->d_wall_cell;
-  a.wall_side = h->d_wall_side;
+  a.wall_side = h->d_wall_patch;  // the mask selects sides (patches of an unstructured mesh)
   a.nwall = h->nwall;
   a.area = h->general ? h->d_wall_area : nullptr;
   for (int d = 0; d < 3; ++d) {

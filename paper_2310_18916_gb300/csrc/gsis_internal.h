@@ -125,7 +125,20 @@ struct KinArgs {
                             // (area-integrated, over the cell's faces); nullptr: not wanted
   const double *wden;       // [wall face] re-emission flux of M(u_w, T_w) over every velocity
                             // (all shards), the denominator of rho_w
+  // unstructured meshes (nullptr on structured blocks): per cell and side the neighbour's side
+  // of the shared face (else the opposite side s ^ 1), the boundary patch (else the side s)
+  const unsigned char *gnf;
+  const unsigned char *gpat;
+  // unstructured meshes: the least-squares stencil as CSR (cell c: entries gso[c] .. gso[c+1]-1
+  // of neighbour gsi[e] with weight gsw[e][3]; gradient = sum_e w_e (q_j - q_c)); nullptr: the
+  // per-side weights of GenCell over the face neighbours
+  const int *gso;
+  const int *gsi;
+  const T *gsw;
 };
+// the neighbour's side of the face a cell shares through side s, and the boundary patch of side s
+__host__ __device__ inline int nb_side(const unsigned char *gnf, int c, int s) { return gnf ? gnf[6 * c + s] : (s ^ 1); }
+__host__ __device__ inline int patch_of(const unsigned char *gpat, int c, int s) { return gpat ? gpat[6 * c + s] : s; }
 
 // ---- launchers (defined in the .cu files) ----
 template <typename T, typename S>
@@ -288,8 +301,14 @@ struct MacroArgs {
   int *iters;              // out
 };
 // The synthetic solve on general meshes (one thread per cell, one launch per phase)
+constexpr int MACRO_MAX_COLOURS = 32;  // colours of the synthetic solve's sweeps at most
 struct MacroGenArgs {
   int nc, nW, model, steps, sweeps, closed, ncol0;
+  int ncolm;                   // colours of the LU-SGS passes (cells of colour k: colcells[colm_off[k] ..])
+  int colm_off[MACRO_MAX_COLOURS + 1];
+  const unsigned char *gnf, *gpat;  // unstructured meshes (see KinArgs), else nullptr
+  const int *gso, *gsi;             // least-squares stencil (see KinArgs), else nullptr
+  const double *gsw;
   int euler;                   // 1: the inviscid presteps (slip walls, no correction, K unused)
   int mh_stride;               // doubles per cell of Mh (18: the moments; 6: a primitive state)
   double mu0, omega, cfl, tol, d_r, Z_r, A[4], mass_ref;

@@ -1284,13 +1284,22 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
 #pragma unroll
         for (int s = 0; s < NF; ++s) {
           if (nb[s] < 0) continue;
-          const T d = fj[s] - fi;
-          gr[0] += g.f[s].w[0] * d;
-          gr[1] += g.f[s].w[1] * d;
-          gr[2] += g.f[s].w[2] * d;
+          if (!A.gso) {
+            const T d = fj[s] - fi;
+            gr[0] += g.f[s].w[0] * d;
+            gr[1] += g.f[s].w[1] * d;
+            gr[2] += g.f[s].w[2] * d;
+          }
           fmax = larger(fmax, fj[s]);
           fmin = smaller(fmin, fj[s]);
         }
+        if (A.gso)
+          for (int e = __ldg(A.gso + c); e < __ldg(A.gso + c + 1); ++e) {
+            const T d = FC(__ldg(A.gsi + e), q) - fi;
+            gr[0] += A.gsw[3 * e] * d;
+            gr[1] += A.gsw[3 * e + 1] * d;
+            gr[2] += A.gsw[3 * e + 2] * d;
+          }
         const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
 #pragma unroll
         for (int s = 0; s < NF; ++s)
@@ -1322,10 +1331,10 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
         } else if (sn < (T)0) {
           if (nb >= 0) {
 #pragma unroll
-            for (int q = 0; q < NV; ++q) e[q] = FF(nb, q, s ^ 1);
+            for (int q = 0; q < NV; ++q) e[q] = FF(nb, q, nb_side(A.gnf, c, s));
           } else if (nb == NB_WALL || A.gin[6 * c + s]) {
             // the wall's re-emission rho_w M_w, or the free stream entering (f1: (d_r T / 4) M)
-            const double *uT = A.wall_uT + 4 * s;
+            const double *uT = A.wall_uT + 4 * patch_of(A.gpat, c, s);
             const T M = wall_maxwellian<T>(uT, x, y, z) * (nb == NB_WALL ? (T)A.rho_w[__ldg(A.gwid + 6 * c + s)] : (T)1);
             e[0] = M;
             if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
@@ -1413,9 +1422,9 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
           } else if (sn < (T)0) {
             if (nb >= 0) {
 #pragma unroll
-              for (int q = 0; q < NV; ++q) e[q] = FF(nb, q, s ^ 1) + DF(nb, q);
+              for (int q = 0; q < NV; ++q) e[q] = FF(nb, q, nb_side(A.gnf, c, s)) + DF(nb, q);
             } else if (nb == NB_WALL || A.gin[6 * c + s]) {
-              const double *uT = A.wall_uT + 4 * s;
+              const double *uT = A.wall_uT + 4 * patch_of(A.gpat, c, s);
               const T M = wall_maxwellian<T>(uT, x, y, z) * (nb == NB_WALL ? (T)A.rho_w[__ldg(A.gwid + 6 * c + s)] : (T)1);
               e[0] = M;
               if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
@@ -1452,7 +1461,7 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
 #pragma unroll
           for (int q = 0; q < NV; ++q) e[q] = FF(c, q, s) + df[q];
         } else {
-          const double *uT = A.wall_uT + 4 * s;
+          const double *uT = A.wall_uT + 4 * patch_of(A.gpat, c, s);
           const T M = sn < (T)0 ? wall_maxwellian<T>(uT, x, y, z) * (T)A.rho_w[wid] : (T)0;
           e[0] = M;
           if constexpr (NV == 2) e[NV - 1] = (T)(A.d_r * uT[3] / 4.0) * M;
@@ -1492,7 +1501,7 @@ __global__ void __launch_bounds__(256) wall_prepass_general_kernel(const KinArgs
 #pragma unroll
   for (int s = 0; s < 6; ++s) nb[s] = __ldg(A.gnb + 6 * c + s);
   const GenFace<T> &fa = g.f[side];
-  const double *uT = A.wall_uT + 4 * side;
+  const double *uT = A.wall_uT + 4 * patch_of(A.gpat, c, side);
   double num = 0.0, den = 0.0;
   for (int b = warp; b < A.nblocks; b += nw) {
     const T *vp = A.vel + ((size_t)b * VB + lane) * 4;
@@ -1513,12 +1522,21 @@ __global__ void __launch_bounds__(256) wall_prepass_general_kernel(const KinArgs
       for (int s = 0; s < 6; ++s) {
         if (nb[s] < 0) continue;
         const T fj = fn(nb[s]), d = fj - fi;
-        gr[0] += g.f[s].w[0] * d;
-        gr[1] += g.f[s].w[1] * d;
-        gr[2] += g.f[s].w[2] * d;
+        if (!A.gso) {
+          gr[0] += g.f[s].w[0] * d;
+          gr[1] += g.f[s].w[1] * d;
+          gr[2] += g.f[s].w[2] * d;
+        }
         fmax = larger(fmax, fj);
         fmin = smaller(fmin, fj);
       }
+      if (A.gso)
+        for (int e = __ldg(A.gso + c); e < __ldg(A.gso + c + 1); ++e) {
+          const T d = fn(__ldg(A.gsi + e)) - fi;
+          gr[0] += A.gsw[3 * e] * d;
+          gr[1] += A.gsw[3 * e + 1] * d;
+          gr[2] += A.gsw[3 * e + 2] * d;
+        }
       const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
       const T ff = fi + (phi * gr[0]) * fa.r[0] + (phi * gr[1]) * fa.r[1] + (phi * gr[2]) * fa.r[2];
       num += (double)(wv * sn * ff);
@@ -1554,7 +1572,7 @@ __global__ void __launch_bounds__(256) wall_den_general_kernel(const KinArgs<T, 
   const int w = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = wall_cell[w], side = wall_side[w];
   const GenFace<T> &fa = A.gen[c].f[side];
-  const double *uT = A.wall_uT + 4 * side;
+  const double *uT = A.wall_uT + 4 * patch_of(A.gpat, c, side);
   double den = 0.0;
   for (int v = threadIdx.x; v < nslots; v += blockDim.x) {
     const T x = (T)vel64[4 * v], y = (T)vel64[4 * v + 1], z = (T)vel64[4 * v + 2], wv = (T)vel64[4 * v + 3];

@@ -105,8 +105,8 @@ __device__ void kappas(const MacroGenArgs &m, double mu, double *kt, double *kr)
 // Outward flux per unit area of local equilibrium at the cell state p meeting the diffuse wall of
 // `side` (u_w, T_w) along the unit normal n: the half moving into the wall leaves with the
 // half-range moments J_k of N(u_n, T/2), the wall re-emits rho_w M(u_w, T_w) with zero net mass.
-__device__ void wall_eq_flux(const MacroGenArgs &m, int side, const double *p, const double *n, double *F) {
-  const double *uT = m.wall_uT + 4 * side;
+__device__ void wall_eq_flux(const MacroGenArgs &m, int patch, const double *p, const double *n, double *F) {
+  const double *uT = m.wall_uT + 4 * patch;
   const double rho = p[0], T = p[4], un = p[1] * n[0] + p[2] * n[1] + p[3] * n[2], Tw = uT[3];
   const double sr = un / sqrt(T);
   const double M0 = exp(-sr * sr) / sqrt(kPi * T);
@@ -178,10 +178,10 @@ __device__ void face_flux(const MacroGenArgs &m, int i, int side, int j, const d
   face_state(m, i, side, WL, pL);
   int jv = i;
   if (j >= 0) {
-    face_state(m, j, side ^ 1, WR, pR);
+    face_state(m, j, nb_side(m.gnf, i, side), WR, pR);
     jv = j;
   } else {
-    const double *uT = m.wall_uT + 4 * side;
+    const double *uT = m.wall_uT + 4 * patch_of(m.gpat, i, side);
     const double pinf[6] = {1.0, uT[0], uT[1], uT[2], uT[3], uT[3]};
     cons_of(m, pinf, WR);
     prim_of(m, WR, pR);
@@ -240,10 +240,16 @@ __global__ void grad_kernel(MacroGenArgs m) {
       for (int s = 0; s < 6; ++s) {
         if (nb[s] < 0) continue;
         const double qj = m.W[6 * (size_t)nb[s] + k], d = qj - qi;
-        for (int a = 0; a < 3; ++a) gr[a] += g.f[s].w[a] * d;
+        if (!m.gso)
+          for (int a = 0; a < 3; ++a) gr[a] += g.f[s].w[a] * d;
         qmax = qj > qmax ? qj : qmax;
         qmin = qj < qmin ? qj : qmin;
       }
+      if (m.gso)
+        for (int e = m.gso[c]; e < m.gso[c + 1]; ++e) {
+          const double d = m.W[6 * (size_t)m.gsi[e] + k] - qi;
+          for (int a = 0; a < 3; ++a) gr[a] += m.gsw[3 * e + a] * d;
+        }
       double phi = 1.0;
       for (int s = 0; s < 6; ++s) {
         if (nb[s] == NB_ABSENT || nb[s] == NB_AXIS) continue;
@@ -262,10 +268,17 @@ __global__ void grad_kernel(MacroGenArgs m) {
     for (int k = 0; k < 5; ++k) {
       const double qi = m.pr[6 * (size_t)c + 1 + k];
       double gr[3] = {0.0, 0.0, 0.0};
-      for (int s = 0; s < 6; ++s) {
-        if (nb[s] < 0) continue;
-        const double d = m.pr[6 * (size_t)nb[s] + 1 + k] - qi;
-        for (int a = 0; a < 3; ++a) gr[a] += g.f[s].w[a] * d;
+      if (m.gso) {
+        for (int e = m.gso[c]; e < m.gso[c + 1]; ++e) {
+          const double d = m.pr[6 * (size_t)m.gsi[e] + 1 + k] - qi;
+          for (int a = 0; a < 3; ++a) gr[a] += m.gsw[3 * e + a] * d;
+        }
+      } else {
+        for (int s = 0; s < 6; ++s) {
+          if (nb[s] < 0) continue;
+          const double d = m.pr[6 * (size_t)nb[s] + 1 + k] - qi;
+          for (int a = 0; a < 3; ++a) gr[a] += g.f[s].w[a] * d;
+        }
       }
       for (int a = 0; a < 3; ++a) m.gP[15 * (size_t)c + 3 * k + a] = gr[a];
     }
@@ -273,14 +286,16 @@ __global__ void grad_kernel(MacroGenArgs m) {
 }
 
 // Interior faces once each, from the cell on their lower side (the upper sides 1, 3, 5 of every
-// cell): the flux seen from the other cell is its exact negative (opposite normal, swapped
-// states), so each cell's residual reads it instead of computing it again.
+// cell of a structured block; on an unstructured mesh the cell of lower index): the flux seen
+// from the other cell is its exact negative (opposite normal, swapped states), so each cell's
+// residual reads it instead of computing it again.
 __global__ void face_kernel(MacroGenArgs m) {
   if (done(m)) return;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * m.nc; t += gridDim.x * blockDim.x) {
-    const int c = t / 3, s = 2 * (t - 3 * c) + 1;
+  const int per = m.gnf ? 6 : 3;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < per * m.nc; t += gridDim.x * blockDim.x) {
+    const int c = t / per, s = m.gnf ? t - 6 * c : 2 * (t - 3 * c) + 1;
     const int nb = m.gnb[6 * (size_t)c + s];
-    if (nb < 0) continue;
+    if (nb < 0 || (m.gnf && nb < c)) continue;
     const double *S = m.gen[c].f[s].S;
     const double A = sqrt(dot3(S, S)), iA = 1.0 / A, n[3] = {S[0] * iA, S[1] * iA, S[2] * iA};
     face_flux(m, c, s, nb, n, m.Ff + 36 * (size_t)c + 6 * s);
@@ -306,10 +321,12 @@ __global__ void resid_kernel(MacroGenArgs m, int step) {
         for (int k = 0; k < 6; ++k) F[k] = 0.0;
         for (int a = 0; a < 3; ++a) F[1 + a] = pt * n[a];
       } else if (nb == NB_WALL) {
-        wall_eq_flux(m, s, m.pr + 6 * (size_t)c, n, F);
+        wall_eq_flux(m, patch_of(m.gpat, c, s), m.pr + 6 * (size_t)c, n, F);
       } else if (nb >= 0) {
-        const double *Fs = (s & 1) ? m.Ff + 36 * (size_t)c + 6 * s : m.Ff + 36 * (size_t)nb + 6 * (s ^ 1);
-        for (int k = 0; k < 6; ++k) F[k] = (s & 1) ? Fs[k] : -Fs[k];
+        // each interior face flux is computed once, by its owner (see face_kernel)
+        const bool own = m.gnf ? c < nb : (s & 1) != 0;
+        const double *Fs = own ? m.Ff + 36 * (size_t)c + 6 * s : m.Ff + 36 * (size_t)nb + 6 * nb_side(m.gnf, c, s);
+        for (int k = 0; k < 6; ++k) F[k] = own ? Fs[k] : -Fs[k];
       } else {
         face_flux(m, c, s, nb, n, F);
       }
@@ -503,8 +520,8 @@ cudaError_t run_macro_general(const MacroGenArgs &m, cudaStream_t s) {
     resid_kernel<<<grid, kBlock, 0, s>>>(m, step);
     diag_kernel<<<grid, kBlock, 0, s>>>(m);
     for (int sw = 0; sw < m.sweeps; ++sw) {
-      sweep_kernel<<<grid, kBlock, 0, s>>>(m, 0, m.ncol0);
-      sweep_kernel<<<grid, kBlock, 0, s>>>(m, m.ncol0, m.nc - m.ncol0);
+      for (int k = 0; k < m.ncolm; ++k)
+        sweep_kernel<<<grid, kBlock, 0, s>>>(m, m.colm_off[k], m.colm_off[k + 1] - m.colm_off[k]);
     }
     update_kernel<<<grid, kBlock, 0, s>>>(m);
     check_kernel<<<1, 32, 0, s>>>(m, grid, step);

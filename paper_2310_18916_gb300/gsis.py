@@ -30,7 +30,8 @@ ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void
 
 class Mesh(C.Structure):
     _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nk", C.c_int), ("nodes", D), ("bc", C.c_int * 6),
-                ("wall_u", (C.c_double * 3) * 6), ("wall_T", C.c_double * 6)]
+                ("wall_u", (C.c_double * 3) * 6), ("wall_T", C.c_double * 6), ("ncells", C.c_int), ("nnodes", C.c_int),
+                ("unodes", D), ("cells", C.POINTER(C.c_int)), ("face_patch", C.POINTER(C.c_int))]
 
 
 class Vgrid(C.Structure):
@@ -112,6 +113,15 @@ def build_structs(problem, keep):
     m = Mesh()
     m.ni, m.nj, m.nk = problem.ni, problem.nj, problem.nk
     m.nodes = _p(nodes)
+    if getattr(problem, "ucells", None) is not None:
+        un = np.ascontiguousarray(problem.unodes, dtype=np.float64)
+        uc = np.ascontiguousarray(problem.ucells, dtype=np.int32)
+        up = np.ascontiguousarray(problem.upatch, dtype=np.int32)
+        keep += [un, uc, up]
+        m.ncells, m.nnodes = len(uc), len(un)
+        m.unodes = _p(un)
+        m.cells = uc.ctypes.data_as(C.POINTER(C.c_int))
+        m.face_patch = up.ctypes.data_as(C.POINTER(C.c_int))
     for s in range(6):
         m.bc[s] = int(problem.bc[s])
         m.wall_T[s] = float(problem.wall_T[s])

@@ -47,9 +47,14 @@ class Problem:
     W0: np.ndarray = field(default=None)   # (ncells, 6): rho, ux, uy, uz, Tt, Tr
     name: str = ""
     vpoints: np.ndarray = field(default=None)  # (nv, 4) unstructured velocity set: xi(3), weight
+    unodes: np.ndarray = field(default=None)   # unstructured mesh: (nnodes, 3) node coordinates
+    ucells: np.ndarray = field(default=None)   # (ncells, 8) node ids per cell (hexahedron order)
+    upatch: np.ndarray = field(default=None)   # (ncells, 6) boundary patch per side, -1 if shared
 
     @property
     def ncells(self) -> int:
+        if self.ucells is not None:
+            return len(self.ucells)
         return self.ni * self.nj * self.nk
 
     @property
@@ -66,8 +71,9 @@ class Problem:
         c^2 = gamma T / 2 (T in T0, speeds in sqrt(2 R T0)) and gamma = (5 + d_r) / (3 + d_r)."""
         d_r = self.d_r if self.model == RYKOV else 0.0
         gamma = (5.0 + d_r) / (3.0 + d_r)
-        far = [s for s in range(6) if self.bc[s] == FARFIELD]
-        sides = far if far else [s for s in range(6) if self.bc[s] == WALL]
+        used = set(range(6)) if self.upatch is None else {int(q) for q in np.unique(self.upatch) if q >= 0}
+        far = [s for s in range(6) if s in used and self.bc[s] == FARFIELD]
+        sides = far if far else [s for s in range(6) if s in used and self.bc[s] == WALL]
         return max([float(np.linalg.norm(self.wall_u[s])) / np.sqrt(0.5 * gamma * self.wall_T[s]) for s in sides],
                    default=0.0)
 
@@ -371,4 +377,123 @@ def with_velocity_set(p: Problem, points) -> Problem:
     """The same problem on an unstructured velocity set (points: (nv, 4) = xi(3), weight)."""
     p.vpoints = np.ascontiguousarray(points, dtype=np.float64)
     p.name += f"_vset{len(points)}"
+    return p
+
+
+# Sides of a hexahedral cell (corner t at offsets (t & 1, (t >> 1) & 1, t >> 2)), the order of
+# the library's unstructured meshes: x-, x+, y-, y+, z-, z+ for an axis-aligned cell.
+HEX_SIDES = ((0, 2, 6, 4), (1, 3, 7, 5), (0, 1, 5, 4), (2, 3, 7, 6), (0, 1, 3, 2), (4, 5, 7, 6))
+
+
+def _patches_by_position(nodes, cells, box):
+    """Boundary patch of each cell side from where its face lies on the axis-aligned box
+    ((x0, x1), (y0, y1), (z0, z1)): 0/1 on x = x0/x1, 2/3 on y, 4/5 on z; -1 for inner sides.
+    Sides whose corners span no area are left -1 (they carry no flux)."""
+    patch = np.full((len(cells), 6), -1, dtype=np.int32)
+    for c, ids in enumerate(cells):
+        for sd, corners in enumerate(HEX_SIDES):
+            q = np.array([ids[t] for t in corners])
+            if len(set(q.tolist())) < 3:
+                continue
+            P = nodes[q]
+            for a in range(3):
+                for hi in range(2):
+                    if np.all(np.abs(P[:, a] - box[a][hi]) < 1e-12):
+                        patch[c, sd] = 2 * a + hi
+    return patch
+
+
+def as_unstructured(p: Problem) -> Problem:
+    """The same block as an unstructured mesh: every cell a hexahedron of node ids, sides on the
+    block's boundary in the patch of that side; the nodes of a closed (wrapped) axis merged.  A
+    one-cell periodic axis becomes a one-layer PERIODIC patch and must lie along z."""
+    ni, nj, nk = p.ni, p.nj, p.nk
+    n = (ni, nj, nk)
+    wrap = [p.bc[2 * a] == PERIODIC and n[a] >= 3 for a in range(3)]
+    N = (ni + 1, nj + 1, nk + 1)
+    X = p.nodes.reshape(-1, 3)
+    def nid(I, J, K):
+        I, J, K = [q % n[a] if wrap[a] else q for a, q in enumerate((I, J, K))]
+        return I + N[0] * (J + N[1] * K)
+    cells, patch = [], []
+    for k in range(nk):
+        for j in range(nj):
+            for i in range(ni):
+                cells.append([nid(i + (t & 1), j + ((t >> 1) & 1), k + (t >> 2)) for t in range(8)])
+                idx = (i, j, k)
+                pt = []
+                for sd in range(6):
+                    a, hi = sd // 2, sd & 1
+                    at_edge = idx[a] == (n[a] - 1 if hi else 0)
+                    pt.append(sd if at_edge and not wrap[a] else -1)
+                patch.append(pt)
+    q = Problem(ni, nj, nk, p.nodes, list(p.bc), p.wall_u.copy(), p.wall_T.copy(), p.vx, p.vy, p.vz, p.wx, p.wy, p.wz,
+                p.model, p.omega, p.Kn, p.d_r, p.Z_r, p.A, p.W0, p.name + "_unstructured", p.vpoints)
+    q.unodes = np.ascontiguousarray(X, dtype=np.float64)
+    q.ucells = np.ascontiguousarray(cells, dtype=np.int32)
+    q.upatch = np.ascontiguousarray(patch, dtype=np.int32)
+    return q
+
+
+def unstructured_cavity(n=8, nv=12, vmax=5.0, lid=0.16, Kn=0.1, omega=0.81, hybrid=0.5) -> Problem:
+    """The lid-driven cavity [0, 1]^2 as a one-layer unstructured mesh: the n x n squares with
+    x < hybrid split into two triangles each (alternating diagonals), the others kept whole;
+    extruded one cell in z (prisms and hexahedra sharing quadrilateral faces).  Walls on the
+    four sides (patches 0..3, the lid y = 1 moving along x), a PERIODIC patch on the two z faces."""
+    xs = np.linspace(0.0, 1.0, n + 1)
+    dz = 1.0 / n
+    nid = lambda i, j, k: i + (n + 1) * (j + (n + 1) * k)
+    nodes = np.array([[xs[i], xs[j], k * dz] for k in range(2) for j in range(n + 1) for i in range(n + 1)])
+    cells = []
+    for j in range(n):
+        for i in range(n):
+            a, b, c, d = nid(i, j, 0), nid(i + 1, j, 0), nid(i, j + 1, 0), nid(i + 1, j + 1, 0)
+            A_, B_, C_, D_ = a + (n + 1) ** 2, b + (n + 1) ** 2, c + (n + 1) ** 2, d + (n + 1) ** 2
+            if (i + 0.5) / n < hybrid:
+                tris = ((a, b, d), (a, d, c)) if (i + j) % 2 == 0 else ((a, b, c), (b, d, c))
+                top = {a: A_, b: B_, c: C_, d: D_}
+                for t0, t1, t2 in tris:
+                    cells.append([t0, t1, t2, t2, top[t0], top[t1], top[t2], top[t2]])
+            else:
+                cells.append([a, b, c, d, A_, B_, C_, D_])
+    cells = np.array(cells, dtype=np.int32)
+    patch = _patches_by_position(nodes, cells, ((0.0, 1.0), (0.0, 1.0), (0.0, dz)))
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[3, 0] = lid
+    p = Problem(1, 1, 1, np.zeros((2, 2, 2, 3)), [WALL, WALL, WALL, WALL, PERIODIC, PERIODIC], wall_u, np.ones(6), v,
+                v.copy(), v.copy(), w, w.copy(), w.copy(), SHAKHOV, omega, Kn, W0=_uniform_state(len(cells)),
+                name=f"ucavity{n}x{nv}^3_h{hybrid:g}")
+    p.unodes, p.ucells, p.upatch = np.ascontiguousarray(nodes), cells, patch
+    return p
+
+
+def tet_box(n=3, nv=8, vmax=5.0, Kn=0.1, omega=0.81, wall_speed=0.2) -> Problem:
+    """The unit cube with diffuse walls (the z = 1 wall moving along x), its n^3 cubes each split
+    into six tetrahedra along the main diagonal (the Kuhn split: conforming across cubes)."""
+    import itertools
+
+    nid = lambda i, j, k: i + (n + 1) * (j + (n + 1) * k)
+    h = 1.0 / n
+    nodes = np.array([[i * h, j * h, k * h] for k in range(n + 1) for j in range(n + 1) for i in range(n + 1)])
+    cells = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                for perm in itertools.permutations(range(3)):
+                    cur = [i, j, k]
+                    path = [nid(*cur)]
+                    for ax in perm:
+                        cur[ax] += 1
+                        path.append(nid(*cur))
+                    a, b, c, d = path
+                    cells.append([a, b, c, c, d, d, d, d])
+    cells = np.array(cells, dtype=np.int32)
+    patch = _patches_by_position(nodes, cells, ((0.0, 1.0), (0.0, 1.0), (0.0, 1.0)))
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[5, 0] = wall_speed
+    p = Problem(1, 1, 1, np.zeros((2, 2, 2, 3)), [WALL] * 6, wall_u, np.ones(6), v, v.copy(), v.copy(), w, w.copy(),
+                w.copy(), SHAKHOV, omega, Kn, W0=_uniform_state(len(cells)), name=f"tetbox{n}x{nv}^3")
+    p.unodes, p.ucells, p.upatch = np.ascontiguousarray(nodes), cells, patch
     return p

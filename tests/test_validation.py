@@ -179,3 +179,32 @@ def test_unstructured_velocity_sets_are_validated():
     # footprints grow with the padded point count, not with the ignored tensor axes
     big = wl.with_velocity_set(wl.cavity(n=8, nv=4), np.concatenate([p.vpoints, p.vpoints + [0.01, 0, 0, 0]]))
     assert gsis.footprint_bytes(big) > gsis.footprint_bytes(p)
+
+
+def test_unstructured_meshes_are_validated():
+    """Unstructured cells through gsis_footprint_bytes (the same checks and set-up as
+    gsis_create): shapes and shared sides accepted; a side neither shared nor on a patch, a
+    shared side carrying a patch, a node id out of range, a PERIODIC patch not normal to z and
+    GSIS on prisms or tetrahedra are refused."""
+    GSIS_E_UNSUPPORTED = -7
+    good = (wl.tet_box(n=2, nv=8), wl.unstructured_cavity(n=4, nv=8), wl.as_unstructured(wl.cavity(n=6, nv=8)),
+            wl.as_unstructured(wl.cylinder(n_r=4, n_theta=8, nv=8)))
+    for p in good:
+        assert code(p, mode=gsis.MODE_DVM) == gsis.GSIS_OK, p.name
+    assert code(good[2]) == gsis.GSIS_OK and code(good[3]) == gsis.GSIS_OK   # hexahedra: GSIS too
+    assert code(good[0]) == GSIS_E_UNSUPPORTED and code(good[1]) == GSIS_E_UNSUPPORTED
+    p = wl.tet_box(n=2, nv=8)
+    q = dataclasses.replace(p, upatch=p.upatch.copy())
+    c, s = np.argwhere(q.upatch >= 0)[0]
+    q.upatch[c, s] = -1   # a boundary side with no patch
+    assert code(q, mode=gsis.MODE_DVM) == GSIS_E_INVALID
+    q = dataclasses.replace(p, upatch=p.upatch.copy())
+    shared = [(c, s) for c in range(q.ncells) for s in (0, 1, 2, 4) if p.upatch[c, s] < 0]
+    q.upatch[shared[0]] = 1   # a shared side that also names a patch
+    assert code(q, mode=gsis.MODE_DVM) == GSIS_E_INVALID
+    q = dataclasses.replace(p, ucells=p.ucells.copy())
+    q.ucells[3, 2] = len(p.unodes)
+    assert code(q, mode=gsis.MODE_DVM) == GSIS_E_INVALID
+    c2 = wl.unstructured_cavity(n=4, nv=8)
+    q = dataclasses.replace(c2, bc=[wl.PERIODIC, wl.PERIODIC, wl.WALL, wl.WALL, wl.WALL, wl.WALL])
+    assert code(q, mode=gsis.MODE_DVM) == GSIS_E_UNSUPPORTED
