@@ -357,6 +357,14 @@ BODIES = {
     # cells, Ma 0.5, Kn 0.05, 40^3 velocities on [-6, 6]^3
     "cylinder_gsis": dict(kind="cylinder", n=(64, 1, 128), nv=40, vmax=6.0, Ma=0.5, Kn=0.05, first=0.01, R_out=10.0,
                           mode="gsis", euler_presteps=300),
+    # capsule forebody (heat-shield cap of radius 1, 33 deg conical afterbody): 50 radial x 40 polar
+    # x 50 azimuthal cells (100,000), diatomic Rykov gas (two reduced VDFs), Ma 10, Kn 0.01, wall at
+    # 0.3 T0, 48^3 velocities clustered about the free stream on [-16, 16]^3 (1.1e10 points)
+    "capsule": dict(kind="capsule", n=(50, 40, 50), nv=48, vmax=None, Ma=10.0, Kn=0.01, first=None, R_out=6.0,
+                    T_w=0.3, oracle_nv=8),
+    # the capsule at 1/8 of the cells with 24^3 velocities, the size its oracle parity runs at
+    "capsule_small": dict(kind="capsule", n=(25, 20, 25), nv=24, vmax=None, Ma=10.0, Kn=0.01, first=None,
+                          R_out=6.0, T_w=0.3, oracle_nv=8),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }
@@ -367,6 +375,9 @@ def body_problem(name):
     from paper_2310_18916_gb300 import workloads as wl
 
     b = BODIES[name]
+    if b["kind"] == "capsule":
+        return wl.capsule(n_r=b["n"][0], n_pol=b["n"][1], n_az=b["n"][2], nv=b["nv"], R_out=b["R_out"],
+                          first=b["first"], Ma=b["Ma"], Kn=b["Kn"], T_w=b["T_w"], vmax=b["vmax"])
     if b["kind"] == "sphere":
         p = wl.sphere(n_r=b["n"][0], n_pol=b["n"][1], n_az=b["n"][2], nv=b["nv"], R=0.5, R_out=b["R_out"],
                       first=b["first"], Ma=b["Ma"], Kn=b["Kn"], vmax=b["vmax"])
@@ -387,11 +398,13 @@ def run_body(args):
     import torch
 
     from paper_2310_18916_gb300 import gsis
+    from paper_2310_18916_gb300 import workloads as wl
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     p = body_problem(args.body)
-    pts = p.ncells * p.nvel
+    nvdf = 2 if p.model == wl.RYKOV else 1   # a phase-space update counts each reduced VDF's point
+    pts = p.ncells * p.nvel * nvdf
     b = BODIES[args.body]
     mode = b.get("mode", "dvm")
     if mode == "gsis":
@@ -438,7 +451,7 @@ def run_body(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
         "config": {"workload": f"{p.name}: {BODIES[args.body]}", "precision": f"{args.precision} VDF",
-                   "cells": p.ncells, "velocities": p.nvel, "points": pts, "n_sweeps": BODY_SWEEPS,
+                   "cells": p.ncells, "velocities": p.nvel, "vdfs": nvdf, "points": pts, "n_sweeps": BODY_SWEEPS,
                    "mode": mode, "kin_inv_dt": kw.get("kin_inv_dt", 0.0),
                    "euler_presteps": kw.get("euler_presteps", 0), "parallelism": "1 GPU",
                    "l2": f"inputs larger than L2 (VDF {pts * sbytes / 1e9:.2f} GB)", "eps_last": eps,
@@ -464,14 +477,18 @@ def run_body(args):
 
 
 def body_oracle_sample(name):
-    """The oracle on the same mesh with 12^3 velocities (one step of the same mode, all host
-    cores; the Euler presteps of a GSIS body untimed), scaled to updates/s."""
+    """The oracle on the same mesh with 12^3 velocities (8^3 on the capsule; one step of the same
+    mode, all host cores; the Euler presteps of a GSIS body untimed), scaled to updates/s."""
+    import numpy as np
+
     from oracle.oracle import Oracle
     from paper_2310_18916_gb300 import workloads as wl
 
     p = body_problem(name)
     b = BODIES[name]
-    v, w = wl.midpoint_grid(12, -b["vmax"], b["vmax"])
+    nvo = b.get("oracle_nv", 12)
+    vmax = b["vmax"] or float(max(np.abs(p.vx).max(), np.abs(p.vy).max(), np.abs(p.vz).max()))
+    v, w = wl.midpoint_grid(nvo, -vmax, vmax)
     p.vx, p.vy, p.vz, p.wx, p.wy, p.wz = v, v.copy(), v.copy(), w, w.copy(), w.copy()
     p.vpoints = None
     cores = os.cpu_count() or 1
@@ -485,8 +502,9 @@ def body_oracle_sample(name):
     t0 = time.perf_counter()
     o.step()
     dt = time.perf_counter() - t0
-    return {"value": p.ncells * p.nvel / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one {what} of the same mesh with 12^3 velocities ({dt:.1f} s)"}
+    nvdf = 2 if p.model == wl.RYKOV else 1
+    return {"value": p.ncells * p.nvel * nvdf / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one {what} of the same mesh with {nvo}^3 velocities ({dt:.1f} s)"}
 
 
 def run_serve(args):

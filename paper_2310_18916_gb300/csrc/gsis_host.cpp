@@ -1505,7 +1505,8 @@ static int plan_kinetic(gsis_solver *s) {
   if (s->general) {
     // persistent grid of 8-warp CTAs over the velocity blocks, as many as the SMs hold (the
     // kernel is latency-bound) while their whole-mesh work arrays, one set per CTA for its
-    // block of 32 velocities, stay within 48 GB
+    // block of 32 velocities, stay within 144 GB (half of the GPU's memory: a 100,000-cell
+    // mesh with two reduced VDFs takes 243 MB per CTA, four CTAs per SM)
     s->kin_smem = 0;
     s->kin_warps = 8;
     s->kin_gstride = kinetic_general_stride<T, S>(s->nc, s->nvdf, s->kg.nact);
@@ -1516,7 +1517,7 @@ static int plan_kinetic(gsis_solver *s) {
     } else {
       cudaGetLastError();
     }
-    const size_t budget = (size_t)48 << 30;
+    const size_t budget = (size_t)144 << 30;
     const int by_mem = (int)std::max<size_t>(1, budget / ((size_t)sms * s->kin_gstride));
     s->kin_grid = std::max(1, std::min(s->nblocks, std::max(1, std::min(occ, by_mem)) * sms));
     s->kin_scratch_bytes = (size_t)s->kin_grid * s->kin_gstride;

@@ -497,3 +497,61 @@ def tet_box(n=3, nv=8, vmax=5.0, Kn=0.1, omega=0.81, wall_speed=0.2) -> Problem:
                 w.copy(), SHAKHOV, omega, Kn, W0=_uniform_state(len(cells)), name=f"tetbox{n}x{nv}^3")
     p.unodes, p.ucells, p.upatch = np.ascontiguousarray(nodes), cells, patch
     return p
+
+
+def capsule_profile(theta, x_o=-0.2, cap_half_angle=np.pi / 3, cone_half_angle=np.radians(33.0)):
+    """Distance from the origin (x_o, 0) to the capsule's surface along the meridian ray at polar
+    angle theta from +x: a spherical-cap heat shield of radius 1 centred at the origin of x, facing
+    -x, up to the shoulder at cap_half_angle from the -x axis, then a cone converging downstream at
+    cone_half_angle to its apex on the axis."""
+    c, s = np.cos(theta), np.sin(theta)
+    # the cap: |(x_o + t c, t s)| = 1
+    b = x_o * c
+    t_cap = -b + np.sqrt(b * b - x_o * x_o + 1.0)
+    xs, ys = -np.cos(cap_half_angle), np.sin(cap_half_angle)        # the shoulder
+    xa = xs + ys / np.tan(cone_half_angle)                          # the apex
+    # the cone: points (x, y) with y = (xa - x) tan(cone_half_angle), x in [xs, xa]
+    k = np.tan(cone_half_angle)
+    t_cone = (xa - x_o) * k / (s + c * k)
+    x_cap = x_o + t_cap * c
+    return np.where(x_cap <= xs, t_cap, t_cone)
+
+
+def capsule(n_r=50, n_pol=40, n_az=50, nv=48, R_out=6.0, first=None, Ma=10.0, Kn=0.01, T_w=0.3, vmax=None,
+            rykov=True) -> Problem:
+    """Hypersonic capsule forebody in a flow along +x: the body of revolution of capsule_profile
+    (heat-shield cap radius 1, 33 deg conical afterbody), a spherical O-grid about (-0.2, 0, 0):
+    i radial from the body (diffuse wall at T_w) to a far field at R_out, j polar from +x (AXIS at
+    both poles), k azimuth (closed).  The diatomic Rykov gas of Section 5 (d_r = 2, Z_r = 5,
+    nitrogen A, omega 0.74) by default, free stream U = Ma sqrt(gamma T / 2) with gamma = 7/5,
+    T = 1; velocities clustered about the free stream on [-vmax, vmax]^3 (default: 3.5 thermal
+    speeds of the stagnation gas, and 4.5 beyond the free-stream speed)."""
+    gamma = 7.0 / 5.0 if rykov else 5.0 / 3.0
+    U = Ma * np.sqrt(gamma / 2.0)
+    if vmax is None:
+        vmax = max(U + 4.5, 3.5 * np.sqrt(1.0 + 0.5 * (gamma - 1.0) * Ma * Ma))
+    th = np.pi * np.arange(n_pol + 1) / n_pol
+    ct, st = np.cos(th), np.sin(th)
+    ct[0], st[0], ct[-1], st[-1] = 1.0, 0.0, -1.0, 0.0
+    rb = capsule_profile(th)
+    ph = 2.0 * np.pi * np.arange(n_az + 1) / n_az
+    cp, sp = np.cos(ph), np.sin(ph)
+    cp[-1], sp[-1] = cp[0], sp[0]
+    nodes = np.zeros((n_az + 1, n_pol + 1, n_r + 1, 3))
+    for j in range(n_pol + 1):
+        r = radial_nodes(n_r, rb[j], R_out, None if first is None else first * rb[j])
+        nodes[:, j, :, 0] = -0.2 + ct[j] * r[None, :]
+        nodes[:, j, :, 1] = (st[j] * cp[:, None]) * r[None, :]
+        nodes[:, j, :, 2] = (st[j] * sp[:, None]) * r[None, :]
+    v, w = midpoint_grid(nv, -vmax, vmax)
+    wall_u = np.zeros((6, 3))
+    wall_u[1, 0] = U
+    wall_T = np.ones(6)
+    wall_T[0] = T_w
+    nc = n_r * n_pol * n_az
+    p = Problem(n_r, n_pol, n_az, nodes, [WALL, FARFIELD, AXIS, AXIS, PERIODIC, PERIODIC], wall_u, wall_T,
+                v, v.copy(), v.copy(), w, w.copy(), w.copy(), SHAKHOV, 0.81, Kn,
+                W0=_uniform_state(nc, u=(U, 0.0, 0.0)), name=f"capsule{n_r}x{n_pol}x{n_az}_Ma{Ma:g}")
+    if rykov:
+        p = as_rykov(p)
+    return with_clustered_velocities(p, nv, vmax)
