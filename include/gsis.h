@@ -46,6 +46,15 @@ enum gsis_bc_type { GSIS_BC_WALL = 1, GSIS_BC_PERIODIC = 2, GSIS_BC_FARFIELD = 3
 enum gsis_model { GSIS_SHAKHOV = 0, GSIS_RYKOV = 1 };
 enum gsis_precision { GSIS_F64 = 0, GSIS_F32 = 1, GSIS_BF16 = 2 };
 enum gsis_mode { GSIS_MODE_GSIS = 0, GSIS_MODE_DVM = 1 };
+/* Wall flux of the synthetic solve (Section 3.3).  Both enter as increments on the wall flux the
+   kinetic step produced (their values at W^{n+1/2} cancel), so the converged state is the
+   kinetic one either way; they differ in how the wall responds to the inner steps. */
+enum gsis_wall_flux {
+  GSIS_WALL_EQ = 0,   /* the half-range flux of the wall cell's local Maxwellian */
+  GSIS_WALL_G13 = 1   /* that of its Grad-13 VDF (Eq. G13_VDF): the cell's rho, u, T of the inner
+                         step with the stress and heat fluxes of the kinetic step (Eq.
+                         GSIS-DVM-flux) */
+};
 
 /* Structured hexahedral block (spatial finite-volume cells of Section 3.2).
  * nodes: (ni+1)(nj+1)(nk+1) x 3 doubles (host), node (I,J,K) at index I + (ni+1)(J + (nj+1)K).
@@ -191,6 +200,7 @@ typedef struct {
                            kinetic presteps; f then starts as the Maxwellian of their result
                            (the Euler preconditioning of Algorithm 1 for strong shocks).  Default
                            0; general blocks only (GSIS_E_UNSUPPORTED on rectilinear ones). */
+  int wall_flux;        /* GSIS_WALL_EQ (default) or GSIS_WALL_G13 */
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;

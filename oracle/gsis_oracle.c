@@ -914,6 +914,124 @@ static void wall_eq_flux(const orc_solver *s, int side, const double *pr, const 
   F[5] = rin + rout;
 }
 
+/* Polynomials in one variable of degree <= 6 (coefficients of x^0 .. x^6). */
+typedef struct { double c[7]; } poly6;
+
+static poly6 poly_of(int n, const double *c) {
+  poly6 p;
+  for (int k = 0; k < 7; ++k) p.c[k] = k < n ? c[k] : 0.0;
+  return p;
+}
+
+static poly6 poly_mul(poly6 a, poly6 b) {
+  poly6 r = poly_of(0, NULL);
+  for (int i = 0; i < 7; ++i)
+    for (int j = 0; i + j < 7; ++j) r.c[i + j] += a.c[i] * b.c[j];
+  return r;
+}
+
+static poly6 poly_add(poly6 a, double s, poly6 b) { /* a + s b */
+  for (int k = 0; k < 7; ++k) a.c[k] += s * b.c[k];
+  return a;
+}
+
+static double poly_dot(poly6 a, const double *H) {
+  double r = 0.0;
+  for (int k = 0; k < 7; ++k) r += a.c[k] * H[k];
+  return r;
+}
+
+/* Wall flux of the Grad-13 reconstruction of Eq. G13_VDF.  In the units of this code (velocity
+   in sqrt(2 R T0), p = rho T / 2, sigma = int c c f - p I, q_t = int c^2 c f / 2, q_r = int c f1)
+   the 13-moment VDF that reproduces rho, u, T_t, sigma and q_t is
+     f0 = M [1 + A:cc + (B.c)(c^2/T - 5/2)],  A = 2 sigma / (rho T^2),  B = 8 q_t / (5 rho T^2),
+   M = rho (pi T)^(-3/2) exp(-c^2/T), and the rotational VDF with (d_r/4) rho T_r and q_r is
+     f1 = (d_r T_r / 4) f0 + 2 M (q_r.c) / (rho T).
+   The half moving into the wall (xi.n > 0) leaves with this VDF; the wall re-emits
+   rho_w M(u_w, T_w) with zero net mass flux.  With c = x n + c_t, the tangential Gaussian
+   moments are taken in closed form, which leaves per flux a polynomial in x against
+   H_k = int_{x > -u_n} x^k g(x) dx, g the one-dimensional Maxwellian of variance T/2:
+     H_0 = erfc(-u_n / sqrt T) / 2,  H_k = (k-1) (T/2) H_{k-2} + (T/2) (-u_n)^(k-1) g(-u_n).
+   The tangential averages of the bracket Q = f0 / M:
+     <Q> = 1 - A_nn T/2 + A_nn x^2 + B_n x (x^2/T - 3/2),
+     <c_t Q> = T x A_nt + B_t (x^2/2 - T/4),
+     <|c_t|^2 Q> = T - A_nn T^2 + A_nn T x^2 + B_n x (x^2 - T/2),
+   A_nn = n.A.n, A_nt and B_t the tangential parts of A n and B. */
+static void wall_g13_flux(const orc_solver *s, int patch, const double *pr, const double *m18, const double *n,
+                          double *F) {
+  const double rho = pr[0], T = pr[4], Tr = pr[5], Tw = s->wall_T[patch];
+  const double *u = pr + 1, *uw = s->wall_u[patch];
+  const double sig[3][3] = {{m18[6], m18[9], m18[10]}, {m18[9], m18[7], m18[11]}, {m18[10], m18[11], m18[8]}};
+  const double *qt = m18 + 12, *qr = m18 + 15;
+  double un = dot3(u, n), sn[3];
+  for (int a = 0; a < 3; ++a) sn[a] = sig[a][0] * n[0] + sig[a][1] * n[1] + sig[a][2] * n[2];
+  const double kA = 2.0 / (rho * T * T), kB = 8.0 / (5.0 * rho * T * T);
+  const double snn = dot3(sn, n), qn = dot3(qt, n);
+  const double Ann = kA * snn, Bn = kB * qn;
+  double Ant[3], Bt[3], ut[3];
+  for (int a = 0; a < 3; ++a) {
+    Ant[a] = kA * (sn[a] - snn * n[a]);
+    Bt[a] = kB * (qt[a] - qn * n[a]);
+    ut[a] = u[a] - un * n[a];
+  }
+  const double cQ0[4] = {1.0 - 0.5 * Ann * T, -1.5 * Bn, Ann, Bn / T};
+  const double cQ2[4] = {T - Ann * T * T, -0.5 * Bn * T, Ann * T, Bn};
+  const double cL[2] = {un, 1.0};
+  poly6 Q0 = poly_of(4, cQ0), Q2 = poly_of(4, cQ2), L = poly_of(2, cL), Qt[3];
+  for (int a = 0; a < 3; ++a) {
+    const double c[3] = {-0.25 * Bt[a] * T, T * Ant[a], 0.5 * Bt[a]};
+    Qt[a] = poly_of(3, c);
+  }
+  const poly6 mass = poly_mul(L, Q0), normal = poly_mul(L, mass);
+  /* the energy bracket (|u|^2/2 + u_n x + x^2/2) <Q> + u_t.<c_t Q> + <|c_t|^2 Q>/2 */
+  const double ce[3] = {0.5 * dot3(u, u), un, 0.5};
+  poly6 eb = poly_add(poly_mul(poly_of(3, ce), Q0), 0.5, Q2);
+  for (int a = 0; a < 3; ++a) eb = poly_add(eb, ut[a], Qt[a]);
+  const poly6 energy = poly_mul(L, eb);
+  poly6 rot = poly_of(0, NULL);
+  if (s->nW == 6) {
+    const double cx[2] = {0.0, 2.0 * dot3(qr, n) / (rho * T)};
+    rot = poly_add(poly_mul(poly_of(2, cx), L), s->g.d_r * Tr / 4.0, mass);
+  }
+  /* half-range moments of x */
+  const double sr = un / sqrt(T), g0 = exp(-sr * sr) / sqrt(PI * T);
+  double H[7];
+  H[0] = 0.5 * erfc(-sr);
+  H[1] = 0.5 * T * g0;
+  for (int k = 2; k < 7; ++k) H[k] = (k - 1) * 0.5 * T * H[k - 2] + 0.5 * T * pow(-un, k - 1) * g0;
+  const double min = rho * poly_dot(mass, H), rin = rho * poly_dot(rot, H);
+  /* the wall's half (as for the Maxwellian flux) */
+  const double K1 = -sqrt(Tw) / (2.0 * SQRT_PI), K2 = Tw / 4.0, K3 = Tw * K1;
+  const double rw = -min / K1;
+  double uwt[3];
+  for (int a = 0; a < 3; ++a) uwt[a] = uw[a] - dot3(uw, n) * n[a];
+  F[0] = min + rw * K1;
+  for (int a = 0; a < 3; ++a)
+    F[1 + a] = rho * (n[a] * poly_dot(normal, H) + ut[a] * poly_dot(mass, H) + poly_dot(poly_mul(L, Qt[a]), H)) +
+               n[a] * rw * K2 + rw * K1 * uwt[a];
+  const double rout = s->nW == 6 ? s->g.d_r * Tw / 4.0 * rw * K1 : 0.0;
+  F[4] = rho * poly_dot(energy, H) + rin + 0.5 * rw * (K3 + K1 * (dot3(uwt, uwt) + Tw)) + rout;
+  F[5] = rin + rout;
+}
+
+/* the wall flux model of the synthetic solve (orc_opts.wall_flux) */
+static void wall_model_flux(const orc_solver *s, int patch, const double *pr, const double *m18, const double *n,
+                            double *F) {
+  if (s->o.wall_flux == ORC_WALL_G13)
+    wall_g13_flux(s, patch, pr, m18, n, F);
+  else
+    wall_eq_flux(s, patch, pr, n, F);
+}
+
+void orc_wall_flux(const orc_solver *s, int mode, int patch, const double *pr, const double *m18, const double *n,
+                   double *F) {
+  for (int k = 0; k < 6; ++k) F[k] = 0.0;
+  if (mode == ORC_WALL_G13)
+    wall_g13_flux(s, patch, pr, m18, n, F);
+  else
+    wall_eq_flux(s, patch, pr, n, F);
+}
+
 typedef struct {
   double *pr, *gW, *phW, *gP, *R, *dt, *D, *dW, *mu;
 } macro_work;
@@ -965,7 +1083,7 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
     const double *S = s->S + 18 * i + 3 * side;
     double A = sqrt(dot3(S, S)), n[3] = {S[0] / A, S[1] / A, S[2] / A}, pr[6];
     prim_of(s, W + 6 * i, pr);
-    wall_eq_flux(s, patch_of(s, i, side), pr, n, feq0 + 6 * wf);
+    wall_model_flux(s, patch_of(s, i, side), pr, s->Mh + 18 * i, n, feq0 + 6 * wf);
   }
   for (int step = 0; step < max_steps; ++step) {
     for (int i = 0; i < nc; ++i) {
@@ -994,9 +1112,9 @@ static int macro_solve(orc_solver *s, double *W, const double *fkin, int euler, 
             double p = 0.5 * m.pr[6 * i] * m.pr[6 * i + 4];
             for (int a = 0; a < 3; ++a) m.R[6 * i + 1 + a] -= p * n[a] * A;
           } else {
-            /* frozen kinetic wall flux plus the increment of the equilibrium wall flux */
+            /* frozen kinetic wall flux plus the increment of the model wall flux */
             double feq[6];
-            wall_eq_flux(s, patch_of(s, i, side), m.pr + 6 * i, n, feq);
+            wall_model_flux(s, patch_of(s, i, side), m.pr + 6 * i, s->Mh + 18 * i, n, feq);
             for (int k = 0; k < nW; ++k) m.R[6 * i + k] -= fkin[36 * i + 6 * side + k] + (feq[k] - feq0[6 * wf + k]) * A;
           }
           continue;

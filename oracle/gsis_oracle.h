@@ -67,7 +67,13 @@ typedef struct {
   double macro_cfl, macro_tol;
   double kin_inv_dt, venkat_K;
   int nthreads;         /* OpenMP threads over velocity (results do not depend on it) */
+  int wall_flux;        /* wall flux of the synthetic solve, both as increments on the frozen
+                           kinetic wall flux: ORC_WALL_EQ (0) the half-range flux of the local
+                           Maxwellian, ORC_WALL_G13 (1) that of the Grad-13 reconstruction of
+                           Eq. G13_VDF (Section 3.3) */
 } orc_opts;
+
+enum { ORC_WALL_EQ = 0, ORC_WALL_G13 = 1 };
 
 typedef struct orc_solver orc_solver;
 
@@ -91,6 +97,14 @@ int orc_presteps(orc_solver *s, int n);
 /* Euler preconditioning: n inner steps of the inviscid synthetic solve (slip walls, far field
    against the free stream) from the current state; f restarts as the Maxwellian of the result. */
 int orc_euler_presteps(orc_solver *s, int n);
+
+/* The outward wall flux (per unit area; rho, momentum, energy, rotational energy) of a cell
+   state pr = (rho, u, Tt, Tr) meeting the diffuse wall of boundary patch `patch` along the unit
+   normal n: mode ORC_WALL_EQ uses the local Maxwellian, ORC_WALL_G13 the Grad-13 VDF built
+   with the stress, translational and rotational heat fluxes of m18 (the layout of
+   orc_get_half_moments). */
+void orc_wall_flux(const orc_solver *s, int mode, int patch, const double *pr, const double *m18, const double *n,
+                   double *F);
 
 /* Parts of one outer step, for timing and unit tests. */
 int orc_wall_prepass(orc_solver *s);                       /* rho_w from the current f */

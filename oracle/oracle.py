@@ -33,7 +33,8 @@ class OrcGas(C.Structure):
 class OrcOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("schedule", C.c_int), ("n_sweeps", C.c_int), ("macro_steps", C.c_int),
                 ("macro_sweeps", C.c_int), ("macro_cfl", C.c_double), ("macro_tol", C.c_double),
-                ("kin_inv_dt", C.c_double), ("venkat_K", C.c_double), ("nthreads", C.c_int)]
+                ("kin_inv_dt", C.c_double), ("venkat_K", C.c_double), ("nthreads", C.c_int),
+                ("wall_flux", C.c_int)]
 
 
 def lib():
@@ -68,6 +69,7 @@ def lib():
         L.orc_cell_limiter.argtypes = [C.c_void_p, C.c_int, D]
         L.orc_cell_limiter.restype = C.c_double
         L.orc_get_face_flux.argtypes = [C.c_void_p, D]
+        L.orc_wall_flux.argtypes = [C.c_void_p, C.c_int, C.c_int, D, D, D, D]
         L.orc_tau.argtypes = [C.POINTER(OrcGas), C.c_double, C.c_double]
         L.orc_tau.restype = C.c_double
         L.orc_conductivity.argtypes = [C.POINTER(OrcGas), C.c_double, D, D]
@@ -90,7 +92,7 @@ def gas_struct(p) -> OrcGas:
 
 
 DEFAULTS = dict(mode=0, schedule=0, n_sweeps=1, macro_steps=300, macro_sweeps=4, macro_cfl=100.0,
-                macro_tol=1e-10, kin_inv_dt=0.0, venkat_K=1.0, nthreads=0)
+                macro_tol=1e-10, kin_inv_dt=0.0, venkat_K=1.0, nthreads=0, wall_flux=0)
 
 
 class Oracle:
@@ -239,6 +241,15 @@ class Oracle:
         lib().orc_get_wall(self.h, cell.ctypes.data_as(C.POINTER(C.c_int)), side.ctypes.data_as(C.POINTER(C.c_int)),
                            _p(rw), _p(fl))
         return cell, side, rw, fl
+
+    def wall_flux(self, mode, patch, pr, m18, n):
+        """orc_wall_flux: the outward wall flux (rho, momentum, energy, rotational energy) of the
+        state pr = (rho, u, Tt, Tr) on patch `patch` along the unit normal n; mode 0 the local
+        Maxwellian, 1 the Grad-13 VDF with the stress and heat fluxes of m18."""
+        out = np.zeros(6)
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (pr, m18, n)]
+        lib().orc_wall_flux(self.h, int(mode), int(patch), _p(a[0]), _p(a[1]), _p(a[2]), _p(out))
+        return out
 
     def face_flux(self):
         out = np.empty((self.nc, 6, 6))

@@ -27,7 +27,8 @@ def nvcc() -> str:
 
 def _deps_mtime() -> float:
     paths = [os.path.join(CSRC, s) for s in SOURCES]
-    paths += [os.path.join(CSRC, "gsis_internal.h"), os.path.join(os.path.dirname(HERE), "include", "gsis.h")]
+    paths += [os.path.join(CSRC, "gsis_internal.h"), os.path.join(CSRC, "wall_flux.cuh"),
+              os.path.join(os.path.dirname(HERE), "include", "gsis.h")]
     return max(os.path.getmtime(p) for p in paths)
 
 

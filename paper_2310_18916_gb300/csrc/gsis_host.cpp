@@ -274,6 +274,7 @@ struct gsis_solver {
     m.gsw = d_gsw64;
     m.euler = 0;
     m.mh_stride = 18;
+    m.wall_g13 = opt.wall_flux == GSIS_WALL_G13;
     m.mu0 = Kn / std::sqrt(3.14159265358979323846);
     m.omega = omega;
     m.cfl = opt.macro_cfl;
@@ -484,6 +485,7 @@ struct gsis_solver {
       m.den_floor = 1e-24 * vsum;
       m.closed = closed;
       m.Mh = d_Mh;
+      m.wall_g13 = opt.wall_flux == GSIS_WALL_G13;
       m.K = d_K;
       m.wall_cell = d_wall_cell;
       m.wall_side = d_wall_side;
@@ -677,6 +679,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   if (o->mode != GSIS_MODE_GSIS && o->mode != GSIS_MODE_DVM) { why = "bad mode"; return GSIS_E_INVALID; }
   if (o->kinetic_ring != 0 && o->kinetic_ring != 1) { why = "kinetic_ring must be 0 or 1"; return GSIS_E_INVALID; }
   if (o->euler_presteps < 0) { why = "euler_presteps must be >= 0"; return GSIS_E_INVALID; }
+  if (o->wall_flux != GSIS_WALL_EQ && o->wall_flux != GSIS_WALL_G13) { why = "bad wall_flux"; return GSIS_E_INVALID; }
   if (o->shard_count > 1 && (o->shard_index < 0 || o->shard_index >= o->shard_count || !o->allreduce)) {
     why = "velocity sharding needs 0 <= shard_index < shard_count and an allreduce callback";
     return GSIS_E_INVALID;
@@ -1808,6 +1811,7 @@ static int init_state(gsis_solver *s) {
 static int euler_presteps(gsis_solver *s) {
   MacroGenArgs m = s->macro_general_args();
   m.euler = 1;
+  m.wall_g13 = 0;
   m.steps = s->opt.euler_presteps;
   m.Mh = s->d_Wstate;
   m.mh_stride = 6;

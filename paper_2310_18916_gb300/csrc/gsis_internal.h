@@ -285,6 +285,7 @@ struct MacroArgs {
   double den_floor;        // 1e-24 x total volume: fields with sum W_k^2 V below it count as zero
   int closed;
   const double *Mh;        // [cell][18] initial state W^{n+1/2}
+  int wall_g13;            // wall flux increments of the Grad-13 VDF (else of the local Maxwellian)
   const double *K;         // [cell][6] sum over the cell's faces of the outward kinetic flux (area-integrated)
   const int *wall_cell, *wall_side;
   int nwall;
@@ -310,6 +311,7 @@ struct MacroGenArgs {
   const int *gso, *gsi;             // least-squares stencil (see KinArgs), else nullptr
   const double *gsw;
   int euler;                   // 1: the inviscid presteps (slip walls, no correction, K unused)
+  int wall_g13;                // wall flux of the Grad-13 VDF (needs mh_stride 18: the moments)
   int mh_stride;               // doubles per cell of Mh (18: the moments; 6: a primitive state)
   double mu0, omega, cfl, tol, d_r, Z_r, A[4], mass_ref;
   double vsum;                 // total volume (fields with sum W_k^2 V <= 1e-24 vsum count as zero)

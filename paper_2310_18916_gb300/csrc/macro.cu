@@ -29,6 +29,7 @@
 #include <cmath>
 
 #include "gsis_internal.h"
+#include "wall_flux.cuh"
 
 namespace gsis {
 
@@ -481,7 +482,8 @@ __device__ void face_item(const MacroArgs &m, const int *cs, int c, int a) {
   for (int k = 0; k < 6; ++k) Ff[k] = F[k];
 }
 
-// C, one wall item: equilibrium wall flux (area-integrated) of wall face wf
+// C, one wall item: the model wall flux (area-integrated) of wall face wf: local equilibrium or
+// the Grad-13 VDF with the kinetic step's stress and heat fluxes
 template <int NW>
 __device__ void wall_item(const MacroArgs &m, int wf) {
   const int c = m.wall_cell[wf], side = m.wall_side[wf], a = side / 2;
@@ -491,7 +493,15 @@ __device__ void wall_item(const MacroArgs &m, int wf) {
   double p[6], feq[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) p[k] = m.pr[(size_t)c * 6 + k];
-  equilibrium_wall_flux<NW>(m, p, a, (side & 1) ? 1.0 : -1.0, m.wall_uT + 4 * side, feq);
+  const double sg = (side & 1) ? 1.0 : -1.0;
+  if (m.wall_g13) {
+    const double n[3] = {a == 0 ? sg : 0.0, a == 1 ? sg : 0.0, a == 2 ? sg : 0.0};
+    const double *M = m.Mh + (size_t)c * 18;
+    grad13_wall_flux(NW, m.d_r, p[0], p + 1, p[4], p[5], n, M + 6, M + 12, M + 15, m.wall_uT + 4 * side,
+                     m.wall_uT[4 * side + 3], feq);
+  } else {
+    equilibrium_wall_flux<NW>(m, p, a, sg, m.wall_uT + 4 * side, feq);
+  }
 #pragma unroll
   for (int k = 0; k < 6; ++k) m.wfl[(size_t)wf * 6 + k] = k < NW ? feq[k] * A : 0.0;
 }

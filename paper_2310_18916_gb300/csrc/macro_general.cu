@@ -24,6 +24,7 @@
 #include <cmath>
 
 #include "gsis_internal.h"
+#include "wall_flux.cuh"
 
 namespace gsis {
 
@@ -320,6 +321,10 @@ __global__ void resid_kernel(MacroGenArgs m, int step) {
         const double pt = 0.5 * pc[0] * pc[4];
         for (int k = 0; k < 6; ++k) F[k] = 0.0;
         for (int a = 0; a < 3; ++a) F[1 + a] = pt * n[a];
+      } else if (nb == NB_WALL && m.wall_g13) {
+        const int pt = patch_of(m.gpat, c, s);
+        const double *pc = m.pr + 6 * (size_t)c, *M = m.Mh + 18 * (size_t)c, *uT = m.wall_uT + 4 * pt;
+        grad13_wall_flux(m.nW, m.d_r, pc[0], pc + 1, pc[4], pc[5], n, M + 6, M + 12, M + 15, uT, uT[3], F);
       } else if (nb == NB_WALL) {
         wall_eq_flux(m, patch_of(m.gpat, c, s), m.pr + 6 * (size_t)c, n, F);
       } else if (nb >= 0) {
