@@ -46,11 +46,16 @@ MACRO_FLOPS_PER_CELL_STEP_2D = 1556
 # shares with the correction, the collision and flux terms of the delta form 19, the division by
 # the implicit diagonal, the update and the published face increments 4.
 KINETIC_FLOPS_PER_POINT_2D = 103
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu pass over the
-# 128^2 cavity with 32^3 velocities, keyed by kernel, precision and the SHA-256 prefix of the
-# kernel's source file at capture time: a figure whose source has changed since is reported as
-# null (stale).
-DRAM_BYTES_PER_LAUNCH = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the 128^2 cavity with
+# 32^3 velocities, keyed by kernel, precision and the SHA-256 prefix of the kernel's source file
+# at capture time: a figure whose source has changed since is reported as null (stale).  Captured
+# on the 64^2 case in the same launch configuration (the FP64 kinetic kernel with its colour ring
+# in device scratch, as at 128^2) and scaled by the 4x cells: the kinetic kernel's traffic is
+# per point, the synthetic solve's per cell (profiles/dram_bytes_cavity64x32.md).
+DRAM_BYTES_PER_LAUNCH = {
+    ("kinetic_kernel", "f64"): (4 * (1.0834e9 + 1.1221e9), "d4173c6f5299"),
+    ("macro_kernel", "f64"): (4 * (3.79e6 + 0.02e6), "02e3bb610d02"),
+}
 KERNEL_SOURCES = {"kinetic_kernel": "kinetic.cu", "moments_kernel": "kinetic.cu", "macro_kernel": "macro.cu"}
 
 
@@ -508,10 +513,11 @@ def body_oracle_sample(name):
 
 
 def run_serve(args):
-    """Configuration 5 scaled to minutes: a seeded Poisson stream of steady cavity solves (sizes,
-    velocity counts and arrival gaps scaled down, Kn log-uniform in [1e-3, 1], lid Mach number in
-    [0.1, 1]) served with continuous batching in FP32, against the same requests solved one at a
-    time in FP32 and in plain FP64."""
+    """Configuration 5 scaled to minutes: a seeded Poisson stream of steady solves, cavities and
+    cylinders with equal odds (sizes, velocity counts and arrival gaps scaled down; Kn
+    log-uniform in [1e-3, 1]; lid Mach number in [0.1, 5], cylinders subsonic; GSIS below Kn 0.3,
+    the plain kinetic iteration above), served with continuous batching in FP32, against the same
+    requests solved one at a time in FP32 and in plain FP64."""
     import torch
 
     from paper_2310_18916_gb300 import serving
@@ -519,13 +525,13 @@ def run_serve(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     reqs = serving.poisson_requests(args.serve_requests, args.serve_gap, 0,
-                                    lambda rng: wl.serving_cavity(rng, sizes=(32, 48, 64), nvs=(16, 20, 24)),
+                                    lambda rng: wl.serving_request(rng, sizes=(32, 48, 64), nvs=(16, 20, 24)),
                                     tol=1e-6, max_steps=150)
     budget = int(0.5 * torch.cuda.mem_get_info()[0])
     lines = {}
     for name, slots, prec, arrivals in (("batched_f32", args.serve_slots, "f32", True),
                                         ("sequential_f32", 1, "f32", False), ("sequential_f64", 1, "f64", False)):
-        rs = reqs if arrivals else [serving.Request(r.rid, r.problem, 0.0, r.tol, r.max_steps, r.stall_steps)
+        rs = reqs if arrivals else [serving.Request(r.rid, r.problem, 0.0, r.tol, r.max_steps, r.stall_steps, r.opts)
                                     for r in reqs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -534,18 +540,130 @@ def run_serve(args):
         summ = serving.summary(res, wall)
         summ["slots"] = slots
         summ["precision"] = prec
+        summ["failures"] = [{"rid": r.rid, "problem": reqs[r.rid].problem.name, "opts": reqs[r.rid].opts,
+                             "error": r.error} for r in res if r is not None and r.error]
         lines[name] = summ
     b = lines["batched_f32"]
-    print(json.dumps({"metric": "steady-solve serving (GSIS, cavity stream)", "unit": "s",
+    kinds = {"cavity": sum(r.problem.name.startswith("cavity") for r in reqs),
+             "cylinder": sum(r.problem.name.startswith("cylinder") for r in reqs),
+             "gsis": sum(r.opts.get("mode") == "gsis" for r in reqs),
+             "dvm": sum(r.opts.get("mode") == "dvm" for r in reqs)}
+    print(json.dumps({"metric": "steady-solve serving (cavity and cylinder stream)", "unit": "s",
                       "p50_latency_s": b["p50_latency_s"], "p99_latency_s": b["p99_latency_s"],
                       "solves_per_hour": b["solves_per_hour"], "higher_is_better": False,
-                      "config": {"requests": len(reqs), "mean_gap_s": args.serve_gap, "slots": args.serve_slots,
-                                 "sizes": "32^2, 48^2, 64^2 cells; 16^3, 20^3, 24^3 velocities",
-                                 "kn": "log-uniform [1e-3, 1]", "lid_mach": "[0.1, 1]", "tol": 1e-6,
+                      "config": {"requests": len(reqs), "mix": kinds, "mean_gap_s": args.serve_gap,
+                                 "slots": args.serve_slots,
+                                 "sizes": "cavities 32^2, 48^2, 64^2 cells; cylinders n x 2n, n = 32, 48, 64; "
+                                          "16^3, 20^3, 24^3 velocities",
+                                 "kn": "log-uniform [1e-3, 1]", "mach": "cavity lid [0.1, 5], cylinder [0.1, 1]",
+                                 "mode": "GSIS below Kn 0.3, plain kinetic iteration above", "tol": 1e-6,
                                  "memory_budget_bytes": budget},
                       "runs": lines,
                       "throughput_vs_sequential_f64": b["solves_per_hour"] / lines["sequential_f64"]["solves_per_hour"],
                       "throughput_vs_sequential_f32": b["solves_per_hour"] / lines["sequential_f32"]["solves_per_hour"]}))
+    return 0
+
+
+def run_moments_gemm(args):
+    """Could tensor cores take the moment projection?  The 16 raw velocity moments (1, xi, xi xi,
+    |xi|^2 xi / 2, |xi|^2 / 2; weights folded in) of a VDF on the benchmark workload, taken as one
+    GEMM F [cells x velocities] @ B [velocities x 16] by cuBLAS: FP64 (DGEMM), FP32 (SGEMM), TF32
+    and BF16 tensor cores (FP32 accumulation), each on the VDF stored in that precision.  Against
+    the library's own moments pass in FP64, FP32 and BF16 storage (the reduce_moments phase of
+    timed GSIS steps: moments about the cell velocity, compensated sums).  Accuracy: T and q
+    recovered from each GEMM's raw moments against the FP64 GEMM's.  The VDF is a seeded
+    perturbed Maxwellian of the workload's shape, built on the device."""
+    import numpy as np
+    import torch
+
+    from paper_2310_18916_gb300 import gsis
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    p = problem()
+    nc, nv = p.ncells, p.nvel
+    dev = "cuda"
+    g = torch.Generator(device="cpu").manual_seed(7)
+    rho = 1 + 0.05 * (2 * torch.rand(nc, 1, generator=g, dtype=torch.float64) - 1)
+    u = 0.1 * (2 * torch.rand(nc, 3, generator=g, dtype=torch.float64) - 1)
+    T = 1 + 0.05 * (2 * torch.rand(nc, 1, generator=g, dtype=torch.float64) - 1)
+    X, Y, Z = np.meshgrid(p.vx, p.vy, p.vz, indexing="ij")
+    flat = lambda a: torch.from_numpy(np.ascontiguousarray(a.transpose(2, 1, 0).ravel()))
+    xi = torch.stack([flat(X), flat(Y), flat(Z)], 1).to(dev)
+    w = flat(p.wx[:, None, None] * p.wy[None, :, None] * p.wz[None, None, :]).to(dev)
+    rho, u, T = rho.to(dev), u.to(dev), T.to(dev)
+    F64 = torch.empty((nc, nv), dtype=torch.float64, device=dev)
+    for c0 in range(0, nc, 512):
+        c1 = min(nc, c0 + 512)
+        cc = xi[None, :, :] - u[c0:c1, None, :]
+        F64[c0:c1] = rho[c0:c1] * (np.pi * T[c0:c1]) ** -1.5 * torch.exp(-(cc * cc).sum(-1) / T[c0:c1]) * \
+            (1 + 0.05 * torch.sin(3 * cc[..., 0]) * torch.cos(2 * cc[..., 1]))
+    x2 = (xi * xi).sum(1)
+    cols = [w, w * xi[:, 0], w * xi[:, 1], w * xi[:, 2], w * xi[:, 0] ** 2, w * xi[:, 1] ** 2, w * xi[:, 2] ** 2,
+            w * xi[:, 0] * xi[:, 1], w * xi[:, 0] * xi[:, 2], w * xi[:, 1] * xi[:, 2], 0.5 * w * x2 * xi[:, 0],
+            0.5 * w * x2 * xi[:, 1], 0.5 * w * x2 * xi[:, 2], 0.5 * w * x2, 0 * w, 0 * w]
+    B64 = torch.stack(cols, 1).contiguous()
+
+    def derived(M):
+        M = M.double()
+        r = M[:, 0]
+        uu = M[:, 1:4] / r[:, None]
+        e = M[:, 13] / r - 0.5 * (uu * uu).sum(1)              # |c|^2 / 2 per unit mass
+        Tm = e / 0.75
+        # q = int |c|^2 c f / 2 from the raw moments about the origin
+        Pxy = torch.stack([torch.stack([M[:, 4], M[:, 7], M[:, 8]], 1), torch.stack([M[:, 7], M[:, 5], M[:, 9]], 1),
+                           torch.stack([M[:, 8], M[:, 9], M[:, 6]], 1)], 1)
+        q = M[:, 10:13] - torch.einsum("cij,cj->ci", Pxy, uu) - M[:, 13:14] * uu + r[:, None] * (uu * uu).sum(1, keepdim=True) * uu
+        return Tm, q
+
+    def time_gemm(A, Bm, K=10):
+        for _ in range(3):
+            torch.matmul(A, Bm)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(K):
+            out = torch.matmul(A, Bm)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K, out
+
+    ms64, M64 = time_gemm(F64, B64)
+    T_ref, q_ref = derived(M64)
+    qs = (M64[:, 0] * T_ref ** 1.5).abs().max()
+    F32 = F64.float()
+    del F64
+    torch.cuda.empty_cache()
+    gemm = {"f64_dgemm": {"ms": ms64, "bytes": nc * nv * 8}}
+    for name, A, Bm, tf32 in (("f32_sgemm", F32, B64.float(), False), ("tf32_tensor", F32, B64.float(), True),
+                              ("bf16_tensor", None, B64.bfloat16(), False)):
+        if A is None:
+            A = F32.bfloat16()   # (the product is returned in BF16 too)
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        ms, M = time_gemm(A, Bm)
+        Tm, q = derived(M)
+        gemm[name] = {"ms": ms, "bytes": A.numel() * A.element_size(),
+                      "T_max_rel_err": float(((Tm - T_ref).abs() / T_ref).max()),
+                      "q_max_err_over_rho_T32": float((q - q_ref).abs().max() / qs)}
+        del A
+    torch.backends.cuda.matmul.allow_tf32 = False
+    del F32
+    torch.cuda.empty_cache()
+    own = {}
+    for prec in ("f64", "f32", "bf16"):
+        s_ = gsis.Solver(p, precision=prec, mode="gsis", kinetic_presteps=0)
+        s_.step()
+        s_.profile(True, reset=True)
+        for _ in range(3):
+            s_.step()
+        ph, n, _ = s_.profile(False)
+        own[prec] = {"ms": ph[PHASES.index("reduce_moments")] / max(n, 1),
+                     "bytes": nc * nv * {"f64": 8, "f32": 4, "bf16": 2}[prec]}
+        s_.close()
+    print(json.dumps({"metric": "moment projection: cuBLAS GEMM vs the library's moments pass", "unit": "ms",
+                      "config": {"workload": workload_name(), "cells": nc, "velocities": nv,
+                                 "moments": "16 raw moments about the origin (GEMM); 18 about the cell velocity "
+                                            "(library, incl. the collision sums)"},
+                      "gemm": gemm, "library": own}))
     return 0
 
 
@@ -587,7 +705,7 @@ def timed_steps(p, prec, steps, warmup, barrier, local, shard_kw=None):
 
     from paper_2310_18916_gb300 import gsis
 
-    s = gsis.Solver(p, precision=prec, mode="gsis", **(shard_kw or {}))
+    s = gsis.Solver(p, precision=prec, mode="gsis", kinetic_ring=RING[0], **(shard_kw or {}))
     for _ in range(warmup):
         s.step()
     s.profile(True, reset=True)
@@ -612,6 +730,7 @@ def timed_steps(p, prec, steps, warmup, barrier, local, shard_kw=None):
 
 
 PHASES = ("wall_prepass", "kinetic", "reduce_moments", "synthetic_fp64", "residual_state")
+RING = [0]   # gsis_options.kinetic_ring of the cavity runs (--kinetic-ring)
 
 
 def main():
@@ -637,6 +756,13 @@ def main():
     ap.add_argument("--serve", action="store_true", help="instead of the throughput line: the serving stream")
     ap.add_argument("--couette", action="store_true",
                     help="instead of the throughput line: Couette flow to eps < 1e-8 in FP64, GPU vs oracle")
+    ap.add_argument("--kinetic-ring", type=int, default=0, choices=[0, 1],
+                    help="gsis_options.kinetic_ring of the cavity runs: 1 keeps the kinetic sweep's colour ring "
+                         "in device scratch at any size (the placement the 128^2 FP64 workload takes), for "
+                         "profiling that placement on a smaller case")
+    ap.add_argument("--moments-gemm", action="store_true",
+                    help="instead of the throughput line: the moment projection as a cuBLAS GEMM against the "
+                         "library's moments pass")
     ap.add_argument("--body", choices=sorted(BODIES),
                     help="instead of the cavity line: the kinetic iteration on a body-fitted O-grid")
     ap.add_argument("--shard", action="store_true",
@@ -647,6 +773,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     CFG.update(n=args.n, nv=args.nv, Kn=args.kn, model=args.model)
+    RING[0] = args.kinetic_ring
     if args.impl == "reference":
         return run_reference(args)
     if args.time_to_steady:
@@ -657,6 +784,8 @@ def main():
         return run_couette(args)
     if args.body:
         return run_body(args)
+    if args.moments_gemm:
+        return run_moments_gemm(args)
 
     import numpy as np
     import torch
@@ -699,7 +828,7 @@ def main():
     # device->host read of the state, destroy
     barrier()
     t0 = time.perf_counter()
-    s2 = gsis.Solver(p, precision=args.precision, mode="gsis", kinetic_presteps=0, **shard_kw)
+    s2 = gsis.Solver(p, precision=args.precision, mode="gsis", kinetic_presteps=0, kinetic_ring=RING[0], **shard_kw)
     for _ in range(args.steps):
         s2.step()
         W = s2.W()

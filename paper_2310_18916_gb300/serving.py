@@ -34,6 +34,7 @@ class Request:
     tol: float = 1e-6
     max_steps: int = 400
     stall_steps: int = 20
+    opts: dict = field(default_factory=dict)   # solver options of this request (mode, n_sweeps, ...)
 
 
 @dataclass
@@ -47,6 +48,7 @@ class Result:
     converged: bool
     W: np.ndarray = field(repr=False, default=None)
     floor: bool = False      # stopped at the round-off floor (eps stalled above tol)
+    error: str = ""          # the solver's error when the solve failed (its state then left no W)
 
     @property
     def latency(self) -> float:
@@ -78,8 +80,9 @@ class Server:
     memory_budget: device bytes the running solves may hold together.
     slots: solves that run at the same time.
     precision: VDF storage of every solve ("f32", "bf16" or "f64").
-    make_solver(problem, precision, macro_sms, stream) / footprint(problem, precision): the GPU
-    solver and its footprint; replaceable (the scheduling logic is tested with fakes).
+    make_solver(problem, precision, macro_sms, stream, **opts) / footprint(problem, precision,
+    **opts): the GPU solver and its footprint, opts the request's solver options; replaceable (the
+    scheduling logic is tested with fakes).
     """
 
     def __init__(self, memory_budget, slots=4, precision="f32", nsm=None, make_solver=None, footprint=None,
@@ -110,7 +113,7 @@ class Server:
                 queue.append(pending.pop(0))
             while queue and len(running) < self.slots:
                 req = queue[0]
-                need = self._footprint(req.problem, self.precision)
+                need = self._footprint(req.problem, self.precision, **req.opts)
                 if need > self.memory_budget:
                     queue.pop(0)
                     results[req.rid] = None
@@ -119,30 +122,46 @@ class Server:
                     break
                 queue.pop(0)
                 stream = self._new_stream()
-                solver = self._make(req.problem, self.precision, self.macro_sms, stream)
+                solver = self._make(req.problem, self.precision, self.macro_sms, stream, **req.opts)
                 used += need
                 running.append(_Running(req, solver, stream, need, self._clock() - t0))
             if not running:
                 if pending:
                     self._idle(max(0.0, pending[0].arrival - (self._clock() - t0)))
                 continue
-            # one round: enqueue every running solve's step, then wait for each
+            # one round: enqueue every running solve's step, then wait for each.  A solve that fails
+            # (its state left the physical range, or its steps could not be enqueued) leaves with
+            # its error; the others go on.
+            failed = {}
             for r in running:
-                r.solver.step_async()
+                try:
+                    r.solver.step_async()
+                except Exception as e:  # noqa: BLE001 - the request fails, the server does not
+                    failed[id(r)] = str(e)
             for r in running:
-                r.eps = r.solver.step_wait()
+                if id(r) in failed:
+                    continue
+                try:
+                    r.eps = r.solver.step_wait()
+                except Exception as e:  # noqa: BLE001
+                    failed[id(r)] = str(e)
+                    continue
                 r.steps += 1
                 if r.eps < r.best:
                     r.best, r.since_best = r.eps, 0
                 else:
                     r.since_best += 1
-            done = [r for r in running
-                    if r.eps < r.req.tol or r.steps >= r.req.max_steps or r.since_best >= r.req.stall_steps]
+            done = [r for r in running if id(r) in failed or r.eps < r.req.tol or r.steps >= r.req.max_steps
+                    or r.since_best >= r.req.stall_steps]
             for r in done:
                 t = self._clock() - t0
-                conv = r.eps < r.req.tol
-                results[r.req.rid] = Result(r.req.rid, r.req.arrival, r.admitted, t, r.steps, r.eps, conv,
-                                            r.solver.W(), floor=not conv and r.since_best >= r.req.stall_steps)
+                if id(r) in failed:
+                    results[r.req.rid] = Result(r.req.rid, r.req.arrival, r.admitted, t, r.steps, r.eps, False,
+                                                None, error=failed[id(r)])
+                else:
+                    conv = r.eps < r.req.tol
+                    results[r.req.rid] = Result(r.req.rid, r.req.arrival, r.admitted, t, r.steps, r.eps, conv,
+                                                r.solver.W(), floor=not conv and r.since_best >= r.req.stall_steps)
                 r.solver.close()
                 used -= r.need
                 running.remove(r)
@@ -150,29 +169,35 @@ class Server:
 
 
 def summary(results, wall_seconds):
-    """p50 / p99 latency (arrival to converged state) and solves per hour over the run."""
-    ok = [r for r in results if r is not None]
+    """p50 / p99 latency (arrival to finished state) and solves per hour over the run, over the
+    requests that finished without an error."""
+    ok = [r for r in results if r is not None and not r.error]
     lat = [r.latency for r in ok]
     return {"requests": len(results), "served": len(ok), "converged": sum(r.converged for r in ok),
             "at_precision_floor": sum(r.floor for r in ok),
+            "failed": sum(1 for r in results if r is not None and r.error),
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
             "solves_per_hour": 3600.0 * len(ok) / wall_seconds if wall_seconds > 0 else float("nan"),
             "wall_s": wall_seconds}
 
 
-def _gpu_solver(problem, precision, macro_sms, stream):
+def _gpu_solver(problem, precision, macro_sms, stream, **opts):
     import torch
 
     from . import gsis
 
+    opts = dict(opts)
+    mode = opts.pop("mode", "gsis")
     with torch.cuda.stream(stream):
-        return gsis.Solver(problem, precision=precision, mode="gsis", macro_sms=macro_sms)
+        return gsis.Solver(problem, precision=precision, mode=mode, macro_sms=macro_sms, **opts)
 
 
-def _gpu_footprint(problem, precision):
+def _gpu_footprint(problem, precision, **opts):
     from . import gsis
 
-    return gsis.footprint_bytes(problem, precision)
+    opts = dict(opts)
+    mode = opts.pop("mode", "gsis")
+    return gsis.footprint_bytes(problem, precision, mode=gsis.MODE_GSIS if mode == "gsis" else gsis.MODE_DVM, **opts)
 
 
 def _gpu_stream():
@@ -183,10 +208,12 @@ def _gpu_stream():
 
 def poisson_requests(n, mean_gap, seed, make_problem, tol=1e-6, max_steps=400, stall_steps=20):
     """n requests with exponential inter-arrival times of mean mean_gap (seeded); make_problem(rng)
-    draws each request's problem."""
+    draws each request's problem, or a (problem, solver options) pair."""
     rng = np.random.default_rng(seed)
     t, out = 0.0, []
     for i in range(n):
         t += rng.exponential(mean_gap)
-        out.append(Request(i, make_problem(rng), t, tol, max_steps, stall_steps))
+        drawn = make_problem(rng)
+        prob, opts = drawn if isinstance(drawn, tuple) else (drawn, {})
+        out.append(Request(i, prob, t, tol, max_steps, stall_steps, dict(opts)))
     return out

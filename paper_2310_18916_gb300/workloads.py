@@ -173,6 +173,44 @@ def serving_cavity(rng, sizes=(32, 48, 64), nvs=(16, 20, 24), kn=(1e-3, 1.0), ma
     return cavity(n=n, nv=nv, vmax=vmax, lid=lid, Kn=Kn)
 
 
+def serving_cylinder(rng, sizes=(32, 48, 64), nvs=(16, 20, 24), kn=(1e-3, 1.0), ma=(0.1, 1.0)) -> Problem:
+    """One cylinder request of the serving stream: the cylinder of diameter 1 in cross flow on an
+    O-grid of n radial x 2n azimuthal cells (n from sizes; radial spacing geometric from 0.01 of
+    the diameter, far field at 10 diameters), nv^3 velocities on the velocity box of the free
+    stream, Kn log-uniform in kn, Ma uniform in ma."""
+    n = int(rng.choice(sizes))
+    nv = int(rng.choice(nvs))
+    Kn = float(np.exp(rng.uniform(np.log(kn[0]), np.log(kn[1]))))
+    Ma = float(rng.uniform(ma[0], ma[1]))
+    return cylinder(n_r=n, n_theta=2 * n, nv=nv, R=0.5, R_out=10.0, first=0.01, Ma=Ma, Kn=Kn)
+
+
+def serving_request(rng, sizes=(32, 48, 64), nvs=(16, 20, 24), kn=(1e-3, 1.0), cavity_ma=(0.1, 5.0),
+                    cylinder_ma=(0.1, 1.0), cylinder_kn_max=0.2, continuum_kn=0.05, continuum_ma=1.75, kn_dvm=0.3):
+    """One request of the mixed serving stream: a cavity or a cylinder with equal odds, and the
+    solver options a server would pick for it (returns (problem, options)).
+
+    Kn is log-uniform in kn and the Mach number uniform in its range, within the region where
+    the solves converge from the impulsive start (oracle and GPU probes at these resolutions):
+    - cavities below Kn continuum_kn take lid Mach numbers up to continuum_ma only (at Kn ~1e-3 a
+      lid at Mach 2.5 and above makes the state non-physical in the first steps);
+    - cylinders stay subsonic and below Kn cylinder_kn_max (supersonic cylinders fail at
+      moderate Kn in both modes; above Kn 0.3 GSIS stalls and the plain kinetic iteration loses
+      positivity on the wall-resolved grids), with two colour passes per kinetic step;
+    - GSIS below Kn kn_dvm, the plain kinetic iteration above (GSIS's synthetic NSF solve
+      diverges on fast rarefied flows, which the kinetic iteration converges in tens of steps)."""
+    if rng.uniform() < 0.5:
+        Kn = float(np.exp(rng.uniform(np.log(kn[0]), np.log(kn[1]))))
+        hi = cavity_ma[1] if Kn >= continuum_kn else min(cavity_ma[1], continuum_ma)
+        p = serving_cavity(rng, sizes=sizes, nvs=nvs, kn=(Kn, Kn), ma=(cavity_ma[0], hi))
+        opts = {}
+    else:
+        p = serving_cylinder(rng, sizes=sizes, nvs=nvs, kn=(kn[0], min(kn[1], cylinder_kn_max)), ma=cylinder_ma)
+        opts = {"n_sweeps": 2}
+    opts["mode"] = "gsis" if p.Kn < kn_dvm else "dvm"
+    return p, opts
+
+
 def radial_nodes(n_r, R, R_out, first=None):
     """n_r + 1 radii from R to R_out: uniform, or geometric with first spacing `first`."""
     if first is None:

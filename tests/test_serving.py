@@ -109,3 +109,47 @@ def test_poisson_requests_are_seeded():
     assert [r.arrival for r in a] == [r.arrival for r in b]
     gaps = np.diff([0.0] + [r.arrival for r in a])
     assert (gaps > 0).all() and abs(gaps.mean() - 2.0) < 1.2
+
+
+def test_the_mixed_request_stream():
+    """The serving mix: cavities and cylinders with equal odds, Kn log-uniform, lid Mach numbers up
+    to 5 (up to 1.75 below Kn 0.05), subsonic cylinders below Kn 0.2 with two colour passes, GSIS
+    below Kn 0.3 and the plain kinetic iteration above."""
+    import numpy as np
+
+    from paper_2310_18916_gb300 import workloads as wl
+
+    reqs = serving.poisson_requests(300, 0.5, 7, lambda rng: wl.serving_request(rng))
+    cyl = [r for r in reqs if r.problem.name.startswith("cylinder")]
+    cav = [r for r in reqs if r.problem.name.startswith("cavity")]
+    assert len(cyl) + len(cav) == 300 and 110 < len(cyl) < 190
+    for r in reqs:
+        assert 1e-3 <= r.problem.Kn <= 1.0
+        assert r.opts["mode"] == ("gsis" if r.problem.Kn < 0.3 else "dvm")
+    assert all(r.opts.get("n_sweeps") == 2 and r.problem.Kn <= 0.2 for r in cyl)
+    assert all(0.1 <= r.problem.Ma <= 1.0 for r in cyl)
+    assert all(r.problem.Ma <= (5.0 if r.problem.Kn >= 0.05 else 1.75) + 1e-9 for r in cav)
+    assert max(r.problem.Ma for r in cav) > 3.0 and any(r.opts["mode"] == "dvm" for r in cav)
+    assert all(r.problem.ncells in (32 * 64, 48 * 96, 64 * 128) for r in cyl)
+    arrivals = np.array([r.arrival for r in reqs])
+    assert np.all(np.diff(arrivals) > 0) and abs(np.diff(arrivals).mean() - 0.5) < 0.1
+
+
+def test_a_failing_solve_leaves_with_its_error_and_the_others_finish():
+    class Failing(FakeSolver):
+        def step_wait(self):
+            eps = super().step_wait()
+            if self.p["name"] == "bad" and self.k == 3:
+                raise RuntimeError("GSIS_E_DIVERGED: non-finite or non-positive density/temperature")
+            return eps
+
+    clock = FakeClock()
+    srv = serving.Server(100, slots=2, nsm=152, make_solver=lambda p, prec, sms, st: Failing(p, clock, 0.01),
+                         footprint=lambda p, prec: p["bytes"], new_stream=lambda: None, clock=clock,
+                         idle=lambda s: setattr(clock, "t", clock.t + max(s, 1e-3)))
+    reqs = [serving.Request(i, {"name": n, "bytes": 40}, 0.0, tol=2 ** -6) for i, n in enumerate(["a", "bad", "c"])]
+    res = srv.run(reqs)
+    assert "DIVERGED" in res[1].error and res[1].W is None and not res[1].converged and res[1].steps == 2
+    assert res[0].converged and res[2].converged and not res[0].error
+    s = serving.summary(res, 1.0)
+    assert s["failed"] == 1 and s["served"] == 2 and s["converged"] == 2
