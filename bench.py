@@ -49,11 +49,13 @@ KINETIC_FLOPS_PER_POINT_2D = 103
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the 128^2 cavity with
 # 32^3 velocities, keyed by kernel, precision and the SHA-256 prefix of the kernel's source file
 # at capture time: a figure whose source has changed since is reported as null (stale).  Captured
-# on the 64^2 case in the same launch configuration (the FP64 kinetic kernel with its colour ring
-# in device scratch, as at 128^2) and scaled by the 4x cells: the kinetic kernel's traffic is
-# per point, the synthetic solve's per cell (profiles/dram_bytes_cavity64x32.md).
+# on the 64^2 case in the same launch configuration as at 128^2 (FP64: the colour ring in device
+# scratch; FP32 and BF16: in shared memory) and scaled by the 4x cells: the kinetic kernel's
+# traffic is per point, the synthetic solve's per cell (profiles/dram_bytes_cavity64x32.md).
 DRAM_BYTES_PER_LAUNCH = {
     ("kinetic_kernel", "f64"): (4 * (1.0834e9 + 1.1221e9), "d4173c6f5299"),
+    ("kinetic_kernel", "f32"): (4 * (0.5409e9 + 0.4763e9), "d4173c6f5299"),
+    ("kinetic_kernel", "bf16"): (4 * (0.2708e9 + 0.2127e9), "d4173c6f5299"),
     ("macro_kernel", "f64"): (4 * (3.79e6 + 0.02e6), "02e3bb610d02"),
 }
 KERNEL_SOURCES = {"kinetic_kernel": "kinetic.cu", "moments_kernel": "kinetic.cu", "macro_kernel": "macro.cu"}
