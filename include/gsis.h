@@ -201,6 +201,14 @@ typedef struct {
                            (the Euler preconditioning of Algorithm 1 for strong shocks).  Default
                            0; general blocks only (GSIS_E_UNSUPPORTED on rectilinear ones). */
   int wall_flux;        /* GSIS_WALL_EQ (default) or GSIS_WALL_G13 */
+  int positive_faces;   /* general blocks (body-fitted and unstructured meshes): 1 makes the kinetic
+                           step's reconstructed face values keep the sign of the cell value.  Where
+                           the limited linear value f_i + d (Section 3.2) falls below f_i, the face
+                           takes f_i^2 / (f_i - d), which agrees with it to first order in d / f_i.
+                           The linear form lets a VDF's steep fall into a near-vacuum wake
+                           reconstruct negative face values, which empties cells behind a body in
+                           supersonic flow.  Default 0 (the linear form); GSIS_E_UNSUPPORTED on
+                           rectilinear blocks. */
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;

@@ -356,16 +356,25 @@ static double venkat_cell(const orc_solver *s, int i, const double *q, int strid
   return phi;
 }
 
-/* Face values of cell i on each of its sides: q_i + phi grad q_i . (x_f - x_i). */
+/* Face values of cell i on each of its sides: q_i + d, d = phi grad q_i . (x_f - x_i).  With
+   orc_opts.positive_faces a face value that would fall below the cell value (d < 0) is
+   q_i^2 / (q_i - d) instead: positive whenever q_i is, equal to q_i + d to first order in d / q_i
+   (the two differ by d^2 / (q_i - d)), and continuous with its first derivative at d = 0.  The
+   linear form lets a VDF's steep fall into near-vacuum or into a velocity tail reconstruct
+   negative face values; a non-positive q_i keeps its own value. */
 static void reconstruct(const orc_solver *s, int i, const double *q, int stride, double out[6]) {
   double g[3];
   lsq_grad(s, i, q, stride, g);
   double phi = venkat_cell(s, i, q, stride, g);
-  const double *xc = s->xc + 3 * i;
+  const double *xc = s->xc + 3 * i, qi = q[(size_t)i * stride];
   for (int side = 0; side < 6; ++side) {
     const double *xf = s->xf + 18 * i + 3 * side;
     double r[3] = {xf[0] - xc[0], xf[1] - xc[1], xf[2] - xc[2]};
-    out[side] = q[(size_t)i * stride] + phi * dot3(g, r);
+    double d = phi * dot3(g, r);
+    if (s->o.positive_faces && d < 0)
+      out[side] = qi > 0 ? qi * qi / (qi - d) : qi;
+    else
+      out[side] = qi + d;
   }
 }
 
@@ -1673,6 +1682,8 @@ void orc_get_geometry(const orc_solver *s, double *vol, double *centre3, double 
 /* ---------------- pieces exposed for the pins ---------------- */
 
 void orc_cell_gradient(const orc_solver *s, int i, const double *q, double *g) { lsq_grad(s, i, q, 1, g); }
+
+void orc_cell_faces(const orc_solver *s, int i, const double *q, double *out6) { reconstruct(s, i, q, 1, out6); }
 
 double orc_cell_limiter(const orc_solver *s, int i, const double *q) {
   double g[3];

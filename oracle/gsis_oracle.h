@@ -71,6 +71,8 @@ typedef struct {
                            kinetic wall flux: ORC_WALL_EQ (0) the half-range flux of the local
                            Maxwellian, ORC_WALL_G13 (1) that of the Grad-13 reconstruction of
                            Eq. G13_VDF (Section 3.3) */
+  int positive_faces;   /* 1: the kinetic face values keep the sign of the cell value (see
+                           orc_cell_faces); 0: the linear reconstruction of Section 3.2 */
 } orc_opts;
 
 enum { ORC_WALL_EQ = 0, ORC_WALL_G13 = 1 };
@@ -134,6 +136,9 @@ void orc_get_geometry(const orc_solver *s, double *vol, double *centre3, double 
 /* LSQ gradient and Venkatakrishnan cell limiter of a cell field q[cell] (pins). */
 void orc_cell_gradient(const orc_solver *s, int cell, const double *q, double *grad3);
 double orc_cell_limiter(const orc_solver *s, int cell, const double *q);
+/* Face values of a cell on its six sides for a field q over cells (the reconstruction the kinetic
+   step applies to each velocity's f, orc_opts.positive_faces included). */
+void orc_cell_faces(const orc_solver *s, int cell, const double *q, double *out6);
 /* per cell and side the outward kinetic face flux (mass, momentum(3), energy, internal
    energy) of the last kinetic step: 36 per cell */
 void orc_get_face_flux(const orc_solver *s, double *out36);

@@ -34,7 +34,7 @@ class OrcOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("schedule", C.c_int), ("n_sweeps", C.c_int), ("macro_steps", C.c_int),
                 ("macro_sweeps", C.c_int), ("macro_cfl", C.c_double), ("macro_tol", C.c_double),
                 ("kin_inv_dt", C.c_double), ("venkat_K", C.c_double), ("nthreads", C.c_int),
-                ("wall_flux", C.c_int)]
+                ("wall_flux", C.c_int), ("positive_faces", C.c_int)]
 
 
 def lib():
@@ -68,6 +68,7 @@ def lib():
         L.orc_cell_gradient.argtypes = [C.c_void_p, C.c_int, D, D]
         L.orc_cell_limiter.argtypes = [C.c_void_p, C.c_int, D]
         L.orc_cell_limiter.restype = C.c_double
+        L.orc_cell_faces.argtypes = [C.c_void_p, C.c_int, D, D]
         L.orc_get_face_flux.argtypes = [C.c_void_p, D]
         L.orc_wall_flux.argtypes = [C.c_void_p, C.c_int, C.c_int, D, D, D, D]
         L.orc_tau.argtypes = [C.POINTER(OrcGas), C.c_double, C.c_double]
@@ -92,7 +93,7 @@ def gas_struct(p) -> OrcGas:
 
 
 DEFAULTS = dict(mode=0, schedule=0, n_sweeps=1, macro_steps=300, macro_sweeps=4, macro_cfl=100.0,
-                macro_tol=1e-10, kin_inv_dt=0.0, venkat_K=1.0, nthreads=0, wall_flux=0)
+                macro_tol=1e-10, kin_inv_dt=0.0, venkat_K=1.0, nthreads=0, wall_flux=0, positive_faces=0)
 
 
 class Oracle:
@@ -254,6 +255,13 @@ class Oracle:
     def face_flux(self):
         out = np.empty((self.nc, 6, 6))
         lib().orc_get_face_flux(self.h, _p(out))
+        return out
+
+    def cell_faces(self, cell, q):
+        """The reconstructed face values of `cell` on its six sides for the field q (one per cell)."""
+        out = np.zeros(6)
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        lib().orc_cell_faces(self.h, int(cell), _p(qq), _p(out))
         return out
 
     def cell_gradient(self, cell, q):

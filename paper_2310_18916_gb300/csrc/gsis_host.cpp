@@ -245,6 +245,7 @@ struct gsis_solver {
     a.gwid = d_gwid;
     a.gin = d_gin;
     a.n_sweeps = opt.n_sweeps;
+    a.pos_faces = opt.positive_faces;
     a.wden = d_wden;
     a.gnf = d_gnf;
     a.gpat = d_gpat;
@@ -680,6 +681,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   if (o->kinetic_ring != 0 && o->kinetic_ring != 1) { why = "kinetic_ring must be 0 or 1"; return GSIS_E_INVALID; }
   if (o->euler_presteps < 0) { why = "euler_presteps must be >= 0"; return GSIS_E_INVALID; }
   if (o->wall_flux != GSIS_WALL_EQ && o->wall_flux != GSIS_WALL_G13) { why = "bad wall_flux"; return GSIS_E_INVALID; }
+  if (o->positive_faces != 0 && o->positive_faces != 1) { why = "positive_faces must be 0 or 1"; return GSIS_E_INVALID; }
   if (o->shard_count > 1 && (o->shard_index < 0 || o->shard_index >= o->shard_count || !o->allreduce)) {
     why = "velocity sharding needs 0 <= shard_index < shard_count and an allreduce callback";
     return GSIS_E_INVALID;
@@ -736,6 +738,10 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
     }
   if (!general && o->euler_presteps > 0) {
     why = "Euler presteps are built on general meshes only";
+    return GSIS_E_UNSUPPORTED;
+  }
+  if (!general && o->positive_faces) {
+    why = "positive face values are built on general meshes only";
     return GSIS_E_UNSUPPORTED;
   }
   if (general) return GSIS_OK;  // volumes are checked when the geometry is built

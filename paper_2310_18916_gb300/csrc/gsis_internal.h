@@ -121,6 +121,7 @@ struct KinArgs {
   const int *gwid;          // [cell][6] wall-face id, -1 if the side is not a wall
   const unsigned char *gin; // [cell][6] far-field sides: 1 where the free stream enters
   int n_sweeps;             // point-implicit passes over the colours
+  int pos_faces;            // general meshes: face values that keep the sign of the cell value
   double *kpart;            // [CTA][cell][6] per-CTA sums of the outward kinetic face fluxes
                             // (area-integrated, over the cell's faces); nullptr: not wanted
   const double *wden;       // [wall face] re-emission flux of M(u_w, T_w) over every velocity

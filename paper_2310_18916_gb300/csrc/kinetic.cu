@@ -1204,6 +1204,15 @@ __device__ __forceinline__ T dot_xi(const T *S, T x, T y, T z) {
   return x * S[0] + y * S[1] + z * S[2];
 }
 
+// The kinetic face value from the cell value fi and its limited increment d = phi grad f . r: fi + d,
+// or with positive faces fi^2 / (fi - d) where d < 0 (positive whenever fi is; equal to fi + d to
+// first order in d / fi, the two differing by d^2 / (fi - d)); a non-positive fi keeps its value.
+template <typename T>
+__device__ __forceinline__ T face_value(T fi, T d, int pos) {
+  if (pos && d < (T)0) return fi > (T)0 ? ddiv(fi * fi, fi - d) : fi;
+  return fi + d;
+}
+
 // Venkatakrishnan factor of one cell from its unlimited gradient gr and neighbour bounds: the
 // minimum over its faces (not the absent or pole sides) of
 //   (Dm^2 + e^2 + 2 D2 Dm) / (Dm^2 + 2 D2^2 + D2 Dm + e^2),  D2 = gr . r,
@@ -1303,7 +1312,7 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
         const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
 #pragma unroll
         for (int s = 0; s < NF; ++s)
-          FF(c, q, s) = fi + phi * (gr[0] * g.f[s].r[0] + gr[1] * g.f[s].r[1] + gr[2] * g.f[s].r[2]);
+          FF(c, q, s) = face_value(fi, phi * (gr[0] * g.f[s].r[0] + gr[1] * g.f[s].r[1] + gr[2] * g.f[s].r[2]), A.pos_faces);
       }
     }
     __syncthreads();
@@ -1538,7 +1547,8 @@ __global__ void __launch_bounds__(256) wall_prepass_general_kernel(const KinArgs
           gr[2] += A.gsw[3 * e + 2] * d;
         }
       const T phi = venkat_general<T>(g, nb, fi, fmax, fmin, gr);
-      const T ff = fi + (phi * gr[0]) * fa.r[0] + (phi * gr[1]) * fa.r[1] + (phi * gr[2]) * fa.r[2];
+      const T ff = A.pos_faces ? face_value(fi, phi * (gr[0] * fa.r[0] + gr[1] * fa.r[1] + gr[2] * fa.r[2]), 1)
+                               : fi + (phi * gr[0]) * fa.r[0] + (phi * gr[1]) * fa.r[1] + (phi * gr[2]) * fa.r[2];
       num += (double)(wv * sn * ff);
     } else if (sn < (T)0) {
       den += (double)(wv * -sn * wall_maxwellian<T>(uT, x, y, z));

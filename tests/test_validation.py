@@ -208,3 +208,11 @@ def test_unstructured_meshes_are_validated():
     c2 = wl.unstructured_cavity(n=4, nv=8)
     q = dataclasses.replace(c2, bc=[wl.PERIODIC, wl.PERIODIC, wl.WALL, wl.WALL, wl.WALL, wl.WALL])
     assert code(q, mode=gsis.MODE_DVM) == GSIS_E_UNSUPPORTED
+
+
+def test_positive_faces_on_general_meshes_only_and_wall_flux_values():
+    assert code(wl.cavity(n=6, nv=8), positive_faces=1) == gsis.GSIS_E_UNSUPPORTED
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), positive_faces=1) == 0
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), positive_faces=2) == GSIS_E_INVALID
+    assert code(wl.cavity(n=6, nv=8), wall_flux=1) == 0
+    assert code(wl.cavity(n=6, nv=8), wall_flux=2) == GSIS_E_INVALID
