@@ -373,10 +373,11 @@ BODIES = {
     "capsule_small": dict(kind="capsule", n=(25, 20, 25), nv=24, vmax=None, Ma=10.0, Kn=0.01, first=None,
                           R_out=6.0, T_w=0.3, oracle_nv=8),
     # configuration 3 in GSIS: the same sphere and velocity box, reached by Mach continuation
-    # 1.5 -> 2.5 -> 3.25 -> 4 (each stage from the previous converged state) with positive face
-    # values, every stage to eps < 1e-6
+    # 0.5 -> 1 -> ... -> 4 in steps of 0.5 (each stage from the previous converged state; the first
+    # from 300 Euler presteps) with positive face values, every stage to eps < 1e-6
     "sphere_gsis": dict(kind="sphere", n=(32, 24, 48), nv=48, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0,
-                        clustered=True, mode="continuation", stages=(1.5, 2.5, 3.25, 4.0)),
+                        clustered=True, mode="continuation", stages=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0),
+                        euler_presteps=300),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }
@@ -513,21 +514,35 @@ def run_body_continuation(args):
             p = body_problem(args.body, Ma=Ma)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s = gsis.Solver(p, precision=args.precision, mode="gsis", n_sweeps=BODY_SWEEPS, init_W=W,
-                            positive_faces=1)
+            euler = b.get("euler_presteps", 0) if W is None else 0
+            try:
+                s = gsis.Solver(p, precision=args.precision, mode="gsis", n_sweeps=BODY_SWEEPS, init_W=W,
+                                positive_faces=1, euler_presteps=euler)
+            except gsis.GsisError as err:
+                stages.append({"Ma": Ma, "error": str(err)})
+                break
             s.profile(True, reset=True)
             stream = torch.cuda.current_stream()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            best, since, hist = np.inf, 0, []
+            best, since, hist, failed = np.inf, 0, [], None
             for _ in range(args.steps if args.steps > 20 else 80):
-                e = s.step()
+                try:
+                    e = s.step()
+                except gsis.GsisError as err:
+                    failed = str(err)
+                    break
                 hist.append(e)
                 best, since = (e, 0) if e < best else (best, since + 1)
                 if e < 1e-6 or since >= 15:
                     break
             e1.record(stream)
             torch.cuda.synchronize()
+            if failed or not hist:
+                s.close()
+                stages.append({"Ma": Ma, "steps": len(hist), "error": failed or "no step",
+                               "eps_history": [float(h) for h in hist]})
+                break
             wall = time.perf_counter() - t0
             phase, nsteps, launches = s.profile(False)
             U = float(np.linalg.norm(p.wall_u[1]))
@@ -539,6 +554,11 @@ def run_body_continuation(args):
                            "seconds": wall, "ms_per_step_device": e0.elapsed_time(e1) / len(hist),
                            "phase_ms_per_step": {k: v / max(nsteps, 1) for k, v in zip(PHASES, phase)},
                            "C_D": float(loads[4]), "C_H": float(loads[5]), "rho_min": float(W[:, 0].min())})
+    if "error" in stages[-1]:
+        print(json.dumps({"metric": "phase-space updates/s (GSIS outer step, sphere O-grid, Mach continuation)",
+                          "value": None, "unit": UNIT, "failed_stage": stages[-1], "stages": stages,
+                          "config": {"workload": f"{p.name}: {b}", "precision": args.precision}}))
+        return 1
     last = stages[-1]
     pts = p.ncells * p.nvel
     peak, peak_kind, _ = measured_peaks()
