@@ -374,10 +374,11 @@ BODIES = {
                           R_out=6.0, T_w=0.3, oracle_nv=8),
     # configuration 3 in GSIS: the same sphere and velocity box, reached by Mach continuation
     # 0.5 -> 1 -> ... -> 4 in steps of 0.5 (each stage from the previous converged state; the first
-    # from 300 Euler presteps) with positive face values, every stage to eps < 1e-6
+    # from 300 Euler presteps) with positive face values and the state update relaxed by 0.5, every
+    # stage to eps < 1e-6
     "sphere_gsis": dict(kind="sphere", n=(32, 24, 48), nv=48, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0,
                         clustered=True, mode="continuation", stages=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0),
-                        euler_presteps=300),
+                        euler_presteps=300, relax=0.5),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }
@@ -495,7 +496,8 @@ def run_body_continuation(args):
     """GSIS on a body-fitted grid from the free stream at the target Mach number, reached by Mach
     continuation: each stage starts from the previous stage's converged state (its Maxwellian,
     then 10 kinetic presteps) with a faster free stream, and runs GSIS outer steps (two colour
-    passes, positive face values) to eps < 1e-6, or until eps stops falling for 15 steps.
+    passes, positive face values, the configured update relaxation) to eps < 1e-6, or until eps
+    stops falling for 15 steps.
     Reports the time to the converged target state (creation and presteps included), the GSIS
     outer-step throughput of the last stage (CUDA events), its phase split and the drag and
     heat-flux coefficients."""
@@ -517,7 +519,7 @@ def run_body_continuation(args):
             euler = b.get("euler_presteps", 0) if W is None else 0
             try:
                 s = gsis.Solver(p, precision=args.precision, mode="gsis", n_sweeps=BODY_SWEEPS, init_W=W,
-                                positive_faces=1, euler_presteps=euler)
+                                positive_faces=1, euler_presteps=euler, relax=b.get("relax", 0.0))
             except gsis.GsisError as err:
                 stages.append({"Ma": Ma, "error": str(err)})
                 break

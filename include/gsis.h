@@ -209,6 +209,18 @@ typedef struct {
                            reconstruct negative face values, which empties cells behind a body in
                            supersonic flow.  Default 0 (the linear form); GSIS_E_UNSUPPORTED on
                            rectilinear blocks. */
+  double relax;         /* general blocks, GSIS mode: the outer step's update of the state is
+                           W^{n+1/2} + relax (W^{n+1} - W^{n+1/2}) (in rho, u, T_t, T_r) instead of
+                           the synthetic solve's W^{n+1}.  0 or 1 (default 0): the full update of
+                           Algorithm 1; values in (0, 1) damp it.  The converged state is the same
+                           wherever the discrete reference distribution conserves mass, momentum
+                           and energy on the velocity grid; otherwise the two differ by that
+                           quadrature error.
+                           On O-grids whose cells next to the poles are thin wedges, the full
+                           update lets a slowly growing mode in (sphere of 16 x 24 x 48 cells, Kn
+                           0.05: eps falls to 7e-5, then grows); 0.5 converges it.
+                           GSIS_E_INVALID outside [0, 1]; GSIS_E_UNSUPPORTED below 1 on rectilinear
+                           blocks. */
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;

@@ -1420,8 +1420,12 @@ static int run_step(orc_solver *s, int mode) {
        local-time-step iteration does not conserve mass, so its density is rescaled to the
        domain's total mass (velocity and temperatures unchanged). */
     double mk = s->mass_ref, mm = 0.0;
-    for (int i = 0; i < nc; ++i) mm += Wc[6 * i] * s->vol[i];
     for (int i = 0; i < nc; ++i) prim_of(s, Wc + 6 * i, Wnew + 6 * i);
+    /* orc_opts.relax < 1: the update is W^{n+1/2} + relax (W^{n+1} - W^{n+1/2}), in primitives */
+    if (s->o.relax > 0.0 && s->o.relax < 1.0)
+      for (int i = 0; i < nc; ++i)
+        for (int t = 0; t < 6; ++t) Wnew[6 * i + t] = s->Mh[18 * i + t] + s->o.relax * (Wnew[6 * i + t] - s->Mh[18 * i + t]);
+    for (int i = 0; i < nc; ++i) mm += Wnew[6 * i] * s->vol[i];
     if (!s->open)
       for (int i = 0; i < nc; ++i) Wnew[6 * i] *= mk / mm;
     free(Wc);

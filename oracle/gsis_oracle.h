@@ -73,6 +73,8 @@ typedef struct {
                            Eq. G13_VDF (Section 3.3) */
   int positive_faces;   /* 1: the kinetic face values keep the sign of the cell value (see
                            orc_cell_faces); 0: the linear reconstruction of Section 3.2 */
+  double relax;         /* GSIS update W^{n+1/2} + relax (W^{n+1} - W^{n+1/2}); 0 or 1: the full
+                           update of Algorithm 1 */
 } orc_opts;
 
 enum { ORC_WALL_EQ = 0, ORC_WALL_G13 = 1 };

@@ -34,7 +34,8 @@ class OrcOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("schedule", C.c_int), ("n_sweeps", C.c_int), ("macro_steps", C.c_int),
                 ("macro_sweeps", C.c_int), ("macro_cfl", C.c_double), ("macro_tol", C.c_double),
                 ("kin_inv_dt", C.c_double), ("venkat_K", C.c_double), ("nthreads", C.c_int),
-                ("wall_flux", C.c_int), ("positive_faces", C.c_int)]
+                ("wall_flux", C.c_int), ("positive_faces", C.c_int),
+                ("relax", C.c_double)]
 
 
 def lib():
@@ -93,7 +94,7 @@ def gas_struct(p) -> OrcGas:
 
 
 DEFAULTS = dict(mode=0, schedule=0, n_sweeps=1, macro_steps=300, macro_sweeps=4, macro_cfl=100.0,
-                macro_tol=1e-10, kin_inv_dt=0.0, venkat_K=1.0, nthreads=0, wall_flux=0, positive_faces=0)
+                macro_tol=1e-10, kin_inv_dt=0.0, venkat_K=1.0, nthreads=0, wall_flux=0, positive_faces=0, relax=0.0)
 
 
 class Oracle:

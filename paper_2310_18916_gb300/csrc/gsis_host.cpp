@@ -276,6 +276,7 @@ struct gsis_solver {
     m.euler = 0;
     m.mh_stride = 18;
     m.wall_g13 = opt.wall_flux == GSIS_WALL_G13;
+    m.relax = opt.relax > 0.0 ? opt.relax : 1.0;
     m.mu0 = Kn / std::sqrt(3.14159265358979323846);
     m.omega = omega;
     m.cfl = opt.macro_cfl;
@@ -682,6 +683,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   if (o->euler_presteps < 0) { why = "euler_presteps must be >= 0"; return GSIS_E_INVALID; }
   if (o->wall_flux != GSIS_WALL_EQ && o->wall_flux != GSIS_WALL_G13) { why = "bad wall_flux"; return GSIS_E_INVALID; }
   if (o->positive_faces != 0 && o->positive_faces != 1) { why = "positive_faces must be 0 or 1"; return GSIS_E_INVALID; }
+  if (!(o->relax >= 0.0 && o->relax <= 1.0)) { why = "relax must be in [0, 1]"; return GSIS_E_INVALID; }
   if (o->shard_count > 1 && (o->shard_index < 0 || o->shard_index >= o->shard_count || !o->allreduce)) {
     why = "velocity sharding needs 0 <= shard_index < shard_count and an allreduce callback";
     return GSIS_E_INVALID;
@@ -742,6 +744,10 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   }
   if (!general && o->positive_faces) {
     why = "positive face values are built on general meshes only";
+    return GSIS_E_UNSUPPORTED;
+  }
+  if (!general && o->relax > 0.0 && o->relax < 1.0) {
+    why = "the relaxed GSIS update is built on general meshes only";
     return GSIS_E_UNSUPPORTED;
   }
   if (general) return GSIS_OK;  // volumes are checked when the geometry is built
@@ -1818,6 +1824,7 @@ static int euler_presteps(gsis_solver *s) {
   MacroGenArgs m = s->macro_general_args();
   m.euler = 1;
   m.wall_g13 = 0;
+  m.relax = 1.0;
   m.steps = s->opt.euler_presteps;
   m.Mh = s->d_Wstate;
   m.mh_stride = 6;

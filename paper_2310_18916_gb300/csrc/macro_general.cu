@@ -493,6 +493,11 @@ __global__ void final_kernel(MacroGenArgs m) {
   for (int c = threadIdx.x; c < m.nc; c += blockDim.x) {
     double *p = m.Wout + 6 * (size_t)c;
     prim_of(m, m.W + 6 * (size_t)c, p);
+    if (m.relax < 1.0 && !m.euler) {
+      // under-relaxed update: W^{n+1/2} + relax (W^{n+1} - W^{n+1/2}) in primitives
+      const double *q = m.Mh + (size_t)m.mh_stride * c;
+      for (int k = 0; k < 6; ++k) p[k] = q[k] + m.relax * (p[k] - q[k]);
+    }
     mm += p[0] * m.vol[c];
   }
   red[threadIdx.x] = mm;

@@ -51,7 +51,8 @@ class Options(C.Structure):
                 ("alloc_ctx", C.c_void_p), ("macro_sms", C.c_int), ("shard_count", C.c_int),
                 ("shard_index", C.c_int), ("allreduce", ALLREDUCE_FN), ("allreduce_ctx", C.c_void_p),
                 ("kinetic_ring", C.c_int), ("euler_presteps", C.c_int),
-                ("wall_flux", C.c_int), ("positive_faces", C.c_int)]
+                ("wall_flux", C.c_int), ("positive_faces", C.c_int),
+                ("relax", C.c_double)]
 
 
 _lib = None

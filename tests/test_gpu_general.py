@@ -160,6 +160,21 @@ def test_gsis_rykov_cylinder_fp64():
         scaled_close(g.W(), o.W(), 1e-10, f"Rykov cylinder GSIS W, step {it}")
 
 
+def test_relaxed_gsis_update_on_a_cylinder_fp64():
+    """gsis_options.relax = 0.5: the state after each GSIS step is the blend of the half-step
+    moments and the synthetic solution, on the GPU as in the oracle, element by element."""
+    p = wl.cylinder(n_r=6, n_theta=12, nv=12, R=0.5, R_out=3.0, first=0.15, Ma=0.5, Kn=0.2, T_w=1.5)
+    W = wl.perturbed_state(p, seed=46, amp=0.03)
+    g = gsis.Solver(p, precision="f64", mode="gsis", init_W=W, kinetic_presteps=0, n_sweeps=2, macro_steps=40,
+                    macro_tol=0.0, relax=0.5)
+    o = Oracle(p, W0=W, mode=0, n_sweeps=2, macro_steps=40, macro_tol=0.0, relax=0.5)
+    for it in range(3):
+        g.step()
+        o.step()
+        scaled_close(g.W(), o.W(), 1e-10, f"relaxed cylinder GSIS W, step {it}")
+    g.close()
+
+
 def test_gsis_cylinder_fp32_and_early_exit():
     p = wl.cylinder(n_r=6, n_theta=12, nv=16, R=0.5, R_out=3.0, Ma=0.5, Kn=0.2)
     g, o = gsis_pair(p, "f32", 2, macro_steps=60)

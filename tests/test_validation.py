@@ -216,3 +216,11 @@ def test_positive_faces_on_general_meshes_only_and_wall_flux_values():
     assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), positive_faces=2) == GSIS_E_INVALID
     assert code(wl.cavity(n=6, nv=8), wall_flux=1) == 0
     assert code(wl.cavity(n=6, nv=8), wall_flux=2) == GSIS_E_INVALID
+
+
+def test_relaxed_update_only_on_general_meshes_and_in_range():
+    assert code(wl.cavity(n=6, nv=8), relax=0.5) == gsis.GSIS_E_UNSUPPORTED
+    assert code(wl.cavity(n=6, nv=8), relax=1.0) == 0
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), relax=0.5) == 0
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), relax=1.5) == GSIS_E_INVALID
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), relax=-0.1) == GSIS_E_INVALID
