@@ -98,9 +98,9 @@ typedef struct {
    * order, each taking the smallest colour none of its neighbours holds): n_sweeps passes in
    * the kinetic step, the synthetic solve's LU-SGS over the same colours.  Least-squares
    * gradients: over the face neighbours on a mesh of hexahedra, over every node-sharing cell on
-   * a mesh with prisms, pyramids or tetrahedra.  GSIS_MODE_GSIS and Euler presteps need a mesh
-   * of hexahedra (GSIS_E_UNSUPPORTED otherwise); the kinetic iteration runs on every shape.  Faces must be planar
-   * to round-off, cells of positive volume; an unmatched side with patch -1, a patch out of
+   * a mesh with prisms, pyramids or tetrahedra; the synthetic solve takes its gradients over
+   * the same stencils.  Both modes and the Euler presteps run on every shape.  Faces must be
+   * planar to round-off, cells of positive volume; an unmatched side with patch -1, a patch out of
    * range or a shared side with a patch gives GSIS_E_INVALID. */
   int ncells;
   int nnodes;
@@ -221,6 +221,20 @@ typedef struct {
                            0.05: eps falls to 7e-5, then grows); 0.5 converges it.
                            GSIS_E_INVALID outside [0, 1]; GSIS_E_UNSUPPORTED below 1 on rectilinear
                            blocks. */
+  double visc_jump;     /* general blocks: the weight alpha of the jump term in the synthetic
+                           solve's viscous face gradients (Eq. NSF_constitutive at a face between
+                           cells i and j, d = x_j - x_i the line between their centres):
+                             grad_f = g + alpha (phi_j - phi_i - g.d) d / |d|^2,
+                           g the mean of the two cells' least-squares gradients, for u, T_t and
+                           T_r.  The mean alone is not dissipative on meshes with prisms, pyramids
+                           or tetrahedra (their node-sharing stencils): the synthetic solve's inner
+                           iteration diverges there at Kn 0.2 on a 16 x 16 cavity, at every CFL.
+                           The full correction (alpha = 1) makes the outer coupling with the
+                           kinetic step stall or diverge; 1/4 converges both.  The fixed point does
+                           not depend on alpha.  Negative (default -1): 1/4 on meshes with
+                           prisms, pyramids or tetrahedra, 0 on others; a value in [0, 1] applies
+                           on every general block.  GSIS_E_INVALID above 1 or NaN;
+                           GSIS_E_UNSUPPORTED above 0 on rectilinear blocks. */
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;

@@ -19,7 +19,9 @@
  *   refinement, GSIS-vs-DVM fixed point, O-grid geometry (wrapped azimuth, pole faces),
  *   far field (uniform free stream, collisionless reservoir against a wall), the
  *   free-molecular force on a cylinder, the Euler presteps (mirror symmetry of the converged
- *   inviscid cylinder flow): pinned.
+ *   inviscid cylinder flow), the jump term of the viscous face gradients on meshes with
+ *   simplices (no jump for linear fields, the difference quotient along the centre line at
+ *   weight 1, affine in the weight): pinned.
  *   Macro-solver details the paper leaves to its references (face gradient,
  *   Gamma, time step): pinned only through the fixed point (kinetic/GSIS agree).
  */
@@ -77,6 +79,8 @@ struct orc_solver {
      every other cell sharing a node with it, ascending (face neighbours alone leave the
      second-order upwind scheme unstable on simplices) */
   int *sten;
+  int simplex;           /* an unstructured mesh with prisms, pyramids or tetrahedra */
+  double jump;           /* the weight of the jump term in the viscous face gradients */
   double mass_ref;       /* total mass of the closed domain (set with f) */
   double mass_scale;     /* rescaling applied after the last kinetic step */
 };
@@ -762,6 +766,7 @@ static int build_geometry_unstructured(orc_solver *s, const orc_mesh *m) {
       }
       if (ndist < 8) all_hex = 0;
     }
+    s->simplex = !all_hex;
     for (int c = 0; c < nc; ++c) {
       int *st = s->sten + (size_t)STENCIL_MAX * c, k = 0;
       for (int t = 0; t < STENCIL_MAX; ++t) st[t] = -1;
@@ -1047,13 +1052,28 @@ typedef struct {
 
 /* NSF stress and heat fluxes at the face between cells i and j (Eq. NSF_constitutive):
    face gradient = mean of the two cells' LSQ gradients, mu at the face = mean of the
-   cells' mu.  out: sigma(xx,yy,zz,xy,xz,yz), qt(3), qr(3). */
+   cells' mu.  Between two different cells, with the weight alpha = s->jump > 0, each field
+   phi in (u_x, u_y, u_z, T_t, T_r) replaces the fraction alpha of the mean gradient's change
+   along the centre line d = x_j - x_i by the cells' difference:
+     grad_f = mean + alpha (phi_j - phi_i - mean . d) d / |d|^2
+   (alpha = 1 makes grad_f . d = phi_j - phi_i).  out: sigma(xx,yy,zz,xy,xz,yz), qt(3), qr(3). */
 static void face_nsf(const orc_solver *s, const macro_work *m, int i, int j, double *out) {
   double G[3][3], gT[3], gTr[3];
   for (int a = 0; a < 3; ++a) {
     for (int b = 0; b < 3; ++b) G[a][b] = 0.5 * (m->gP[15 * i + 3 * a + b] + m->gP[15 * j + 3 * a + b]);
     gT[a] = 0.5 * (m->gP[15 * i + 9 + a] + m->gP[15 * j + 9 + a]);
     gTr[a] = 0.5 * (m->gP[15 * i + 12 + a] + m->gP[15 * j + 12 + a]);
+  }
+  if (s->jump > 0.0 && j != i) {
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = s->xc[3 * j + a] - s->xc[3 * i + a];
+    double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double *grad[5] = {G[0], G[1], G[2], gT, gTr};
+    for (int k = 0; k < 5; ++k) {
+      double along = grad[k][0] * d[0] + grad[k][1] * d[1] + grad[k][2] * d[2];
+      double jump = m->pr[6 * j + 1 + k] - m->pr[6 * i + 1 + k] - along;
+      for (int a = 0; a < 3; ++a) grad[k][a] += s->jump * jump * d[a] / dd;
+    }
   }
   double muf = 0.5 * (m->mu[i] + m->mu[j]), kt, kr;
   orc_conductivity(&s->g, muf, &kt, &kr);
@@ -1580,6 +1600,7 @@ int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const o
   }
   int rc = m->ncells > 0 ? build_geometry_unstructured(s, m) : build_geometry(s, m);
   if (rc) { orc_destroy(s); return rc; }
+  s->jump = s->o.visc_jump >= 0.0 ? s->o.visc_jump : (s->simplex ? 0.25 : 0.0);
   s->corder = (int *)malloc(sizeof(int) * 8 * (size_t)nc);
   if (!s->corder) { orc_destroy(s); return ORC_E_OOM; }
   if (s->colour) {
@@ -1688,6 +1709,29 @@ void orc_get_geometry(const orc_solver *s, double *vol, double *centre3, double 
 void orc_cell_gradient(const orc_solver *s, int i, const double *q, double *g) { lsq_grad(s, i, q, 1, g); }
 
 void orc_cell_faces(const orc_solver *s, int i, const double *q, double *out6) { reconstruct(s, i, q, 1, out6); }
+
+int orc_face_nsf(const orc_solver *s, const double *W, int i, int side, double *out12) {
+  int nc = s->nc;
+  if (i < 0 || i >= nc || side < 0 || side > 5) return ORC_E_INVALID;
+  int j = s->nb[6 * i + side] >= 0 ? s->nb[6 * i + side] : i;
+  macro_work m;
+  memset(&m, 0, sizeof m);
+  m.pr = (double *)malloc(sizeof(double) * 6 * nc);
+  m.gP = (double *)calloc(15 * (size_t)nc, sizeof(double));
+  m.mu = (double *)malloc(sizeof(double) * nc);
+  if (!m.pr || !m.gP || !m.mu) { free(m.pr); free(m.gP); free(m.mu); return ORC_E_OOM; }
+  for (int c = 0; c < nc; ++c) {
+    prim_of(s, W + 6 * c, m.pr + 6 * c);
+    m.mu[c] = visc(&s->g, m.pr[6 * c + 4]);
+  }
+  for (int k = 0; k < 5; ++k) {
+    lsq_grad(s, i, m.pr + 1 + k, 6, m.gP + 15 * i + 3 * k);
+    lsq_grad(s, j, m.pr + 1 + k, 6, m.gP + 15 * j + 3 * k);
+  }
+  face_nsf(s, &m, i, j, out12);
+  free(m.pr); free(m.gP); free(m.mu);
+  return ORC_OK;
+}
 
 double orc_cell_limiter(const orc_solver *s, int i, const double *q) {
   double g[3];

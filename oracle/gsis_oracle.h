@@ -75,6 +75,9 @@ typedef struct {
                            orc_cell_faces); 0: the linear reconstruction of Section 3.2 */
   double relax;         /* GSIS update W^{n+1/2} + relax (W^{n+1} - W^{n+1/2}); 0 or 1: the full
                            update of Algorithm 1 */
+  double visc_jump;     /* weight alpha of the jump along the centre line in the viscous face
+                           gradients (see face_nsf); negative: 1/4 on meshes with prisms,
+                           pyramids or tetrahedra, 0 on others */
 } orc_opts;
 
 enum { ORC_WALL_EQ = 0, ORC_WALL_G13 = 1 };
@@ -141,6 +144,10 @@ double orc_cell_limiter(const orc_solver *s, int cell, const double *q);
 /* Face values of a cell on its six sides for a field q over cells (the reconstruction the kinetic
    step applies to each velocity's f, orc_opts.positive_faces included). */
 void orc_cell_faces(const orc_solver *s, int cell, const double *q, double *out6);
+/* NSF stress and heat fluxes (sigma xx yy zz xy xz yz, q_t, q_r) of the synthetic solve at the
+   face between `cell` and its neighbour on `side` (the cell itself on a boundary side) for the
+   conservative state W [cell][6]. */
+int orc_face_nsf(const orc_solver *s, const double *W, int cell, int side, double *out12);
 /* per cell and side the outward kinetic face flux (mass, momentum(3), energy, internal
    energy) of the last kinetic step: 36 per cell */
 void orc_get_face_flux(const orc_solver *s, double *out36);

@@ -35,7 +35,7 @@ class OrcOpts(C.Structure):
                 ("macro_sweeps", C.c_int), ("macro_cfl", C.c_double), ("macro_tol", C.c_double),
                 ("kin_inv_dt", C.c_double), ("venkat_K", C.c_double), ("nthreads", C.c_int),
                 ("wall_flux", C.c_int), ("positive_faces", C.c_int),
-                ("relax", C.c_double)]
+                ("relax", C.c_double), ("visc_jump", C.c_double)]
 
 
 def lib():
@@ -70,6 +70,7 @@ def lib():
         L.orc_cell_limiter.argtypes = [C.c_void_p, C.c_int, D]
         L.orc_cell_limiter.restype = C.c_double
         L.orc_cell_faces.argtypes = [C.c_void_p, C.c_int, D, D]
+        L.orc_face_nsf.argtypes = [C.c_void_p, D, C.c_int, C.c_int, D]
         L.orc_get_face_flux.argtypes = [C.c_void_p, D]
         L.orc_wall_flux.argtypes = [C.c_void_p, C.c_int, C.c_int, D, D, D, D]
         L.orc_tau.argtypes = [C.POINTER(OrcGas), C.c_double, C.c_double]
@@ -94,7 +95,8 @@ def gas_struct(p) -> OrcGas:
 
 
 DEFAULTS = dict(mode=0, schedule=0, n_sweeps=1, macro_steps=300, macro_sweeps=4, macro_cfl=100.0,
-                macro_tol=1e-10, kin_inv_dt=0.0, venkat_K=1.0, nthreads=0, wall_flux=0, positive_faces=0, relax=0.0)
+                macro_tol=1e-10, kin_inv_dt=0.0, venkat_K=1.0, nthreads=0, wall_flux=0, positive_faces=0, relax=0.0,
+                visc_jump=-1.0)
 
 
 class Oracle:
@@ -263,6 +265,14 @@ class Oracle:
         out = np.zeros(6)
         qq = np.ascontiguousarray(q, dtype=np.float64)
         lib().orc_cell_faces(self.h, int(cell), _p(qq), _p(out))
+        return out
+
+    def face_nsf(self, W, cell, side):
+        """orc_face_nsf: the synthetic solve's NSF stress (xx yy zz xy xz yz) and heat fluxes
+        q_t, q_r at the face of `cell` on `side` for the conservative state W [cell][6]."""
+        out = np.zeros(12)
+        Wc = np.ascontiguousarray(W, dtype=np.float64)
+        self._rc(lib().orc_face_nsf(self.h, _p(Wc), int(cell), int(side), _p(out)), "orc_face_nsf")
         return out
 
     def cell_gradient(self, cell, q):

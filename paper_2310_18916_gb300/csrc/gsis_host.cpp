@@ -81,6 +81,7 @@ struct gsis_solver {
   // general (curvilinear) meshes: per-cell geometry, neighbour codes, wall-face ids, far-field
   // inflow sides, wall-face areas; the kinetic kernel's persistent grid
   bool general = false;
+  bool simplex = false;  // an unstructured mesh with prisms, pyramids or tetrahedra
   // unstructured meshes: the neighbour's side of each shared face and the boundary patch of each
   // boundary face (both absent on structured blocks, whose opposite side is s ^ 1 and whose
   // patches are the block sides); the synthetic solve's colour offsets into colcells
@@ -277,6 +278,7 @@ struct gsis_solver {
     m.mh_stride = 18;
     m.wall_g13 = opt.wall_flux == GSIS_WALL_G13;
     m.relax = opt.relax > 0.0 ? opt.relax : 1.0;
+    m.visc_jump = opt.visc_jump >= 0.0 ? opt.visc_jump : (simplex ? 0.25 : 0.0);
     m.mu0 = Kn / std::sqrt(3.14159265358979323846);
     m.omega = omega;
     m.cfl = opt.macro_cfl;
@@ -597,6 +599,7 @@ extern "C" void gsis_default_options(gsis_options *o) {
   o->kin_inv_dt = 0.0;
   o->venkat_K = 1.0;
   o->kinetic_presteps = 10;
+  o->visc_jump = -1.0;
 }
 
 namespace {
@@ -684,6 +687,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   if (o->wall_flux != GSIS_WALL_EQ && o->wall_flux != GSIS_WALL_G13) { why = "bad wall_flux"; return GSIS_E_INVALID; }
   if (o->positive_faces != 0 && o->positive_faces != 1) { why = "positive_faces must be 0 or 1"; return GSIS_E_INVALID; }
   if (!(o->relax >= 0.0 && o->relax <= 1.0)) { why = "relax must be in [0, 1]"; return GSIS_E_INVALID; }
+  if (!(o->visc_jump <= 1.0)) { why = "visc_jump must be at most 1"; return GSIS_E_INVALID; }
   if (o->shard_count > 1 && (o->shard_index < 0 || o->shard_index >= o->shard_count || !o->allreduce)) {
     why = "velocity sharding needs 0 <= shard_index < shard_count and an allreduce callback";
     return GSIS_E_INVALID;
@@ -748,6 +752,10 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   }
   if (!general && o->relax > 0.0 && o->relax < 1.0) {
     why = "the relaxed GSIS update is built on general meshes only";
+    return GSIS_E_UNSUPPORTED;
+  }
+  if (!general && o->visc_jump > 0.0) {
+    why = "the viscous face-gradient jump term is built on general meshes only";
     return GSIS_E_UNSUPPORTED;
   }
   if (general) return GSIS_OK;  // volumes are checked when the geometry is built
@@ -1227,10 +1235,7 @@ static int setup_unstructured_mesh(gsis_solver *s, const gsis_mesh *m) {
   // (a mesh with any simplex cell takes node-sharing stencils everywhere: face stencils on its
   // hexahedra next to simplices' node stencils left the mixed scheme unstable too)
   const bool all_hex = std::all_of(ndist.begin(), ndist.end(), [](int k) { return k == 8; });
-  if (!all_hex && (s->opt.mode == GSIS_MODE_GSIS || s->opt.euler_presteps > 0))
-    return s->fail(GSIS_E_UNSUPPORTED,
-                   "the synthetic solve is built on hexahedral meshes only; prisms, pyramids and tetrahedra take "
-                   "GSIS_MODE_DVM");
+  s->simplex = !all_hex;
   s->gs_off.assign(nc + 1, 0);
   s->gs_idx.clear();
   s->gs_w.clear();
@@ -1825,6 +1830,7 @@ static int euler_presteps(gsis_solver *s) {
   m.euler = 1;
   m.wall_g13 = 0;
   m.relax = 1.0;
+  m.visc_jump = 0.0;
   m.steps = s->opt.euler_presteps;
   m.Mh = s->d_Wstate;
   m.mh_stride = 6;

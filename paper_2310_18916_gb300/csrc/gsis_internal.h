@@ -314,6 +314,7 @@ struct MacroGenArgs {
   int euler;                   // 1: the inviscid presteps (slip walls, no correction, K unused)
   int wall_g13;                // wall flux of the Grad-13 VDF (needs mh_stride 18: the moments)
   double relax;                // GSIS update W^{n+1/2} + relax (W^{n+1} - W^{n+1/2}) (1: the full one)
+  double visc_jump;            // weight of the jump term in the viscous face gradients (0: the mean)
   int mh_stride;               // doubles per cell of Mh (18: the moments; 6: a primitive state)
   double mu0, omega, cfl, tol, d_r, Z_r, A[4], mass_ref;
   double vsum;                 // total volume (fields with sum W_k^2 V <= 1e-24 vsum count as zero)

@@ -135,13 +135,25 @@ __device__ void wall_eq_flux(const MacroGenArgs &m, int patch, const double *p, 
 }
 
 // NSF stress and heat fluxes at a face: gradients and viscosity the means of cells i and j
-// (j = i on a far-field face).  out: sigma (xx yy zz xy xz yz), q_t (3), q_r (3).
+// (j = i on a far-field face); between two cells, with visc_jump = alpha > 0, each gradient g of
+// u, T_t, T_r takes alpha times the jump along the centre line d = x_j - x_i,
+// g + alpha (phi_j - phi_i - g.d) d / |d|^2.  out: sigma (xx yy zz xy xz yz), q_t (3), q_r (3).
 __device__ void face_nsf(const MacroGenArgs &m, int i, int j, double *out) {
   double G[3][3], gT[3], gTr[3];
   for (int a = 0; a < 3; ++a) {
     for (int b = 0; b < 3; ++b) G[a][b] = 0.5 * (m.gP[15 * (size_t)i + 3 * a + b] + m.gP[15 * (size_t)j + 3 * a + b]);
     gT[a] = 0.5 * (m.gP[15 * (size_t)i + 9 + a] + m.gP[15 * (size_t)j + 9 + a]);
     gTr[a] = 0.5 * (m.gP[15 * (size_t)i + 12 + a] + m.gP[15 * (size_t)j + 12 + a]);
+  }
+  if (m.visc_jump > 0.0 && j != i) {
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = m.xc[3 * (size_t)j + a] - m.xc[3 * (size_t)i + a];
+    const double s = m.visc_jump / dot3(d, d);
+    double *g[5] = {G[0], G[1], G[2], gT, gTr};
+    for (int k = 0; k < 5; ++k) {
+      const double c = m.pr[6 * (size_t)j + 1 + k] - m.pr[6 * (size_t)i + 1 + k] - dot3(g[k], d);
+      for (int a = 0; a < 3; ++a) g[k][a] += s * c * d[a];
+    }
   }
   const double muf = 0.5 * (m.mu[i] + m.mu[j]);
   double kt, kr;

@@ -52,7 +52,7 @@ class Options(C.Structure):
                 ("shard_index", C.c_int), ("allreduce", ALLREDUCE_FN), ("allreduce_ctx", C.c_void_p),
                 ("kinetic_ring", C.c_int), ("euler_presteps", C.c_int),
                 ("wall_flux", C.c_int), ("positive_faces", C.c_int),
-                ("relax", C.c_double)]
+                ("relax", C.c_double), ("visc_jump", C.c_double)]
 
 
 _lib = None

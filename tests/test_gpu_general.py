@@ -175,6 +175,24 @@ def test_relaxed_gsis_update_on_a_cylinder_fp64():
     g.close()
 
 
+def test_viscous_jump_weight_on_a_cylinder_fp64():
+    """gsis_options.visc_jump = 0.5 on a hexahedral O-grid (where the default is none): the
+    synthetic solve's viscous face gradients with the jump term, GSIS steps element by element."""
+    p = wl.cylinder(n_r=6, n_theta=12, nv=12, R=0.5, R_out=3.0, first=0.15, Ma=0.5, Kn=0.2, T_w=1.5)
+    W = wl.perturbed_state(p, seed=47, amp=0.03)
+    g = gsis.Solver(p, precision="f64", mode="gsis", init_W=W, kinetic_presteps=0, n_sweeps=2, macro_steps=40,
+                    macro_tol=0.0, visc_jump=0.5)
+    o = Oracle(p, W0=W, mode=0, n_sweeps=2, macro_steps=40, macro_tol=0.0, visc_jump=0.5)
+    o0 = Oracle(p, W0=W, mode=0, n_sweeps=2, macro_steps=40, macro_tol=0.0)
+    for it in range(3):
+        g.step()
+        o.step()
+        o0.step()
+        scaled_close(g.W(), o.W(), 1e-10, f"cylinder GSIS W with the jump term, step {it}")
+    assert np.abs(o.W() - o0.W()).max() > 1e-8   # the term is there
+    g.close()
+
+
 def test_gsis_cylinder_fp32_and_early_exit():
     p = wl.cylinder(n_r=6, n_theta=12, nv=16, R=0.5, R_out=3.0, Ma=0.5, Kn=0.2)
     g, o = gsis_pair(p, "f32", 2, macro_steps=60)

@@ -1,6 +1,6 @@
 """Unstructured meshes on the GPU against the oracle: tetrahedra, a hybrid prism/hexahedron
-cavity (node-sharing least-squares stencils, greedy colour sweeps) and the unstructured forms of
-a cavity and a cylinder O-grid (face stencils, GSIS).  FP64 within 1e-10 (rounding order only),
+cavity (node-sharing least-squares stencils, greedy colour sweeps, both modes) and the
+unstructured forms of a cavity and a cylinder O-grid (face stencils, GSIS).  FP64 within 1e-10 (rounding order only),
 FP32 within the FP32 bounds of the structured tests (2e-5; heat flux 2e-4)."""
 import numpy as np
 import pytest
@@ -67,3 +67,43 @@ def test_unstructured_hexahedra_gsis_steps(make):
         scaled_close(g.W()[:, [0, 1, 2, 4]], o.W()[:, [0, 1, 2, 4]], 1e-10, f"{make} unstructured GSIS W, step {it}")
     assert g.stats()[1] == o.macro_iters
     g.close()
+
+
+@pytest.mark.parametrize("make", ["hybrid", "tetrahedra"])
+@pytest.mark.parametrize("precision,rel", [("f64", 1e-10), ("f32", 5e-5)])
+def test_gsis_steps_on_simplices(make, precision, rel):
+    """GSIS outer steps on prisms and tetrahedra (the synthetic solve's gradients over the
+    node-sharing stencils, LU-SGS over the greedy colours) from a perturbed state."""
+    if make == "hybrid":
+        p = wl.unstructured_cavity(n=6, nv=12, Kn=0.2, lid=0.3, hybrid=0.5)
+    else:
+        p = wl.tet_box(n=3, nv=8, Kn=0.2, wall_speed=0.3)
+    W = wl.perturbed_state(p, seed=7, amp=0.03)
+    g = gsis.Solver(p, precision=precision, mode="gsis", init_W=W, kinetic_presteps=0, n_sweeps=2, macro_steps=40,
+                    macro_tol=0.0)
+    o = Oracle(p, W0=W, mode=0, n_sweeps=2, macro_steps=40, macro_tol=0.0)
+    for it in range(3):
+        g.step()
+        o.step()
+        scaled_close(g.W()[:, [0, 1, 2, 4]], o.W()[:, [0, 1, 2, 4]], rel, f"{precision} {make} GSIS W, step {it}")
+    assert g.stats()[1] == o.macro_iters
+    g.close()
+
+
+def test_gsis_converges_on_a_hybrid_cavity():
+    """The hybrid cavity (16^2 squares, half of them split into triangles) at Kn 0.2, where the
+    synthetic solve needs the jump term of its viscous face gradients, 40 GSIS steps on the GPU in
+    FP64 (eps reaches its rounding floor of 1e-10 .. 1e-9 after about 30): the oracle's converged
+    state within 1e-7 of scale."""
+    p = wl.unstructured_cavity(n=16, nv=16, Kn=0.2, lid=0.3, hybrid=0.5)
+    g = gsis.Solver(p, precision="f64", mode="gsis", kinetic_presteps=0, n_sweeps=4)
+    o = Oracle(p, mode=0, n_sweeps=4, nthreads=8)
+    eps = []
+    for s in (g, o):
+        for _ in range(40):
+            e = s.step()
+        eps.append(e)
+    Wg, Wo = g.W(), o.W()
+    g.close()
+    assert max(eps) < 5e-9
+    scaled_close(Wg[:, [0, 1, 2, 4]], Wo[:, [0, 1, 2, 4]], 1e-7, "converged hybrid cavity GSIS W")

@@ -184,15 +184,15 @@ def test_unstructured_velocity_sets_are_validated():
 def test_unstructured_meshes_are_validated():
     """Unstructured cells through gsis_footprint_bytes (the same checks and set-up as
     gsis_create): shapes and shared sides accepted; a side neither shared nor on a patch, a
-    shared side carrying a patch, a node id out of range, a PERIODIC patch not normal to z and
-    GSIS on prisms or tetrahedra are refused."""
+    shared side carrying a patch, a node id out of range and a PERIODIC patch not normal to z
+    are refused; GSIS runs on every shape."""
     GSIS_E_UNSUPPORTED = -7
     good = (wl.tet_box(n=2, nv=8), wl.unstructured_cavity(n=4, nv=8), wl.as_unstructured(wl.cavity(n=6, nv=8)),
             wl.as_unstructured(wl.cylinder(n_r=4, n_theta=8, nv=8)))
     for p in good:
         assert code(p, mode=gsis.MODE_DVM) == gsis.GSIS_OK, p.name
-    assert code(good[2]) == gsis.GSIS_OK and code(good[3]) == gsis.GSIS_OK   # hexahedra: GSIS too
-    assert code(good[0]) == GSIS_E_UNSUPPORTED and code(good[1]) == GSIS_E_UNSUPPORTED
+    for p in good:
+        assert code(p) == gsis.GSIS_OK, p.name
     p = wl.tet_box(n=2, nv=8)
     q = dataclasses.replace(p, upatch=p.upatch.copy())
     c, s = np.argwhere(q.upatch >= 0)[0]
@@ -224,3 +224,12 @@ def test_relaxed_update_only_on_general_meshes_and_in_range():
     assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), relax=0.5) == 0
     assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), relax=1.5) == GSIS_E_INVALID
     assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), relax=-0.1) == GSIS_E_INVALID
+
+
+def test_viscous_jump_weight_values():
+    assert code(wl.cavity(n=6, nv=8), visc_jump=0.25) == gsis.GSIS_E_UNSUPPORTED
+    assert code(wl.cavity(n=6, nv=8), visc_jump=0.0) == 0
+    assert code(wl.cavity(n=6, nv=8), visc_jump=-1.0) == 0
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), visc_jump=0.5) == 0
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), visc_jump=1.5) == GSIS_E_INVALID
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), visc_jump=float("nan")) == GSIS_E_INVALID
