@@ -635,17 +635,19 @@ def run_serve(args):
                                     tol=1e-6, max_steps=150)
     budget = int(0.5 * torch.cuda.mem_get_info()[0])
     lines = {}
-    for name, slots, prec, arrivals in (("batched_f32", args.serve_slots, "f32", True),
-                                        ("sequential_f32", 1, "f32", False), ("sequential_f64", 1, "f64", False)):
+    for name, slots, prec, arrivals, graphs in (("batched_f32", args.serve_slots, "f32", True, False),
+                                                ("sequential_f32", 1, "f32", False, False),
+                                                ("sequential_f64", 1, "f64", False, False)):
         rs = reqs if arrivals else [serving.Request(r.rid, r.problem, 0.0, r.tol, r.max_steps, r.stall_steps, r.opts)
                                     for r in reqs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = serving.Server(budget, slots=slots, precision=prec).run(rs)
+        res = serving.Server(budget, slots=slots, precision=prec, graphs=graphs).run(rs)
         wall = time.perf_counter() - t0
         summ = serving.summary(res, wall)
         summ["slots"] = slots
         summ["precision"] = prec
+        summ["cuda_graphs"] = graphs
         summ["failures"] = [{"rid": r.rid, "problem": reqs[r.rid].problem.name, "opts": reqs[r.rid].opts,
                              "error": r.error} for r in res if r is not None and r.error]
         lines[name] = summ

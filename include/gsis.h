@@ -235,6 +235,13 @@ typedef struct {
                            prisms, pyramids or tetrahedra, 0 on others; a value in [0, 1] applies
                            on every general block.  GSIS_E_INVALID above 1 or NaN;
                            GSIS_E_UNSUPPORTED above 0 on rectilinear blocks. */
+  int capture_graphs;   /* 1: each outer step runs as a CUDA graph, captured from the solver's
+                           stream on the first step of each mode and state buffer (two alternate)
+                           and replayed afterwards: one launch per step on the host instead of one
+                           per kernel (about 4,500 per GSIS step on a general mesh).  Results are
+                           identical to direct launches.  Steps launch directly while profiling
+                           (gsis_profile) or with velocity shards, and for good if a capture fails;
+                           gsis_set_f drops the graphs.  Default 0; GSIS_E_INVALID unless 0 or 1. */
 } gsis_options;
 
 typedef struct gsis_solver *gsis_handle;
@@ -336,6 +343,11 @@ int gsis_profile(gsis_handle h, int enable, int reset, double *ms, int n, int *s
 
 /* Counters: outer iterations run so far, inner synthetic steps of the last outer step. */
 int gsis_stats(gsis_handle h, int *outer_total, int *macro_iters_last);
+
+/* Step graphs (gsis_options.capture_graphs): the number of captured outer-step graphs the solver
+ * holds (0 before the first captured step or without the option), or -1 once a capture has
+ * failed and the solver launches its steps directly.  No GPU work; 0 for a NULL handle. */
+int gsis_graphs(gsis_handle h);
 
 /* Allocation-free velocity moments of a VDF held by the caller (no counterpart in the paper).
  * For callers that cannot allocate device memory where they need moments: code running inside

@@ -152,6 +152,42 @@ struct gsis_solver {
   size_t kin_smem = 0;     // dynamic shared memory of the kinetic kernel (0 with a global ring)
   size_t kin_gstride = 0;  // bytes of global ring scratch per velocity block (0: shared memory)
   void *d_kscratch = nullptr;
+  // CUDA graphs of one outer step (opt.capture_graphs): one per mode and current state buffer
+  // (the step swaps the state buffers, so two alternate), captured on first use and replayed
+  struct StepGraph {
+    int mode;
+    const double *wstate;
+    cudaGraphExec_t exec;
+    int launches;
+  };
+  std::vector<StepGraph> graphs;
+  bool graphs_off = false;  // a capture failed: every later step launches directly
+  // graphs are captured on and launched into a stream of the solver's own (the caller's stream
+  // may be the legacy default stream, which cannot be captured), ordered after the caller's
+  // earlier work and before its later work by two events
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {};
+  void drop_graphs() {
+    for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
+  void release_graphs() {
+    drop_graphs();
+    for (auto &e : gev)
+      if (e) cudaEventDestroy(e);
+    if (gstream) cudaStreamDestroy(gstream);
+    gstream = nullptr;
+    gev[0] = gev[1] = nullptr;
+  }
+  // the caller's stream -> the graph stream, launch, graph stream -> the caller's stream
+  int launch_graph(cudaGraphExec_t exec) {
+    int rc = cuda(cudaEventRecord(gev[0], stream), "event");
+    if (!rc) rc = cuda(cudaStreamWaitEvent(gstream, gev[0], 0), "stream wait");
+    if (!rc) rc = cuda(cudaGraphLaunch(exec, gstream), "graph launch");
+    if (!rc) rc = cuda(cudaEventRecord(gev[1], gstream), "event");
+    if (!rc) rc = cuda(cudaStreamWaitEvent(stream, gev[1], 0), "stream wait");
+    return rc;
+  }
   // profiling
   bool profiling = false;
   cudaEvent_t ev[6] = {};
@@ -194,6 +230,8 @@ struct gsis_solver {
   }
 
   void release() {
+    if (!graphs.empty()) cudaStreamSynchronize(stream);
+    release_graphs();
     if (pin) {
       cudaFreeHost(pin);
       pin = nullptr;
@@ -577,7 +615,67 @@ struct gsis_solver {
 
   int enqueue_step(int mode) {
     if (pending) return fail(GSIS_E_INVALID, "a step is pending: call gsis_step_wait first");
-    return GSIS_DISPATCH(prec, (step_impl<T, S>(mode)));
+    // direct launches: no graphs asked for, profiling (the phase events are recorded per step),
+    // velocity shards (the host all-reduce callback runs inside the step) or a failed capture
+    if (!opt.capture_graphs || profiling || opt.shard_count > 1 || graphs_off)
+      return GSIS_DISPATCH(prec, (step_impl<T, S>(mode)));
+    for (const StepGraph &g : graphs)
+      if (g.mode == mode && g.wstate == d_Wstate) {
+        // the host side of step_impl: the read-back word the step may leave alone, the buffer swap
+        pin->iters = 0;
+        int rc = launch_graph(g.exec);
+        if (rc) return rc;
+        std::swap(d_Wstate, d_Wnew);
+        pending = true;
+        pending_mode = mode;
+        pending_launches = g.launches;
+        return GSIS_OK;
+      }
+    cudaError_t ce = cudaSuccess;
+    if (!gstream) {
+      ce = cudaStreamCreateWithFlags(&gstream, cudaStreamNonBlocking);
+      for (auto &e : gev)
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    }
+    double *ws = d_Wstate, *wn = d_Wnew;
+    cudaStream_t user = stream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = GSIS_OK;
+    const char *where = "stream or event creation";
+    if (ce == cudaSuccess) {
+      where = "begin capture";
+      ce = cudaStreamBeginCapture(gstream, cudaStreamCaptureModeThreadLocal);
+    }
+    if (ce == cudaSuccess) {
+      stream = gstream;  // step_impl enqueues on the capturing stream
+      rc = GSIS_DISPATCH(prec, (step_impl<T, S>(mode)));
+      stream = user;
+      where = "end capture";
+      ce = cudaStreamEndCapture(gstream, &graph);
+      if (!rc && ce == cudaSuccess && graph) {
+        where = "instantiate";
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+      }
+      if (graph) cudaGraphDestroy(graph);
+    }
+    if (rc || ce != cudaSuccess || !exec) {
+      // nothing of the captured step ran: undo its host bookkeeping and launch it directly
+      const std::string why = rc ? last_error : std::string(where) + ": " + cudaGetErrorString(ce);
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      d_Wstate = ws;
+      d_Wnew = wn;
+      pending = false;
+      graphs_off = true;
+      rc = GSIS_DISPATCH(prec, (step_impl<T, S>(mode)));
+      if (!rc) last_error = "CUDA graph capture failed, steps launch directly (" + why + ")";
+      return rc;
+    }
+    graphs.push_back({mode, ws, exec, pending_launches});
+    rc = launch_graph(exec);
+    if (rc) pending = false;
+    return rc;
   }
   int step(int mode) {
     int rc = enqueue_step(mode);
@@ -686,6 +784,7 @@ int validate(const gsis_mesh *m, const gsis_vgrid *vg, const gsis_gas *g, double
   if (o->euler_presteps < 0) { why = "euler_presteps must be >= 0"; return GSIS_E_INVALID; }
   if (o->wall_flux != GSIS_WALL_EQ && o->wall_flux != GSIS_WALL_G13) { why = "bad wall_flux"; return GSIS_E_INVALID; }
   if (o->positive_faces != 0 && o->positive_faces != 1) { why = "positive_faces must be 0 or 1"; return GSIS_E_INVALID; }
+  if (o->capture_graphs != 0 && o->capture_graphs != 1) { why = "capture_graphs must be 0 or 1"; return GSIS_E_INVALID; }
   if (!(o->relax >= 0.0 && o->relax <= 1.0)) { why = "relax must be in [0, 1]"; return GSIS_E_INVALID; }
   if (!(o->visc_jump <= 1.0)) { why = "visc_jump must be at most 1"; return GSIS_E_INVALID; }
   if (o->shard_count > 1 && (o->shard_index < 0 || o->shard_index >= o->shard_count || !o->allreduce)) {
@@ -2114,6 +2213,7 @@ extern "C" int gsis_set_f(gsis_handle h, const double *f0, const double *f1) {
   cudaFree(tmp);
   cudaFree(canon);
   if (rc) return rc;
+  h->drop_graphs();  // the step's arguments include the new f's mass reference
   return GSIS_DISPATCH(h->prec, (h->state_from_f<T, S>()));
 }
 
@@ -2139,6 +2239,11 @@ extern "C" int gsis_stats(gsis_handle h, int *outer_total, int *macro_iters_last
   if (outer_total) *outer_total = h->outer_total;
   if (macro_iters_last) *macro_iters_last = h->macro_iters_last;
   return GSIS_OK;
+}
+
+extern "C" int gsis_graphs(gsis_handle h) {
+  if (!h) return 0;
+  return h->graphs_off ? -1 : (int)h->graphs.size();
 }
 
 extern "C" int gsis_destroy(gsis_handle h) {

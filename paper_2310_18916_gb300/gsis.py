@@ -52,13 +52,14 @@ class Options(C.Structure):
                 ("shard_index", C.c_int), ("allreduce", ALLREDUCE_FN), ("allreduce_ctx", C.c_void_p),
                 ("kinetic_ring", C.c_int), ("euler_presteps", C.c_int),
                 ("wall_flux", C.c_int), ("positive_faces", C.c_int),
-                ("relax", C.c_double), ("visc_jump", C.c_double)]
+                ("relax", C.c_double), ("visc_jump", C.c_double), ("capture_graphs", C.c_int)]
 
 
 _lib = None
 SYMBOLS = ("gsis_default_options", "gsis_footprint_bytes", "gsis_create", "gsis_iterate", "gsis_step_async",
            "gsis_step_wait", "gsis_moments",
            "gsis_residual", "gsis_nwall", "gsis_wall", "gsis_wall_loads", "gsis_kinetic_flux_sum", "gsis_get_f", "gsis_set_f", "gsis_stats",
+           "gsis_graphs",
            "gsis_destroy", "gsis_last_error", "gsis_profile", "gsis_vdf_moments_noalloc", "gsis_selftest_wait_timeout")
 
 
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH):
     L.gsis_get_f.argtypes = [P, D, D]
     L.gsis_set_f.argtypes = [P, D, D]
     L.gsis_stats.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.gsis_graphs.argtypes = [P]
     L.gsis_profile.argtypes = [P, C.c_int, C.c_int, D, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.gsis_vdf_moments_noalloc.argtypes = [P, P, C.c_int, C.c_int, P, P]
     L.gsis_destroy.argtypes = [P]
@@ -327,6 +329,10 @@ class Solver:
         a, b = C.c_int(), C.c_int()
         self._check(load().gsis_stats(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def graphs(self):
+        """Captured outer-step graphs held (-1: a capture failed, steps launch directly)."""
+        return load().gsis_graphs(self.h)
 
 
 _NO_EXCHANGE = ALLREDUCE_FN(lambda ptr, count, stream, ctx: 1)  # footprints never exchange

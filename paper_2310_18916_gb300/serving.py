@@ -83,13 +83,16 @@ class Server:
     make_solver(problem, precision, macro_sms, stream, **opts) / footprint(problem, precision,
     **opts): the GPU solver and its footprint, opts the request's solver options; replaceable (the
     scheduling logic is tested with fakes).
+    graphs: every solve runs its outer steps as captured CUDA graphs (gsis_options.capture_graphs)
+    unless its request's options say otherwise.
     """
 
     def __init__(self, memory_budget, slots=4, precision="f32", nsm=None, make_solver=None, footprint=None,
-                 new_stream=None, clock=time.perf_counter, idle=lambda s: time.sleep(min(s, 0.01))):
+                 new_stream=None, clock=time.perf_counter, idle=lambda s: time.sleep(min(s, 0.01)), graphs=False):
         self.memory_budget = int(memory_budget)
         self.slots = int(slots)
         self.precision = precision
+        self.graphs = bool(graphs)
         if nsm is None:
             import torch
             nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -122,7 +125,10 @@ class Server:
                     break
                 queue.pop(0)
                 stream = self._new_stream()
-                solver = self._make(req.problem, self.precision, self.macro_sms, stream, **req.opts)
+                opts = dict(req.opts)
+                if self.graphs:
+                    opts.setdefault("capture_graphs", 1)
+                solver = self._make(req.problem, self.precision, self.macro_sms, stream, **opts)
                 used += need
                 running.append(_Running(req, solver, stream, need, self._clock() - t0))
             if not running:

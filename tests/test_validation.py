@@ -233,3 +233,9 @@ def test_viscous_jump_weight_values():
     assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), visc_jump=0.5) == 0
     assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), visc_jump=1.5) == GSIS_E_INVALID
     assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), visc_jump=float("nan")) == GSIS_E_INVALID
+
+
+def test_capture_graphs_values():
+    assert code(wl.cavity(n=6, nv=8), capture_graphs=1) == 0
+    assert code(wl.cylinder(n_r=4, n_theta=8, nv=8), capture_graphs=1) == 0
+    assert code(wl.cavity(n=6, nv=8), capture_graphs=2) == GSIS_E_INVALID
