@@ -171,9 +171,11 @@ __device__ __forceinline__ bool nonneg_lt(float a, float b) { return a < b; }
 // E = e^2 / D2^2 (the same on both faces, |r_lo| = |r_hi|) the function (y^2 + 2y + E) /
 // (y^2 + y + 2 + E) rises while y < 2 + sqrt(8 + E) and exceeds 1 exactly when y > 2.
 template <typename T, int NACT>
-__device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const T *rlo, const T *rhi, T eps2) {
+__device__ __forceinline__ void venkat_parts(T fi, T fmax, T fmin, const T *gr, const T *rlo, const T *rhi, T eps2,
+                                             T &bn, T &bd) {
   const T dp = fmax - fi, dn = fmin - fi;
-  T bn = (T)1, bd = (T)1;
+  bn = (T)1;
+  bd = (T)1;
 #pragma unroll
   for (int a = 0; a < NACT; ++a) {
     const T dh = gr[a] * rhi[a], dl = gr[a] * rlo[a];
@@ -187,6 +189,11 @@ __device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const
     const T d = d2 * ((T)2 * d2 + dm) + dm2;
     if (nonneg_lt(n * bd, bn * d)) { bn = n; bd = d; }
   }
+}
+template <typename T, int NACT>
+__device__ __forceinline__ T venkat_phi(T fi, T fmax, T fmin, const T *gr, const T *rlo, const T *rhi, T eps2) {
+  T bn, bd;
+  venkat_parts<T, NACT>(fi, fmax, fmin, gr, rlo, rhi, eps2, bn, bd);
   return ddiv(bn, bd);
 }
 
@@ -569,9 +576,26 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
           invh[a] = gc.invh;
         }
       }
-      T phi[NV];
+      // the implicit diagonal D = 1/dt + 1/tau + the outflow coefficients, then the limiter.  In
+      // FP64 one reciprocal r = 1 / (bd D) gives both phi = bn / bd = bn D r and the update's
+      // 1 / D = bd r (an FP64 division costs several FP64 instructions on this GPU)
+      T D = st[15];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) phi[q] = venkat_phi<T, NACT>(fi[q], fmax[q], fmin[q], gr[q], rlo, rhi, K3 * V);
+      for (int a = 0; a < NACT; ++a) D += axi[a] * invh[a];
+      T phi[NV], invD[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        if constexpr (std::is_same<T, double>::value) {
+          T bn, bd;
+          venkat_parts<T, NACT>(fi[q], fmax[q], fmin[q], gr[q], rlo, rhi, K3 * V, bn, bd);
+          const T r = (T)1 / (bd * D);
+          phi[q] = bn * D * r;
+          invD[q] = bd * r;
+        } else {
+          phi[q] = venkat_phi<T, NACT>(fi[q], fmax[q], fmin[q], gr[q], rlo, rhi, K3 * V);
+          invD[q] = (T)0;
+        }
+      }
       // reference distributions of the state W^n
       const T cx = xi[0] - st[0], cy = xi[1] - st[1], cz = xi[2] - st[2];
       const T c2 = cx * cx + cy * cy + cz * cz;
@@ -588,12 +612,10 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
       T acc[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) acc[q] = (g[q] - fi[q]) * st[11];
-      T D = st[15];
       T fout[NV][3];
 #pragma unroll
       for (int a = 0; a < NACT; ++a) {
         const T k = axi[a] * invh[a];
-        D += k;
         T rho_w = (T)0;
         if (nb[2 * a] < 0) {
           // upwind boundary: the natural transverse index of the wall face
@@ -610,7 +632,8 @@ __global__ void kinetic_kernel(const KinArgs<T, S> A) {
       T df[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        df[q] = ddiv(acc[q], D);
+        if constexpr (std::is_same<T, double>::value) df[q] = acc[q] * invD[q];
+        else df[q] = ddiv(acc[q], D);
         // relative storage keeps the deviation from the reference: M_t for f0, (d_r Tr_n / 4) M_t for f1
         const T ref = q == 0 ? mw : st[NV == 2 ? 29 : 0] * mw;
         Fio<T, S>::st(F[q] + (size_t)cell * VB + lane, StoredRelative<S>::value ? fi[q] + df[q] - ref : fi[q] + df[q]);
