@@ -53,9 +53,9 @@ KINETIC_FLOPS_PER_POINT_2D = 103
 # scratch; FP32 and BF16: in shared memory) and scaled by the 4x cells: the kinetic kernel's
 # traffic is per point, the synthetic solve's per cell (profiles/dram_bytes_cavity64x32.md).
 DRAM_BYTES_PER_LAUNCH = {
-    ("kinetic_kernel", "f64"): (4 * (1.0845e9 + 1.1232e9), "8cb311fbcc54"),
-    ("kinetic_kernel", "f32"): (4 * (0.5405e9 + 0.4760e9), "8cb311fbcc54"),
-    ("kinetic_kernel", "bf16"): (4 * (0.2706e9 + 0.2124e9), "8cb311fbcc54"),
+    ("kinetic_kernel", "f64"): (4 * (1.0845e9 + 1.1232e9), "03162e244003"),
+    ("kinetic_kernel", "f32"): (4 * (0.5405e9 + 0.4760e9), "03162e244003"),
+    ("kinetic_kernel", "bf16"): (4 * (0.2706e9 + 0.2124e9), "03162e244003"),
     ("macro_kernel", "f64"): (4 * (3.79e6 + 0.02e6), "02e3bb610d02"),
 }
 KERNEL_SOURCES = {"kinetic_kernel": "kinetic.cu", "moments_kernel": "kinetic.cu", "macro_kernel": "macro.cu"}

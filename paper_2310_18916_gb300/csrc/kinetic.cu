@@ -11,8 +11,9 @@
 //   - solves the point-implicit delta form with the first-order upwind implicit operator,
 //     taking the inflow value "face value + upwind increment" from the previous colour
 //     (exact in one pass on a rectilinear grid: every inflow neighbour has a lower colour),
-//   - writes f^{n+1/2} in place and reduces, over its 32 velocities, the 13 raw moments about
-//     the state velocity and the moments of its outflow face fluxes.
+//   - writes f^{n+1/2} in place, and the outgoing flux moments of its wall faces.
+// The velocity moments of f^{n+1/2} are a separate streaming pass (moments_kernel, and
+// moments_origin_kernel for FP64 storage on tensor-product grids).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
