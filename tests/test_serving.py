@@ -153,3 +153,21 @@ def test_a_failing_solve_leaves_with_its_error_and_the_others_finish():
     assert res[0].converged and res[2].converged and not res[0].error
     s = serving.summary(res, 1.0)
     assert s["failed"] == 1 and s["served"] == 2 and s["converged"] == 2
+
+
+def test_graphs_option_reaches_every_solver_unless_the_request_sets_it():
+    FakeSolver.log = []
+    clock = FakeClock()
+    seen = []
+
+    def make(p, prec, sms, st, **opts):
+        seen.append((p["name"], opts.get("capture_graphs")))
+        return FakeSolver(p, clock, 0.01)
+
+    srv = serving.Server(100, slots=2, nsm=152, make_solver=make, footprint=lambda p, prec, **o: p["bytes"],
+                         new_stream=lambda: None, clock=clock,
+                         idle=lambda s: setattr(clock, "t", clock.t + max(s, 1e-3)), graphs=True)
+    reqs = [serving.Request(0, {"name": "a", "bytes": 10}, 0.0, tol=1.5 * 2 ** -5),
+            serving.Request(1, {"name": "b", "bytes": 10}, 0.0, tol=1.5 * 2 ** -5, opts={"capture_graphs": 0})]
+    srv.run(reqs)
+    assert sorted(seen) == [("a", 1), ("b", 0)]
