@@ -107,3 +107,18 @@ def test_gsis_converges_on_a_hybrid_cavity():
     g.close()
     assert max(eps) < 5e-9
     scaled_close(Wg[:, [0, 1, 2, 4]], Wo[:, [0, 1, 2, 4]], 1e-7, "converged hybrid cavity GSIS W")
+
+
+def test_rykov_gsis_steps_on_prisms_fp64():
+    """The diatomic Rykov gas (two reduced VDFs, the rotational energy equation in the synthetic
+    solve) in GSIS on the hybrid prism/hexahedron cavity, with the viscous jump term."""
+    p = wl.as_rykov(wl.unstructured_cavity(n=6, nv=10, Kn=0.2, lid=0.3, hybrid=0.5))
+    W = wl.perturbed_state(p, seed=8, amp=0.03)
+    g = gsis.Solver(p, precision="f64", mode="gsis", init_W=W, kinetic_presteps=0, n_sweeps=2, macro_steps=40,
+                    macro_tol=0.0)
+    o = Oracle(p, W0=W, mode=0, n_sweeps=2, macro_steps=40, macro_tol=0.0)
+    for it in range(2):
+        g.step()
+        o.step()
+        scaled_close(g.W()[:, [0, 1, 2, 4, 5]], o.W()[:, [0, 1, 2, 4, 5]], 1e-10, f"Rykov prism GSIS W, step {it}")
+    g.close()
