@@ -379,6 +379,12 @@ BODIES = {
     "sphere_gsis": dict(kind="sphere", n=(32, 24, 48), nv=48, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0,
                         clustered=True, mode="continuation", stages=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0),
                         euler_presteps=300, relax=0.5),
+    # GSIS on an unstructured mesh with simplices: the lid-driven cavity of 32 x 32 squares, the
+    # half with x < 1/2 split into two triangles each, extruded one layer (prisms and hexahedra,
+    # 1536 cells), 32^3 velocities, Kn 0.1, four colour passes (greedy colours are far from the
+    # upwind order; with two the outer iteration stalls)
+    "hybrid_cavity": dict(kind="hybrid", n=32, nv=32, vmax=5.0, lid=0.16, Kn=0.1, hybrid=0.5, mode="gsis",
+                          euler_presteps=0, n_sweeps=4),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }
@@ -394,6 +400,9 @@ def body_problem(name, Ma=None):
     if b["kind"] == "capsule":
         return wl.capsule(n_r=b["n"][0], n_pol=b["n"][1], n_az=b["n"][2], nv=b["nv"], R_out=b["R_out"],
                           first=b["first"], Ma=b["Ma"], Kn=b["Kn"], T_w=b["T_w"], vmax=b["vmax"])
+    if b["kind"] == "hybrid":
+        return wl.unstructured_cavity(n=b["n"], nv=b["nv"], vmax=b["vmax"], lid=b["lid"], Kn=b["Kn"],
+                                      hybrid=b["hybrid"])
     if b["kind"] == "sphere":
         p = wl.sphere(n_r=b["n"][0], n_pol=b["n"][1], n_az=b["n"][2], nv=b["nv"], R=0.5, R_out=b["R_out"],
                       first=b["first"], Ma=b["Ma"], Kn=b["Kn"], vmax=b["vmax"])
@@ -424,7 +433,8 @@ def run_body(args):
     b = BODIES[args.body]
     mode = b.get("mode", "dvm")
     if mode == "gsis":
-        kw = dict(precision=args.precision, mode="gsis", n_sweeps=BODY_SWEEPS, euler_presteps=b["euler_presteps"])
+        kw = dict(precision=args.precision, mode="gsis", n_sweeps=b.get("n_sweeps", BODY_SWEEPS),
+                  euler_presteps=b["euler_presteps"])
     else:
         kw = dict(precision=args.precision, mode="dvm", n_sweeps=BODY_SWEEPS, kin_inv_dt=BODY_INV_DT)
     if args.graphs:
@@ -471,13 +481,14 @@ def run_body(args):
     ms = ms_total / args.steps
     line = {
         "metric": f"phase-space updates/s ({'GSIS outer step' if mode == 'gsis' else 'kinetic iteration'}, "
-                  f"{b['kind']} O-grid)", "value": pts * args.steps / (ms_total / 1e3),
+                  f"{b['kind']} {'mesh' if p.ucells is not None else 'O-grid'})",
+        "value": pts * args.steps / (ms_total / 1e3),
         "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "f64" else "f32", "data": "synthetic",
         "config": {"workload": f"{p.name}: {BODIES[args.body]}", "precision": f"{args.precision} VDF",
                    "cuda_graphs": (graphs_held if args.graphs else False),
-                   "cells": p.ncells, "velocities": p.nvel, "vdfs": nvdf, "points": pts, "n_sweeps": BODY_SWEEPS,
+                   "cells": p.ncells, "velocities": p.nvel, "vdfs": nvdf, "points": pts, "n_sweeps": kw["n_sweeps"],
                    "mode": mode, "kin_inv_dt": kw.get("kin_inv_dt", 0.0),
                    "euler_presteps": kw.get("euler_presteps", 0), "parallelism": "1 GPU",
                    "l2": f"inputs larger than L2 (VDF {pts * sbytes / 1e9:.2f} GB)", "eps_last": eps,
@@ -490,7 +501,8 @@ def run_body(args):
                      "traffic": None, "algorithmic_bytes_per_launch": 2 * sbytes * pts, "launch_ms": kin_ms,
                      "share_of_step": kin_ms / ms},
         "e2e": {"value": pts * args.steps / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": (p.nodes.nbytes + 6 * p.vx.nbytes + p.W0.nbytes) / args.steps,
+                "h2d_bytes_per_step": ((p.unodes.nbytes + p.ucells.nbytes if p.ucells is not None else p.nodes.nbytes)
+                                       + 6 * p.vx.nbytes + (p.W0.nbytes if p.W0 is not None else 0)) / args.steps,
                 "d2h_bytes_per_step": W2.nbytes, "seconds": e2e_s,
                 "includes": "create from host inputs, steps, per-step state read, destroy"},
         "gpu_launches": launches / max(nsteps, 1) * args.steps,
@@ -614,8 +626,9 @@ def body_oracle_sample(name):
     p.vpoints = None
     cores = os.cpu_count() or 1
     if b.get("mode", "dvm") == "gsis":
-        o = Oracle(p, mode=0, n_sweeps=BODY_SWEEPS, nthreads=cores)
-        o.euler_presteps(b["euler_presteps"])
+        o = Oracle(p, mode=0, n_sweeps=b.get("n_sweeps", BODY_SWEEPS), nthreads=cores)
+        if b["euler_presteps"]:
+            o.euler_presteps(b["euler_presteps"])
         what = "GSIS outer step (300 inner synthetic steps at most)"
     else:
         o = Oracle(p, mode=1, n_sweeps=BODY_SWEEPS, kin_inv_dt=BODY_INV_DT, nthreads=cores)
