@@ -379,12 +379,11 @@ BODIES = {
     "sphere_gsis": dict(kind="sphere", n=(32, 24, 48), nv=48, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0,
                         clustered=True, mode="continuation", stages=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0),
                         euler_presteps=300, relax=0.5),
-    # GSIS on an unstructured mesh with simplices: the lid-driven cavity of 32 x 32 squares, the
+    # GSIS on an unstructured mesh with simplices: the lid-driven cavity of 64 x 64 squares, the
     # half with x < 1/2 split into two triangles each, extruded one layer (prisms and hexahedra,
-    # 1536 cells), 32^3 velocities, Kn 0.1, four colour passes (greedy colours are far from the
-    # upwind order; with two the outer iteration stalls)
-    "hybrid_cavity": dict(kind="hybrid", n=32, nv=32, vmax=5.0, lid=0.16, Kn=0.1, hybrid=0.5, mode="gsis",
-                          euler_presteps=0, n_sweeps=4),
+    # 6144 cells), 32^3 velocities, Kn 0.1, two colour passes in each octant's upwind order
+    "hybrid_cavity": dict(kind="hybrid", n=64, nv=32, vmax=5.0, lid=0.16, Kn=0.1, hybrid=0.5, mode="gsis",
+                          euler_presteps=0, n_sweeps=2),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }

@@ -94,9 +94,12 @@ typedef struct {
    *               mesh one cell layer thick in z (faces normal to z): no transport across them
    *               and no z gradient, the unstructured form of a one-cell periodic axis; AXIS
    *               faces carry no flux.
-   * Cells are swept in the colours of a greedy colouring of the face graph (cells in index
-   * order, each taking the smallest colour none of its neighbours holds): n_sweeps passes in
-   * the kinetic step, the synthetic solve's LU-SGS over the same colours.  Least-squares
+   * The kinetic step sweeps each velocity octant (signs d) in its own upwind order: cells ranked
+   * by the mean over their distinct nodes of ((d_x x) + (d_y y)) + (d_z z), ties by index, each
+   * cell's colour one more than the largest colour of its face neighbours ranked before it;
+   * n_sweeps passes, colour by colour.  The synthetic solve's LU-SGS runs over a greedy
+   * colouring of the face graph (cells in index order, each taking the smallest colour none of
+   * its neighbours holds).  Least-squares
    * gradients: over the face neighbours on a mesh of hexahedra, over every node-sharing cell on
    * a mesh with prisms, pyramids or tetrahedra; the synthetic solve takes its gradients over
    * the same stencils.  Both modes and the Euler presteps run on every shape.  Faces must be

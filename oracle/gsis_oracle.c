@@ -1604,13 +1604,57 @@ int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const o
   s->corder = (int *)malloc(sizeof(int) * 8 * (size_t)nc);
   if (!s->corder) { orc_destroy(s); return ORC_E_OOM; }
   if (s->colour) {
-    /* every octant sweeps the cells colour by colour, in index order within a colour */
+    /* unstructured meshes: each octant (signs d of its velocities) ranks the cells by the mean over
+       their distinct nodes of ((d_x x) + (d_y y)) + (d_z z), ties by index, which places a cell
+       after the cells its flow comes from, as the hyperplanes do on a structured block.  A cell's
+       sweep colour is one more than the largest colour of its face neighbours ranked before it (0
+       without one); the octant sweeps colour by colour, in index order within a colour */
+    double *key = (double *)malloc(sizeof(double) * nc);
+    int *rank = (int *)malloc(sizeof(int) * nc), *byk = (int *)malloc(sizeof(int) * nc);
+    int *kc = (int *)malloc(sizeof(int) * nc);
+    if (!key || !rank || !byk || !kc) { free(key); free(rank); free(byk); free(kc); orc_destroy(s); return ORC_E_OOM; }
     for (int oct = 0; oct < 8; ++oct) {
+      double d[3] = {oct & 1 ? -1.0 : 1.0, oct & 2 ? -1.0 : 1.0, oct & 4 ? -1.0 : 1.0};
+      for (int c = 0; c < nc; ++c) {
+        const int *ids = m->cells + 8 * (size_t)c;
+        double sum = 0.0;
+        int cnt = 0;
+        for (int t = 0; t < 8; ++t) {
+          int dup = 0;
+          for (int u = 0; u < t; ++u) dup |= ids[u] == ids[t];
+          if (dup) continue;
+          const double *x = m->unodes + 3 * (size_t)ids[t];
+          sum += ((d[0] * x[0]) + (d[1] * x[1])) + (d[2] * x[2]);
+          ++cnt;
+        }
+        key[c] = sum / cnt;
+        byk[c] = c;
+      }
+      for (int a = 1; a < nc; ++a) { /* insertion sort by (key, index) */
+        int x = byk[a], b = a;
+        while (b > 0 && (key[byk[b - 1]] > key[x] || (key[byk[b - 1]] == key[x] && byk[b - 1] > x))) {
+          byk[b] = byk[b - 1];
+          --b;
+        }
+        byk[b] = x;
+      }
+      for (int r = 0; r < nc; ++r) rank[byk[r]] = r;
+      int ncol = 0;
+      for (int r = 0; r < nc; ++r) {
+        int c = byk[r], k = 0;
+        for (int side = 0; side < 6; ++side) {
+          int j = s->nb[6 * c + side];
+          if (j >= 0 && rank[j] < r && kc[j] + 1 > k) k = kc[j] + 1;
+        }
+        kc[c] = k;
+        if (k + 1 > ncol) ncol = k + 1;
+      }
       int t = 0;
-      for (int col = 0; col < s->ncolour; ++col)
+      for (int col = 0; col < ncol; ++col)
         for (int i = 0; i < nc; ++i)
-          if (s->colour[i] == col) s->corder[(size_t)oct * nc + t++] = i;
+          if (kc[i] == col) s->corder[(size_t)oct * nc + t++] = i;
     }
+    free(key); free(rank); free(byk); free(kc);
   } else {
     int ncol = s->ni + s->nj + s->nk - 2;
     for (int oct = 0; oct < 8; ++oct) {

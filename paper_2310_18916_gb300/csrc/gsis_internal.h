@@ -98,7 +98,8 @@ struct KinArgs {
   const AxisCell<T> *ax[3];
   const T *vel;          // [slot][4]: xi_x, xi_y, xi_z, w
   const int8_t *boct;    // octant of each block: bit a set => xi_a < 0
-  const int *col_off;    // [ncol+1]
+  const int *col_off;    // [ncol+1], or per octant [8][col_stride] when col_stride > 0
+  int col_stride;        // 0: one colour list for every octant (general kernel)
   const EntryInfo *entry;  // [entry] neighbour positions and transverse indices
   const int4 *natcell;     // [octant][entry]: cell index and natural coordinates
   const T *st;           // [cell][NST]

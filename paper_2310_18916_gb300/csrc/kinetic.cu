@@ -1391,7 +1391,8 @@ __global__ void __launch_bounds__(256) kinetic_general_kernel(const KinArgs<T, S
     const int4 *natcell = A.natcell + (size_t)oct * nc;
     for (int pass = 0; pass < A.n_sweeps; ++pass) {
       for (int col = 0; col < G.ncol; ++col) {
-        const int e0 = A.col_off[col], e1 = A.col_off[col + 1];
+        const int *co = A.col_off + (size_t)oct * A.col_stride;
+        const int e0 = co[col], e1 = co[col + 1];
         for (int e = e0 + warp; e < e1; e += nw) {
           const int c = __ldg(&natcell[e].x);
           const GenCell<T> &g = A.gen[c];

@@ -207,3 +207,17 @@ def test_jump_term_keeps_the_synthetic_solve_stable_on_triangles():
         if o.step() < 1e-8:
             break
     assert o.eps < 1e-8
+
+
+def test_upwind_ordered_sweeps_let_gsis_converge_on_finer_hybrid_meshes():
+    """Each octant sweeps the unstructured cells in its own upwind order (ranked by the cell's
+    projection on the octant's diagonal, colours one above the earlier neighbours'): on a 24 x 24
+    hybrid cavity two passes carry the kinetic step close enough to steady that GSIS converges
+    geometrically (the same order for every octant, a greedy colouring, stalled at eps ~ 3e-2 on
+    32 x 32 and diverged on 64 x 64)."""
+    p = wl.unstructured_cavity(n=24, nv=10, Kn=0.1, lid=0.16, hybrid=0.5)
+    o = Oracle(p, mode=0, n_sweeps=2, nthreads=4)
+    for i in range(30):
+        if o.step() < 1e-8:
+            break
+    assert o.eps < 1e-8 and i < 25
