@@ -374,11 +374,10 @@ BODIES = {
                           R_out=6.0, T_w=0.3, oracle_nv=8),
     # configuration 3 in GSIS: the same sphere and velocity box, reached by Mach continuation
     # 0.5 -> 1 -> ... -> 4 in steps of 0.5 (each stage from the previous converged state; the first
-    # from 300 Euler presteps) with positive face values and the state update relaxed by 0.5, every
-    # stage to eps < 1e-6
+    # from 300 Euler presteps) with positive face values, every stage to eps < 1e-6
     "sphere_gsis": dict(kind="sphere", n=(32, 24, 48), nv=48, vmax=12.0, Ma=4.0, Kn=0.05, first=0.0224, R_out=5.0,
                         clustered=True, mode="continuation", stages=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0),
-                        euler_presteps=300, relax=0.5),
+                        euler_presteps=300),
     # GSIS on an unstructured mesh with simplices: the lid-driven cavity of 64 x 64 squares, the
     # half with x < 1/2 split into two triangles each, extruded one layer (prisms and hexahedra,
     # 6144 cells), 32^3 velocities, Kn 0.1, two colour passes in each octant's upwind order

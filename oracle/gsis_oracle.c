@@ -451,13 +451,6 @@ static void boundary_in(const orc_solver *s, int i, int side, const double *xi, 
   }
 }
 
-static int colour_of(const orc_solver *s, int c, const int sgn[3]) {
-  int i = c % s->ni, j = (c / s->ni) % s->nj, k = c / (s->ni * s->nj);
-  int a = sgn[0] >= 0 ? i : s->ni - 1 - i;
-  int b = sgn[1] >= 0 ? j : s->nj - 1 - j;
-  int d = sgn[2] >= 0 ? k : s->nk - 1 - k;
-  return a + b + d;
-}
 
 static void point_implicit(const orc_solver *s, const double *xi, int i, kin_work *wk, int q) {
   double acc = wk->r[(size_t)q * s->nc + i];
@@ -1545,6 +1538,79 @@ static int init_state_from_f(orc_solver *s) {
   return ORC_OK;
 }
 
+/* The order in which each velocity octant (signs d of its velocities) sweeps the cells
+   (Section 3.2's sweeps in upwind order).  A cell's rank key is the mean over its nodes of
+   ((d_x x) + (d_y y)) + (d_z z): its 8 corners on a structured block, its distinct nodes on an
+   unstructured mesh, summed in that order; ties go by index.  A cell's colour is one more than
+   the largest colour of its face neighbours ranked before it (0 without one), and the octant
+   sweeps colour by colour, in index order within a colour.  On a rectilinear block this is the
+   hyperplane order i' + j' + k' of the octant; on a curved or unstructured mesh it follows the
+   flow, where index-space hyperplanes or a colouring shared by all octants do not. */
+static const double *g_sort_key;
+static int by_key(const void *pa, const void *pb) {
+  int a = *(const int *)pa, b = *(const int *)pb;
+  if (g_sort_key[a] < g_sort_key[b]) return -1;
+  if (g_sort_key[a] > g_sort_key[b]) return 1;
+  return (a > b) - (a < b);
+}
+
+static int sweep_orders(orc_solver *s, const orc_mesh *m) {
+  int nc = s->nc;
+  double *key = (double *)malloc(sizeof(double) * nc);
+  int *rank = (int *)malloc(sizeof(int) * nc), *byk = (int *)malloc(sizeof(int) * nc);
+  int *kc = (int *)malloc(sizeof(int) * nc), *start = (int *)malloc(sizeof(int) * (nc + 1));
+  if (!key || !rank || !byk || !kc || !start) { free(key); free(rank); free(byk); free(kc); free(start); return ORC_E_OOM; }
+  int N0 = s->ni + 1, N1 = s->nj + 1;
+  for (int oct = 0; oct < 8; ++oct) {
+    double d[3] = {oct & 1 ? -1.0 : 1.0, oct & 2 ? -1.0 : 1.0, oct & 4 ? -1.0 : 1.0};
+    for (int c = 0; c < nc; ++c) {
+      double sum = 0.0;
+      int cnt = 0;
+      if (m->ncells > 0) {
+        const int *ids = m->cells + 8 * (size_t)c;
+        for (int t = 0; t < 8; ++t) {
+          int dup = 0;
+          for (int u = 0; u < t; ++u) dup |= ids[u] == ids[t];
+          if (dup) continue;
+          const double *x = m->unodes + 3 * (size_t)ids[t];
+          sum += ((d[0] * x[0]) + (d[1] * x[1])) + (d[2] * x[2]);
+          ++cnt;
+        }
+      } else {
+        int i = c % s->ni, j = (c / s->ni) % s->nj, k = c / (s->ni * s->nj);
+        for (int t = 0; t < 8; ++t) {
+          int I = i + (t & 1), J = j + (t >> 1 & 1), K = k + (t >> 2);
+          const double *x = m->nodes + 3 * ((size_t)I + (size_t)N0 * ((size_t)J + (size_t)N1 * K));
+          sum += ((d[0] * x[0]) + (d[1] * x[1])) + (d[2] * x[2]);
+          ++cnt;
+        }
+      }
+      key[c] = sum / cnt;
+      byk[c] = c;
+    }
+    g_sort_key = key;
+    qsort(byk, (size_t)nc, sizeof(int), by_key);
+    for (int r = 0; r < nc; ++r) rank[byk[r]] = r;
+    int ncol = 0;
+    for (int r = 0; r < nc; ++r) {
+      int c = byk[r], k = 0;
+      for (int side = 0; side < 6; ++side) {
+        int j = s->nb[6 * c + side];
+        if (j >= 0 && rank[j] < r && kc[j] + 1 > k) k = kc[j] + 1;
+      }
+      kc[c] = k;
+      if (k + 1 > ncol) ncol = k + 1;
+    }
+    /* colour by colour, index order within a colour (a counting sort) */
+    for (int k = 0; k <= ncol; ++k) start[k] = 0;
+    for (int c = 0; c < nc; ++c) ++start[kc[c] + 1];
+    for (int k = 0; k < ncol; ++k) start[k + 1] += start[k];
+    for (int c = 0; c < nc; ++c) s->corder[(size_t)oct * nc + start[kc[c]]++] = c;
+  }
+  free(key); free(rank); free(byk); free(kc); free(start);
+  return ORC_OK;
+}
+
 int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const orc_opts *o, const double *W0,
                orc_solver **out) {
   *out = NULL;
@@ -1603,67 +1669,8 @@ int orc_create(const orc_mesh *m, const orc_vgrid *vg, const orc_gas *g, const o
   s->jump = s->o.visc_jump >= 0.0 ? s->o.visc_jump : (s->simplex ? 0.25 : 0.0);
   s->corder = (int *)malloc(sizeof(int) * 8 * (size_t)nc);
   if (!s->corder) { orc_destroy(s); return ORC_E_OOM; }
-  if (s->colour) {
-    /* unstructured meshes: each octant (signs d of its velocities) ranks the cells by the mean over
-       their distinct nodes of ((d_x x) + (d_y y)) + (d_z z), ties by index, which places a cell
-       after the cells its flow comes from, as the hyperplanes do on a structured block.  A cell's
-       sweep colour is one more than the largest colour of its face neighbours ranked before it (0
-       without one); the octant sweeps colour by colour, in index order within a colour */
-    double *key = (double *)malloc(sizeof(double) * nc);
-    int *rank = (int *)malloc(sizeof(int) * nc), *byk = (int *)malloc(sizeof(int) * nc);
-    int *kc = (int *)malloc(sizeof(int) * nc);
-    if (!key || !rank || !byk || !kc) { free(key); free(rank); free(byk); free(kc); orc_destroy(s); return ORC_E_OOM; }
-    for (int oct = 0; oct < 8; ++oct) {
-      double d[3] = {oct & 1 ? -1.0 : 1.0, oct & 2 ? -1.0 : 1.0, oct & 4 ? -1.0 : 1.0};
-      for (int c = 0; c < nc; ++c) {
-        const int *ids = m->cells + 8 * (size_t)c;
-        double sum = 0.0;
-        int cnt = 0;
-        for (int t = 0; t < 8; ++t) {
-          int dup = 0;
-          for (int u = 0; u < t; ++u) dup |= ids[u] == ids[t];
-          if (dup) continue;
-          const double *x = m->unodes + 3 * (size_t)ids[t];
-          sum += ((d[0] * x[0]) + (d[1] * x[1])) + (d[2] * x[2]);
-          ++cnt;
-        }
-        key[c] = sum / cnt;
-        byk[c] = c;
-      }
-      for (int a = 1; a < nc; ++a) { /* insertion sort by (key, index) */
-        int x = byk[a], b = a;
-        while (b > 0 && (key[byk[b - 1]] > key[x] || (key[byk[b - 1]] == key[x] && byk[b - 1] > x))) {
-          byk[b] = byk[b - 1];
-          --b;
-        }
-        byk[b] = x;
-      }
-      for (int r = 0; r < nc; ++r) rank[byk[r]] = r;
-      int ncol = 0;
-      for (int r = 0; r < nc; ++r) {
-        int c = byk[r], k = 0;
-        for (int side = 0; side < 6; ++side) {
-          int j = s->nb[6 * c + side];
-          if (j >= 0 && rank[j] < r && kc[j] + 1 > k) k = kc[j] + 1;
-        }
-        kc[c] = k;
-        if (k + 1 > ncol) ncol = k + 1;
-      }
-      int t = 0;
-      for (int col = 0; col < ncol; ++col)
-        for (int i = 0; i < nc; ++i)
-          if (kc[i] == col) s->corder[(size_t)oct * nc + t++] = i;
-    }
-    free(key); free(rank); free(byk); free(kc);
-  } else {
-    int ncol = s->ni + s->nj + s->nk - 2;
-    for (int oct = 0; oct < 8; ++oct) {
-      int sgn[3] = {oct & 1 ? -1 : 1, oct & 2 ? -1 : 1, oct & 4 ? -1 : 1}, t = 0;
-      for (int col = 0; col < ncol; ++col)
-        for (int i = 0; i < nc; ++i)
-          if (colour_of(s, i, sgn) == col) s->corder[(size_t)oct * nc + t++] = i;
-    }
-  }
+  rc = sweep_orders(s, m);
+  if (rc) { orc_destroy(s); return rc; }
   set_maxwellian(s, W0);
   rc = init_state_from_f(s);
   if (rc) { orc_destroy(s); return rc; }

@@ -1130,6 +1130,84 @@ static int build_general(gsis_solver *s, const gsis_mesh *m) {
   return GSIS_OK;
 }
 
+// The kinetic sweeps of general meshes, per velocity octant (signs d): the cells ranked by the
+// mean over their nodes of ((d_x x) + (d_y y)) + (d_z z) (a structured cell's 8 corners, an
+// unstructured cell's distinct nodes, summed in that order), ties by index, which places a cell
+// after the cells its flow comes from.  A cell's colour is one more than the largest colour of
+// its face neighbours ranked before it (0 without one): a colour's cells share no face, and the
+// octant sweeps colour by colour, in index order within a colour, from per-octant offsets
+// (col_stride).  On curved blocks the index-space hyperplanes do not follow the flow (near a
+// sphere's poles they run across it, and GSIS there grew instead of converging), and a greedy
+// colouring shared by every octant carries information one cell against the flow per pass.
+static void octant_sweeps(gsis_solver *s, const gsis_mesh *m) {
+  const int nc = (int)s->nc;
+  KinGeom &g = s->kg;
+  std::vector<std::vector<int>> korder(8), koff(8);
+  int kmax = 0;
+  std::vector<double> pkey(nc);
+  std::vector<int> byk(nc), rank(nc), kc(nc);
+  const size_t N0 = (size_t)m->ni + 1, N1 = (size_t)m->nj + 1;
+  for (int oct = 0; oct < 8; ++oct) {
+    const double d[3] = {oct & 1 ? -1.0 : 1.0, oct & 2 ? -1.0 : 1.0, oct & 4 ? -1.0 : 1.0};
+    for (int c = 0; c < nc; ++c) {
+      double sum = 0.0;
+      int cnt = 0;
+      if (m->ncells > 0) {
+        const int *ids = m->cells + 8 * (size_t)c;
+        for (int t = 0; t < 8; ++t) {
+          bool dup = false;
+          for (int u = 0; u < t; ++u) dup = dup || ids[u] == ids[t];
+          if (dup) continue;
+          const double *x = m->unodes + 3 * (size_t)ids[t];
+          sum += ((d[0] * x[0]) + (d[1] * x[1])) + (d[2] * x[2]);
+          ++cnt;
+        }
+      } else {
+        const int i = c % m->ni, j = (c / m->ni) % m->nj, k = c / (m->ni * m->nj);
+        for (int t = 0; t < 8; ++t) {
+          const size_t I = i + (t & 1), J = j + (t >> 1 & 1), K = k + (t >> 2);
+          const double *x = m->nodes + 3 * (I + N0 * (J + N1 * K));
+          sum += ((d[0] * x[0]) + (d[1] * x[1])) + (d[2] * x[2]);
+          ++cnt;
+        }
+      }
+      pkey[c] = sum / cnt;
+      byk[c] = c;
+    }
+    std::sort(byk.begin(), byk.end(), [&](int a, int b) { return pkey[a] < pkey[b] || (pkey[a] == pkey[b] && a < b); });
+    for (int r = 0; r < nc; ++r) rank[byk[r]] = r;
+    int nk = 0;
+    for (int r = 0; r < nc; ++r) {
+      const int c = byk[r];
+      int k = 0;
+      for (int side = 0; side < 6; ++side) {
+        const int nb = s->gnb[6 * (size_t)c + side];
+        if (nb >= 0 && rank[nb] < r) k = std::max(k, kc[nb] + 1);
+      }
+      kc[c] = k;
+      nk = std::max(nk, k + 1);
+    }
+    std::vector<int> cnt(nk + 1, 0);
+    for (int c = 0; c < nc; ++c) ++cnt[kc[c] + 1];
+    for (int k = 0; k < nk; ++k) cnt[k + 1] += cnt[k];
+    koff[oct] = cnt;
+    korder[oct].assign(nc, 0);
+    for (int c = 0; c < nc; ++c) korder[oct][cnt[kc[c]]++] = c;  // index order within a colour
+    kmax = std::max(kmax, nk);
+  }
+  s->col_stride = kmax + 1;
+  s->col_off.assign((size_t)8 * s->col_stride, 0);
+  g.ncol = kmax;
+  g.maxcol = 0;
+  s->natcell.assign((size_t)8 * nc, int4{0, 0, 0, 0});
+  for (int oct = 0; oct < 8; ++oct) {
+    const int nk = (int)koff[oct].size() - 1;
+    for (int k = 0; k <= kmax; ++k) s->col_off[(size_t)oct * s->col_stride + k] = koff[oct][std::min(k, nk)];
+    for (int k = 0; k < nk; ++k) g.maxcol = std::max(g.maxcol, koff[oct][k + 1] - koff[oct][k]);
+    for (int e = 0; e < nc; ++e) s->natcell[(size_t)oct * nc + e] = int4{korder[oct][e], 0, 0, 0};
+  }
+}
+
 // Unstructured meshes: every cell a hexahedron of node ids (other shapes repeat ids), its six
 // sides with corners in cyclic order; a side's geometry as on structured blocks (a quadrilateral:
 // half the cross product of its diagonals, centre the corner mean), a side with three distinct
@@ -1420,66 +1498,7 @@ static int setup_unstructured_mesh(gsis_solver *s, const gsis_mesh *m) {
   s->colcells = order;
   s->mcol_off = s->col_off;
   s->ncol0 = s->col_off[1];
-  // The kinetic sweeps, per octant (signs d of its velocities): the cells ranked by the mean over
-  // their distinct nodes of ((d_x x) + (d_y y)) + (d_z z), ties by index, which places a cell
-  // after the cells its flow comes from, as the hyperplanes do on a structured block.  A cell's
-  // colour is one more than the largest colour of its face neighbours ranked before it (0 without
-  // one): a colour's cells share no face, and the octant sweeps colour by colour, in index order
-  // within a colour.  (Greedy colours, the same for every octant, leave a pass carrying
-  // information one cell against the flow: GSIS stalls or diverges on fine meshes.)
-  std::vector<std::vector<int>> korder(8), koff(8);
-  int kmax = 0;
-  std::vector<double> pkey(nc);
-  std::vector<int> byk(nc), rank(nc), kc(nc);
-  for (int oct = 0; oct < 8; ++oct) {
-    const double d[3] = {oct & 1 ? -1.0 : 1.0, oct & 2 ? -1.0 : 1.0, oct & 4 ? -1.0 : 1.0};
-    for (int c = 0; c < nc; ++c) {
-      const int *ids = m->cells + 8 * (size_t)c;
-      double sum = 0.0;
-      int cnt = 0;
-      for (int t = 0; t < 8; ++t) {
-        bool dup = false;
-        for (int u = 0; u < t; ++u) dup = dup || ids[u] == ids[t];
-        if (dup) continue;
-        const double *x = m->unodes + 3 * (size_t)ids[t];
-        sum += ((d[0] * x[0]) + (d[1] * x[1])) + (d[2] * x[2]);
-        ++cnt;
-      }
-      pkey[c] = sum / cnt;
-      byk[c] = c;
-    }
-    std::sort(byk.begin(), byk.end(), [&](int a, int b) { return pkey[a] < pkey[b] || (pkey[a] == pkey[b] && a < b); });
-    for (int r = 0; r < nc; ++r) rank[byk[r]] = r;
-    int nk = 0;
-    for (int r = 0; r < nc; ++r) {
-      const int c = byk[r];
-      int k = 0;
-      for (int side = 0; side < 6; ++side) {
-        const int nb = s->gnb[6 * (size_t)c + side];
-        if (nb >= 0 && rank[nb] < r) k = std::max(k, kc[nb] + 1);
-      }
-      kc[c] = k;
-      nk = std::max(nk, k + 1);
-    }
-    std::vector<int> cnt(nk + 1, 0);
-    for (int c = 0; c < nc; ++c) ++cnt[kc[c] + 1];
-    for (int k = 0; k < nk; ++k) cnt[k + 1] += cnt[k];
-    koff[oct] = cnt;
-    korder[oct].assign(nc, 0);
-    for (int c = 0; c < nc; ++c) korder[oct][cnt[kc[c]]++] = c;  // index order within a colour
-    kmax = std::max(kmax, nk);
-  }
-  s->col_stride = kmax + 1;
-  s->col_off.assign((size_t)8 * s->col_stride, 0);
-  g.ncol = kmax;
-  g.maxcol = 0;
-  s->natcell.assign((size_t)8 * nc, int4{0, 0, 0, 0});
-  for (int oct = 0; oct < 8; ++oct) {
-    const int nk = (int)koff[oct].size() - 1;
-    for (int k = 0; k <= kmax; ++k) s->col_off[(size_t)oct * s->col_stride + k] = koff[oct][std::min(k, nk)];
-    for (int k = 0; k < nk; ++k) g.maxcol = std::max(g.maxcol, koff[oct][k + 1] - koff[oct][k]);
-    for (int e = 0; e < nc; ++e) s->natcell[(size_t)oct * nc + e] = int4{korder[oct][e], 0, 0, 0};
-  }
+  octant_sweeps(s, m);
   return GSIS_OK;
 }
 
@@ -1626,6 +1645,7 @@ static int setup_mesh(gsis_solver *s, const gsis_mesh *m) {
     for (int side = 0; side < 6; ++side) g.wall_base[side] = -1;
     const int rc = build_general(s, m);
     if (rc) return rc;
+    octant_sweeps(s, m);
   }
   // red/black cell lists of the synthetic solve's sweeps
   s->colcells.clear();

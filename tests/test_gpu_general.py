@@ -76,7 +76,10 @@ def test_cylinder_ogrid_reduced_precision(precision, rel):
     p = wl.cylinder(n_r=6, n_theta=12, nv=16, R=0.5, R_out=3.0, Ma=0.5, Kn=0.2)
     g, o, out = run_pair(p, precision, 3, 2)
     for it, (Wg, Wo) in enumerate(out):
-        scaled_close(Wg, Wo, rel, f"{precision} cylinder W, step {it}")
+        # rho and temperatures per column, the velocity as one vector (u_z of this 2D flow is
+        # rounding noise, which a per-column scale would compare instead of the flow)
+        scaled_close(Wg[:, [0, 4, 5]], Wo[:, [0, 4, 5]], rel, f"{precision} cylinder rho, T, step {it}")
+        scaled_close(Wg[:, 1:4], Wo[:, 1:4], rel, f"{precision} cylinder u, step {it}", vector=True)
 
 
 def test_cylinder_pseudo_time_step_fp64():

@@ -168,7 +168,9 @@ def cylinder_free_molecular():
 def test_free_molecular_cylinder_drag():
     """At Kn = 1e6 the kinetic iteration on a cylinder O-grid approaches collisionless flow: the
     force on the body matches the discrete free-molecular force above (1e-4; the scheme's own
-    error is ~1e-5 on this grid), along the stream, with no side force."""
+    error is ~1e-5 on this grid), along the stream, with no side force (below 1e-9 of the drag
+    after 15 two-pass steps: the mirrored octants sweep in mirrored upwind orders up to the
+    rounding of the cells' projections)."""
     p = cylinder_free_molecular()
     o = Oracle(p, mode=1, n_sweeps=2, kin_inv_dt=2.0)
     S = o.geometry()[2].reshape(32, 10, 6, 3)[:, 0, 0, :]
@@ -177,7 +179,7 @@ def test_free_molecular_cylinder_drag():
     _, side, _, fl = o.wall()
     F = fl[side == 0, 1:4].sum(axis=0)
     assert exact[0] > 0 and abs(F[0] - exact[0]) < 1e-4 * exact[0]
-    assert abs(F[1]) < 1e-10 * exact[0] and abs(exact[1]) < 1e-12 * exact[0]
+    assert abs(F[1]) < 1e-9 * exact[0] and abs(exact[1]) < 1e-12 * exact[0]
 
 
 def test_free_molecular_sphere_drag():
