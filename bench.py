@@ -383,6 +383,12 @@ BODIES = {
     # 6144 cells), 32^3 velocities, Kn 0.1, two colour passes in each octant's upwind order
     "hybrid_cavity": dict(kind="hybrid", n=64, nv=32, vmax=5.0, lid=0.16, Kn=0.1, hybrid=0.5, mode="gsis",
                           euler_presteps=0, n_sweeps=2),
+    # configuration 4 in GSIS: the capsule and its cold Rykov wall reached by Mach continuation
+    # 1 -> 2 -> ... -> 10 (the velocity box of each stage from its own Mach number), positive face
+    # values, each stage to eps < 1e-6 or until eps stops falling; reference area pi (radius 1)
+    "capsule_gsis": dict(kind="capsule", n=(50, 40, 50), nv=48, vmax=None, Ma=10.0, Kn=0.01, first=None, R_out=6.0,
+                         T_w=0.3, mode="continuation", stages=(1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0),
+                         euler_presteps=300, ref_area=3.141592653589793),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }
@@ -568,7 +574,7 @@ def run_body_continuation(args):
             wall = time.perf_counter() - t0
             phase, nsteps, launches = s.profile(False)
             U = float(np.linalg.norm(p.wall_u[1]))
-            loads = s.wall_loads([0], (1.0, 0.0, 0.0), 1.0, U, np.pi * 0.5 ** 2)
+            loads = s.wall_loads([0], (1.0, 0.0, 0.0), 1.0, U, b.get("ref_area", np.pi * 0.5 ** 2))
             W = s.W()
             s.close()
             t_all += wall
@@ -577,17 +583,17 @@ def run_body_continuation(args):
                            "phase_ms_per_step": {k: v / max(nsteps, 1) for k, v in zip(PHASES, phase)},
                            "C_D": float(loads[4]), "C_H": float(loads[5]), "rho_min": float(W[:, 0].min())})
     if "error" in stages[-1]:
-        print(json.dumps({"metric": "phase-space updates/s (GSIS outer step, sphere O-grid, Mach continuation)",
+        print(json.dumps({"metric": f"phase-space updates/s (GSIS outer step, {b['kind']} O-grid, Mach continuation)",
                           "value": None, "unit": UNIT, "failed_stage": stages[-1], "stages": stages,
                           "config": {"workload": f"{p.name}: {b}", "precision": args.precision}}))
         return 1
     last = stages[-1]
-    pts = p.ncells * p.nvel
+    pts = p.ncells * p.nvel * (2 if p.model == wl.RYKOV else 1)   # both reduced VDFs for Rykov
     peak, peak_kind, _ = measured_peaks()
     sbytes = {"f32": 4, "f64": 8, "bf16": 2}[args.precision]
     kin_ms = last["phase_ms_per_step"]["kinetic"]
     line = {
-        "metric": "phase-space updates/s (GSIS outer step, sphere O-grid, Mach continuation)",
+        "metric": f"phase-space updates/s (GSIS outer step, {b['kind']} O-grid, Mach continuation)",
         "value": pts / (last["ms_per_step_device"] / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": last["steps"], "warmup": 0, "ms_per_step": last["ms_per_step_device"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32",
