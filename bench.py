@@ -384,10 +384,12 @@ BODIES = {
     "hybrid_cavity": dict(kind="hybrid", n=64, nv=32, vmax=5.0, lid=0.16, Kn=0.1, hybrid=0.5, mode="gsis",
                           euler_presteps=0, n_sweeps=2),
     # configuration 4 in GSIS: the capsule and its cold Rykov wall reached by Mach continuation
-    # 1 -> 2 -> ... -> 10 (the velocity box of each stage from its own Mach number), positive face
-    # values, each stage to eps < 1e-6 or until eps stops falling; reference area pi (radius 1)
+    # 1 -> 2 -> 2.5 -> ... -> 5 -> 6 -> ... -> 10 (the velocity box of each stage from its own Mach
+    # number; 2 -> 3 in one stage diverges), positive face values, each stage to eps < 1e-6 or until
+    # eps stops falling; reference area pi (radius 1)
     "capsule_gsis": dict(kind="capsule", n=(50, 40, 50), nv=48, vmax=None, Ma=10.0, Kn=0.01, first=None, R_out=6.0,
-                         T_w=0.3, mode="continuation", stages=(1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0),
+                         T_w=0.3, mode="continuation",
+                         stages=(1.0, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0),
                          euler_presteps=300, ref_area=3.141592653589793),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
