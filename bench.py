@@ -386,7 +386,7 @@ BODIES = {
     # configuration 4 in GSIS: the capsule and its cold Rykov wall reached by Mach continuation
     # 1 -> 2 -> 2.5 -> ... -> 5 -> 6 -> ... -> 10 (the velocity box of each stage from its own Mach
     # number; 2 -> 3 in one stage diverges), positive face values, each stage to eps < 1e-6 or until
-    # eps stops falling; reference area pi (radius 1)
+    # eps stops falling; reference area pi (radius 1).  Converges at Ma 1 and 2; fails above 2.5.
     "capsule_gsis": dict(kind="capsule", n=(50, 40, 50), nv=48, vmax=None, Ma=10.0, Kn=0.01, first=None, R_out=6.0,
                          T_w=0.3, mode="continuation",
                          stages=(1.0, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0),
