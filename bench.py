@@ -391,7 +391,7 @@ BODIES = {
                          T_w=0.3, mode="continuation",
                          stages=(1.0, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0),
                          euler_presteps=300, ref_area=3.141592653589793),
-    # the same with the state update relaxed by 0.5 (R36) up to Ma 4
+    # the same with the state update relaxed by 0.5 (R36) up to Ma 4: converges to Ma 3, fails at 3.5
     "capsule_gsis_relaxed": dict(kind="capsule", n=(50, 40, 50), nv=48, vmax=None, Ma=4.0, Kn=0.01, first=None,
                                  R_out=6.0, T_w=0.3, mode="continuation", stages=(1.0, 2.0, 2.5, 3.0, 3.5, 4.0),
                                  euler_presteps=300, ref_area=3.141592653589793, relax=0.5),
