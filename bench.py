@@ -394,7 +394,7 @@ BODIES = {
     # the same with the state update relaxed by 0.5 (R36) up to Ma 4: converges to Ma 3, fails at 3.5
     "capsule_gsis_relaxed": dict(kind="capsule", n=(50, 40, 50), nv=48, vmax=None, Ma=4.0, Kn=0.01, first=None,
                                  R_out=6.0, T_w=0.3, mode="continuation", stages=(1.0, 2.0, 2.5, 3.0, 3.5, 4.0),
-                                 euler_presteps=300, ref_area=3.141592653589793, relax=0.5, stage_presteps=0),
+                                 euler_presteps=300, ref_area=3.141592653589793, relax=0.5),
     # the sphere at profiling size: 16 x 12 x 24 cells, 32^3 velocities (151M points)
     "sphere_small": dict(kind="sphere", n=(16, 12, 24), nv=32, vmax=12.0, Ma=4.0, Kn=0.05, first=0.05, R_out=5.0),
 }
